@@ -1,0 +1,216 @@
+/*
+ * polylab.h -- C ABI of the B300-native sparse-monomial engine and the
+ * affine-normal direction (libpolylab.so, CUDA kernels for sm_103a).
+ *
+ * Data model (paper Sec. 2, Table "apisignature"; Sec. 3.2): a polynomial is
+ * (vars.id, coef, pow): n unique 64-bit variable ids, an n_terms x n exponent
+ * matrix (uint8, row-major) and a coefficient vector (double).  Repeated
+ * exponent rows are allowed and mean a sum.
+ *
+ * Conventions shared by every call
+ *   - Pointers documented as DEVICE point to memory of the current CUDA device
+ *     and are owned by the caller; pointers documented as HOST are host memory.
+ *   - Work is enqueued on `stream` (a cudaStream_t; NULL is the legacy default
+ *     stream) and is asynchronous unless a call says it synchronises.
+ *   - Scratch memory is taken from the stream-ordered allocator
+ *     (cudaMallocAsync/cudaFreeAsync on `stream`) and released before the call
+ *     returns, in stream order.
+ *   - Every call returns a polylab_status.  Argument and launch errors are
+ *     statuses; a call never aborts, traps or exits.  Per-point numerical
+ *     failures of the affine-normal direction are flags in polylab_an_info,
+ *     not errors.
+ *   - A call that fails with POLYLAB_ERR_CUDA leaves the message of the CUDA
+ *     error in polylab_last_error() (per thread).
+ */
+#ifndef POLYLAB_H
+#define POLYLAB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* polylab_stream; /* == cudaStream_t */
+
+typedef enum {
+  POLYLAB_OK = 0,
+  POLYLAB_ERR_INVALID_ARG = 1,   /* null pointer, negative size, bad enum, n mismatch */
+  POLYLAB_ERR_EXP_OVERFLOW = 2,  /* a product exponent exceeds 255 */
+  POLYLAB_ERR_DUP_VAR_ID = 3,    /* an operand lists one variable id twice */
+  POLYLAB_ERR_OOM = 4,           /* scratch or output allocation failed */
+  POLYLAB_ERR_CUDA = 5,          /* a CUDA runtime/driver call or launch failed */
+  POLYLAB_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up */
+  POLYLAB_ERR_UNSUPPORTED = 7    /* outside this library's stated limits */
+} polylab_status;
+
+/* Human-readable name of a status. */
+const char* polylab_status_string(polylab_status s);
+/* Message of the last CUDA error seen by a call on this thread ("" if none). */
+const char* polylab_last_error(void);
+
+/* ------------------------------------------------------------------ data model */
+
+typedef struct {
+  int32_t n_vars;           /* n >= 1 */
+  const uint64_t* var_ids;  /* HOST, n unique ids (Sec. 3.2 vars.id)            */
+  int64_t n_terms;          /* m >= 0                                           */
+  const uint8_t* exps;      /* DEVICE, m x n row-major exponents                */
+  const double* coef;       /* DEVICE, m coefficients                           */
+} polylab_poly;
+
+/* Output of simplify/mul.  The caller sets var_ids (HOST buffer with room for
+ * the result's variables: p.n_vars for simplify, a.n_vars + b.n_vars for mul);
+ * the call fills n_vars, var_ids, n_terms and sets exps/coef to DEVICE memory
+ * obtained from the caller's allocator. */
+typedef struct {
+  int32_t n_vars;
+  uint64_t* var_ids;
+  int64_t n_terms;
+  uint8_t* exps;            /* n_terms x n_vars row-major, from alloc */
+  double* coef;             /* n_terms, from alloc                    */
+} polylab_poly_out;
+
+/* Caller-owned output allocation: return `bytes` of DEVICE memory usable in
+ * stream order on the call's stream, or NULL on failure (-> POLYLAB_ERR_OOM).
+ * Called at most twice per call, never with bytes == 0. */
+typedef void* (*polylab_alloc_fn)(size_t bytes, void* ctx);
+
+/* --------------------------------------------------------------- simplify / mul */
+
+/* simplify(p, zeroprec) (Sec. 2, Table "coresemantics"; Sec. 6.3): merge the
+ * coefficients of equal exponent rows, drop merged terms with
+ * |c| <= zeroprec (zeroprec = 0 drops exact zeros), emit the terms in the
+ * engine's canonical monomial order -- total degree, then ascending
+ * lexicographic order of the reversed exponent row, the order of Polylab's
+ * monolist (Sec. 3.1).  Variables keep the input's order and ids.
+ * Exponents of the result are bit-exact; coefficient sums are FP64 in an
+ * order of the library's choosing.
+ * Synchronises `stream` once (to size the output).
+ * Limit: the number of distinct monomials of degree <= max row degree in n
+ * variables must be below 2^128 (POLYLAB_ERR_UNSUPPORTED otherwise), and
+ * n_terms < 2^31. */
+polylab_status polylab_simplify(const polylab_poly* p, double zeroprec, polylab_poly_out* out,
+                                polylab_alloc_fn alloc, void* alloc_ctx, polylab_stream stream);
+
+/* a * b (Sec. 2 "mtimes"; Sec. 3.2 alignment): the operands' variable spaces
+ * are aligned by id first -- the result's variables are the union of both id
+ * sets in ascending id order -- then every pair of terms is expanded
+ * (exponents added, coefficients multiplied) and the expansion is simplified
+ * as by polylab_simplify.  POLYLAB_ERR_EXP_OVERFLOW if an exponent sum
+ * exceeds 255; POLYLAB_ERR_DUP_VAR_ID if an operand repeats an id.
+ * Synchronises `stream` once.  Limit: n_terms(a) * n_terms(b) < 2^31. */
+polylab_status polylab_mul(const polylab_poly* a, const polylab_poly* b, double zeroprec,
+                           polylab_poly_out* out, polylab_alloc_fn alloc, void* alloc_ctx,
+                           polylab_stream stream);
+
+/* a + b (Table "coresemantics" "plus"; Sec. 3.2 aligns the variable spaces of
+ * operands before they combine): variables aligned by id as for polylab_mul (union in
+ * ascending id order), the terms of both operands concatenated and
+ * simplified as by polylab_simplify.  Synchronises `stream` once.
+ * Limit: n_terms(a) + n_terms(b) < 2^31. */
+polylab_status polylab_add(const polylab_poly* a, const polylab_poly* b, double zeroprec,
+                           polylab_poly_out* out, polylab_alloc_fn alloc, void* alloc_ctx,
+                           polylab_stream stream);
+
+/* ------------------------------------------------------------------------ plans */
+
+/* A plan is the device-resident preprocessed form of one polynomial (its term
+ * list and, on request, the derived-coefficient matrix of the tensor-core
+ * derivative forms).  Creating one synchronises `stream` once; a plan may be
+ * passed to any later eval/affine call on the same device and is read-only
+ * there.  Passing NULL as the plan makes those calls build a temporary one.
+ * Limit of the term list: at most 8 active variables per term and n < 65536
+ * (POLYLAB_ERR_UNSUPPORTED otherwise). */
+typedef struct polylab_plan polylab_plan;
+
+#define POLYLAB_PLAN_TERMS 0u  /* term list only                         */
+#define POLYLAB_PLAN_GEMM  1u  /* also the derived-coefficient matrix    */
+
+polylab_status polylab_plan_create(const polylab_poly* p, uint32_t what, polylab_stream stream,
+                                   polylab_plan** plan);
+/* Frees the plan's memory after all work already enqueued on `stream`. */
+polylab_status polylab_plan_destroy(polylab_plan* plan, polylab_stream stream);
+/* Closure-set size K (rows of the derived-coefficient matrix) or -1. */
+int64_t polylab_plan_closure_size(const polylab_plan* plan);
+
+/* ------------------------------------------------------------ derivatives at points */
+
+typedef enum {
+  POLYLAB_FP64 = 0,    /* FP64 throughout (direct per-term sums)                          */
+  POLYLAB_TF32X3 = 1,  /* monomial x derived-coefficient contraction on tensor cores,
+                          3xTF32 split operands, FP32 accumulation                         */
+  POLYLAB_BF16 = 2,    /* same contraction in BF16 with FP32 accumulation, per-column
+                          coefficient scaling                                              */
+  POLYLAB_FP32 = 3     /* FP32 direct per-term sums (affine normal: FP32 derivative sums,
+                          FP64 Cholesky / log-det / normalisation)                         */
+} polylab_precision;
+
+/* f, grad f and the Hessian at P points (Sec. 3.3 differentiation and eval;
+ * batched).  X: DEVICE, P x n row-major, in the polynomial's variable order.
+ * order = 0, 1 or 2 selects which of F, G, H are written.
+ * F: DEVICE P; G: DEVICE P x n (order >= 1); H: DEVICE P x n x n, full
+ * symmetric matrix (order 2).  Outputs are overwritten.  With POLYLAB_FP64
+ * every output agrees with the plain definition within ~1e-15 of the sum of
+ * |term contributions|; reduced forms carry their stated error. */
+polylab_status polylab_eval_derivs(const polylab_poly* p, const polylab_plan* plan, const double* X,
+                                   int64_t P, int32_t order, polylab_precision prec, double* F,
+                                   double* G, double* H, polylab_stream stream);
+
+/* ------------------------------------------------------------ affine normal (Sec. 5) */
+
+typedef enum { POLYLAB_MF_EXACT = 0, POLYLAB_MF_STOCHASTIC = 1 } polylab_an_method;
+typedef enum {
+  POLYLAB_PRECOND_JACOBI = 0,  /* |diag(H)| + r of the ambient Hessian, projected      */
+  POLYLAB_PRECOND_NONE = 1,
+  POLYLAB_PRECOND_MLP = 2      /* learned diagonal-plus-low-rank (needs mlp_weights)   */
+} polylab_precond;
+
+/* Options (Sec. 5, Table "affineopts").  Paper defaults: method MF_EXACT,
+ * regularization 1e-6, num_probes 8, krylov_tol 1e-4, krylov_maxit 40. */
+typedef struct {
+  polylab_an_method method;
+  double regularization;     /* r: H_T + r I in every tangent solve                 */
+  int32_t num_probes;        /* q, stochastic only                                  */
+  double krylov_tol;         /* stop when |residual| <= tol |rhs|, stochastic only  */
+  int32_t krylov_maxit;      /* stochastic only                                     */
+  int32_t assume_nonzero_x;  /* skip the relative zero-gradient check               */
+  uint64_t seed;             /* probe generator seed, stochastic only               */
+  polylab_precision prec;    /* POLYLAB_FP64 or POLYLAB_FP32                        */
+  polylab_precond precond;   /* stochastic only                                     */
+  const void* mlp_weights;   /* DEVICE, POLYLAB_PRECOND_MLP only                    */
+} polylab_an_opts;
+
+void polylab_an_opts_default(polylab_an_opts* o);
+
+#define POLYLAB_FLAG_ZERO_GRAD 1    /* |grad f| = 0 (or relatively negligible)    */
+#define POLYLAB_FLAG_NOT_PD 2       /* Cholesky of H_T + r I failed              */
+#define POLYLAB_FLAG_KRYLOV_MAXIT 4 /* a Krylov solve stopped at krylov_maxit    */
+
+/* Per-point diagnostics (Sec. 5 "info": gradient norm and work counters). */
+typedef struct {
+  double grad_norm;
+  double logdet;       /* log det(H_T + r I), exact method (NaN for stochastic) */
+  int32_t flags;
+  int32_t hv_evals;    /* exact: n; stochastic: Krylov iterations + 1           */
+  int32_t third_evals; /* exact: n - 1; stochastic: q                           */
+  int32_t krylov_iters;
+} polylab_an_info;
+
+/* The affine-normal direction at P points (Sec. 5):
+ *   e = g/|g|, Q = [Q_T, e], H_T = Q_T^T H Q_T + r I, h = Q_T^T H e,
+ *   a_i = tr(H_T^{-1} d_{t_i} H_T), tau = H_T^{-1}(h - |g|/(n+1) a),
+ *   D = nu = Q_T tau - e   (the paper's d: nu . e = -1, not unit length).
+ * MF_EXACT forms a with the exact trace; MF_STOCHASTIC with a Hutchinson
+ * estimate over num_probes probes and preconditioned CG solves.
+ * X: DEVICE P x n.  D: DEVICE P x n.  Dunit: DEVICE P x n or NULL (nu/|nu|).
+ * info: DEVICE array of P records or NULL.  Flagged points get NaN rows. */
+polylab_status polylab_affine_normal(const polylab_poly* p, const polylab_plan* plan, const double* X,
+                                     int64_t P, const polylab_an_opts* opts, double* D, double* Dunit,
+                                     polylab_an_info* info, polylab_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* POLYLAB_H */

@@ -56,22 +56,26 @@ def align(ids_a, ids_b):
 
 
 def _lift(exps, cols, n):
-    out = np.zeros((exps.shape[0], n), dtype=np.int64)
+    out = np.zeros((exps.shape[0], n), dtype=np.uint16)
     out[:, cols] = exps
     return out
 
 
-def simplify_rows(exps_i64: np.ndarray, coef: np.ndarray, zeroprec: float = 0.0):
+def simplify_rows(rows: np.ndarray, coef: np.ndarray, zeroprec: float = 0.0):
     """Merge equal rows (coefficients summed in input order), drop |c| <= zeroprec,
     return rows in canonical order.  Also returns sum |contributions| per merged
     row, the error scale for comparisons.  Raises ExponentOverflow above 255."""
-    exps_i64 = np.asarray(exps_i64, dtype=np.int64)
-    n = exps_i64.shape[1]
-    if exps_i64.size and exps_i64.max() > 255:
+    rows = np.asarray(rows)
+    n = rows.shape[1]
+    if rows.size and int(rows.max()) > 255:
         raise ExponentOverflow("exponent above 255")
-    if exps_i64.shape[0] == 0:
+    if rows.shape[0] == 0:
         return np.zeros((0, n), np.uint8), np.zeros(0), np.zeros(0)
-    uniq, inv = np.unique(exps_i64, axis=0, return_inverse=True)
+    # group equal rows: each uint8 row is compared as one n-byte string (np.unique sorts them)
+    rows8 = np.ascontiguousarray(rows, dtype=np.uint8)
+    _, first, inv = np.unique(rows8.view(np.dtype((np.void, n))).reshape(-1), return_index=True,
+                              return_inverse=True)
+    uniq = rows8[first]
     inv = inv.reshape(-1)
     # np.bincount adds the weights in index order, i.e. in input order per group
     c = np.bincount(inv, weights=coef, minlength=uniq.shape[0])
@@ -79,12 +83,12 @@ def simplify_rows(exps_i64: np.ndarray, coef: np.ndarray, zeroprec: float = 0.0)
     keep = np.abs(c) > zeroprec
     uniq, c, s = uniq[keep], c[keep], s[keep]
     o = canonical_order(uniq)
-    return uniq[o].astype(np.uint8), c[o], s[o]
+    return uniq[o], c[o], s[o]
 
 
 def simplify(var_ids, exps, coef, zeroprec: float = 0.0):
     """Sec. 2 ``simplify``: same variables, merged monomials, small terms removed."""
-    e, c, s = simplify_rows(np.asarray(exps, dtype=np.int64), np.asarray(coef, dtype=np.float64), zeroprec)
+    e, c, s = simplify_rows(np.asarray(exps), np.asarray(coef, dtype=np.float64), zeroprec)
     return np.asarray(var_ids, dtype=np.uint64), e, c, s
 
 
@@ -94,8 +98,8 @@ def mul(a, b, zeroprec: float = 0.0):
     multiply), then simplify.  Pairs are enumerated i-major, j-minor."""
     ids, ca_cols, cb_cols = align(a[0], b[0])
     n = len(ids)
-    ea = _lift(np.asarray(a[1], dtype=np.int64), ca_cols, n)
-    eb = _lift(np.asarray(b[1], dtype=np.int64), cb_cols, n)
+    ea = _lift(np.asarray(a[1]), ca_cols, n)
+    eb = _lift(np.asarray(b[1]), cb_cols, n)
     ma, mb = ea.shape[0], eb.shape[0]
     rows = (ea[:, None, :] + eb[None, :, :]).reshape(ma * mb, n)
     coefs = (np.asarray(a[2], np.float64)[:, None] * np.asarray(b[2], np.float64)[None, :]).reshape(-1)
@@ -107,8 +111,7 @@ def add(a, b, zeroprec: float = 0.0):
     """Sum of two polynomials: align ids, concatenate terms, simplify (Sec. 3.2)."""
     ids, ca_cols, cb_cols = align(a[0], b[0])
     n = len(ids)
-    rows = np.concatenate([_lift(np.asarray(a[1], np.int64), ca_cols, n),
-                           _lift(np.asarray(b[1], np.int64), cb_cols, n)])
+    rows = np.concatenate([_lift(np.asarray(a[1]), ca_cols, n), _lift(np.asarray(b[1]), cb_cols, n)])
     coefs = np.concatenate([np.asarray(a[2], np.float64), np.asarray(b[2], np.float64)])
     e, c, s = simplify_rows(rows, coefs, zeroprec)
     return ids, e, c, s
@@ -121,8 +124,8 @@ def coefficient_of(a, b, target_row_merged: np.ndarray) -> tuple[float, float]:
     full-size products."""
     ids, ca_cols, cb_cols = align(a[0], b[0])
     n = len(ids)
-    ea = _lift(np.asarray(a[1], np.int64), ca_cols, n)
-    eb = _lift(np.asarray(b[1], np.int64), cb_cols, n)
+    ea = _lift(np.asarray(a[1]), ca_cols, n).astype(np.int64)
+    eb = _lift(np.asarray(b[1]), cb_cols, n).astype(np.int64)
     t = np.asarray(target_row_merged, dtype=np.int64)
     need = t[None, :] - ea                                  # b-row each a-term needs
     multi: dict[bytes, list[int]] = {}  # b rows may repeat: keep every index

@@ -1,0 +1,123 @@
+// Internal definitions shared by the CUDA translation units of libpolylab.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "polylab.h"
+
+namespace polylab {
+
+// ------------------------------------------------------------------ errors
+
+void set_last_error(const char* where, cudaError_t e);
+
+#define PL_CUDA(call)                                   \
+  do {                                                  \
+    cudaError_t e__ = (call);                           \
+    if (e__ != cudaSuccess) {                           \
+      ::polylab::set_last_error(#call, e__);            \
+      return POLYLAB_ERR_CUDA;                          \
+    }                                                   \
+  } while (0)
+
+#define PL_TRY(expr)                          \
+  do {                                        \
+    polylab_status s__ = (expr);              \
+    if (s__ != POLYLAB_OK) return s__;        \
+  } while (0)
+
+inline polylab_status launch_status(const char* where) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_last_error(where, e);
+    return POLYLAB_ERR_CUDA;
+  }
+  return POLYLAB_OK;
+}
+
+// ------------------------------------------------------------ scratch memory
+// Stream-ordered scratch buffers: freed in stream order when the guard dies.
+
+struct Scratch {
+  cudaStream_t s;
+  std::vector<void*> ptrs;
+  explicit Scratch(cudaStream_t st) : s(st) {}
+  ~Scratch() {
+    for (void* p : ptrs) cudaFreeAsync(p, s);
+  }
+  template <typename T>
+  polylab_status get(T** out, size_t count) {
+    *out = nullptr;
+    if (count == 0) count = 1;
+    void* p = nullptr;
+    cudaError_t e = cudaMallocAsync(&p, count * sizeof(T), s);
+    if (e != cudaSuccess) {
+      set_last_error("cudaMallocAsync", e);
+      cudaGetLastError();
+      return POLYLAB_ERR_OOM;
+    }
+    ptrs.push_back(p);
+    *out = static_cast<T*>(p);
+    return POLYLAB_OK;
+  }
+};
+
+// --------------------------------------------------------------- term list
+// Packed sparse form of one term: at most kMaxSupport active variables, in
+// ascending variable order; unused slots have exp == 0.  32 bytes, so a term
+// is two aligned 16-byte loads.
+
+constexpr int kMaxSupport = 8;
+
+struct __align__(16) Term {
+  double coef;
+  uint16_t var[kMaxSupport];
+  uint8_t exp[kMaxSupport];
+};
+static_assert(sizeof(Term) == 32, "Term layout");
+
+// Device-resident preprocessed polynomial (the opaque polylab_plan).
+struct GemmOperand;  // defined with the tensor-core contraction
+
+}  // namespace polylab
+
+struct polylab_plan {
+  int32_t n = 0;
+  int64_t m = 0;
+  int32_t max_exp = 0;       // largest single exponent (power-table depth)
+  int32_t max_support = 0;   // largest number of active variables in a term
+  polylab::Term* terms = nullptr;  // DEVICE, m terms
+  // derived-coefficient data for the tensor-core forms (nullptr unless built)
+  polylab::GemmOperand* gemm = nullptr;
+  int64_t closure = -1;
+};
+
+namespace polylab {
+
+// Fill `plan` (terms, m, n, max_exp, max_support); synchronises `s`.
+polylab_status build_term_plan(const polylab_poly* p, cudaStream_t s, polylab_plan* plan);
+polylab_status build_gemm_operand(polylab_plan* plan, cudaStream_t s);
+void free_gemm_operand(GemmOperand* g, cudaStream_t s);
+
+polylab_status check_poly(const polylab_poly* p);
+
+// Kernel launchers (one per translation unit)
+polylab_status eval_direct(const polylab_plan* plan, const double* X, int64_t P, int order, bool fp32,
+                           double* F, double* G, double* H, cudaStream_t s);
+polylab_status eval_gemm(const polylab_plan* plan, const double* X, int64_t P, int order, int prec,
+                         double* F, double* G, double* H, cudaStream_t s);
+polylab_status affine_exact(const polylab_plan* plan, const double* X, int64_t P, const polylab_an_opts* o,
+                            double* D, double* Dunit, polylab_an_info* info, cudaStream_t s);
+polylab_status affine_stochastic(const polylab_plan* plan, const double* X, int64_t P,
+                                 const polylab_an_opts* o, double* D, double* Dunit, polylab_an_info* info,
+                                 cudaStream_t s);
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+int num_sms();
+
+}  // namespace polylab

@@ -1,0 +1,721 @@
+// simplify and mul (Sec. 2 "simplify"/"mtimes", Sec. 3.2 alignment, Sec. 6.3
+// expansion-and-merge workloads) as key generation + LSD radix sort +
+// warp-shuffle segmented reduce-by-key + threshold compaction + unpack.
+//
+// Key = position of the exponent row in Polylab's internal monomial order
+// (Sec. 3.1 monolist: graded, then ascending lexicographic order of the
+// reversed row).  With S(c, R) = C(R + c, c), the number of monomials of
+// degree <= R in c variables, a row alpha of degree d over n variables has
+//
+//   rank(alpha) = S(n, d-1) + sum_{c = n-1 .. 1} [ S(c, R_c) - S(c, R_c - alpha_c) ],
+//   R_c = d - sum_{c' > c} alpha_c'
+//
+// and only nonzero entries contribute, so a sparse row costs O(support).
+// The key therefore needs only ceil(log2 S(n, D)) bits (34 for a product of
+// two degree-6 polynomials in 30 variables), and sorting by it emits the
+// result in the canonical order directly.  Keys of up to 64 bits sort as
+// uint64, up to 128 bits as unsigned __int128.
+#include <algorithm>
+#include <cstring>
+#include <unordered_map>
+#include <vector>
+
+#include "common.cuh"
+
+namespace polylab {
+namespace {
+
+typedef unsigned __int128 u128;
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+// ------------------------------------------------------------------ scan
+
+__global__ void scan_tiles(const uint32_t* __restrict__ in, uint32_t* __restrict__ out, uint32_t* __restrict__ sums,
+                           int64_t n) {
+  __shared__ uint32_t warp_tot[kScanThreads / 32];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  uint32_t v[kScanItems];
+  uint32_t run = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    v[i] = base + i < n ? in[base + i] : 0u;
+    const uint32_t t = v[i];
+    v[i] = run;
+    run += t;
+  }
+  // exclusive scan of thread totals across the block
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t inc = run;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) warp_tot[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t t = lane < kScanThreads / 32 ? warp_tot[lane] : 0u;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    if (lane < kScanThreads / 32) warp_tot[lane] = t;
+  }
+  __syncthreads();
+  const uint32_t off = (wid ? warp_tot[wid - 1] : 0u) + inc - run;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i)
+    if (base + i < n) out[base + i] = v[i] + off;
+  if (threadIdx.x == kScanThreads - 1) sums[blockIdx.x] = warp_tot[kScanThreads / 32 - 1];
+}
+
+__global__ void add_tile_offsets(uint32_t* __restrict__ out, const uint32_t* __restrict__ offs, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] += offs[i / kScanTile];
+}
+
+// Exclusive scan of n uint32 values (in may alias out).
+polylab_status exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, Scratch& scr, cudaStream_t s) {
+  if (n <= 0) return POLYLAB_OK;
+  const int64_t tiles = ceil_div(n, kScanTile);
+  uint32_t* sums = nullptr;
+  PL_TRY(scr.get(&sums, tiles));
+  scan_tiles<<<(unsigned)tiles, kScanThreads, 0, s>>>(in, out, sums, n);
+  PL_TRY(launch_status("scan_tiles"));
+  if (tiles > 1) {
+    PL_TRY(exclusive_scan(sums, sums, tiles, scr, s));
+    add_tile_offsets<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(out, sums, n);
+    PL_TRY(launch_status("add_tile_offsets"));
+  }
+  return POLYLAB_OK;
+}
+
+// ------------------------------------------------------- term supports (CSR)
+// Supports are stored in DESCENDING merged-column order, the order in which
+// the rank formula consumes them.
+
+__global__ void count_support(const uint8_t* __restrict__ exps, int64_t m, int n, uint32_t* __restrict__ cnt,
+                              uint32_t* __restrict__ deg, int* __restrict__ maxdeg) {
+  const int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (t >= m) return;
+  const uint8_t* row = exps + t * (int64_t)n;
+  uint32_t c = 0, d = 0;
+  for (int j = lane; j < n; j += 32) {
+    const uint32_t e = row[j];
+    c += e != 0;
+    d += e;
+  }
+  for (int o = 16; o; o >>= 1) {
+    c += __shfl_xor_sync(0xffffffffu, c, o);
+    d += __shfl_xor_sync(0xffffffffu, d, o);
+  }
+  if (lane == 0) {
+    cnt[t] = c;
+    deg[t] = d;
+    atomicMax(maxdeg, (int)d);
+  }
+}
+
+// ord[q] = operand column with the q-th smallest merged column; colmap[j] =
+// merged column of operand column j.  Entries are emitted for q descending.
+__global__ void fill_support(const uint8_t* __restrict__ exps, int64_t m, int n, const int* __restrict__ ord,
+                             const int* __restrict__ colmap, const uint32_t* __restrict__ ptr,
+                             uint32_t* __restrict__ col, uint8_t* __restrict__ ex) {
+  const int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (t >= m) return;
+  const uint8_t* row = exps + t * (int64_t)n;
+  const uint32_t start = ptr[t];
+  uint32_t written = 0;
+  for (int base = n - 1; base >= 0; base -= 32) {
+    const int q = base - lane;
+    const int j = q >= 0 ? ord[q] : 0;
+    const uint32_t e = q >= 0 ? row[j] : 0u;
+    const unsigned mask = __ballot_sync(0xffffffffu, e != 0);
+    if (e) {
+      const uint32_t pos = written + __popc(mask & ((1u << lane) - 1u));
+      col[start + pos] = (uint32_t)colmap[j];
+      ex[start + pos] = (uint8_t)e;
+    }
+    written += __popc(mask);
+  }
+}
+
+// ------------------------------------------------------------ keys
+
+template <typename K>
+__device__ __forceinline__ K tbl(const K* S, int D1, int c, int R) {  // S(c, R), 0 for R < 0
+  return R < 0 ? K(0) : S[c * D1 + R];
+}
+
+template <typename K>
+__global__ void keys_simplify(const uint32_t* __restrict__ ptr, const uint32_t* __restrict__ col,
+                              const uint8_t* __restrict__ ex, const uint32_t* __restrict__ deg, int64_t m, int n,
+                              const K* __restrict__ S, int D1, K* __restrict__ keys, uint32_t* __restrict__ vals) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= m) return;
+  const int d = (int)deg[t];
+  K r = tbl(S, D1, n, d - 1);
+  int R = d;
+  for (uint32_t q = ptr[t]; q < ptr[t + 1]; ++q) {
+    const int c = (int)col[q], a = ex[q];
+    r += tbl(S, D1, c, R) - tbl(S, D1, c, R - a);
+    R -= a;
+  }
+  keys[t] = r;
+  vals[t] = (uint32_t)t;
+}
+
+// Item t < ma is term t of A, otherwise term t - ma of B (the sum a + b).
+template <typename K>
+__global__ void keys_add(const uint32_t* __restrict__ pa, const uint32_t* __restrict__ ca,
+                         const uint8_t* __restrict__ ea, const uint32_t* __restrict__ da,
+                         const uint32_t* __restrict__ pb, const uint32_t* __restrict__ cb,
+                         const uint8_t* __restrict__ eb, const uint32_t* __restrict__ db, int64_t ma, int64_t mb,
+                         int n, const K* __restrict__ S, int D1, K* __restrict__ keys, uint32_t* __restrict__ vals) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ma + mb) return;
+  const bool fa = t < ma;
+  const int64_t i = fa ? t : t - ma;
+  const uint32_t* ptr = fa ? pa : pb;
+  const uint32_t* col = fa ? ca : cb;
+  const uint8_t* ex = fa ? ea : eb;
+  const int d = (int)(fa ? da[i] : db[i]);
+  K r = tbl(S, D1, n, d - 1);
+  int R = d;
+  for (uint32_t q = ptr[i]; q < ptr[i + 1]; ++q) {
+    const int c = (int)col[q], a = ex[q];
+    r += tbl(S, D1, c, R) - tbl(S, D1, c, R - a);
+    R -= a;
+  }
+  keys[t] = r;
+  vals[t] = (uint32_t)t;
+}
+
+template <typename K>
+__global__ void keys_mul(const uint32_t* __restrict__ pa, const uint32_t* __restrict__ ca,
+                         const uint8_t* __restrict__ ea, const uint32_t* __restrict__ da,
+                         const uint32_t* __restrict__ pb, const uint32_t* __restrict__ cb,
+                         const uint8_t* __restrict__ eb, const uint32_t* __restrict__ db, int64_t ma, int64_t mb,
+                         int n, const K* __restrict__ S, int D1, K* __restrict__ keys, uint32_t* __restrict__ vals,
+                         int* __restrict__ overflow) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= ma * mb) return;
+  const int64_t i = k / mb, j = k - i * mb;
+  const int d = (int)(da[i] + db[j]);
+  K r = tbl(S, D1, n, d - 1);
+  int R = d;
+  uint32_t qa = pa[i], qa_end = pa[i + 1], qb = pb[j], qb_end = pb[j + 1];
+  // merge two descending column lists
+  while (qa < qa_end || qb < qb_end) {
+    int c, a;
+    const int cA = qa < qa_end ? (int)ca[qa] : -1;
+    const int cB = qb < qb_end ? (int)cb[qb] : -1;
+    if (cA > cB) {
+      c = cA;
+      a = ea[qa++];
+    } else if (cB > cA) {
+      c = cB;
+      a = eb[qb++];
+    } else {
+      c = cA;
+      a = (int)ea[qa++] + (int)eb[qb++];
+      if (a > 255) *overflow = 1;
+    }
+    r += tbl(S, D1, c, R) - tbl(S, D1, c, R - a);
+    R -= a;
+  }
+  keys[k] = r;
+  vals[k] = (uint32_t)k;
+}
+
+// -------------------------------------------------------------- radix sort
+// LSD, 8-bit digits.  Tile = 8 warps x 32 lanes x 16 items; within a tile each
+// warp owns a contiguous segment and ranks its items stably with
+// __match_any_sync; per-digit warp counts are prefix-summed across warps.
+
+constexpr int kSortWarps = 8;
+constexpr int kSortIPT = 16;
+constexpr int kSortTile = kSortWarps * 32 * kSortIPT;
+
+template <typename K>
+__device__ __forceinline__ uint32_t digit_of(K key, int shift) {
+  return (uint32_t)(key >> shift) & 0xffu;
+}
+
+template <typename K>
+__global__ void __launch_bounds__(256) sort_hist(const K* __restrict__ keys, int64_t N, int shift,
+                                                 uint32_t* __restrict__ hist, int tiles) {
+  __shared__ uint32_t h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kSortTile;
+  for (int i = threadIdx.x; i < kSortTile; i += 256) {
+    const int64_t k = base + i;
+    if (k < N) atomicAdd(&h[digit_of(keys[k], shift)], 1u);
+  }
+  __syncthreads();
+  hist[(int64_t)threadIdx.x * tiles + blockIdx.x] = h[threadIdx.x];  // digit-major
+}
+
+template <typename K>
+__global__ void __launch_bounds__(256) sort_scatter(const K* __restrict__ keys, const uint32_t* __restrict__ vals,
+                                                    K* __restrict__ okeys, uint32_t* __restrict__ ovals, int64_t N,
+                                                    int shift, const uint32_t* __restrict__ offs, int tiles) {
+  __shared__ uint32_t wcnt[kSortWarps][256];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < kSortWarps * 256; i += 256) (&wcnt[0][0])[i] = 0;
+  __syncthreads();
+  const int64_t seg = (int64_t)blockIdx.x * kSortTile + (int64_t)wid * 32 * kSortIPT;
+  K kk[kSortIPT];
+  uint32_t vv[kSortIPT], rk[kSortIPT], dg[kSortIPT];
+  const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+  for (int it = 0; it < kSortIPT; ++it) {
+    const int64_t k = seg + it * 32 + lane;
+    const bool ok = k < N;
+    kk[it] = ok ? keys[k] : K(0);
+    vv[it] = ok ? vals[k] : 0u;
+    const uint32_t d = ok ? digit_of(kk[it], shift) : 256u;
+    dg[it] = d;
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const uint32_t before = __popc(peers & lt);
+    uint32_t basec = 0;
+    if (ok) basec = wcnt[wid][d];
+    rk[it] = basec + before;
+    __syncwarp();
+    if (ok && before == 0) wcnt[wid][d] = basec + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  // exclusive prefix over warps for each digit (thread = digit)
+  {
+    const int d = threadIdx.x;
+    uint32_t run = offs[(int64_t)d * tiles + blockIdx.x];
+    for (int w = 0; w < kSortWarps; ++w) {
+      const uint32_t c = wcnt[w][d];
+      wcnt[w][d] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < kSortIPT; ++it) {
+    if (dg[it] < 256u) {
+      const uint32_t pos = wcnt[wid][dg[it]] + rk[it];
+      okeys[pos] = kk[it];
+      ovals[pos] = vv[it];
+    }
+  }
+}
+
+// Sorts (keys, vals) by the low `bits` bits of the key; returns which buffer
+// holds the result (0 = the input buffers, 1 = the alternates).
+template <typename K>
+polylab_status radix_sort(K* keys, uint32_t* vals, K* akeys, uint32_t* avals, int64_t N, int bits, Scratch& scr,
+                          cudaStream_t s, int* which) {
+  *which = 0;
+  if (N <= 1 || bits <= 0) return POLYLAB_OK;
+  const int tiles = (int)ceil_div(N, kSortTile);
+  uint32_t* hist = nullptr;
+  PL_TRY(scr.get(&hist, (size_t)256 * tiles));
+  K* src_k = keys;
+  uint32_t* src_v = vals;
+  K* dst_k = akeys;
+  uint32_t* dst_v = avals;
+  for (int shift = 0; shift < bits; shift += 8) {
+    sort_hist<K><<<tiles, 256, 0, s>>>(src_k, N, shift, hist, tiles);
+    PL_TRY(launch_status("sort_hist"));
+    PL_TRY(exclusive_scan(hist, hist, (int64_t)256 * tiles, scr, s));
+    sort_scatter<K><<<tiles, 256, 0, s>>>(src_k, src_v, dst_k, dst_v, N, shift, hist, tiles);
+    PL_TRY(launch_status("sort_scatter"));
+    std::swap(src_k, dst_k);
+    std::swap(src_v, dst_v);
+    *which ^= 1;
+  }
+  return POLYLAB_OK;
+}
+
+// ------------------------------------------------- segmented reduce-by-key
+
+template <typename K>
+__global__ void mark_heads(const K* __restrict__ keys, int64_t N, uint32_t* __restrict__ head) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < N) head[k] = (k == 0 || keys[k] != keys[k - 1]) ? 1u : 0u;
+}
+
+// Coefficient of a sorted item: the input for simplify, one IEEE product for
+// mul, the input of either operand for add.
+enum Mode { kSimplify = 0, kMul = 1, kAdd = 2 };
+
+struct CoefOf {
+  const double* ca;
+  const double* cb;
+  int64_t ma, mb;
+  int mode;
+  __device__ __forceinline__ double operator()(uint32_t idx) const {
+    if (mode == kSimplify) return ca[idx];
+    if (mode == kAdd) return idx < ma ? ca[idx] : cb[idx - ma];
+    const int64_t i = idx / mb, j = idx - i * mb;
+    return ca[i] * cb[j];
+  }
+};
+
+// Each warp owns the segments whose head lies in its chunk [w*CH, (w+1)*CH),
+// so no segment is split between warps and the summation order is fixed.
+// Within a 32-item window a Hillis-Steele segmented scan on (head, value)
+// runs over shuffles; the open segment's partial sum is carried to the next
+// window.  The lane holding a segment's last item writes sums[slot].
+template <typename K>
+__global__ void seg_reduce(const K* __restrict__ keys, const uint32_t* __restrict__ vals,
+                           const uint32_t* __restrict__ head, const uint32_t* __restrict__ slot, int64_t N, int64_t CH,
+                           CoefOf coef, K* __restrict__ ukeys, double* __restrict__ sums) {
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int64_t lo = w * CH;
+  if (lo >= N) return;
+  const int64_t hi_nominal = std::min<int64_t>(lo + CH, N);
+  // first head at or after lo
+  int64_t start = lo;
+  while (true) {
+    const int64_t k = start + lane;
+    const bool h = k < N && head[k];
+    const unsigned b = __ballot_sync(0xffffffffu, h);
+    if (b) {
+      start += __ffs(b) - 1;
+      break;
+    }
+    start += 32;
+    if (start >= hi_nominal) return;  // no segment starts in this chunk
+  }
+  if (start >= hi_nominal) return;
+  double carry = 0.0;
+  for (int64_t base = start;; base += 32) {
+    const int64_t k = base + lane;
+    const bool in = k < N;
+    const bool h = in ? head[k] != 0u : true;
+    // stop at the first head at or beyond the nominal end (that segment belongs to the next warp)
+    const bool stop_here = h && k >= hi_nominal;
+    const unsigned stopmask = __ballot_sync(0xffffffffu, stop_here || !in);
+    const int first_stop = stopmask ? __ffs(stopmask) - 1 : 32;
+    const bool active = lane < first_stop;
+    double v = active ? coef(vals[k]) : 0.0;
+    bool f = active ? h : true;
+    // segmented inclusive scan
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const double yv = __shfl_up_sync(0xffffffffu, v, o);
+      const bool yf = __shfl_up_sync(0xffffffffu, f, o);
+      if (lane >= o && !f) {
+        v += yv;
+        f = yf;
+      }
+      // f now tells whether a head lies in (lane - 2o, lane]
+    }
+    // lanes before the first head of this window continue the carried segment
+    const unsigned heads = __ballot_sync(0xffffffffu, active && h);
+    const int first_head = heads ? __ffs(heads) - 1 : 32;
+    if (active && lane < first_head) v += carry;
+    // segment end: next item is a head, or is inactive
+    const bool next_is_head = __shfl_down_sync(0xffffffffu, (int)(!active || h), 1) != 0;
+    const bool end = active && (lane == 31 ? false : next_is_head);
+    // segment index of item k: heads before k, plus its own head, minus one
+    if (end) {
+      const uint32_t sl = slot[k] + (h ? 1u : 0u) - 1u;
+      sums[sl] = v;
+      ukeys[sl] = keys[k];
+    }
+    // a window that reached a stop closed every segment it holds (the lane
+    // before the stop sees an inactive successor, so `end` was set there)
+    if (first_stop < 32) return;
+    // all 32 lanes active: lane 31's segment stays open
+    carry = __shfl_sync(0xffffffffu, v, 31);
+    // if lane 31 was the end of its segment (next window starts with a head) it
+    // is written when that is known: peek at the next item
+    const int64_t nk = base + 32;
+    const bool nh = nk >= N || head[nk] != 0u;
+    if (nh && lane == 31) {
+      const uint32_t sl = slot[k] + (h ? 1u : 0u) - 1u;
+      sums[sl] = v;
+      ukeys[sl] = keys[k];
+    }
+    if (nh) carry = 0.0;
+  }
+}
+
+__global__ void keep_flags(const double* __restrict__ sums, int64_t U, double zeroprec, uint32_t* __restrict__ keep) {
+  const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u < U) keep[u] = fabs(sums[u]) > zeroprec ? 1u : 0u;
+}
+
+// Unrank a key into an exponent row (inverse of the rank formula above).
+template <typename K>
+__global__ void unpack_rows(const K* __restrict__ ukeys, const double* __restrict__ sums,
+                            const uint32_t* __restrict__ keep, const uint32_t* __restrict__ kpos, int64_t U, int n,
+                            const K* __restrict__ S, int D1, uint8_t* __restrict__ out_exps,
+                            double* __restrict__ out_coef) {
+  const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= U || !keep[u]) return;
+  const int64_t o = kpos[u];
+  uint8_t* row = out_exps + o * (int64_t)n;
+  for (int c = 0; c < n; ++c) row[c] = 0;
+  K r = ukeys[u];
+  const int D = D1 - 1;
+  int d = 0;
+  while (d < D && S[n * D1 + d] <= r) ++d;
+  K w = r - (d > 0 ? S[n * D1 + d - 1] : K(0));
+  int R = d;
+  for (int c = n - 1; c >= 1 && R > 0; --c) {
+    const K top = S[c * D1 + R];
+    int a = 0;
+    while (a < R && top - S[c * D1 + (R - a - 1)] <= w) ++a;
+    if (a) {
+      w -= top - S[c * D1 + (R - a)];
+      R -= a;
+      row[c] = (uint8_t)a;
+    }
+  }
+  row[0] = (uint8_t)R;
+  out_coef[o] = sums[u];
+}
+
+// ------------------------------------------------------------- host side
+
+struct Operand {
+  int64_t m = 0;
+  uint32_t* ptr = nullptr;  // m + 1
+  uint32_t* col = nullptr;
+  uint8_t* ex = nullptr;
+  uint32_t* deg = nullptr;
+  int maxdeg = 0;
+  uint32_t nnz = 0;
+};
+
+polylab_status build_operand(const polylab_poly* p, const std::vector<int>& colmap_h, Operand* op, Scratch& scr,
+                             cudaStream_t s) {
+  op->m = p->n_terms;
+  const int64_t m = op->m;
+  PL_TRY(scr.get(&op->ptr, m + 1));
+  PL_TRY(scr.get(&op->deg, m + 1));
+  int* dev_max = nullptr;
+  PL_TRY(scr.get(&dev_max, 1));
+  // operand columns in increasing merged-column order
+  std::vector<int> both(2 * colmap_h.size());
+  for (size_t j = 0; j < colmap_h.size(); ++j) both[j] = (int)j;
+  std::sort(both.begin(), both.begin() + colmap_h.size(), [&](int x, int y) { return colmap_h[x] < colmap_h[y]; });
+  std::copy(colmap_h.begin(), colmap_h.end(), both.begin() + colmap_h.size());
+  int* ordmap = nullptr;  // [ord | colmap]
+  PL_TRY(scr.get(&ordmap, both.size()));
+  // the staging vector must outlive the copy: synchronous copy from pageable memory
+  PL_CUDA(cudaMemcpyAsync(ordmap, both.data(), both.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  PL_CUDA(cudaStreamSynchronize(s));
+  PL_CUDA(cudaMemsetAsync(dev_max, 0, sizeof(int), s));
+  PL_CUDA(cudaMemsetAsync(op->ptr, 0, (m + 1) * sizeof(uint32_t), s));
+  if (m > 0) {
+    count_support<<<(unsigned)ceil_div(m, 8), 256, 0, s>>>(p->exps, m, p->n_vars, op->ptr, op->deg, dev_max);
+    PL_TRY(launch_status("count_support"));
+  }
+  PL_TRY(exclusive_scan(op->ptr, op->ptr, m + 1, scr, s));
+  int hmax = 0;
+  uint32_t hnnz = 0;
+  PL_CUDA(cudaMemcpyAsync(&hmax, dev_max, sizeof(int), cudaMemcpyDeviceToHost, s));
+  PL_CUDA(cudaMemcpyAsync(&hnnz, op->ptr + m, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  PL_CUDA(cudaStreamSynchronize(s));
+  op->maxdeg = hmax;
+  op->nnz = hnnz;
+  PL_TRY(scr.get(&op->col, std::max<uint32_t>(hnnz, 1)));
+  PL_TRY(scr.get(&op->ex, std::max<uint32_t>(hnnz, 1)));
+  if (m > 0) {
+    fill_support<<<(unsigned)ceil_div(m, 8), 256, 0, s>>>(p->exps, m, p->n_vars, ordmap, ordmap + p->n_vars,
+                                                          op->ptr, op->col, op->ex);
+    PL_TRY(launch_status("fill_support"));
+  }
+  return POLYLAB_OK;
+}
+
+// S(c, R) = C(R + c, c) for c = 0..n, R = 0..D, as K; false if S(n, D) >= 2^bits(K).
+template <typename K>
+bool build_table(int n, int D, std::vector<K>& S) {
+  const int D1 = D + 1;
+  S.assign((size_t)(n + 1) * D1, K(0));
+  for (int R = 0; R <= D; ++R) S[R] = 1;
+  for (int c = 1; c <= n; ++c) {
+    S[(size_t)c * D1] = 1;
+    for (int R = 1; R <= D; ++R) {
+      const K a = S[(size_t)(c - 1) * D1 + R], b = S[(size_t)c * D1 + R - 1];
+      const K v = a + b;
+      if (v < a) return false;  // wrapped
+      S[(size_t)c * D1 + R] = v;
+    }
+  }
+  return true;
+}
+
+int key_bits_u128(u128 total) {  // bits to represent values 0 .. total-1
+  int b = 0;
+  u128 t = total - 1;
+  while (t) {
+    ++b;
+    t >>= 1;
+  }
+  return b;
+}
+
+template <typename K>
+polylab_status run_pipeline(int n, int D, int64_t N, const std::vector<K>& Sh, int mode, const Operand& A,
+                            const Operand& B, const polylab_poly* pa, const polylab_poly* pb, double zeroprec,
+                            int bits, polylab_poly_out* out, polylab_alloc_fn alloc, void* ctx, Scratch& scr,
+                            cudaStream_t s) {
+  const int D1 = D + 1;
+  K* S = nullptr;
+  PL_TRY(scr.get(&S, Sh.size()));
+  PL_CUDA(cudaMemcpyAsync(S, Sh.data(), Sh.size() * sizeof(K), cudaMemcpyHostToDevice, s));
+  K *keys, *akeys;
+  uint32_t *vals, *avals;
+  PL_TRY(scr.get(&keys, N));
+  PL_TRY(scr.get(&akeys, N));
+  PL_TRY(scr.get(&vals, N));
+  PL_TRY(scr.get(&avals, N));
+  int* ovf = nullptr;
+  PL_TRY(scr.get(&ovf, 1));
+  PL_CUDA(cudaMemsetAsync(ovf, 0, sizeof(int), s));
+  if (mode == kMul) {
+    keys_mul<K><<<(unsigned)ceil_div(N, 256), 256, 0, s>>>(A.ptr, A.col, A.ex, A.deg, B.ptr, B.col, B.ex, B.deg, A.m,
+                                                           B.m, n, S, D1, keys, vals, ovf);
+  } else if (mode == kAdd) {
+    keys_add<K><<<(unsigned)ceil_div(N, 256), 256, 0, s>>>(A.ptr, A.col, A.ex, A.deg, B.ptr, B.col, B.ex, B.deg, A.m,
+                                                           B.m, n, S, D1, keys, vals);
+  } else {
+    keys_simplify<K><<<(unsigned)ceil_div(N, 256), 256, 0, s>>>(A.ptr, A.col, A.ex, A.deg, N, n, S, D1, keys, vals);
+  }
+  PL_TRY(launch_status("keys"));
+  int which = 0;
+  PL_TRY(radix_sort<K>(keys, vals, akeys, avals, N, bits, scr, s, &which));
+  if (which) {
+    std::swap(keys, akeys);
+    std::swap(vals, avals);
+  }
+  uint32_t *head, *slot;
+  PL_TRY(scr.get(&head, N));
+  PL_TRY(scr.get(&slot, N));
+  mark_heads<K><<<(unsigned)ceil_div(N, 256), 256, 0, s>>>(keys, N, head);
+  PL_TRY(launch_status("mark_heads"));
+  PL_TRY(exclusive_scan(head, slot, N, scr, s));
+  uint32_t hU[2] = {0, 0};
+  PL_CUDA(cudaMemcpyAsync(&hU[0], slot + N - 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  PL_CUDA(cudaMemcpyAsync(&hU[1], head + N - 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  int hovf = 0;
+  PL_CUDA(cudaMemcpyAsync(&hovf, ovf, sizeof(int), cudaMemcpyDeviceToHost, s));
+  PL_CUDA(cudaStreamSynchronize(s));
+  if (hovf) return POLYLAB_ERR_EXP_OVERFLOW;
+  const int64_t U = (int64_t)hU[0] + hU[1];
+  K* ukeys;
+  double* sums;
+  PL_TRY(scr.get(&ukeys, U));
+  PL_TRY(scr.get(&sums, U));
+  const int64_t CH = 512;
+  const int64_t warps = ceil_div(N, CH);
+  CoefOf cf{pa->coef, mode != kSimplify ? pb->coef : nullptr, pa->n_terms, mode != kSimplify ? pb->n_terms : 0,
+            mode};
+  seg_reduce<K><<<(unsigned)ceil_div(warps * 32, 256), 256, 0, s>>>(keys, vals, head, slot, N, CH, cf, ukeys, sums);
+  PL_TRY(launch_status("seg_reduce"));
+  uint32_t *keep, *kpos;
+  PL_TRY(scr.get(&keep, U));
+  PL_TRY(scr.get(&kpos, U));
+  keep_flags<<<(unsigned)ceil_div(U, 256), 256, 0, s>>>(sums, U, zeroprec, keep);
+  PL_TRY(launch_status("keep_flags"));
+  PL_TRY(exclusive_scan(keep, kpos, U, scr, s));
+  uint32_t hM[2] = {0, 0};
+  PL_CUDA(cudaMemcpyAsync(&hM[0], kpos + U - 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  PL_CUDA(cudaMemcpyAsync(&hM[1], keep + U - 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  PL_CUDA(cudaStreamSynchronize(s));
+  const int64_t M = (int64_t)hM[0] + hM[1];
+  out->n_terms = M;
+  out->exps = nullptr;
+  out->coef = nullptr;
+  if (M == 0) return POLYLAB_OK;
+  out->exps = (uint8_t*)alloc((size_t)M * n, ctx);
+  out->coef = (double*)alloc((size_t)M * sizeof(double), ctx);
+  if (!out->exps || !out->coef) return POLYLAB_ERR_OOM;
+  unpack_rows<K><<<(unsigned)ceil_div(U, 128), 128, 0, s>>>(ukeys, sums, keep, kpos, U, n, S, D1, out->exps,
+                                                            out->coef);
+  return launch_status("unpack_rows");
+}
+
+polylab_status engine(const polylab_poly* pa, const polylab_poly* pb, int mode, double zeroprec,
+                      polylab_poly_out* out, polylab_alloc_fn alloc, void* ctx, cudaStream_t s) {
+  if (!out || !alloc || !out->var_ids || !(zeroprec >= 0.0)) return POLYLAB_ERR_INVALID_ARG;
+  PL_TRY(check_poly(pa));
+  const bool is_mul = mode != kSimplify;  // two operands (mul or add)
+  if (is_mul) PL_TRY(check_poly(pb));
+  // alignment (Sec. 3.2): merged ids ascending; column maps per operand
+  std::vector<uint64_t> ids(pa->var_ids, pa->var_ids + pa->n_vars);
+  std::vector<int> mapA(pa->n_vars), mapB;
+  int n;
+  if (is_mul) {
+    ids.insert(ids.end(), pb->var_ids, pb->var_ids + pb->n_vars);
+    std::sort(ids.begin(), ids.end());
+    ids.erase(std::unique(ids.begin(), ids.end()), ids.end());
+    n = (int)ids.size();
+    std::unordered_map<uint64_t, int> pos;
+    for (int i = 0; i < n; ++i) pos[ids[i]] = i;
+    for (int i = 0; i < pa->n_vars; ++i) mapA[i] = pos[pa->var_ids[i]];
+    mapB.resize(pb->n_vars);
+    for (int i = 0; i < pb->n_vars; ++i) mapB[i] = pos[pb->var_ids[i]];
+  } else {
+    n = pa->n_vars;
+    for (int i = 0; i < n; ++i) mapA[i] = i;
+  }
+  out->n_vars = n;
+  std::memcpy(out->var_ids, ids.data(), ids.size() * sizeof(uint64_t));
+  out->n_terms = 0;
+  out->exps = nullptr;
+  out->coef = nullptr;
+  const int64_t N = mode == kMul ? pa->n_terms * pb->n_terms
+                   : mode == kAdd ? pa->n_terms + pb->n_terms : pa->n_terms;
+  if (N >= ((int64_t)1 << 31)) return POLYLAB_ERR_UNSUPPORTED;
+  if (N == 0) return POLYLAB_OK;
+  Scratch scr(s);
+  Operand A, B;
+  PL_TRY(build_operand(pa, mapA, &A, scr, s));
+  if (is_mul) PL_TRY(build_operand(pb, mapB, &B, scr, s));
+  const int D = std::max(1, mode == kMul ? A.maxdeg + B.maxdeg
+                            : mode == kAdd ? std::max(A.maxdeg, B.maxdeg) : A.maxdeg);
+  std::vector<u128> S128;
+  if (!build_table<u128>(n, D, S128)) return POLYLAB_ERR_UNSUPPORTED;
+  const u128 total = S128[(size_t)n * (D + 1) + D];
+  const int bits = key_bits_u128(total);
+  if (bits <= 64) {
+    std::vector<uint64_t> S64(S128.size());
+    for (size_t i = 0; i < S128.size(); ++i) S64[i] = (uint64_t)S128[i];
+    return run_pipeline<uint64_t>(n, D, N, S64, mode, A, B, pa, pb, zeroprec, bits, out, alloc, ctx, scr, s);
+  }
+  return run_pipeline<u128>(n, D, N, S128, mode, A, B, pa, pb, zeroprec, bits, out, alloc, ctx, scr, s);
+}
+
+}  // namespace
+}  // namespace polylab
+
+extern "C" {
+
+polylab_status polylab_simplify(const polylab_poly* p, double zeroprec, polylab_poly_out* out,
+                                polylab_alloc_fn alloc, void* alloc_ctx, polylab_stream stream) {
+  return polylab::engine(p, nullptr, polylab::kSimplify, zeroprec, out, alloc, alloc_ctx, (cudaStream_t)stream);
+}
+
+polylab_status polylab_mul(const polylab_poly* a, const polylab_poly* b, double zeroprec, polylab_poly_out* out,
+                           polylab_alloc_fn alloc, void* alloc_ctx, polylab_stream stream) {
+  if (!b) return POLYLAB_ERR_INVALID_ARG;
+  return polylab::engine(a, b, polylab::kMul, zeroprec, out, alloc, alloc_ctx, (cudaStream_t)stream);
+}
+
+polylab_status polylab_add(const polylab_poly* a, const polylab_poly* b, double zeroprec, polylab_poly_out* out,
+                           polylab_alloc_fn alloc, void* alloc_ctx, polylab_stream stream) {
+  if (!b) return POLYLAB_ERR_INVALID_ARG;
+  return polylab::engine(a, b, polylab::kAdd, zeroprec, out, alloc, alloc_ctx, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,167 @@
+// Plans: the device-resident term list of a polynomial, status strings and
+// argument checks shared by every entry point.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <unordered_set>
+
+#include "common.cuh"
+
+namespace polylab {
+
+static thread_local char g_last_error[512] = "";
+
+void set_last_error(const char* where, cudaError_t e) {
+  snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%s)", where, cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+int num_sms() {
+  static int cached = 0;
+  if (!cached) {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    cached = v > 0 ? v : 148;
+  }
+  return cached;
+}
+
+polylab_status check_poly(const polylab_poly* p) {
+  if (!p || p->n_vars < 1 || p->n_terms < 0 || !p->var_ids) return POLYLAB_ERR_INVALID_ARG;
+  if (p->n_terms > 0 && (!p->exps || !p->coef)) return POLYLAB_ERR_INVALID_ARG;
+  std::unordered_set<uint64_t> seen;
+  for (int i = 0; i < p->n_vars; ++i)
+    if (!seen.insert(p->var_ids[i]).second) return POLYLAB_ERR_DUP_VAR_ID;
+  return POLYLAB_OK;
+}
+
+// One warp per term: scan the exponent row, keep the nonzero entries in
+// column order.  stats[0] = max exponent, stats[1] = max support.
+__global__ void pack_terms_kernel(const uint8_t* __restrict__ exps, const double* __restrict__ coef, int64_t m,
+                                  int n, Term* __restrict__ terms, int* __restrict__ stats) {
+  __shared__ Term stage[8];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t t = (int64_t)blockIdx.x * 8 + wib;
+  if (t >= m) return;
+  Term& st = stage[wib];
+  if (lane < kMaxSupport) {
+    st.var[lane] = 0;
+    st.exp[lane] = 0;
+  }
+  __syncwarp();
+  const uint8_t* row = exps + t * (int64_t)n;
+  int count = 0, maxe = 0;
+  for (int base = 0; base < n; base += 32) {
+    const int j = base + lane;
+    const int e = j < n ? row[j] : 0;
+    const unsigned mask = __ballot_sync(0xffffffffu, e != 0);
+    if (e) {
+      const int pos = count + __popc(mask & ((1u << lane) - 1u));
+      if (pos < kMaxSupport) {
+        st.var[pos] = (uint16_t)j;
+        st.exp[pos] = (uint8_t)e;
+      }
+    }
+    count += __popc(mask);
+    maxe = max(maxe, e);
+  }
+  for (int o = 16; o; o >>= 1) maxe = max(maxe, __shfl_xor_sync(0xffffffffu, maxe, o));
+  __syncwarp();
+  if (lane == 0) {
+    st.coef = coef[t];
+    terms[t] = st;
+    atomicMax(&stats[0], maxe);
+    atomicMax(&stats[1], count);
+  }
+}
+
+polylab_status build_term_plan(const polylab_poly* p, cudaStream_t s, polylab_plan* plan) {
+  PL_TRY(check_poly(p));
+  if (p->n_vars > 65535) return POLYLAB_ERR_UNSUPPORTED;
+  plan->n = p->n_vars;
+  plan->m = p->n_terms;
+  int* stats = nullptr;
+  PL_CUDA(cudaMallocAsync(&stats, 2 * sizeof(int), s));
+  PL_CUDA(cudaMemsetAsync(stats, 0, 2 * sizeof(int), s));
+  PL_CUDA(cudaMallocAsync(&plan->terms, std::max<int64_t>(p->n_terms, 1) * sizeof(Term), s));
+  if (p->n_terms > 0) {
+    pack_terms_kernel<<<(unsigned)ceil_div(p->n_terms, 8), 256, 0, s>>>(p->exps, p->coef, p->n_terms, p->n_vars,
+                                                                          plan->terms, stats);
+    PL_TRY(launch_status("pack_terms_kernel"));
+  }
+  int h[2] = {0, 0};
+  PL_CUDA(cudaMemcpyAsync(h, stats, sizeof(h), cudaMemcpyDeviceToHost, s));
+  PL_CUDA(cudaFreeAsync(stats, s));
+  PL_CUDA(cudaStreamSynchronize(s));
+  plan->max_exp = h[0];
+  plan->max_support = h[1];
+  if (h[1] > kMaxSupport) return POLYLAB_ERR_UNSUPPORTED;
+  return POLYLAB_OK;
+}
+
+}  // namespace polylab
+
+using namespace polylab;
+
+extern "C" {
+
+const char* polylab_status_string(polylab_status s) {
+  switch (s) {
+    case POLYLAB_OK: return "POLYLAB_OK";
+    case POLYLAB_ERR_INVALID_ARG: return "POLYLAB_ERR_INVALID_ARG";
+    case POLYLAB_ERR_EXP_OVERFLOW: return "POLYLAB_ERR_EXP_OVERFLOW";
+    case POLYLAB_ERR_DUP_VAR_ID: return "POLYLAB_ERR_DUP_VAR_ID";
+    case POLYLAB_ERR_OOM: return "POLYLAB_ERR_OOM";
+    case POLYLAB_ERR_CUDA: return "POLYLAB_ERR_CUDA";
+    case POLYLAB_ERR_TIMEOUT: return "POLYLAB_ERR_TIMEOUT";
+    case POLYLAB_ERR_UNSUPPORTED: return "POLYLAB_ERR_UNSUPPORTED";
+  }
+  return "POLYLAB_UNKNOWN_STATUS";
+}
+
+const char* polylab_last_error(void) { return g_last_error; }
+
+polylab_status polylab_plan_create(const polylab_poly* p, uint32_t what, polylab_stream stream,
+                                   polylab_plan** out) {
+  if (!out) return POLYLAB_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (what > POLYLAB_PLAN_GEMM) return POLYLAB_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  polylab_plan* plan = new polylab_plan();
+  polylab_status st = build_term_plan(p, s, plan);
+  if (st == POLYLAB_OK && (what & POLYLAB_PLAN_GEMM)) st = build_gemm_operand(plan, s);
+  if (st != POLYLAB_OK) {
+    polylab_plan_destroy(plan, stream);
+    return st;
+  }
+  *out = plan;
+  return POLYLAB_OK;
+}
+
+polylab_status polylab_plan_destroy(polylab_plan* plan, polylab_stream stream) {
+  if (!plan) return POLYLAB_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (plan->terms) cudaFreeAsync(plan->terms, s);
+  if (plan->gemm) free_gemm_operand(plan->gemm, s);
+  delete plan;
+  return launch_status("polylab_plan_destroy");
+}
+
+int64_t polylab_plan_closure_size(const polylab_plan* plan) { return plan ? plan->closure : -1; }
+
+void polylab_an_opts_default(polylab_an_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->method = POLYLAB_MF_EXACT;
+  o->regularization = 1e-6;
+  o->num_probes = 8;
+  o->krylov_tol = 1e-4;
+  o->krylov_maxit = 40;
+  o->assume_nonzero_x = 0;
+  o->seed = 20260321ull;
+  o->prec = POLYLAB_FP64;
+  o->precond = POLYLAB_PRECOND_JACOBI;
+  o->mlp_weights = nullptr;
+}
+
+}  // extern "C"

@@ -1,0 +1,269 @@
+"""Thin ctypes binding of libpolylab.so (the C ABI declared in include/polylab.h).
+
+Argument marshalling only: torch tensors are passed as raw device pointers
+together with the current torch stream; every computation runs in the
+library's CUDA kernels.  Importing this module loads the in-tree library and
+raises if it is missing -- there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpolylab.so")
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libpolylab.so not built ({LIB_PATH}); run __graft_entry__.build()")
+_lib = C.CDLL(LIB_PATH)
+
+OK = 0
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "EXP_OVERFLOW", 3: "DUP_VAR_ID", 4: "OOM", 5: "CUDA", 6: "TIMEOUT",
+          7: "UNSUPPORTED"}
+PREC = {"fp64": 0, "tf32x3": 1, "bf16": 2, "fp32": 3}
+METHOD = {"mf-exact": 0, "mf-stochastic": 1}
+PRECOND = {"jacobi": 0, "none": 1, "mlp": 2}
+FLAG_ZERO_GRAD, FLAG_NOT_PD, FLAG_KRYLOV_MAXIT = 1, 2, 4
+
+
+class PolylabError(RuntimeError):
+    def __init__(self, fn: str, status: int):
+        msg = _lib.polylab_last_error().decode()
+        super().__init__(f"{fn}: {STATUS.get(status, status)}" + (f" [{msg}]" if msg and status == 5 else ""))
+        self.status = status
+
+
+class _Poly(C.Structure):
+    _fields_ = [("n_vars", C.c_int32), ("var_ids", C.POINTER(C.c_uint64)), ("n_terms", C.c_int64),
+                ("exps", C.c_void_p), ("coef", C.c_void_p)]
+
+
+class _PolyOut(C.Structure):
+    _fields_ = [("n_vars", C.c_int32), ("var_ids", C.POINTER(C.c_uint64)), ("n_terms", C.c_int64),
+                ("exps", C.c_void_p), ("coef", C.c_void_p)]
+
+
+class _AnOpts(C.Structure):
+    _fields_ = [("method", C.c_int), ("regularization", C.c_double), ("num_probes", C.c_int32),
+                ("krylov_tol", C.c_double), ("krylov_maxit", C.c_int32), ("assume_nonzero_x", C.c_int32),
+                ("seed", C.c_uint64), ("prec", C.c_int), ("precond", C.c_int), ("mlp_weights", C.c_void_p)]
+
+
+INFO_DTYPE = np.dtype([("grad_norm", "<f8"), ("logdet", "<f8"), ("flags", "<i4"), ("hv_evals", "<i4"),
+                       ("third_evals", "<i4"), ("krylov_iters", "<i4")])
+assert INFO_DTYPE.itemsize == 32
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+
+_lib.polylab_status_string.restype = C.c_char_p
+_lib.polylab_last_error.restype = C.c_char_p
+_lib.polylab_plan_closure_size.restype = C.c_int64
+_lib.polylab_plan_closure_size.argtypes = [C.c_void_p]
+_lib.polylab_plan_create.argtypes = [C.POINTER(_Poly), C.c_uint32, C.c_void_p, C.POINTER(C.c_void_p)]
+_lib.polylab_plan_destroy.argtypes = [C.c_void_p, C.c_void_p]
+_lib.polylab_eval_derivs.argtypes = [C.POINTER(_Poly), C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_int,
+                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+_lib.polylab_affine_normal.argtypes = [C.POINTER(_Poly), C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(_AnOpts),
+                                       C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+_lib.polylab_simplify.argtypes = [C.POINTER(_Poly), C.c_double, C.POINTER(_PolyOut), ALLOC_FN, C.c_void_p,
+                                  C.c_void_p]
+_lib.polylab_mul.argtypes = [C.POINTER(_Poly), C.POINTER(_Poly), C.c_double, C.POINTER(_PolyOut), ALLOC_FN,
+                             C.c_void_p, C.c_void_p]
+_lib.polylab_add.argtypes = _lib.polylab_mul.argtypes
+_lib.polylab_an_opts_default.argtypes = [C.POINTER(_AnOpts)]
+for _f in ("polylab_plan_create", "polylab_plan_destroy", "polylab_eval_derivs", "polylab_affine_normal",
+           "polylab_simplify", "polylab_mul", "polylab_add"):
+    getattr(_lib, _f).restype = C.c_int
+
+EXPORTED = ["polylab_status_string", "polylab_last_error", "polylab_simplify", "polylab_mul", "polylab_add",
+            "polylab_plan_create", "polylab_plan_destroy", "polylab_plan_closure_size", "polylab_eval_derivs",
+            "polylab_an_opts_default", "polylab_affine_normal"]
+
+
+def lib():
+    return _lib
+
+
+def _check(fn: str, st: int):
+    if st != OK:
+        raise PolylabError(fn, st)
+
+
+def _stream() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _ptr(t: torch.Tensor | None) -> int | None:
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous()
+    return t.data_ptr()
+
+
+@dataclass
+class DevPoly:
+    """A polynomial whose exponents and coefficients live on the device."""
+    var_ids: np.ndarray   # uint64[n] (host)
+    exps: torch.Tensor    # uint8 [m, n] cuda
+    coef: torch.Tensor    # float64 [m] cuda
+
+    @property
+    def n(self) -> int:
+        return int(self.var_ids.shape[0])
+
+    @property
+    def m(self) -> int:
+        return int(self.coef.shape[0])
+
+    def cstruct(self) -> _Poly:
+        ids = np.ascontiguousarray(self.var_ids, dtype=np.uint64)
+        self._ids_keep = ids
+        return _Poly(self.n, ids.ctypes.data_as(C.POINTER(C.c_uint64)), self.m, _ptr(self.exps), _ptr(self.coef))
+
+
+def to_device(poly, device="cuda") -> DevPoly:
+    """From any object with var_ids / exps / coef arrays (e.g. workloads.Poly)."""
+    return DevPoly(np.asarray(poly.var_ids, dtype=np.uint64),
+                   torch.as_tensor(np.ascontiguousarray(poly.exps, dtype=np.uint8), device=device),
+                   torch.as_tensor(np.ascontiguousarray(poly.coef, dtype=np.float64), device=device))
+
+
+class Plan:
+    """Device-resident preprocessed polynomial (polylab_plan)."""
+
+    def __init__(self, p: DevPoly, gemm: bool = False):
+        self.p = p
+        self.h = C.c_void_p()
+        cp = p.cstruct()
+        _check("polylab_plan_create", _lib.polylab_plan_create(C.byref(cp), 1 if gemm else 0, _stream(),
+                                                               C.byref(self.h)))
+
+    @property
+    def closure_size(self) -> int:
+        return int(_lib.polylab_plan_closure_size(self.h))
+
+    def close(self):
+        if self.h:
+            _lib.polylab_plan_destroy(self.h, _stream())
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def eval_derivs(p: DevPoly, X: torch.Tensor, order: int = 2, prec: str = "fp64", plan: Plan | None = None,
+                out=None):
+    """F[P], G[P,n], H[P,n,n] (float64, device)."""
+    P, n = X.shape
+    assert n == p.n and X.dtype == torch.float64
+    if out is None:
+        F = torch.empty(P, dtype=torch.float64, device=X.device)
+        G = torch.empty(P, n, dtype=torch.float64, device=X.device) if order >= 1 else None
+        H = torch.empty(P, n, n, dtype=torch.float64, device=X.device) if order >= 2 else None
+    else:
+        F, G, H = out
+    cp = p.cstruct()
+    _check("polylab_eval_derivs", _lib.polylab_eval_derivs(C.byref(cp), plan.h if plan else None, _ptr(X), P, order,
+                                                           PREC[prec], _ptr(F), _ptr(G), _ptr(H), _stream()))
+    return F, G, H
+
+
+def an_opts(method="mf-exact", regularization=1e-6, num_probes=8, krylov_tol=1e-4, krylov_maxit=40,
+            assume_nonzero_x=False, seed=20260321, prec="fp64", precond="jacobi", mlp_weights=None) -> _AnOpts:
+    o = _AnOpts()
+    _lib.polylab_an_opts_default(C.byref(o))
+    o.method = METHOD[method]
+    o.regularization = regularization
+    o.num_probes = num_probes
+    o.krylov_tol = krylov_tol
+    o.krylov_maxit = krylov_maxit
+    o.assume_nonzero_x = int(bool(assume_nonzero_x))
+    o.seed = seed
+    o.prec = PREC[prec]
+    o.precond = PRECOND[precond]
+    o.mlp_weights = _ptr(mlp_weights)
+    return o
+
+
+def affine_normal(p: DevPoly, X: torch.Tensor, opts: _AnOpts | None = None, plan: Plan | None = None,
+                  want_unit: bool = True, want_info: bool = True, out=None, **kw):
+    """(D, Dunit, info_bytes) on the device; ``info_numpy`` decodes info."""
+    P, n = X.shape
+    assert n == p.n and X.dtype == torch.float64
+    o = opts if opts is not None else an_opts(**kw)
+    if out is None:
+        D = torch.empty(P, n, dtype=torch.float64, device=X.device)
+        Du = torch.empty(P, n, dtype=torch.float64, device=X.device) if want_unit else None
+        info = torch.empty(P, 32, dtype=torch.uint8, device=X.device) if want_info else None
+    else:
+        D, Du, info = out
+    cp = p.cstruct()
+    _check("polylab_affine_normal", _lib.polylab_affine_normal(C.byref(cp), plan.h if plan else None, _ptr(X), P,
+                                                               C.byref(o), _ptr(D), _ptr(Du), _ptr(info), _stream()))
+    return D, Du, info
+
+
+def info_numpy(info: torch.Tensor) -> np.ndarray:
+    return info.cpu().numpy().view(INFO_DTYPE).reshape(-1)
+
+
+class _Allocs:
+    def __init__(self, device):
+        self.keep = []
+        self.device = device
+
+        def fn(nbytes, ctx):
+            t = torch.empty(int(nbytes), dtype=torch.uint8, device=self.device)
+            self.keep.append(t)
+            return t.data_ptr()
+
+        self.fn = ALLOC_FN(fn)
+
+
+def _run_out(name, call, n_cap: int, device):
+    ids = np.zeros(max(n_cap, 1), dtype=np.uint64)
+    out = _PolyOut(0, ids.ctypes.data_as(C.POINTER(C.c_uint64)), 0, None, None)
+    al = _Allocs(device)
+    _check(name, call(C.byref(out), al.fn))
+    n, m = out.n_vars, out.n_terms
+    by_ptr = {t.data_ptr(): t for t in al.keep}
+    if m > 0:
+        exps = by_ptr[out.exps][: m * n].view(m, n)
+        coef = by_ptr[out.coef][: m * 8].view(torch.float64)
+    else:
+        exps = torch.zeros(0, n, dtype=torch.uint8, device=device)
+        coef = torch.zeros(0, dtype=torch.float64, device=device)
+    return DevPoly(ids[:n].copy(), exps, coef)
+
+
+def simplify(p: DevPoly, zeroprec: float = 0.0) -> DevPoly:
+    cp = p.cstruct()
+    return _run_out("polylab_simplify",
+                    lambda o, fn: _lib.polylab_simplify(C.byref(cp), zeroprec, o, fn, None, _stream()),
+                    p.n, p.coef.device)
+
+
+def mul(a: DevPoly, b: DevPoly, zeroprec: float = 0.0) -> DevPoly:
+    ca, cb = a.cstruct(), b.cstruct()
+    return _run_out("polylab_mul",
+                    lambda o, fn: _lib.polylab_mul(C.byref(ca), C.byref(cb), zeroprec, o, fn, None, _stream()),
+                    a.n + b.n, a.coef.device)
+
+
+def add(a: DevPoly, b: DevPoly, zeroprec: float = 0.0) -> DevPoly:
+    ca, cb = a.cstruct(), b.cstruct()
+    return _run_out("polylab_add",
+                    lambda o, fn: _lib.polylab_add(C.byref(ca), C.byref(cb), zeroprec, o, fn, None, _stream()),
+                    a.n + b.n, a.coef.device)
