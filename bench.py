@@ -1,0 +1,439 @@
+"""Benchmark: exact affine-normal directions per second on a batch of 256
+uneven polynomials, plus the per-row measurements of the rest of the path.
+
+Headline workload (one "step"): for 256 convexified polynomials
+(n ~ U{5..60}, random-part term counts log-uniform in [50, 20000], degree <= 6,
+128..4096 points each on the shell 0.5 <= |x| <= 1.5) compute the exact
+(MF-logDet-Exact) affine-normal direction, its unit copy and the per-point
+diagnostics at every point, with the polynomials' plans and the points
+resident in HBM.  ``value`` is directions per second of the chosen form (the
+FP32-sum / FP64-Cholesky form when it meets its stated error against the FP64
+form, otherwise the FP64 form); the plain FP64 form is reported beside it.
+
+Other rows of the path are measured in the same run and reported as
+sub-objects: the 4M-term product simplify (terms/s), the 65,536-point
+derivative evaluation (evals/s per precision form).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+``--impl reference`` times the CPU oracle (the plain FP64 'ad' formula) on a
+bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "affine-normal dirs/s (exact, 256 uneven polys) and f/grad/Hessian evals/s vs plain FP64 GPU"
+WORKLOAD = ("batched_uneven_exact: 256 convexified polys (sum x^4 + sum x^2 + 0.1 random), n~U{5..60}, "
+            "random terms log-U[50,20000] deg<=6, 128-4096 shell points each")
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--polys", type=int, default=256)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-rows", action="store_true", help="skip the per-row sub-measurements")
+    ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work per sample")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ flop model
+
+def term_stats(exps: np.ndarray):
+    k = (exps > 0).sum(axis=1).astype(np.int64)
+    d = exps.astype(np.int64).sum(axis=1)
+    return k, d
+
+
+def exact_flops(poly, P: int):
+    """Algorithmic flops of one exact direction (stated in the design doc), split
+    into the parts the FP32 form runs in FP32 (term sums, triangular inverse)
+    and those kept in FP64 (Cholesky, frame updates, tau, normalisation)."""
+    n = poly.n
+    m = n - 1
+    k, d = term_stats(poly.exps)
+    f_terms = float(np.sum(2 * (k + k * (k + 1) // 2)))
+    k3 = k[d >= 3]
+    f_third = float(np.sum(2 * (k3 + 2 * k3 * (k3 - 1) + 3 * (k3 * (k3 - 1) * (k3 - 2) // 6))))
+    f_chol = 2.0 * m ** 3 / 3.0
+    f_inv = 2.0 * m ** 3 / 3.0
+    f_small = 14.0 * n * n
+    per = dict(terms=f_terms, third=f_third, chol=f_chol, inv=f_inv, small=f_small)
+    return {key: val * P for key, val in per.items()}
+
+
+def alu_roofline(flops: dict, t_s: float, form: str, p32: float, p64: float):
+    if form == "fp64":
+        f64 = sum(flops.values())
+        f32 = 0.0
+    else:
+        f32 = flops["terms"] + flops["third"] + flops["inv"]
+        f64 = flops["chol"] + flops["small"]
+    tot = f32 + f64
+    t_min = f32 / (p32 * 1e12) + f64 / (p64 * 1e12)
+    peak = tot / t_min / 1e12
+    achieved = tot / t_s / 1e12
+    return dict(bound="alu", achieved=round(achieved, 4), peak=round(peak, 4), unit="TFLOP/s",
+                frac=round(achieved / peak, 4), traffic=None,
+                peak_source=f"measured FMA probe: fp32 {p32:.1f} TF/s, fp64 {p64:.3f} TF/s; op mix of this form",
+                flops_fp32=f32, flops_fp64=f64)
+
+
+# ------------------------------------------------------------------ clocks
+
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [c.strip() for c in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, r[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return dict(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=max(mx) if mx else None,
+                    reasons=sorted(reasons), samples=len(sm))
+
+
+# ------------------------------------------------------------------ reference / cpu baseline
+
+def oracle_sample(polys, Xs, budget_s: float, r: float = 1e-6):
+    """Run the CPU oracle ('ad' formula) over points taken round-robin from the
+    polynomials until ``budget_s`` seconds of work; returns (directions, seconds,
+    description, {(poly, point): nu})."""
+    from oracle import affine
+    try:
+        from threadpoolctl import threadpool_limits
+        lim = threadpool_limits(1)
+    except Exception:
+        lim = None
+    done, out = 0, {}
+    t0 = time.perf_counter()
+    j = 0
+    while time.perf_counter() - t0 < budget_s and j < 64:
+        for i in range(len(polys)):
+            if j < Xs[i].shape[0]:
+                nu, _, _ = affine.affine_normal_ad(polys[i].exps, polys[i].coef, Xs[i][j], r=r, third="contract")
+                out[(i, j)] = nu
+                done += 1
+            if time.perf_counter() - t0 >= budget_s:
+                break
+        j += 1
+    dt = time.perf_counter() - t0
+    if lim is not None:
+        lim.unregister() if hasattr(lim, "unregister") else None
+    desc = f"{done} points taken round-robin over the {len(polys)} polys (point j of every poly, j=0,1,..), 1 thread"
+    return done, dt, desc, out
+
+
+def run_reference(args):
+    from paper_2604_06575_b300 import workloads
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    polys, Xs = workloads.batched_uneven(n_polys=args.polys)
+    for _ in range(args.warmup):
+        oracle_sample(polys, Xs, 0.5)
+    vals = []
+    t_all = 0.0
+    for _ in range(args.steps):
+        done, dt, desc, _ = oracle_sample(polys, Xs, args.cpu_budget / max(args.steps, 1) * 2)
+        vals.append(done / dt)
+        t_all += dt
+    v = float(statistics.median(vals))
+    line = dict(metric=METRIC, value=v, unit="dirs/s", n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
+                ms_per_step=t_all / args.steps * 1e3, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f64", data="synthetic", impl="reference",
+                config=dict(workload=WORKLOAD, polys=args.polys, sample="bounded CPU sample per step"),
+                cpu_baseline=dict(value=v, unit="dirs/s", cores=1, kind="oracle", sample=desc),
+                e2e=dict(value=v, unit="dirs/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ ours
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import ctypes
+
+    from paper_2604_06575_b300 import polylab as pl
+    from paper_2604_06575_b300 import workloads
+
+    probe = ctypes.CDLL(os.path.join(ROOT, "paper_2604_06575_b300", "libpolylab_probe.so"))
+    probe.polylab_probe_alu.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_double)]
+
+    def alu_peak(kind, iters):
+        v = ctypes.c_double()
+        rc = probe.polylab_probe_alu(kind, iters, 4, 5, ctypes.byref(v))
+        return v.value if rc == 0 else float("nan")
+
+    # ---- workload (rank r: its own batch, weak scaling)
+    polys, Xs = workloads.batched_uneven(seed_off=rank, n_polys=args.polys)
+    dps = [pl.to_device(p, dev) for p in polys]
+    plans = [pl.Plan(d) for d in dps]
+    Xd = [torch.as_tensor(X, device=dev) for X in Xs]
+    npts = sum(X.shape[0] for X in Xs)
+    outs = {}
+    for form in ("fp64", "fp32"):
+        outs[form] = [(torch.empty(X.shape, dtype=torch.float64, device=dev),
+                       torch.empty(X.shape, dtype=torch.float64, device=dev),
+                       torch.empty(X.shape[0], 32, dtype=torch.uint8, device=dev)) for X in Xs]
+    opts = {f: pl.an_opts(prec=f, regularization=1e-6) for f in ("fp64", "fp32")}
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(form, events=None):
+        for i in range(len(dps)):
+            if events is not None:
+                events[i][0].record(stream)
+            pl.affine_normal(dps[i], Xd[i], opts[form], plan=plans[i], out=outs[form][i])
+            if events is not None:
+                events[i][1].record(stream)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+
+    def timed(form, steps, warmup):
+        for _ in range(warmup):
+            step(form)
+        barrier()
+        step_ms, kern_ms = [], []
+        for _ in range(steps):
+            flush.zero_()  # L2 flush between timed steps (outside the timed region)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in dps]
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            s0.record(stream)
+            step(form, ev)
+            s1.record(stream)
+            torch.cuda.synchronize()
+            step_ms.append(s0.elapsed_time(s1))
+            kern_ms.append(sum(a.elapsed_time(b) for a, b in ev))
+        barrier()
+        return step_ms, kern_ms
+
+    clocks = Clocks()
+    res = {}
+    for form in ("fp64", "fp32"):
+        step_ms, kern_ms = timed(form, args.steps, args.warmup)
+        t = torch.tensor([sum(step_ms)], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        res[form] = dict(total_ms=float(t.item()), step_ms=step_ms, kern_ms=kern_ms)
+    clk = clocks.stop()
+
+    # error of the FP32 form against the FP64 form, every point (angle, radians)
+    worst = 0.0
+    flags_equal = True
+    for i in range(len(dps)):
+        a, b = outs["fp64"][i][1], outs["fp32"][i][1]
+        ok = torch.isfinite(a).all(dim=1) & torch.isfinite(b).all(dim=1)
+        flags_equal &= bool(torch.equal(torch.isfinite(a).all(dim=1), torch.isfinite(b).all(dim=1)))
+        if ok.any():
+            c = (a[ok] * b[ok]).sum(dim=1).clamp(-1, 1)
+            worst = max(worst, float(torch.arccos(c).max()))
+    FP32_BOUND = 1e-3  # stated error of the FP32-sum form (radians), checked against the FP64 form
+    chosen = "fp32" if (worst <= FP32_BOUND and flags_equal) else "fp64"
+
+    def rate(form):
+        return npts * world * args.steps / (res[form]["total_ms"] * 1e-3)
+
+    # ---- e2e through the public API: pinned host points in, directions out, every step
+    Xcat = torch.cat([torch.as_tensor(X).reshape(-1) for X in Xs]).pin_memory()
+    Dhost = torch.empty(Xcat.shape, dtype=torch.float64).pin_memory()
+    offs = np.cumsum([0] + [X.shape[0] * X.shape[1] for X in Xs])
+    Xdev_flat = torch.empty(Xcat.numel(), dtype=torch.float64, device=dev)
+    Ddev_flat = torch.empty(Xcat.numel(), dtype=torch.float64, device=dev)
+    Xcat_flat, Dhost_flat = Xcat.view(-1), Dhost.view(-1)
+
+    def e2e_step():
+        Xdev_flat.copy_(Xcat_flat, non_blocking=True)
+        for i in range(len(dps)):
+            n = polys[i].n
+            xv = Xdev_flat[offs[i]:offs[i + 1]].view(-1, n)
+            dv = Ddev_flat[offs[i]:offs[i + 1]].view(-1, n)
+            pl.affine_normal(dps[i], xv, opts[chosen], plan=plans[i], out=(dv, None, None))
+        Dhost_flat.copy_(Ddev_flat, non_blocking=True)
+
+    for _ in range(args.warmup):
+        e2e_step()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(e2e_ms, op=dist.ReduceOp.MAX)
+    e2e_rate = npts * world * args.steps / (float(e2e_ms.item()) * 1e-3)
+    nbytes = int(Xcat.numel() * 8)
+
+    # ---- roofline of the dominant kernel (the exact affine-normal kernel, every launch of a step)
+    p32 = alu_peak(0, 20000)
+    p64 = alu_peak(1, 2000)
+    flops = {}
+    for p, X in zip(polys, Xs):
+        for key, val in exact_flops(p, X.shape[0]).items():
+            flops[key] = flops.get(key, 0.0) + val
+    kern_s = statistics.median(res[chosen]["kern_ms"]) * 1e-3
+    roof = alu_roofline(flops, kern_s, chosen, p32, p64)
+    roof["launches_per_step"] = len(dps)
+    roof["kernel"] = "affine_exact_kernel"
+
+    line = dict(metric=METRIC, value=round(rate(chosen), 1), unit="dirs/s", n_gpus=world, steps=args.steps,
+                warmup=args.warmup, ms_per_step=round(res[chosen]["total_ms"] / args.steps, 3),
+                higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f32 sums + f64 factorization" if chosen == "fp32" else "f64",
+                data="synthetic",
+                config=dict(workload=WORKLOAD, polys=args.polys, points=npts, form=chosen,
+                            regularization=1e-6, l2="flushed (256 MB write) before every timed step",
+                            parallelism=f"weak: each rank its own {args.polys}-poly batch" if world > 1 else "1 GPU"),
+                forms=dict(fp64=dict(dirs_per_s=round(rate("fp64"), 1),
+                                     ms_per_step=round(res["fp64"]["total_ms"] / args.steps, 3)),
+                           fp32=dict(dirs_per_s=round(rate("fp32"), 1),
+                                     ms_per_step=round(res["fp32"]["total_ms"] / args.steps, 3),
+                                     max_angle_vs_fp64_rad=worst, stated_bound_rad=FP32_BOUND,
+                                     flags_equal=flags_equal),
+                           speedup_vs_fp64=round(rate(chosen) / rate("fp64"), 3)),
+                e2e=dict(value=round(e2e_rate, 1), unit="dirs/s", h2d_bytes_per_step=nbytes,
+                         d2h_bytes_per_step=nbytes),
+                gpu_launches=len(dps) * args.steps,
+                roofline=roof, clocks=clk)
+
+    # ---- other rows of the path, measured after the headline
+    if not args.no_rows:
+        line["rows"] = measure_rows(pl, workloads, torch, dev, p32, p64)
+
+    if rank == 0 and not args.no_cpu_baseline:
+        done, dt, desc, ref = oracle_sample(polys, Xs, args.cpu_budget)
+        errs = []
+        for (i, j), nu in ref.items():
+            d = outs[chosen][i][0][j].cpu().numpy()
+            if np.all(np.isfinite(nu)):
+                errs.append(float(np.linalg.norm(d - nu) / np.linalg.norm(nu)))
+        line["cpu_baseline"] = dict(value=round(done / dt, 3), unit="dirs/s", cores=1, kind="oracle", sample=desc,
+                                    max_rel_err_of_reported_form=max(errs) if errs else None)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def measure_rows(pl, workloads, torch, dev, p32, p64):
+    rows = {}
+    stream = torch.cuda.current_stream()
+
+    def ev_time(fn, reps=5, warm=2):
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    # product simplify (4M-term expansion -> merged terms), host syncs included
+    A, B = workloads.product_pair()
+    da, db = pl.to_device(A, dev), pl.to_device(B, dev)
+    r = pl.mul(da, db)
+    for _ in range(2):
+        pl.mul(da, db)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(5):
+        t0 = time.perf_counter()
+        pl.mul(da, db)
+        torch.cuda.synchronize()
+        ts.append((time.perf_counter() - t0) * 1e3)
+    ms = statistics.median(ts)
+    rows["mul_product_pair"] = dict(workload="2 x 2,000 terms, n=20 each, 10 shared ids, deg<=6: 4,000,000 products",
+                                    ms=round(ms, 3), merged_terms=r.m,
+                                    expanded_terms_per_s=round(4e6 / (ms * 1e-3), 1))
+    # derivative evaluation forms
+    poly, X = workloads.eval_batch()
+    dp = pl.to_device(poly, dev)
+    Xd = torch.as_tensor(X, device=dev)
+    P, n = X.shape
+    out = (torch.empty(P, dtype=torch.float64, device=dev), torch.empty(P, n, dtype=torch.float64, device=dev),
+           torch.empty(P, n, n, dtype=torch.float64, device=dev))
+    ev = {}
+    with pl.Plan(dp) as plan:
+        for prec in ("fp64", "fp32"):
+            ms = ev_time(lambda: pl.eval_derivs(dp, Xd, plan=plan, prec=prec, out=out))
+            ev[prec] = dict(ms=round(ms, 3), evals_per_s=round(P / (ms * 1e-3), 1))
+    rows["eval_derivs"] = dict(workload="n=30, 5,000 terms deg<=4 <=4 active, 65,536 points in [-1,1]^30",
+                               forms=ev)
+    return rows
+
+
+if __name__ == "__main__":
+    main()
