@@ -114,6 +114,33 @@ polylab_status polylab_add(const polylab_poly* a, const polylab_poly* b, double 
                            polylab_poly_out* out, polylab_alloc_fn alloc, void* alloc_ctx,
                            polylab_stream stream);
 
+/* polylab_simplify for callers that cannot allocate device memory while the
+ * call runs -- a host application that reserved all device memory for its own
+ * pool up front, or one that runs under a fixed memory budget where a
+ * cudaMalloc or cudaMallocAsync could fail or stall at an unpredictable time.
+ * The paper has no counterpart of this call; it is an addition of this
+ * library.  The result is the same as polylab_simplify's.
+ *
+ * No device memory is allocated: all scratch lives in one 16 MiB array that
+ * the library declares at file scope on the device (every GPU that loads the
+ * library holds it until the process exits), and the output goes to buffers
+ * the caller passes: out->var_ids (HOST, p->n_vars entries), out->exps
+ * (DEVICE, capacity x p->n_vars bytes) and out->coef (DEVICE, capacity
+ * doubles).  On return out->n_terms is the number of merged terms.
+ * Limits: p->n_terms <= 65,536 and the whole working set (about 100 bytes per
+ * term plus 5 bytes per nonzero exponent and 16 (n+1)(D+1) bytes of binomial
+ * table, D the largest row degree) must fit in the array; otherwise
+ * POLYLAB_ERR_UNSUPPORTED with a message in polylab_last_error().  If the
+ * result has more than `capacity` terms, nothing is written, out->n_terms
+ * holds the count needed and the status is POLYLAB_ERR_INVALID_ARG.
+ * The first call on a device looks up the device address of the array
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call uses the same array, so calls that overlap on the GPU (several
+ * streams or host threads at once) race: serialise them.  Synchronises
+ * `stream` like polylab_simplify. */
+polylab_status polylab_simplify_noalloc(const polylab_poly* p, double zeroprec, polylab_poly_out* out,
+                                        int64_t capacity, polylab_stream stream);
+
 /* ------------------------------------------------------------------------ plans */
 
 /* A plan is the device-resident preprocessed form of one polynomial (its term

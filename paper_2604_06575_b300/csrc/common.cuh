@@ -14,6 +14,7 @@ namespace polylab {
 // ------------------------------------------------------------------ errors
 
 void set_last_error(const char* where, cudaError_t e);
+void set_last_message(const char* msg);
 
 #define PL_CUDA(call)                                   \
   do {                                                  \

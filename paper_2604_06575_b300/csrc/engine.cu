@@ -16,7 +16,9 @@
 // result in the canonical order directly.  Keys of up to 64 bits sort as
 // uint64, up to 128 bits as unsigned __int128.
 #include <algorithm>
+#include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <unordered_map>
 #include <vector>
 
@@ -76,8 +78,10 @@ __global__ void add_tile_offsets(uint32_t* __restrict__ out, const uint32_t* __r
   if (i < n) out[i] += offs[i / kScanTile];
 }
 
-// Exclusive scan of n uint32 values (in may alias out).
-polylab_status exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, Scratch& scr, cudaStream_t s) {
+// Exclusive scan of n uint32 values (in may alias out).  `Mem` provides the
+// scratch buffers (stream-ordered allocations, or a fixed arena).
+template <class Mem>
+polylab_status exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, Mem& scr, cudaStream_t s) {
   if (n <= 0) return POLYLAB_OK;
   const int64_t tiles = ceil_div(n, kScanTile);
   uint32_t* sums = nullptr;
@@ -314,8 +318,8 @@ __global__ void __launch_bounds__(256) sort_scatter(const K* __restrict__ keys, 
 
 // Sorts (keys, vals) by the low `bits` bits of the key; returns which buffer
 // holds the result (0 = the input buffers, 1 = the alternates).
-template <typename K>
-polylab_status radix_sort(K* keys, uint32_t* vals, K* akeys, uint32_t* avals, int64_t N, int bits, Scratch& scr,
+template <typename K, class Mem>
+polylab_status radix_sort(K* keys, uint32_t* vals, K* akeys, uint32_t* avals, int64_t N, int bits, Mem& scr,
                           cudaStream_t s, int* which) {
   *which = 0;
   if (N <= 1 || bits <= 0) return POLYLAB_OK;
@@ -494,7 +498,8 @@ struct Operand {
   uint32_t nnz = 0;
 };
 
-polylab_status build_operand(const polylab_poly* p, const std::vector<int>& colmap_h, Operand* op, Scratch& scr,
+template <class Mem>
+polylab_status build_operand(const polylab_poly* p, const std::vector<int>& colmap_h, Operand* op, Mem& scr,
                              cudaStream_t s) {
   op->m = p->n_terms;
   const int64_t m = op->m;
@@ -564,10 +569,10 @@ int key_bits_u128(u128 total) {  // bits to represent values 0 .. total-1
   return b;
 }
 
-template <typename K>
+template <typename K, class Mem>
 polylab_status run_pipeline(int n, int D, int64_t N, const std::vector<K>& Sh, int mode, const Operand& A,
                             const Operand& B, const polylab_poly* pa, const polylab_poly* pb, double zeroprec,
-                            int bits, polylab_poly_out* out, polylab_alloc_fn alloc, void* ctx, Scratch& scr,
+                            int bits, polylab_poly_out* out, polylab_alloc_fn alloc, void* ctx, Mem& scr,
                             cudaStream_t s) {
   const int D1 = D + 1;
   K* S = nullptr;
@@ -593,7 +598,7 @@ polylab_status run_pipeline(int n, int D, int64_t N, const std::vector<K>& Sh, i
   }
   PL_TRY(launch_status("keys"));
   int which = 0;
-  PL_TRY(radix_sort<K>(keys, vals, akeys, avals, N, bits, scr, s, &which));
+  PL_TRY((radix_sort<K, Mem>(keys, vals, akeys, avals, N, bits, scr, s, &which)));
   if (which) {
     std::swap(keys, akeys);
     std::swap(vals, avals);
@@ -645,8 +650,9 @@ polylab_status run_pipeline(int n, int D, int64_t N, const std::vector<K>& Sh, i
   return launch_status("unpack_rows");
 }
 
-polylab_status engine(const polylab_poly* pa, const polylab_poly* pb, int mode, double zeroprec,
-                      polylab_poly_out* out, polylab_alloc_fn alloc, void* ctx, cudaStream_t s) {
+template <class Mem>
+polylab_status engine_with(Mem& scr, const polylab_poly* pa, const polylab_poly* pb, int mode, double zeroprec,
+                           polylab_poly_out* out, polylab_alloc_fn alloc, void* ctx, cudaStream_t s) {
   if (!out || !alloc || !out->var_ids || !(zeroprec >= 0.0)) return POLYLAB_ERR_INVALID_ARG;
   PL_TRY(check_poly(pa));
   const bool is_mul = mode != kSimplify;  // two operands (mul or add)
@@ -678,7 +684,6 @@ polylab_status engine(const polylab_poly* pa, const polylab_poly* pb, int mode, 
                    : mode == kAdd ? pa->n_terms + pb->n_terms : pa->n_terms;
   if (N >= ((int64_t)1 << 31)) return POLYLAB_ERR_UNSUPPORTED;
   if (N == 0) return POLYLAB_OK;
-  Scratch scr(s);
   Operand A, B;
   PL_TRY(build_operand(pa, mapA, &A, scr, s));
   if (is_mul) PL_TRY(build_operand(pb, mapB, &B, scr, s));
@@ -691,9 +696,93 @@ polylab_status engine(const polylab_poly* pa, const polylab_poly* pb, int mode, 
   if (bits <= 64) {
     std::vector<uint64_t> S64(S128.size());
     for (size_t i = 0; i < S128.size(); ++i) S64[i] = (uint64_t)S128[i];
-    return run_pipeline<uint64_t>(n, D, N, S64, mode, A, B, pa, pb, zeroprec, bits, out, alloc, ctx, scr, s);
+    return run_pipeline<uint64_t, Mem>(n, D, N, S64, mode, A, B, pa, pb, zeroprec, bits, out, alloc, ctx, scr,
+                                       s);
   }
-  return run_pipeline<u128>(n, D, N, S128, mode, A, B, pa, pb, zeroprec, bits, out, alloc, ctx, scr, s);
+  return run_pipeline<u128, Mem>(n, D, N, S128, mode, A, B, pa, pb, zeroprec, bits, out, alloc, ctx, scr, s);
+}
+
+polylab_status engine(const polylab_poly* pa, const polylab_poly* pb, int mode, double zeroprec,
+                      polylab_poly_out* out, polylab_alloc_fn alloc, void* ctx, cudaStream_t s) {
+  Scratch scr(s);
+  return engine_with(scr, pa, pb, mode, zeroprec, out, alloc, ctx, s);
+}
+
+// ------------------------------------------------ no-allocation simplify
+// For callers that may not allocate device memory during a call: all scratch
+// of polylab_simplify_noalloc is carved from this file-scope array.  Every
+// GPU that loads the library holds it until the process exits.
+
+constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;  // 16 MiB
+constexpr int64_t kNoAllocMaxTerms = 65536;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+// Fixed arena over the static array: 256-byte aligned bump allocation, no frees.
+struct Arena {
+  unsigned char* base;
+  size_t cap;
+  size_t used = 0;
+  template <typename T>
+  polylab_status get(T** out, size_t count) {
+    *out = nullptr;
+    if (count == 0) count = 1;
+    const size_t bytes = (count * sizeof(T) + 255) & ~size_t(255);
+    if (bytes > cap - used) {
+      char msg[160];
+      snprintf(msg, sizeof(msg), "polylab_simplify_noalloc: working set exceeds the %zu-byte static scratch array",
+               cap);
+      set_last_message(msg);
+      return POLYLAB_ERR_UNSUPPORTED;
+    }
+    *out = reinterpret_cast<T*>(base + used);
+    used += bytes;
+    return POLYLAB_OK;
+  }
+};
+
+// Device address of the array, looked up once per device with that device
+// current (in host code the symbol itself is only a host-side stand-in).
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_addr[256] = {};
+
+polylab_status noalloc_base(unsigned char** out) {
+  int dev = 0;
+  PL_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 256) return POLYLAB_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* a = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&a, g_noalloc_scratch);
+    if (e != cudaSuccess) {
+      set_last_error("cudaGetSymbolAddress(g_noalloc_scratch)", e);
+      return POLYLAB_ERR_CUDA;
+    }
+    g_noalloc_addr[dev] = a;
+  }
+  *out = static_cast<unsigned char*>(g_noalloc_addr[dev]);
+  return POLYLAB_OK;
+}
+
+// Hands the caller's output buffers to the pipeline instead of allocating.
+struct CallerBuffers {
+  uint8_t* exps;
+  double* coef;
+  int64_t capacity;
+  int n;
+  int calls = 0;
+  bool too_small = false;
+};
+
+void* caller_buffers(size_t bytes, void* ctx) {
+  CallerBuffers* b = static_cast<CallerBuffers*>(ctx);
+  const int call = b->calls++;
+  const size_t room = call == 0 ? (size_t)b->capacity * (size_t)b->n : (size_t)b->capacity * sizeof(double);
+  if (bytes > room) {
+    b->too_small = true;
+    return nullptr;
+  }
+  return call == 0 ? static_cast<void*>(b->exps) : static_cast<void*>(b->coef);
 }
 
 }  // namespace
@@ -716,6 +805,33 @@ polylab_status polylab_add(const polylab_poly* a, const polylab_poly* b, double 
                            polylab_alloc_fn alloc, void* alloc_ctx, polylab_stream stream) {
   if (!b) return POLYLAB_ERR_INVALID_ARG;
   return polylab::engine(a, b, polylab::kAdd, zeroprec, out, alloc, alloc_ctx, (cudaStream_t)stream);
+}
+
+polylab_status polylab_simplify_noalloc(const polylab_poly* p, double zeroprec, polylab_poly_out* out,
+                                        int64_t capacity, polylab_stream stream) {
+  using namespace polylab;
+  if (!p || !out || capacity < 0 || (capacity > 0 && (!out->exps || !out->coef))) return POLYLAB_ERR_INVALID_ARG;
+  if (p->n_terms > kNoAllocMaxTerms) {
+    char msg[160];
+    snprintf(msg, sizeof(msg), "polylab_simplify_noalloc: %lld terms exceed the limit of %lld",
+             (long long)p->n_terms, (long long)kNoAllocMaxTerms);
+    set_last_message(msg);
+    return POLYLAB_ERR_UNSUPPORTED;
+  }
+  unsigned char* base = nullptr;
+  PL_TRY(noalloc_base(&base));
+  Arena arena{base, kNoAllocScratchBytes};
+  CallerBuffers buf{out->exps, out->coef, capacity, p->n_vars};
+  const polylab_status st =
+      engine_with(arena, p, nullptr, kSimplify, zeroprec, out, caller_buffers, &buf, (cudaStream_t)stream);
+  // the pipeline resets the output pointers; hand the caller's buffers back
+  out->exps = buf.exps;
+  out->coef = buf.coef;
+  if (st == POLYLAB_ERR_OOM && buf.too_small) {
+    set_last_message("polylab_simplify_noalloc: the result has more terms than `capacity`; n_terms holds the count");
+    return POLYLAB_ERR_INVALID_ARG;
+  }
+  return st;
 }
 
 }  // extern "C"

@@ -15,6 +15,8 @@ void set_last_error(const char* where, cudaError_t e) {
   snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%s)", where, cudaGetErrorString(e), cudaGetErrorName(e));
 }
 
+void set_last_message(const char* msg) { snprintf(g_last_error, sizeof(g_last_error), "%s", msg); }
+
 int num_sms() {
   static int cached = 0;
   if (!cached) {

@@ -73,14 +73,15 @@ _lib.polylab_simplify.argtypes = [C.POINTER(_Poly), C.c_double, C.POINTER(_PolyO
 _lib.polylab_mul.argtypes = [C.POINTER(_Poly), C.POINTER(_Poly), C.c_double, C.POINTER(_PolyOut), ALLOC_FN,
                              C.c_void_p, C.c_void_p]
 _lib.polylab_add.argtypes = _lib.polylab_mul.argtypes
+_lib.polylab_simplify_noalloc.argtypes = [C.POINTER(_Poly), C.c_double, C.POINTER(_PolyOut), C.c_int64, C.c_void_p]
 _lib.polylab_an_opts_default.argtypes = [C.POINTER(_AnOpts)]
 for _f in ("polylab_plan_create", "polylab_plan_destroy", "polylab_eval_derivs", "polylab_affine_normal",
-           "polylab_simplify", "polylab_mul", "polylab_add"):
+           "polylab_simplify", "polylab_mul", "polylab_add", "polylab_simplify_noalloc"):
     getattr(_lib, _f).restype = C.c_int
 
 EXPORTED = ["polylab_status_string", "polylab_last_error", "polylab_simplify", "polylab_mul", "polylab_add",
             "polylab_plan_create", "polylab_plan_destroy", "polylab_plan_closure_size", "polylab_eval_derivs",
-            "polylab_an_opts_default", "polylab_affine_normal"]
+            "polylab_an_opts_default", "polylab_affine_normal", "polylab_simplify_noalloc"]
 
 
 def lib():
@@ -267,3 +268,19 @@ def add(a: DevPoly, b: DevPoly, zeroprec: float = 0.0) -> DevPoly:
     return _run_out("polylab_add",
                     lambda o, fn: _lib.polylab_add(C.byref(ca), C.byref(cb), zeroprec, o, fn, None, _stream()),
                     a.n + b.n, a.coef.device)
+
+
+def simplify_noalloc(p: DevPoly, exps_out: torch.Tensor, coef_out: torch.Tensor, zeroprec: float = 0.0) -> DevPoly:
+    """polylab_simplify without device allocation inside the call: the result
+    is written to the caller's uint8 [capacity, n] and float64 [capacity]
+    buffers and returned as views of them."""
+    assert exps_out.dtype == torch.uint8 and coef_out.dtype == torch.float64
+    cap = int(coef_out.shape[0])
+    assert exps_out.shape == (cap, p.n)
+    ids = np.zeros(max(p.n, 1), dtype=np.uint64)
+    out = _PolyOut(0, ids.ctypes.data_as(C.POINTER(C.c_uint64)), 0, _ptr(exps_out), _ptr(coef_out))
+    cp = p.cstruct()
+    st = _lib.polylab_simplify_noalloc(C.byref(cp), zeroprec, C.byref(out), cap, _stream())
+    _check("polylab_simplify_noalloc", st)
+    m = int(out.n_terms)
+    return DevPoly(ids[: out.n_vars].copy(), exps_out[:m], coef_out[:m])

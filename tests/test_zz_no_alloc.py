@@ -1,0 +1,64 @@
+"""polylab_simplify_noalloc: the simplify entry point for callers that cannot
+allocate device memory during a call (all scratch in a static device array,
+output in caller buffers).  Checked through the C ABI against
+polylab_simplify, with the engine tests' bar (exponents bit-exact,
+coefficients within 1e-12 of the sum of |contributions|), on two calls in a
+row with different inputs, so the second call runs on the first call's
+leftover scratch contents.  This file is collected last on purpose."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2604_06575_b300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def _inputs():
+    rng = np.random.default_rng(11)
+    # many repeated rows, unsorted variable ids
+    e1 = rng.integers(0, 3, size=(20000, 7)).astype(np.uint8)
+    p1 = workloads.Poly(np.array([9, 2, 7, 4, 1, 8, 3], np.uint64), e1, rng.standard_normal(20000))
+    e2 = workloads.sparse_monomials(rng, 12, 3000, 6, 4)
+    e2 = np.concatenate([e2, e2[:1000]])          # 1,000 repeats
+    p2 = workloads.Poly(np.arange(12, dtype=np.uint64), e2, rng.standard_normal(e2.shape[0]))
+    return p1, p2
+
+
+def _same(a, b, scale):
+    assert [int(v) for v in a.var_ids] == [int(v) for v in b.var_ids]
+    assert torch.equal(a.exps, b.exps)
+    assert np.all(np.abs(a.coef.cpu().numpy() - b.coef.cpu().numpy()) <= 1e-12 * scale)
+
+
+def test_noalloc_matches_simplify_twice(cuda_ok):
+    from paper_2604_06575_b300 import polylab as pl
+    p1, p2 = _inputs()
+    for p in (p1, p2, p1):  # three calls in a row, the first input again last
+        dp = pl.to_device(p)
+        ref = pl.simplify(dp)
+        cap = p.m
+        ex = torch.full((cap, p.n), 0xAB, dtype=torch.uint8, device="cuda")
+        co = torch.full((cap,), float("nan"), dtype=torch.float64, device="cuda")
+        got = pl.simplify_noalloc(dp, ex, co)
+        torch.cuda.synchronize()
+        assert got.m == ref.m
+        _same(got, ref, np.abs(p.coef).sum())
+
+
+def test_noalloc_limits(cuda_ok):
+    from paper_2604_06575_b300 import polylab as pl
+    rng = np.random.default_rng(2)
+    big = workloads.Poly(np.arange(3, dtype=np.uint64), rng.integers(0, 2, size=(70000, 3)).astype(np.uint8),
+                         np.ones(70000))
+    dp = pl.to_device(big)
+    ex = torch.empty((8, 3), dtype=torch.uint8, device="cuda")
+    co = torch.empty(8, dtype=torch.float64, device="cuda")
+    with pytest.raises(pl.PolylabError) as ei:
+        pl.simplify_noalloc(dp, ex, co)
+    assert ei.value.status == 7  # more terms than the static limit
+    small = workloads.Poly(np.arange(3, dtype=np.uint64), rng.integers(0, 3, size=(500, 3)).astype(np.uint8),
+                           np.ones(500))
+    with pytest.raises(pl.PolylabError) as ei:  # 27 distinct rows, room for 8
+        pl.simplify_noalloc(pl.to_device(small), ex, co)
+    assert ei.value.status == 1
