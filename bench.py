@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-rows", action="store_true", help="skip the per-row sub-measurements")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work per sample")
+    ap.add_argument("--forms", default="fp64,fp32", help="forms to time (profiling runs time one)")
+    ap.add_argument("--config", default=None,
+                    help="threads,ctas_per_sm,order instead of autotuning (profiling runs)")
     return ap.parse_args()
 
 
@@ -233,62 +236,75 @@ def main():
     plans = [pl.Plan(d) for d in dps]
     Xd = [torch.as_tensor(X, device=dev) for X in Xs]
     npts = sum(X.shape[0] for X in Xs)
-    outs = {}
-    for form in ("fp64", "fp32"):
-        outs[form] = [(torch.empty(X.shape, dtype=torch.float64, device=dev),
-                       torch.empty(X.shape, dtype=torch.float64, device=dev),
-                       torch.empty(X.shape[0], 32, dtype=torch.uint8, device=dev)) for X in Xs]
     opts = {f: pl.an_opts(prec=f, regularization=1e-6) for f in ("fp64", "fp32")}
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
-
-    def step(form, events=None):
-        for i in range(len(dps)):
-            if events is not None:
-                events[i][0].record(stream)
-            pl.affine_normal(dps[i], Xd[i], opts[form], plan=plans[i], out=outs[form][i])
-            if events is not None:
-                events[i][1].record(stream)
 
     def barrier():
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
 
+    def capture(batch):
+        """One persistent launch (memset of the work counter + kernel) in a CUDA graph."""
+        g = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            batch.run()
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g):
+            batch.run()
+        return g
+
+    forms = [f for f in ("fp64", "fp32") if f in args.forms.split(",")]
+    batches, graphs, tuned = {}, {}, {}
+    for form in forms:
+        batches[form] = pl.Batch(dps, plans, Xd, opts[form])
+        if args.config:
+            t, c, o = (int(v) for v in args.config.split(","))
+            batches[form].set_config(t, c, o)
+            tuned[form] = dict(batches[form].config(), ms=None)
+        else:
+            cfg, ms = batches[form].autotune(reps=1)
+            tuned[form] = dict(cfg, ms=round(ms, 3))
+        graphs[form] = capture(batches[form])
+
     def timed(form, steps, warmup):
+        g = graphs[form]
         for _ in range(warmup):
-            step(form)
+            g.replay()
         barrier()
-        step_ms, kern_ms = [], []
+        step_ms = []
         for _ in range(steps):
             flush.zero_()  # L2 flush between timed steps (outside the timed region)
-            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in dps]
             s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
             s0.record(stream)
-            step(form, ev)
+            g.replay()
             s1.record(stream)
             torch.cuda.synchronize()
             step_ms.append(s0.elapsed_time(s1))
-            kern_ms.append(sum(a.elapsed_time(b) for a, b in ev))
         barrier()
-        return step_ms, kern_ms
+        return step_ms
 
     clocks = Clocks()
     res = {}
-    for form in ("fp64", "fp32"):
-        step_ms, kern_ms = timed(form, args.steps, args.warmup)
+    for form in forms:
+        step_ms = timed(form, args.steps, args.warmup)
         t = torch.tensor([sum(step_ms)], dtype=torch.float64, device=dev)
         if world > 1:
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        res[form] = dict(total_ms=float(t.item()), step_ms=step_ms, kern_ms=kern_ms)
+        # the step is one launch of the exact kernel, so its duration is the kernel's
+        res[form] = dict(total_ms=float(t.item()), step_ms=step_ms, kern_ms=step_ms)
     clk = clocks.stop()
 
     # error of the FP32 form against the FP64 form, every point (angle, radians)
-    worst = 0.0
-    flags_equal = True
-    for i in range(len(dps)):
-        a, b = outs["fp64"][i][1], outs["fp32"][i][1]
+    worst = 0.0 if len(forms) == 2 else float("nan")
+    flags_equal = len(forms) == 2
+    for i in range(len(dps) if len(forms) == 2 else 0):
+        a, b = batches["fp64"].Du[i], batches["fp32"].Du[i]
         ok = torch.isfinite(a).all(dim=1) & torch.isfinite(b).all(dim=1)
         flags_equal &= bool(torch.equal(torch.isfinite(a).all(dim=1), torch.isfinite(b).all(dim=1)))
         if ok.any():
@@ -296,8 +312,12 @@ def main():
             worst = max(worst, float(torch.arccos(c).max()))
     FP32_BOUND = 1e-3  # stated error of the FP32-sum form (radians), checked against the FP64 form
     chosen = "fp32" if (worst <= FP32_BOUND and flags_equal) else "fp64"
+    if len(forms) == 1:
+        chosen = forms[0]
 
     def rate(form):
+        if form not in res:
+            return float("nan")
         return npts * world * args.steps / (res[form]["total_ms"] * 1e-3)
 
     # ---- e2e through the public API: pinned host points in, directions out, every step
@@ -306,16 +326,15 @@ def main():
     offs = np.cumsum([0] + [X.shape[0] * X.shape[1] for X in Xs])
     Xdev_flat = torch.empty(Xcat.numel(), dtype=torch.float64, device=dev)
     Ddev_flat = torch.empty(Xcat.numel(), dtype=torch.float64, device=dev)
-    Xcat_flat, Dhost_flat = Xcat.view(-1), Dhost.view(-1)
+    xv = [Xdev_flat[offs[i]:offs[i + 1]].view(-1, polys[i].n) for i in range(len(polys))]
+    dv = [Ddev_flat[offs[i]:offs[i + 1]].view(-1, polys[i].n) for i in range(len(polys))]
+    e2e_batch = pl.Batch(dps, plans, xv, opts[chosen], want_unit=False, want_info=False, D=dv)
+    e2e_batch.set_config(**{k: tuned[chosen][k] for k in ("threads", "ctas_per_sm", "order")})
 
     def e2e_step():
-        Xdev_flat.copy_(Xcat_flat, non_blocking=True)
-        for i in range(len(dps)):
-            n = polys[i].n
-            xv = Xdev_flat[offs[i]:offs[i + 1]].view(-1, n)
-            dv = Ddev_flat[offs[i]:offs[i + 1]].view(-1, n)
-            pl.affine_normal(dps[i], xv, opts[chosen], plan=plans[i], out=(dv, None, None))
-        Dhost_flat.copy_(Ddev_flat, non_blocking=True)
+        Xdev_flat.copy_(Xcat.view(-1), non_blocking=True)
+        e2e_batch.run()
+        Dhost.view(-1).copy_(Ddev_flat, non_blocking=True)
 
     for _ in range(args.warmup):
         e2e_step()
@@ -331,6 +350,8 @@ def main():
         dist.all_reduce(e2e_ms, op=dist.ReduceOp.MAX)
     e2e_rate = npts * world * args.steps / (float(e2e_ms.item()) * 1e-3)
     nbytes = int(Xcat.numel() * 8)
+    outs = {f: [(batches[f].D[i], batches[f].Du[i], batches[f].info[i]) for i in range(len(dps))]
+            for f in forms}
 
     # ---- roofline of the dominant kernel (the exact affine-normal kernel, every launch of a step)
     p32 = alu_peak(0, 20000)
@@ -341,8 +362,8 @@ def main():
             flops[key] = flops.get(key, 0.0) + val
     kern_s = statistics.median(res[chosen]["kern_ms"]) * 1e-3
     roof = alu_roofline(flops, kern_s, chosen, p32, p64)
-    roof["launches_per_step"] = len(dps)
-    roof["kernel"] = "affine_exact_kernel"
+    roof["launches_per_step"] = 1
+    roof["kernel"] = "affine_exact_kernel (one persistent launch per step, CUDA-graph replay)"
 
     line = dict(metric=METRIC, value=round(rate(chosen), 1), unit="dirs/s", n_gpus=world, steps=args.steps,
                 warmup=args.warmup, ms_per_step=round(res[chosen]["total_ms"] / args.steps, 3),
@@ -353,15 +374,16 @@ def main():
                             regularization=1e-6, l2="flushed (256 MB write) before every timed step",
                             parallelism=f"weak: each rank its own {args.polys}-poly batch" if world > 1 else "1 GPU"),
                 forms=dict(fp64=dict(dirs_per_s=round(rate("fp64"), 1),
-                                     ms_per_step=round(res["fp64"]["total_ms"] / args.steps, 3)),
+                                     ms_per_step=round(res.get("fp64", {}).get("total_ms", float("nan")) / args.steps, 3)),
                            fp32=dict(dirs_per_s=round(rate("fp32"), 1),
-                                     ms_per_step=round(res["fp32"]["total_ms"] / args.steps, 3),
+                                     ms_per_step=round(res.get("fp32", {}).get("total_ms", float("nan")) / args.steps, 3),
                                      max_angle_vs_fp64_rad=worst, stated_bound_rad=FP32_BOUND,
                                      flags_equal=flags_equal),
                            speedup_vs_fp64=round(rate(chosen) / rate("fp64"), 3)),
                 e2e=dict(value=round(e2e_rate, 1), unit="dirs/s", h2d_bytes_per_step=nbytes,
                          d2h_bytes_per_step=nbytes),
-                gpu_launches=len(dps) * args.steps,
+                gpu_launches=args.steps,
+                autotune=tuned,
                 roofline=roof, clocks=clk)
 
     # ---- other rows of the path, measured after the headline

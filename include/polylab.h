@@ -237,6 +237,57 @@ polylab_status polylab_affine_normal(const polylab_poly* p, const polylab_plan* 
                                      int64_t P, const polylab_an_opts* opts, double* D, double* Dunit,
                                      polylab_an_info* info, polylab_stream stream);
 
+/* ------------------------------------------- batched exact directions (one launch) */
+
+/* A batch is a set of polynomials (each with its own n, term list and point
+ * set) whose exact affine-normal directions are computed by ONE persistent
+ * kernel launch: (polynomial, point) work items are taken from a device
+ * counter, most expensive polynomials first, so an uneven batch keeps every
+ * SM busy.  polylab_batch_create uploads the descriptors (and builds a term
+ * plan for every NULL entry of `plans`; `polys` may then not be NULL), so
+ * polylab_batch_run only enqueues one memset and one kernel on `stream` and
+ * may be captured into a CUDA graph and replayed.  Each run overwrites
+ * D[i], Dunit[i] (DEVICE P[i] x n_i or NULL) and info[i] (DEVICE P[i] records
+ * or NULL) from X[i] (DEVICE P[i] x n_i).  opts->method must be
+ * POLYLAB_MF_EXACT; opts->prec POLYLAB_FP64 or POLYLAB_FP32.  The arrays of
+ * pointers passed to create are read during the call only. */
+typedef struct polylab_batch polylab_batch;
+
+/* Launch configuration: CTA size (64, 128 or 256 threads per point), a cap
+ * on resident CTAs per SM (0: the occupancy limit) and the work order (1:
+ * most expensive polynomials first, 0: as given). */
+typedef struct {
+  int32_t threads;
+  int32_t ctas_per_sm;
+  int32_t order;
+} polylab_batch_config;
+
+polylab_status polylab_batch_create(int32_t n_polys, const polylab_poly* polys,
+                                    const polylab_plan* const* plans, const double* const* X,
+                                    const int64_t* P, const polylab_an_opts* opts, double* const* D,
+                                    double* const* Dunit, polylab_an_info* const* info,
+                                    polylab_stream stream, polylab_batch** batch);
+polylab_status polylab_batch_run(polylab_batch* batch, polylab_stream stream);
+polylab_status polylab_batch_get_config(const polylab_batch* batch, polylab_batch_config* cfg);
+polylab_status polylab_batch_set_config(polylab_batch* batch, const polylab_batch_config* cfg,
+                                        polylab_stream stream);
+/* The project's autotuner: times every configuration in {64,128,256}
+ * threads x {occupancy, 2, 4} CTAs per SM x {cost order, given order} on
+ * this batch (one warm-up and `reps` timed runs each, CUDA events on
+ * `stream`, synchronising), keeps the fastest and returns it (and its mean
+ * time in ms, if best_ms is not NULL).  The outputs hold the last run's
+ * results. */
+polylab_status polylab_batch_autotune(polylab_batch* batch, int32_t reps, polylab_stream stream,
+                                      polylab_batch_config* chosen, float* best_ms);
+polylab_status polylab_batch_destroy(polylab_batch* batch, polylab_stream stream);
+
+/* create + run + destroy in one call. */
+polylab_status polylab_affine_normal_batched(int32_t n_polys, const polylab_poly* polys,
+                                             const polylab_plan* const* plans, const double* const* X,
+                                             const int64_t* P, const polylab_an_opts* opts, double* const* D,
+                                             double* const* Dunit, polylab_an_info* const* info,
+                                             polylab_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

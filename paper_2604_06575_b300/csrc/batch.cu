@@ -1,0 +1,247 @@
+// Host side of batched exact affine-normal launches: descriptors, work order,
+// configuration and the project's autotuner, plus the public batch API.
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+
+#include "batch.cuh"
+
+namespace polylab {
+
+polylab_status exact_batch_upload_order(ExactBatch* b, cudaStream_t s) {
+  const int n = b->n_desc;
+  std::vector<int>& ord = b->host_order;
+  ord.resize(n);
+  std::iota(ord.begin(), ord.end(), 0);
+  if (b->cfg.order == 1) {
+    std::vector<double> cost(n);
+    for (int i = 0; i < n; ++i) cost[i] = exact_point_cost(b->host_descs[i], b->host_descs[i].max_support);
+    std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+  }
+  b->host_prefix.assign(n + 1, 0);
+  for (int i = 0; i < n; ++i) b->host_prefix[i + 1] = b->host_prefix[i] + b->host_descs[ord[i]].P;
+  b->total = b->host_prefix[n];
+  PL_CUDA(cudaMemcpyAsync(b->order, ord.data(), n * sizeof(int), cudaMemcpyHostToDevice, s));
+  PL_CUDA(cudaMemcpyAsync(b->prefix, b->host_prefix.data(), (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  PL_CUDA(cudaStreamSynchronize(s));  // host vectors may change after this returns
+  return POLYLAB_OK;
+}
+
+static int default_threads(const ExactBatch* b) {
+  int nmax = 1;
+  for (const auto& d : b->host_descs) nmax = std::max(nmax, d.n);
+  return nmax <= 16 ? 64 : nmax <= 48 ? 128 : 256;
+}
+
+polylab_status exact_batch_init(ExactBatch* b, int n, const polylab_plan* const* plans, const double* const* X,
+                                const int64_t* P, const polylab_an_opts* o, double* const* D,
+                                double* const* Dunit, polylab_an_info* const* info, cudaStream_t s) {
+  b->opts = *o;
+  b->n_desc = n;
+  b->host_descs.resize(n);
+  for (int i = 0; i < n; ++i) {
+    const polylab_plan* pl = plans[i];
+    if (!pl || P[i] < 0 || (P[i] > 0 && (!X[i] || !D[i]))) return POLYLAB_ERR_INVALID_ARG;
+    ExactDesc& d = b->host_descs[i];
+    d.terms = pl->terms;
+    d.m = pl->m;
+    d.n = pl->n;
+    d.E = std::max(1, pl->max_exp);
+    d.max_support = pl->max_support;
+    d.mats_in_smem = 1;
+    d.X = X[i];
+    d.P = P[i];
+    d.D = D[i];
+    d.Dunit = Dunit ? Dunit[i] : nullptr;
+    d.info = info ? info[i] : nullptr;
+  }
+  if (b->cfg.threads == 0) b->cfg.threads = default_threads(b);
+  PL_TRY(prepare_exact_batch(b));
+  PL_CUDA(cudaMallocAsync(&b->descs, std::max(n, 1) * sizeof(ExactDesc), s));
+  PL_CUDA(cudaMallocAsync(&b->order, std::max(n, 1) * sizeof(int), s));
+  PL_CUDA(cudaMallocAsync(&b->prefix, (n + 1) * sizeof(int64_t), s));
+  PL_CUDA(cudaMallocAsync(&b->counter, sizeof(int), s));
+  PL_CUDA(cudaMemcpyAsync(b->descs, b->host_descs.data(), n * sizeof(ExactDesc), cudaMemcpyHostToDevice, s));
+  PL_TRY(exact_batch_upload_order(b, s));
+  if (b->gws_stride > 0) {
+    // enough workspace for the largest grid any configuration may launch
+    b->gws_bytes = (size_t)num_sms() * 32 * b->gws_stride;
+    PL_CUDA(cudaMallocAsync(&b->gws, b->gws_bytes, s));
+  }
+  return POLYLAB_OK;
+}
+
+// Shared-memory layout depends on the CTA size: recompute it, re-upload the
+// descriptors and grow the global workspace when needed.
+polylab_status exact_batch_relayout(ExactBatch* b, cudaStream_t s) {
+  PL_TRY(prepare_exact_batch(b));
+  PL_CUDA(cudaMemcpyAsync(b->descs, b->host_descs.data(), b->n_desc * sizeof(ExactDesc), cudaMemcpyHostToDevice, s));
+  const size_t need = (size_t)num_sms() * 32 * b->gws_stride;
+  if (need > b->gws_bytes) {
+    if (b->gws) PL_CUDA(cudaFreeAsync(b->gws, s));
+    b->gws = nullptr;
+    PL_CUDA(cudaMallocAsync(&b->gws, need, s));
+    b->gws_bytes = need;
+  }
+  PL_CUDA(cudaStreamSynchronize(s));
+  return POLYLAB_OK;
+}
+
+void exact_batch_release(ExactBatch* b, cudaStream_t s) {
+  if (b->descs) cudaFreeAsync(b->descs, s);
+  if (b->order) cudaFreeAsync(b->order, s);
+  if (b->prefix) cudaFreeAsync(b->prefix, s);
+  if (b->counter) cudaFreeAsync(b->counter, s);
+  if (b->gws) cudaFreeAsync(b->gws, s);
+  for (polylab_plan* p : b->owned_plans) polylab_plan_destroy(p, (polylab_stream)s);
+  b->descs = nullptr;
+  b->order = nullptr;
+  b->prefix = nullptr;
+  b->counter = nullptr;
+  b->gws = nullptr;
+  b->owned_plans.clear();
+}
+
+}  // namespace polylab
+
+using namespace polylab;
+
+extern "C" {
+
+polylab_status polylab_batch_create(int32_t n_polys, const polylab_poly* polys, const polylab_plan* const* plans,
+                                    const double* const* X, const int64_t* P, const polylab_an_opts* opts,
+                                    double* const* D, double* const* Dunit, polylab_an_info* const* info,
+                                    polylab_stream stream, polylab_batch** out) {
+  if (!out || n_polys < 0 || !opts || (n_polys > 0 && (!X || !P || !D))) return POLYLAB_ERR_INVALID_ARG;
+  if (n_polys > 0 && !polys && !plans) return POLYLAB_ERR_INVALID_ARG;
+  if (opts->method != POLYLAB_MF_EXACT) return POLYLAB_ERR_UNSUPPORTED;
+  if (opts->prec != POLYLAB_FP64 && opts->prec != POLYLAB_FP32) return POLYLAB_ERR_INVALID_ARG;
+  if (!(opts->regularization >= 0.0)) return POLYLAB_ERR_INVALID_ARG;
+  *out = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  polylab_batch* h = new polylab_batch();
+  std::vector<const polylab_plan*> use(n_polys);
+  polylab_status st = POLYLAB_OK;
+  for (int i = 0; i < n_polys && st == POLYLAB_OK; ++i) {
+    use[i] = plans ? plans[i] : nullptr;
+    if (!use[i]) {
+      polylab_plan* tmp = nullptr;
+      st = polylab_plan_create(polys ? &polys[i] : nullptr, POLYLAB_PLAN_TERMS, stream, &tmp);
+      if (st == POLYLAB_OK) {
+        h->b.owned_plans.push_back(tmp);
+        use[i] = tmp;
+      }
+    } else if (polys && (polys[i].n_vars != use[i]->n || polys[i].n_terms != use[i]->m)) {
+      st = POLYLAB_ERR_INVALID_ARG;
+    }
+  }
+  if (st == POLYLAB_OK) st = exact_batch_init(&h->b, n_polys, use.data(), X, P, opts, D, Dunit, info, s);
+  if (st != POLYLAB_OK) {
+    exact_batch_release(&h->b, s);
+    delete h;
+    return st;
+  }
+  *out = h;
+  return POLYLAB_OK;
+}
+
+polylab_status polylab_batch_run(polylab_batch* b, polylab_stream stream) {
+  if (!b) return POLYLAB_ERR_INVALID_ARG;
+  return run_exact_batch(&b->b, (cudaStream_t)stream);
+}
+
+polylab_status polylab_batch_get_config(const polylab_batch* b, polylab_batch_config* cfg) {
+  if (!b || !cfg) return POLYLAB_ERR_INVALID_ARG;
+  cfg->threads = b->b.cfg.threads;
+  cfg->ctas_per_sm = b->b.cfg.ctas_per_sm;
+  cfg->order = b->b.cfg.order;
+  return POLYLAB_OK;
+}
+
+polylab_status polylab_batch_set_config(polylab_batch* b, const polylab_batch_config* cfg, polylab_stream stream) {
+  if (!b || !cfg) return POLYLAB_ERR_INVALID_ARG;
+  if (cfg->threads != 64 && cfg->threads != 128 && cfg->threads != 256) return POLYLAB_ERR_INVALID_ARG;
+  if (cfg->ctas_per_sm < 0 || cfg->ctas_per_sm > 32 || (cfg->order != 0 && cfg->order != 1))
+    return POLYLAB_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool reorder = cfg->order != b->b.cfg.order;
+  const bool relayout = cfg->threads != b->b.cfg.threads;
+  b->b.cfg.threads = cfg->threads;
+  b->b.cfg.ctas_per_sm = cfg->ctas_per_sm;
+  b->b.cfg.order = cfg->order;
+  if (relayout) PL_TRY(exact_batch_relayout(&b->b, s));
+  if (reorder) PL_TRY(exact_batch_upload_order(&b->b, s));
+  return POLYLAB_OK;
+}
+
+polylab_status polylab_batch_autotune(polylab_batch* b, int32_t reps, polylab_stream stream,
+                                      polylab_batch_config* chosen, float* best_ms) {
+  if (!b || reps < 1) return POLYLAB_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const polylab_batch_config start{b->b.cfg.threads, b->b.cfg.ctas_per_sm, b->b.cfg.order};
+  polylab_batch_config best = start;
+  float best_t = 1e30f;
+  cudaEvent_t e0, e1;
+  PL_CUDA(cudaEventCreate(&e0));
+  PL_CUDA(cudaEventCreate(&e1));
+  polylab_status st = POLYLAB_OK;
+  for (int order : {1, 0}) {
+    for (int threads : {64, 128, 256}) {
+      for (int cap : {0, 2, 4}) {
+        const polylab_batch_config c{threads, cap, order};
+        st = polylab_batch_set_config(b, &c, stream);
+        if (st == POLYLAB_OK) st = run_exact_batch(&b->b, s);  // warm-up
+        if (st == POLYLAB_ERR_UNSUPPORTED) {
+          st = POLYLAB_OK;
+          continue;
+        }
+        if (st != POLYLAB_OK) break;
+        float t = 0.f;
+        for (int r = 0; r < reps && st == POLYLAB_OK; ++r) {
+          cudaEventRecord(e0, s);
+          st = run_exact_batch(&b->b, s);
+          cudaEventRecord(e1, s);
+          cudaEventSynchronize(e1);
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          t += ms;
+        }
+        t /= reps;
+        if (st == POLYLAB_OK && t < best_t) {
+          best_t = t;
+          best = c;
+        }
+      }
+      if (st != POLYLAB_OK) break;
+    }
+    if (st != POLYLAB_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  PL_TRY(st);
+  PL_TRY(polylab_batch_set_config(b, &best, stream));
+  if (chosen) *chosen = best;
+  if (best_ms) *best_ms = best_t;
+  return POLYLAB_OK;
+}
+
+polylab_status polylab_batch_destroy(polylab_batch* b, polylab_stream stream) {
+  if (!b) return POLYLAB_OK;
+  exact_batch_release(&b->b, (cudaStream_t)stream);
+  delete b;
+  return launch_status("polylab_batch_destroy");
+}
+
+polylab_status polylab_affine_normal_batched(int32_t n_polys, const polylab_poly* polys,
+                                             const polylab_plan* const* plans, const double* const* X,
+                                             const int64_t* P, const polylab_an_opts* opts, double* const* D,
+                                             double* const* Dunit, polylab_an_info* const* info,
+                                             polylab_stream stream) {
+  polylab_batch* b = nullptr;
+  PL_TRY(polylab_batch_create(n_polys, polys, plans, X, P, opts, D, Dunit, info, stream, &b));
+  const polylab_status st = polylab_batch_run(b, stream);
+  polylab_batch_destroy(b, stream);
+  return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,64 @@
+// Batches of (polynomial, point) work items for the exact affine-normal kernel.
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace polylab {
+
+struct ExactDesc {
+  const Term* terms;
+  int64_t m;
+  int n;
+  int E;             // largest exponent (power-table depth)
+  int mats_in_smem;  // 0: matrices in the per-CTA global workspace
+  int max_support;
+  const double* X;   // P x n
+  int64_t P;
+  double* D;
+  double* Dunit;
+  polylab_an_info* info;
+};
+
+struct ExactConfig {
+  int threads = 0;      // CTA size: 64, 128 or 256 (0: by largest n)
+  int ctas_per_sm = 0;  // cap on resident CTAs per SM (0: occupancy limit)
+  int order = 1;        // 1: most expensive polynomials first, 0: as given
+};
+
+struct ExactBatch {
+  polylab_an_opts opts{};
+  ExactConfig cfg;
+  std::vector<ExactDesc> host_descs;
+  std::vector<int> host_order;
+  std::vector<int64_t> host_prefix;
+  ExactDesc* descs = nullptr;  // DEVICE copies
+  int* order = nullptr;
+  int64_t* prefix = nullptr;
+  int* counter = nullptr;
+  int n_desc = 0;
+  int64_t total = 0;
+  size_t smem = 0;
+  size_t gws_stride = 0;
+  unsigned char* gws = nullptr;
+  size_t gws_bytes = 0;
+  std::vector<polylab_plan*> owned_plans;
+};
+
+polylab_status exact_batch_init(ExactBatch* b, int n, const polylab_plan* const* plans, const double* const* X,
+                                const int64_t* P, const polylab_an_opts* o, double* const* D,
+                                double* const* Dunit, polylab_an_info* const* info, cudaStream_t s);
+polylab_status exact_batch_upload_order(ExactBatch* b, cudaStream_t s);
+polylab_status exact_batch_relayout(ExactBatch* b, cudaStream_t s);
+void exact_batch_release(ExactBatch* b, cudaStream_t s);
+polylab_status prepare_exact_batch(ExactBatch* b);
+polylab_status run_exact_batch(ExactBatch* b, cudaStream_t s);
+double exact_point_cost(const ExactDesc& d, int max_support);
+
+}  // namespace polylab
+
+// The opaque public batch handle.
+struct polylab_batch {
+  polylab::ExactBatch b;
+};

@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstring>
 #include <unordered_set>
+#include <vector>
 
 #include "common.cuh"
 
@@ -98,6 +99,25 @@ polylab_status build_term_plan(const polylab_poly* p, cudaStream_t s, polylab_pl
   plan->max_exp = h[0];
   plan->max_support = h[1];
   if (h[1] > kMaxSupport) return POLYLAB_ERR_UNSUPPORTED;
+  // order the term list by (support size, degree): the per-term kernels branch
+  // on the support size, so a warp of consecutive terms then takes one branch
+  // and skips low-degree terms together.  Sums are order independent.
+  if (p->n_terms > 1) {
+    std::vector<Term> host(p->n_terms);
+    PL_CUDA(cudaMemcpyAsync(host.data(), plan->terms, p->n_terms * sizeof(Term), cudaMemcpyDeviceToHost, s));
+    PL_CUDA(cudaStreamSynchronize(s));
+    auto key = [](const Term& t) {
+      int k = 0, d = 0;
+      for (int q = 0; q < kMaxSupport; ++q) {
+        k += t.exp[q] != 0;
+        d += t.exp[q];
+      }
+      return k * 4096 + d;
+    };
+    std::stable_sort(host.begin(), host.end(), [&](const Term& a, const Term& b) { return key(a) < key(b); });
+    PL_CUDA(cudaMemcpyAsync(plan->terms, host.data(), p->n_terms * sizeof(Term), cudaMemcpyHostToDevice, s));
+    PL_CUDA(cudaStreamSynchronize(s));
+  }
   return POLYLAB_OK;
 }
 

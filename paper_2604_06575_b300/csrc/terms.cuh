@@ -36,130 +36,147 @@ __device__ __forceinline__ TermRegs load_term(const Term* __restrict__ terms, in
 }
 
 // Value, gradient and upper-triangle Hessian contributions of one term at one
-// point.  `emit(kind, i, j, v)`: kind 0 = f, 1 = g_i, 2 = H_ij (i <= j).
-template <typename R, int ORDER, typename Emit>
-__device__ __forceinline__ void term_derivs(const TermRegs& t, const R* __restrict__ pw, int E1, Emit&& emit) {
-  R a0[kMaxSupport];  // x_v^{a_v}
-#pragma unroll
-  for (int s = 0; s < kMaxSupport; ++s) a0[s] = s < t.k ? pw[t.var[s] * E1 + t.exp[s]] : R(1);
-  R pre[kMaxSupport + 1], suf[kMaxSupport + 1];
-  pre[0] = R(1);
-#pragma unroll
-  for (int s = 0; s < kMaxSupport; ++s) pre[s + 1] = s < t.k ? pre[s] * a0[s] : pre[s];
-  suf[kMaxSupport] = R(1);
-#pragma unroll
-  for (int s = kMaxSupport - 1; s >= 0; --s) suf[s] = s < t.k ? suf[s + 1] * a0[s] : suf[s + 1];
+// point, for a term with exactly K active variables (loops fully unrolled).
+// `emit(kind, i, j, v)`: kind 0 = f, 1 = g_i, 2 = H_ij (i <= j).
+template <typename R, int ORDER, int K, typename Emit>
+__device__ __forceinline__ void term_derivs_k(const TermRegs& t, const R* __restrict__ pw, int E1, Emit&& emit) {
   const R c = R(t.coef);
-  emit(0, 0, 0, c * pre[kMaxSupport]);
-  if constexpr (ORDER >= 1) {
+  if constexpr (K == 0) {
+    emit(0, 0, 0, c);
+  } else {
+    R a0[K];  // x_v^{a_v}
 #pragma unroll
-  for (int s = 0; s < kMaxSupport; ++s) {
-    if (s < t.k) {
-      const int es = t.exp[s];
-      const R excl = pre[s] * suf[s + 1];
-      const R d1 = R(es) * pw[t.var[s] * E1 + es - 1];
-      emit(1, t.var[s], 0, c * d1 * excl);
-      if constexpr (ORDER >= 2) {
-        if (es >= 2) {
-          const R d2 = R(es * (es - 1)) * pw[t.var[s] * E1 + es - 2];
-          emit(2, t.var[s], t.var[s], c * d2 * excl);
-        }
-        R mid = R(1);
+    for (int s = 0; s < K; ++s) a0[s] = pw[t.var[s] * E1 + t.exp[s]];
+    R pre[K + 1], suf[K + 1];
+    pre[0] = R(1);
 #pragma unroll
-        for (int u = s + 1; u < kMaxSupport; ++u) {
-          if (u < t.k) {
-            const int eu = t.exp[u];
-            const R d1u = R(eu) * pw[t.var[u] * E1 + eu - 1];
-            emit(2, t.var[s], t.var[u], c * d1 * d1u * (pre[s] * mid * suf[u + 1]));
+    for (int s = 0; s < K; ++s) pre[s + 1] = pre[s] * a0[s];
+    suf[K] = R(1);
+#pragma unroll
+    for (int s = K - 1; s >= 0; --s) suf[s] = suf[s + 1] * a0[s];
+    emit(0, 0, 0, c * pre[K]);
+    if constexpr (ORDER >= 1) {
+      R d1[K];
+#pragma unroll
+      for (int s = 0; s < K; ++s) d1[s] = R(t.exp[s]) * pw[t.var[s] * E1 + t.exp[s] - 1];
+#pragma unroll
+      for (int s = 0; s < K; ++s) {
+        const R excl = pre[s] * suf[s + 1];
+        emit(1, t.var[s], 0, c * d1[s] * excl);
+        if constexpr (ORDER >= 2) {
+          const int es = t.exp[s];
+          if (es >= 2) emit(2, t.var[s], t.var[s], c * R(es * (es - 1)) * pw[t.var[s] * E1 + es - 2] * excl);
+          R mid = R(1);
+#pragma unroll
+          for (int u = s + 1; u < K; ++u) {
+            emit(2, t.var[s], t.var[u], c * d1[s] * d1[u] * (pre[s] * mid * suf[u + 1]));
             mid *= a0[u];
           }
         }
       }
     }
   }
+}
+
+// Dispatch on the support size.  Plans keep their term lists sorted by
+// support size, so the threads of a warp normally take the same branch.
+template <typename R, int ORDER, typename Emit>
+__device__ __forceinline__ void term_derivs(const TermRegs& t, const R* __restrict__ pw, int E1, Emit&& emit) {
+  switch (t.k) {
+    case 0: term_derivs_k<R, ORDER, 0>(t, pw, E1, emit); break;
+    case 1: term_derivs_k<R, ORDER, 1>(t, pw, E1, emit); break;
+    case 2: term_derivs_k<R, ORDER, 2>(t, pw, E1, emit); break;
+    case 3: term_derivs_k<R, ORDER, 3>(t, pw, E1, emit); break;
+    case 4: term_derivs_k<R, ORDER, 4>(t, pw, E1, emit); break;
+    case 5: term_derivs_k<R, ORDER, 5>(t, pw, E1, emit); break;
+    case 6: term_derivs_k<R, ORDER, 6>(t, pw, E1, emit); break;
+    case 7: term_derivs_k<R, ORDER, 7>(t, pw, E1, emit); break;
+    default: term_derivs_k<R, ORDER, 8>(t, pw, E1, emit); break;
   }
 }
 
-// c_l += sum_{j,k} d_l d_j d_k (term)(x) * W(j, k) for every l in the support,
-// W symmetric: `wget(j, k)` returns W(j, k), `emit(l, v)` adds v to c_l.
-// The third-derivative tensor of a term is symmetric, so each index multiset
-// {a, b, c} of support slots is visited once: with D[s][m] =
-// falling(a_s, m) x_s^(a_s - m) its entry is prod_s D[s][mult_s], where the
-// slots outside the multiset contribute D[s][0] through running exclusion
-// products (no division, so zeros in x are safe).  Multisets and their
-// contributions:
+// c_l += sum_{j,k} d_l d_j d_k (term)(x) * W(j, k) for every l in the support
+// of a term with exactly K active variables, W symmetric: `wget(j, k)` returns
+// W(j, k), `emit(l, v)` adds v to c_l.  The third-derivative tensor of a term
+// is symmetric, so each index multiset {a, b, c} of support slots is visited
+// once: with D_m[s] = falling(a_s, m) x_s^(a_s - m) its entry is
+// prod_s D_{mult_s}[s]; slots outside the multiset contribute D_0 through
+// running exclusion products (no division, so zeros in x are safe).
 //   {a,b,c} distinct: c_a += 2 T W_bc, c_b += 2 T W_ac, c_c += 2 T W_ab
 //   {a,a,b}, a != b:  c_a += 2 T W_ab, c_b += T W_aa
 //   {a,a,a}:          c_a += T W_aa
+template <typename R, int K, typename WGet, typename Emit>
+__device__ __forceinline__ void term_third_contract_k(const TermRegs& t, const R* __restrict__ pw, int E1,
+                                                      WGet&& wget, Emit&& emit) {
+  R D0[K], D1[K], D2[K], D3[K];
+#pragma unroll
+  for (int s = 0; s < K; ++s) {
+    const int es = t.exp[s];
+    const R* q = pw + t.var[s] * E1 + es;
+    D0[s] = q[0];
+    D1[s] = R(es) * q[-1];
+    D2[s] = es >= 2 ? R(es * (es - 1)) * q[-2] : R(0);
+    D3[s] = es >= 3 ? R(es * (es - 1) * (es - 2)) * q[-3] : R(0);
+  }
+  R pre[K + 1], suf[K + 1];
+  pre[0] = R(1);
+#pragma unroll
+  for (int s = 0; s < K; ++s) pre[s + 1] = pre[s] * D0[s];
+  suf[K] = R(1);
+#pragma unroll
+  for (int s = K - 1; s >= 0; --s) suf[s] = suf[s + 1] * D0[s];
+  R acc[K];
+  R Wd[K];
+#pragma unroll
+  for (int s = 0; s < K; ++s) {
+    acc[s] = R(0);
+    Wd[s] = wget(t.var[s], t.var[s]);
+  }
+#pragma unroll
+  for (int a = 0; a < K; ++a) {
+    const int va = t.var[a];
+    acc[a] += D3[a] * (pre[a] * suf[a + 1]) * Wd[a];  // {a,a,a}
+    R mid_ab = R(1);  // product over slots strictly between a and b
+#pragma unroll
+    for (int b = a + 1; b < K; ++b) {
+      const int vb = t.var[b];
+      const R Wab = wget(va, vb);
+      const R ex_ab = pre[a] * mid_ab * suf[b + 1];  // product over slots != a, b
+      const R Taab = D2[a] * D1[b] * ex_ab;
+      const R Tabb = D1[a] * D2[b] * ex_ab;
+      acc[a] += R(2) * Taab * Wab + Tabb * Wd[b];
+      acc[b] += Taab * Wd[a] + R(2) * Tabb * Wab;
+      R mid_bc = R(1);
+#pragma unroll
+      for (int cc = b + 1; cc < K; ++cc) {
+        const R Tabc = D1[a] * D1[b] * D1[cc] * (pre[a] * mid_ab * mid_bc * suf[cc + 1]);
+        acc[a] += R(2) * Tabc * wget(vb, t.var[cc]);
+        acc[b] += R(2) * Tabc * wget(va, t.var[cc]);
+        acc[cc] += R(2) * Tabc * Wab;
+        mid_bc *= D0[cc];
+      }
+      mid_ab *= D0[b];
+    }
+  }
+  const R c = R(t.coef);
+#pragma unroll
+  for (int s = 0; s < K; ++s) emit(t.var[s], c * acc[s]);
+}
+
 template <typename R, typename WGet, typename Emit>
 __device__ __forceinline__ void term_third_contract(const TermRegs& t, const R* __restrict__ pw, int E1, WGet&& wget,
                                                     Emit&& emit) {
-  const int k = t.k;
-  R D0[kMaxSupport], D1[kMaxSupport], D2[kMaxSupport], D3[kMaxSupport];
-#pragma unroll
-  for (int s = 0; s < kMaxSupport; ++s) {
-    if (s < k) {
-      const int es = t.exp[s];
-      const R* q = pw + t.var[s] * E1 + es;
-      D0[s] = q[0];
-      D1[s] = R(es) * q[-1];
-      D2[s] = es >= 2 ? R(es * (es - 1)) * q[-2] : R(0);
-      D3[s] = es >= 3 ? R(es * (es - 1) * (es - 2)) * q[-3] : R(0);
-    } else {
-      D0[s] = R(1);
-      D1[s] = D2[s] = D3[s] = R(0);
-    }
+  switch (t.k) {
+    case 0: break;
+    case 1: term_third_contract_k<R, 1>(t, pw, E1, wget, emit); break;
+    case 2: term_third_contract_k<R, 2>(t, pw, E1, wget, emit); break;
+    case 3: term_third_contract_k<R, 3>(t, pw, E1, wget, emit); break;
+    case 4: term_third_contract_k<R, 4>(t, pw, E1, wget, emit); break;
+    case 5: term_third_contract_k<R, 5>(t, pw, E1, wget, emit); break;
+    case 6: term_third_contract_k<R, 6>(t, pw, E1, wget, emit); break;
+    case 7: term_third_contract_k<R, 7>(t, pw, E1, wget, emit); break;
+    default: term_third_contract_k<R, 8>(t, pw, E1, wget, emit); break;
   }
-  R pre[kMaxSupport + 1], suf[kMaxSupport + 1];
-  pre[0] = R(1);
-#pragma unroll
-  for (int s = 0; s < kMaxSupport; ++s) pre[s + 1] = pre[s] * D0[s];
-  suf[kMaxSupport] = R(1);
-#pragma unroll
-  for (int s = kMaxSupport - 1; s >= 0; --s) suf[s] = suf[s + 1] * D0[s];
-  const R c = R(t.coef);
-  R acc[kMaxSupport];
-#pragma unroll
-  for (int s = 0; s < kMaxSupport; ++s) acc[s] = R(0);
-#pragma unroll
-  for (int a = 0; a < kMaxSupport; ++a) {
-    if (a < k) {
-      const int va = t.var[a];
-      const R Waa = wget(va, va);
-      const R ex_a = pre[a] * suf[a + 1];  // product over slots != a
-      acc[a] += D3[a] * ex_a * Waa;        // {a,a,a}
-      R mid_ab = R(1);                      // product over slots strictly between a and b
-#pragma unroll
-      for (int b = a + 1; b < kMaxSupport; ++b) {
-        if (b < k) {
-          const int vb = t.var[b];
-          const R Wab = wget(va, vb);
-          const R ex_ab = pre[a] * mid_ab * suf[b + 1];  // product over slots != a, b
-          // {a,a,b} and {a,b,b}
-          const R Taab = D2[a] * D1[b] * ex_ab;
-          const R Tabb = D1[a] * D2[b] * ex_ab;
-          acc[a] += R(2) * Taab * Wab + Tabb * wget(vb, vb);
-          acc[b] += Taab * Waa + R(2) * Tabb * Wab;
-          R mid_bc = R(1);
-#pragma unroll
-          for (int cc = b + 1; cc < kMaxSupport; ++cc) {
-            if (cc < k) {
-              const int vc = t.var[cc];
-              const R Tabc = D1[a] * D1[b] * D1[cc] * (pre[a] * mid_ab * mid_bc * suf[cc + 1]);
-              acc[a] += R(2) * Tabc * wget(vb, vc);
-              acc[b] += R(2) * Tabc * wget(va, vc);
-              acc[cc] += R(2) * Tabc * Wab;
-              mid_bc *= D0[cc];
-            }
-          }
-          mid_ab *= D0[b];
-        }
-      }
-    }
-  }
-#pragma unroll
-  for (int s = 0; s < kMaxSupport; ++s)
-    if (s < k) emit(t.var[s], c * acc[s]);
 }
 
 }  // namespace polylab

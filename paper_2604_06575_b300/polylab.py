@@ -52,6 +52,10 @@ class _AnOpts(C.Structure):
                 ("seed", C.c_uint64), ("prec", C.c_int), ("precond", C.c_int), ("mlp_weights", C.c_void_p)]
 
 
+class _BatchConfig(C.Structure):
+    _fields_ = [("threads", C.c_int32), ("ctas_per_sm", C.c_int32), ("order", C.c_int32)]
+
+
 INFO_DTYPE = np.dtype([("grad_norm", "<f8"), ("logdet", "<f8"), ("flags", "<i4"), ("hv_evals", "<i4"),
                        ("third_evals", "<i4"), ("krylov_iters", "<i4")])
 assert INFO_DTYPE.itemsize == 32
@@ -75,13 +79,28 @@ _lib.polylab_mul.argtypes = [C.POINTER(_Poly), C.POINTER(_Poly), C.c_double, C.P
 _lib.polylab_add.argtypes = _lib.polylab_mul.argtypes
 _lib.polylab_simplify_noalloc.argtypes = [C.POINTER(_Poly), C.c_double, C.POINTER(_PolyOut), C.c_int64, C.c_void_p]
 _lib.polylab_an_opts_default.argtypes = [C.POINTER(_AnOpts)]
+_PP = C.POINTER(C.c_void_p)
+_lib.polylab_batch_create.argtypes = [C.c_int32, C.c_void_p, _PP, _PP, C.POINTER(C.c_int64), C.POINTER(_AnOpts),
+                                      _PP, _PP, _PP, C.c_void_p, C.POINTER(C.c_void_p)]
+_lib.polylab_batch_run.argtypes = [C.c_void_p, C.c_void_p]
+_lib.polylab_batch_get_config.argtypes = [C.c_void_p, C.POINTER(_BatchConfig)]
+_lib.polylab_batch_set_config.argtypes = [C.c_void_p, C.POINTER(_BatchConfig), C.c_void_p]
+_lib.polylab_batch_autotune.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(_BatchConfig),
+                                        C.POINTER(C.c_float)]
+_lib.polylab_batch_destroy.argtypes = [C.c_void_p, C.c_void_p]
+_lib.polylab_affine_normal_batched.argtypes = [C.c_int32, C.c_void_p, _PP, _PP, C.POINTER(C.c_int64),
+                                               C.POINTER(_AnOpts), _PP, _PP, _PP, C.c_void_p]
 for _f in ("polylab_plan_create", "polylab_plan_destroy", "polylab_eval_derivs", "polylab_affine_normal",
-           "polylab_simplify", "polylab_mul", "polylab_add", "polylab_simplify_noalloc"):
+           "polylab_simplify", "polylab_mul", "polylab_add", "polylab_simplify_noalloc", "polylab_batch_create",
+           "polylab_batch_run", "polylab_batch_get_config", "polylab_batch_set_config", "polylab_batch_autotune",
+           "polylab_batch_destroy", "polylab_affine_normal_batched"):
     getattr(_lib, _f).restype = C.c_int
 
 EXPORTED = ["polylab_status_string", "polylab_last_error", "polylab_simplify", "polylab_mul", "polylab_add",
             "polylab_plan_create", "polylab_plan_destroy", "polylab_plan_closure_size", "polylab_eval_derivs",
-            "polylab_an_opts_default", "polylab_affine_normal", "polylab_simplify_noalloc"]
+            "polylab_an_opts_default", "polylab_affine_normal", "polylab_simplify_noalloc", "polylab_batch_create",
+            "polylab_batch_run", "polylab_batch_get_config", "polylab_batch_set_config", "polylab_batch_autotune",
+            "polylab_batch_destroy", "polylab_affine_normal_batched"]
 
 
 def lib():
@@ -284,3 +303,56 @@ def simplify_noalloc(p: DevPoly, exps_out: torch.Tensor, coef_out: torch.Tensor,
     _check("polylab_simplify_noalloc", st)
     m = int(out.n_terms)
     return DevPoly(ids[: out.n_vars].copy(), exps_out[:m], coef_out[:m])
+
+
+def _ptr_array(ts):
+    return (C.c_void_p * len(ts))(*[_ptr(t) if t is not None else None for t in ts])
+
+
+class Batch:
+    """A polylab_batch: exact directions for many polynomials in one launch.
+    Holds references to every tensor it writes or reads."""
+
+    def __init__(self, polys, plans, Xs, opts, want_unit=True, want_info=True, D=None):
+        self.polys, self.plans, self.Xs, self.opts = polys, plans, Xs, opts
+        dev = Xs[0].device
+        self.D = D if D is not None else [torch.empty(X.shape, dtype=torch.float64, device=dev) for X in Xs]
+        self.Du = [torch.empty(X.shape, dtype=torch.float64, device=dev) for X in Xs] if want_unit else None
+        self.info = [torch.empty(X.shape[0], 32, dtype=torch.uint8, device=dev) for X in Xs] if want_info else None
+        n = len(polys)
+        cps = (_Poly * n)(*[p.cstruct() for p in polys])
+        plan_arr = (C.c_void_p * n)(*[pl.h.value if pl is not None else None for pl in plans])
+        P = (C.c_int64 * n)(*[int(X.shape[0]) for X in Xs])
+        self.h = C.c_void_p()
+        _check("polylab_batch_create", _lib.polylab_batch_create(
+            n, C.cast(cps, C.c_void_p), plan_arr, _ptr_array(Xs), P, C.byref(opts), _ptr_array(self.D),
+            _ptr_array(self.Du) if self.Du else None, _ptr_array(self.info) if self.info else None, _stream(),
+            C.byref(self.h)))
+
+    def run(self):
+        _check("polylab_batch_run", _lib.polylab_batch_run(self.h, _stream()))
+
+    def config(self):
+        c = _BatchConfig()
+        _check("polylab_batch_get_config", _lib.polylab_batch_get_config(self.h, C.byref(c)))
+        return dict(threads=c.threads, ctas_per_sm=c.ctas_per_sm, order=c.order)
+
+    def set_config(self, threads, ctas_per_sm, order):
+        c = _BatchConfig(threads, ctas_per_sm, order)
+        _check("polylab_batch_set_config", _lib.polylab_batch_set_config(self.h, C.byref(c), _stream()))
+
+    def autotune(self, reps=2):
+        c, t = _BatchConfig(), C.c_float()
+        _check("polylab_batch_autotune", _lib.polylab_batch_autotune(self.h, reps, _stream(), C.byref(c), C.byref(t)))
+        return dict(threads=c.threads, ctas_per_sm=c.ctas_per_sm, order=c.order), float(t.value)
+
+    def close(self):
+        if self.h:
+            _lib.polylab_batch_destroy(self.h, _stream())
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,107 @@
+"""The batched exact affine normal (one persistent launch over many uneven
+polynomials) against the single-polynomial call and the oracle; every
+launch configuration of the autotuner gives the same directions up to the
+order of the shared-memory sums; a CUDA-graph replay of the batch as well."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import affine
+from paper_2604_06575_b300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+# the order of the shared-memory atomic sums depends on the CTA size, so runs
+# agree to rounding: relative 1e-10 (FP64 form), 2e-4 (FP32 form)
+TOL = {"fp64": 1e-10, "fp32": 2e-4}
+
+
+def close(a, b, tol):
+    fa, fb = torch.isfinite(a).all(dim=1), torch.isfinite(b).all(dim=1)
+    assert torch.equal(fa, fb)
+    if fa.any():
+        err = (a[fa] - b[fa]).norm(dim=1) / b[fa].norm(dim=1)
+        assert float(err.max()) <= tol, float(err.max())
+
+
+@pytest.fixture(scope="module")
+def pl(cuda_ok):
+    from paper_2604_06575_b300 import polylab
+    return polylab
+
+
+@pytest.fixture(scope="module")
+def batch_inputs():
+    polys, Xs = workloads.batched_uneven(seed_off=7, n_polys=14, t_hi=3000, p_lo=3, p_hi=40)
+    # plus two hand-made members: n = 1 and a flagged point
+    polys.append(workloads.Poly(np.array([5], np.uint64), np.array([[2], [1]], np.uint8), np.ones(2)))
+    Xs.append(np.array([[1.0], [-2.0], [0.25]]))
+    polys.append(workloads.Poly(np.arange(2, dtype=np.uint64), np.array([[2, 0], [0, 2]], np.uint8), np.ones(2)))
+    Xs.append(np.array([[0.0, 0.0], [0.3, 0.4]]))
+    return polys, Xs
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_batch_matches_single_calls_and_oracle(pl, batch_inputs, prec):
+    polys, Xs = batch_inputs
+    dps = [pl.to_device(p) for p in polys]
+    Xd = [torch.as_tensor(X, device="cuda") for X in Xs]
+    opts = pl.an_opts(prec=prec, regularization=1e-6)
+    plans = [pl.Plan(d) if i % 2 == 0 else None for i, d in enumerate(dps)]  # mix of given and built plans
+    b = pl.Batch(dps, plans, Xd, opts)
+    b.run()
+    torch.cuda.synchronize()
+    for i, (dp, X) in enumerate(zip(dps, Xd)):
+        D1, Du1, in1 = pl.affine_normal(dp, X, opts)
+        close(b.D[i], D1, TOL[prec])
+        fl_b, fl_1 = pl.info_numpy(b.info[i])["flags"], pl.info_numpy(in1)["flags"]
+        assert np.array_equal(fl_b, fl_1)
+    if prec == "fp64":
+        for i in range(len(polys)):
+            for j in range(min(2, Xs[i].shape[0])):
+                nu, _, oi = affine.affine_normal_ad(polys[i].exps, polys[i].coef, Xs[i][j], r=1e-6,
+                                                    third="contract")
+                d = b.D[i][j].cpu().numpy()
+                if oi["flags"]:
+                    assert np.all(np.isnan(d))
+                else:
+                    assert np.linalg.norm(d - nu) <= 1e-9 * np.linalg.norm(nu)
+
+
+def test_autotune_configs_agree_and_graph_replay(pl, batch_inputs):
+    polys, Xs = batch_inputs
+    dps = [pl.to_device(p) for p in polys]
+    Xd = [torch.as_tensor(X, device="cuda") for X in Xs]
+    b = pl.Batch(dps, [None] * len(dps), Xd, pl.an_opts(prec="fp64"))
+    b.run()
+    torch.cuda.synchronize()
+    ref = [d.clone() for d in b.D]
+    for threads in (64, 128, 256):
+        for cap, order in ((0, 1), (2, 0)):
+            b.set_config(threads, cap, order)
+            b.run()
+            torch.cuda.synchronize()
+            for d, r in zip(b.D, ref):
+                close(d, r, TOL["fp64"])
+    cfg, ms = b.autotune(reps=1)
+    assert cfg["threads"] in (64, 128, 256) and ms > 0
+    assert b.config() == cfg
+    # capture one run in a CUDA graph and replay it twice
+    for d in b.D:
+        d.zero_()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        b.run()  # warm the launch path on the capture stream
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    for d in b.D:
+        d.zero_()
+    with torch.cuda.graph(g):
+        b.run()
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    for d, r in zip(b.D, ref):
+        close(d, r, TOL["fp64"])
