@@ -41,6 +41,17 @@ WORKLOAD = ("batched_uneven_exact: 256 convexified polys (sum x^4 + sum x^2 + 0.
 L2_FLUSH_BYTES = 256 << 20
 
 
+def _measured_bf16():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"])
+    except Exception:
+        return 1800.0  # the recipe's fallback figure
+
+
+MEASURED_BF16_TFLOPS = _measured_bf16()
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -52,6 +63,7 @@ def parse():
     ap.add_argument("--no-rows", action="store_true", help="skip the per-row sub-measurements")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work per sample")
     ap.add_argument("--forms", default="fp64,fp32", help="forms to time (profiling runs time one)")
+    ap.add_argument("--rows-only", action="store_true", help="only the per-row measurements (profiling runs)")
     ap.add_argument("--config", default=None,
                     help="threads,ctas_per_sm,order instead of autotuning (profiling runs)")
     return ap.parse_args()
@@ -229,6 +241,10 @@ def main():
         v = ctypes.c_double()
         rc = probe.polylab_probe_alu(kind, iters, 4, 5, ctypes.byref(v))
         return v.value if rc == 0 else float("nan")
+
+    if args.rows_only:
+        print(json.dumps(dict(rows=measure_rows(pl, workloads, torch, dev, 0.0, 0.0))), flush=True)
+        return
 
     # ---- workload (rank r: its own batch, weak scaling)
     polys, Xs = workloads.batched_uneven(seed_off=rank, n_polys=args.polys)
@@ -448,12 +464,27 @@ def measure_rows(pl, workloads, torch, dev, p32, p64):
     out = (torch.empty(P, dtype=torch.float64, device=dev), torch.empty(P, n, dtype=torch.float64, device=dev),
            torch.empty(P, n, n, dtype=torch.float64, device=dev))
     ev = {}
-    with pl.Plan(dp) as plan:
-        for prec in ("fp64", "fp32"):
+    with pl.Plan(dp, gemm=True) as plan:
+        gi = plan.gemm_info()
+        for prec in ("fp64", "fp32", "tf32x3", "bf16"):
             ms = ev_time(lambda: pl.eval_derivs(dp, Xd, plan=plan, prec=prec, out=out))
             ev[prec] = dict(ms=round(ms, 3), evals_per_s=round(P / (ms * 1e-3), 1))
+    tiles = -(-P // 128)
+    # tensor work the kernels issue: per 128-point tile, every live block is
+    # 128 x 256 x K_block MACs (BF16 K_block 64; TF32 K_block 32, three products)
+    issued_bf16 = 2.0 * 128 * 256 * 64 * gi["bf16_live_halves"] * tiles
+    issued_tf32 = 3 * 2.0 * 128 * 256 * 32 * gi["tf32_live_tiles"] * tiles
+    bf16_peak = MEASURED_BF16_TFLOPS
+    tf32_peak = MEASURED_BF16_TFLOPS * 1.1 / 2.25  # nominal dense tf32/bf16 ratio
+    for prec, fl, pk in (("bf16", issued_bf16, bf16_peak), ("tf32x3", issued_tf32, tf32_peak)):
+        t = ev[prec]["ms"] * 1e-3
+        ev[prec]["roofline"] = dict(bound="tensor", achieved=round(fl / t / 1e12, 2), peak=round(pk, 1),
+                                    unit="TFLOP/s", frac=round(fl / t / 1e12 / pk, 4),
+                                    note="issued MMA work of live blocks; peak: measured bf16 burst"
+                                         + (" x nominal tf32/bf16 ratio" if prec == "tf32x3" else ""))
     rows["eval_derivs"] = dict(workload="n=30, 5,000 terms deg<=4 <=4 active, 65,536 points in [-1,1]^30",
-                               forms=ev)
+                               closure_K=gi["K"], output_columns_padded=gi["Npad"], forms=ev,
+                               speedup_vs_fp64={k: round(ev["fp64"]["ms"] / v["ms"], 2) for k, v in ev.items()})
     return rows
 
 

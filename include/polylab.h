@@ -161,6 +161,13 @@ polylab_status polylab_plan_create(const polylab_poly* p, uint32_t what, polylab
 polylab_status polylab_plan_destroy(polylab_plan* plan, polylab_stream stream);
 /* Closure-set size K (rows of the derived-coefficient matrix) or -1. */
 int64_t polylab_plan_closure_size(const polylab_plan* plan);
+/* Shape of a plan's derived-coefficient matrix (plans built with
+ * POLYLAB_PLAN_GEMM): closure size K, padded output columns Npad, the number
+ * of 64 x 256 BF16 blocks and of 32 x 256 TF32 blocks that hold a nonzero
+ * (the tensor-core work one 128-point tile issues).  Any pointer may be NULL.
+ * Synchronous (reads a small table back). */
+polylab_status polylab_plan_gemm_info(const polylab_plan* plan, int64_t* K, int32_t* Npad,
+                                      int64_t* bf16_live_halves, int64_t* tf32_live_tiles);
 
 /* ------------------------------------------------------------ derivatives at points */
 

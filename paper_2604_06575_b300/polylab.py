@@ -68,6 +68,8 @@ _lib.polylab_plan_closure_size.restype = C.c_int64
 _lib.polylab_plan_closure_size.argtypes = [C.c_void_p]
 _lib.polylab_plan_create.argtypes = [C.POINTER(_Poly), C.c_uint32, C.c_void_p, C.POINTER(C.c_void_p)]
 _lib.polylab_plan_destroy.argtypes = [C.c_void_p, C.c_void_p]
+_lib.polylab_plan_gemm_info.argtypes = [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int32),
+                                        C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
 _lib.polylab_eval_derivs.argtypes = [C.POINTER(_Poly), C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_int,
                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
 _lib.polylab_affine_normal.argtypes = [C.POINTER(_Poly), C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(_AnOpts),
@@ -93,14 +95,14 @@ _lib.polylab_affine_normal_batched.argtypes = [C.c_int32, C.c_void_p, _PP, _PP, 
 for _f in ("polylab_plan_create", "polylab_plan_destroy", "polylab_eval_derivs", "polylab_affine_normal",
            "polylab_simplify", "polylab_mul", "polylab_add", "polylab_simplify_noalloc", "polylab_batch_create",
            "polylab_batch_run", "polylab_batch_get_config", "polylab_batch_set_config", "polylab_batch_autotune",
-           "polylab_batch_destroy", "polylab_affine_normal_batched"):
+           "polylab_batch_destroy", "polylab_affine_normal_batched", "polylab_plan_gemm_info"):
     getattr(_lib, _f).restype = C.c_int
 
 EXPORTED = ["polylab_status_string", "polylab_last_error", "polylab_simplify", "polylab_mul", "polylab_add",
             "polylab_plan_create", "polylab_plan_destroy", "polylab_plan_closure_size", "polylab_eval_derivs",
             "polylab_an_opts_default", "polylab_affine_normal", "polylab_simplify_noalloc", "polylab_batch_create",
             "polylab_batch_run", "polylab_batch_get_config", "polylab_batch_set_config", "polylab_batch_autotune",
-            "polylab_batch_destroy", "polylab_affine_normal_batched"]
+            "polylab_batch_destroy", "polylab_affine_normal_batched", "polylab_plan_gemm_info"]
 
 
 def lib():
@@ -164,6 +166,12 @@ class Plan:
     @property
     def closure_size(self) -> int:
         return int(_lib.polylab_plan_closure_size(self.h))
+
+    def gemm_info(self) -> dict:
+        K, N, h16, t32 = C.c_int64(), C.c_int32(), C.c_int64(), C.c_int64()
+        _check("polylab_plan_gemm_info", _lib.polylab_plan_gemm_info(self.h, C.byref(K), C.byref(N), C.byref(h16),
+                                                                     C.byref(t32)))
+        return dict(K=K.value, Npad=N.value, bf16_live_halves=h16.value, tf32_live_tiles=t32.value)
 
     def close(self):
         if self.h:
