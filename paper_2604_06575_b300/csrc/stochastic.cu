@@ -1,0 +1,523 @@
+// MF-logDet-Stochastic affine-normal direction (Sec. 5): the trace term a is
+// replaced by a Hutchinson estimate over q probes and every tangent solve by
+// preconditioned CG, with Hessian-vector products formed matrix-free from the
+// term list.
+//
+// Everything runs in the ambient space on vectors orthogonal to e: with
+// Pi = I - e e^T, the tangent system (H_T + r I) y = z of a frame Q_T is the
+// system Pi (H + r I) Pi u = Pi w with u = Q_T y, w = Q_T z, and CG on it
+// produces the tangent iterates mapped by Q_T (the preconditioner
+// Pi D^{-1} Pi corresponds to Q_T^T D^{-1} Q_T), so no frame is formed.
+//
+// Per point (one CTA):
+//   g, |diag H| from the terms; e = g/|g|; D = |diag H| + r (1 where 0)
+//   for each chunk of QC probes:  w_s Rademacher (SplitMix64),
+//       b_s = Pi w_s;  PCG:  u_s ~ (Pi (H + rI) Pi)^+ b_s
+//       cbar += (1/q) sum_s T(., u_s, b_s)   (term by term, symmetrised)
+//   a = Pi cbar;  PCG: u_tau solves Pi (H + rI) Pi u = Pi H e - |g|/(n+1) a
+//   nu = u_tau - e
+//
+// R = float (POLYLAB_FP32): HVPs, CG vectors and sums in FP32, the final
+// direction and its normalisation in FP64; R = double: FP64 throughout.
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+#include "terms.cuh"
+
+namespace polylab {
+
+namespace {
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t k) {
+  uint64_t z = seed + (k + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Symmetric k x k Hessian block of one term at one point (slots a, b).
+template <typename R, int K>
+__device__ __forceinline__ void term_hessian_block(const TermRegs& t, const R* __restrict__ pw, int E1, R* blk) {
+  R a0[K], d1[K], d2[K];
+#pragma unroll
+  for (int s = 0; s < K; ++s) {
+    const int es = t.exp[s];
+    const R* q = pw + t.var[s] * E1 + es;
+    a0[s] = q[0];
+    d1[s] = R(es) * q[-1];
+    d2[s] = es >= 2 ? R(es * (es - 1)) * q[-2] : R(0);
+  }
+  R pre[K + 1], suf[K + 1];
+  pre[0] = R(1);
+#pragma unroll
+  for (int s = 0; s < K; ++s) pre[s + 1] = pre[s] * a0[s];
+  suf[K] = R(1);
+#pragma unroll
+  for (int s = K - 1; s >= 0; --s) suf[s] = suf[s + 1] * a0[s];
+  const R c = R(t.coef);
+#pragma unroll
+  for (int s = 0; s < K; ++s) {
+    blk[s * K + s] = c * d2[s] * pre[s] * suf[s + 1];
+    R mid = R(1);
+#pragma unroll
+    for (int u = s + 1; u < K; ++u) {
+      const R v = c * d1[s] * d1[u] * (pre[s] * mid * suf[u + 1]);
+      blk[s * K + u] = v;
+      blk[u * K + s] = v;
+      mid *= a0[u];
+    }
+  }
+}
+
+// Y[var_a][s] += sum_b blk[a][b] V[var_b][s] for the QC probes of a chunk
+// (4 probes per pass, shared-memory atomics into Y).
+template <typename R, int K, int QC>
+__device__ __forceinline__ void term_hvp(const TermRegs& t, const R* __restrict__ pw, int E1,
+                                         const R* __restrict__ V, R* Y, const int* active) {
+  R blk[K * K];
+  term_hessian_block<R, K>(t, pw, E1, blk);
+#pragma unroll 1
+  for (int s0 = 0; s0 < QC; s0 += 4) {
+    if (!(active[s0] | active[s0 + 1] | active[s0 + 2] | active[s0 + 3])) continue;
+    R v[K][4];
+#pragma unroll
+    for (int b = 0; b < K; ++b)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) v[b][q] = V[t.var[b] * QC + s0 + q];
+#pragma unroll
+    for (int a = 0; a < K; ++a) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        R acc = R(0);
+#pragma unroll
+        for (int b = 0; b < K; ++b) acc += blk[a * K + b] * v[b][q];
+        atomicAdd(&Y[t.var[a] * QC + s0 + q], acc);
+      }
+    }
+  }
+}
+
+template <typename R, int QC>
+__device__ __forceinline__ void term_hvp_dispatch(const TermRegs& t, const R* pw, int E1, const R* V, R* Y,
+                                                  const int* active) {
+  switch (t.k) {
+    case 0: break;
+    case 1: term_hvp<R, 1, QC>(t, pw, E1, V, Y, active); break;
+    case 2: term_hvp<R, 2, QC>(t, pw, E1, V, Y, active); break;
+    case 3: term_hvp<R, 3, QC>(t, pw, E1, V, Y, active); break;
+    case 4: term_hvp<R, 4, QC>(t, pw, E1, V, Y, active); break;
+    case 5: term_hvp<R, 5, QC>(t, pw, E1, V, Y, active); break;
+    case 6: term_hvp<R, 6, QC>(t, pw, E1, V, Y, active); break;
+    case 7: term_hvp<R, 7, QC>(t, pw, E1, V, Y, active); break;
+    default: term_hvp<R, 8, QC>(t, pw, E1, V, Y, active); break;
+  }
+}
+
+// block-wide sums of QC values per thread; result broadcast to all threads
+template <int NT, int QC>
+__device__ __forceinline__ void block_sums(double (&v)[QC], double* red) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+  for (int s = 0; s < QC; ++s)
+    for (int o = 16; o; o >>= 1) v[s] += __shfl_xor_sync(0xffffffffu, v[s], o);
+  __syncthreads();
+  if (l == 0)
+#pragma unroll
+    for (int s = 0; s < QC; ++s) red[w * QC + s] = v[s];
+  __syncthreads();
+  if (threadIdx.x < QC) {
+    double acc = 0.0;
+    for (int q = 0; q < NT / 32; ++q) acc += red[q * QC + threadIdx.x];
+    red[(NT / 32) * QC + threadIdx.x] = acc;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int s = 0; s < QC; ++s) v[s] = red[(NT / 32) * QC + s];
+  __syncthreads();
+}
+
+struct StochArgs {
+  const Term* terms;
+  int64_t m;
+  int n, E;
+  const double* X;
+  int64_t P;
+  double r, tol;
+  int maxit, q, assume_nonzero_x;
+  uint64_t seed;
+  int precond;
+  const float* mlp;  // reserved for the learned preconditioner (diag D and low-rank U per point)
+  double* D;
+  double* Dunit;
+  polylab_an_info* info;
+  unsigned char* gws;  // per CTA: 6 vectors of n*QC R
+  size_t gws_stride;
+};
+
+}  // namespace
+
+template <typename R, int NT, int QC>
+__global__ void __launch_bounds__(NT) stochastic_kernel(StochArgs a) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const int n = a.n, E1 = a.E + 1, tid = threadIdx.x;
+  // shared: power table, Y accumulators, vectors g, dg (|diag H|), e, cbar, Dinv; reductions
+  R* pw = (R*)sm;
+  R* Y = pw + (size_t)n * E1;
+  // per-point vectors in the form's precision (FP32 form: shared memory for n up to ~2000)
+  R* g = (R*)(((uintptr_t)(Y + (size_t)n * QC) + 15) & ~(uintptr_t)15);
+  R* dg = g + n;
+  R* e = dg + n;
+  R* cbar = e + n;
+  R* Dinv = cbar + n;
+  double* red = (double*)(((uintptr_t)(Dinv + n) + 15) & ~(uintptr_t)15);  // (NT/32 + 1) * QC doubles
+  __shared__ int s_active[QC];
+  __shared__ int s_iters[QC];
+  __shared__ double s_bnorm[QC], s_rz[QC];
+  __shared__ int s_maxed;
+
+  unsigned char* gb = a.gws + (size_t)blockIdx.x * a.gws_stride;
+  const size_t vec = (size_t)n * QC;
+  R* Xv = (R*)gb;  // solutions u_s
+  R* Rv = Xv + vec;  // residuals
+  R* Pv = Rv + vec;  // search directions
+  R* Zv = Pv + vec;  // preconditioned residuals
+  R* Bv = Zv + vec;  // right-hand sides b_s = Pi w_s
+
+  for (int64_t p = blockIdx.x; p < a.P; p += gridDim.x) {
+    __syncthreads();
+    const double* X = a.X + p * n;
+    for (int i = tid; i < n; i += NT) {
+      const double x = X[i];
+      R cur = R(1);
+      pw[i * E1] = cur;
+      for (int k = 1; k < E1; ++k) {
+        cur = cur * R(x);
+        pw[i * E1 + k] = cur;
+      }
+      g[i] = R(0);
+      dg[i] = R(0);
+      cbar[i] = R(0);
+    }
+    __syncthreads();
+    // gradient, |gradient contributions| (for the zero test, kept in Y) and diag(H)
+    for (int i = tid; i < n; i += NT) Y[i] = R(0);
+    __syncthreads();
+    for (int64_t t = tid; t < a.m; t += NT) {
+      const TermRegs tr = load_term(a.terms, t);
+      term_derivs<R, 2>(tr, pw, E1, [&](int kind, int i, int j, R val) {
+        if (kind == 1) {
+          atomicAdd(&g[i], val);
+          atomicAdd(&Y[i], (R)fabs((double)val));
+        } else if (kind == 2 && i == j) {
+          atomicAdd(&dg[i], val);
+        }
+      });
+    }
+    __syncthreads();
+    double gg[QC], ss[QC];
+#pragma unroll
+    for (int s = 0; s < QC; ++s) gg[s] = ss[s] = 0.0;
+    for (int i = tid; i < n; i += NT) {
+      gg[0] += (double)g[i] * (double)g[i];
+      ss[0] += (double)Y[i] * (double)Y[i];
+    }
+    block_sums<NT, QC>(gg, red);
+    block_sums<NT, QC>(ss, red);
+    const double gn = sqrt(gg[0]);
+    bool zero = !(gn > 0.0) || !isfinite(gn);
+    if (!a.assume_nonzero_x && gn <= (sizeof(R) == 8 ? 1e-14 : 1e-6) * sqrt(ss[0])) zero = true;
+    if (zero) {
+      if (tid == 0 && a.info) {
+        polylab_an_info in{gn, nan(""), POLYLAB_FLAG_ZERO_GRAD, 0, a.q, 0};
+        a.info[p] = in;
+      }
+      for (int i = tid; i < n; i += NT) {
+        a.D[p * n + i] = nan("");
+        if (a.Dunit) a.Dunit[p * n + i] = nan("");
+      }
+      continue;
+    }
+    for (int i = tid; i < n; i += NT) {
+      e[i] = R((double)g[i] / gn);
+      const double d = fabs((double)dg[i]) + a.r;
+      Dinv[i] = a.precond == POLYLAB_PRECOND_NONE ? R(1) : R(d > 0.0 ? 1.0 / d : 1.0);
+    }
+    if (tid == 0) s_maxed = 0;
+    __syncthreads();
+    int total_iters = 0;
+    const int words = (n + 63) / 64;
+
+    // ---------------------------------------------------------------- PCG
+    // Solves Pi (H + rI) Pi u_s = b_s for the `nq` columns present in Bv.
+    auto project = [&](R* V, int nq) {  // V_s <- V_s - e (e . V_s)
+      double d[QC];
+#pragma unroll
+      for (int s = 0; s < QC; ++s) d[s] = 0.0;
+      for (int i = tid; i < n; i += NT)
+#pragma unroll
+        for (int s = 0; s < QC; ++s) d[s] += (double)e[i] * (double)V[i * QC + s];
+      block_sums<NT, QC>(d, red);
+      for (int i = tid; i < n; i += NT)
+#pragma unroll
+        for (int s = 0; s < QC; ++s)
+          if (s < nq) V[i * QC + s] -= R((double)e[i] * d[s]);
+    };
+    auto apply_A = [&](const R* V) {  // Y = Pi (H + rI) V (V in e-perp), into shared memory
+      for (int i = tid; i < (int)vec; i += NT) Y[i] = R(0);
+      __syncthreads();
+      for (int64_t t = tid; t < a.m; t += NT) {
+        const TermRegs tr = load_term(a.terms, t);
+        term_hvp_dispatch<R, QC>(tr, pw, E1, V, Y, s_active);
+      }
+      __syncthreads();
+      for (int i = tid; i < (int)vec; i += NT) Y[i] += R(a.r) * V[i];
+      __syncthreads();
+      project(Y, QC);
+      __syncthreads();
+    };
+    auto precondition = [&](int nq) {  // Z = Pi D^{-1} R
+      for (int i = tid; i < (int)vec; i += NT) Zv[i] = Dinv[i / QC] * Rv[i];
+      __syncthreads();
+      project(Zv, nq);
+      __syncthreads();
+    };
+    auto pcg = [&](int nq) {
+      for (int i = tid; i < (int)vec; i += NT) {
+        Xv[i] = R(0);
+        Rv[i] = Bv[i];
+      }
+      if (tid < QC) {
+        s_active[tid] = tid < nq;
+        s_iters[tid] = 0;
+      }
+      __syncthreads();
+      precondition(nq);
+      for (int i = tid; i < (int)vec; i += NT) Pv[i] = Zv[i];
+      double bb[QC], rz[QC];
+#pragma unroll
+      for (int s = 0; s < QC; ++s) bb[s] = rz[s] = 0.0;
+      for (int i = tid; i < n; i += NT)
+#pragma unroll
+        for (int s = 0; s < QC; ++s) {
+          const double b = Bv[i * QC + s];
+          bb[s] += b * b;
+          rz[s] += b * (double)Zv[i * QC + s];
+        }
+      block_sums<NT, QC>(bb, red);
+      block_sums<NT, QC>(rz, red);
+      if (tid < QC) {
+        s_bnorm[tid] = sqrt(bb[tid]);
+        s_rz[tid] = rz[tid];
+      }
+      __syncthreads();
+      double rr[QC];
+#pragma unroll
+      for (int s = 0; s < QC; ++s) rr[s] = bb[s];
+      for (int k = 0;; ++k) {
+        // convergence test before every iteration: |r_s| <= tol |b_s|
+        if (tid < QC && s_active[tid]) {
+          if (sqrt(rr[tid]) <= a.tol * s_bnorm[tid]) {
+            s_active[tid] = 0;
+          } else if (k >= a.maxit) {
+            s_active[tid] = 0;
+            s_maxed = 1;
+          }
+        }
+        __syncthreads();
+        int any = 0;
+#pragma unroll
+        for (int s = 0; s < QC; ++s) any |= s_active[s];
+        if (!any) break;
+        apply_A(Pv);
+        double py[QC];
+#pragma unroll
+        for (int s = 0; s < QC; ++s) py[s] = 0.0;
+        for (int i = tid; i < n; i += NT)
+#pragma unroll
+          for (int s = 0; s < QC; ++s) py[s] += (double)Pv[i * QC + s] * (double)Y[i * QC + s];
+        block_sums<NT, QC>(py, red);
+        // breakdown guard: a probe whose curvature p.Ap is not positive (or not
+        // finite) stops here with its current iterate
+        if (tid < QC && s_active[tid] && !(py[tid] > 0.0 && isfinite(py[tid]) && isfinite(s_rz[tid])))
+          s_active[tid] = 0;
+        __syncthreads();
+        for (int i = tid; i < (int)vec; i += NT) {
+          const int s = i % QC;
+          if (!s_active[s]) continue;
+          const R alpha = R(s_rz[s] / py[s]);
+          Xv[i] += alpha * Pv[i];
+          Rv[i] -= alpha * Y[i];
+        }
+        __syncthreads();
+        precondition(nq);
+        double rzn[QC];
+#pragma unroll
+        for (int s = 0; s < QC; ++s) rzn[s] = rr[s] = 0.0;
+        for (int i = tid; i < n; i += NT)
+#pragma unroll
+          for (int s = 0; s < QC; ++s) {
+            const double rv = Rv[i * QC + s];
+            rzn[s] += rv * (double)Zv[i * QC + s];
+            rr[s] += rv * rv;
+          }
+        block_sums<NT, QC>(rzn, red);
+        block_sums<NT, QC>(rr, red);
+        for (int i = tid; i < (int)vec; i += NT) {
+          const int s = i % QC;
+          if (!s_active[s]) continue;
+          const R beta = R(rzn[s] / s_rz[s]);
+          Pv[i] = Zv[i] + beta * Pv[i];
+        }
+        __syncthreads();
+        if (tid < QC && s_active[tid]) {
+          s_rz[tid] = rzn[tid];
+          s_iters[tid] += 1;
+        }
+        __syncthreads();
+      }
+      int it = 0;
+#pragma unroll
+      for (int s = 0; s < QC; ++s) it += s < nq ? s_iters[s] : 0;
+      __syncthreads();
+      return it;
+    };
+
+    // ----------------------------------------------------- probes, trace term
+    for (int s0 = 0; s0 < a.q; s0 += QC) {
+      const int nq = min(QC, a.q - s0);
+      for (int i = tid; i < (int)vec; i += NT) {
+        const int row = i / QC, s = i % QC;
+        R w = R(0);
+        if (s < nq) {
+          const uint64_t k = ((uint64_t)p * a.q + s0 + s) * words + (uint64_t)(row >> 6);
+          w = ((splitmix64(a.seed, k) >> (row & 63)) & 1ull) ? R(-1) : R(1);
+        }
+        Bv[i] = w;
+      }
+      __syncthreads();
+      project(Bv, nq);
+      __syncthreads();
+      total_iters += pcg(nq);
+      // cbar += (1/q) sum_s T(., u_s, b_s): per term, the symmetrised block
+      // Z_jk = (1/2q) sum_s (u_s[j] b_s[k] + u_s[k] b_s[j]) contracted with T
+      const double inv2q = 0.5 / (double)a.q;
+      for (int64_t t = tid; t < a.m; t += NT) {
+        const TermRegs tr = load_term(a.terms, t);
+        int deg = 0;
+#pragma unroll
+        for (int s2 = 0; s2 < kMaxSupport; ++s2) deg += tr.exp[s2];
+        if (deg < 3) continue;
+        term_third_contract<R>(
+            tr, pw, E1,
+            [&](int j, int k) {
+              R acc = R(0);
+              for (int s = 0; s < nq; ++s)
+                acc += Xv[j * QC + s] * Bv[k * QC + s] + Xv[k * QC + s] * Bv[j * QC + s];
+              return R(acc * R(inv2q));
+            },
+            [&](int l, R val) { atomicAdd(&cbar[l], val); });
+      }
+      __syncthreads();
+    }
+    // ---------------------------------------------------------- tau solve
+    // right-hand side Pi (H e) - |g|/(n+1) Pi cbar, one column
+    for (int i = tid; i < (int)vec; i += NT) Pv[i] = (i % QC == 0) ? R(e[i / QC]) : R(0);
+    if (tid < QC) s_active[tid] = tid == 0;
+    __syncthreads();
+    for (int i = tid; i < (int)vec; i += NT) Y[i] = R(0);
+    __syncthreads();
+    for (int64_t t = tid; t < a.m; t += NT) {  // Y = H e (ambient, column 0)
+      const TermRegs tr = load_term(a.terms, t);
+      term_hvp_dispatch<R, QC>(tr, pw, E1, Pv, Y, s_active);
+    }
+    __syncthreads();
+    const double wgt = gn / (double)(n + 1);
+    for (int i = tid; i < (int)vec; i += NT)
+      Bv[i] = (i % QC == 0) ? R((double)Y[i] - wgt * (double)cbar[i / QC]) : R(0);
+    __syncthreads();
+    project(Bv, 1);
+    __syncthreads();
+    total_iters += pcg(1);
+    // ---------------------------------------------------------- direction
+    double nrm[QC];
+#pragma unroll
+    for (int s = 0; s < QC; ++s) nrm[s] = 0.0;
+    for (int i = tid; i < n; i += NT) {
+      const double nu = (double)Xv[i * QC] - (double)e[i];
+      nrm[0] += nu * nu;
+    }
+    block_sums<NT, QC>(nrm, red);
+    const double inv = 1.0 / sqrt(nrm[0]);
+    for (int i = tid; i < n; i += NT) {
+      const double nu = (double)Xv[i * QC] - (double)e[i];
+      a.D[p * n + i] = nu;
+      if (a.Dunit) a.Dunit[p * n + i] = nu * inv;
+    }
+    if (tid == 0 && a.info) {
+      polylab_an_info in{gn, nan(""), s_maxed ? POLYLAB_FLAG_KRYLOV_MAXIT : 0, total_iters + 1, a.q, total_iters};
+      a.info[p] = in;
+    }
+  }
+}
+
+namespace {
+
+template <typename R, int QC>
+size_t stoch_smem(int n, int E1, int NT) {
+  size_t b = (size_t)n * E1 * sizeof(R) + (size_t)n * QC * sizeof(R);
+  b = (b + 15) & ~size_t(15);
+  b += 5 * (size_t)n * sizeof(R);
+  b = (b + 15) & ~size_t(15);
+  b += (size_t)(NT / 32 + 1) * QC * 8;
+  return b + 64;
+}
+
+template <typename R, int NT, int QC>
+polylab_status launch_stoch(const polylab_plan* plan, const double* X, int64_t P, const polylab_an_opts* o, double* D,
+                            double* Dunit, polylab_an_info* info, cudaStream_t s) {
+  const int n = plan->n, E1 = std::max(plan->max_exp, 1) + 1;
+  const size_t smem = stoch_smem<R, QC>(n, E1, NT);
+  if (smem > 220 * 1024) return POLYLAB_ERR_UNSUPPORTED;
+  auto k = stochastic_kernel<R, NT, QC>;
+  PL_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  PL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NT, smem));
+  per_sm = std::max(1, per_sm);
+  const int64_t grid = std::min<int64_t>(P, (int64_t)num_sms() * per_sm);
+  StochArgs a{};
+  a.terms = plan->terms;
+  a.m = plan->m;
+  a.n = n;
+  a.E = E1 - 1;
+  a.X = X;
+  a.P = P;
+  a.r = o->regularization;
+  a.tol = o->krylov_tol;
+  a.maxit = o->krylov_maxit;
+  a.q = o->num_probes;
+  a.assume_nonzero_x = o->assume_nonzero_x;
+  a.seed = o->seed;
+  a.precond = o->precond;
+  a.mlp = (const float*)o->mlp_weights;
+  a.D = D;
+  a.Dunit = Dunit;
+  a.info = info;
+  a.gws_stride = ((size_t)5 * n * QC * sizeof(R) + 255) & ~size_t(255);
+  Scratch scr(s);
+  PL_TRY(scr.get(&a.gws, (size_t)grid * a.gws_stride));
+  k<<<(unsigned)grid, NT, smem, s>>>(a);
+  return launch_status("stochastic_kernel");
+}
+
+}  // namespace
+
+polylab_status affine_stochastic(const polylab_plan* plan, const double* X, int64_t P, const polylab_an_opts* o,
+                                 double* D, double* Dunit, polylab_an_info* info, cudaStream_t s) {
+  if (P == 0) return POLYLAB_OK;
+  if (o->precond == POLYLAB_PRECOND_MLP) return POLYLAB_ERR_UNSUPPORTED;
+  if (o->prec == POLYLAB_FP32) return launch_stoch<float, 256, 16>(plan, X, P, o, D, Dunit, info, s);
+  return launch_stoch<double, 256, 8>(plan, X, P, o, D, Dunit, info, s);
+}
+
+}  // namespace polylab
