@@ -6,8 +6,8 @@ The paper is silent on learned preconditioners; this network is the
 project's own design, and this module is its plain definition:
 
 * per-coordinate features of a point x (H = Hessian, g = gradient,
-  e = g/|g|, r = regularisation):
-      f_i = [log(|H_ii| + r), log(sum_{j != i} |H_ij| + r), x_i, n e_i^2,
+  e = g/|g|, r = regularisation, S_ij = sum over terms of |term's d_i d_j|):
+      f_i = [log(|H_ii| + r), log(sum_{j != i} S_ij + r), x_i, n e_i^2,
              log(|g_i| + 1e-30)]
 * one MLP shared by all coordinates: h = tanh(W1^T f + b1) (32 units),
   o = W2^T h + b2 (3 outputs);
@@ -45,10 +45,11 @@ def unpack(theta: np.ndarray):
     return W1, b1, W2, b2
 
 
-def features(H: np.ndarray, g: np.ndarray, x: np.ndarray, r: float) -> np.ndarray:
+def features(H: np.ndarray, SH: np.ndarray, g: np.ndarray, x: np.ndarray, r: float) -> np.ndarray:
+    """SH: per-entry sums of |term contributions| to H (``derivs.eval_derivs``)."""
     n = x.shape[0]
     d = np.abs(np.diag(H))
-    off = np.abs(H).sum(axis=1) - d
+    off = SH.sum(axis=1) - np.diag(SH)
     e = g / np.linalg.norm(g)
     return np.column_stack([np.log(d + r), np.log(off + r), x, n * e * e, np.log(np.abs(g) + 1e-30)])
 

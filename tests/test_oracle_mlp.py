@@ -12,13 +12,13 @@ def point_data(seed=0, n=7, nz=3, r=1e-3):
     rng = np.random.default_rng(seed)
     poly = workloads.convexified(rng, n, workloads.sparse_monomials(rng, n, 20, 4, 3), 0.3)
     x = workloads.shell_points(rng, n, 1)[0]
-    F, G, H, *_ = derivs.eval_derivs(poly.exps, poly.coef, x[None, :])
-    g, H = G[0], H[0]
+    F, G, H, SF, SG, SH = derivs.eval_derivs(poly.exps, poly.coef, x[None, :])
+    g, H, SH = G[0], H[0], SH[0]
     e = g / np.linalg.norm(g)
     Pi = np.eye(n) - np.outer(e, e)
     Z = np.column_stack([Pi @ rademacher(seed, 0, s, nz, n) for s in range(nz)])
     Y = Pi @ (H + r * np.eye(n)) @ Z
-    return mlp.features(H, g, x, r), np.diag(H), r, e, Z, Y, H
+    return mlp.features(H, SH, g, x, r), np.diag(H), r, e, Z, Y, H
 
 
 def test_gradient_matches_finite_differences():
