@@ -244,6 +244,45 @@ polylab_status polylab_affine_normal(const polylab_poly* p, const polylab_plan* 
                                      int64_t P, const polylab_an_opts* opts, double* D, double* Dunit,
                                      polylab_an_info* info, polylab_stream stream);
 
+/* ------------------------------------------------- learned preconditioner */
+
+/* A small network mapping per-coordinate Hessian features of a point to a
+ * diagonal-plus-low-rank preconditioner Pi (D + U U^T) Pi for the Krylov
+ * solves of POLYLAB_MF_STOCHASTIC (this library's addition; the paper uses
+ * plain Krylov solves).  Features of coordinate i:
+ *   [log(|H_ii| + r), log(sum_{j != i} sum_t |d_i d_j t(x)| + r), x_i, n e_i^2, log(|g_i| + 1e-30)];
+ * network 5 -> 32 (tanh) -> 3; D_i = exp(clip(o_0, -5, 5)) / (|H_ii| + r),
+ * U_ik = 0.1 o_k / sqrt(|H_ii| + r).  Zero output weights reproduce Jacobi.
+ * Parameters: POLYLAB_MLP_PARAMS floats (W1 5x32 row-major, b1, W2 32x3, b2).
+ * Inference uses a BF16 copy (polylab_mlp_pack) passed as opts.mlp_weights. */
+#define POLYLAB_MLP_PARAMS 291
+#define POLYLAB_MLP_FEATURES 5
+#define POLYLAB_MLP_PROBES 4
+
+int32_t polylab_mlp_param_count(void);
+/* W1 uniform in +-1/sqrt(5) from SplitMix64(seed), everything else 0. DEVICE params. */
+polylab_status polylab_mlp_init(float* params, uint64_t seed, polylab_stream stream);
+/* Training data generated by the method itself at P points: per point,
+ * feats (DEVICE P x n x 5), hdiag = H_ii (P x n), e = g/|g| (P x n), and
+ * POLYLAB_MLP_PROBES probe pairs z_k = Pi w_k (Rademacher w_k from
+ * SplitMix64(seed), probe index p*4 + k, the probe convention of the
+ * stochastic method) and y_k = Pi (H + rI) z_k, stored Z, Y (P x n x 4).
+ * FP32.  Points with zero gradient are not allowed here. */
+polylab_status polylab_mlp_data(const polylab_poly* p, const polylab_plan* plan, const double* X, int64_t P,
+                                double regularization, uint64_t seed, float* feats, float* hdiag, float* e,
+                                float* Z, float* Y, polylab_stream stream);
+/* Mean over points and probes of |Pi (D y + U U^T y) - z|^2 / |z|^2 and its
+ * gradient (hand-written backpropagation).  grad: DEVICE 291 floats, loss:
+ * DEVICE 1 float, both overwritten. */
+polylab_status polylab_mlp_loss_grad(const float* params, int64_t P, int32_t n, const float* feats,
+                                     const float* hdiag, const float* e, const float* Z, const float* Y,
+                                     double regularization, float* grad, float* loss, polylab_stream stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8); m, v: DEVICE 291 floats, zero at step 1. */
+polylab_status polylab_mlp_adam(float* params, const float* grad, float* m, float* v, int32_t step, float lr,
+                                polylab_stream stream);
+/* BF16 copy of the parameters for inference (DEVICE, 291 x 2 bytes). */
+polylab_status polylab_mlp_pack(const float* params, void* packed, polylab_stream stream);
+
 /* ------------------------------------------- batched exact directions (one launch) */
 
 /* A batch is a set of polynomials (each with its own n, term list and point

@@ -22,7 +22,10 @@
 #include <algorithm>
 #include <cmath>
 
+#include <cuda_bf16.h>
+
 #include "common.cuh"
+#include "mlp.cuh"
 #include "terms.cuh"
 
 namespace polylab {
@@ -147,11 +150,11 @@ struct StochArgs {
   int maxit, q, assume_nonzero_x;
   uint64_t seed;
   int precond;
-  const float* mlp;  // reserved for the learned preconditioner (diag D and low-rank U per point)
+  const __nv_bfloat16* mlp;  // learned preconditioner weights (BF16), POLYLAB_PRECOND_MLP
   double* D;
   double* Dunit;
   polylab_an_info* info;
-  unsigned char* gws;  // per CTA: 6 vectors of n*QC R
+  unsigned char* gws;  // per CTA: 5 vectors of n*QC R, then U (2 n floats) for the learned preconditioner
   size_t gws_stride;
 };
 
@@ -175,6 +178,10 @@ __global__ void __launch_bounds__(NT) stochastic_kernel(StochArgs a) {
   __shared__ int s_iters[QC];
   __shared__ double s_bnorm[QC], s_rz[QC];
   __shared__ int s_maxed;
+  __shared__ float th[kMlpParams];
+  const bool use_mlp = a.precond == POLYLAB_PRECOND_MLP;
+  if (use_mlp)
+    for (int j = tid; j < kMlpParams; j += NT) th[j] = __bfloat162float(a.mlp[j]);
 
   unsigned char* gb = a.gws + (size_t)blockIdx.x * a.gws_stride;
   const size_t vec = (size_t)n * QC;
@@ -183,6 +190,8 @@ __global__ void __launch_bounds__(NT) stochastic_kernel(StochArgs a) {
   R* Pv = Rv + vec;  // search directions
   R* Zv = Pv + vec;  // preconditioned residuals
   R* Bv = Zv + vec;  // right-hand sides b_s = Pi w_s
+  float* U0 = (float*)(Bv + vec);  // learned low-rank factor, columns 0 and 1
+  float* U1 = U0 + n;
 
   for (int64_t p = blockIdx.x; p < a.P; p += gridDim.x) {
     __syncthreads();
@@ -200,8 +209,9 @@ __global__ void __launch_bounds__(NT) stochastic_kernel(StochArgs a) {
       cbar[i] = R(0);
     }
     __syncthreads();
-    // gradient, |gradient contributions| (for the zero test, kept in Y) and diag(H)
-    for (int i = tid; i < n; i += NT) Y[i] = R(0);
+    // gradient, |gradient contributions| (zero test, Y[0, n)), diag(H) and the
+    // off-diagonal |contribution| mass of every row (learned preconditioner, Y[n, 2n))
+    for (int i = tid; i < 2 * n; i += NT) Y[i] = R(0);
     __syncthreads();
     for (int64_t t = tid; t < a.m; t += NT) {
       const TermRegs tr = load_term(a.terms, t);
@@ -209,8 +219,13 @@ __global__ void __launch_bounds__(NT) stochastic_kernel(StochArgs a) {
         if (kind == 1) {
           atomicAdd(&g[i], val);
           atomicAdd(&Y[i], (R)fabs((double)val));
-        } else if (kind == 2 && i == j) {
-          atomicAdd(&dg[i], val);
+        } else if (kind == 2) {
+          if (i == j) {
+            atomicAdd(&dg[i], val);
+          } else if (use_mlp) {
+            atomicAdd(&Y[n + i], (R)fabs((double)val));
+            atomicAdd(&Y[n + j], (R)fabs((double)val));
+          }
         }
       });
     }
@@ -242,6 +257,15 @@ __global__ void __launch_bounds__(NT) stochastic_kernel(StochArgs a) {
       e[i] = R((double)g[i] / gn);
       const double d = fabs((double)dg[i]) + a.r;
       Dinv[i] = a.precond == POLYLAB_PRECOND_NONE ? R(1) : R(d > 0.0 ? 1.0 / d : 1.0);
+      if (use_mlp) {  // BF16 weights, FP32 arithmetic
+        float f[kMlpF], h[kMlpH], o[kMlpO], D, u0, u1;
+        mlp_features(f, (float)dg[i], (float)Y[n + i], (float)X[i], (float)e[i], (float)g[i], n, (float)a.r);
+        mlp_forward(th, f, h, o);
+        mlp_factors(o, (float)dg[i], (float)a.r, &D, &u0, &u1);
+        Dinv[i] = R(D);
+        U0[i] = u0;
+        U1[i] = u1;
+      }
     }
     if (tid == 0) s_maxed = 0;
     __syncthreads();
@@ -276,8 +300,26 @@ __global__ void __launch_bounds__(NT) stochastic_kernel(StochArgs a) {
       project(Y, QC);
       __syncthreads();
     };
-    auto precondition = [&](int nq) {  // Z = Pi D^{-1} R
-      for (int i = tid; i < (int)vec; i += NT) Zv[i] = Dinv[i / QC] * Rv[i];
+    auto precondition = [&](int nq) {  // Z = Pi D^{-1} R, or Pi (D + U U^T) R when learned
+      if (use_mlp) {
+        double u0r[QC], u1r[QC];
+#pragma unroll
+        for (int s = 0; s < QC; ++s) u0r[s] = u1r[s] = 0.0;
+        for (int i = tid; i < n; i += NT)
+#pragma unroll
+          for (int s = 0; s < QC; ++s) {
+            u0r[s] += (double)U0[i] * (double)Rv[i * QC + s];
+            u1r[s] += (double)U1[i] * (double)Rv[i * QC + s];
+          }
+        block_sums<NT, QC>(u0r, red);
+        block_sums<NT, QC>(u1r, red);
+        for (int i = tid; i < (int)vec; i += NT) {
+          const int row = i / QC, s = i % QC;
+          Zv[i] = Dinv[row] * Rv[i] + R(U0[row] * u0r[s] + U1[row] * u1r[s]);
+        }
+      } else {
+        for (int i = tid; i < (int)vec; i += NT) Zv[i] = Dinv[i / QC] * Rv[i];
+      }
       __syncthreads();
       project(Zv, nq);
       __syncthreads();
@@ -499,11 +541,11 @@ polylab_status launch_stoch(const polylab_plan* plan, const double* X, int64_t P
   a.assume_nonzero_x = o->assume_nonzero_x;
   a.seed = o->seed;
   a.precond = o->precond;
-  a.mlp = (const float*)o->mlp_weights;
+  a.mlp = (const __nv_bfloat16*)o->mlp_weights;
   a.D = D;
   a.Dunit = Dunit;
   a.info = info;
-  a.gws_stride = ((size_t)5 * n * QC * sizeof(R) + 255) & ~size_t(255);
+  a.gws_stride = ((size_t)5 * n * QC * sizeof(R) + 2 * (size_t)n * sizeof(float) + 255) & ~size_t(255);
   Scratch scr(s);
   PL_TRY(scr.get(&a.gws, (size_t)grid * a.gws_stride));
   k<<<(unsigned)grid, NT, smem, s>>>(a);
@@ -512,12 +554,130 @@ polylab_status launch_stoch(const polylab_plan* plan, const double* X, int64_t P
 
 }  // namespace
 
+// Training data for the learned preconditioner: per point the features,
+// |H_ii| (signed diagonal), e, four probes z_k = Pi w_k (SplitMix64, probe
+// index p * 4 + k) and y_k = Pi (H + rI) z_k, all in FP32.
+template <int NT>
+__global__ void __launch_bounds__(NT) mlp_data_kernel(const Term* __restrict__ terms, int64_t m, int n, int E,
+                                                      const double* __restrict__ X, int64_t P, float r,
+                                                      uint64_t seed, float* __restrict__ feats,
+                                                      float* __restrict__ hdiag, float* __restrict__ E_out,
+                                                      float* __restrict__ Z, float* __restrict__ Yg) {
+  constexpr int QC = 4;
+  extern __shared__ __align__(16) unsigned char sm[];
+  const int E1 = E + 1, tid = threadIdx.x;
+  float* pw = (float*)sm;
+  float* Y = pw + (size_t)n * E1;
+  float* g = Y + (size_t)n * QC;
+  float* dg = g + n;
+  float* off = dg + n;
+  double* red = (double*)(((uintptr_t)(off + n) + 15) & ~(uintptr_t)15);
+  __shared__ int s_all[QC];
+  if (tid < QC) s_all[tid] = 1;
+  const int words = (n + 63) / 64;
+  for (int64_t p = blockIdx.x; p < P; p += gridDim.x) {
+    __syncthreads();
+    const double* x = X + p * n;
+    for (int i = tid; i < n; i += NT) {
+      float cur = 1.f;
+      pw[i * E1] = cur;
+      for (int k = 1; k < E1; ++k) {
+        cur *= (float)x[i];
+        pw[i * E1 + k] = cur;
+      }
+      g[i] = dg[i] = off[i] = 0.f;
+    }
+    __syncthreads();
+    for (int64_t t = tid; t < m; t += NT) {
+      const TermRegs tr = load_term(terms, t);
+      term_derivs<float, 2>(tr, pw, E1, [&](int kind, int i, int j, float val) {
+        if (kind == 1) atomicAdd(&g[i], val);
+        else if (kind == 2) {
+          if (i == j) atomicAdd(&dg[i], val);
+          else {
+            atomicAdd(&off[i], fabsf(val));
+            atomicAdd(&off[j], fabsf(val));
+          }
+        }
+      });
+    }
+    __syncthreads();
+    double gg[QC] = {0.0, 0.0, 0.0, 0.0};
+    for (int i = tid; i < n; i += NT) gg[0] += (double)g[i] * (double)g[i];
+    block_sums<NT, QC>(gg, red);
+    const float ginv = (float)(1.0 / sqrt(gg[0]));
+    float* zp = Z + p * (int64_t)n * QC;
+    float* yp = Yg + p * (int64_t)n * QC;
+    for (int i = tid; i < n; i += NT) {
+      const float ei = g[i] * ginv;
+      E_out[p * n + i] = ei;
+      hdiag[p * n + i] = dg[i];
+      mlp_features(feats + (p * (int64_t)n + i) * kMlpF, dg[i], off[i], (float)x[i], ei, g[i], n, r);
+      for (int k = 0; k < QC; ++k) {
+        const uint64_t key = ((uint64_t)p * QC + k) * words + (uint64_t)(i >> 6);
+        zp[i * QC + k] = ((splitmix64(seed, key) >> (i & 63)) & 1ull) ? -1.f : 1.f;
+      }
+    }
+    __syncthreads();
+    // z <- Pi z
+    double d[QC] = {0.0, 0.0, 0.0, 0.0};
+    for (int i = tid; i < n; i += NT)
+      for (int k = 0; k < QC; ++k) d[k] += (double)E_out[p * n + i] * zp[i * QC + k];
+    block_sums<NT, QC>(d, red);
+    for (int i = tid; i < n; i += NT)
+      for (int k = 0; k < QC; ++k) zp[i * QC + k] -= (float)(E_out[p * n + i] * d[k]);
+    for (int i = tid; i < n * QC; i += NT) Y[i] = 0.f;
+    __syncthreads();
+    for (int64_t t = tid; t < m; t += NT) {
+      const TermRegs tr = load_term(terms, t);
+      term_hvp_dispatch<float, QC>(tr, pw, E1, zp, Y, s_all);
+    }
+    __syncthreads();
+    double dy[QC] = {0.0, 0.0, 0.0, 0.0};
+    for (int i = tid; i < n; i += NT)
+      for (int k = 0; k < QC; ++k) {
+        Y[i * QC + k] += r * zp[i * QC + k];
+        dy[k] += (double)E_out[p * n + i] * Y[i * QC + k];
+      }
+    block_sums<NT, QC>(dy, red);
+    for (int i = tid; i < n; i += NT)
+      for (int k = 0; k < QC; ++k) yp[i * QC + k] = Y[i * QC + k] - (float)(E_out[p * n + i] * dy[k]);
+  }
+}
+
 polylab_status affine_stochastic(const polylab_plan* plan, const double* X, int64_t P, const polylab_an_opts* o,
                                  double* D, double* Dunit, polylab_an_info* info, cudaStream_t s) {
   if (P == 0) return POLYLAB_OK;
-  if (o->precond == POLYLAB_PRECOND_MLP) return POLYLAB_ERR_UNSUPPORTED;
   if (o->prec == POLYLAB_FP32) return launch_stoch<float, 256, 16>(plan, X, P, o, D, Dunit, info, s);
   return launch_stoch<double, 256, 8>(plan, X, P, o, D, Dunit, info, s);
 }
 
 }  // namespace polylab
+
+extern "C" polylab_status polylab_mlp_data(const polylab_poly* p, const polylab_plan* plan, const double* X,
+                                           int64_t P, double regularization, uint64_t seed, float* feats,
+                                           float* hdiag, float* e, float* Z, float* Y, polylab_stream stream) {
+  using namespace polylab;
+  if (P < 0 || !X || !feats || !hdiag || !e || !Z || !Y || (!p && !plan)) return POLYLAB_ERR_INVALID_ARG;
+  if (P == 0) return POLYLAB_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  polylab_plan* owned = nullptr;
+  if (!plan) {
+    PL_TRY(polylab_plan_create(p, POLYLAB_PLAN_TERMS, stream, &owned));
+    plan = owned;
+  }
+  const int n = plan->n, E = std::max(plan->max_exp, 1);
+  const size_t smem = (size_t)n * (E + 1) * 4 + (size_t)n * 4 * 4 + 3 * (size_t)n * 4 + 64 + 16 * 8 * 5;
+  polylab_status st = POLYLAB_OK;
+  if (smem > 220 * 1024) {
+    st = POLYLAB_ERR_UNSUPPORTED;
+  } else {
+    auto k = mlp_data_kernel<256>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int grid = (int)std::min<int64_t>(P, (int64_t)num_sms() * 2);
+    k<<<grid, 256, smem, s>>>(plan->terms, plan->m, n, E, X, P, (float)regularization, seed, feats, hdiag, e, Z, Y);
+    st = launch_status("mlp_data_kernel");
+  }
+  if (owned) polylab_plan_destroy(owned, stream);
+  return st;
+}

@@ -90,19 +90,31 @@ _lib.polylab_batch_set_config.argtypes = [C.c_void_p, C.POINTER(_BatchConfig), C
 _lib.polylab_batch_autotune.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(_BatchConfig),
                                         C.POINTER(C.c_float)]
 _lib.polylab_batch_destroy.argtypes = [C.c_void_p, C.c_void_p]
+_lib.polylab_mlp_param_count.restype = C.c_int32
+_lib.polylab_mlp_init.argtypes = [C.c_void_p, C.c_uint64, C.c_void_p]
+_lib.polylab_mlp_data.argtypes = [C.POINTER(_Poly), C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_uint64,
+                                  C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+_lib.polylab_mlp_loss_grad.argtypes = [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                                       C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]
+_lib.polylab_mlp_adam.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_float,
+                                  C.c_void_p]
+_lib.polylab_mlp_pack.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
 _lib.polylab_affine_normal_batched.argtypes = [C.c_int32, C.c_void_p, _PP, _PP, C.POINTER(C.c_int64),
                                                C.POINTER(_AnOpts), _PP, _PP, _PP, C.c_void_p]
 for _f in ("polylab_plan_create", "polylab_plan_destroy", "polylab_eval_derivs", "polylab_affine_normal",
            "polylab_simplify", "polylab_mul", "polylab_add", "polylab_simplify_noalloc", "polylab_batch_create",
            "polylab_batch_run", "polylab_batch_get_config", "polylab_batch_set_config", "polylab_batch_autotune",
-           "polylab_batch_destroy", "polylab_affine_normal_batched", "polylab_plan_gemm_info"):
+           "polylab_batch_destroy", "polylab_affine_normal_batched", "polylab_plan_gemm_info", "polylab_mlp_init",
+           "polylab_mlp_data", "polylab_mlp_loss_grad", "polylab_mlp_adam", "polylab_mlp_pack"):
     getattr(_lib, _f).restype = C.c_int
 
 EXPORTED = ["polylab_status_string", "polylab_last_error", "polylab_simplify", "polylab_mul", "polylab_add",
             "polylab_plan_create", "polylab_plan_destroy", "polylab_plan_closure_size", "polylab_eval_derivs",
             "polylab_an_opts_default", "polylab_affine_normal", "polylab_simplify_noalloc", "polylab_batch_create",
             "polylab_batch_run", "polylab_batch_get_config", "polylab_batch_set_config", "polylab_batch_autotune",
-            "polylab_batch_destroy", "polylab_affine_normal_batched", "polylab_plan_gemm_info"]
+            "polylab_batch_destroy", "polylab_affine_normal_batched", "polylab_plan_gemm_info",
+            "polylab_mlp_param_count", "polylab_mlp_init", "polylab_mlp_data", "polylab_mlp_loss_grad",
+            "polylab_mlp_adam", "polylab_mlp_pack"]
 
 
 def lib():
@@ -364,3 +376,54 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+MLP_PARAMS = 291
+MLP_PROBES = 4
+
+
+def mlp_data(p: DevPoly, X: torch.Tensor, regularization: float, seed: int, plan: Plan | None = None):
+    """(feats, hdiag, e, Z, Y) float32 device tensors (polylab_mlp_data)."""
+    P, n = X.shape
+    dev = X.device
+    feats = torch.empty(P, n, 5, dtype=torch.float32, device=dev)
+    hd = torch.empty(P, n, dtype=torch.float32, device=dev)
+    e = torch.empty(P, n, dtype=torch.float32, device=dev)
+    Z = torch.empty(P, n, MLP_PROBES, dtype=torch.float32, device=dev)
+    Y = torch.empty(P, n, MLP_PROBES, dtype=torch.float32, device=dev)
+    cp = p.cstruct()
+    _check("polylab_mlp_data", _lib.polylab_mlp_data(C.byref(cp), plan.h if plan else None, _ptr(X), P, regularization,
+                                                     seed, _ptr(feats), _ptr(hd), _ptr(e), _ptr(Z), _ptr(Y),
+                                                     _stream()))
+    return feats, hd, e, Z, Y
+
+
+def mlp_loss_grad(params, data, regularization):
+    feats, hd, e, Z, Y = data
+    P, n = hd.shape
+    grad = torch.empty(MLP_PARAMS, dtype=torch.float32, device=params.device)
+    loss = torch.empty(1, dtype=torch.float32, device=params.device)
+    _check("polylab_mlp_loss_grad", _lib.polylab_mlp_loss_grad(_ptr(params), P, n, _ptr(feats), _ptr(hd), _ptr(e),
+                                                               _ptr(Z), _ptr(Y), regularization, _ptr(grad),
+                                                               _ptr(loss), _stream()))
+    return loss, grad
+
+
+def train_preconditioner(data, regularization, steps=200, lr=3e-3, seed=1, device="cuda"):
+    """Adam on the library's loss/gradient kernels; returns (fp32 params,
+    packed bf16 weights for opts.mlp_weights, loss history)."""
+    params = torch.empty(MLP_PARAMS, dtype=torch.float32, device=device)
+    m = torch.zeros_like(params)
+    v = torch.zeros_like(params)
+    _check("polylab_mlp_init", _lib.polylab_mlp_init(_ptr(params), seed, _stream()))
+    hist = []
+    for step in range(1, steps + 1):
+        loss, grad = mlp_loss_grad(params, data, regularization)
+        hist.append(loss)
+        _check("polylab_mlp_adam", _lib.polylab_mlp_adam(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), step, lr,
+                                                         _stream()))
+    final, _ = mlp_loss_grad(params, data, regularization)
+    hist.append(final)
+    packed = torch.empty(MLP_PARAMS, dtype=torch.bfloat16, device=device)
+    _check("polylab_mlp_pack", _lib.polylab_mlp_pack(_ptr(params), _ptr(packed), _stream()))
+    return params, packed, [float(h) for h in torch.cat(hist).cpu()]
