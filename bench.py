@@ -485,7 +485,108 @@ def measure_rows(pl, workloads, torch, dev, p32, p64):
     rows["eval_derivs"] = dict(workload="n=30, 5,000 terms deg<=4 <=4 active, 65,536 points in [-1,1]^30",
                                closure_K=gi["K"], output_columns_padded=gi["Npad"], forms=ev,
                                speedup_vs_fp64={k: round(ev["fp64"]["ms"] / v["ms"], 2) for k, v in ev.items()})
+    del out, Xd
+    rows["stochastic"] = measure_stochastic(pl, workloads, torch, dev, p32)
+    rows["crossover"] = measure_crossover(pl, workloads, torch, dev)
+    rows["simplify_pd_cubed"] = measure_pd3(pl, workloads, torch, dev)
     return rows
+
+
+def _time_call(torch, fn, stream):
+    fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    res = fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b), res
+
+
+def _angle(torch, D, ref):
+    c = (torch.nn.functional.normalize(D, dim=1) * torch.nn.functional.normalize(ref, dim=1)).sum(1)
+    return float(torch.arccos(c.clamp(-1, 1)).mean())
+
+
+def measure_stochastic(pl, workloads, torch, dev, p32):
+    """Large sparse family (n in {500, 1000, 2000}, 20n random terms of degree
+    <= 4, 4,096 points in [-1,1]^n): MF-logDet-Stochastic, FP32, q = 16,
+    tol 1e-4, maxit 80; Jacobi at every n, the learned preconditioner (trained
+    on 48 other points) and the exact form at n = 500 as the judge of error."""
+    stream = torch.cuda.current_stream()
+    out = {}
+    r = 1e-4
+    for n in (500, 1000, 2000):
+        poly, X = workloads.large_sparse(n, P=4096)
+        dp = pl.to_device(poly, dev)
+        Xd = torch.as_tensor(X, device=dev)
+        row = dict(terms=poly.m, points=4096)
+        with pl.Plan(dp) as plan:
+            kw = dict(method="mf-stochastic", regularization=r, num_probes=16, krylov_tol=1e-4, krylov_maxit=80,
+                      prec="fp32", plan=plan, seed=7)
+            ms, res = _time_call(torch, lambda: pl.affine_normal(dp, Xd, precond="jacobi", **kw), stream)
+            info = pl.info_numpy(res[2])
+            row["jacobi"] = dict(ms=round(ms, 2), dirs_per_s=round(4096 / (ms * 1e-3), 1),
+                                 krylov_iters_per_point=round(float(info["krylov_iters"].mean()), 2))
+            if n == 500:
+                tr = workloads.large_sparse(n, P=48, seed_off=1)[1]
+                data = pl.mlp_data(dp, torch.as_tensor(tr, device=dev), r, seed=21, plan=plan)
+                t0 = time.perf_counter()
+                params, packed, hist = pl.train_preconditioner(data, r, steps=150, lr=3e-3)
+                torch.cuda.synchronize()
+                train_s = time.perf_counter() - t0
+                ms2, res2 = _time_call(torch, lambda: pl.affine_normal(dp, Xd, precond="mlp", mlp_weights=packed,
+                                                                       **kw), stream)
+                info2 = pl.info_numpy(res2[2])
+                sub = Xd[:256]
+                msx, rex = _time_call(torch, lambda: pl.affine_normal(dp, sub, plan=plan, regularization=r,
+                                                                      prec="fp32"), stream)
+                row["mlp"] = dict(ms=round(ms2, 2), dirs_per_s=round(4096 / (ms2 * 1e-3), 1),
+                                  krylov_iters_per_point=round(float(info2["krylov_iters"].mean()), 2),
+                                  train_steps=150, train_seconds=round(train_s, 2),
+                                  loss_first_last=[round(hist[0], 5), round(hist[-1], 5)])
+                row["exact_fp32_256_points"] = dict(ms=round(msx, 2), dirs_per_s=round(256 / (msx * 1e-3), 1))
+                row["angle_to_exact_rad"] = dict(jacobi=_angle(torch, res[0][:256], rex[0]),
+                                                 mlp=_angle(torch, res2[0][:256], rex[0]))
+        out[f"n{n}"] = row
+    return out
+
+
+def measure_crossover(pl, workloads, torch, dev):
+    """Paper-shaped stochastic-crossover family (sparse quartics, support 2,
+    m = 3d, speed preset q=1, r=5e-4, tol 2e-2, maxit 6), 512 points each:
+    exact / stochastic time ratio (the paper reports 1.84 / 5.07 / 1.52 on its
+    hardware, one point per call)."""
+    stream = torch.cuda.current_stream()
+    out = {}
+    for d in (80, 260, 500):
+        poly, X = workloads.sparse_quartic(d, 3 * d, 2, P=512)
+        dp = pl.to_device(poly, dev)
+        Xd = torch.as_tensor(X, device=dev)
+        with pl.Plan(dp) as plan:
+            mse, _ = _time_call(torch, lambda: pl.affine_normal(dp, Xd, plan=plan, regularization=5e-4, prec="fp64"),
+                                stream)
+            mss, _ = _time_call(torch, lambda: pl.affine_normal(dp, Xd, plan=plan, method="mf-stochastic",
+                                                                regularization=5e-4, num_probes=1, krylov_tol=2e-2,
+                                                                krylov_maxit=6, prec="fp64"), stream)
+        out[f"d{d}"] = dict(exact_ms=round(mse, 2), stochastic_ms=round(mss, 2), ratio=round(mse / mss, 2))
+    return out
+
+
+def measure_pd3(pl, workloads, torch, dev):
+    """simplify(p_d^3) for p_d = sum_{|a|<=d} x^a in 5 variables, as two
+    products (the paper's heavy-simplify family; it reports 0.158 s for
+    MPOLY-HP at d = 4 on its hardware)."""
+    out = {}
+    for d in (2, 3, 4):
+        dp = pl.to_device(workloads.dense_power_base(d), dev)
+        pl.mul(pl.mul(dp, dp), dp)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        c = pl.mul(pl.mul(dp, dp), dp)
+        torch.cuda.synchronize()
+        out[f"d{d}"] = dict(ms=round((time.perf_counter() - t0) * 1e3, 3), terms=c.m)
+    return out
 
 
 if __name__ == "__main__":
