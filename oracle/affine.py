@@ -20,7 +20,8 @@ Readings (listed in DESIGN.md):
   -1), not a unit vector; ``unit`` is nu/|nu|;
 * no orientation flip: if the Cholesky factorisation of H_T + r I fails the
   point is flagged NOT_PD; if |g| = 0 (or, unless ``assume_nonzero_x``,
-  |g| <= 1e-14 * sum of |gradient contributions|) it is flagged ZERO_GRAD;
+  |g| <= 1e-14 * S with S the sum over all terms and coordinates of
+  |gradient contributions|) it is flagged ZERO_GRAD;
   flagged points return NaN directions;
 * work counters follow the paper's example: hv_evals = n, third_evals = n-1
   for the exact method.
@@ -57,7 +58,7 @@ def _grad_hess(exps, coef, x):
 def _zero_grad(gn, sg, assume_nonzero_x):
     if gn == 0.0 or not np.isfinite(gn):
         return True
-    return (not assume_nonzero_x) and gn <= 1e-14 * float(np.linalg.norm(sg))
+    return (not assume_nonzero_x) and gn <= 1e-14 * float(np.sum(sg))
 
 
 def affine_normal_ad(exps, coef, x, r: float = 1e-6, assume_nonzero_x: bool = False, frame=None,

@@ -201,15 +201,15 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 512 / NT : 1) affine_exac
       s_logdet = 0.0;
     }
     __syncthreads();
+    double gabs = 0.0;  // this thread's share of sum |gradient contributions|
     {
       R* gw = g + wid * n;
-      R* sgw = sg + wid * n;
       for (int64_t t = tid; t < pd.m; t += NT) {
         const TermRegs tr = load_term(pd.terms, t);
         term_derivs<R, 2>(tr, pw, E1, [&](int kind, int i, int j, R val) {
           if (kind == 1) {
             atomicAdd(&gw[i], val);
-            atomicAdd(&sgw[i], fabs(val));
+            gabs += fabs((double)val);
           } else if (kind == 2) {
             atomicAdd(&Hr[i * n + j], val);
           }
@@ -218,30 +218,22 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 512 / NT : 1) affine_exac
     }
     __syncthreads();
     for (int i = tid; i < n; i += NT) {  // fold the warp replicas into replica 0
-      R a = g[i], b = sg[i];
-      for (int q = 1; q < NW; ++q) {
-        a += g[q * n + i];
-        b += sg[q * n + i];
-      }
+      R a = g[i];
+      for (int q = 1; q < NW; ++q) a += g[q * n + i];
       g[i] = a;
-      sg[i] = b;
     }
     for (int idx = tid; idx < nn; idx += NT) {  // mirror the upper triangle
       const int i = idx / n, j = idx - i * n;
       if (i > j) Hr[idx] = Hr[j * n + i];
     }
     // ---------------------------------------------------------- phase 2
-    double gg = 0.0, ss = 0.0;
-    for (int i = tid; i < n; i += NT) {
-      gg += (double)g[i] * (double)g[i];
-      ss += (double)sg[i] * (double)sg[i];
-    }
-    const double2 sums = block_sum2<NT>(gg, ss, red);
+    double gg = 0.0;
+    for (int i = tid; i < n; i += NT) gg += (double)g[i] * (double)g[i];
+    const double2 sums = block_sum2<NT>(gg, gabs, red);
     const double gn = sqrt(sums.x);
-    const double sgn2 = sums.y;
     bool zero = !(gn > 0.0) || !isfinite(gn);
     // relative test at the resolution of the form: 1e-14 (FP64), 1e-6 (FP32 sums)
-    if (!assume_nonzero_x && gn <= (kF64 ? 1e-14 : 1e-6) * sqrt(sgn2)) zero = true;
+    if (!assume_nonzero_x && gn <= (kF64 ? 1e-14 : 1e-6) * sums.y) zero = true;
     if (zero) {
       if (tid == 0 && pd.info) {
         polylab_an_info in{gn, nan(""), POLYLAB_FLAG_ZERO_GRAD, n, n - 1, 0};
@@ -256,14 +248,16 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 512 / NT : 1) affine_exac
     const double en = (double)g[n - 1] / gn;
     const double sgn = en >= 0.0 ? 1.0 : -1.0;
     const double beta = 1.0 / (1.0 + sgn * en);  // 2 / v^T v with v^T v = 2 (1 + s e_n)
+    R* vr = sg;  // v in the form's precision (sg is free): no conversions inside n^2 loops
     for (int i = tid; i < n; i += NT) {
       e[i] = (double)g[i] / gn;
       v[i] = e[i] + (i == n - 1 ? sgn : 0.0);
+      vr[i] = R(v[i]);
     }
     __syncthreads();
     for (int i = tid; i < n; i += NT) {  // u = H v
       R acc = R(0);
-      for (int j = 0; j < n; ++j) acc += Hr[i * n + j] * R(v[j]);
+      for (int j = 0; j < n; ++j) acc += Hr[i * n + j] * vr[j];
       u[i] = acc;
     }
     __syncthreads();
@@ -274,7 +268,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 512 / NT : 1) affine_exac
     __syncthreads();
     for (int idx = tid; idx < nn; idx += NT) {  // P H P = H - v w^T - w v^T
       const int i = idx / n, j = idx - i * n;
-      Hr[idx] -= R(v[i]) * w[j] + w[i] * R(v[j]);
+      Hr[idx] -= vr[i] * w[j] + w[i] * vr[j];
     }
     __syncthreads();
     for (int i = tid; i < m; i += NT) h[i] = -sgn * (double)Hr[i * n + (n - 1)];
@@ -311,6 +305,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 512 / NT : 1) affine_exac
         for (int i = k + 1 + lane; i < m; i += 32) {
           const double lik = Ld[LI(i, k)];
           double* row = Ld + LI(i, 0);
+#pragma unroll 4
           for (int j = k + 1; j <= i; ++j) row[j] -= lik * Ld[LI(j, k)];
         }
         __syncwarp();
@@ -374,7 +369,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 512 / NT : 1) affine_exac
     __syncthreads();
     for (int i = tid; i < n; i += NT) {  // u = [M 0; 0 0] v
       R acc = R(0);
-      for (int j = 0; j < n; ++j) acc += Mr[i * n + j] * R(v[j]);
+      for (int j = 0; j < n; ++j) acc += Mr[i * n + j] * vr[j];
       u[i] = acc;
     }
     __syncthreads();
@@ -385,7 +380,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 512 / NT : 1) affine_exac
     __syncthreads();
     for (int idx = tid; idx < nn; idx += NT) {  // Hr <- W
       const int i = idx / n, j = idx - i * n;
-      Hr[idx] = Mr[idx] - (R(v[i]) * w[j] + w[i] * R(v[j]));
+      Hr[idx] = Mr[idx] - (vr[i] * w[j] + w[i] * vr[j]);
     }
     __syncthreads();
     // ---------------------------------------------------------- phase 3
@@ -416,11 +411,14 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 512 / NT : 1) affine_exac
     for (int i = tid; i < m; i += NT) tv[i] = h[i] - wgt * ((double)c[i] - beta * v[i] * vc);
     __syncthreads();
     double* tau = xs;  // x is no longer needed
+    R* tvr = u;          // right-hand side in the form's precision
+    for (int i = tid; i < m; i += NT) tvr[i] = R(tv[i]);
+    __syncthreads();
     for (int i = tid; i < n; i += NT) {
-      double acc = 0.0;
+      R acc = R(0);
       if (i < m)
-        for (int j = 0; j < m; ++j) acc += (double)Mr[i * n + j] * tv[j];
-      tau[i] = acc;
+        for (int j = 0; j < m; ++j) acc += Mr[i * n + j] * tvr[j];
+      tau[i] = (double)acc;
     }
     __syncthreads();
     part = 0.0;

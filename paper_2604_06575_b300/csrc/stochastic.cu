@@ -209,16 +209,17 @@ __global__ void __launch_bounds__(NT) stochastic_kernel(StochArgs a) {
       cbar[i] = R(0);
     }
     __syncthreads();
-    // gradient, |gradient contributions| (zero test, Y[0, n)), diag(H) and the
+    // gradient, sum of |gradient contributions| (zero test), diag(H) and the
     // off-diagonal |contribution| mass of every row (learned preconditioner, Y[n, 2n))
     for (int i = tid; i < 2 * n; i += NT) Y[i] = R(0);
     __syncthreads();
+    double gabs = 0.0;  // this thread's share of sum |gradient contributions|
     for (int64_t t = tid; t < a.m; t += NT) {
       const TermRegs tr = load_term(a.terms, t);
       term_derivs<R, 2>(tr, pw, E1, [&](int kind, int i, int j, R val) {
         if (kind == 1) {
           atomicAdd(&g[i], val);
-          atomicAdd(&Y[i], (R)fabs((double)val));
+          gabs += fabs((double)val);
         } else if (kind == 2) {
           if (i == j) {
             atomicAdd(&dg[i], val);
@@ -233,15 +234,13 @@ __global__ void __launch_bounds__(NT) stochastic_kernel(StochArgs a) {
     double gg[QC], ss[QC];
 #pragma unroll
     for (int s = 0; s < QC; ++s) gg[s] = ss[s] = 0.0;
-    for (int i = tid; i < n; i += NT) {
-      gg[0] += (double)g[i] * (double)g[i];
-      ss[0] += (double)Y[i] * (double)Y[i];
-    }
+    for (int i = tid; i < n; i += NT) gg[0] += (double)g[i] * (double)g[i];
+    ss[0] = gabs;
     block_sums<NT, QC>(gg, red);
     block_sums<NT, QC>(ss, red);
     const double gn = sqrt(gg[0]);
     bool zero = !(gn > 0.0) || !isfinite(gn);
-    if (!a.assume_nonzero_x && gn <= (sizeof(R) == 8 ? 1e-14 : 1e-6) * sqrt(ss[0])) zero = true;
+    if (!a.assume_nonzero_x && gn <= (sizeof(R) == 8 ? 1e-14 : 1e-6) * ss[0]) zero = true;
     if (zero) {
       if (tid == 0 && a.info) {
         polylab_an_info in{gn, nan(""), POLYLAB_FLAG_ZERO_GRAD, 0, a.q, 0};
