@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 512 / NT : 1) affine_exac
       s_logdet = 0.0;
     }
     __syncthreads();
-    double gabs = 0.0;  // this thread's share of sum |gradient contributions|
+    R gabs = R(0);  // this thread's share of sum |gradient contributions|
     {
       R* gw = g + wid * n;
       for (int64_t t = tid; t < pd.m; t += NT) {
@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 512 / NT : 1) affine_exac
         term_derivs<R, 2>(tr, pw, E1, [&](int kind, int i, int j, R val) {
           if (kind == 1) {
             atomicAdd(&gw[i], val);
-            gabs += fabs((double)val);
+            gabs += fabs(val);
           } else if (kind == 2) {
             atomicAdd(&Hr[i * n + j], val);
           }
@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 512 / NT : 1) affine_exac
     // ---------------------------------------------------------- phase 2
     double gg = 0.0;
     for (int i = tid; i < n; i += NT) gg += (double)g[i] * (double)g[i];
-    const double2 sums = block_sum2<NT>(gg, gabs, red);
+    const double2 sums = block_sum2<NT>(gg, (double)gabs, red);
     const double gn = sqrt(sums.x);
     bool zero = !(gn > 0.0) || !isfinite(gn);
     // relative test at the resolution of the form: 1e-14 (FP64), 1e-6 (FP32 sums)

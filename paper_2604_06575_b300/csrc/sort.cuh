@@ -85,7 +85,7 @@ polylab_status exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, Mem&
 // __match_any_sync; per-digit warp counts are prefix-summed across warps.
 
 constexpr int kSortWarps = 8;
-constexpr int kSortIPT = 16;
+constexpr int kSortIPT = 8;
 constexpr int kSortTile = kSortWarps * 32 * kSortIPT;
 
 template <typename K>

@@ -74,7 +74,9 @@ __device__ __forceinline__ void term_hessian_block(const TermRegs& t, const R* _
 }
 
 // Y[var_a][s] += sum_b blk[a][b] V[var_b][s] for the QC probes of a chunk
-// (4 probes per pass, shared-memory atomics into Y).
+// (4 probes per pass, shared-memory atomics into Y).  V rows are QC apart,
+// Y rows QC + 1 apart (an odd stride keeps lanes with different variables on
+// different banks).
 template <typename R, int K, int QC>
 __device__ __forceinline__ void term_hvp(const TermRegs& t, const R* __restrict__ pw, int E1,
                                          const R* __restrict__ V, R* Y, const int* active) {
@@ -95,7 +97,7 @@ __device__ __forceinline__ void term_hvp(const TermRegs& t, const R* __restrict_
         R acc = R(0);
 #pragma unroll
         for (int b = 0; b < K; ++b) acc += blk[a * K + b] * v[b][q];
-        atomicAdd(&Y[t.var[a] * QC + s0 + q], acc);
+        atomicAdd(&Y[t.var[a] * (QC + 1) + s0 + q], acc);
       }
     }
   }
@@ -168,7 +170,8 @@ __global__ void __launch_bounds__(NT) stochastic_kernel(StochArgs a) {
   R* pw = (R*)sm;
   R* Y = pw + (size_t)n * E1;
   // per-point vectors in the form's precision (FP32 form: shared memory for n up to ~2000)
-  R* g = (R*)(((uintptr_t)(Y + (size_t)n * QC) + 15) & ~(uintptr_t)15);
+  constexpr int YS = QC + 1;  // row stride of Y (see term_hvp)
+  R* g = (R*)(((uintptr_t)(Y + (size_t)n * YS) + 15) & ~(uintptr_t)15);
   R* dg = g + n;
   R* e = dg + n;
   R* cbar = e + n;
@@ -273,30 +276,30 @@ __global__ void __launch_bounds__(NT) stochastic_kernel(StochArgs a) {
 
     // ---------------------------------------------------------------- PCG
     // Solves Pi (H + rI) Pi u_s = b_s for the `nq` columns present in Bv.
-    auto project = [&](R* V, int nq) {  // V_s <- V_s - e (e . V_s)
+    auto project = [&](R* V, int nq, int stride) {  // V_s <- V_s - e (e . V_s); rows `stride` apart
       double d[QC];
 #pragma unroll
       for (int s = 0; s < QC; ++s) d[s] = 0.0;
       for (int i = tid; i < n; i += NT)
 #pragma unroll
-        for (int s = 0; s < QC; ++s) d[s] += (double)e[i] * (double)V[i * QC + s];
+        for (int s = 0; s < QC; ++s) d[s] += (double)e[i] * (double)V[i * stride + s];
       block_sums<NT, QC>(d, red);
       for (int i = tid; i < n; i += NT)
 #pragma unroll
         for (int s = 0; s < QC; ++s)
-          if (s < nq) V[i * QC + s] -= R((double)e[i] * d[s]);
+          if (s < nq) V[i * stride + s] -= R((double)e[i] * d[s]);
     };
     auto apply_A = [&](const R* V) {  // Y = Pi (H + rI) V (V in e-perp), into shared memory
-      for (int i = tid; i < (int)vec; i += NT) Y[i] = R(0);
+      for (int i = tid; i < n * YS; i += NT) Y[i] = R(0);
       __syncthreads();
       for (int64_t t = tid; t < a.m; t += NT) {
         const TermRegs tr = load_term(a.terms, t);
         term_hvp_dispatch<R, QC>(tr, pw, E1, V, Y, s_active);
       }
       __syncthreads();
-      for (int i = tid; i < (int)vec; i += NT) Y[i] += R(a.r) * V[i];
+      for (int i = tid; i < (int)vec; i += NT) Y[(i / QC) * YS + i % QC] += R(a.r) * V[i];
       __syncthreads();
-      project(Y, QC);
+      project(Y, QC, YS);
       __syncthreads();
     };
     auto precondition = [&](int nq) {  // Z = Pi D^{-1} R, or Pi (D + U U^T) R when learned
@@ -320,7 +323,7 @@ __global__ void __launch_bounds__(NT) stochastic_kernel(StochArgs a) {
         for (int i = tid; i < (int)vec; i += NT) Zv[i] = Dinv[i / QC] * Rv[i];
       }
       __syncthreads();
-      project(Zv, nq);
+      project(Zv, nq, QC);
       __syncthreads();
     };
     auto pcg = [&](int nq) {
@@ -376,7 +379,7 @@ __global__ void __launch_bounds__(NT) stochastic_kernel(StochArgs a) {
         for (int s = 0; s < QC; ++s) py[s] = 0.0;
         for (int i = tid; i < n; i += NT)
 #pragma unroll
-          for (int s = 0; s < QC; ++s) py[s] += (double)Pv[i * QC + s] * (double)Y[i * QC + s];
+          for (int s = 0; s < QC; ++s) py[s] += (double)Pv[i * QC + s] * (double)Y[i * YS + s];
         block_sums<NT, QC>(py, red);
         // breakdown guard: a probe whose curvature p.Ap is not positive (or not
         // finite) stops here with its current iterate
@@ -388,7 +391,7 @@ __global__ void __launch_bounds__(NT) stochastic_kernel(StochArgs a) {
           if (!s_active[s]) continue;
           const R alpha = R(s_rz[s] / py[s]);
           Xv[i] += alpha * Pv[i];
-          Rv[i] -= alpha * Y[i];
+          Rv[i] -= alpha * Y[(i / QC) * YS + s];
         }
         __syncthreads();
         precondition(nq);
@@ -437,7 +440,7 @@ __global__ void __launch_bounds__(NT) stochastic_kernel(StochArgs a) {
         Bv[i] = w;
       }
       __syncthreads();
-      project(Bv, nq);
+      project(Bv, nq, QC);
       __syncthreads();
       total_iters += pcg(nq);
       // cbar += (1/q) sum_s T(., u_s, b_s): per term, the symmetrised block
@@ -466,7 +469,7 @@ __global__ void __launch_bounds__(NT) stochastic_kernel(StochArgs a) {
     for (int i = tid; i < (int)vec; i += NT) Pv[i] = (i % QC == 0) ? R(e[i / QC]) : R(0);
     if (tid < QC) s_active[tid] = tid == 0;
     __syncthreads();
-    for (int i = tid; i < (int)vec; i += NT) Y[i] = R(0);
+    for (int i = tid; i < n * YS; i += NT) Y[i] = R(0);
     __syncthreads();
     for (int64_t t = tid; t < a.m; t += NT) {  // Y = H e (ambient, column 0)
       const TermRegs tr = load_term(a.terms, t);
@@ -475,9 +478,9 @@ __global__ void __launch_bounds__(NT) stochastic_kernel(StochArgs a) {
     __syncthreads();
     const double wgt = gn / (double)(n + 1);
     for (int i = tid; i < (int)vec; i += NT)
-      Bv[i] = (i % QC == 0) ? R((double)Y[i] - wgt * (double)cbar[i / QC]) : R(0);
+      Bv[i] = (i % QC == 0) ? R((double)Y[(i / QC) * YS] - wgt * (double)cbar[i / QC]) : R(0);
     __syncthreads();
-    project(Bv, 1);
+    project(Bv, 1, QC);
     __syncthreads();
     total_iters += pcg(1);
     // ---------------------------------------------------------- direction
@@ -506,7 +509,7 @@ namespace {
 
 template <typename R, int QC>
 size_t stoch_smem(int n, int E1, int NT) {
-  size_t b = (size_t)n * E1 * sizeof(R) + (size_t)n * QC * sizeof(R);
+  size_t b = (size_t)n * E1 * sizeof(R) + (size_t)n * (QC + 1) * sizeof(R);
   b = (b + 15) & ~size_t(15);
   b += 5 * (size_t)n * sizeof(R);
   b = (b + 15) & ~size_t(15);
@@ -567,7 +570,7 @@ __global__ void __launch_bounds__(NT) mlp_data_kernel(const Term* __restrict__ t
   const int E1 = E + 1, tid = threadIdx.x;
   float* pw = (float*)sm;
   float* Y = pw + (size_t)n * E1;
-  float* g = Y + (size_t)n * QC;
+  float* g = Y + (size_t)n * (QC + 1);
   float* dg = g + n;
   float* off = dg + n;
   double* red = (double*)(((uintptr_t)(off + n) + 15) & ~(uintptr_t)15);
@@ -625,7 +628,7 @@ __global__ void __launch_bounds__(NT) mlp_data_kernel(const Term* __restrict__ t
     block_sums<NT, QC>(d, red);
     for (int i = tid; i < n; i += NT)
       for (int k = 0; k < QC; ++k) zp[i * QC + k] -= (float)(E_out[p * n + i] * d[k]);
-    for (int i = tid; i < n * QC; i += NT) Y[i] = 0.f;
+    for (int i = tid; i < n * (QC + 1); i += NT) Y[i] = 0.f;
     __syncthreads();
     for (int64_t t = tid; t < m; t += NT) {
       const TermRegs tr = load_term(terms, t);
@@ -635,12 +638,12 @@ __global__ void __launch_bounds__(NT) mlp_data_kernel(const Term* __restrict__ t
     double dy[QC] = {0.0, 0.0, 0.0, 0.0};
     for (int i = tid; i < n; i += NT)
       for (int k = 0; k < QC; ++k) {
-        Y[i * QC + k] += r * zp[i * QC + k];
-        dy[k] += (double)E_out[p * n + i] * Y[i * QC + k];
+        Y[i * (QC + 1) + k] += r * zp[i * QC + k];
+        dy[k] += (double)E_out[p * n + i] * Y[i * (QC + 1) + k];
       }
     block_sums<NT, QC>(dy, red);
     for (int i = tid; i < n; i += NT)
-      for (int k = 0; k < QC; ++k) yp[i * QC + k] = Y[i * QC + k] - (float)(E_out[p * n + i] * dy[k]);
+      for (int k = 0; k < QC; ++k) yp[i * QC + k] = Y[i * (QC + 1) + k] - (float)(E_out[p * n + i] * dy[k]);
   }
 }
 
@@ -666,7 +669,7 @@ extern "C" polylab_status polylab_mlp_data(const polylab_poly* p, const polylab_
     plan = owned;
   }
   const int n = plan->n, E = std::max(plan->max_exp, 1);
-  const size_t smem = (size_t)n * (E + 1) * 4 + (size_t)n * 4 * 4 + 3 * (size_t)n * 4 + 64 + 16 * 8 * 5;
+  const size_t smem = (size_t)n * (E + 1) * 4 + (size_t)n * 5 * 4 + 3 * (size_t)n * 4 + 64 + 16 * 8 * 5;
   polylab_status st = POLYLAB_OK;
   if (smem > 220 * 1024) {
     st = POLYLAB_ERR_UNSUPPORTED;
