@@ -220,9 +220,8 @@ def main():
     import torch
     import torch.distributed as dist
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2604_06575_b300 import dist as pdist
+    rank, world, local = pdist.rank_info()
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
@@ -247,7 +246,7 @@ def main():
         return
 
     # ---- workload (rank r: its own batch, weak scaling)
-    polys, Xs = workloads.batched_uneven(seed_off=rank, n_polys=args.polys)
+    polys, Xs = workloads.batched_uneven(seed_off=pdist.workload_seed_offset(rank), n_polys=args.polys)
     dps = [pl.to_device(p, dev) for p in polys]
     plans = [pl.Plan(d) for d in dps]
     Xd = [torch.as_tensor(X, device=dev) for X in Xs]
@@ -309,11 +308,8 @@ def main():
     res = {}
     for form in forms:
         step_ms = timed(form, args.steps, args.warmup)
-        t = torch.tensor([sum(step_ms)], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
         # the step is one launch of the exact kernel, so its duration is the kernel's
-        res[form] = dict(total_ms=float(t.item()), step_ms=step_ms, kern_ms=step_ms)
+        res[form] = dict(total_ms=pdist.max_over_ranks(sum(step_ms), dev), step_ms=step_ms, kern_ms=step_ms)
     clk = clocks.stop()
 
     # error of the FP32 form against the FP64 form, every point (angle, radians)
@@ -334,7 +330,7 @@ def main():
     def rate(form):
         if form not in res:
             return float("nan")
-        return npts * world * args.steps / (res[form]["total_ms"] * 1e-3)
+        return pdist.job_rate(npts, world, args.steps, res[form]["total_ms"])
 
     # ---- e2e through the public API: pinned host points in, directions out, every step
     Xcat = torch.cat([torch.as_tensor(X).reshape(-1) for X in Xs]).pin_memory()
@@ -361,10 +357,7 @@ def main():
         e2e_step()
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(e2e_ms, op=dist.ReduceOp.MAX)
-    e2e_rate = npts * world * args.steps / (float(e2e_ms.item()) * 1e-3)
+    e2e_rate = pdist.job_rate(npts, world, args.steps, pdist.max_over_ranks(e0.elapsed_time(e1), dev))
     nbytes = int(Xcat.numel() * 8)
     outs = {f: [(batches[f].D[i], batches[f].Du[i], batches[f].info[i]) for i in range(len(dps))]
             for f in forms}
