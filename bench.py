@@ -77,30 +77,37 @@ def term_stats(exps: np.ndarray):
     return k, d
 
 
+STAGES = ("terms", "frame", "third")
+
+
 def exact_flops(poly, P: int):
-    """Algorithmic flops of one exact direction (stated in the design doc), split
-    into the parts the FP32 form runs in FP32 (term sums, triangular inverse)
-    and those kept in FP64 (Cholesky, frame updates, tau, normalisation)."""
+    """Algorithmic flops of one exact direction (stated in the design doc), per
+    stage: the gradient/Hessian term sweep, the frame stage (LDL^T in FP64,
+    inverse and the n^2 frame updates in the form's precision) and the
+    third-derivative sweep with the direction (W y)."""
     n = poly.n
     m = n - 1
     k, d = term_stats(poly.exps)
     f_terms = float(np.sum(2 * (k + k * (k + 1) // 2)))
     k3 = k[d >= 3]
     f_third = float(np.sum(2 * (k3 + 2 * k3 * (k3 - 1) + 3 * (k3 * (k3 - 1) * (k3 - 2) // 6))))
-    f_chol = 2.0 * m ** 3 / 3.0
-    f_inv = 2.0 * m ** 3 / 3.0
-    f_small = 14.0 * n * n
-    per = dict(terms=f_terms, third=f_third, chol=f_chol, inv=f_inv, small=f_small)
+    f_ldlt = m ** 3 / 3.0           # m^3/6 multiply-adds
+    f_inv = 2.0 * m ** 3 / 3.0      # L^{-1} and M = X'^T X', m^3/6 multiply-adds each
+    f_small = 14.0 * n * n          # H v, P H P, M v, W
+    f_dir = 2.0 * n * n             # W y
+    per = dict(terms=f_terms, third=f_third + f_dir, ldlt=f_ldlt, inv=f_inv, small=f_small)
     return {key: val * P for key, val in per.items()}
 
 
-def alu_roofline(flops: dict, t_s: float, form: str, p32: float, p64: float):
-    if form == "fp64":
-        f64 = sum(flops.values())
-        f32 = 0.0
-    else:
-        f32 = flops["terms"] + flops["third"] + flops["inv"]
-        f64 = flops["chol"] + flops["small"]
+STAGE_PARTS = dict(terms=("terms",), frame=("ldlt", "inv", "small"), third=("third",))
+
+
+def alu_roofline(flops: dict, t_s: float, form: str, p32: float, p64: float, parts=None):
+    """Op-mix ALU roofline: FP64 work at the FP64 peak, the rest at the peak
+    of the form's precision (the LDL^T is FP64 in both forms)."""
+    keys = parts or tuple(flops)
+    f64 = sum(flops[k] for k in keys if form == "fp64" or k == "ldlt")
+    f32 = sum(flops[k] for k in keys) - f64
     tot = f32 + f64
     t_min = f32 / (p32 * 1e12) + f64 / (p64 * 1e12)
     peak = tot / t_min / 1e12
@@ -261,7 +268,7 @@ def main():
             dist.barrier()
 
     def capture(batch):
-        """One persistent launch (memset of the work counter + kernel) in a CUDA graph."""
+        """One run (three memsets of the work counters + three persistent launches) in a CUDA graph."""
         g = torch.cuda.CUDAGraph()
         side = torch.cuda.Stream()
         side.wait_stream(torch.cuda.current_stream())
@@ -278,8 +285,7 @@ def main():
     for form in forms:
         batches[form] = pl.Batch(dps, plans, Xd, opts[form])
         if args.config:
-            t, c, o = (int(v) for v in args.config.split(","))
-            batches[form].set_config(t, c, o)
+            batches[form].set_config(*(int(v) for v in args.config.split(",")))
             tuned[form] = dict(batches[form].config(), ms=None)
         else:
             cfg, ms = batches[form].autotune(reps=1)
@@ -304,12 +310,31 @@ def main():
         barrier()
         return step_ms
 
+    def stage_times(form, steps):
+        """Mean duration of each stage's launch (CUDA events on the launching
+        stream, L2 flushed before every launch), same batch and configuration."""
+        b = batches[form]
+        b.run()
+        out = {}
+        for s, name in enumerate(STAGES):
+            ms = []
+            for _ in range(steps):
+                flush.zero_()
+                s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                s0.record(stream)
+                b.run_stage(s)
+                s1.record(stream)
+                torch.cuda.synchronize()
+                ms.append(s0.elapsed_time(s1))
+            out[name] = statistics.mean(ms)
+        return out
+
     clocks = Clocks()
     res = {}
     for form in forms:
         step_ms = timed(form, args.steps, args.warmup)
-        # the step is one launch of the exact kernel, so its duration is the kernel's
-        res[form] = dict(total_ms=pdist.max_over_ranks(sum(step_ms), dev), step_ms=step_ms, kern_ms=step_ms)
+        res[form] = dict(total_ms=pdist.max_over_ranks(sum(step_ms), dev), step_ms=step_ms,
+                         stage_ms=stage_times(form, args.steps))
     clk = clocks.stop()
 
     # error of the FP32 form against the FP64 form, every point (angle, radians)
@@ -341,7 +366,7 @@ def main():
     xv = [Xdev_flat[offs[i]:offs[i + 1]].view(-1, polys[i].n) for i in range(len(polys))]
     dv = [Ddev_flat[offs[i]:offs[i + 1]].view(-1, polys[i].n) for i in range(len(polys))]
     e2e_batch = pl.Batch(dps, plans, xv, opts[chosen], want_unit=False, want_info=False, D=dv)
-    e2e_batch.set_config(**{k: tuned[chosen][k] for k in ("threads", "ctas_per_sm", "order")})
+    e2e_batch.set_config(**{k: tuned[chosen][k] for k in ("threads", "ctas_per_sm", "order", "term_threads")})
 
     def e2e_step():
         Xdev_flat.copy_(Xcat.view(-1), non_blocking=True)
@@ -369,10 +394,19 @@ def main():
     for p, X in zip(polys, Xs):
         for key, val in exact_flops(p, X.shape[0]).items():
             flops[key] = flops.get(key, 0.0) + val
-    kern_s = statistics.median(res[chosen]["kern_ms"]) * 1e-3
-    roof = alu_roofline(flops, kern_s, chosen, p32, p64)
+    kernels = dict(terms="exact_terms_kernel", frame="exact_frame_kernel", third="exact_third_kernel")
+    stage_ms = res[chosen]["stage_ms"]
+    stages = {}
+    for name in STAGES:
+        r = alu_roofline(flops, stage_ms[name] * 1e-3, chosen, p32, p64, STAGE_PARTS[name])
+        stages[name] = dict(kernel=kernels[name], ms=round(stage_ms[name], 3), achieved=r["achieved"],
+                            peak=r["peak"], frac=r["frac"])
+    dom = max(STAGES, key=lambda k: stage_ms[k])
+    roof = alu_roofline(flops, stage_ms[dom] * 1e-3, chosen, p32, p64, STAGE_PARTS[dom])
+    roof["kernel"] = f"{kernels[dom]} (the longest of the three launches of a step)"
     roof["launches_per_step"] = 1
-    roof["kernel"] = "affine_exact_kernel (one persistent launch per step, CUDA-graph replay)"
+    roof["stages"] = stages
+    roof["path"] = alu_roofline(flops, statistics.median(res[chosen]["step_ms"]) * 1e-3, chosen, p32, p64)
 
     line = dict(metric=METRIC, value=round(rate(chosen), 1), unit="dirs/s", n_gpus=world, steps=args.steps,
                 warmup=args.warmup, ms_per_step=round(res[chosen]["total_ms"] / args.steps, 3),
@@ -391,7 +425,7 @@ def main():
                            speedup_vs_fp64=round(rate(chosen) / rate("fp64"), 3)),
                 e2e=dict(value=round(e2e_rate, 1), unit="dirs/s", h2d_bytes_per_step=nbytes,
                          d2h_bytes_per_step=nbytes),
-                gpu_launches=args.steps,
+                gpu_launches=3 * args.steps,
                 autotune=tuned,
                 roofline=roof, clocks=clk)
 

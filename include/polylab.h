@@ -286,26 +286,35 @@ polylab_status polylab_mlp_pack(const float* params, void* packed, polylab_strea
 /* ------------------------------------------- batched exact directions (one launch) */
 
 /* A batch is a set of polynomials (each with its own n, term list and point
- * set) whose exact affine-normal directions are computed by ONE persistent
- * kernel launch: (polynomial, point) work items are taken from a device
- * counter, most expensive polynomials first, so an uneven batch keeps every
- * SM busy.  polylab_batch_create uploads the descriptors (and builds a term
- * plan for every NULL entry of `plans`; `polys` may then not be NULL), so
- * polylab_batch_run only enqueues one memset and one kernel on `stream` and
- * may be captured into a CUDA graph and replayed.  Each run overwrites
+ * set) whose exact affine-normal directions are computed by three persistent
+ * kernel launches over all of them (the stages of polylab_batch_config):
+ * (polynomial, point) work items are taken from a device counter per stage,
+ * most expensive polynomials first, so an uneven batch keeps every SM busy.
+ * The stages pass each point's H, W (n x n in the form's precision) and a few
+ * vectors through a workspace the batch owns (sum over polynomials of
+ * P_i (n_i^2 x 2 x element size + (4 n_i + 8) x 8) bytes).
+ * polylab_batch_create uploads the descriptors and allocates the workspace
+ * (and builds a term plan for every NULL entry of `plans`; `polys` may then
+ * not be NULL), so polylab_batch_run only enqueues three memsets and three
+ * kernels on `stream` and may be captured into a CUDA graph and replayed.  Each run overwrites
  * D[i], Dunit[i] (DEVICE P[i] x n_i or NULL) and info[i] (DEVICE P[i] records
  * or NULL) from X[i] (DEVICE P[i] x n_i).  opts->method must be
  * POLYLAB_MF_EXACT; opts->prec POLYLAB_FP64 or POLYLAB_FP32.  The arrays of
  * pointers passed to create are read during the call only. */
 typedef struct polylab_batch polylab_batch;
 
-/* Launch configuration: CTA size (64, 128 or 256 threads per point), a cap
- * on resident CTAs per SM (0: the occupancy limit) and the work order (1:
- * most expensive polynomials first, 0: as given). */
+/* Launch configuration.  A run is three persistent launches over the same
+ * (polynomial, point) items: the gradient/Hessian term sweep, the frame stage
+ * (projected Hessian, FP64 LDL^T, inverse) and the third-derivative sweep with
+ * the direction.  threads: frame-stage CTA size (64, 128 or 256 threads per
+ * point); ctas_per_sm: cap on resident frame-stage CTAs per SM (0: the
+ * occupancy limit); order: 1 = most expensive polynomials first, 0 = as
+ * given; term_threads: CTA size of both term sweeps (64, 128 or 256). */
 typedef struct {
   int32_t threads;
   int32_t ctas_per_sm;
   int32_t order;
+  int32_t term_threads;
 } polylab_batch_config;
 
 polylab_status polylab_batch_create(int32_t n_polys, const polylab_poly* polys,
@@ -314,14 +323,22 @@ polylab_status polylab_batch_create(int32_t n_polys, const polylab_poly* polys,
                                     double* const* Dunit, polylab_an_info* const* info,
                                     polylab_stream stream, polylab_batch** batch);
 polylab_status polylab_batch_run(polylab_batch* batch, polylab_stream stream);
+/* One stage of a run (0: term sweep, 1: frame stage, 2: third-derivative
+ * sweep and directions), for timing the stages separately: a stage reads what
+ * the previous stages of an earlier or the same run left in the workspace,
+ * so stage s may only be run after stages 0..s-1 have run on the same inputs.
+ * POLYLAB_ERR_INVALID_ARG for another stage number. */
+polylab_status polylab_batch_run_stage(polylab_batch* batch, int32_t stage, polylab_stream stream);
 polylab_status polylab_batch_get_config(const polylab_batch* batch, polylab_batch_config* cfg);
 polylab_status polylab_batch_set_config(polylab_batch* batch, const polylab_batch_config* cfg,
                                         polylab_stream stream);
-/* The project's autotuner: times every configuration in {64,128,256}
- * threads x {occupancy, 2, 4} CTAs per SM x {cost order, given order} on
- * this batch (one warm-up and `reps` timed runs each, CUDA events on
- * `stream`, synchronising), keeps the fastest and returns it (and its mean
- * time in ms, if best_ms is not NULL).  The outputs hold the last run's
+/* The project's autotuner, stage by stage on this batch (one warm-up and
+ * `reps` timed runs per trial, CUDA events on `stream`, synchronising):
+ * term_threads in {64,128,256} timed over the two term sweeps, then threads in
+ * {64,128,256} x ctas_per_sm in {occupancy, 2, 4} timed over the frame stage,
+ * then order in {cost order, given order} timed over the whole run.  Keeps
+ * the fastest of each step and returns the result (and the mean time of a
+ * whole run in ms, if best_ms is not NULL).  The outputs hold the last run's
  * results. */
 polylab_status polylab_batch_autotune(polylab_batch* batch, int32_t reps, polylab_stream stream,
                                       polylab_batch_config* chosen, float* best_ms);

@@ -1,26 +1,35 @@
-// MF-logDet-Exact affine-normal direction (Sec. 5), one CTA per point, one
-// persistent launch for any number of polynomials.
+// MF-logDet-Exact affine-normal direction (Sec. 5) for a batch of
+// (polynomial, point) work items, in three persistent launches that pass
+// per-point data through a device workspace:
 //
-//   phase 1  g, H at x from the term list (shared-memory accumulation)
-//   phase 2  e = g/|g|; Householder reflector P = I - beta v v^T with
-//            v = e + s e_n (s = sign(e_n)), so P e_n = -s e and the first
-//            n-1 columns of P are an orthonormal frame Q_T of e-perp;
-//            P H P by a rank-2 update; H_T = (PHP)[0:m,0:m] + r I (m = n-1),
-//            h = Q_T^T H e = -s (PHP)[0:m, n-1];
-//            Cholesky H_T = L L^T in FP64 by one warp (failure -> NOT_PD),
-//            log-det; M = (H_T)^{-1} = L^{-T} L^{-1}; W = Q_T M Q_T^T = P [M 0; 0 0] P
-//   phase 3  c_l = sum_jk d_l d_j d_k f(x) W_jk from the term list, which is
-//            a_i = tr(H_T^{-1} d_{t_i} H_T) = (Q_T^T c)_i without forming the
-//            third-derivative tensor
-//   phase 4  tau = M (h - |g|/(n+1) a);  nu = Q_T tau - e = P [tau; 0] - e.
+//   stage 1 (terms)  g = grad f(x) and H = Hess f(x) from the term list,
+//                    accumulated in shared memory            -> H, g, sum |g terms|
+//   stage 2 (frame)  e = g/|g|; Householder reflector P = I - beta v v^T with
+//                    v = e + s e_n (s = sign(e_n)), so P e_n = -s e and the
+//                    first m = n-1 columns of P are an orthonormal frame Q_T
+//                    of e-perp; P H P by a rank-2 update; H_T = (PHP)[0:m,0:m]
+//                    + r I, h = Q_T^T H e = -s (PHP)[0:m, n-1]; LDL^T of H_T in
+//                    FP64 (a non-positive pivot flags NOT_PD), log-det;
+//                    M = H_T^{-1}; W = Q_T M Q_T^T = P [M 0; 0 0] P
+//                                                  -> W, v, e, h, beta, |g|, log-det
+//   stage 3 (third)  c_l = sum_jk d_l d_j d_k f(x) W_jk from the term list, so
+//                    a_i = tr(H_T^{-1} d_{t_i} H_T) = (Q_T^T c)_i = (P c)_i
+//                    without forming the third-derivative tensor;
+//                    tau = M (h - |g|/(n+1) a) and, because [M 0; 0 0] = P W P,
+//                    nu = Q_T tau - e = W P [h - |g|/(n+1) a; 0] - e.
+//
+// The two term sweeps are latency bound and run best with many resident CTAs;
+// the frame stage is bound by the dependent FP64 factorisation chain.  As
+// separate launches each stage gets its own CTA size, register budget and
+// shared memory.
 //
 // R = double: every step in FP64.  R = float (POLYLAB_FP32): term sums, frame
-// update, triangular inverse, W and the trace term in FP32; the Cholesky
-// factorisation, log-det, tau and normalisation in FP64.
+// update, inverse, W and the trace term in FP32; the LDL^T factorisation,
+// log-det, the O(n) vectors and the normalisation in FP64.
 //
-// Work items are (polynomial, point) pairs taken from an atomic counter in the
-// order of a host-built permutation (most expensive polynomials first), so an
-// uneven batch keeps every SM busy in a single launch.
+// Work items are taken from one device counter per stage in the order of a
+// host-built permutation (most expensive polynomials first), so an uneven
+// batch keeps every SM busy.
 #include <algorithm>
 #include <cmath>
 #include <numeric>
@@ -33,6 +42,12 @@
 namespace polylab {
 
 namespace {
+
+// Per-point record of small vectors in the workspace (doubles):
+// [0,n) g | [n,2n) v | [2n,3n) e | [3n,4n) h | 4n: sum |g terms| | 4n+1: |g|
+// | 4n+2: beta | 4n+3: log-det | 4n+4: status
+__host__ __device__ inline int64_t vrec(int n) { return 4 * (int64_t)n + 8; }
+constexpr double kStOk = 0.0, kStZero = 1.0, kStNotPd = 2.0;
 
 template <int NT>
 __device__ __forceinline__ double block_sum(double v, double* red) {
@@ -50,214 +65,359 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return red[32];
 }
 
-template <int NT>
-__device__ __forceinline__ double2 block_sum2(double a, double b, double* red) {
-  for (int o = 16; o; o >>= 1) {
-    a += __shfl_xor_sync(0xffffffffu, a, o);
-    b += __shfl_xor_sync(0xffffffffu, b, o);
-  }
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+// next work item of this CTA (uniform across the CTA)
+__device__ __forceinline__ int64_t next_item(int* counter, int64_t* s_item) {
   __syncthreads();
-  if (l == 0) {
-    red[w] = a;
-    red[16 + w] = b;
-  }
+  if (threadIdx.x == 0) *s_item = (int64_t)atomicAdd(counter, 1);
   __syncthreads();
-  if (threadIdx.x < 32) {
-    double ta = threadIdx.x < NT / 32 ? red[threadIdx.x] : 0.0;
-    double tb = threadIdx.x < NT / 32 ? red[16 + threadIdx.x] : 0.0;
-    for (int o = 16; o; o >>= 1) {
-      ta += __shfl_xor_sync(0xffffffffu, ta, o);
-      tb += __shfl_xor_sync(0xffffffffu, tb, o);
-    }
-    if (threadIdx.x == 0) {
-      red[32] = ta;
-      red[33] = tb;
-    }
-  }
-  __syncthreads();
-  return make_double2(red[32], red[33]);
+  return *s_item;
 }
 
-struct Layout {
-  size_t x, e, v, h, tv, red, g, sg, c, u, w, pw, Hr, Mr, Ld, total;
-};
+// position of `item` in the permuted polynomial list: prefix[] is over the
+// polynomials in work order
+__device__ __forceinline__ int find_poly(const int64_t* __restrict__ prefix, int n_desc, int64_t item) {
+  int lo = 0, hi = n_desc;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (prefix[mid] <= item) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
 
-// Shared-memory layout for one point of an n-variable polynomial with power
-// tables up to exponent E1-1.  `mats` false: Hr/Mr/Ld live in global memory.
-template <typename R, int NW>
-__host__ __device__ Layout exact_layout(int n, int E1, bool mats) {
-  Layout L{};
+// x_v^k for k < E1, one row per variable
+template <typename R, int NT>
+__device__ __forceinline__ void power_table(const double* __restrict__ X, int n, int E1, R* pw) {
+  for (int i = threadIdx.x; i < n; i += NT) {
+    const R x = R(X[i]);
+    R cur = R(1);
+    pw[i * E1] = cur;
+    for (int k = 1; k < E1; ++k) {
+      cur = cur * x;
+      pw[i * E1 + k] = cur;
+    }
+  }
+}
+
+// LDL^T factorisation of the symmetric positive definite leading m x m block
+// in FP64, right-looking, by the whole CTA with one barrier per column.
+// col(j)[i] addresses element (i, j), i >= j (consecutive i are consecutive
+// doubles).  On return col(j)[i] = l_ij (i > j), dv[k] = d_k, di[k] = 1/d_k.
+// Column k+1 is updated and pivoted by warp 0 while the other warps apply
+// column k to columns k+2.. (a_ij -= l_ik a_jk, with the unscaled a_jk kept
+// in uc), so a step needs no second barrier.  A pivot that is not positive
+// and finite sets *flag (the block is not positive definite); the caller
+// reads it after the final barrier.
+template <int NT, typename Col>
+__device__ __forceinline__ void ldlt_block(int m, Col col, double* __restrict__ uc, double* __restrict__ dv,
+                                           double* __restrict__ di, int* flag) {
+  static_assert(NT >= 64, "one pivot warp plus at least one update warp");
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (m == 0) return;
+  auto pivot = [&](int c) {  // warp 0
+    double* cc = col(c);
+    const double d = cc[c];
+    if (!(d > 0.0) || !isfinite(d)) {
+      if (lane == 0) *flag = 1;
+      return;
+    }
+    const double inv = 1.0 / d;
+    if (lane == 0) {
+      dv[c] = d;
+      di[c] = inv;
+    }
+    double* u = uc + (c & 1) * m;
+    for (int i = c + 1 + lane; i < m; i += 32) {
+      const double a = cc[i];
+      u[i] = a;
+      cc[i] = a * inv;
+    }
+  };
+  if (wid == 0) pivot(0);
+  __syncthreads();
+  for (int k = 0; k + 1 < m; ++k) {
+    if (*flag) return;
+    const double* ck = col(k);
+    const double* uk = uc + (k & 1) * m;
+    if (wid == 0) {
+      double* c1 = col(k + 1);
+      const double u1 = uk[k + 1];
+      for (int i = k + 1 + lane; i < m; i += 32) c1[i] -= ck[i] * u1;
+      __syncwarp();
+      pivot(k + 1);
+    } else {
+      // columns k+2..m-1 of the trailing triangle, enumerated column-major
+      // over the threads of warps 1..NW-1
+      constexpr int S = NT - 32;
+      int len = m - k - 2, c = 0, r = tid - 32;
+      while (len > 0 && r >= len) {
+        r -= len;
+        ++c;
+        --len;
+      }
+      while (len > 0) {
+        const int j = k + 2 + c;
+        col(j)[j + r] -= ck[j + r] * uk[j];
+        r += S;
+        while (len > 0 && r >= len) {
+          r -= len;
+          ++c;
+          --len;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+struct Bump {
   size_t o = 0;
-  auto take = [&](size_t bytes) {
+  __host__ __device__ size_t take(size_t bytes) {
     const size_t r = o;
     o += (bytes + 15) & ~size_t(15);
     return r;
-  };
-  const size_t m = n > 1 ? n - 1 : 1;
-  L.x = take(n * 8);
-  L.e = take(n * 8);
-  L.v = take(n * 8);
-  L.h = take(n * 8);
-  L.tv = take(n * 8);
-  L.red = take(40 * 8);
-  // one replica per warp for the contended vector sums
-  L.g = take((size_t)NW * n * sizeof(R));
-  L.sg = take((size_t)NW * n * sizeof(R));
-  L.c = take((size_t)NW * n * sizeof(R));
-  L.u = take(n * sizeof(R));
-  L.w = take(n * sizeof(R));
-  L.pw = take((size_t)n * E1 * sizeof(R));
-  L.Hr = mats ? take((size_t)n * n * sizeof(R)) : 0;
-  L.Mr = mats ? take((size_t)n * n * sizeof(R)) : 0;
-  // FP32 form: separate FP64 Cholesky storage (packed lower triangle); FP64 form factors in place in Hr
-  L.Ld = (mats && sizeof(R) == 4) ? take(m * (m + 1) / 2 * 8) : 0;
-  L.total = o;
+  }
+};
+
+// ---------------------------------------------------------------- layouts
+// `in_smem` false: the n x n matrices live in global memory instead.
+
+struct Lay1 {
+  size_t pw, g, red, H, total;
+};
+template <typename R, int NW>
+__host__ __device__ Lay1 lay_terms(int n, int E1, bool in_smem) {
+  Lay1 L{};
+  Bump b;
+  L.pw = b.take((size_t)n * E1 * sizeof(R));
+  L.g = b.take((size_t)NW * n * sizeof(R));  // one replica per warp
+  L.red = b.take(40 * 8);
+  L.H = in_smem ? b.take((size_t)n * n * sizeof(R)) : 0;
+  L.total = b.o;
   return L;
 }
 
-// global-memory bytes per CTA when the matrices do not fit in shared memory
+struct Lay2 {
+  size_t g, e, v, h, red, dv, di, uc, vr, u, w, Hr, Mr, Ld, total;
+};
 template <typename R>
-__host__ __device__ size_t exact_gmem(int n) {
+__host__ __device__ Lay2 lay_frame(int n, bool in_smem) {
+  Lay2 L{};
+  Bump b;
+  const size_t m = n > 1 ? n - 1 : 1;
+  L.g = b.take(n * 8);
+  L.e = b.take(n * 8);
+  L.v = b.take(n * 8);
+  L.h = b.take(n * 8);
+  L.red = b.take(40 * 8);
+  L.dv = b.take(m * 8);      // LDL^T pivots d_k
+  L.di = b.take(m * 8);      // 1 / d_k
+  L.uc = b.take(2 * m * 8);  // unscaled pivot columns (two buffers)
+  L.vr = b.take(n * sizeof(R));
+  L.u = b.take(n * sizeof(R));
+  L.w = b.take(n * sizeof(R));
+  L.Hr = in_smem ? b.take((size_t)n * n * sizeof(R)) : 0;
+  L.Mr = in_smem ? b.take((size_t)n * n * sizeof(R)) : 0;
+  // FP32 form: separate FP64 factor storage (packed lower triangle,
+  // column-major); the FP64 form factors in place in Hr
+  L.Ld = (in_smem && sizeof(R) == 4) ? b.take(m * (m + 1) / 2 * 8) : 0;
+  L.total = b.o;
+  return L;
+}
+// global-memory bytes per CTA when the frame matrices do not fit in shared memory
+template <typename R>
+size_t frame_gmem(int n) {
   const size_t m = n > 1 ? n - 1 : 1;
   return 2 * (size_t)n * n * sizeof(R) + (sizeof(R) == 4 ? m * (m + 1) / 2 * 8 : 0) + 256;
 }
 
+struct Lay3 {
+  size_t pw, c, red, v, e, y, yr, W, total;
+};
+template <typename R, int NW>
+__host__ __device__ Lay3 lay_third(int n, int E1, bool in_smem) {
+  Lay3 L{};
+  Bump b;
+  L.pw = b.take((size_t)n * E1 * sizeof(R));
+  L.c = b.take((size_t)NW * n * sizeof(R));  // one replica per warp
+  L.red = b.take(40 * 8);
+  L.v = b.take(n * 8);
+  L.e = b.take(n * 8);
+  L.y = b.take(n * 8);
+  L.yr = b.take(n * sizeof(R));
+  L.W = in_smem ? b.take((size_t)n * n * sizeof(R)) : 0;
+  L.total = b.o;
+  return L;
+}
+
+template <typename R>
+struct StageArgs {
+  const ExactDesc* descs;
+  int n_desc;
+  const int64_t* prefix;
+  const int* order;
+  int64_t total;
+  int* counter;
+  R* mats_h;  // per point n x n: H (stage 1 -> 2)
+  R* mats_w;  // per point n x n: W (stage 2 -> 3)
+  double* vecs;
+  double r;
+  int assume_nonzero_x;
+  unsigned char* gws;
+  size_t gws_stride;
+};
+
+__device__ __forceinline__ void write_failed(const ExactDesc& pd, int64_t p, int n, double gn, int flag) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    pd.D[p * n + i] = nan("");
+    if (pd.Dunit) pd.Dunit[p * n + i] = nan("");
+  }
+  if (threadIdx.x == 0 && pd.info) {
+    polylab_an_info in{gn, nan(""), flag, n, n - 1, 0};
+    pd.info[p] = in;
+  }
+}
+
 }  // namespace
 
+// ------------------------------------------------------------------ stage 1
 template <typename R, int NT>
-__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 512 / NT : 1) affine_exact_kernel(const ExactDesc* __restrict__ descs, int n_desc,
-                                                          const int64_t* __restrict__ prefix,
-                                                          const int* __restrict__ order, int64_t total,
-                                                          int* __restrict__ counter, double r,
-                                                          int assume_nonzero_x, unsigned char* __restrict__ gws,
-                                                          size_t gws_stride) {
+__global__ void __launch_bounds__(NT) exact_terms_kernel(StageArgs<R> a) {
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ int64_t s_item;
-  __shared__ int s_flag;
-  __shared__ double s_logdet;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  constexpr bool kF64 = sizeof(R) == 8;
   constexpr int NW = NT / 32;
-
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   while (true) {
-    __syncthreads();
-    if (tid == 0) s_item = (int64_t)atomicAdd(counter, 1);
-    __syncthreads();
-    const int64_t item = s_item;
-    if (item >= total) break;
-    // locate the polynomial: prefix[] is over polynomials in `order`
-    int lo = 0, hi = n_desc;
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (prefix[mid] <= item) lo = mid;
-      else hi = mid;
-    }
-    const ExactDesc& pd = descs[order[lo]];
-    const int64_t p = item - prefix[lo];
-    const int n = pd.n, m = n - 1, nn = n * n, E1 = pd.E + 1;
-    const Layout L = exact_layout<R, NW>(n, E1, pd.mats_in_smem);
-    double* xs = (double*)(sm + L.x);
-    double* e = (double*)(sm + L.e);
-    double* v = (double*)(sm + L.v);
-    double* h = (double*)(sm + L.h);
-    double* tv = (double*)(sm + L.tv);
-    double* red = (double*)(sm + L.red);
-    R* g = (R*)(sm + L.g);
-    R* sg = (R*)(sm + L.sg);
-    R* c = (R*)(sm + L.c);
-    R* u = (R*)(sm + L.u);
-    R* w = (R*)(sm + L.w);
+    const int64_t item = next_item(a.counter, &s_item);
+    if (item >= a.total) break;
+    const int lo = find_poly(a.prefix, a.n_desc, item);
+    const ExactDesc& pd = a.descs[a.order[lo]];
+    const int64_t p = item - a.prefix[lo];
+    const int n = pd.n, nn = n * n, E1 = pd.E + 1;
+    const Lay1 L = lay_terms<R, NW>(n, E1, pd.h_in_smem);
     R* pw = (R*)(sm + L.pw);
-    unsigned char* gb = gws + (size_t)blockIdx.x * gws_stride;
-    R* Hr = pd.mats_in_smem ? (R*)(sm + L.Hr) : (R*)gb;
-    R* Mr = pd.mats_in_smem ? (R*)(sm + L.Mr) : (R*)(gb + (size_t)nn * sizeof(R));
-    // FP64 Cholesky storage: in place in Hr (row stride n) for the FP64 form,
-    // a packed lower triangle for the FP32 form
-    double* Ld = kF64 ? (double*)Hr
-                      : (pd.mats_in_smem ? (double*)(sm + L.Ld) : (double*)(gb + 2 * (size_t)nn * sizeof(R)));
-    auto LI = [n](int i, int j) { return kF64 ? i * n + j : i * (i + 1) / 2 + j; };
-    const double* X = pd.X + p * n;
-
-    // ---------------------------------------------------------- phase 1
-    for (int i = tid; i < NW * n; i += NT) {
-      g[i] = R(0);
-      sg[i] = R(0);
-      c[i] = R(0);
-    }
-    for (int i = tid; i < n; i += NT) {
-      const double x = X[i];
-      xs[i] = x;
-      R cur = R(1);
-      pw[i * E1] = cur;
-      for (int k = 1; k < E1; ++k) {
-        cur = cur * R(x);
-        pw[i * E1 + k] = cur;
-      }
-    }
+    R* g = (R*)(sm + L.g);
+    double* red = (double*)(sm + L.red);
+    R* Hg = a.mats_h + pd.mat_off + p * nn;
+    R* Hr = pd.h_in_smem ? (R*)(sm + L.H) : Hg;
+    for (int i = tid; i < NW * n; i += NT) g[i] = R(0);
+    power_table<R, NT>(pd.X + p * n, n, E1, pw);
     for (int i = tid; i < nn; i += NT) Hr[i] = R(0);
-    if (tid == 0) {
-      s_flag = 0;
-      s_logdet = 0.0;
-    }
     __syncthreads();
     R gabs = R(0);  // this thread's share of sum |gradient contributions|
     {
       R* gw = g + wid * n;
-      for (int64_t t = tid; t < pd.m; t += NT) {
-        const TermRegs tr = load_term(pd.terms, t);
-        term_derivs<R, 2>(tr, pw, E1, [&](int kind, int i, int j, R val) {
-          if (kind == 1) {
-            atomicAdd(&gw[i], val);
-            gabs += fabs(val);
-          } else if (kind == 2) {
-            atomicAdd(&Hr[i * n + j], val);
-          }
-        });
-      }
+      auto emit = [&](int kind, int i, int j, R val) {
+        if (kind == 1) {
+          atomicAdd(&gw[i], val);
+          gabs += fabs(val);
+        } else if (kind == 2) {
+          atomicAdd(&Hr[i * n + j], val);
+        }
+      };
+      // one loop per support-size group: inside each loop the support size
+      // is a compile-time constant and the warp never branches on it
+      for_support<kMaxSupport>([&](auto kc) {
+        constexpr int K = decltype(kc)::value;
+        for (int64_t t = pd.koff[K] + tid; t < pd.koff[K + 1]; t += NT) {
+          const TermRegs tr = load_term(pd.terms, t);
+          term_derivs_group<R, 2, K>(tr, pw, E1, emit);
+        }
+      });
     }
     __syncthreads();
-    for (int i = tid; i < n; i += NT) {  // fold the warp replicas into replica 0
-      R a = g[i];
-      for (int q = 1; q < NW; ++q) a += g[q * n + i];
-      g[i] = a;
+    double* rec = a.vecs + pd.vec_off + p * vrec(n);
+    for (int i = tid; i < n; i += NT) {
+      R s = g[i];
+      for (int q = 1; q < NW; ++q) s += g[q * n + i];
+      rec[i] = (double)s;
     }
-    for (int idx = tid; idx < nn; idx += NT) {  // mirror the upper triangle
-      const int i = idx / n, j = idx - i * n;
-      if (i > j) Hr[idx] = Hr[j * n + i];
-    }
-    // ---------------------------------------------------------- phase 2
+    const double ga = block_sum<NT>((double)gabs, red);
+    if (tid == 0) rec[4 * n] = ga;
+    // full symmetric H from the upper triangle the sweep filled
+    for (int i = wid; i < n; i += NW)
+      for (int j = lane; j < n; j += 32) {
+        if (pd.h_in_smem) Hg[i * n + j] = i <= j ? Hr[i * n + j] : Hr[j * n + i];
+        else if (i > j) Hg[i * n + j] = Hg[j * n + i];
+      }
+  }
+}
+
+// ------------------------------------------------------------------ stage 2
+template <typename R, int NT>
+__global__ void __launch_bounds__(NT) exact_frame_kernel(StageArgs<R> a) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  __shared__ int64_t s_item;
+  __shared__ int s_flag;
+  constexpr bool kF64 = sizeof(R) == 8;
+  constexpr int NW = NT / 32;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  while (true) {
+    const int64_t item = next_item(a.counter, &s_item);
+    if (item >= a.total) break;
+    const int lo = find_poly(a.prefix, a.n_desc, item);
+    const ExactDesc& pd = a.descs[a.order[lo]];
+    const int64_t p = item - a.prefix[lo];
+    const int n = pd.n, m = n - 1, nn = n * n;
+    const Lay2 L = lay_frame<R>(n, pd.mats_in_smem);
+    double* gd = (double*)(sm + L.g);
+    double* e = (double*)(sm + L.e);
+    double* v = (double*)(sm + L.v);
+    double* h = (double*)(sm + L.h);
+    double* red = (double*)(sm + L.red);
+    double* dv = (double*)(sm + L.dv);
+    double* di = (double*)(sm + L.di);
+    double* uc = (double*)(sm + L.uc);
+    R* vr = (R*)(sm + L.vr);
+    R* u = (R*)(sm + L.u);
+    R* w = (R*)(sm + L.w);
+    unsigned char* gb = a.gws + (size_t)blockIdx.x * a.gws_stride;
+    R* Hr = pd.mats_in_smem ? (R*)(sm + L.Hr) : (R*)gb;
+    R* Mr = pd.mats_in_smem ? (R*)(sm + L.Mr) : (R*)(gb + (size_t)nn * sizeof(R));
+    // FP64 factor storage, element (i, j) of the leading block at col(j)[i]:
+    // in place in Hr (col(j) = row j of the symmetric Hr) for the FP64 form, a
+    // packed column-major lower triangle for the FP32 form
+    double* Ld = kF64 ? (double*)Hr
+                      : (pd.mats_in_smem ? (double*)(sm + L.Ld) : (double*)(gb + 2 * (size_t)nn * sizeof(R)));
+    auto col = [Ld, n, m](int j) -> double* {
+      return kF64 ? Ld + (size_t)j * n : Ld + ((size_t)j * m - (size_t)j * (j - 1) / 2 - j);
+    };
+    const R* Hg = a.mats_h + pd.mat_off + p * nn;
+    R* Wg = a.mats_w + pd.mat_off + p * nn;
+    double* rec = a.vecs + pd.vec_off + p * vrec(n);
+    for (int i = wid; i < n; i += NW)
+      for (int j = lane; j < n; j += 32) Hr[i * n + j] = Hg[i * n + j];
     double gg = 0.0;
-    for (int i = tid; i < n; i += NT) gg += (double)g[i] * (double)g[i];
-    const double2 sums = block_sum2<NT>(gg, (double)gabs, red);
-    const double gn = sqrt(sums.x);
+    for (int i = tid; i < n; i += NT) {
+      const double gi = rec[i];
+      gd[i] = gi;
+      gg += gi * gi;
+    }
+    if (tid == 0) s_flag = 0;
+    const double gn = sqrt(block_sum<NT>(gg, red));
     bool zero = !(gn > 0.0) || !isfinite(gn);
     // relative test at the resolution of the form: 1e-14 (FP64), 1e-6 (FP32 sums)
-    if (!assume_nonzero_x && gn <= (kF64 ? 1e-14 : 1e-6) * sums.y) zero = true;
+    if (!a.assume_nonzero_x && gn <= (kF64 ? 1e-14 : 1e-6) * rec[4 * n]) zero = true;
     if (zero) {
-      if (tid == 0 && pd.info) {
-        polylab_an_info in{gn, nan(""), POLYLAB_FLAG_ZERO_GRAD, n, n - 1, 0};
-        pd.info[p] = in;
-      }
-      for (int i = tid; i < n; i += NT) {
-        pd.D[p * n + i] = nan("");
-        if (pd.Dunit) pd.Dunit[p * n + i] = nan("");
+      write_failed(pd, p, n, gn, POLYLAB_FLAG_ZERO_GRAD);
+      if (tid == 0) {
+        rec[4 * n + 1] = gn;
+        rec[4 * n + 4] = kStZero;
       }
       continue;
     }
-    const double en = (double)g[n - 1] / gn;
+    const double en = gd[n - 1] / gn;
     const double sgn = en >= 0.0 ? 1.0 : -1.0;
     const double beta = 1.0 / (1.0 + sgn * en);  // 2 / v^T v with v^T v = 2 (1 + s e_n)
-    R* vr = sg;  // v in the form's precision (sg is free): no conversions inside n^2 loops
     for (int i = tid; i < n; i += NT) {
-      e[i] = (double)g[i] / gn;
+      e[i] = gd[i] / gn;
       v[i] = e[i] + (i == n - 1 ? sgn : 0.0);
       vr[i] = R(v[i]);
     }
     __syncthreads();
-    for (int i = tid; i < n; i += NT) {  // u = H v
+    for (int i = tid; i < n; i += NT) {  // u = H v (H symmetric: column access, conflict-free)
       R acc = R(0);
-      for (int j = 0; j < n; ++j) acc += Hr[i * n + j] * vr[j];
+      for (int j = 0; j < n; ++j) acc += Hr[j * n + i] * vr[j];
       u[i] = acc;
     }
     __syncthreads();
@@ -266,94 +426,66 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 512 / NT : 1) affine_exac
     const double gamma = block_sum<NT>(part, red);
     for (int i = tid; i < n; i += NT) w[i] = R(beta * (double)u[i] - 0.5 * beta * beta * gamma * v[i]);
     __syncthreads();
-    for (int idx = tid; idx < nn; idx += NT) {  // P H P = H - v w^T - w v^T
-      const int i = idx / n, j = idx - i * n;
-      Hr[idx] -= vr[i] * w[j] + w[i] * vr[j];
-    }
+    for (int i = wid; i < n; i += NW)  // P H P = H - v w^T - w v^T
+      for (int j = lane; j < n; j += 32) Hr[i * n + j] -= vr[i] * w[j] + w[i] * vr[j];
     __syncthreads();
-    for (int i = tid; i < m; i += NT) h[i] = -sgn * (double)Hr[i * n + (n - 1)];
+    for (int i = tid; i < n; i += NT) h[i] = i < m ? -sgn * (double)Hr[i * n + (n - 1)] : 0.0;
     if constexpr (kF64) {
-      for (int i = tid; i < m; i += NT) Hr[i * n + i] += r;
+      for (int i = tid; i < m; i += NT) Hr[i * n + i] += a.r;
     } else {
-      for (int idx = tid; idx < m * m; idx += NT) {
-        const int i = idx / m, j = idx - i * m;
-        if (j <= i) Ld[LI(i, j)] = (double)Hr[i * n + j] + (i == j ? r : 0.0);
-      }
+      for (int j = wid; j < m; j += NW)
+        for (int i = j + lane; i < m; i += 32) col(j)[i] = (double)Hr[j * n + i] + (i == j ? a.r : 0.0);
     }
     __syncthreads();
-    // Cholesky of the leading m x m block (lower, in place), one warp
-    if (wid == 0) {
-      double logdet = 0.0;
-      bool bad = false;
-      for (int k = 0; k < m; ++k) {
-        double lk = 0.0, inv = 0.0;
-        if (lane == 0) {
-          const double d = Ld[LI(k, k)];
-          bad = !(d > 0.0) || !isfinite(d);
-          if (!bad) {
-            lk = sqrt(d);
-            inv = 1.0 / lk;
-            Ld[LI(k, k)] = lk;
-            logdet += 2.0 * log(lk);
-          }
-        }
-        bad = __shfl_sync(0xffffffffu, (int)bad, 0) != 0;
-        if (bad) break;
-        inv = __shfl_sync(0xffffffffu, inv, 0);
-        for (int i = k + 1 + lane; i < m; i += 32) Ld[LI(i, k)] *= inv;
-        __syncwarp();
-        for (int i = k + 1 + lane; i < m; i += 32) {
-          const double lik = Ld[LI(i, k)];
-          double* row = Ld + LI(i, 0);
-#pragma unroll 4
-          for (int j = k + 1; j <= i; ++j) row[j] -= lik * Ld[LI(j, k)];
-        }
-        __syncwarp();
-      }
-      if (lane == 0) {
-        s_flag = bad ? 1 : 0;
-        s_logdet = logdet;
-      }
-    }
+    ldlt_block<NT>(m, col, uc, dv, di, &s_flag);
     __syncthreads();
     if (s_flag) {
-      if (tid == 0 && pd.info) {
-        polylab_an_info in{gn, nan(""), POLYLAB_FLAG_NOT_PD, n, n - 1, 0};
-        pd.info[p] = in;
-      }
-      for (int i = tid; i < n; i += NT) {
-        pd.D[p * n + i] = nan("");
-        if (pd.Dunit) pd.Dunit[p * n + i] = nan("");
+      write_failed(pd, p, n, gn, POLYLAB_FLAG_NOT_PD);
+      if (tid == 0) {
+        rec[4 * n + 1] = gn;
+        rec[4 * n + 4] = kStNotPd;
       }
       continue;
     }
-    // L in R precision: the FP32 form converts the factor once (into Hr, free now)
-    const R* Lr;
-    const int lr = n;
-    if constexpr (kF64) {
-      Lr = (const R*)Ld;
-    } else {
-      for (int idx = tid; idx < m * m; idx += NT) {
-        const int i = idx / m, j = idx - i * m;
-        if (j <= i) Hr[i * n + j] = (R)Ld[LI(i, j)];
+    double lsum = 0.0;
+    for (int i = tid; i < m; i += NT) lsum += log(dv[i]);
+    const double logdet = block_sum<NT>(lsum, red);
+    // Lt(i, j) = Hr[j*n + i] = l_ij (i > j) in the form's precision; sq = d^{-1/2}
+    R* sq = w;
+    for (int i = tid; i < m; i += NT) sq[i] = R(sqrt(di[i]));
+    if constexpr (!kF64) {
+      for (int j = wid; j < m; j += NW)
+        for (int i = j + 1 + lane; i < m; i += 32) Hr[j * n + i] = (R)col(j)[i];
+    }
+    // X = L^{-1} (unit lower), stored transposed: Mr[j*n + i] = X_ij, i >= j
+    for (int j = wid; j < m; j += NW)
+      for (int i = j + lane; i < m; i += 32) Mr[j * n + i] = i == j ? R(1) : R(0);
+    __syncthreads();
+    // right-looking: after step k row k of X is final; X_ij -= l_ik X_kj for
+    // j <= k < i, the (m-k-1) x (k+1) rectangle enumerated over the CTA
+    for (int k = 0; k + 1 < m; ++k) {
+      const int rows = m - k - 1, total = rows * (k + 1);
+      const float rinv = 1.0f / (float)rows;
+      for (int q = tid; q < total; q += NT) {
+        int j = (int)((float)q * rinv);
+        int i0 = q - j * rows;
+        if (i0 < 0) {
+          --j;
+          i0 += rows;
+        } else if (i0 >= rows) {
+          ++j;
+          i0 -= rows;
+        }
+        const int i = k + 1 + i0;
+        Mr[j * n + i] -= Hr[k * n + i] * Mr[j * n + k];
       }
       __syncthreads();
-      Lr = Hr;
     }
-    // L^{-1} by forward substitution, one thread per column; stored transposed:
-    // Mr[j*n + i] = Linv[i][j] for i >= j.  Reciprocal diagonal first (w is free).
-    for (int i = tid; i < m; i += NT) w[i] = R(1) / Lr[i * lr + i];
+    // X' = D^{-1/2} X (row i scaled by d_i^{-1/2}), so M = X'^T X'
+    for (int j = wid; j < m; j += NW)
+      for (int i = j + lane; i < m; i += 32) Mr[j * n + i] *= sq[i];
     __syncthreads();
-    for (int j = tid; j < m; j += NT) {
-      Mr[j * n + j] = w[j];
-      for (int i = j + 1; i < m; ++i) {
-        R acc = R(0);
-        for (int k = j; k < i; ++k) acc += Lr[i * lr + k] * Mr[j * n + k];
-        Mr[j * n + i] = -acc * w[i];
-      }
-    }
-    __syncthreads();
-    // M = L^{-T} L^{-1}, upper triangle into Hr (L no longer needed)
+    // M = H_T^{-1} = X'^T X', upper triangle into Hr (L no longer needed)
     for (int idx = tid; idx < m * m; idx += NT) {
       const int i = idx / m, j = idx - i * m;
       if (j < i) continue;
@@ -362,14 +494,13 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 512 / NT : 1) affine_exac
       Hr[i * n + j] = acc;
     }
     __syncthreads();
-    for (int idx = tid; idx < nn; idx += NT) {  // Mr <- [M 0; 0 0], full symmetric
-      const int i = idx / n, j = idx - i * n;
-      Mr[idx] = (i == n - 1 || j == n - 1) ? R(0) : (i <= j ? Hr[i * n + j] : Hr[j * n + i]);
-    }
+    for (int i = wid; i < n; i += NW)  // Mr <- [M 0; 0 0], full symmetric
+      for (int j = lane; j < n; j += 32)
+        Mr[i * n + j] = (i == n - 1 || j == n - 1) ? R(0) : (i <= j ? Hr[i * n + j] : Hr[j * n + i]);
     __syncthreads();
     for (int i = tid; i < n; i += NT) {  // u = [M 0; 0 0] v
       R acc = R(0);
-      for (int j = 0; j < n; ++j) acc += Mr[i * n + j] * vr[j];
+      for (int j = 0; j < n; ++j) acc += Mr[j * n + i] * vr[j];
       u[i] = acc;
     }
     __syncthreads();
@@ -378,65 +509,112 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 512 / NT : 1) affine_exac
     const double gam2 = block_sum<NT>(part, red);
     for (int i = tid; i < n; i += NT) w[i] = R(beta * (double)u[i] - 0.5 * beta * beta * gam2 * v[i]);
     __syncthreads();
-    for (int idx = tid; idx < nn; idx += NT) {  // Hr <- W
-      const int i = idx / n, j = idx - i * n;
-      Hr[idx] = Mr[idx] - (vr[i] * w[j] + w[i] * vr[j]);
+    for (int i = wid; i < n; i += NW)  // W = P [M 0; 0 0] P
+      for (int j = lane; j < n; j += 32) Wg[i * n + j] = Mr[i * n + j] - (vr[i] * w[j] + w[i] * vr[j]);
+    for (int i = tid; i < n; i += NT) {
+      rec[n + i] = v[i];
+      rec[2 * n + i] = e[i];
+      rec[3 * n + i] = h[i];
+    }
+    if (tid == 0) {
+      rec[4 * n + 1] = gn;
+      rec[4 * n + 2] = beta;
+      rec[4 * n + 3] = logdet;
+      rec[4 * n + 4] = kStOk;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ stage 3
+template <typename R, int NT>
+__global__ void __launch_bounds__(NT) exact_third_kernel(StageArgs<R> a) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  __shared__ int64_t s_item;
+  constexpr int NW = NT / 32;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  while (true) {
+    const int64_t item = next_item(a.counter, &s_item);
+    if (item >= a.total) break;
+    const int lo = find_poly(a.prefix, a.n_desc, item);
+    const ExactDesc& pd = a.descs[a.order[lo]];
+    const int64_t p = item - a.prefix[lo];
+    const int n = pd.n, m = n - 1, nn = n * n, E1 = pd.E + 1;
+    const double* rec = a.vecs + pd.vec_off + p * vrec(n);
+    if (rec[4 * n + 4] != kStOk) continue;  // flagged by stage 2 (same value for the whole CTA)
+    const Lay3 L = lay_third<R, NW>(n, E1, pd.w_in_smem);
+    R* pw = (R*)(sm + L.pw);
+    R* c = (R*)(sm + L.c);
+    double* red = (double*)(sm + L.red);
+    double* v = (double*)(sm + L.v);
+    double* e = (double*)(sm + L.e);
+    double* y = (double*)(sm + L.y);
+    R* yr = (R*)(sm + L.yr);
+    const R* Wg = a.mats_w + pd.mat_off + p * nn;
+    R* Ws = (R*)(sm + L.W);
+    const R* W = pd.w_in_smem ? Ws : Wg;
+    for (int i = tid; i < NW * n; i += NT) c[i] = R(0);
+    power_table<R, NT>(pd.X + p * n, n, E1, pw);
+    if (pd.w_in_smem)
+      for (int i = wid; i < n; i += NW)
+        for (int j = lane; j < n; j += 32) Ws[i * n + j] = Wg[i * n + j];
+    for (int i = tid; i < n; i += NT) {
+      v[i] = rec[n + i];
+      e[i] = rec[2 * n + i];
     }
     __syncthreads();
-    // ---------------------------------------------------------- phase 3
     {
       R* cw = c + wid * n;
-      for (int64_t t = tid; t < pd.m; t += NT) {
-        const TermRegs tr = load_term(pd.terms, t);
-        int deg = 0;
-#pragma unroll
-        for (int s2 = 0; s2 < kMaxSupport; ++s2) deg += tr.exp[s2];
-        if (deg < 3) continue;
-        term_third_contract<R>(tr, pw, E1, [&](int j, int k) { return Hr[j * n + k]; },
-                               [&](int l, R val) { atomicAdd(&cw[l], val); });
-      }
+      auto wget = [&](int j, int k) { return W[j * n + k]; };
+      auto emit = [&](int l, R val) { atomicAdd(&cw[l], val); };
+      // terms of degree < 3 have no third derivatives: each group starts at
+      // its first term of degree >= 3
+      for_support<kMaxSupport>([&](auto kc) {
+        constexpr int K = decltype(kc)::value;
+        if constexpr (K >= 1) {
+          for (int64_t t = pd.k3off[K] + tid; t < pd.koff[K + 1]; t += NT) {
+            const TermRegs tr = load_term(pd.terms, t);
+            term_third_group<R, K>(tr, pw, E1, wget, emit);
+          }
+        }
+      });
     }
     __syncthreads();
+    const double gn = rec[4 * n + 1], beta = rec[4 * n + 2], logdet = rec[4 * n + 3];
+    // a = (P c)[0:m] = c - beta v (v.c);  tv = [h - |g|/(n+1) a; 0]
+    double part = 0.0;
     for (int i = tid; i < n; i += NT) {
-      R a = c[i];
-      for (int q = 1; q < NW; ++q) a += c[q * n + i];
-      c[i] = a;
+      R s = c[i];
+      for (int q = 1; q < NW; ++q) s += c[q * n + i];
+      y[i] = (double)s;
+      part += v[i] * (double)s;
     }
-    __syncthreads();
-    // ---------------------------------------------------------- phase 4
-    part = 0.0;
-    for (int i = tid; i < n; i += NT) part += v[i] * (double)c[i];
-    const double vc = block_sum<NT>(part, red);  // a = (P c)[0:m] = c - beta v (v.c)
+    const double vc = block_sum<NT>(part, red);
     const double wgt = gn / (double)(n + 1);
-    for (int i = tid; i < m; i += NT) tv[i] = h[i] - wgt * ((double)c[i] - beta * v[i] * vc);
-    __syncthreads();
-    double* tau = xs;  // x is no longer needed
-    R* tvr = u;          // right-hand side in the form's precision
-    for (int i = tid; i < m; i += NT) tvr[i] = R(tv[i]);
-    __syncthreads();
-    for (int i = tid; i < n; i += NT) {
-      R acc = R(0);
-      if (i < m)
-        for (int j = 0; j < m; ++j) acc += Mr[i * n + j] * tvr[j];
-      tau[i] = (double)acc;
-    }
-    __syncthreads();
     part = 0.0;
-    for (int i = tid; i < n; i += NT) part += v[i] * tau[i];
+    for (int i = tid; i < n; i += NT) {
+      const double tv = i < m ? rec[3 * n + i] - wgt * (y[i] - beta * v[i] * vc) : 0.0;
+      y[i] = tv;
+      part += v[i] * tv;
+    }
     const double vt = block_sum<NT>(part, red);
+    for (int i = tid; i < n; i += NT) yr[i] = R(y[i] - beta * v[i] * vt);  // P tv
+    __syncthreads();
+    // nu = W P tv - e  (W symmetric: column access, conflict-free)
     double nrm = 0.0;
     for (int i = tid; i < n; i += NT) {
-      const double nu = tau[i] - beta * v[i] * vt - e[i];
-      tv[i] = nu;
+      R acc = R(0);
+      for (int j = 0; j < n; ++j) acc += W[j * n + i] * yr[j];
+      const double nu = (double)acc - e[i];
+      y[i] = nu;
       nrm += nu * nu;
     }
     const double inv = 1.0 / sqrt(block_sum<NT>(nrm, red));
     for (int i = tid; i < n; i += NT) {
-      pd.D[p * n + i] = tv[i];
-      if (pd.Dunit) pd.Dunit[p * n + i] = tv[i] * inv;
+      pd.D[p * n + i] = y[i];
+      if (pd.Dunit) pd.Dunit[p * n + i] = y[i] * inv;
     }
     if (tid == 0 && pd.info) {
-      polylab_an_info in{gn, s_logdet, 0, n, n - 1, 0};
+      polylab_an_info in{gn, logdet, 0, n, n - 1, 0};
       pd.info[p] = in;
     }
   }
@@ -448,60 +626,99 @@ namespace {
 
 constexpr size_t kSmemCap = 200 * 1024;
 
+template <typename R, int NW>
+size_t lay_bytes(int stage, int n, int E1, bool in_smem) {
+  if (stage == 0) return lay_terms<R, NW>(n, E1, in_smem).total;
+  if (stage == 1) return lay_frame<R>(n, in_smem).total;
+  return lay_third<R, NW>(n, E1, in_smem).total;
+}
+
 template <typename R>
-size_t layout_bytes(int n, int E1, bool mats, int threads) {
-  if (threads == 64) return exact_layout<R, 2>(n, E1, mats).total;
-  if (threads == 128) return exact_layout<R, 4>(n, E1, mats).total;
-  return exact_layout<R, 8>(n, E1, mats).total;
+size_t stage_bytes(int stage, int threads, int n, int E1, bool in_smem) {
+  if (threads == 64) return lay_bytes<R, 2>(stage, n, E1, in_smem);
+  if (threads == 128) return lay_bytes<R, 4>(stage, n, E1, in_smem);
+  return lay_bytes<R, 8>(stage, n, E1, in_smem);
 }
 
 }  // namespace
 
 template <typename R>
 static polylab_status prepare_exact(ExactBatch* b) {
-  size_t smem = 0, gstride = 0;
+  size_t smem[3] = {0, 0, 0}, gstride = 0;
+  int64_t mat = 0, vec = 0;
   for (auto& d : b->host_descs) {
     const int E1 = d.E + 1;
-    const size_t in = layout_bytes<R>(d.n, E1, true, b->cfg.threads);
-    d.mats_in_smem = in <= kSmemCap ? 1 : 0;
-    const size_t need = d.mats_in_smem ? in : layout_bytes<R>(d.n, E1, false, b->cfg.threads);
-    if (need > kSmemCap) return POLYLAB_ERR_UNSUPPORTED;
-    smem = std::max(smem, need);
-    if (!d.mats_in_smem) gstride = std::max(gstride, exact_gmem<R>(d.n));
+    const int tt = b->cfg.term_threads, ft = b->cfg.threads;
+    d.h_in_smem = stage_bytes<R>(0, tt, d.n, E1, true) <= kSmemCap ? 1 : 0;
+    d.mats_in_smem = stage_bytes<R>(1, ft, d.n, E1, true) <= kSmemCap ? 1 : 0;
+    d.w_in_smem = stage_bytes<R>(2, tt, d.n, E1, true) <= kSmemCap ? 1 : 0;
+    const size_t need[3] = {stage_bytes<R>(0, tt, d.n, E1, d.h_in_smem), stage_bytes<R>(1, ft, d.n, E1, d.mats_in_smem),
+                            stage_bytes<R>(2, tt, d.n, E1, d.w_in_smem)};
+    for (int st = 0; st < 3; ++st) {
+      if (need[st] > kSmemCap) return POLYLAB_ERR_UNSUPPORTED;
+      smem[st] = std::max(smem[st], need[st]);
+    }
+    if (!d.mats_in_smem) gstride = std::max(gstride, frame_gmem<R>(d.n));
+    d.mat_off = mat;
+    d.vec_off = vec;
+    mat += d.P * (int64_t)d.n * d.n;
+    vec += d.P * vrec(d.n);
   }
-  b->smem = smem;
+  for (int st = 0; st < 3; ++st) b->smem[st] = smem[st];
   b->gws_stride = gstride;
+  b->ws_mat_bytes = (size_t)mat * sizeof(R);
+  b->ws_vec_bytes = (size_t)vec * sizeof(double);
   return POLYLAB_OK;
 }
 
 template <typename R, int NT>
-static polylab_status launch_exact_t(ExactBatch* b, cudaStream_t s) {
-  auto k = affine_exact_kernel<R, NT>;
-  PL_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
+static polylab_status launch_stage_t(ExactBatch* b, int stage, cudaStream_t s) {
+  void (*k)(StageArgs<R>) = stage == 0   ? exact_terms_kernel<R, NT>
+                            : stage == 1 ? exact_frame_kernel<R, NT>
+                                         : exact_third_kernel<R, NT>;
+  const size_t smem = b->smem[stage];
+  PL_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
-  PL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NT, b->smem));
+  PL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NT, smem));
   per_sm = std::max(1, per_sm);
-  if (b->cfg.ctas_per_sm > 0) per_sm = std::min(per_sm, b->cfg.ctas_per_sm);
+  if (stage == 1 && b->cfg.ctas_per_sm > 0) per_sm = std::min(per_sm, b->cfg.ctas_per_sm);
   const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(b->total, (int64_t)num_sms() * per_sm));
-  if (b->gws_stride > 0 && (size_t)grid * b->gws_stride > b->gws_bytes) return POLYLAB_ERR_UNSUPPORTED;
-  PL_CUDA(cudaMemsetAsync(b->counter, 0, sizeof(int), s));
-  k<<<(unsigned)grid, NT, b->smem, s>>>(b->descs, b->n_desc, b->prefix, b->order, b->total, b->counter,
-                                         b->opts.regularization, b->opts.assume_nonzero_x, b->gws, b->gws_stride);
-  return launch_status("affine_exact_kernel");
+  if (stage == 1 && b->gws_stride > 0 && (size_t)grid * b->gws_stride > b->gws_bytes) return POLYLAB_ERR_UNSUPPORTED;
+  StageArgs<R> a{};
+  a.descs = b->descs;
+  a.n_desc = b->n_desc;
+  a.prefix = b->prefix;
+  a.order = b->order;
+  a.total = b->total;
+  a.counter = b->counter + stage;
+  a.mats_h = (R*)b->ws_h;
+  a.mats_w = (R*)b->ws_w;
+  a.vecs = (double*)b->ws_v;
+  a.r = b->opts.regularization;
+  a.assume_nonzero_x = b->opts.assume_nonzero_x;
+  a.gws = b->gws;
+  a.gws_stride = b->gws_stride;
+  PL_CUDA(cudaMemsetAsync(b->counter + stage, 0, sizeof(int), s));
+  k<<<(unsigned)grid, NT, smem, s>>>(a);
+  return launch_status(stage == 0 ? "exact_terms_kernel" : stage == 1 ? "exact_frame_kernel" : "exact_third_kernel");
+}
+
+template <typename R>
+static polylab_status launch_stage(ExactBatch* b, int stage, cudaStream_t s) {
+  const int nt = stage == 1 ? b->cfg.threads : b->cfg.term_threads;
+  if (nt == 64) return launch_stage_t<R, 64>(b, stage, s);
+  if (nt == 128) return launch_stage_t<R, 128>(b, stage, s);
+  return launch_stage_t<R, 256>(b, stage, s);
+}
+
+polylab_status run_exact_stage(ExactBatch* b, int stage, cudaStream_t s) {
+  if (b->total == 0) return POLYLAB_OK;
+  return b->opts.prec == POLYLAB_FP32 ? launch_stage<float>(b, stage, s) : launch_stage<double>(b, stage, s);
 }
 
 polylab_status run_exact_batch(ExactBatch* b, cudaStream_t s) {
-  if (b->total == 0) return POLYLAB_OK;
-  const bool f32 = b->opts.prec == POLYLAB_FP32;
-  const int nt = b->cfg.threads;
-  if (f32) {
-    if (nt == 64) return launch_exact_t<float, 64>(b, s);
-    if (nt == 128) return launch_exact_t<float, 128>(b, s);
-    return launch_exact_t<float, 256>(b, s);
-  }
-  if (nt == 64) return launch_exact_t<double, 64>(b, s);
-  if (nt == 128) return launch_exact_t<double, 128>(b, s);
-  return launch_exact_t<double, 256>(b, s);
+  for (int st = 0; st < 3; ++st) PL_TRY(run_exact_stage(b, st, s));
+  return POLYLAB_OK;
 }
 
 polylab_status prepare_exact_batch(ExactBatch* b) {

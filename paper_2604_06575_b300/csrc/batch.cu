@@ -48,6 +48,8 @@ polylab_status exact_batch_init(ExactBatch* b, int n, const polylab_plan* const*
     d.n = pl->n;
     d.E = std::max(1, pl->max_exp);
     d.max_support = pl->max_support;
+    for (int k = 0; k < kMaxSupport + 2; ++k) d.koff[k] = pl->koff[k];
+    for (int k = 0; k < kMaxSupport + 1; ++k) d.k3off[k] = pl->k3off[k];
     d.mats_in_smem = 1;
     d.X = X[i];
     d.P = P[i];
@@ -56,11 +58,15 @@ polylab_status exact_batch_init(ExactBatch* b, int n, const polylab_plan* const*
     d.info = info ? info[i] : nullptr;
   }
   if (b->cfg.threads == 0) b->cfg.threads = default_threads(b);
+  if (b->cfg.term_threads == 0) b->cfg.term_threads = 128;
   PL_TRY(prepare_exact_batch(b));
   PL_CUDA(cudaMallocAsync(&b->descs, std::max(n, 1) * sizeof(ExactDesc), s));
   PL_CUDA(cudaMallocAsync(&b->order, std::max(n, 1) * sizeof(int), s));
   PL_CUDA(cudaMallocAsync(&b->prefix, (n + 1) * sizeof(int64_t), s));
-  PL_CUDA(cudaMallocAsync(&b->counter, sizeof(int), s));
+  PL_CUDA(cudaMallocAsync(&b->counter, 3 * sizeof(int), s));
+  PL_CUDA(cudaMallocAsync(&b->ws_h, std::max<size_t>(b->ws_mat_bytes, 16), s));
+  PL_CUDA(cudaMallocAsync(&b->ws_w, std::max<size_t>(b->ws_mat_bytes, 16), s));
+  PL_CUDA(cudaMallocAsync(&b->ws_v, std::max<size_t>(b->ws_vec_bytes, 16), s));
   PL_CUDA(cudaMemcpyAsync(b->descs, b->host_descs.data(), n * sizeof(ExactDesc), cudaMemcpyHostToDevice, s));
   PL_TRY(exact_batch_upload_order(b, s));
   if (b->gws_stride > 0) {
@@ -93,6 +99,10 @@ void exact_batch_release(ExactBatch* b, cudaStream_t s) {
   if (b->prefix) cudaFreeAsync(b->prefix, s);
   if (b->counter) cudaFreeAsync(b->counter, s);
   if (b->gws) cudaFreeAsync(b->gws, s);
+  if (b->ws_h) cudaFreeAsync(b->ws_h, s);
+  if (b->ws_w) cudaFreeAsync(b->ws_w, s);
+  if (b->ws_v) cudaFreeAsync(b->ws_v, s);
+  b->ws_h = b->ws_w = b->ws_v = nullptr;
   for (polylab_plan* p : b->owned_plans) polylab_plan_destroy(p, (polylab_stream)s);
   b->descs = nullptr;
   b->order = nullptr;
@@ -150,23 +160,31 @@ polylab_status polylab_batch_run(polylab_batch* b, polylab_stream stream) {
   return run_exact_batch(&b->b, (cudaStream_t)stream);
 }
 
+polylab_status polylab_batch_run_stage(polylab_batch* b, int32_t stage, polylab_stream stream) {
+  if (!b || stage < 0 || stage > 2) return POLYLAB_ERR_INVALID_ARG;
+  return run_exact_stage(&b->b, stage, (cudaStream_t)stream);
+}
+
 polylab_status polylab_batch_get_config(const polylab_batch* b, polylab_batch_config* cfg) {
   if (!b || !cfg) return POLYLAB_ERR_INVALID_ARG;
   cfg->threads = b->b.cfg.threads;
   cfg->ctas_per_sm = b->b.cfg.ctas_per_sm;
   cfg->order = b->b.cfg.order;
+  cfg->term_threads = b->b.cfg.term_threads;
   return POLYLAB_OK;
 }
 
 polylab_status polylab_batch_set_config(polylab_batch* b, const polylab_batch_config* cfg, polylab_stream stream) {
   if (!b || !cfg) return POLYLAB_ERR_INVALID_ARG;
-  if (cfg->threads != 64 && cfg->threads != 128 && cfg->threads != 256) return POLYLAB_ERR_INVALID_ARG;
+  auto ok_threads = [](int t) { return t == 64 || t == 128 || t == 256; };
+  if (!ok_threads(cfg->threads) || !ok_threads(cfg->term_threads)) return POLYLAB_ERR_INVALID_ARG;
   if (cfg->ctas_per_sm < 0 || cfg->ctas_per_sm > 32 || (cfg->order != 0 && cfg->order != 1))
     return POLYLAB_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   const bool reorder = cfg->order != b->b.cfg.order;
-  const bool relayout = cfg->threads != b->b.cfg.threads;
+  const bool relayout = cfg->threads != b->b.cfg.threads || cfg->term_threads != b->b.cfg.term_threads;
   b->b.cfg.threads = cfg->threads;
+  b->b.cfg.term_threads = cfg->term_threads;
   b->b.cfg.ctas_per_sm = cfg->ctas_per_sm;
   b->b.cfg.order = cfg->order;
   if (relayout) PL_TRY(exact_batch_relayout(&b->b, s));
@@ -178,49 +196,94 @@ polylab_status polylab_batch_autotune(polylab_batch* b, int32_t reps, polylab_st
                                       polylab_batch_config* chosen, float* best_ms) {
   if (!b || reps < 1) return POLYLAB_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
-  const polylab_batch_config start{b->b.cfg.threads, b->b.cfg.ctas_per_sm, b->b.cfg.order};
-  polylab_batch_config best = start;
-  float best_t = 1e30f;
+  ExactBatch* eb = &b->b;
+  polylab_batch_config cur{eb->cfg.threads, eb->cfg.ctas_per_sm, eb->cfg.order, eb->cfg.term_threads};
   cudaEvent_t e0, e1;
   PL_CUDA(cudaEventCreate(&e0));
   PL_CUDA(cudaEventCreate(&e1));
-  polylab_status st = POLYLAB_OK;
-  for (int order : {1, 0}) {
+  // mean time of `reps` runs of stages [s0, s1] after one warm-up run
+  auto time_stages = [&](int s0, int s1, float* ms_out) -> polylab_status {
+    for (int r = 0; r <= reps; ++r) {
+      if (r == 1) cudaEventRecord(e0, s);
+      for (int st = s0; st <= s1; ++st) PL_TRY(run_exact_stage(eb, st, s));
+    }
+    cudaEventRecord(e1, s);
+    PL_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    *ms_out = ms / reps;
+    return POLYLAB_OK;
+  };
+  // try `c` on stages [s0, s1]; configurations a stage cannot run are skipped
+  auto trial = [&](const polylab_batch_config& c, int s0, int s1, float* ms) -> polylab_status {
+    *ms = 1e30f;
+    polylab_status st = polylab_batch_set_config(b, &c, stream);
+    if (st == POLYLAB_OK) st = time_stages(s0, s1, ms);
+    if (st == POLYLAB_ERR_UNSUPPORTED) {
+      *ms = 1e30f;
+      return POLYLAB_OK;
+    }
+    return st;
+  };
+  polylab_status st = polylab_batch_set_config(b, &cur, stream);
+  if (st == POLYLAB_OK) st = run_exact_batch(eb, s);  // every stage's inputs exist from here on
+  float best_t = 1e30f, t = 0.f;
+  // 1. CTA size of the two term sweeps
+  if (st == POLYLAB_OK) {
+    polylab_batch_config best = cur;
+    for (int tt : {64, 128, 256}) {
+      polylab_batch_config c = cur;
+      c.term_threads = tt;
+      if ((st = trial(c, 0, 0, &t)) != POLYLAB_OK) break;
+      float t3 = 0.f;
+      if ((st = time_stages(2, 2, &t3)) != POLYLAB_OK) break;
+      if (t + t3 < best_t) {
+        best_t = t + t3;
+        best = c;
+      }
+    }
+    cur = best;
+  }
+  // 2. CTA size and residency cap of the frame stage
+  if (st == POLYLAB_OK) {
+    polylab_batch_config best = cur;
+    best_t = 1e30f;
     for (int threads : {64, 128, 256}) {
       for (int cap : {0, 2, 4}) {
-        const polylab_batch_config c{threads, cap, order};
-        st = polylab_batch_set_config(b, &c, stream);
-        if (st == POLYLAB_OK) st = run_exact_batch(&b->b, s);  // warm-up
-        if (st == POLYLAB_ERR_UNSUPPORTED) {
-          st = POLYLAB_OK;
-          continue;
-        }
-        if (st != POLYLAB_OK) break;
-        float t = 0.f;
-        for (int r = 0; r < reps && st == POLYLAB_OK; ++r) {
-          cudaEventRecord(e0, s);
-          st = run_exact_batch(&b->b, s);
-          cudaEventRecord(e1, s);
-          cudaEventSynchronize(e1);
-          float ms = 0.f;
-          cudaEventElapsedTime(&ms, e0, e1);
-          t += ms;
-        }
-        t /= reps;
-        if (st == POLYLAB_OK && t < best_t) {
+        polylab_batch_config c = cur;
+        c.threads = threads;
+        c.ctas_per_sm = cap;
+        if ((st = trial(c, 1, 1, &t)) != POLYLAB_OK) break;
+        if (t < best_t) {
           best_t = t;
           best = c;
         }
       }
       if (st != POLYLAB_OK) break;
     }
-    if (st != POLYLAB_OK) break;
+    cur = best;
+  }
+  // 3. work order, timed over the whole pipeline
+  if (st == POLYLAB_OK) {
+    polylab_batch_config best = cur;
+    best_t = 1e30f;
+    for (int order : {1, 0}) {
+      polylab_batch_config c = cur;
+      c.order = order;
+      if ((st = trial(c, 0, 2, &t)) != POLYLAB_OK) break;
+      if (t < best_t) {
+        best_t = t;
+        best = c;
+      }
+    }
+    cur = best;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   PL_TRY(st);
-  PL_TRY(polylab_batch_set_config(b, &best, stream));
-  if (chosen) *chosen = best;
+  if (best_t >= 1e30f) return POLYLAB_ERR_UNSUPPORTED;
+  PL_TRY(polylab_batch_set_config(b, &cur, stream));
+  if (chosen) *chosen = cur;
   if (best_ms) *best_ms = best_t;
   return POLYLAB_OK;
 }

@@ -12,8 +12,14 @@ struct ExactDesc {
   int64_t m;
   int n;
   int E;             // largest exponent (power-table depth)
-  int mats_in_smem;  // 0: matrices in the per-CTA global workspace
+  int mats_in_smem;  // frame stage: 0 = matrices in the per-CTA global workspace
+  int h_in_smem;     // term stage: 0 = H accumulated in the point's workspace slot
+  int w_in_smem;     // third stage: 0 = W read from the point's workspace slot
+  int64_t mat_off;   // first element of point 0's n x n slot in the matrix workspaces
+  int64_t vec_off;   // first element of point 0's record in the vector workspace
   int max_support;
+  int64_t koff[kMaxSupport + 2];   // support-size groups of the sorted term list
+  int64_t k3off[kMaxSupport + 1];  // first term of degree >= 3 in each group
   const double* X;   // P x n
   int64_t P;
   double* D;
@@ -22,9 +28,10 @@ struct ExactDesc {
 };
 
 struct ExactConfig {
-  int threads = 0;      // CTA size: 64, 128 or 256 (0: by largest n)
-  int ctas_per_sm = 0;  // cap on resident CTAs per SM (0: occupancy limit)
-  int order = 1;        // 1: most expensive polynomials first, 0: as given
+  int threads = 0;        // frame-stage CTA size: 64, 128 or 256 (0: by largest n)
+  int ctas_per_sm = 0;    // cap on resident frame-stage CTAs per SM (0: occupancy limit)
+  int order = 1;          // 1: most expensive polynomials first, 0: as given
+  int term_threads = 0;   // CTA size of the two term sweeps (0: 128)
 };
 
 struct ExactBatch {
@@ -36,10 +43,15 @@ struct ExactBatch {
   ExactDesc* descs = nullptr;  // DEVICE copies
   int* order = nullptr;
   int64_t* prefix = nullptr;
-  int* counter = nullptr;
+  int* counter = nullptr;  // one work counter per stage
   int n_desc = 0;
   int64_t total = 0;
-  size_t smem = 0;
+  size_t smem[3] = {0, 0, 0};
+  // workspaces: H and W (one n x n slot per point each), small vectors
+  void* ws_h = nullptr;
+  void* ws_w = nullptr;
+  void* ws_v = nullptr;
+  size_t ws_mat_bytes = 0, ws_vec_bytes = 0;
   size_t gws_stride = 0;
   unsigned char* gws = nullptr;
   size_t gws_bytes = 0;
@@ -54,6 +66,7 @@ polylab_status exact_batch_relayout(ExactBatch* b, cudaStream_t s);
 void exact_batch_release(ExactBatch* b, cudaStream_t s);
 polylab_status prepare_exact_batch(ExactBatch* b);
 polylab_status run_exact_batch(ExactBatch* b, cudaStream_t s);
+polylab_status run_exact_stage(ExactBatch* b, int stage, cudaStream_t s);
 double exact_point_cost(const ExactDesc& d, int max_support);
 
 }  // namespace polylab

@@ -91,7 +91,11 @@ struct polylab_plan {
   int64_t m = 0;
   int32_t max_exp = 0;       // largest single exponent (power-table depth)
   int32_t max_support = 0;   // largest number of active variables in a term
-  polylab::Term* terms = nullptr;  // DEVICE, m terms
+  polylab::Term* terms = nullptr;  // DEVICE, m terms, sorted by (support size, degree)
+  // koff[k]: first term with support size k (koff[kMaxSupport + 1] = m);
+  // k3off[k]: first term of that group with degree >= 3
+  int64_t koff[polylab::kMaxSupport + 2] = {};
+  int64_t k3off[polylab::kMaxSupport + 1] = {};
   // derived-coefficient data for the tensor-core forms (nullptr unless built)
   polylab::GemmOperand* gemm = nullptr;
   int64_t closure = -1;

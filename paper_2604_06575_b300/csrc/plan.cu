@@ -78,6 +78,29 @@ __global__ void pack_terms_kernel(const uint8_t* __restrict__ exps, const double
   }
 }
 
+// Group boundaries of a term list sorted by (support size, degree).
+static void group_offsets(const std::vector<Term>& host, polylab_plan* plan) {
+  const int64_t m = (int64_t)host.size();
+  std::vector<int> ks(m), ds(m);
+  for (int64_t t = 0; t < m; ++t) {
+    int k = 0, d = 0;
+    for (int q = 0; q < kMaxSupport; ++q) {
+      k += host[t].exp[q] != 0;
+      d += host[t].exp[q];
+    }
+    ks[t] = k;
+    ds[t] = d;
+  }
+  int64_t t = 0;
+  for (int k = 0; k <= kMaxSupport; ++k) {
+    plan->koff[k] = t;
+    while (t < m && ks[t] == k && ds[t] < 3) ++t;
+    plan->k3off[k] = t;
+    while (t < m && ks[t] == k) ++t;
+  }
+  plan->koff[kMaxSupport + 1] = m;
+}
+
 polylab_status build_term_plan(const polylab_poly* p, cudaStream_t s, polylab_plan* plan) {
   PL_TRY(check_poly(p));
   if (p->n_vars > 65535) return POLYLAB_ERR_UNSUPPORTED;
@@ -117,6 +140,14 @@ polylab_status build_term_plan(const polylab_poly* p, cudaStream_t s, polylab_pl
     std::stable_sort(host.begin(), host.end(), [&](const Term& a, const Term& b) { return key(a) < key(b); });
     PL_CUDA(cudaMemcpyAsync(plan->terms, host.data(), p->n_terms * sizeof(Term), cudaMemcpyHostToDevice, s));
     PL_CUDA(cudaStreamSynchronize(s));
+    group_offsets(host, plan);
+  } else {
+    std::vector<Term> host(p->n_terms);
+    if (p->n_terms > 0) {
+      PL_CUDA(cudaMemcpyAsync(host.data(), plan->terms, sizeof(Term), cudaMemcpyDeviceToHost, s));
+      PL_CUDA(cudaStreamSynchronize(s));
+    }
+    group_offsets(host, plan);
   }
   return POLYLAB_OK;
 }

@@ -5,6 +5,8 @@
 // repeated multiplication.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace polylab {
@@ -17,11 +19,8 @@ struct TermRegs {
   int exp[kMaxSupport];
 };
 
-__device__ __forceinline__ TermRegs load_term(const Term* __restrict__ terms, int64_t t) {
+__device__ __forceinline__ TermRegs decode_term(uint4 a, uint4 b) {
   TermRegs r;
-  const uint4* p = reinterpret_cast<const uint4*>(terms + t);
-  uint4 a = __ldg(p);
-  uint4 b = __ldg(p + 1);
   r.coef = __hiloint2double((int)a.y, (int)a.x);
   const uint32_t v[4] = {a.z, a.w, b.x, b.y};
   const uint32_t e[2] = {b.z, b.w};
@@ -34,6 +33,39 @@ __device__ __forceinline__ TermRegs load_term(const Term* __restrict__ terms, in
   }
   return r;
 }
+
+__device__ __forceinline__ TermRegs load_term(const Term* __restrict__ terms, int64_t t) {
+  const uint4* p = reinterpret_cast<const uint4*>(terms + t);
+  return decode_term(__ldg(p), __ldg(p + 1));
+}
+
+// Strided walk t = start, start + stride, ... < m over a term list with the
+// next term's 32 bytes loaded one step ahead, so the load latency of the term
+// stream overlaps the current term's arithmetic.
+struct TermStream {
+  const uint4* p;
+  int64_t t, m, stride;
+  uint4 a, b;
+  __device__ __forceinline__ TermStream(const Term* __restrict__ terms, int64_t m_, int64_t start, int64_t stride_)
+      : p(reinterpret_cast<const uint4*>(terms)), t(start), m(m_), stride(stride_) {
+    if (t < m) {
+      a = __ldg(p + 2 * t);
+      b = __ldg(p + 2 * t + 1);
+    }
+  }
+  __device__ __forceinline__ bool next(TermRegs& r) {
+    if (t >= m) return false;
+    const uint4 ca = a, cb = b;
+    const int64_t tn = t + stride;
+    if (tn < m) {
+      a = __ldg(p + 2 * tn);
+      b = __ldg(p + 2 * tn + 1);
+    }
+    r = decode_term(ca, cb);
+    t = tn;
+    return true;
+  }
+};
 
 // Value, gradient and upper-triangle Hessian contributions of one term at one
 // point, for a term with exactly K active variables (loops fully unrolled).
@@ -78,6 +110,13 @@ __device__ __forceinline__ void term_derivs_k(const TermRegs& t, const R* __rest
   }
 }
 
+// Terms with more than six active variables are rare; they run out of line so
+// that their register demand does not set the budget of the common cases.
+template <typename R, int ORDER, int K, typename Emit>
+__device__ __noinline__ void term_derivs_wide(const TermRegs& t, const R* __restrict__ pw, int E1, Emit emit) {
+  term_derivs_k<R, ORDER, K>(t, pw, E1, emit);
+}
+
 // Dispatch on the support size.  Plans keep their term lists sorted by
 // support size, so the threads of a warp normally take the same branch.
 template <typename R, int ORDER, typename Emit>
@@ -90,8 +129,8 @@ __device__ __forceinline__ void term_derivs(const TermRegs& t, const R* __restri
     case 4: term_derivs_k<R, ORDER, 4>(t, pw, E1, emit); break;
     case 5: term_derivs_k<R, ORDER, 5>(t, pw, E1, emit); break;
     case 6: term_derivs_k<R, ORDER, 6>(t, pw, E1, emit); break;
-    case 7: term_derivs_k<R, ORDER, 7>(t, pw, E1, emit); break;
-    default: term_derivs_k<R, ORDER, 8>(t, pw, E1, emit); break;
+    case 7: term_derivs_wide<R, ORDER, 7>(t, pw, E1, emit); break;
+    default: term_derivs_wide<R, ORDER, 8>(t, pw, E1, emit); break;
   }
 }
 
@@ -163,6 +202,12 @@ __device__ __forceinline__ void term_third_contract_k(const TermRegs& t, const R
   for (int s = 0; s < K; ++s) emit(t.var[s], c * acc[s]);
 }
 
+template <typename R, int K, typename WGet, typename Emit>
+__device__ __noinline__ void term_third_contract_wide(const TermRegs& t, const R* __restrict__ pw, int E1, WGet wget,
+                                                      Emit emit) {
+  term_third_contract_k<R, K>(t, pw, E1, wget, emit);
+}
+
 template <typename R, typename WGet, typename Emit>
 __device__ __forceinline__ void term_third_contract(const TermRegs& t, const R* __restrict__ pw, int E1, WGet&& wget,
                                                     Emit&& emit) {
@@ -174,9 +219,31 @@ __device__ __forceinline__ void term_third_contract(const TermRegs& t, const R* 
     case 4: term_third_contract_k<R, 4>(t, pw, E1, wget, emit); break;
     case 5: term_third_contract_k<R, 5>(t, pw, E1, wget, emit); break;
     case 6: term_third_contract_k<R, 6>(t, pw, E1, wget, emit); break;
-    case 7: term_third_contract_k<R, 7>(t, pw, E1, wget, emit); break;
-    default: term_third_contract_k<R, 8>(t, pw, E1, wget, emit); break;
+    case 7: term_third_contract_wide<R, 7>(t, pw, E1, wget, emit); break;
+    default: term_third_contract_wide<R, 8>(t, pw, E1, wget, emit); break;
   }
+}
+
+// Call f(std::integral_constant<int, K>{}) for K = 0..KMAX in order.
+template <int KMAX, int K = 0, typename F>
+__device__ __forceinline__ void for_support(F&& f) {
+  f(std::integral_constant<int, K>{});
+  if constexpr (K < KMAX) for_support<KMAX, K + 1>(f);
+}
+
+// Per-group entry points: groups up to six active variables inline, wider
+// groups out of line (see term_derivs_wide).
+template <typename R, int ORDER, int K, typename Emit>
+__device__ __forceinline__ void term_derivs_group(const TermRegs& t, const R* __restrict__ pw, int E1, Emit& emit) {
+  if constexpr (K <= 6) term_derivs_k<R, ORDER, K>(t, pw, E1, emit);
+  else term_derivs_wide<R, ORDER, K>(t, pw, E1, emit);
+}
+
+template <typename R, int K, typename WGet, typename Emit>
+__device__ __forceinline__ void term_third_group(const TermRegs& t, const R* __restrict__ pw, int E1, WGet& wget,
+                                                 Emit& emit) {
+  if constexpr (K <= 6) term_third_contract_k<R, K>(t, pw, E1, wget, emit);
+  else term_third_contract_wide<R, K>(t, pw, E1, wget, emit);
 }
 
 }  // namespace polylab

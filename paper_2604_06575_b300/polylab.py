@@ -53,7 +53,8 @@ class _AnOpts(C.Structure):
 
 
 class _BatchConfig(C.Structure):
-    _fields_ = [("threads", C.c_int32), ("ctas_per_sm", C.c_int32), ("order", C.c_int32)]
+    _fields_ = [("threads", C.c_int32), ("ctas_per_sm", C.c_int32), ("order", C.c_int32),
+                ("term_threads", C.c_int32)]
 
 
 INFO_DTYPE = np.dtype([("grad_norm", "<f8"), ("logdet", "<f8"), ("flags", "<i4"), ("hv_evals", "<i4"),
@@ -85,6 +86,7 @@ _PP = C.POINTER(C.c_void_p)
 _lib.polylab_batch_create.argtypes = [C.c_int32, C.c_void_p, _PP, _PP, C.POINTER(C.c_int64), C.POINTER(_AnOpts),
                                       _PP, _PP, _PP, C.c_void_p, C.POINTER(C.c_void_p)]
 _lib.polylab_batch_run.argtypes = [C.c_void_p, C.c_void_p]
+_lib.polylab_batch_run_stage.argtypes = [C.c_void_p, C.c_int32, C.c_void_p]
 _lib.polylab_batch_get_config.argtypes = [C.c_void_p, C.POINTER(_BatchConfig)]
 _lib.polylab_batch_set_config.argtypes = [C.c_void_p, C.POINTER(_BatchConfig), C.c_void_p]
 _lib.polylab_batch_autotune.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(_BatchConfig),
@@ -103,16 +105,17 @@ _lib.polylab_affine_normal_batched.argtypes = [C.c_int32, C.c_void_p, _PP, _PP, 
                                                C.POINTER(_AnOpts), _PP, _PP, _PP, C.c_void_p]
 for _f in ("polylab_plan_create", "polylab_plan_destroy", "polylab_eval_derivs", "polylab_affine_normal",
            "polylab_simplify", "polylab_mul", "polylab_add", "polylab_simplify_noalloc", "polylab_batch_create",
-           "polylab_batch_run", "polylab_batch_get_config", "polylab_batch_set_config", "polylab_batch_autotune",
-           "polylab_batch_destroy", "polylab_affine_normal_batched", "polylab_plan_gemm_info", "polylab_mlp_init",
+           "polylab_batch_run", "polylab_batch_run_stage", "polylab_batch_get_config", "polylab_batch_set_config",
+           "polylab_batch_autotune", "polylab_batch_destroy", "polylab_affine_normal_batched",
+           "polylab_plan_gemm_info", "polylab_mlp_init",
            "polylab_mlp_data", "polylab_mlp_loss_grad", "polylab_mlp_adam", "polylab_mlp_pack"):
     getattr(_lib, _f).restype = C.c_int
 
 EXPORTED = ["polylab_status_string", "polylab_last_error", "polylab_simplify", "polylab_mul", "polylab_add",
             "polylab_plan_create", "polylab_plan_destroy", "polylab_plan_closure_size", "polylab_eval_derivs",
             "polylab_an_opts_default", "polylab_affine_normal", "polylab_simplify_noalloc", "polylab_batch_create",
-            "polylab_batch_run", "polylab_batch_get_config", "polylab_batch_set_config", "polylab_batch_autotune",
-            "polylab_batch_destroy", "polylab_affine_normal_batched", "polylab_plan_gemm_info",
+            "polylab_batch_run", "polylab_batch_run_stage", "polylab_batch_get_config", "polylab_batch_set_config",
+            "polylab_batch_autotune", "polylab_batch_destroy", "polylab_affine_normal_batched", "polylab_plan_gemm_info",
             "polylab_mlp_param_count", "polylab_mlp_init", "polylab_mlp_data", "polylab_mlp_loss_grad",
             "polylab_mlp_adam", "polylab_mlp_pack"]
 
@@ -352,19 +355,27 @@ class Batch:
     def run(self):
         _check("polylab_batch_run", _lib.polylab_batch_run(self.h, _stream()))
 
+    STAGES = ("terms", "frame", "third")
+
+    def run_stage(self, stage: int):
+        _check("polylab_batch_run_stage", _lib.polylab_batch_run_stage(self.h, stage, _stream()))
+
     def config(self):
         c = _BatchConfig()
         _check("polylab_batch_get_config", _lib.polylab_batch_get_config(self.h, C.byref(c)))
-        return dict(threads=c.threads, ctas_per_sm=c.ctas_per_sm, order=c.order)
+        return dict(threads=c.threads, ctas_per_sm=c.ctas_per_sm, order=c.order, term_threads=c.term_threads)
 
-    def set_config(self, threads, ctas_per_sm, order):
-        c = _BatchConfig(threads, ctas_per_sm, order)
+    def set_config(self, threads, ctas_per_sm, order, term_threads=None):
+        if term_threads is None:
+            term_threads = self.config()["term_threads"]
+        c = _BatchConfig(threads, ctas_per_sm, order, term_threads)
         _check("polylab_batch_set_config", _lib.polylab_batch_set_config(self.h, C.byref(c), _stream()))
 
     def autotune(self, reps=2):
         c, t = _BatchConfig(), C.c_float()
         _check("polylab_batch_autotune", _lib.polylab_batch_autotune(self.h, reps, _stream(), C.byref(c), C.byref(t)))
-        return dict(threads=c.threads, ctas_per_sm=c.ctas_per_sm, order=c.order), float(t.value)
+        return (dict(threads=c.threads, ctas_per_sm=c.ctas_per_sm, order=c.order, term_threads=c.term_threads),
+                float(t.value))
 
     def close(self):
         if self.h:
