@@ -49,20 +49,10 @@ namespace {
 __host__ __device__ inline int64_t vrec(int n) { return 4 * (int64_t)n + 8; }
 constexpr double kStOk = 0.0, kStZero = 1.0, kStNotPd = 2.0;
 
-template <int NT>
-__device__ __forceinline__ double block_sum(double v, double* red) {
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
   for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  __syncthreads();
-  if (l == 0) red[w] = v;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double t = threadIdx.x < NT / 32 ? red[threadIdx.x] : 0.0;
-    for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (threadIdx.x == 0) red[32] = t;
-  }
-  __syncthreads();
-  return red[32];
+  return v;
 }
 
 // next work item of this CTA (uniform across the CTA)
@@ -121,7 +111,7 @@ __device__ __forceinline__ void ldlt_block(int m, Col col, double* __restrict__ 
       if (lane == 0) *flag = 1;
       return;
     }
-    const double inv = 1.0 / d;
+    const double inv = __drcp_rn(d);
     if (lane == 0) {
       dv[c] = d;
       di[c] = inv;
@@ -198,29 +188,36 @@ __host__ __device__ Lay1 lay_terms(int n, int E1, bool in_smem) {
 }
 
 struct Lay2 {
-  size_t g, e, v, h, red, dv, di, uc, vr, u, w, Hr, Mr, Ld, total;
+  size_t e, v, h, dv, di, uc, vr, u, w, Hr, Ld, X, total;
 };
+// row stride of X = L^{-1}: odd, so that lanes reading rows j, j+1, ... at a
+// common column hit different banks
+__host__ __device__ inline int x_stride(int m) { return m | 1; }
 template <typename R>
 __host__ __device__ Lay2 lay_frame(int n, bool in_smem) {
   Lay2 L{};
   Bump b;
   const size_t m = n > 1 ? n - 1 : 1;
-  L.g = b.take(n * 8);
   L.e = b.take(n * 8);
   L.v = b.take(n * 8);
   L.h = b.take(n * 8);
-  L.red = b.take(40 * 8);
   L.dv = b.take(m * 8);      // LDL^T pivots d_k
   L.di = b.take(m * 8);      // 1 / d_k
   L.uc = b.take(2 * m * 8);  // unscaled pivot columns (two buffers)
   L.vr = b.take(n * sizeof(R));
   L.u = b.take(n * sizeof(R));
   L.w = b.take(n * sizeof(R));
-  L.Hr = in_smem ? b.take((size_t)n * n * sizeof(R)) : 0;
-  L.Mr = in_smem ? b.take((size_t)n * n * sizeof(R)) : 0;
-  // FP32 form: separate FP64 factor storage (packed lower triangle,
-  // column-major); the FP64 form factors in place in Hr
-  L.Ld = (in_smem && sizeof(R) == 4) ? b.take(m * (m + 1) / 2 * 8) : 0;
+  if (in_smem) {
+    L.Hr = b.take((size_t)n * n * sizeof(R));
+    // FP32 form: FP64 factor in a packed column-major lower triangle, whose
+    // m(m+1)/2 doubles then hold X (m rows of stride m|1 floats); the FP64
+    // form factors in place in Hr and keeps X apart
+    if (sizeof(R) == 4) {
+      L.Ld = L.X = b.take(m * (m + 1) / 2 * 8);
+    } else {
+      L.X = b.take(m * x_stride((int)m) * sizeof(R));
+    }
+  }
   L.total = b.o;
   return L;
 }
@@ -228,11 +225,11 @@ __host__ __device__ Lay2 lay_frame(int n, bool in_smem) {
 template <typename R>
 size_t frame_gmem(int n) {
   const size_t m = n > 1 ? n - 1 : 1;
-  return 2 * (size_t)n * n * sizeof(R) + (sizeof(R) == 4 ? m * (m + 1) / 2 * 8 : 0) + 256;
+  return (size_t)n * n * sizeof(R) + (sizeof(R) == 4 ? m * (m + 1) / 2 * 8 : m * x_stride((int)m) * sizeof(R)) + 256;
 }
 
 struct Lay3 {
-  size_t pw, c, red, v, e, y, yr, W, total;
+  size_t pw, c, v, e, y, yr, W, total;
 };
 template <typename R, int NW>
 __host__ __device__ Lay3 lay_third(int n, int E1, bool in_smem) {
@@ -240,7 +237,6 @@ __host__ __device__ Lay3 lay_third(int n, int E1, bool in_smem) {
   Bump b;
   L.pw = b.take((size_t)n * E1 * sizeof(R));
   L.c = b.take((size_t)NW * n * sizeof(R));  // one replica per warp
-  L.red = b.take(40 * 8);
   L.v = b.take(n * 8);
   L.e = b.take(n * 8);
   L.y = b.take(n * 8);
@@ -327,13 +323,19 @@ __global__ void __launch_bounds__(NT) exact_terms_kernel(StageArgs<R> a) {
     }
     __syncthreads();
     double* rec = a.vecs + pd.vec_off + p * vrec(n);
+    gabs = warp_sum(gabs);
+    if (lane == 0) red[wid] = (double)gabs;
     for (int i = tid; i < n; i += NT) {
       R s = g[i];
       for (int q = 1; q < NW; ++q) s += g[q * n + i];
       rec[i] = (double)s;
     }
-    const double ga = block_sum<NT>((double)gabs, red);
-    if (tid == 0) rec[4 * n] = ga;
+    __syncthreads();
+    if (tid == 0) {
+      double ga = 0.0;
+      for (int q = 0; q < NW; ++q) ga += red[q];
+      rec[4 * n] = ga;
+    }
     // full symmetric H from the upper triangle the sweep filled
     for (int i = wid; i < n; i += NW)
       for (int j = lane; j < n; j += 32) {
@@ -349,6 +351,7 @@ __global__ void __launch_bounds__(NT) exact_frame_kernel(StageArgs<R> a) {
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ int64_t s_item;
   __shared__ int s_flag;
+  __shared__ double s_sc[4];
   constexpr bool kF64 = sizeof(R) == 8;
   constexpr int NW = NT / 32;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -358,13 +361,11 @@ __global__ void __launch_bounds__(NT) exact_frame_kernel(StageArgs<R> a) {
     const int lo = find_poly(a.prefix, a.n_desc, item);
     const ExactDesc& pd = a.descs[a.order[lo]];
     const int64_t p = item - a.prefix[lo];
-    const int n = pd.n, m = n - 1, nn = n * n;
+    const int n = pd.n, m = n - 1, nn = n * n, xs = x_stride(m);
     const Lay2 L = lay_frame<R>(n, pd.mats_in_smem);
-    double* gd = (double*)(sm + L.g);
     double* e = (double*)(sm + L.e);
     double* v = (double*)(sm + L.v);
     double* h = (double*)(sm + L.h);
-    double* red = (double*)(sm + L.red);
     double* dv = (double*)(sm + L.dv);
     double* di = (double*)(sm + L.di);
     double* uc = (double*)(sm + L.uc);
@@ -373,12 +374,13 @@ __global__ void __launch_bounds__(NT) exact_frame_kernel(StageArgs<R> a) {
     R* w = (R*)(sm + L.w);
     unsigned char* gb = a.gws + (size_t)blockIdx.x * a.gws_stride;
     R* Hr = pd.mats_in_smem ? (R*)(sm + L.Hr) : (R*)gb;
-    R* Mr = pd.mats_in_smem ? (R*)(sm + L.Mr) : (R*)(gb + (size_t)nn * sizeof(R));
+    unsigned char* rest = pd.mats_in_smem ? nullptr : gb + (size_t)nn * sizeof(R);
     // FP64 factor storage, element (i, j) of the leading block at col(j)[i]:
     // in place in Hr (col(j) = row j of the symmetric Hr) for the FP64 form, a
-    // packed column-major lower triangle for the FP32 form
-    double* Ld = kF64 ? (double*)Hr
-                      : (pd.mats_in_smem ? (double*)(sm + L.Ld) : (double*)(gb + 2 * (size_t)nn * sizeof(R)));
+    // packed column-major lower triangle for the FP32 form; X = L^{-1} with
+    // row stride xs (the FP32 form reuses the factor's storage)
+    double* Ld = kF64 ? (double*)Hr : (pd.mats_in_smem ? (double*)(sm + L.Ld) : (double*)rest);
+    R* Xs = kF64 ? (pd.mats_in_smem ? (R*)(sm + L.X) : (R*)rest) : (R*)Ld;
     auto col = [Ld, n, m](int j) -> double* {
       return kF64 ? Ld + (size_t)j * n : Ld + ((size_t)j * m - (size_t)j * (j - 1) / 2 - j);
     };
@@ -387,18 +389,38 @@ __global__ void __launch_bounds__(NT) exact_frame_kernel(StageArgs<R> a) {
     double* rec = a.vecs + pd.vec_off + p * vrec(n);
     for (int i = wid; i < n; i += NW)
       for (int j = lane; j < n; j += 32) Hr[i * n + j] = Hg[i * n + j];
-    double gg = 0.0;
-    for (int i = tid; i < n; i += NT) {
-      const double gi = rec[i];
-      gd[i] = gi;
-      gg += gi * gi;
+    // |g|, the zero-gradient test and the Householder vector (warp 0)
+    if (wid == 0) {
+      double gg = 0.0;
+      for (int i = lane; i < n; i += 32) gg += rec[i] * rec[i];
+      const double gn = sqrt(warp_sum(gg));
+      bool zero = !(gn > 0.0) || !isfinite(gn);
+      // relative test at the resolution of the form: 1e-14 (FP64), 1e-6 (FP32 sums)
+      if (!a.assume_nonzero_x && gn <= (kF64 ? 1e-14 : 1e-6) * rec[4 * n]) zero = true;
+      double beta = 0.0, sgn = 1.0;
+      if (!zero) {
+        const double ign = 1.0 / gn;
+        const double en = rec[n - 1] * ign;
+        sgn = en >= 0.0 ? 1.0 : -1.0;
+        beta = 1.0 / (1.0 + sgn * en);  // 2 / v^T v with v^T v = 2 (1 + s e_n)
+        for (int i = lane; i < n; i += 32) {
+          const double ei = rec[i] * ign;
+          e[i] = ei;
+          v[i] = ei + (i == n - 1 ? sgn : 0.0);
+          vr[i] = R(v[i]);
+        }
+      }
+      if (lane == 0) {
+        s_sc[0] = gn;
+        s_sc[1] = zero ? 1.0 : 0.0;
+        s_sc[2] = beta;
+        s_sc[3] = sgn;
+        s_flag = 0;
+      }
     }
-    if (tid == 0) s_flag = 0;
-    const double gn = sqrt(block_sum<NT>(gg, red));
-    bool zero = !(gn > 0.0) || !isfinite(gn);
-    // relative test at the resolution of the form: 1e-14 (FP64), 1e-6 (FP32 sums)
-    if (!a.assume_nonzero_x && gn <= (kF64 ? 1e-14 : 1e-6) * rec[4 * n]) zero = true;
-    if (zero) {
+    __syncthreads();
+    const double gn = s_sc[0], beta = s_sc[2], sgn = s_sc[3];
+    if (s_sc[1] != 0.0) {
       write_failed(pd, p, n, gn, POLYLAB_FLAG_ZERO_GRAD);
       if (tid == 0) {
         rec[4 * n + 1] = gn;
@@ -406,25 +428,18 @@ __global__ void __launch_bounds__(NT) exact_frame_kernel(StageArgs<R> a) {
       }
       continue;
     }
-    const double en = gd[n - 1] / gn;
-    const double sgn = en >= 0.0 ? 1.0 : -1.0;
-    const double beta = 1.0 / (1.0 + sgn * en);  // 2 / v^T v with v^T v = 2 (1 + s e_n)
-    for (int i = tid; i < n; i += NT) {
-      e[i] = gd[i] / gn;
-      v[i] = e[i] + (i == n - 1 ? sgn : 0.0);
-      vr[i] = R(v[i]);
-    }
-    __syncthreads();
     for (int i = tid; i < n; i += NT) {  // u = H v (H symmetric: column access, conflict-free)
       R acc = R(0);
       for (int j = 0; j < n; ++j) acc += Hr[j * n + i] * vr[j];
       u[i] = acc;
     }
     __syncthreads();
-    double part = 0.0;
-    for (int i = tid; i < n; i += NT) part += v[i] * (double)u[i];
-    const double gamma = block_sum<NT>(part, red);
-    for (int i = tid; i < n; i += NT) w[i] = R(beta * (double)u[i] - 0.5 * beta * beta * gamma * v[i]);
+    if (wid == 0) {  // w = beta u - (beta^2 / 2) (v.u) v
+      double part = 0.0;
+      for (int i = lane; i < n; i += 32) part += v[i] * (double)u[i];
+      const double gamma = warp_sum(part);
+      for (int i = lane; i < n; i += 32) w[i] = R(beta * (double)u[i] - 0.5 * beta * beta * gamma * v[i]);
+    }
     __syncthreads();
     for (int i = wid; i < n; i += NW)  // P H P = H - v w^T - w v^T
       for (int j = lane; j < n; j += 32) Hr[i * n + j] -= vr[i] * w[j] + w[i] * vr[j];
@@ -447,19 +462,24 @@ __global__ void __launch_bounds__(NT) exact_frame_kernel(StageArgs<R> a) {
       }
       continue;
     }
-    double lsum = 0.0;
-    for (int i = tid; i < m; i += NT) lsum += log(dv[i]);
-    const double logdet = block_sum<NT>(lsum, red);
-    // Lt(i, j) = Hr[j*n + i] = l_ij (i > j) in the form's precision; sq = d^{-1/2}
+    // log-det (warp 0) while the others take the factor into the form's
+    // precision: Lt(i, j) = Hr[j*n + i] = l_ij (i > j); sq = d^{-1/2}
     R* sq = w;
-    for (int i = tid; i < m; i += NT) sq[i] = R(sqrt(di[i]));
+    if (wid == 0) {
+      double lsum = 0.0;
+      for (int k = lane; k < m; k += 32) lsum += log(dv[k]);
+      lsum = warp_sum(lsum);
+      if (lane == 0) s_sc[1] = lsum;
+    }
+    for (int i = tid; i < m; i += NT) sq[i] = kF64 ? R(sqrt(di[i])) : R(sqrtf((float)di[i]));
     if constexpr (!kF64) {
       for (int j = wid; j < m; j += NW)
         for (int i = j + 1 + lane; i < m; i += 32) Hr[j * n + i] = (R)col(j)[i];
+      __syncthreads();  // the factor's storage becomes X
     }
-    // X = L^{-1} (unit lower), stored transposed: Mr[j*n + i] = X_ij, i >= j
+    // X = L^{-1} (unit lower), stored transposed: Xs[j*xs + i] = X_ij, i >= j
     for (int j = wid; j < m; j += NW)
-      for (int i = j + lane; i < m; i += 32) Mr[j * n + i] = i == j ? R(1) : R(0);
+      for (int i = j + lane; i < m; i += 32) Xs[j * xs + i] = i == j ? R(1) : R(0);
     __syncthreads();
     // right-looking: after step k row k of X is final; X_ij -= l_ik X_kj for
     // j <= k < i, the (m-k-1) x (k+1) rectangle enumerated over the CTA
@@ -477,57 +497,61 @@ __global__ void __launch_bounds__(NT) exact_frame_kernel(StageArgs<R> a) {
           i0 -= rows;
         }
         const int i = k + 1 + i0;
-        Mr[j * n + i] -= Hr[k * n + i] * Mr[j * n + k];
+        Xs[j * xs + i] -= Hr[k * n + i] * Xs[j * xs + k];
       }
       __syncthreads();
     }
     // X' = D^{-1/2} X (row i scaled by d_i^{-1/2}), so M = X'^T X'
     for (int j = wid; j < m; j += NW)
-      for (int i = j + lane; i < m; i += 32) Mr[j * n + i] *= sq[i];
+      for (int i = j + lane; i < m; i += 32) Xs[j * xs + i] *= sq[i];
     __syncthreads();
     // M = H_T^{-1} = X'^T X', upper triangle into Hr (L no longer needed)
     for (int idx = tid; idx < m * m; idx += NT) {
       const int i = idx / m, j = idx - i * m;
       if (j < i) continue;
       R acc = R(0);
-      for (int k = j; k < m; ++k) acc += Mr[i * n + k] * Mr[j * n + k];
+      for (int k = j; k < m; ++k) acc += Xs[i * xs + k] * Xs[j * xs + k];
       Hr[i * n + j] = acc;
     }
     __syncthreads();
-    for (int i = wid; i < n; i += NW)  // Mr <- [M 0; 0 0], full symmetric
-      for (int j = lane; j < n; j += 32)
-        Mr[i * n + j] = (i == n - 1 || j == n - 1) ? R(0) : (i <= j ? Hr[i * n + j] : Hr[j * n + i]);
+    for (int i = wid; i < n; i += NW)  // Hr <- [M 0; 0 0], full symmetric, in place
+      for (int j = lane; j < n; j += 32) {
+        if (i == n - 1 || j == n - 1) Hr[i * n + j] = R(0);
+        else if (i > j) Hr[i * n + j] = Hr[j * n + i];
+      }
     __syncthreads();
     for (int i = tid; i < n; i += NT) {  // u = [M 0; 0 0] v
       R acc = R(0);
-      for (int j = 0; j < n; ++j) acc += Mr[j * n + i] * vr[j];
+      for (int j = 0; j < n; ++j) acc += Hr[j * n + i] * vr[j];
       u[i] = acc;
     }
     __syncthreads();
-    part = 0.0;
-    for (int i = tid; i < n; i += NT) part += v[i] * (double)u[i];
-    const double gam2 = block_sum<NT>(part, red);
-    for (int i = tid; i < n; i += NT) w[i] = R(beta * (double)u[i] - 0.5 * beta * beta * gam2 * v[i]);
+    if (wid == 0) {
+      double part = 0.0;
+      for (int i = lane; i < n; i += 32) part += v[i] * (double)u[i];
+      const double gam2 = warp_sum(part);
+      for (int i = lane; i < n; i += 32) {
+        w[i] = R(beta * (double)u[i] - 0.5 * beta * beta * gam2 * v[i]);
+        rec[n + i] = v[i];
+        rec[2 * n + i] = e[i];
+        rec[3 * n + i] = h[i];
+      }
+      if (lane == 0) {
+        rec[4 * n + 1] = gn;
+        rec[4 * n + 2] = beta;
+        rec[4 * n + 3] = s_sc[1];
+        rec[4 * n + 4] = kStOk;
+      }
+    }
     __syncthreads();
     for (int i = wid; i < n; i += NW)  // W = P [M 0; 0 0] P
-      for (int j = lane; j < n; j += 32) Wg[i * n + j] = Mr[i * n + j] - (vr[i] * w[j] + w[i] * vr[j]);
-    for (int i = tid; i < n; i += NT) {
-      rec[n + i] = v[i];
-      rec[2 * n + i] = e[i];
-      rec[3 * n + i] = h[i];
-    }
-    if (tid == 0) {
-      rec[4 * n + 1] = gn;
-      rec[4 * n + 2] = beta;
-      rec[4 * n + 3] = logdet;
-      rec[4 * n + 4] = kStOk;
-    }
+      for (int j = lane; j < n; j += 32) Wg[i * n + j] = Hr[i * n + j] - (vr[i] * w[j] + w[i] * vr[j]);
   }
 }
 
 // ------------------------------------------------------------------ stage 3
 template <typename R, int NT>
-__global__ void __launch_bounds__(NT) exact_third_kernel(StageArgs<R> a) {
+__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 640 / NT : 1) exact_third_kernel(StageArgs<R> a) {
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ int64_t s_item;
   constexpr int NW = NT / 32;
@@ -544,7 +568,6 @@ __global__ void __launch_bounds__(NT) exact_third_kernel(StageArgs<R> a) {
     const Lay3 L = lay_third<R, NW>(n, E1, pd.w_in_smem);
     R* pw = (R*)(sm + L.pw);
     R* c = (R*)(sm + L.c);
-    double* red = (double*)(sm + L.red);
     double* v = (double*)(sm + L.v);
     double* e = (double*)(sm + L.e);
     double* y = (double*)(sm + L.y);
@@ -579,43 +602,47 @@ __global__ void __launch_bounds__(NT) exact_third_kernel(StageArgs<R> a) {
       });
     }
     __syncthreads();
-    const double gn = rec[4 * n + 1], beta = rec[4 * n + 2], logdet = rec[4 * n + 3];
-    // a = (P c)[0:m] = c - beta v (v.c);  tv = [h - |g|/(n+1) a; 0]
-    double part = 0.0;
-    for (int i = tid; i < n; i += NT) {
-      R s = c[i];
-      for (int q = 1; q < NW; ++q) s += c[q * n + i];
-      y[i] = (double)s;
-      part += v[i] * (double)s;
+    const double gn = rec[4 * n + 1], beta = rec[4 * n + 2];
+    // a = (P c)[0:m] = c - beta v (v.c);  tv = [h - |g|/(n+1) a; 0];  yr = P tv  (warp 0)
+    if (wid == 0) {
+      double vc = 0.0;
+      for (int i = lane; i < n; i += 32) {
+        R s = c[i];
+        for (int q = 1; q < NW; ++q) s += c[q * n + i];
+        y[i] = (double)s;
+        vc += v[i] * (double)s;
+      }
+      vc = warp_sum(vc);
+      const double wgt = gn / (double)(n + 1);
+      double vt = 0.0;
+      for (int i = lane; i < n; i += 32) {
+        const double tv = i < m ? rec[3 * n + i] - wgt * (y[i] - beta * v[i] * vc) : 0.0;
+        y[i] = tv;
+        vt += v[i] * tv;
+      }
+      vt = warp_sum(vt);
+      for (int i = lane; i < n; i += 32) yr[i] = R(y[i] - beta * v[i] * vt);
     }
-    const double vc = block_sum<NT>(part, red);
-    const double wgt = gn / (double)(n + 1);
-    part = 0.0;
-    for (int i = tid; i < n; i += NT) {
-      const double tv = i < m ? rec[3 * n + i] - wgt * (y[i] - beta * v[i] * vc) : 0.0;
-      y[i] = tv;
-      part += v[i] * tv;
-    }
-    const double vt = block_sum<NT>(part, red);
-    for (int i = tid; i < n; i += NT) yr[i] = R(y[i] - beta * v[i] * vt);  // P tv
     __syncthreads();
     // nu = W P tv - e  (W symmetric: column access, conflict-free)
-    double nrm = 0.0;
     for (int i = tid; i < n; i += NT) {
       R acc = R(0);
       for (int j = 0; j < n; ++j) acc += W[j * n + i] * yr[j];
-      const double nu = (double)acc - e[i];
-      y[i] = nu;
-      nrm += nu * nu;
+      y[i] = (double)acc - e[i];
     }
-    const double inv = 1.0 / sqrt(block_sum<NT>(nrm, red));
-    for (int i = tid; i < n; i += NT) {
-      pd.D[p * n + i] = y[i];
-      if (pd.Dunit) pd.Dunit[p * n + i] = y[i] * inv;
-    }
-    if (tid == 0 && pd.info) {
-      polylab_an_info in{gn, logdet, 0, n, n - 1, 0};
-      pd.info[p] = in;
+    __syncthreads();
+    if (wid == 0) {
+      double nrm = 0.0;
+      for (int i = lane; i < n; i += 32) nrm += y[i] * y[i];
+      const double inv = 1.0 / sqrt(warp_sum(nrm));
+      for (int i = lane; i < n; i += 32) {
+        pd.D[p * n + i] = y[i];
+        if (pd.Dunit) pd.Dunit[p * n + i] = y[i] * inv;
+      }
+      if (lane == 0 && pd.info) {
+        polylab_an_info in{gn, rec[4 * n + 3], 0, n, n - 1, 0};
+        pd.info[p] = in;
+      }
     }
   }
 }
