@@ -329,6 +329,10 @@ polylab_status polylab_batch_run(polylab_batch* batch, polylab_stream stream);
  * so stage s may only be run after stages 0..s-1 have run on the same inputs.
  * POLYLAB_ERR_INVALID_ARG for another stage number. */
 polylab_status polylab_batch_run_stage(polylab_batch* batch, int32_t stage, polylab_stream stream);
+/* Synchronises `stream` and reports whether any run of this batch gave up a
+ * bounded wait (a bulk copy into shared memory that did not complete within
+ * two seconds): POLYLAB_ERR_TIMEOUT then, POLYLAB_OK otherwise. */
+polylab_status polylab_batch_check(polylab_batch* batch, polylab_stream stream);
 polylab_status polylab_batch_get_config(const polylab_batch* batch, polylab_batch_config* cfg);
 polylab_status polylab_batch_set_config(polylab_batch* batch, const polylab_batch_config* cfg,
                                         polylab_stream stream);

@@ -35,6 +35,7 @@
 #include <numeric>
 #include <vector>
 
+#include "async.cuh"
 #include "batch.cuh"
 #include "common.cuh"
 #include "terms.cuh"
@@ -48,6 +49,14 @@ namespace {
 // | 4n+2: beta | 4n+3: log-det | 4n+4: status
 __host__ __device__ inline int64_t vrec(int n) { return 4 * (int64_t)n + 8; }
 constexpr double kStOk = 0.0, kStZero = 1.0, kStNotPd = 2.0;
+
+// Elements of a point's n x n slot in the matrix workspaces: n^2 rounded up to
+// 16 bytes, so that every slot can move by one bulk copy.
+template <typename R>
+__host__ __device__ inline int64_t mat_slot(int n) {
+  constexpr int q = 16 / sizeof(R);
+  return ((int64_t)n * n + q - 1) / q * q;
+}
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
@@ -182,7 +191,7 @@ __host__ __device__ Lay1 lay_terms(int n, int E1, bool in_smem) {
   L.pw = b.take((size_t)n * E1 * sizeof(R));
   L.g = b.take((size_t)NW * n * sizeof(R));  // one replica per warp
   L.red = b.take(40 * 8);
-  L.H = in_smem ? b.take((size_t)n * n * sizeof(R)) : 0;
+  L.H = in_smem ? b.take((size_t)mat_slot<R>(n) * sizeof(R)) : 0;
   L.total = b.o;
   return L;
 }
@@ -208,7 +217,7 @@ __host__ __device__ Lay2 lay_frame(int n, bool in_smem) {
   L.u = b.take(n * sizeof(R));
   L.w = b.take(n * sizeof(R));
   if (in_smem) {
-    L.Hr = b.take((size_t)n * n * sizeof(R));
+    L.Hr = b.take((size_t)mat_slot<R>(n) * sizeof(R));
     // FP32 form: FP64 factor in a packed column-major lower triangle, whose
     // m(m+1)/2 doubles then hold X (m rows of stride m|1 floats); the FP64
     // form factors in place in Hr and keeps X apart
@@ -225,7 +234,7 @@ __host__ __device__ Lay2 lay_frame(int n, bool in_smem) {
 template <typename R>
 size_t frame_gmem(int n) {
   const size_t m = n > 1 ? n - 1 : 1;
-  return (size_t)n * n * sizeof(R) + (sizeof(R) == 4 ? m * (m + 1) / 2 * 8 : m * x_stride((int)m) * sizeof(R)) + 256;
+  return (size_t)mat_slot<R>(n) * sizeof(R) + (sizeof(R) == 4 ? m * (m + 1) / 2 * 8 : m * x_stride((int)m) * sizeof(R)) + 256;
 }
 
 struct Lay3 {
@@ -241,7 +250,7 @@ __host__ __device__ Lay3 lay_third(int n, int E1, bool in_smem) {
   L.e = b.take(n * 8);
   L.y = b.take(n * 8);
   L.yr = b.take(n * sizeof(R));
-  L.W = in_smem ? b.take((size_t)n * n * sizeof(R)) : 0;
+  L.W = in_smem ? b.take((size_t)mat_slot<R>(n) * sizeof(R)) : 0;
   L.total = b.o;
   return L;
 }
@@ -261,6 +270,7 @@ struct StageArgs {
   int assume_nonzero_x;
   unsigned char* gws;
   size_t gws_stride;
+  int* err;  // set when a bounded wait expires
 };
 
 __device__ __forceinline__ void write_failed(const ExactDesc& pd, int64_t p, int n, double gn, int flag) {
@@ -289,16 +299,16 @@ __global__ void __launch_bounds__(NT) exact_terms_kernel(StageArgs<R> a) {
     const int lo = find_poly(a.prefix, a.n_desc, item);
     const ExactDesc& pd = a.descs[a.order[lo]];
     const int64_t p = item - a.prefix[lo];
-    const int n = pd.n, nn = n * n, E1 = pd.E + 1;
+    const int n = pd.n, E1 = pd.E + 1;
     const Lay1 L = lay_terms<R, NW>(n, E1, pd.h_in_smem);
     R* pw = (R*)(sm + L.pw);
     R* g = (R*)(sm + L.g);
     double* red = (double*)(sm + L.red);
-    R* Hg = a.mats_h + pd.mat_off + p * nn;
+    R* Hg = a.mats_h + pd.mat_off + p * mat_slot<R>(n);
     R* Hr = pd.h_in_smem ? (R*)(sm + L.H) : Hg;
     for (int i = tid; i < NW * n; i += NT) g[i] = R(0);
     power_table<R, NT>(pd.X + p * n, n, E1, pw);
-    for (int i = tid; i < nn; i += NT) Hr[i] = R(0);
+    for (int64_t i = tid; i < mat_slot<R>(n); i += NT) Hr[i] = R(0);
     __syncthreads();
     R gabs = R(0);  // this thread's share of sum |gradient contributions|
     {
@@ -336,13 +346,16 @@ __global__ void __launch_bounds__(NT) exact_terms_kernel(StageArgs<R> a) {
       for (int q = 0; q < NW; ++q) ga += red[q];
       rec[4 * n] = ga;
     }
-    // full symmetric H from the upper triangle the sweep filled
-    for (int i = wid; i < n; i += NW)
-      for (int j = lane; j < n; j += 32) {
-        if (pd.h_in_smem) Hg[i * n + j] = i <= j ? Hr[i * n + j] : Hr[j * n + i];
-        else if (i > j) Hg[i * n + j] = Hg[j * n + i];
-      }
+    // the upper triangle the sweep filled (zeros below) to the workspace by
+    // one bulk copy; its shared-memory source is read before the next item
+    if (pd.h_in_smem && tid == 0) {
+      fence_proxy_async_smem();
+      bulk_s2g(Hg, Hr, (uint32_t)(mat_slot<R>(n) * sizeof(R)));
+      bulk_commit();
+      bulk_wait_read();
+    }
   }
+  if (tid == 0) bulk_wait_all();
 }
 
 // ------------------------------------------------------------------ stage 2
@@ -352,9 +365,15 @@ __global__ void __launch_bounds__(NT) exact_frame_kernel(StageArgs<R> a) {
   __shared__ int64_t s_item;
   __shared__ int s_flag;
   __shared__ double s_sc[4];
+  __shared__ __align__(8) uint64_t s_bar;
   constexpr bool kF64 = sizeof(R) == 8;
   constexpr int NW = NT / 32;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (tid == 0) {
+    mbar_init(&s_bar, 1);
+    mbar_init_fence();
+  }
+  uint32_t phase = 0;
   while (true) {
     const int64_t item = next_item(a.counter, &s_item);
     if (item >= a.total) break;
@@ -374,7 +393,7 @@ __global__ void __launch_bounds__(NT) exact_frame_kernel(StageArgs<R> a) {
     R* w = (R*)(sm + L.w);
     unsigned char* gb = a.gws + (size_t)blockIdx.x * a.gws_stride;
     R* Hr = pd.mats_in_smem ? (R*)(sm + L.Hr) : (R*)gb;
-    unsigned char* rest = pd.mats_in_smem ? nullptr : gb + (size_t)nn * sizeof(R);
+    unsigned char* rest = pd.mats_in_smem ? nullptr : gb + (size_t)mat_slot<R>(n) * sizeof(R);
     // FP64 factor storage, element (i, j) of the leading block at col(j)[i]:
     // in place in Hr (col(j) = row j of the symmetric Hr) for the FP64 form, a
     // packed column-major lower triangle for the FP32 form; X = L^{-1} with
@@ -384,11 +403,21 @@ __global__ void __launch_bounds__(NT) exact_frame_kernel(StageArgs<R> a) {
     auto col = [Ld, n, m](int j) -> double* {
       return kF64 ? Ld + (size_t)j * n : Ld + ((size_t)j * m - (size_t)j * (j - 1) / 2 - j);
     };
-    const R* Hg = a.mats_h + pd.mat_off + p * nn;
-    R* Wg = a.mats_w + pd.mat_off + p * nn;
+    const R* Hg = a.mats_h + pd.mat_off + p * mat_slot<R>(n);
+    R* Wg = a.mats_w + pd.mat_off + p * mat_slot<R>(n);
+    const uint32_t mat_bytes = (uint32_t)(mat_slot<R>(n) * sizeof(R));
     double* rec = a.vecs + pd.vec_off + p * vrec(n);
-    for (int i = wid; i < n; i += NW)
-      for (int j = lane; j < n; j += 32) Hr[i * n + j] = Hg[i * n + j];
+    // H (upper triangle) into shared memory by one bulk copy
+    if (pd.mats_in_smem) {
+      if (tid == 0) {
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&s_bar, mat_bytes);
+        bulk_g2s(Hr, Hg, mat_bytes, &s_bar);
+      }
+    } else {
+      for (int i = wid; i < n; i += NW)
+        for (int j = lane; j < n; j += 32) Hr[i * n + j] = Hg[i * n + j];
+    }
     // |g|, the zero-gradient test and the Householder vector (warp 0)
     if (wid == 0) {
       double gg = 0.0;
@@ -418,6 +447,14 @@ __global__ void __launch_bounds__(NT) exact_frame_kernel(StageArgs<R> a) {
         s_flag = 0;
       }
     }
+    if (pd.mats_in_smem) {
+      const bool ok = mbar_wait(&s_bar, phase, a.err);
+      phase ^= 1u;
+      if (!ok) return;
+    }
+    __syncthreads();
+    for (int i = wid; i < n; i += NW)  // mirror the upper triangle
+      for (int j = lane; j < i; j += 32) Hr[i * n + j] = Hr[j * n + i];
     __syncthreads();
     const double gn = s_sc[0], beta = s_sc[2], sgn = s_sc[3];
     if (s_sc[1] != 0.0) {
@@ -544,9 +581,22 @@ __global__ void __launch_bounds__(NT) exact_frame_kernel(StageArgs<R> a) {
       }
     }
     __syncthreads();
-    for (int i = wid; i < n; i += NW)  // W = P [M 0; 0 0] P
-      for (int j = lane; j < n; j += 32) Wg[i * n + j] = Hr[i * n + j] - (vr[i] * w[j] + w[i] * vr[j]);
+    if (pd.mats_in_smem) {  // W = P [M 0; 0 0] P in place, then one bulk copy out
+      for (int i = wid; i < n; i += NW)
+        for (int j = lane; j < n; j += 32) Hr[i * n + j] -= vr[i] * w[j] + w[i] * vr[j];
+      __syncthreads();
+      if (tid == 0) {
+        fence_proxy_async_smem();
+        bulk_s2g(Wg, Hr, mat_bytes);
+        bulk_commit();
+        bulk_wait_read();
+      }
+    } else {
+      for (int i = wid; i < n; i += NW)
+        for (int j = lane; j < n; j += 32) Wg[i * n + j] = Hr[i * n + j] - (vr[i] * w[j] + w[i] * vr[j]);
+    }
   }
+  if (tid == 0) bulk_wait_all();
 }
 
 // ------------------------------------------------------------------ stage 3
@@ -554,15 +604,21 @@ template <typename R, int NT>
 __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 640 / NT : 1) exact_third_kernel(StageArgs<R> a) {
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ int64_t s_item;
+  __shared__ __align__(8) uint64_t s_bar;
   constexpr int NW = NT / 32;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (tid == 0) {
+    mbar_init(&s_bar, 1);
+    mbar_init_fence();
+  }
+  uint32_t phase = 0;
   while (true) {
     const int64_t item = next_item(a.counter, &s_item);
     if (item >= a.total) break;
     const int lo = find_poly(a.prefix, a.n_desc, item);
     const ExactDesc& pd = a.descs[a.order[lo]];
     const int64_t p = item - a.prefix[lo];
-    const int n = pd.n, m = n - 1, nn = n * n, E1 = pd.E + 1;
+    const int n = pd.n, m = n - 1, E1 = pd.E + 1;
     const double* rec = a.vecs + pd.vec_off + p * vrec(n);
     if (rec[4 * n + 4] != kStOk) continue;  // flagged by stage 2 (same value for the whole CTA)
     const Lay3 L = lay_third<R, NW>(n, E1, pd.w_in_smem);
@@ -572,17 +628,25 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 640 / NT : 1) exact_third
     double* e = (double*)(sm + L.e);
     double* y = (double*)(sm + L.y);
     R* yr = (R*)(sm + L.yr);
-    const R* Wg = a.mats_w + pd.mat_off + p * nn;
+    const R* Wg = a.mats_w + pd.mat_off + p * mat_slot<R>(n);
     R* Ws = (R*)(sm + L.W);
     const R* W = pd.w_in_smem ? Ws : Wg;
+    if (pd.w_in_smem && tid == 0) {  // W into shared memory by one bulk copy
+      const uint32_t bytes = (uint32_t)(mat_slot<R>(n) * sizeof(R));
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(&s_bar, bytes);
+      bulk_g2s(Ws, Wg, bytes, &s_bar);
+    }
     for (int i = tid; i < NW * n; i += NT) c[i] = R(0);
     power_table<R, NT>(pd.X + p * n, n, E1, pw);
-    if (pd.w_in_smem)
-      for (int i = wid; i < n; i += NW)
-        for (int j = lane; j < n; j += 32) Ws[i * n + j] = Wg[i * n + j];
     for (int i = tid; i < n; i += NT) {
       v[i] = rec[n + i];
       e[i] = rec[2 * n + i];
+    }
+    if (pd.w_in_smem) {
+      const bool ok = mbar_wait(&s_bar, phase, a.err);
+      phase ^= 1u;
+      if (!ok) return;
     }
     __syncthreads();
     {
@@ -688,7 +752,7 @@ static polylab_status prepare_exact(ExactBatch* b) {
     if (!d.mats_in_smem) gstride = std::max(gstride, frame_gmem<R>(d.n));
     d.mat_off = mat;
     d.vec_off = vec;
-    mat += d.P * (int64_t)d.n * d.n;
+    mat += d.P * mat_slot<R>(d.n);
     vec += d.P * vrec(d.n);
   }
   for (int st = 0; st < 3; ++st) b->smem[st] = smem[st];
@@ -725,6 +789,7 @@ static polylab_status launch_stage_t(ExactBatch* b, int stage, cudaStream_t s) {
   a.assume_nonzero_x = b->opts.assume_nonzero_x;
   a.gws = b->gws;
   a.gws_stride = b->gws_stride;
+  a.err = b->err;
   PL_CUDA(cudaMemsetAsync(b->counter + stage, 0, sizeof(int), s));
   k<<<(unsigned)grid, NT, smem, s>>>(a);
   return launch_status(stage == 0 ? "exact_terms_kernel" : stage == 1 ? "exact_frame_kernel" : "exact_third_kernel");

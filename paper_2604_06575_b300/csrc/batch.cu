@@ -64,6 +64,8 @@ polylab_status exact_batch_init(ExactBatch* b, int n, const polylab_plan* const*
   PL_CUDA(cudaMallocAsync(&b->order, std::max(n, 1) * sizeof(int), s));
   PL_CUDA(cudaMallocAsync(&b->prefix, (n + 1) * sizeof(int64_t), s));
   PL_CUDA(cudaMallocAsync(&b->counter, 3 * sizeof(int), s));
+  PL_CUDA(cudaMallocAsync(&b->err, sizeof(int), s));
+  PL_CUDA(cudaMemsetAsync(b->err, 0, sizeof(int), s));
   PL_CUDA(cudaMallocAsync(&b->ws_h, std::max<size_t>(b->ws_mat_bytes, 16), s));
   PL_CUDA(cudaMallocAsync(&b->ws_w, std::max<size_t>(b->ws_mat_bytes, 16), s));
   PL_CUDA(cudaMallocAsync(&b->ws_v, std::max<size_t>(b->ws_vec_bytes, 16), s));
@@ -99,6 +101,8 @@ void exact_batch_release(ExactBatch* b, cudaStream_t s) {
   if (b->prefix) cudaFreeAsync(b->prefix, s);
   if (b->counter) cudaFreeAsync(b->counter, s);
   if (b->gws) cudaFreeAsync(b->gws, s);
+  if (b->err) cudaFreeAsync(b->err, s);
+  b->err = nullptr;
   if (b->ws_h) cudaFreeAsync(b->ws_h, s);
   if (b->ws_w) cudaFreeAsync(b->ws_w, s);
   if (b->ws_v) cudaFreeAsync(b->ws_v, s);
@@ -163,6 +167,14 @@ polylab_status polylab_batch_run(polylab_batch* b, polylab_stream stream) {
 polylab_status polylab_batch_run_stage(polylab_batch* b, int32_t stage, polylab_stream stream) {
   if (!b || stage < 0 || stage > 2) return POLYLAB_ERR_INVALID_ARG;
   return run_exact_stage(&b->b, stage, (cudaStream_t)stream);
+}
+
+polylab_status polylab_batch_check(polylab_batch* b, polylab_stream stream) {
+  if (!b) return POLYLAB_ERR_INVALID_ARG;
+  int flag = 0;
+  PL_CUDA(cudaMemcpyAsync(&flag, b->b.err, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+  PL_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  return flag ? POLYLAB_ERR_TIMEOUT : POLYLAB_OK;
 }
 
 polylab_status polylab_batch_get_config(const polylab_batch* b, polylab_batch_config* cfg) {

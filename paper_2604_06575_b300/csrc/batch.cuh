@@ -44,6 +44,7 @@ struct ExactBatch {
   int* order = nullptr;
   int64_t* prefix = nullptr;
   int* counter = nullptr;  // one work counter per stage
+  int* err = nullptr;      // device flag: a bounded wait of a stage expired
   int n_desc = 0;
   int64_t total = 0;
   size_t smem[3] = {0, 0, 0};

@@ -87,6 +87,7 @@ _lib.polylab_batch_create.argtypes = [C.c_int32, C.c_void_p, _PP, _PP, C.POINTER
                                       _PP, _PP, _PP, C.c_void_p, C.POINTER(C.c_void_p)]
 _lib.polylab_batch_run.argtypes = [C.c_void_p, C.c_void_p]
 _lib.polylab_batch_run_stage.argtypes = [C.c_void_p, C.c_int32, C.c_void_p]
+_lib.polylab_batch_check.argtypes = [C.c_void_p, C.c_void_p]
 _lib.polylab_batch_get_config.argtypes = [C.c_void_p, C.POINTER(_BatchConfig)]
 _lib.polylab_batch_set_config.argtypes = [C.c_void_p, C.POINTER(_BatchConfig), C.c_void_p]
 _lib.polylab_batch_autotune.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(_BatchConfig),
@@ -105,8 +106,8 @@ _lib.polylab_affine_normal_batched.argtypes = [C.c_int32, C.c_void_p, _PP, _PP, 
                                                C.POINTER(_AnOpts), _PP, _PP, _PP, C.c_void_p]
 for _f in ("polylab_plan_create", "polylab_plan_destroy", "polylab_eval_derivs", "polylab_affine_normal",
            "polylab_simplify", "polylab_mul", "polylab_add", "polylab_simplify_noalloc", "polylab_batch_create",
-           "polylab_batch_run", "polylab_batch_run_stage", "polylab_batch_get_config", "polylab_batch_set_config",
-           "polylab_batch_autotune", "polylab_batch_destroy", "polylab_affine_normal_batched",
+           "polylab_batch_run", "polylab_batch_run_stage", "polylab_batch_check", "polylab_batch_get_config",
+           "polylab_batch_set_config", "polylab_batch_autotune", "polylab_batch_destroy", "polylab_affine_normal_batched",
            "polylab_plan_gemm_info", "polylab_mlp_init",
            "polylab_mlp_data", "polylab_mlp_loss_grad", "polylab_mlp_adam", "polylab_mlp_pack"):
     getattr(_lib, _f).restype = C.c_int
@@ -114,7 +115,8 @@ for _f in ("polylab_plan_create", "polylab_plan_destroy", "polylab_eval_derivs",
 EXPORTED = ["polylab_status_string", "polylab_last_error", "polylab_simplify", "polylab_mul", "polylab_add",
             "polylab_plan_create", "polylab_plan_destroy", "polylab_plan_closure_size", "polylab_eval_derivs",
             "polylab_an_opts_default", "polylab_affine_normal", "polylab_simplify_noalloc", "polylab_batch_create",
-            "polylab_batch_run", "polylab_batch_run_stage", "polylab_batch_get_config", "polylab_batch_set_config",
+            "polylab_batch_run", "polylab_batch_run_stage", "polylab_batch_check", "polylab_batch_get_config",
+            "polylab_batch_set_config",
             "polylab_batch_autotune", "polylab_batch_destroy", "polylab_affine_normal_batched", "polylab_plan_gemm_info",
             "polylab_mlp_param_count", "polylab_mlp_init", "polylab_mlp_data", "polylab_mlp_loss_grad",
             "polylab_mlp_adam", "polylab_mlp_pack"]
@@ -356,6 +358,10 @@ class Batch:
         _check("polylab_batch_run", _lib.polylab_batch_run(self.h, _stream()))
 
     STAGES = ("terms", "frame", "third")
+
+    def check(self):
+        """Synchronise and raise if a bounded wait of any earlier run expired."""
+        _check("polylab_batch_check", _lib.polylab_batch_check(self.h, _stream()))
 
     def run_stage(self, stage: int):
         _check("polylab_batch_run_stage", _lib.polylab_batch_run_stage(self.h, stage, _stream()))

@@ -50,7 +50,7 @@ def test_batch_matches_single_calls_and_oracle(pl, batch_inputs, prec):
     plans = [pl.Plan(d) if i % 2 == 0 else None for i, d in enumerate(dps)]  # mix of given and built plans
     b = pl.Batch(dps, plans, Xd, opts)
     b.run()
-    torch.cuda.synchronize()
+    b.check()  # no bounded wait expired
     for i, (dp, X) in enumerate(zip(dps, Xd)):
         D1, Du1, in1 = pl.affine_normal(dp, X, opts)
         close(b.D[i], D1, TOL[prec])
@@ -102,6 +102,6 @@ def test_autotune_configs_agree_and_graph_replay(pl, batch_inputs):
         b.run()
     g.replay()
     g.replay()
-    torch.cuda.synchronize()
+    b.check()
     for d, r in zip(b.D, ref):
         close(d, r, TOL["fp64"])
