@@ -65,7 +65,8 @@ def parse():
     ap.add_argument("--forms", default="fp64,fp32", help="forms to time (profiling runs time one)")
     ap.add_argument("--rows-only", action="store_true", help="only the per-row measurements (profiling runs)")
     ap.add_argument("--config", default=None,
-                    help="threads,ctas_per_sm,order instead of autotuning (profiling runs)")
+                    help="threads,ctas_per_sm,order[,term_threads,chunks,terms_ctas,third_ctas] instead of "
+                         "autotuning (profiling runs)")
     return ap.parse_args()
 
 
@@ -366,7 +367,7 @@ def main():
     xv = [Xdev_flat[offs[i]:offs[i + 1]].view(-1, polys[i].n) for i in range(len(polys))]
     dv = [Ddev_flat[offs[i]:offs[i + 1]].view(-1, polys[i].n) for i in range(len(polys))]
     e2e_batch = pl.Batch(dps, plans, xv, opts[chosen], want_unit=False, want_info=False, D=dv)
-    e2e_batch.set_config(**{k: tuned[chosen][k] for k in ("threads", "ctas_per_sm", "order", "term_threads")})
+    e2e_batch.set_config(**{k: tuned[chosen][k] for k in pl.Batch.CONFIG_KEYS})
 
     def e2e_step():
         Xdev_flat.copy_(Xcat.view(-1), non_blocking=True)

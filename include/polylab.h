@@ -315,6 +315,16 @@ typedef struct {
   int32_t ctas_per_sm;
   int32_t order;
   int32_t term_threads;
+  /* chunks (1..32): the work is cut into this many chunks of equal estimated
+   * cost and the three stages run as a pipeline over three streams (stage 2
+   * of chunk c beside stage 1 of chunk c+1 and stage 3 of chunk c-1), so
+   * FP64-bound and shared-memory-bound work share the SMs; 1 runs the stages
+   * one after another.  terms_ctas, third_ctas: caps on resident CTAs per SM
+   * of the term sweeps (0: the occupancy limit), which leave room for the
+   * other stages' CTAs when pipelined. */
+  int32_t chunks;
+  int32_t terms_ctas;
+  int32_t third_ctas;
 } polylab_batch_config;
 
 polylab_status polylab_batch_create(int32_t n_polys, const polylab_poly* polys,
@@ -340,10 +350,12 @@ polylab_status polylab_batch_set_config(polylab_batch* batch, const polylab_batc
  * `reps` timed runs per trial, CUDA events on `stream`, synchronising):
  * term_threads in {64,128,256} timed over the two term sweeps, then threads in
  * {64,128,256} x ctas_per_sm in {occupancy, 2, 4} timed over the frame stage,
- * then order in {cost order, given order} timed over the whole run.  Keeps
- * the fastest of each step and returns the result (and the mean time of a
- * whole run in ms, if best_ms is not NULL).  The outputs hold the last run's
- * results. */
+ * then order in {cost order, given order} timed over the whole run, then
+ * pipelined runs (chunks 8 with residency caps {occupancy} and {4, 4, 3} for
+ * the term, frame and third stages, then chunks 4 with the better caps), kept
+ * if faster than the stages in sequence.  Keeps the fastest of each step and returns the result (and the
+ * mean time of a whole run in ms, if best_ms is not NULL).  The outputs hold
+ * the last run's results. */
 polylab_status polylab_batch_autotune(polylab_batch* batch, int32_t reps, polylab_stream stream,
                                       polylab_batch_config* chosen, float* best_ms);
 polylab_status polylab_batch_destroy(polylab_batch* batch, polylab_stream stream);

@@ -261,7 +261,7 @@ struct StageArgs {
   int n_desc;
   const int64_t* prefix;
   const int* order;
-  int64_t total;
+  int64_t item_begin, item_end;  // this launch's chunk of the work order
   int* counter;
   R* mats_h;  // per point n x n: H (stage 1 -> 2)
   R* mats_w;  // per point n x n: W (stage 2 -> 3)
@@ -294,8 +294,8 @@ __global__ void __launch_bounds__(NT) exact_terms_kernel(StageArgs<R> a) {
   constexpr int NW = NT / 32;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   while (true) {
-    const int64_t item = next_item(a.counter, &s_item);
-    if (item >= a.total) break;
+    const int64_t item = a.item_begin + next_item(a.counter, &s_item);
+    if (item >= a.item_end) break;
     const int lo = find_poly(a.prefix, a.n_desc, item);
     const ExactDesc& pd = a.descs[a.order[lo]];
     const int64_t p = item - a.prefix[lo];
@@ -375,8 +375,8 @@ __global__ void __launch_bounds__(NT) exact_frame_kernel(StageArgs<R> a) {
   }
   uint32_t phase = 0;
   while (true) {
-    const int64_t item = next_item(a.counter, &s_item);
-    if (item >= a.total) break;
+    const int64_t item = a.item_begin + next_item(a.counter, &s_item);
+    if (item >= a.item_end) break;
     const int lo = find_poly(a.prefix, a.n_desc, item);
     const ExactDesc& pd = a.descs[a.order[lo]];
     const int64_t p = item - a.prefix[lo];
@@ -601,7 +601,7 @@ __global__ void __launch_bounds__(NT) exact_frame_kernel(StageArgs<R> a) {
 
 // ------------------------------------------------------------------ stage 3
 template <typename R, int NT>
-__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 640 / NT : 1) exact_third_kernel(StageArgs<R> a) {
+__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 1024 / NT : 1) exact_third_kernel(StageArgs<R> a) {
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ int64_t s_item;
   __shared__ __align__(8) uint64_t s_bar;
@@ -613,8 +613,8 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 640 / NT : 1) exact_third
   }
   uint32_t phase = 0;
   while (true) {
-    const int64_t item = next_item(a.counter, &s_item);
-    if (item >= a.total) break;
+    const int64_t item = a.item_begin + next_item(a.counter, &s_item);
+    if (item >= a.item_end) break;
     const int lo = find_poly(a.prefix, a.n_desc, item);
     const ExactDesc& pd = a.descs[a.order[lo]];
     const int64_t p = item - a.prefix[lo];
@@ -763,25 +763,29 @@ static polylab_status prepare_exact(ExactBatch* b) {
 }
 
 template <typename R, int NT>
-static polylab_status launch_stage_t(ExactBatch* b, int stage, cudaStream_t s) {
+static polylab_status launch_stage_t(ExactBatch* b, int stage, int chunk, cudaStream_t s) {
   void (*k)(StageArgs<R>) = stage == 0   ? exact_terms_kernel<R, NT>
                             : stage == 1 ? exact_frame_kernel<R, NT>
                                          : exact_third_kernel<R, NT>;
+  const int64_t i0 = b->chunk_begin[chunk], i1 = b->chunk_begin[chunk + 1];
+  if (i1 <= i0) return POLYLAB_OK;
   const size_t smem = b->smem[stage];
   PL_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   PL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NT, smem));
   per_sm = std::max(1, per_sm);
-  if (stage == 1 && b->cfg.ctas_per_sm > 0) per_sm = std::min(per_sm, b->cfg.ctas_per_sm);
-  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(b->total, (int64_t)num_sms() * per_sm));
+  const int cap = stage == 0 ? b->cfg.terms_ctas : stage == 1 ? b->cfg.ctas_per_sm : b->cfg.third_ctas;
+  if (cap > 0) per_sm = std::min(per_sm, cap);
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(i1 - i0, (int64_t)num_sms() * per_sm));
   if (stage == 1 && b->gws_stride > 0 && (size_t)grid * b->gws_stride > b->gws_bytes) return POLYLAB_ERR_UNSUPPORTED;
   StageArgs<R> a{};
   a.descs = b->descs;
   a.n_desc = b->n_desc;
   a.prefix = b->prefix;
   a.order = b->order;
-  a.total = b->total;
-  a.counter = b->counter + stage;
+  a.item_begin = i0;
+  a.item_end = i1;
+  a.counter = b->counter + 3 * chunk + stage;
   a.mats_h = (R*)b->ws_h;
   a.mats_w = (R*)b->ws_w;
   a.vecs = (double*)b->ws_v;
@@ -790,26 +794,60 @@ static polylab_status launch_stage_t(ExactBatch* b, int stage, cudaStream_t s) {
   a.gws = b->gws;
   a.gws_stride = b->gws_stride;
   a.err = b->err;
-  PL_CUDA(cudaMemsetAsync(b->counter + stage, 0, sizeof(int), s));
+  PL_CUDA(cudaMemsetAsync(a.counter, 0, sizeof(int), s));
   k<<<(unsigned)grid, NT, smem, s>>>(a);
   return launch_status(stage == 0 ? "exact_terms_kernel" : stage == 1 ? "exact_frame_kernel" : "exact_third_kernel");
 }
 
 template <typename R>
-static polylab_status launch_stage(ExactBatch* b, int stage, cudaStream_t s) {
+static polylab_status launch_stage(ExactBatch* b, int stage, int chunk, cudaStream_t s) {
   const int nt = stage == 1 ? b->cfg.threads : b->cfg.term_threads;
-  if (nt == 64) return launch_stage_t<R, 64>(b, stage, s);
-  if (nt == 128) return launch_stage_t<R, 128>(b, stage, s);
-  return launch_stage_t<R, 256>(b, stage, s);
+  if (nt == 64) return launch_stage_t<R, 64>(b, stage, chunk, s);
+  if (nt == 128) return launch_stage_t<R, 128>(b, stage, chunk, s);
+  return launch_stage_t<R, 256>(b, stage, chunk, s);
+}
+
+static polylab_status launch_chunk(ExactBatch* b, int stage, int chunk, cudaStream_t s) {
+  return b->opts.prec == POLYLAB_FP32 ? launch_stage<float>(b, stage, chunk, s)
+                                      : launch_stage<double>(b, stage, chunk, s);
 }
 
 polylab_status run_exact_stage(ExactBatch* b, int stage, cudaStream_t s) {
   if (b->total == 0) return POLYLAB_OK;
-  return b->opts.prec == POLYLAB_FP32 ? launch_stage<float>(b, stage, s) : launch_stage<double>(b, stage, s);
+  const int C = (int)b->chunk_begin.size() - 1;
+  for (int c = 0; c < C; ++c) PL_TRY(launch_chunk(b, stage, c, s));
+  return POLYLAB_OK;
 }
 
+// One run.  With one chunk the stages follow each other on `s`.  Otherwise
+// stage 1 of every chunk runs on `s`, stage 2 on side[0] and stage 3 on
+// side[1], each chunk's stage waiting on an event of the previous stage of the
+// same chunk: the side streams fork from and join back to `s`, so the run is
+// ordered like any single-stream work on `s` and can be captured in a graph.
 polylab_status run_exact_batch(ExactBatch* b, cudaStream_t s) {
-  for (int st = 0; st < 3; ++st) PL_TRY(run_exact_stage(b, st, s));
+  if (b->total == 0) return POLYLAB_OK;
+  const int C = (int)b->chunk_begin.size() - 1;
+  if (C <= 1) {
+    for (int st = 0; st < 3; ++st) PL_TRY(run_exact_stage(b, st, s));
+    return POLYLAB_OK;
+  }
+  cudaEvent_t* ev = b->events.data();
+  cudaStream_t str[3] = {s, b->side[0], b->side[1]};
+  cudaEvent_t fork = ev[3 * kMaxChunks], join1 = ev[3 * kMaxChunks + 1], join2 = ev[3 * kMaxChunks + 2];
+  PL_CUDA(cudaEventRecord(fork, s));
+  PL_CUDA(cudaStreamWaitEvent(str[1], fork, 0));
+  PL_CUDA(cudaStreamWaitEvent(str[2], fork, 0));
+  for (int c = 0; c < C; ++c) {
+    for (int st = 0; st < 3; ++st) {
+      if (st > 0) PL_CUDA(cudaStreamWaitEvent(str[st], ev[3 * c + st - 1], 0));
+      PL_TRY(launch_chunk(b, st, c, str[st]));
+      if (st < 2) PL_CUDA(cudaEventRecord(ev[3 * c + st], str[st]));
+    }
+  }
+  PL_CUDA(cudaEventRecord(join1, str[1]));
+  PL_CUDA(cudaEventRecord(join2, str[2]));
+  PL_CUDA(cudaStreamWaitEvent(s, join1, 0));
+  PL_CUDA(cudaStreamWaitEvent(s, join2, 0));
   return POLYLAB_OK;
 }
 

@@ -21,10 +21,37 @@ polylab_status exact_batch_upload_order(ExactBatch* b, cudaStream_t s) {
   b->host_prefix.assign(n + 1, 0);
   for (int i = 0; i < n; ++i) b->host_prefix[i + 1] = b->host_prefix[i] + b->host_descs[ord[i]].P;
   b->total = b->host_prefix[n];
+  exact_batch_chunks(b);
   PL_CUDA(cudaMemcpyAsync(b->order, ord.data(), n * sizeof(int), cudaMemcpyHostToDevice, s));
   PL_CUDA(cudaMemcpyAsync(b->prefix, b->host_prefix.data(), (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
   PL_CUDA(cudaStreamSynchronize(s));  // host vectors may change after this returns
   return POLYLAB_OK;
+}
+
+// Chunk boundaries in the work order at equal shares of the estimated cost
+// (items are whole points; a chunk may be empty).
+void exact_batch_chunks(ExactBatch* b) {
+  const int C = std::max(1, std::min(b->cfg.chunks, kMaxChunks));
+  const int n = b->n_desc;
+  std::vector<double> cum(n + 1, 0.0);
+  for (int i = 0; i < n; ++i) {
+    const ExactDesc& d = b->host_descs[b->host_order[i]];
+    cum[i + 1] = cum[i] + exact_point_cost(d, d.max_support) * (double)d.P;
+  }
+  b->chunk_begin.assign(C + 1, b->total);
+  b->chunk_begin[0] = 0;
+  int i = 0;
+  for (int c = 1; c < C; ++c) {
+    const double target = cum[n] * c / C;
+    while (i < n && cum[i + 1] <= target) ++i;
+    int64_t item = b->host_prefix[i];
+    if (i < n) {
+      const ExactDesc& d = b->host_descs[b->host_order[i]];
+      const double per = exact_point_cost(d, d.max_support);
+      if (per > 0) item += std::min<int64_t>(d.P, (int64_t)((target - cum[i]) / per));
+    }
+    b->chunk_begin[c] = std::max(b->chunk_begin[c - 1], std::min(item, b->total));
+  }
 }
 
 static int default_threads(const ExactBatch* b) {
@@ -63,7 +90,10 @@ polylab_status exact_batch_init(ExactBatch* b, int n, const polylab_plan* const*
   PL_CUDA(cudaMallocAsync(&b->descs, std::max(n, 1) * sizeof(ExactDesc), s));
   PL_CUDA(cudaMallocAsync(&b->order, std::max(n, 1) * sizeof(int), s));
   PL_CUDA(cudaMallocAsync(&b->prefix, (n + 1) * sizeof(int64_t), s));
-  PL_CUDA(cudaMallocAsync(&b->counter, 3 * sizeof(int), s));
+  PL_CUDA(cudaMallocAsync(&b->counter, 3 * kMaxChunks * sizeof(int), s));
+  for (auto& st : b->side) PL_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  b->events.resize(3 * kMaxChunks + 3);
+  for (auto& e : b->events) PL_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   PL_CUDA(cudaMallocAsync(&b->err, sizeof(int), s));
   PL_CUDA(cudaMemsetAsync(b->err, 0, sizeof(int), s));
   PL_CUDA(cudaMallocAsync(&b->ws_h, std::max<size_t>(b->ws_mat_bytes, 16), s));
@@ -101,6 +131,15 @@ void exact_batch_release(ExactBatch* b, cudaStream_t s) {
   if (b->prefix) cudaFreeAsync(b->prefix, s);
   if (b->counter) cudaFreeAsync(b->counter, s);
   if (b->gws) cudaFreeAsync(b->gws, s);
+  for (auto& st : b->side) {
+    if (st) {
+      cudaStreamSynchronize(st);
+      cudaStreamDestroy(st);
+    }
+    st = nullptr;
+  }
+  for (auto& e : b->events) cudaEventDestroy(e);
+  b->events.clear();
   if (b->err) cudaFreeAsync(b->err, s);
   b->err = nullptr;
   if (b->ws_h) cudaFreeAsync(b->ws_h, s);
@@ -183,6 +222,9 @@ polylab_status polylab_batch_get_config(const polylab_batch* b, polylab_batch_co
   cfg->ctas_per_sm = b->b.cfg.ctas_per_sm;
   cfg->order = b->b.cfg.order;
   cfg->term_threads = b->b.cfg.term_threads;
+  cfg->chunks = b->b.cfg.chunks;
+  cfg->terms_ctas = b->b.cfg.terms_ctas;
+  cfg->third_ctas = b->b.cfg.third_ctas;
   return POLYLAB_OK;
 }
 
@@ -190,10 +232,16 @@ polylab_status polylab_batch_set_config(polylab_batch* b, const polylab_batch_co
   if (!b || !cfg) return POLYLAB_ERR_INVALID_ARG;
   auto ok_threads = [](int t) { return t == 64 || t == 128 || t == 256; };
   if (!ok_threads(cfg->threads) || !ok_threads(cfg->term_threads)) return POLYLAB_ERR_INVALID_ARG;
-  if (cfg->ctas_per_sm < 0 || cfg->ctas_per_sm > 32 || (cfg->order != 0 && cfg->order != 1))
+  auto ok_cap = [](int c) { return c >= 0 && c <= 32; };
+  if (!ok_cap(cfg->ctas_per_sm) || !ok_cap(cfg->terms_ctas) || !ok_cap(cfg->third_ctas) ||
+      (cfg->order != 0 && cfg->order != 1) || cfg->chunks < 1 || cfg->chunks > kMaxChunks)
     return POLYLAB_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   const bool reorder = cfg->order != b->b.cfg.order;
+  const bool rechunk = cfg->chunks != b->b.cfg.chunks;
+  b->b.cfg.chunks = cfg->chunks;
+  b->b.cfg.terms_ctas = cfg->terms_ctas;
+  b->b.cfg.third_ctas = cfg->third_ctas;
   const bool relayout = cfg->threads != b->b.cfg.threads || cfg->term_threads != b->b.cfg.term_threads;
   b->b.cfg.threads = cfg->threads;
   b->b.cfg.term_threads = cfg->term_threads;
@@ -201,6 +249,7 @@ polylab_status polylab_batch_set_config(polylab_batch* b, const polylab_batch_co
   b->b.cfg.order = cfg->order;
   if (relayout) PL_TRY(exact_batch_relayout(&b->b, s));
   if (reorder) PL_TRY(exact_batch_upload_order(&b->b, s));
+  else if (rechunk) exact_batch_chunks(&b->b);
   return POLYLAB_OK;
 }
 
@@ -209,7 +258,8 @@ polylab_status polylab_batch_autotune(polylab_batch* b, int32_t reps, polylab_st
   if (!b || reps < 1) return POLYLAB_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   ExactBatch* eb = &b->b;
-  polylab_batch_config cur{eb->cfg.threads, eb->cfg.ctas_per_sm, eb->cfg.order, eb->cfg.term_threads};
+  polylab_batch_config cur{eb->cfg.threads,      eb->cfg.ctas_per_sm, eb->cfg.order,     eb->cfg.term_threads,
+                           eb->cfg.chunks,       eb->cfg.terms_ctas,  eb->cfg.third_ctas};
   cudaEvent_t e0, e1;
   PL_CUDA(cudaEventCreate(&e0));
   PL_CUDA(cudaEventCreate(&e1));
@@ -217,7 +267,9 @@ polylab_status polylab_batch_autotune(polylab_batch* b, int32_t reps, polylab_st
   auto time_stages = [&](int s0, int s1, float* ms_out) -> polylab_status {
     for (int r = 0; r <= reps; ++r) {
       if (r == 1) cudaEventRecord(e0, s);
-      for (int st = s0; st <= s1; ++st) PL_TRY(run_exact_stage(eb, st, s));
+      if (s0 == 0 && s1 == 2) PL_TRY(run_exact_batch(eb, s));
+      else
+        for (int st = s0; st <= s1; ++st) PL_TRY(run_exact_stage(eb, st, s));
     }
     cudaEventRecord(e1, s);
     PL_CUDA(cudaEventSynchronize(e1));
@@ -275,7 +327,7 @@ polylab_status polylab_batch_autotune(polylab_batch* b, int32_t reps, polylab_st
     }
     cur = best;
   }
-  // 3. work order, timed over the whole pipeline
+  // 3. work order, timed over the whole run
   if (st == POLYLAB_OK) {
     polylab_batch_config best = cur;
     best_t = 1e30f;
@@ -287,6 +339,42 @@ polylab_status polylab_batch_autotune(polylab_batch* b, int32_t reps, polylab_st
         best_t = t;
         best = c;
       }
+    }
+    cur = best;
+  }
+  // 4. pipelined runs: per-stage residency caps (term sweeps, frame, third)
+  // that let the stages share each SM, then the number of chunks; kept only
+  // when faster than the stages one after another
+  if (st == POLYLAB_OK) {
+    polylab_batch_config best = cur;
+    const int caps[][3] = {{0, 0, 0}, {4, 4, 3}};
+    polylab_batch_config piped = cur;
+    float piped_t = 1e30f;
+    for (const auto& cp : caps) {
+      polylab_batch_config c = cur;
+      c.chunks = 8;
+      c.terms_ctas = cp[0];
+      c.ctas_per_sm = cp[1];
+      c.third_ctas = cp[2];
+      if ((st = trial(c, 0, 2, &t)) != POLYLAB_OK) break;
+      if (t < piped_t) {
+        piped_t = t;
+        piped = c;
+      }
+    }
+    for (int chunks : {4}) {
+      if (st != POLYLAB_OK) break;
+      polylab_batch_config c = piped;
+      c.chunks = chunks;
+      if ((st = trial(c, 0, 2, &t)) != POLYLAB_OK) break;
+      if (t < piped_t) {
+        piped_t = t;
+        piped = c;
+      }
+    }
+    if (piped_t < best_t) {
+      best_t = piped_t;
+      best = piped;
     }
     cur = best;
   }

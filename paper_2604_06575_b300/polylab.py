@@ -54,7 +54,8 @@ class _AnOpts(C.Structure):
 
 class _BatchConfig(C.Structure):
     _fields_ = [("threads", C.c_int32), ("ctas_per_sm", C.c_int32), ("order", C.c_int32),
-                ("term_threads", C.c_int32)]
+                ("term_threads", C.c_int32), ("chunks", C.c_int32), ("terms_ctas", C.c_int32),
+                ("third_ctas", C.c_int32)]
 
 
 INFO_DTYPE = np.dtype([("grad_norm", "<f8"), ("logdet", "<f8"), ("flags", "<i4"), ("hv_evals", "<i4"),
@@ -366,22 +367,26 @@ class Batch:
     def run_stage(self, stage: int):
         _check("polylab_batch_run_stage", _lib.polylab_batch_run_stage(self.h, stage, _stream()))
 
+    CONFIG_KEYS = ("threads", "ctas_per_sm", "order", "term_threads", "chunks", "terms_ctas", "third_ctas")
+
     def config(self):
         c = _BatchConfig()
         _check("polylab_batch_get_config", _lib.polylab_batch_get_config(self.h, C.byref(c)))
-        return dict(threads=c.threads, ctas_per_sm=c.ctas_per_sm, order=c.order, term_threads=c.term_threads)
+        return {k: getattr(c, k) for k in self.CONFIG_KEYS}
 
-    def set_config(self, threads, ctas_per_sm, order, term_threads=None):
-        if term_threads is None:
-            term_threads = self.config()["term_threads"]
-        c = _BatchConfig(threads, ctas_per_sm, order, term_threads)
+    def set_config(self, threads, ctas_per_sm, order, term_threads=None, chunks=None, terms_ctas=None,
+                   third_ctas=None):
+        """Keys left as None keep their current value."""
+        cur = self.config()
+        given = dict(threads=threads, ctas_per_sm=ctas_per_sm, order=order, term_threads=term_threads,
+                     chunks=chunks, terms_ctas=terms_ctas, third_ctas=third_ctas)
+        c = _BatchConfig(*[cur[k] if given[k] is None else given[k] for k in self.CONFIG_KEYS])
         _check("polylab_batch_set_config", _lib.polylab_batch_set_config(self.h, C.byref(c), _stream()))
 
     def autotune(self, reps=2):
         c, t = _BatchConfig(), C.c_float()
         _check("polylab_batch_autotune", _lib.polylab_batch_autotune(self.h, reps, _stream(), C.byref(c), C.byref(t)))
-        return (dict(threads=c.threads, ctas_per_sm=c.ctas_per_sm, order=c.order, term_threads=c.term_threads),
-                float(t.value))
+        return {k: getattr(c, k) for k in self.CONFIG_KEYS}, float(t.value)
 
     def close(self):
         if self.h:
