@@ -116,7 +116,10 @@ __device__ __forceinline__ void ldlt_block(int m, Col col, double* __restrict__ 
   auto pivot = [&](int c) {  // warp 0
     double* cc = col(c);
     const double d = cc[c];
-    if (!(d > 0.0) || !isfinite(d)) {
+    // positive and finite, tested on the bit pattern (sign clear, not zero,
+    // exponent below all-ones) on the integer pipe
+    const long long bits = __double_as_longlong(d);
+    if (!(bits > 0 && bits < 0x7FF0000000000000ll)) {
       if (lane == 0) *flag = 1;
       return;
     }
@@ -486,7 +489,9 @@ __global__ void __launch_bounds__(NT) exact_frame_kernel(StageArgs<R> a) {
       for (int i = tid; i < m; i += NT) Hr[i * n + i] += a.r;
     } else {
       for (int j = wid; j < m; j += NW)
-        for (int i = j + lane; i < m; i += 32) col(j)[i] = (double)Hr[j * n + i] + (i == j ? a.r : 0.0);
+        for (int i = j + lane; i < m; i += 32) col(j)[i] = (double)Hr[j * n + i];
+      __syncthreads();
+      for (int i = tid; i < m; i += NT) col(i)[i] += a.r;
     }
     __syncthreads();
     ldlt_block<NT>(m, col, uc, dv, di, &s_flag);
@@ -521,20 +526,19 @@ __global__ void __launch_bounds__(NT) exact_frame_kernel(StageArgs<R> a) {
     // right-looking: after step k row k of X is final; X_ij -= l_ik X_kj for
     // j <= k < i, the (m-k-1) x (k+1) rectangle enumerated over the CTA
     for (int k = 0; k + 1 < m; ++k) {
-      const int rows = m - k - 1, total = rows * (k + 1);
-      const float rinv = 1.0f / (float)rows;
-      for (int q = tid; q < total; q += NT) {
-        int j = (int)((float)q * rinv);
-        int i0 = q - j * rows;
-        if (i0 < 0) {
-          --j;
-          i0 += rows;
-        } else if (i0 >= rows) {
-          ++j;
+      const int rows = m - k - 1;
+      // thread tid starts at q = tid = j * rows + i0 and steps by NT
+      const int dj = NT / rows, di0 = NT - dj * rows;
+      int j = tid / rows, i0 = tid - j * rows;
+      const R* lk = Hr + k * n + k + 1;
+      while (j <= k) {
+        Xs[j * xs + k + 1 + i0] -= lk[i0] * Xs[j * xs + k];
+        j += dj;
+        i0 += di0;
+        if (i0 >= rows) {
           i0 -= rows;
+          ++j;
         }
-        const int i = k + 1 + i0;
-        Xs[j * xs + i] -= Hr[k * n + i] * Xs[j * xs + k];
       }
       __syncthreads();
     }
@@ -543,13 +547,12 @@ __global__ void __launch_bounds__(NT) exact_frame_kernel(StageArgs<R> a) {
       for (int i = j + lane; i < m; i += 32) Xs[j * xs + i] *= sq[i];
     __syncthreads();
     // M = H_T^{-1} = X'^T X', upper triangle into Hr (L no longer needed)
-    for (int idx = tid; idx < m * m; idx += NT) {
-      const int i = idx / m, j = idx - i * m;
-      if (j < i) continue;
-      R acc = R(0);
-      for (int k = j; k < m; ++k) acc += Xs[i * xs + k] * Xs[j * xs + k];
-      Hr[i * n + j] = acc;
-    }
+    for (int i = wid; i < m; i += NW)
+      for (int j = i + lane; j < m; j += 32) {
+        R acc = R(0);
+        for (int k = j; k < m; ++k) acc += Xs[i * xs + k] * Xs[j * xs + k];
+        Hr[i * n + j] = acc;
+      }
     __syncthreads();
     for (int i = wid; i < n; i += NW)  // Hr <- [M 0; 0 0], full symmetric, in place
       for (int j = lane; j < n; j += 32) {
