@@ -185,15 +185,23 @@ struct Bump {
 // `in_smem` false: the n x n matrices live in global memory instead.
 
 struct Lay1 {
-  size_t pw, g, red, H, total;
+  size_t pw, g, red, ix, gs, ga, mv, H, total;
 };
+// `gather`: room for the gather form (1/x, gradient sums, one chunk of
+// monomial values)
 template <typename R, int NW>
-__host__ __device__ Lay1 lay_terms(int n, int E1, bool in_smem) {
+__host__ __device__ Lay1 lay_terms(int n, int E1, bool in_smem, bool gather) {
   Lay1 L{};
   Bump b;
   L.pw = b.take((size_t)n * E1 * sizeof(R));
   L.g = b.take((size_t)NW * n * sizeof(R));  // one replica per warp
   L.red = b.take(40 * 8);
+  if (gather) {
+    L.ix = b.take(n * sizeof(R));
+    L.gs = b.take(n * sizeof(R));
+    L.ga = b.take(n * sizeof(R));
+    L.mv = b.take((size_t)kGatherChunk * sizeof(R));
+  }
   L.H = in_smem ? b.take((size_t)mat_slot<R>(n) * sizeof(R)) : 0;
   L.total = b.o;
   return L;
@@ -290,6 +298,15 @@ __device__ __forceinline__ void write_failed(const ExactDesc& pd, int64_t p, int
 }  // namespace
 
 // ------------------------------------------------------------------ stage 1
+// Gradient and Hessian by one of two sweeps over the term list:
+//  gather  (the plan has a gather form and every |x_v| is in the range where
+//          monomial values and 1/x stay normal): per chunk of terms, the
+//          monomial values m_t into shared memory, then each thread sums a
+//          contiguous run of the entry-sorted records coef * m_t in registers
+//          and adds a run's sum to its entry when the entry changes; entries
+//          are scaled by 1/x_i (1/x_j) at the end;
+//  scatter (otherwise): every term's derivative values are added to their
+//          entries one by one (per-warp gradient replicas).
 template <typename R, int NT>
 __global__ void __launch_bounds__(NT) exact_terms_kernel(StageArgs<R> a) {
   extern __shared__ __align__(16) unsigned char sm[];
@@ -302,19 +319,87 @@ __global__ void __launch_bounds__(NT) exact_terms_kernel(StageArgs<R> a) {
     const int lo = find_poly(a.prefix, a.n_desc, item);
     const ExactDesc& pd = a.descs[a.order[lo]];
     const int64_t p = item - a.prefix[lo];
-    const int n = pd.n, E1 = pd.E + 1;
-    const Lay1 L = lay_terms<R, NW>(n, E1, pd.h_in_smem);
+    const int n = pd.n, nn = n * n, E1 = pd.E + 1;
+    const Lay1 L = lay_terms<R, NW>(n, E1, pd.h_in_smem, pd.gather != nullptr);
     R* pw = (R*)(sm + L.pw);
     R* g = (R*)(sm + L.g);
     double* red = (double*)(sm + L.red);
     R* Hg = a.mats_h + pd.mat_off + p * mat_slot<R>(n);
     R* Hr = pd.h_in_smem ? (R*)(sm + L.H) : Hg;
-    for (int i = tid; i < NW * n; i += NT) g[i] = R(0);
-    power_table<R, NT>(pd.X + p * n, n, E1, pw);
+    const double* X = pd.X + p * n;
+    bool in_range = true;
+    for (int i = tid; i < n; i += NT) {
+      const double ax = fabs(X[i]);
+      in_range &= ax >= pd.x_lo && ax <= pd.x_hi;
+    }
+    const bool gather = __syncthreads_and(in_range && pd.gather != nullptr) != 0;
+    R* ix = (R*)(sm + L.ix);
+    R* gs = (R*)(sm + L.gs);
+    R* ga = (R*)(sm + L.ga);
+    R* mv = (R*)(sm + L.mv);
+    if (gather) {
+      for (int i = tid; i < n; i += NT) {
+        ix[i] = R(1) / R(X[i]);
+        gs[i] = R(0);
+        ga[i] = R(0);
+      }
+    } else {
+      for (int i = tid; i < NW * n; i += NT) g[i] = R(0);
+    }
+    power_table<R, NT>(X, n, E1, pw);
     for (int64_t i = tid; i < mat_slot<R>(n); i += NT) Hr[i] = R(0);
     __syncthreads();
+    double* rec = a.vecs + pd.vec_off + p * vrec(n);
     R gabs = R(0);  // this thread's share of sum |gradient contributions|
-    {
+    if (gather) {
+      auto flush = [&](int e, R acc, R aacc) {
+        if (e < 0 || e == (int)kGatherPad) return;  // nothing yet, or padding
+        if (e >= nn) {
+          atomicAdd(&gs[e - nn], acc);
+          atomicAdd(&ga[e - nn], aacc);
+        } else {
+          atomicAdd(&Hr[e], acc);
+        }
+      };
+      for (int c = 0; c < pd.n_gchunks; ++c) {
+        const int64_t t0 = (int64_t)c * kGatherChunk, t1 = min(pd.m, t0 + kGatherChunk);
+        for (int64_t t = t0 + tid; t < t1; t += NT) mv[t - t0] = term_value<R>(load_term(pd.terms, t), pw, E1);
+        __syncthreads();
+        const int64_t r0 = pd.gather_chunk[c];
+        const int Lc = (int)((pd.gather_chunk[c + 1] - r0) / kGatherStreams);
+        const uint32_t* recs = pd.gather + r0;
+        for (int st = tid; st < kGatherStreams; st += NT) {
+          int cur = -1;
+          R acc = R(0), aacc = R(0);
+          for (int k = 0; k < Lc; k += kGatherUnroll) {
+            uint32_t rr[kGatherUnroll];
+#pragma unroll
+            for (int u = 0; u < kGatherUnroll; ++u) rr[u] = __ldg(recs + (int64_t)(k + u) * kGatherStreams + st);
+#pragma unroll
+            for (int u = 0; u < kGatherUnroll; ++u) {
+              const int e = (int)((rr[u] >> 11) & 0x3fffu);
+              const R v = R(rr[u] >> 25) * mv[rr[u] & 0x7ffu];
+              if (e != cur) {
+                flush(cur, acc, aacc);
+                cur = e;
+                acc = R(0);
+                aacc = R(0);
+              }
+              acc += v;
+              aacc += fabs(v);
+            }
+          }
+          flush(cur, acc, aacc);
+        }
+        __syncthreads();
+      }
+      for (int i = wid; i < n; i += NW)
+        for (int j = i + lane; j < n; j += 32) Hr[i * n + j] *= ix[i] * ix[j];
+      for (int i = tid; i < n; i += NT) {
+        rec[i] = (double)(gs[i] * ix[i]);
+        gabs += ga[i] * fabs(ix[i]);
+      }
+    } else {
       R* gw = g + wid * n;
       auto emit = [&](int kind, int i, int j, R val) {
         if (kind == 1) {
@@ -333,21 +418,20 @@ __global__ void __launch_bounds__(NT) exact_terms_kernel(StageArgs<R> a) {
           term_derivs_group<R, 2, K>(tr, pw, E1, emit);
         }
       });
+      __syncthreads();
+      for (int i = tid; i < n; i += NT) {
+        R s = g[i];
+        for (int q = 1; q < NW; ++q) s += g[q * n + i];
+        rec[i] = (double)s;
+      }
     }
-    __syncthreads();
-    double* rec = a.vecs + pd.vec_off + p * vrec(n);
     gabs = warp_sum(gabs);
     if (lane == 0) red[wid] = (double)gabs;
-    for (int i = tid; i < n; i += NT) {
-      R s = g[i];
-      for (int q = 1; q < NW; ++q) s += g[q * n + i];
-      rec[i] = (double)s;
-    }
     __syncthreads();
     if (tid == 0) {
-      double ga = 0.0;
-      for (int q = 0; q < NW; ++q) ga += red[q];
-      rec[4 * n] = ga;
+      double gsum = 0.0;
+      for (int q = 0; q < NW; ++q) gsum += red[q];
+      rec[4 * n] = gsum;
     }
     // the upper triangle the sweep filled (zeros below) to the workspace by
     // one bulk copy; its shared-memory source is read before the next item
@@ -721,17 +805,17 @@ namespace {
 constexpr size_t kSmemCap = 200 * 1024;
 
 template <typename R, int NW>
-size_t lay_bytes(int stage, int n, int E1, bool in_smem) {
-  if (stage == 0) return lay_terms<R, NW>(n, E1, in_smem).total;
+size_t lay_bytes(int stage, int n, int E1, bool in_smem, bool gather) {
+  if (stage == 0) return lay_terms<R, NW>(n, E1, in_smem, gather).total;
   if (stage == 1) return lay_frame<R>(n, in_smem).total;
   return lay_third<R, NW>(n, E1, in_smem).total;
 }
 
 template <typename R>
-size_t stage_bytes(int stage, int threads, int n, int E1, bool in_smem) {
-  if (threads == 64) return lay_bytes<R, 2>(stage, n, E1, in_smem);
-  if (threads == 128) return lay_bytes<R, 4>(stage, n, E1, in_smem);
-  return lay_bytes<R, 8>(stage, n, E1, in_smem);
+size_t stage_bytes(int stage, int threads, int n, int E1, bool in_smem, bool gather) {
+  if (threads == 64) return lay_bytes<R, 2>(stage, n, E1, in_smem, gather);
+  if (threads == 128) return lay_bytes<R, 4>(stage, n, E1, in_smem, gather);
+  return lay_bytes<R, 8>(stage, n, E1, in_smem, gather);
 }
 
 }  // namespace
@@ -743,11 +827,13 @@ static polylab_status prepare_exact(ExactBatch* b) {
   for (auto& d : b->host_descs) {
     const int E1 = d.E + 1;
     const int tt = b->cfg.term_threads, ft = b->cfg.threads;
-    d.h_in_smem = stage_bytes<R>(0, tt, d.n, E1, true) <= kSmemCap ? 1 : 0;
-    d.mats_in_smem = stage_bytes<R>(1, ft, d.n, E1, true) <= kSmemCap ? 1 : 0;
-    d.w_in_smem = stage_bytes<R>(2, tt, d.n, E1, true) <= kSmemCap ? 1 : 0;
-    const size_t need[3] = {stage_bytes<R>(0, tt, d.n, E1, d.h_in_smem), stage_bytes<R>(1, ft, d.n, E1, d.mats_in_smem),
-                            stage_bytes<R>(2, tt, d.n, E1, d.w_in_smem)};
+    const bool gat = d.gather != nullptr;
+    d.h_in_smem = stage_bytes<R>(0, tt, d.n, E1, true, gat) <= kSmemCap ? 1 : 0;
+    d.mats_in_smem = stage_bytes<R>(1, ft, d.n, E1, true, false) <= kSmemCap ? 1 : 0;
+    d.w_in_smem = stage_bytes<R>(2, tt, d.n, E1, true, false) <= kSmemCap ? 1 : 0;
+    const size_t need[3] = {stage_bytes<R>(0, tt, d.n, E1, d.h_in_smem, gat),
+                            stage_bytes<R>(1, ft, d.n, E1, d.mats_in_smem, false),
+                            stage_bytes<R>(2, tt, d.n, E1, d.w_in_smem, false)};
     for (int st = 0; st < 3; ++st) {
       if (need[st] > kSmemCap) return POLYLAB_ERR_UNSUPPORTED;
       smem[st] = std::max(smem[st], need[st]);

@@ -1,6 +1,7 @@
 // Host side of batched exact affine-normal launches: descriptors, work order,
 // configuration and the project's autotuner, plus the public batch API.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <numeric>
 
@@ -77,6 +78,17 @@ polylab_status exact_batch_init(ExactBatch* b, int n, const polylab_plan* const*
     d.max_support = pl->max_support;
     for (int k = 0; k < kMaxSupport + 2; ++k) d.koff[k] = pl->koff[k];
     for (int k = 0; k < kMaxSupport + 1; ++k) d.k3off[k] = pl->k3off[k];
+    d.gather = pl->gather;
+    d.gather_chunk = pl->gather_chunk;
+    d.n_gchunks = pl->n_gchunks;
+    {
+      // monomial values c x^a, their partial products and 1/x stay normal:
+      // |x|^deg within [1e-30, 1e30] (FP32 sums) or [1e-280, 1e280] (FP64)
+      const double lim = o->prec == POLYLAB_FP32 ? 30.0 : 280.0;
+      const double deg = std::max(1, pl->max_degree);
+      d.x_lo = std::pow(10.0, -lim / deg);
+      d.x_hi = std::pow(10.0, lim / deg);
+    }
     d.mats_in_smem = 1;
     d.X = X[i];
     d.P = P[i];

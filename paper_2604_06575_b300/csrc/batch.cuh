@@ -20,6 +20,10 @@ struct ExactDesc {
   int max_support;
   int64_t koff[kMaxSupport + 2];   // support-size groups of the sorted term list
   int64_t k3off[kMaxSupport + 1];  // first term of degree >= 3 in each group
+  const uint32_t* gather;           // gather form of the term sweep (or nullptr)
+  const int64_t* gather_chunk;
+  int n_gchunks;
+  double x_lo, x_hi;  // gather form used when every |x_v| is in [x_lo, x_hi]
   const double* X;   // P x n
   int64_t P;
   double* D;

@@ -68,6 +68,18 @@ struct Scratch {
 };
 
 // --------------------------------------------------------------- term list
+// Terms per chunk of the gather-form sweep (monomial values of one chunk are
+// held in shared memory), and the number of record streams per chunk: the
+// entry-sorted records of a chunk are cut into kGatherStreams contiguous
+// runs of equal length, stored interleaved (record k of stream s at
+// k * kGatherStreams + s) so that the threads of a warp, each walking its own
+// run, read consecutive addresses.  Runs are padded to a multiple of
+// kGatherUnroll records with entry kGatherPad and coefficient 0.
+constexpr int kGatherChunk = 2048;
+constexpr int kGatherStreams = 256;
+constexpr int kGatherUnroll = 8;
+constexpr uint32_t kGatherPad = 0x3fff;
+
 // Packed sparse form of one term: at most kMaxSupport active variables, in
 // ascending variable order; unused slots have exp == 0.  32 bytes, so a term
 // is two aligned 16-byte loads.
@@ -96,6 +108,16 @@ struct polylab_plan {
   // k3off[k]: first term of that group with degree >= 3
   int64_t koff[polylab::kMaxSupport + 2] = {};
   int64_t k3off[polylab::kMaxSupport + 1] = {};
+  // gather form of the gradient/Hessian sweep (nullptr when n > 127 or a
+  // falling-factorial coefficient exceeds 127): for every chunk of
+  // kGatherChunk terms, the (term, entry, coefficient) contributions sorted
+  // by entry; entry e < n*n is H(e / n, e % n) (upper triangle), e >= n*n is
+  // g(e - n*n); one 32-bit record: term within the chunk (bits 0-10), entry
+  // (bits 11-24), coefficient (bits 25-31)
+  uint32_t* gather = nullptr;         // DEVICE records
+  int64_t* gather_chunk = nullptr;    // DEVICE, n_gchunks + 1 record offsets (multiples of kGatherStreams)
+  int32_t n_gchunks = 0;
+  int32_t max_degree = 0;
   // derived-coefficient data for the tensor-core forms (nullptr unless built)
   polylab::GemmOperand* gemm = nullptr;
   int64_t closure = -1;

@@ -101,6 +101,86 @@ static void group_offsets(const std::vector<Term>& host, polylab_plan* plan) {
   plan->koff[kMaxSupport + 1] = m;
 }
 
+// Gather form of the gradient/Hessian sweep.  With m_t = c_t prod_s x_s^a_s,
+//   d_i m_t = a_i m_t / x_i,   d_ij m_t = a_i a_j m_t / (x_i x_j),
+//   d_ii m_t = a_i (a_i - 1) m_t / x_i^2,
+// so each entry of g and H is (1/x_i)(1/x_j) sum_t coef_t m_t over the terms
+// that touch it.  The records of every chunk of kGatherChunk terms are sorted
+// by entry, so a sweep sums runs of equal entries in registers.
+static polylab_status build_gather(const std::vector<Term>& host, int n, cudaStream_t s, polylab_plan* plan) {
+  const int64_t m = (int64_t)host.size();
+  int maxdeg = 0;
+  for (const Term& t : host) {
+    int d = 0;
+    for (int q = 0; q < kMaxSupport; ++q) d += t.exp[q];
+    maxdeg = std::max(maxdeg, d);
+  }
+  plan->max_degree = maxdeg;
+  if (n > 127 || m == 0) return POLYLAB_OK;
+  struct Rec {
+    uint64_t key;  // chunk << 48 | entry << 32 | term
+    uint32_t coef;
+  };
+  std::vector<Rec> recs;
+  recs.reserve((size_t)m * 8);
+  const uint64_t nn = (uint64_t)n * n;
+  for (int64_t t = 0; t < m; ++t) {
+    const Term& tm = host[t];
+    const uint64_t chunk = (uint64_t)(t / kGatherChunk);
+    auto add = [&](uint64_t entry, uint32_t coef) {
+      recs.push_back({chunk << 48 | entry << 32 | (uint64_t)t, coef});
+    };
+    for (int a = 0; a < kMaxSupport; ++a) {
+      const uint32_t ea = tm.exp[a];
+      if (!ea) continue;
+      const uint64_t va = tm.var[a];
+      add(nn + va, ea);
+      if (ea >= 2) add(va * n + va, ea * (ea - 1));
+      for (int b = a + 1; b < kMaxSupport; ++b)
+        if (tm.exp[b]) add(va * n + tm.var[b], ea * tm.exp[b]);
+    }
+  }
+  for (const Rec& r : recs)
+    if (r.coef > 127) return POLYLAB_OK;  // no gather form: coefficients beyond 7 bits
+  std::sort(recs.begin(), recs.end(), [](const Rec& x, const Rec& y) { return x.key < y.key; });
+  const int nch = (int)((m + kGatherChunk - 1) / kGatherChunk);
+  // sorted record range of every chunk
+  std::vector<int64_t> sorted_off(nch + 1, (int64_t)recs.size());
+  sorted_off[0] = 0;
+  for (int c = 0, q = 0; q < (int)recs.size(); ++q) {
+    const int ch = (int)(recs[q].key >> 48);
+    while (c < ch) sorted_off[++c] = q;
+  }
+  // interleaved streams: chunk c holds L_c * S records, record k of stream s
+  // at k * S + s, stream s = sorted records [s L_c, (s+1) L_c) of the chunk
+  constexpr int S = kGatherStreams;
+  std::vector<int64_t> off(nch + 1, 0);
+  for (int c = 0; c < nch; ++c) {
+    const int64_t len = sorted_off[c + 1] - sorted_off[c];
+    const int64_t L = (len + S - 1) / S;
+    off[c + 1] = off[c] + (L + kGatherUnroll - 1) / kGatherUnroll * kGatherUnroll * S;
+  }
+  std::vector<uint32_t> dev((size_t)off[nch], kGatherPad << 11);
+  for (int c = 0; c < nch; ++c) {
+    const int64_t len = sorted_off[c + 1] - sorted_off[c], L = (off[c + 1] - off[c]) / S;
+    for (int64_t q = 0; q < len; ++q) {
+      const Rec& r = recs[(size_t)(sorted_off[c] + q)];
+      const int64_t Ls = (len + S - 1) / S;  // records per stream before padding
+      const int64_t s_ = q / Ls, k = q - s_ * Ls;
+      const uint32_t t_local = (uint32_t)((r.key & 0xffffffffu) - (uint64_t)c * kGatherChunk);
+      const uint32_t entry = (uint32_t)((r.key >> 32) & 0xffffu);
+      dev[(size_t)(off[c] + k * S + s_)] = t_local | entry << 11 | r.coef << 25;
+    }
+  }
+  PL_CUDA(cudaMallocAsync(&plan->gather, std::max<size_t>(dev.size(), 1) * sizeof(uint32_t), s));
+  PL_CUDA(cudaMallocAsync(&plan->gather_chunk, (nch + 1) * sizeof(int64_t), s));
+  PL_CUDA(cudaMemcpyAsync(plan->gather, dev.data(), dev.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+  PL_CUDA(cudaMemcpyAsync(plan->gather_chunk, off.data(), (nch + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  PL_CUDA(cudaStreamSynchronize(s));  // host vectors go out of scope
+  plan->n_gchunks = nch;
+  return POLYLAB_OK;
+}
+
 polylab_status build_term_plan(const polylab_poly* p, cudaStream_t s, polylab_plan* plan) {
   PL_TRY(check_poly(p));
   if (p->n_vars > 65535) return POLYLAB_ERR_UNSUPPORTED;
@@ -141,6 +221,7 @@ polylab_status build_term_plan(const polylab_poly* p, cudaStream_t s, polylab_pl
     PL_CUDA(cudaMemcpyAsync(plan->terms, host.data(), p->n_terms * sizeof(Term), cudaMemcpyHostToDevice, s));
     PL_CUDA(cudaStreamSynchronize(s));
     group_offsets(host, plan);
+    PL_TRY(build_gather(host, p->n_vars, s, plan));
   } else {
     std::vector<Term> host(p->n_terms);
     if (p->n_terms > 0) {
@@ -148,6 +229,7 @@ polylab_status build_term_plan(const polylab_poly* p, cudaStream_t s, polylab_pl
       PL_CUDA(cudaStreamSynchronize(s));
     }
     group_offsets(host, plan);
+    PL_TRY(build_gather(host, p->n_vars, s, plan));
   }
   return POLYLAB_OK;
 }
@@ -195,6 +277,8 @@ polylab_status polylab_plan_destroy(polylab_plan* plan, polylab_stream stream) {
   if (!plan) return POLYLAB_OK;
   cudaStream_t s = (cudaStream_t)stream;
   if (plan->terms) cudaFreeAsync(plan->terms, s);
+  if (plan->gather) cudaFreeAsync(plan->gather, s);
+  if (plan->gather_chunk) cudaFreeAsync(plan->gather_chunk, s);
   if (plan->gemm) free_gemm_operand(plan->gemm, s);
   delete plan;
   return launch_status("polylab_plan_destroy");

@@ -2,7 +2,10 @@
 //   d_i x^a = a_i x^(a - e_i),  d_ij x^a = a_i (a_j - delta_ij) x^(a - e_i - e_j),
 //   d_ijk likewise (falling factorials times a shifted monomial).
 // Powers come from a per-point table pw[v * (E + 1) + k] = x_v^k built by
-// repeated multiplication.
+// repeated multiplication.  A term reads two entries per active variable, x_v
+// and its lowest needed power, and rebuilds the higher powers by the same
+// multiplications the table uses (so the values are those of the table):
+// shared-memory loads, not arithmetic, bound these sweeps.
 #pragma once
 
 #include <type_traits>
@@ -76,9 +79,18 @@ __device__ __forceinline__ void term_derivs_k(const TermRegs& t, const R* __rest
   if constexpr (K == 0) {
     emit(0, 0, 0, c);
   } else {
-    R a0[K];  // x_v^{a_v}
+    R a0[K], d1[K], q2[K];  // x^a, a x^(a-1), x^(a-2) (a >= 2 only) per slot
 #pragma unroll
-    for (int s = 0; s < K; ++s) a0[s] = pw[t.var[s] * E1 + t.exp[s]];
+    for (int s = 0; s < K; ++s) {
+      const R* row = pw + t.var[s] * E1;
+      const int es = t.exp[s];
+      const R x = row[1];
+      const R q = row[es >= 2 ? es - 2 : 0];
+      const R p1 = es >= 2 ? q * x : R(1);
+      a0[s] = p1 * x;
+      d1[s] = R(es) * p1;
+      q2[s] = q;
+    }
     R pre[K + 1], suf[K + 1];
     pre[0] = R(1);
 #pragma unroll
@@ -88,16 +100,13 @@ __device__ __forceinline__ void term_derivs_k(const TermRegs& t, const R* __rest
     for (int s = K - 1; s >= 0; --s) suf[s] = suf[s + 1] * a0[s];
     emit(0, 0, 0, c * pre[K]);
     if constexpr (ORDER >= 1) {
-      R d1[K];
-#pragma unroll
-      for (int s = 0; s < K; ++s) d1[s] = R(t.exp[s]) * pw[t.var[s] * E1 + t.exp[s] - 1];
 #pragma unroll
       for (int s = 0; s < K; ++s) {
         const R excl = pre[s] * suf[s + 1];
         emit(1, t.var[s], 0, c * d1[s] * excl);
         if constexpr (ORDER >= 2) {
           const int es = t.exp[s];
-          if (es >= 2) emit(2, t.var[s], t.var[s], c * R(es * (es - 1)) * pw[t.var[s] * E1 + es - 2] * excl);
+          if (es >= 2) emit(2, t.var[s], t.var[s], c * R(es * (es - 1)) * q2[s] * excl);
           R mid = R(1);
 #pragma unroll
           for (int u = s + 1; u < K; ++u) {
@@ -151,11 +160,15 @@ __device__ __forceinline__ void term_third_contract_k(const TermRegs& t, const R
 #pragma unroll
   for (int s = 0; s < K; ++s) {
     const int es = t.exp[s];
-    const R* q = pw + t.var[s] * E1 + es;
-    D0[s] = q[0];
-    D1[s] = R(es) * q[-1];
-    D2[s] = es >= 2 ? R(es * (es - 1)) * q[-2] : R(0);
-    D3[s] = es >= 3 ? R(es * (es - 1) * (es - 2)) * q[-3] : R(0);
+    const R* row = pw + t.var[s] * E1;
+    const R x = row[1];
+    const R r3 = row[es >= 3 ? es - 3 : 0];
+    const R p2 = es >= 3 ? r3 * x : R(1);  // x^(a-2), a >= 2
+    const R p1 = es >= 2 ? p2 * x : R(1);  // x^(a-1)
+    D0[s] = p1 * x;
+    D1[s] = R(es) * p1;
+    D2[s] = es >= 2 ? R(es * (es - 1)) * p2 : R(0);
+    D3[s] = es >= 3 ? R(es * (es - 1) * (es - 2)) * r3 : R(0);
   }
   R pre[K + 1], suf[K + 1];
   pre[0] = R(1);
@@ -222,6 +235,16 @@ __device__ __forceinline__ void term_third_contract(const TermRegs& t, const R* 
     case 7: term_third_contract_wide<R, 7>(t, pw, E1, wget, emit); break;
     default: term_third_contract_wide<R, 8>(t, pw, E1, wget, emit); break;
   }
+}
+
+// c x^a of one term at one point (any support size).
+template <typename R>
+__device__ __forceinline__ R term_value(const TermRegs& t, const R* __restrict__ pw, int E1) {
+  R v = R(t.coef);
+#pragma unroll
+  for (int s = 0; s < kMaxSupport; ++s)
+    if (t.exp[s]) v *= pw[t.var[s] * E1 + t.exp[s]];
+  return v;
 }
 
 // Call f(std::integral_constant<int, K>{}) for K = 0..KMAX in order.
