@@ -598,37 +598,68 @@ __global__ void __launch_bounds__(NT) exact_frame_kernel(StageArgs<R> a) {
       if (lane == 0) s_sc[1] = lsum;
     }
     for (int i = tid; i < m; i += NT) sq[i] = kF64 ? R(sqrt(di[i])) : R(sqrtf((float)di[i]));
-    if constexpr (!kF64) {
+    if constexpr (!kF64) {  // (the factor's storage becomes X after the next barrier)
       for (int j = wid; j < m; j += NW)
         for (int i = j + 1 + lane; i < m; i += 32) Hr[j * n + i] = (R)col(j)[i];
-      __syncthreads();  // the factor's storage becomes X
     }
-    // X = L^{-1} (unit lower), stored transposed: Xs[j*xs + i] = X_ij, i >= j
-    for (int j = wid; j < m; j += NW)
-      for (int i = j + lane; i < m; i += 32) Xs[j * xs + i] = i == j ? R(1) : R(0);
-    __syncthreads();
-    // right-looking: after step k row k of X is final; X_ij -= l_ik X_kj for
-    // j <= k < i, the (m-k-1) x (k+1) rectangle enumerated over the CTA
-    for (int k = 0; k + 1 < m; ++k) {
-      const int rows = m - k - 1;
-      // thread tid starts at q = tid = j * rows + i0 and steps by NT
-      const int dj = NT / rows, di0 = NT - dj * rows;
-      int j = tid / rows, i0 = tid - j * rows;
-      const R* lk = Hr + k * n + k + 1;
-      while (j <= k) {
-        Xs[j * xs + k + 1 + i0] -= lk[i0] * Xs[j * xs + k];
-        j += dj;
-        i0 += di0;
-        if (i0 >= rows) {
-          i0 -= rows;
-          ++j;
+    __syncthreads();  // L in the form's precision and sq complete
+    // X' = D^{-1/2} X with X = L^{-1} (unit lower), stored transposed:
+    // Xs[j*xs + i] = X'_ij, i >= j; then M = X'^T X'
+    if (m <= 64) {
+      // column j of X is the forward substitution of e_j alone, so columns
+      // are independent: warp w takes columns j = w, w + NW, ... two at a
+      // time, lane q holding rows q and q + 32 in registers; x_k reaches the
+      // other lanes by a shuffle once final (no block barrier)
+      for (int ja = wid; ja < m; ja += 2 * NW) {
+        const int jb = ja + NW;  // second column (none if jb >= m)
+        const int r0 = lane, r1 = lane + 32;
+        R a0 = r0 == ja ? R(1) : R(0), a1 = r1 == ja ? R(1) : R(0);
+        R b0 = r0 == jb ? R(1) : R(0), b1 = r1 == jb ? R(1) : R(0);
+        for (int k = ja; k + 1 < m; ++k) {
+          const R l0 = (r0 > k && r0 < m) ? Hr[k * n + r0] : R(0);
+          const R l1 = (r1 > k && r1 < m) ? Hr[k * n + r1] : R(0);
+          const R xa = __shfl_sync(0xffffffffu, k < 32 ? a0 : a1, k & 31);
+          a0 -= l0 * xa;
+          a1 -= l1 * xa;
+          if (k >= jb) {  // column jb is zero above row jb
+            const R xb = __shfl_sync(0xffffffffu, k < 32 ? b0 : b1, k & 31);
+            b0 -= l0 * xb;
+            b1 -= l1 * xb;
+          }
+        }
+        if (r0 >= ja && r0 < m) Xs[ja * xs + r0] = a0 * sq[r0];
+        if (r1 >= ja && r1 < m) Xs[ja * xs + r1] = a1 * sq[r1];
+        if (jb < m) {
+          if (r0 >= jb && r0 < m) Xs[jb * xs + r0] = b0 * sq[r0];
+          if (r1 >= jb && r1 < m) Xs[jb * xs + r1] = b1 * sq[r1];
         }
       }
+    } else {
+      for (int j = wid; j < m; j += NW)
+        for (int i = j + lane; i < m; i += 32) Xs[j * xs + i] = i == j ? R(1) : R(0);
       __syncthreads();
+      // right-looking: after step k row k of X is final; X_ij -= l_ik X_kj for
+      // j <= k < i, the (m-k-1) x (k+1) rectangle enumerated over the CTA
+      for (int k = 0; k + 1 < m; ++k) {
+        const int rows = m - k - 1;
+        // thread tid starts at q = tid = j * rows + i0 and steps by NT
+        const int dj = NT / rows, di0 = NT - dj * rows;
+        int j = tid / rows, i0 = tid - j * rows;
+        const R* lk = Hr + k * n + k + 1;
+        while (j <= k) {
+          Xs[j * xs + k + 1 + i0] -= lk[i0] * Xs[j * xs + k];
+          j += dj;
+          i0 += di0;
+          if (i0 >= rows) {
+            i0 -= rows;
+            ++j;
+          }
+        }
+        __syncthreads();
+      }
+      for (int j = wid; j < m; j += NW)
+        for (int i = j + lane; i < m; i += 32) Xs[j * xs + i] *= sq[i];
     }
-    // X' = D^{-1/2} X (row i scaled by d_i^{-1/2}), so M = X'^T X'
-    for (int j = wid; j < m; j += NW)
-      for (int i = j + lane; i < m; i += 32) Xs[j * xs + i] *= sq[i];
     __syncthreads();
     // M = H_T^{-1} = X'^T X', upper triangle into Hr (L no longer needed)
     for (int i = wid; i < m; i += NW)
