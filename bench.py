@@ -119,6 +119,35 @@ def alu_roofline(flops: dict, t_s: float, form: str, p32: float, p64: float, par
                 flops_fp32=f32, flops_fp64=f64)
 
 
+# ------------------------------------------------------------------ traffic
+
+EXACT_SOURCES = ("affine_exact.cu", "terms.cuh", "async.cuh", "batch.cuh", "common.cuh")
+
+
+def profiled_traffic(kernel: str, units: int):
+    """DRAM bytes (read + write) per launch of `kernel` from a committed ncu
+    summary under profiles/ (a line `traffic: kernel=K bytes=B units=U
+    source=S`), scaled from the captured U units to `units`; None unless the
+    exact-path sources still hash to S (the counters describe this code)."""
+    import glob
+    import hashlib
+    import re
+    h = hashlib.sha256()
+    for f in EXACT_SOURCES:
+        with open(os.path.join(ROOT, "paper_2604_06575_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    src = h.hexdigest()[:16]
+    pat = re.compile(r"^traffic: kernel=(\S+) bytes=(\d+) units=(\d+) source=(\w+)\s*$")
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        with open(path) as fh:
+            for line in fh:
+                mt = pat.match(line.strip())
+                if mt and mt.group(1) == kernel and mt.group(4) == src:
+                    return dict(bytes=int(int(mt.group(2)) * units / int(mt.group(3))),
+                                captured=os.path.basename(path), captured_units=int(mt.group(3)))
+    return None
+
+
 # ------------------------------------------------------------------ clocks
 
 class Clocks:
@@ -405,6 +434,10 @@ def main():
     dom = max(STAGES, key=lambda k: stage_ms[k])
     roof = alu_roofline(flops, stage_ms[dom] * 1e-3, chosen, p32, p64, STAGE_PARTS[dom])
     roof["kernel"] = f"{kernels[dom]} (the longest of the three launches of a step)"
+    tr = profiled_traffic(kernels[dom], npts) if chosen == "fp32" else None
+    roof["traffic"] = tr["bytes"] if tr else None
+    roof["traffic_note"] = (f"dram read+write per launch from {tr['captured']} ({tr['captured_units']} points), "
+                            f"scaled to {npts} points" if tr else "no ncu counters for this kernel at this source")
     roof["launches_per_step"] = 1
     roof["stages"] = stages
     roof["path"] = alu_roofline(flops, statistics.median(res[chosen]["step_ms"]) * 1e-3, chosen, p32, p64)
