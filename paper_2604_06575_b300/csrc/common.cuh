@@ -118,6 +118,16 @@ struct polylab_plan {
   int64_t* gather_chunk = nullptr;    // DEVICE, n_gchunks + 1 record offsets (multiples of kGatherStreams)
   int32_t n_gchunks = 0;
   int32_t max_degree = 0;
+  // sparsity pattern of the Hessian for assembled Hessian-vector products
+  // (built on first use by the stochastic path): CSR of every (i, j) that a
+  // term's support pairs (both orders) plus the whole diagonal; for term t of
+  // support-size group K (t' = t - koff[K]) the CSR positions of its K x K
+  // block are hpos[hbase[K] + t' K^2 + a K + b]
+  int32_t* hrow = nullptr;  // DEVICE, n + 1
+  int32_t* hcol = nullptr;  // DEVICE, hnnz
+  int32_t* hpos = nullptr;  // DEVICE
+  int64_t hnnz = 0;
+  int64_t hbase[polylab::kMaxSupport + 1] = {};
   // derived-coefficient data for the tensor-core forms (nullptr unless built)
   polylab::GemmOperand* gemm = nullptr;
   int64_t closure = -1;
@@ -127,6 +137,8 @@ namespace polylab {
 
 // Fill `plan` (terms, m, n, max_exp, max_support); synchronises `s`.
 polylab_status build_term_plan(const polylab_poly* p, cudaStream_t s, polylab_plan* plan);
+// Build the Hessian sparsity pattern of `plan` if absent (synchronises `s`).
+polylab_status ensure_hessian_pattern(polylab_plan* plan, cudaStream_t s);
 polylab_status build_gemm_operand(polylab_plan* plan, cudaStream_t s);
 void free_gemm_operand(GemmOperand* g, cudaStream_t s);
 

@@ -181,6 +181,58 @@ static polylab_status build_gather(const std::vector<Term>& host, int n, cudaStr
   return POLYLAB_OK;
 }
 
+polylab_status ensure_hessian_pattern(polylab_plan* plan, cudaStream_t s) {
+  if (plan->hrow) return POLYLAB_OK;
+  const int64_t m = plan->m;
+  const int n = plan->n;
+  std::vector<Term> host((size_t)m);
+  if (m > 0) {
+    PL_CUDA(cudaMemcpyAsync(host.data(), plan->terms, m * sizeof(Term), cudaMemcpyDeviceToHost, s));
+    PL_CUDA(cudaStreamSynchronize(s));
+  }
+  std::vector<uint64_t> keys;
+  keys.reserve((size_t)n + (size_t)m * 16);
+  for (int i = 0; i < n; ++i) keys.push_back((uint64_t)i << 32 | (uint64_t)i);
+  for (const Term& t : host)
+    for (int a = 0; a < kMaxSupport; ++a)
+      for (int b = 0; b < kMaxSupport; ++b)
+        if (t.exp[a] && t.exp[b] && a != b) keys.push_back((uint64_t)t.var[a] << 32 | t.var[b]);
+  std::sort(keys.begin(), keys.end());
+  keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+  if (keys.size() > 0x7fffffffu) return POLYLAB_ERR_UNSUPPORTED;
+  std::vector<int32_t> row(n + 1, 0), col(keys.size());
+  for (size_t q = 0; q < keys.size(); ++q) {
+    row[(keys[q] >> 32) + 1] += 1;
+    col[q] = (int32_t)(keys[q] & 0xffffffffu);
+  }
+  for (int i = 0; i < n; ++i) row[i + 1] += row[i];
+  std::vector<int32_t> pos;
+  int64_t base = 0;
+  for (int K = 0; K <= kMaxSupport; ++K) {
+    plan->hbase[K] = base;
+    for (int64_t t = plan->koff[K]; t < plan->koff[K + 1]; ++t) {
+      int var[kMaxSupport], k = 0;
+      for (int q = 0; q < kMaxSupport; ++q)
+        if (host[t].exp[q]) var[k++] = host[t].var[q];
+      for (int a = 0; a < K; ++a)
+        for (int b = 0; b < K; ++b) {
+          const uint64_t key = (uint64_t)var[a] << 32 | (uint64_t)var[b];
+          pos.push_back((int32_t)(std::lower_bound(keys.begin(), keys.end(), key) - keys.begin()));
+        }
+    }
+    base = (int64_t)pos.size();
+  }
+  PL_CUDA(cudaMallocAsync(&plan->hrow, (n + 1) * sizeof(int32_t), s));
+  PL_CUDA(cudaMallocAsync(&plan->hcol, std::max<size_t>(col.size(), 1) * sizeof(int32_t), s));
+  PL_CUDA(cudaMallocAsync(&plan->hpos, std::max<size_t>(pos.size(), 1) * sizeof(int32_t), s));
+  PL_CUDA(cudaMemcpyAsync(plan->hrow, row.data(), (n + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  PL_CUDA(cudaMemcpyAsync(plan->hcol, col.data(), col.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  PL_CUDA(cudaMemcpyAsync(plan->hpos, pos.data(), pos.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  PL_CUDA(cudaStreamSynchronize(s));
+  plan->hnnz = (int64_t)col.size();
+  return POLYLAB_OK;
+}
+
 polylab_status build_term_plan(const polylab_poly* p, cudaStream_t s, polylab_plan* plan) {
   PL_TRY(check_poly(p));
   if (p->n_vars > 65535) return POLYLAB_ERR_UNSUPPORTED;
@@ -278,6 +330,9 @@ polylab_status polylab_plan_destroy(polylab_plan* plan, polylab_stream stream) {
   cudaStream_t s = (cudaStream_t)stream;
   if (plan->terms) cudaFreeAsync(plan->terms, s);
   if (plan->gather) cudaFreeAsync(plan->gather, s);
+  if (plan->hrow) cudaFreeAsync(plan->hrow, s);
+  if (plan->hcol) cudaFreeAsync(plan->hcol, s);
+  if (plan->hpos) cudaFreeAsync(plan->hpos, s);
   if (plan->gather_chunk) cudaFreeAsync(plan->gather_chunk, s);
   if (plan->gemm) free_gemm_operand(plan->gemm, s);
   delete plan;

@@ -10,12 +10,19 @@
 // Pi D^{-1} Pi corresponds to Q_T^T D^{-1} Q_T), so no frame is formed.
 //
 // Per point (one CTA):
-//   g, |diag H| from the terms; e = g/|g|; D = |diag H| + r (1 where 0)
+//   g, |diag H| from the terms; H assembled once into the plan's CSR pattern
+//   (each term's K x K block added at its precomputed positions);
+//   e = g/|g|; D = |diag H| + r (1 where 0)
 //   for each chunk of QC probes:  w_s Rademacher (SplitMix64),
 //       b_s = Pi w_s;  PCG:  u_s ~ (Pi (H + rI) Pi)^+ b_s
 //       cbar += (1/q) sum_s T(., u_s, b_s)   (term by term, symmetrised)
 //   a = Pi cbar;  PCG: u_tau solves Pi (H + rI) Pi u = Pi H e - |g|/(n+1) a
 //   nu = u_tau - e
+//
+// Every Hessian-vector product of the Krylov solves is then a sparse
+// matrix times the QC probe columns: QC consecutive threads take one row, a
+// thread per probe, and read the row's values and column indices as
+// broadcasts and the probe vectors as one contiguous QC-wide load per entry.
 //
 // R = float (POLYLAB_FP32): HVPs, CG vectors and sums in FP32, the final
 // direction and its normalisation in FP64; R = double: FP64 throughout.
@@ -73,6 +80,22 @@ __device__ __forceinline__ void term_hessian_block(const TermRegs& t, const R* _
   }
 }
 
+// Adds a term's K x K Hessian block into the assembled values at its
+// precomputed CSR positions `hp` (wider supports out of line, as in terms.cuh).
+template <typename R, int K>
+__device__ __forceinline__ void term_assemble_k(const TermRegs& t, const R* __restrict__ pw, int E1,
+                                                const int32_t* __restrict__ hp, R* Hv) {
+  R blk[K * K];
+  term_hessian_block<R, K>(t, pw, E1, blk);
+#pragma unroll
+  for (int q = 0; q < K * K; ++q) atomicAdd(&Hv[hp[q]], blk[q]);
+}
+template <typename R, int K>
+__device__ __noinline__ void term_assemble_wide(const TermRegs& t, const R* __restrict__ pw, int E1,
+                                                const int32_t* __restrict__ hp, R* Hv) {
+  term_assemble_k<R, K>(t, pw, E1, hp, Hv);
+}
+
 // Y[var_a][s] += sum_b blk[a][b] V[var_b][s] for the QC probes of a chunk
 // (4 probes per pass, shared-memory atomics into Y).  V rows are QC apart,
 // Y rows QC + 1 apart (an odd stride keeps lanes with different variables on
@@ -120,8 +143,11 @@ __device__ __forceinline__ void term_hvp_dispatch(const TermRegs& t, const R* pw
 }
 
 // block-wide sums of QC values per thread; result broadcast to all threads
-template <int NT, int QC>
-__device__ __forceinline__ void block_sums(double (&v)[QC], double* red) {
+// (T = the form's precision inside the Krylov iterations: B300's FP64 rate is
+// 1/60 of its FP32 rate, and FP32 tree sums over n <= 2000 terms are far more
+// accurate than the solver tolerance)
+template <int NT, int QC, typename T>
+__device__ __forceinline__ void block_sums(T (&v)[QC], T* red) {
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
 #pragma unroll
   for (int s = 0; s < QC; ++s)
@@ -132,7 +158,7 @@ __device__ __forceinline__ void block_sums(double (&v)[QC], double* red) {
     for (int s = 0; s < QC; ++s) red[w * QC + s] = v[s];
   __syncthreads();
   if (threadIdx.x < QC) {
-    double acc = 0.0;
+    T acc = T(0);
     for (int q = 0; q < NT / 32; ++q) acc += red[q * QC + threadIdx.x];
     red[(NT / 32) * QC + threadIdx.x] = acc;
   }
@@ -140,6 +166,40 @@ __device__ __forceinline__ void block_sums(double (&v)[QC], double* red) {
 #pragma unroll
   for (int s = 0; s < QC; ++s) v[s] = red[(NT / 32) * QC + s];
   __syncthreads();
+}
+
+// Sum over the CTA of one value per thread for the thread's probe
+// s = tid % QC (QC a power of two <= 32, NT a multiple of 32): lanes of a warp
+// holding the same probe first, then the warps' partials in shared memory.
+// Every thread receives its probe's total.
+template <int NT, int QC, typename T>
+__device__ __forceinline__ T probe_sum(T v, T* red) {
+  for (int o = QC; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l < QC) red[w * QC + l] = v;
+  __syncthreads();
+  if (threadIdx.x < QC) {
+    T acc = T(0);
+    for (int q = 0; q < NT / 32; ++q) acc += red[q * QC + threadIdx.x];
+    red[(NT / 32) * QC + threadIdx.x] = acc;
+  }
+  __syncthreads();
+  return red[(NT / 32) * QC + threadIdx.x % QC];
+}
+
+// Sum over the CTA of one double per thread, broadcast to every thread.
+template <int NT>
+__device__ __forceinline__ double block_sum1(double v, double* red) {
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double acc = 0.0;
+  for (int q = 0; q < NT / 32; ++q) acc += red[q];
+  __syncthreads();
+  return acc;
 }
 
 struct StochArgs {
@@ -156,22 +216,33 @@ struct StochArgs {
   double* D;
   double* Dunit;
   polylab_an_info* info;
-  unsigned char* gws;  // per CTA: 5 vectors of n*QC R, then U (2 n floats) for the learned preconditioner
+  // assembled Hessian: the plan's CSR pattern and per-term block positions
+  const int32_t* hrow;
+  const int32_t* hcol;
+  const int32_t* hpos;
+  int64_t hbase[kMaxSupport + 1];
+  int64_t koff[kMaxSupport + 2];
+  int64_t k3off[kMaxSupport + 1];
+  // per CTA: 5 vectors of n*QC R, U (2 n floats) for the learned
+  // preconditioner, the HVP output Y (n rows of QC+1 R), then the point's
+  // Hessian values and the trace weight Z on the same pattern (hnnz R each,
+  // 16-byte aligned)
+  unsigned char* gws;
   size_t gws_stride;
+  size_t y_off, hval_off;
 };
 
 }  // namespace
 
 template <typename R, int NT, int QC>
-__global__ void __launch_bounds__(NT) stochastic_kernel(StochArgs a) {
+__global__ void __launch_bounds__(NT, 2) stochastic_kernel(StochArgs a) {
   extern __shared__ __align__(16) unsigned char sm[];
   const int n = a.n, E1 = a.E + 1, tid = threadIdx.x;
-  // shared: power table, Y accumulators, vectors g, dg (|diag H|), e, cbar, Dinv; reductions
+  // shared: power table, vectors g, dg (|diag H|), e, cbar, Dinv; reductions
   R* pw = (R*)sm;
-  R* Y = pw + (size_t)n * E1;
   // per-point vectors in the form's precision (FP32 form: shared memory for n up to ~2000)
-  constexpr int YS = QC + 1;  // row stride of Y (see term_hvp)
-  R* g = (R*)(((uintptr_t)(Y + (size_t)n * YS) + 15) & ~(uintptr_t)15);
+  constexpr int YS = QC + 1;  // row stride of Y, the HVP output (global, see below)
+  R* g = (R*)(((uintptr_t)(pw + (size_t)n * E1) + 15) & ~(uintptr_t)15);
   R* dg = g + n;
   R* e = dg + n;
   R* cbar = e + n;
@@ -179,7 +250,7 @@ __global__ void __launch_bounds__(NT) stochastic_kernel(StochArgs a) {
   double* red = (double*)(((uintptr_t)(Dinv + n) + 15) & ~(uintptr_t)15);  // (NT/32 + 1) * QC doubles
   __shared__ int s_active[QC];
   __shared__ int s_iters[QC];
-  __shared__ double s_bnorm[QC], s_rz[QC];
+  __shared__ double s_bnorm[QC], s_rz[QC], s_rr[QC];
   __shared__ int s_maxed;
   __shared__ float th[kMlpParams];
   const bool use_mlp = a.precond == POLYLAB_PRECOND_MLP;
@@ -195,6 +266,10 @@ __global__ void __launch_bounds__(NT) stochastic_kernel(StochArgs a) {
   R* Bv = Zv + vec;  // right-hand sides b_s = Pi w_s
   float* U0 = (float*)(Bv + vec);  // learned low-rank factor, columns 0 and 1
   float* U1 = U0 + n;
+  R* Y = (R*)(gb + a.y_off);       // HVP output rows (stride YS) and first-sweep scratch
+  R* Hv = (R*)(gb + a.hval_off);  // this point's Hessian values in the CSR pattern
+  const int64_t hnnz = a.hrow[n];
+  R* Zw = Hv + ((hnnz + 3) & ~int64_t(3));  // trace weight on the same pattern
 
   for (int64_t p = blockIdx.x; p < a.P; p += gridDim.x) {
     __syncthreads();
@@ -211,6 +286,7 @@ __global__ void __launch_bounds__(NT) stochastic_kernel(StochArgs a) {
       dg[i] = R(0);
       cbar[i] = R(0);
     }
+    for (int64_t q = tid; q < hnnz; q += NT) Hv[q] = R(0);
     __syncthreads();
     // gradient, sum of |gradient contributions| (zero test), diag(H) and the
     // off-diagonal |contribution| mass of every row (learned preconditioner, Y[n, 2n))
@@ -233,17 +309,26 @@ __global__ void __launch_bounds__(NT) stochastic_kernel(StochArgs a) {
         }
       });
     }
+    // assemble H: every term's K x K block at its precomputed CSR positions
+    for_support<kMaxSupport>([&](auto kc) {
+      constexpr int K = decltype(kc)::value;
+      if constexpr (K >= 1) {
+        for (int64_t t = a.koff[K] + tid; t < a.koff[K + 1]; t += NT) {
+          const TermRegs tr = load_term(a.terms, t);
+          const int32_t* hp = a.hpos + a.hbase[K] + (t - a.koff[K]) * (K * K);
+          if constexpr (K <= 6) term_assemble_k<R, K>(tr, pw, E1, hp, Hv);
+          else term_assemble_wide<R, K>(tr, pw, E1, hp, Hv);
+        }
+      }
+    });
     __syncthreads();
-    double gg[QC], ss[QC];
-#pragma unroll
-    for (int s = 0; s < QC; ++s) gg[s] = ss[s] = 0.0;
-    for (int i = tid; i < n; i += NT) gg[0] += (double)g[i] * (double)g[i];
-    ss[0] = gabs;
-    block_sums<NT, QC>(gg, red);
-    block_sums<NT, QC>(ss, red);
-    const double gn = sqrt(gg[0]);
+    double gg = 0.0;
+    for (int i = tid; i < n; i += NT) gg += (double)g[i] * (double)g[i];
+    gg = block_sum1<NT>(gg, red);
+    const double gsum = block_sum1<NT>(gabs, red);
+    const double gn = sqrt(gg);
     bool zero = !(gn > 0.0) || !isfinite(gn);
-    if (!a.assume_nonzero_x && gn <= (sizeof(R) == 8 ? 1e-14 : 1e-6) * ss[0]) zero = true;
+    if (!a.assume_nonzero_x && gn <= (sizeof(R) == 8 ? 1e-14 : 1e-6) * gsum) zero = true;
     if (zero) {
       if (tid == 0 && a.info) {
         polylab_an_info in{gn, nan(""), POLYLAB_FLAG_ZERO_GRAD, 0, a.q, 0};
@@ -276,48 +361,57 @@ __global__ void __launch_bounds__(NT) stochastic_kernel(StochArgs a) {
 
     // ---------------------------------------------------------------- PCG
     // Solves Pi (H + rI) Pi u_s = b_s for the `nq` columns present in Bv.
+    // Vectors hold QC probe columns per row (element (i, s) at i*QC + s); a
+    // thread always handles the same probe s = tid % QC (NT is a multiple of
+    // QC), so every per-probe reduction is one value per thread.
+    R* redr = (R*)red;
+    const int my_s = tid % QC;
     auto project = [&](R* V, int nq, int stride) {  // V_s <- V_s - e (e . V_s); rows `stride` apart
-      double d[QC];
-#pragma unroll
-      for (int s = 0; s < QC; ++s) d[s] = 0.0;
-      for (int i = tid; i < n; i += NT)
-#pragma unroll
-        for (int s = 0; s < QC; ++s) d[s] += (double)e[i] * (double)V[i * stride + s];
-      block_sums<NT, QC>(d, red);
-      for (int i = tid; i < n; i += NT)
-#pragma unroll
-        for (int s = 0; s < QC; ++s)
-          if (s < nq) V[i * stride + s] -= R((double)e[i] * d[s]);
+      R d = R(0);
+      for (int i = tid; i < (int)vec; i += NT) d += e[i / QC] * V[(i / QC) * stride + my_s];
+      d = probe_sum<NT, QC>(d, redr);
+      if (my_s < nq)
+        for (int i = tid; i < (int)vec; i += NT) V[(i / QC) * stride + my_s] -= e[i / QC] * d;
+    };
+    // Y[i][s] = sum_j H_ij V[j][s] + shift V[i][s] for the active probes s
+    // (QC threads per row, one per probe; rows NT / QC at a time)
+    auto spmv = [&](const R* __restrict__ V, R shift) {
+      constexpr int RPP = NT / QC;
+      const bool on = s_active[my_s] != 0;
+      for (int i = tid / QC; i < n; i += RPP) {
+        R acc = R(0);
+        if (on) {
+          int q = a.hrow[i];
+          const int q1 = a.hrow[i + 1];
+          for (; q + 4 <= q1; q += 4) {
+            const int c0 = a.hcol[q], c1 = a.hcol[q + 1], c2 = a.hcol[q + 2], c3 = a.hcol[q + 3];
+            const R h0 = Hv[q], h1 = Hv[q + 1], h2 = Hv[q + 2], h3 = Hv[q + 3];
+            acc += h0 * V[c0 * QC + my_s] + h1 * V[c1 * QC + my_s] + h2 * V[c2 * QC + my_s] +
+                   h3 * V[c3 * QC + my_s];
+          }
+          for (; q < q1; ++q) acc += Hv[q] * V[a.hcol[q] * QC + my_s];
+        }
+        Y[i * YS + my_s] = acc + shift * V[i * QC + my_s];
+      }
     };
     auto apply_A = [&](const R* V) {  // Y = Pi (H + rI) V (V in e-perp), into shared memory
-      for (int i = tid; i < n * YS; i += NT) Y[i] = R(0);
-      __syncthreads();
-      for (int64_t t = tid; t < a.m; t += NT) {
-        const TermRegs tr = load_term(a.terms, t);
-        term_hvp_dispatch<R, QC>(tr, pw, E1, V, Y, s_active);
-      }
-      __syncthreads();
-      for (int i = tid; i < (int)vec; i += NT) Y[(i / QC) * YS + i % QC] += R(a.r) * V[i];
+      spmv(V, R(a.r));
       __syncthreads();
       project(Y, QC, YS);
       __syncthreads();
     };
     auto precondition = [&](int nq) {  // Z = Pi D^{-1} R, or Pi (D + U U^T) R when learned
       if (use_mlp) {
-        double u0r[QC], u1r[QC];
-#pragma unroll
-        for (int s = 0; s < QC; ++s) u0r[s] = u1r[s] = 0.0;
-        for (int i = tid; i < n; i += NT)
-#pragma unroll
-          for (int s = 0; s < QC; ++s) {
-            u0r[s] += (double)U0[i] * (double)Rv[i * QC + s];
-            u1r[s] += (double)U1[i] * (double)Rv[i * QC + s];
-          }
-        block_sums<NT, QC>(u0r, red);
-        block_sums<NT, QC>(u1r, red);
+        R u0r = R(0), u1r = R(0);
         for (int i = tid; i < (int)vec; i += NT) {
-          const int row = i / QC, s = i % QC;
-          Zv[i] = Dinv[row] * Rv[i] + R(U0[row] * u0r[s] + U1[row] * u1r[s]);
+          u0r += R(U0[i / QC]) * Rv[i];
+          u1r += R(U1[i / QC]) * Rv[i];
+        }
+        u0r = probe_sum<NT, QC>(u0r, redr);
+        u1r = probe_sum<NT, QC>(u1r, redr);
+        for (int i = tid; i < (int)vec; i += NT) {
+          const int row = i / QC;
+          Zv[i] = Dinv[row] * Rv[i] + R(U0[row]) * u0r + R(U1[row]) * u1r;
         }
       } else {
         for (int i = tid; i < (int)vec; i += NT) Zv[i] = Dinv[i / QC] * Rv[i];
@@ -338,30 +432,23 @@ __global__ void __launch_bounds__(NT) stochastic_kernel(StochArgs a) {
       __syncthreads();
       precondition(nq);
       for (int i = tid; i < (int)vec; i += NT) Pv[i] = Zv[i];
-      double bb[QC], rz[QC];
-#pragma unroll
-      for (int s = 0; s < QC; ++s) bb[s] = rz[s] = 0.0;
-      for (int i = tid; i < n; i += NT)
-#pragma unroll
-        for (int s = 0; s < QC; ++s) {
-          const double b = Bv[i * QC + s];
-          bb[s] += b * b;
-          rz[s] += b * (double)Zv[i * QC + s];
-        }
-      block_sums<NT, QC>(bb, red);
-      block_sums<NT, QC>(rz, red);
+      R bb = R(0), rz = R(0);
+      for (int i = tid; i < (int)vec; i += NT) {
+        bb += Bv[i] * Bv[i];
+        rz += Bv[i] * Zv[i];
+      }
+      bb = probe_sum<NT, QC>(bb, redr);
+      rz = probe_sum<NT, QC>(rz, redr);
       if (tid < QC) {
-        s_bnorm[tid] = sqrt(bb[tid]);
-        s_rz[tid] = rz[tid];
+        s_bnorm[tid] = sqrt((double)bb);
+        s_rz[tid] = rz;
+        s_rr[tid] = bb;
       }
       __syncthreads();
-      double rr[QC];
-#pragma unroll
-      for (int s = 0; s < QC; ++s) rr[s] = bb[s];
       for (int k = 0;; ++k) {
         // convergence test before every iteration: |r_s| <= tol |b_s|
         if (tid < QC && s_active[tid]) {
-          if (sqrt(rr[tid]) <= a.tol * s_bnorm[tid]) {
+          if (sqrt(s_rr[tid]) <= a.tol * s_bnorm[tid]) {
             s_active[tid] = 0;
           } else if (k >= a.maxit) {
             s_active[tid] = 0;
@@ -371,58 +458,50 @@ __global__ void __launch_bounds__(NT) stochastic_kernel(StochArgs a) {
         __syncthreads();
         int any = 0;
 #pragma unroll
-        for (int s = 0; s < QC; ++s) any |= s_active[s];
+        for (int q = 0; q < QC; ++q) any |= s_active[q];
         if (!any) break;
         apply_A(Pv);
-        double py[QC];
-#pragma unroll
-        for (int s = 0; s < QC; ++s) py[s] = 0.0;
-        for (int i = tid; i < n; i += NT)
-#pragma unroll
-          for (int s = 0; s < QC; ++s) py[s] += (double)Pv[i * QC + s] * (double)Y[i * YS + s];
-        block_sums<NT, QC>(py, red);
+        R py = R(0);
+        for (int i = tid; i < (int)vec; i += NT) py += Pv[i] * Y[(i / QC) * YS + my_s];
+        py = probe_sum<NT, QC>(py, redr);
         // breakdown guard: a probe whose curvature p.Ap is not positive (or not
         // finite) stops here with its current iterate
-        if (tid < QC && s_active[tid] && !(py[tid] > 0.0 && isfinite(py[tid]) && isfinite(s_rz[tid])))
-          s_active[tid] = 0;
+        if (tid < QC && s_active[tid] && !(py > R(0) && isfinite(py) && isfinite(s_rz[tid]))) s_active[tid] = 0;
         __syncthreads();
-        for (int i = tid; i < (int)vec; i += NT) {
-          const int s = i % QC;
-          if (!s_active[s]) continue;
-          const R alpha = R(s_rz[s] / py[s]);
-          Xv[i] += alpha * Pv[i];
-          Rv[i] -= alpha * Y[(i / QC) * YS + s];
+        if (s_active[my_s]) {
+          const R alpha = R(s_rz[my_s] / (double)py);
+          for (int i = tid; i < (int)vec; i += NT) {
+            Xv[i] += alpha * Pv[i];
+            Rv[i] -= alpha * Y[(i / QC) * YS + my_s];
+          }
         }
         __syncthreads();
         precondition(nq);
-        double rzn[QC];
-#pragma unroll
-        for (int s = 0; s < QC; ++s) rzn[s] = rr[s] = 0.0;
-        for (int i = tid; i < n; i += NT)
-#pragma unroll
-          for (int s = 0; s < QC; ++s) {
-            const double rv = Rv[i * QC + s];
-            rzn[s] += rv * (double)Zv[i * QC + s];
-            rr[s] += rv * rv;
-          }
-        block_sums<NT, QC>(rzn, red);
-        block_sums<NT, QC>(rr, red);
+        R rzn = R(0), rr = R(0);
         for (int i = tid; i < (int)vec; i += NT) {
-          const int s = i % QC;
-          if (!s_active[s]) continue;
-          const R beta = R(rzn[s] / s_rz[s]);
-          Pv[i] = Zv[i] + beta * Pv[i];
+          const R rv = Rv[i];
+          rzn += rv * Zv[i];
+          rr += rv * rv;
+        }
+        rzn = probe_sum<NT, QC>(rzn, redr);
+        rr = probe_sum<NT, QC>(rr, redr);
+        if (s_active[my_s]) {
+          const R beta = R((double)rzn / s_rz[my_s]);
+          for (int i = tid; i < (int)vec; i += NT) Pv[i] = Zv[i] + beta * Pv[i];
         }
         __syncthreads();
         if (tid < QC && s_active[tid]) {
-          s_rz[tid] = rzn[tid];
+          s_rz[tid] = rzn;
+          s_rr[tid] = rr;
           s_iters[tid] += 1;
+        } else if (tid < QC) {
+          s_rr[tid] = rr;
         }
         __syncthreads();
       }
       int it = 0;
 #pragma unroll
-      for (int s = 0; s < QC; ++s) it += s < nq ? s_iters[s] : 0;
+      for (int q = 0; q < QC; ++q) it += q < nq ? s_iters[q] : 0;
       __syncthreads();
       return it;
     };
@@ -443,25 +522,52 @@ __global__ void __launch_bounds__(NT) stochastic_kernel(StochArgs a) {
       project(Bv, nq, QC);
       __syncthreads();
       total_iters += pcg(nq);
-      // cbar += (1/q) sum_s T(., u_s, b_s): per term, the symmetrised block
-      // Z_jk = (1/2q) sum_s (u_s[j] b_s[k] + u_s[k] b_s[j]) contracted with T
-      const double inv2q = 0.5 / (double)a.q;
-      for (int64_t t = tid; t < a.m; t += NT) {
-        const TermRegs tr = load_term(a.terms, t);
-        int deg = 0;
-#pragma unroll
-        for (int s2 = 0; s2 < kMaxSupport; ++s2) deg += tr.exp[s2];
-        if (deg < 3) continue;
-        term_third_contract<R>(
-            tr, pw, E1,
-            [&](int j, int k) {
-              R acc = R(0);
-              for (int s = 0; s < nq; ++s)
-                acc += Xv[j * QC + s] * Bv[k * QC + s] + Xv[k * QC + s] * Bv[j * QC + s];
-              return R(acc * R(inv2q));
-            },
-            [&](int l, R val) { atomicAdd(&cbar[l], val); });
+      // cbar += (1/q) sum_s T(., u_s, b_s): the symmetrised weight
+      // Z_jk = (1/2q) sum_s (u_s[j] b_s[k] + u_s[k] b_s[j]) is formed once on
+      // the Hessian pattern (every pair a term touches), QC threads per row
+      // summing over the probes by shuffles (warp-uniform loops), then each
+      // term of degree >= 3 contracts its third derivatives with its block of Z
+      {
+        const R inv2q = R(0.5 / (double)a.q);
+        constexpr int GPW = 32 / QC;  // rows per warp and pass
+        const int ls = tid % QC, grp = (tid & 31) / QC;
+        for (int base = (tid >> 5) * GPW; base < n; base += (NT / 32) * GPW) {
+          const int i = base + grp;
+          int q0 = 0, len = 0;
+          R xi = R(0), bi = R(0);
+          if (i < n) {
+            q0 = a.hrow[i];
+            len = a.hrow[i + 1] - q0;
+            if (ls < nq) {
+              xi = Xv[i * QC + ls];
+              bi = Bv[i * QC + ls];
+            }
+          }
+          int lmax = len;
+          for (int o = QC; o < 32; o <<= 1) lmax = max(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+          for (int k = 0; k < lmax; ++k) {
+            const bool ok = k < len;
+            const int c = ok ? a.hcol[q0 + k] : 0;
+            R v = (ok && ls < nq) ? xi * Bv[c * QC + ls] + Xv[c * QC + ls] * bi : R(0);
+            for (int o = QC / 2; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (ok && ls == 0) Zw[q0 + k] = v * inv2q;
+          }
+        }
       }
+      __syncthreads();
+      for_support<kMaxSupport>([&](auto kc) {
+        constexpr int K = decltype(kc)::value;
+        if constexpr (K >= 1) {
+          const int32_t* hp = nullptr;
+          auto wget = [&](int sa, int sb) { return Zw[hp[sa * K + sb]]; };
+          auto emit = [&](int l, R val) { atomicAdd(&cbar[l], val); };
+          for (int64_t t = a.k3off[K] + tid; t < a.koff[K + 1]; t += NT) {
+            const TermRegs tr = load_term(a.terms, t);
+            hp = a.hpos + a.hbase[K] + (t - a.koff[K]) * (K * K);
+            term_third_group<R, K>(tr, pw, E1, wget, emit);
+          }
+        }
+      });
       __syncthreads();
     }
     // ---------------------------------------------------------- tau solve
@@ -469,12 +575,7 @@ __global__ void __launch_bounds__(NT) stochastic_kernel(StochArgs a) {
     for (int i = tid; i < (int)vec; i += NT) Pv[i] = (i % QC == 0) ? R(e[i / QC]) : R(0);
     if (tid < QC) s_active[tid] = tid == 0;
     __syncthreads();
-    for (int i = tid; i < n * YS; i += NT) Y[i] = R(0);
-    __syncthreads();
-    for (int64_t t = tid; t < a.m; t += NT) {  // Y = H e (ambient, column 0)
-      const TermRegs tr = load_term(a.terms, t);
-      term_hvp_dispatch<R, QC>(tr, pw, E1, Pv, Y, s_active);
-    }
+    spmv(Pv, R(0));  // Y = H e (ambient, column 0)
     __syncthreads();
     const double wgt = gn / (double)(n + 1);
     for (int i = tid; i < (int)vec; i += NT)
@@ -484,15 +585,12 @@ __global__ void __launch_bounds__(NT) stochastic_kernel(StochArgs a) {
     __syncthreads();
     total_iters += pcg(1);
     // ---------------------------------------------------------- direction
-    double nrm[QC];
-#pragma unroll
-    for (int s = 0; s < QC; ++s) nrm[s] = 0.0;
+    double nrm = 0.0;
     for (int i = tid; i < n; i += NT) {
       const double nu = (double)Xv[i * QC] - (double)e[i];
-      nrm[0] += nu * nu;
+      nrm += nu * nu;
     }
-    block_sums<NT, QC>(nrm, red);
-    const double inv = 1.0 / sqrt(nrm[0]);
+    const double inv = 1.0 / sqrt(block_sum1<NT>(nrm, red));
     for (int i = tid; i < n; i += NT) {
       const double nu = (double)Xv[i * QC] - (double)e[i];
       a.D[p * n + i] = nu;
@@ -509,7 +607,7 @@ namespace {
 
 template <typename R, int QC>
 size_t stoch_smem(int n, int E1, int NT) {
-  size_t b = (size_t)n * E1 * sizeof(R) + (size_t)n * (QC + 1) * sizeof(R);
+  size_t b = (size_t)n * E1 * sizeof(R);
   b = (b + 15) & ~size_t(15);
   b += 5 * (size_t)n * sizeof(R);
   b = (b + 15) & ~size_t(15);
@@ -521,6 +619,8 @@ template <typename R, int NT, int QC>
 polylab_status launch_stoch(const polylab_plan* plan, const double* X, int64_t P, const polylab_an_opts* o, double* D,
                             double* Dunit, polylab_an_info* info, cudaStream_t s) {
   const int n = plan->n, E1 = std::max(plan->max_exp, 1) + 1;
+  // the Hessian pattern is a cached part of the plan, built on first use
+  PL_TRY(ensure_hessian_pattern(const_cast<polylab_plan*>(plan), s));
   const size_t smem = stoch_smem<R, QC>(n, E1, NT);
   if (smem > 220 * 1024) return POLYLAB_ERR_UNSUPPORTED;
   auto k = stochastic_kernel<R, NT, QC>;
@@ -547,7 +647,15 @@ polylab_status launch_stoch(const polylab_plan* plan, const double* X, int64_t P
   a.D = D;
   a.Dunit = Dunit;
   a.info = info;
-  a.gws_stride = ((size_t)5 * n * QC * sizeof(R) + 2 * (size_t)n * sizeof(float) + 255) & ~size_t(255);
+  a.hrow = plan->hrow;
+  a.hcol = plan->hcol;
+  a.hpos = plan->hpos;
+  for (int k = 0; k <= kMaxSupport; ++k) a.hbase[k] = plan->hbase[k];
+  for (int k = 0; k < kMaxSupport + 2; ++k) a.koff[k] = plan->koff[k];
+  for (int k = 0; k < kMaxSupport + 1; ++k) a.k3off[k] = plan->k3off[k];
+  a.y_off = ((size_t)5 * n * QC * sizeof(R) + 2 * (size_t)n * sizeof(float) + 15) & ~size_t(15);
+  a.hval_off = (a.y_off + (size_t)n * (QC + 1) * sizeof(R) + 15) & ~size_t(15);
+  a.gws_stride = (a.hval_off + 2 * (size_t)((plan->hnnz + 3) & ~int64_t(3)) * sizeof(R) + 255) & ~size_t(255);
   Scratch scr(s);
   PL_TRY(scr.get(&a.gws, (size_t)grid * a.gws_stride));
   k<<<(unsigned)grid, NT, smem, s>>>(a);
