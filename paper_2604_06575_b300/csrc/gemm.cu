@@ -378,7 +378,16 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_eval_kernel(GemmArgs a) 
   unsigned char* stA[2] = {sm, sm + Cf::ABYTES};
   unsigned char* stB[2] = {sm + 2 * Cf::ABYTES, sm + 2 * Cf::ABYTES + Cf::BBYTES};
   float* pwt = (float*)(sm + 2 * Cf::ABYTES + 2 * Cf::BBYTES);  // [n][Et][128]: x^(e+1) of row r
-  __shared__ __align__(8) uint64_t full[2], done[2], fin;
+  // closure-monomial records of the K tile being produced and of the next one
+  // (bulk-copied one tile ahead: they are the same for every CTA and would
+  // otherwise be read from L2 by every producer thread)
+  ClosMono* recs[2];
+  {
+    unsigned char* rb = (unsigned char*)(((uintptr_t)(pwt + (size_t)a.n * a.Et * 128) + 15) & ~(uintptr_t)15);
+    recs[0] = (ClosMono*)rb;
+    recs[1] = (ClosMono*)(rb + Cf::KT * sizeof(ClosMono));
+  }
+  __shared__ __align__(8) uint64_t full[2], done[2], fin, mrec[2];
   __shared__ uint32_t s_taddr;
   __shared__ int s_started[2];
   __shared__ int s_abort;
@@ -393,6 +402,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_eval_kernel(GemmArgs a) 
     mbar_init(&done[0], 1);
     mbar_init(&done[1], 1);
     mbar_init(&fin, 1);
+    mbar_init(&mrec[0], 1);
+    mbar_init(&mrec[1], 1);
     s_started[0] = s_started[1] = 0;
     s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -421,6 +432,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_eval_kernel(GemmArgs a) 
   const int* live = a.live + (size_t)chunk * a.Kt;
   int nlive = 0;
   while (nlive < a.Kt && live[nlive] >= 0) ++nlive;
+  constexpr uint32_t kRecBytes = Cf::KT * sizeof(ClosMono);
+  if (tid == 0 && nlive > 0) {
+    mbar_arrive_expect_tx(&mrec[0], kRecBytes);
+    bulk_g2s(recs[0], a.mono + (int64_t)live[0] * Cf::KT, kRecBytes, &mrec[0]);
+  }
   const unsigned char* gblk = a.blocks + (size_t)chunk * a.Kt * Cf::BBYTES;
   constexpr uint32_t kN = KIND == 0 ? 256 : 256;
   constexpr uint32_t idesc = idesc_of(KIND == 0 ? 1u : 2u, kN);
@@ -438,10 +454,16 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_eval_kernel(GemmArgs a) 
     if (tid == 0) {
       mbar_arrive_expect_tx(&full[st], Cf::BBYTES);
       bulk_g2s(stB[st], gblk + (size_t)kt * Cf::BBYTES, Cf::BBYTES, &full[st]);
+      if (it + 1 < nlive) {  // the other record buffer was last read before the barrier above
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&mrec[st ^ 1], kRecBytes);
+        bulk_g2s(recs[st ^ 1], a.mono + (int64_t)live[it + 1] * Cf::KT, kRecBytes, &mrec[st ^ 1]);
+      }
     }
+    if (!mbar_wait(&mrec[st], (it >> 1) & 1, a.err)) s_abort = 1;
     // monomial tile: row r, KT consecutive closure monomials in 16-byte chunks;
     // thread part q fills chunks 2q and 2q+1
-    const ClosMono* mm = a.mono + (int64_t)kt * Cf::KT;
+    const ClosMono* mm = recs[st];
 #pragma unroll 1
     for (int c16 = part * 2; c16 < part * 2 + 2; ++c16) {
       constexpr int PER = 16 / Cf::ESZ;
@@ -450,8 +472,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_eval_kernel(GemmArgs a) 
       for (int q = 0; q < PER; ++q) {
         // two 16-byte loads: variables (8 x u16), then exponents (8 x u8)
         const uint4* src = reinterpret_cast<const uint4*>(mm + c16 * PER + q);
-        const uint4 wv = __ldg(src);
-        const uint4 we = __ldg(src + 1);
+        const uint4 wv = src[0];
+        const uint4 we = src[1];
         const uint32_t vw[4] = {wv.x, wv.y, wv.z, wv.w};
         const uint32_t ew[2] = {we.x, we.y};
         const int kq = we.z & 0xff;  // support size of this monomial (same for the whole warp)
@@ -535,9 +557,56 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_eval_kernel(GemmArgs a) 
   if (issued && !mbar_wait(&fin, 0, a.err)) s_abort = 1;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   __syncthreads();
-  if (!s_abort) {
-    // warps w, w+4, w+8, w+12 read the same TMEM lane quadrant (rows
-    // 32(w%4)..) and split the columns between them
+  if (!s_abort && gridDim.y == 1) {
+    // every output column is in this CTA: stage 64 points' columns in shared
+    // memory (the A/B stage buffers are free now; rows padded to an odd
+    // stride) and write each point's f, g and full H in output order, lanes
+    // over consecutive addresses
+    constexpr int NCS = Cf::NC + 1;
+    static_assert(64 * NCS * 4 <= 2 * Cf::ABYTES + 2 * Cf::BBYTES, "staging tile fits the stage buffers");
+    float* S = (float*)sm;
+    const int nn = n * n, lane = tid & 31;
+    constexpr int kCols = Cf::NC / (kGemmThreads / 128);
+    for (int hf = 0; hf < 2; ++hf) {
+      if (((wid & 3) >> 1) == hf) {  // TMEM quadrants 2hf, 2hf+1 hold rows 64hf..64hf+63
+        const int rloc = ((wid & 3) & 1) * 32 + lane;
+        for (int c = (wid >> 2) * kCols; c < ((wid >> 2) + 1) * kCols; c += 16) {
+          float v[16];
+          tmem_ld16(taddr + ((uint32_t)((wid & 3) * 32) << 16) + c, v);  // all lanes of the warp take part
+          const bool have = KIND == 0 ? s_started[c / 256] != 0 : s_started[0] != 0;
+#pragma unroll
+          for (int q = 0; q < 16; ++q) S[rloc * NCS + c + q] = have ? v[q] : 0.0f;
+        }
+      }
+      __syncthreads();
+      for (int pr = wid; pr < 64; pr += kGemmThreads / 32) {
+        const int64_t p = p0 + 64 * hf + pr;
+        if (p >= a.P) continue;
+        const float* Sr = S + pr * NCS;
+        for (int k = lane; k <= n; k += 32) {  // column 0: f; column 1 + i: g_i
+          const double y = (double)Sr[k] * (double)a.scale[k];
+          if (k == 0) a.F[p] = y;
+          else if (a.order >= 1) a.G[p * n + (k - 1)] = y;
+        }
+        if (a.order >= 2) {
+          int i = lane / n, j = lane - (lane / n) * n;
+          for (int k = lane; k < nn; k += 32) {
+            const int lo = min(i, j), hi = max(i, j);
+            const int col = 1 + n + lo * (2 * n - lo + 1) / 2 + (hi - lo);
+            a.H[p * nn + k] = (double)Sr[col] * (double)a.scale[col];
+            j += 32;
+            while (j >= n) {
+              j -= n;
+              ++i;
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
+  } else if (!s_abort) {
+    // several column chunks: warps w, w+4, w+8, w+12 read the same TMEM lane
+    // quadrant (rows 32(w%4)..) and split the columns between them
     const int64_t p = p0 + (wid & 3) * 32 + (tid & 31);
     const int nn = n * n;
     constexpr int kCols = Cf::NC / (kGemmThreads / 128);
@@ -576,7 +645,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_eval_kernel(GemmArgs a) 
 template <int KIND>
 constexpr size_t gemm_smem(int n, int Et) {
   using Cf = GemmCfg<KIND>;
-  return 1024 + 2 * (size_t)Cf::ABYTES + 2 * (size_t)Cf::BBYTES + (size_t)n * Et * 128 * 4;
+  return 1024 + 2 * (size_t)Cf::ABYTES + 2 * (size_t)Cf::BBYTES + (size_t)n * Et * 128 * 4 + 16 +
+         2 * (size_t)Cf::KT * sizeof(ClosMono);
 }
 
 // deepest power table that fits next to the stages (at least x itself)
