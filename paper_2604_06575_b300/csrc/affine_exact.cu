@@ -769,8 +769,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 1024 / NT : 1) exact_thir
     __syncthreads();
     {
       R* cw = c + wid * n;
-      TermRegs tr;
-      auto wget = [&](int sa, int sb) { return W[tr.var[sa] * n + tr.var[sb]]; };
+      auto wget = [&](int, int, int va, int vb) { return W[va * n + vb]; };
       auto emit = [&](int l, R val) { atomicAdd(&cw[l], val); };
       // terms of degree < 3 have no third derivatives: each group starts at
       // its first term of degree >= 3
@@ -778,7 +777,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 1024 / NT : 1) exact_thir
         constexpr int K = decltype(kc)::value;
         if constexpr (K >= 1) {
           for (int64_t t = pd.k3off[K] + tid; t < pd.koff[K + 1]; t += NT) {
-            tr = load_term(pd.terms, t);
+            const TermRegs tr = load_term(pd.terms, t);
             term_third_group<R, K>(tr, pw, E1, wget, emit);
           }
         }

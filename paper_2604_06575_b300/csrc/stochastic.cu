@@ -559,7 +559,7 @@ __global__ void __launch_bounds__(NT, 2) stochastic_kernel(StochArgs a) {
         constexpr int K = decltype(kc)::value;
         if constexpr (K >= 1) {
           const int32_t* hp = nullptr;
-          auto wget = [&](int sa, int sb) { return Zw[hp[sa * K + sb]]; };
+          auto wget = [&](int sa, int sb, int, int) { return Zw[hp[sa * K + sb]]; };
           auto emit = [&](int l, R val) { atomicAdd(&cbar[l], val); };
           for (int64_t t = a.k3off[K] + tid; t < a.koff[K + 1]; t += NT) {
             const TermRegs tr = load_term(a.terms, t);

@@ -144,9 +144,10 @@ __device__ __forceinline__ void term_derivs(const TermRegs& t, const R* __restri
 }
 
 // c_l += sum_{j,k} d_l d_j d_k (term)(x) * W(j, k) for every l in the support
-// of a term with exactly K active variables, W symmetric: `wget(a, b)` returns
-// W(var_a, var_b) for support slots a, b (so a caller may keep W by variable
-// or by the term's own slots), `emit(l, v)` adds v to c_l (l a variable).  The third-derivative tensor of a term
+// of a term with exactly K active variables, W symmetric: `wget(a, b, va, vb)`
+// returns W(va, vb) for support slots a, b holding variables va, vb (a caller
+// may look W up by variable or by the term's own slots), `emit(l, v)` adds v
+// to c_l (l a variable).  The third-derivative tensor of a term
 // is symmetric, so each index multiset {a, b, c} of support slots is visited
 // once: with D_m[s] = falling(a_s, m) x_s^(a_s - m) its entry is
 // prod_s D_{mult_s}[s]; slots outside the multiset contribute D_0 through
@@ -183,7 +184,7 @@ __device__ __forceinline__ void term_third_contract_k(const TermRegs& t, const R
 #pragma unroll
   for (int s = 0; s < K; ++s) {
     acc[s] = R(0);
-    Wd[s] = wget(s, s);
+    Wd[s] = wget(s, s, t.var[s], t.var[s]);
   }
 #pragma unroll
   for (int a = 0; a < K; ++a) {
@@ -193,7 +194,7 @@ __device__ __forceinline__ void term_third_contract_k(const TermRegs& t, const R
 #pragma unroll
     for (int b = a + 1; b < K; ++b) {
       const int vb = t.var[b];
-      const R Wab = wget(a, b);
+      const R Wab = wget(a, b, va, vb);
       const R ex_ab = pre[a] * mid_ab * suf[b + 1];  // product over slots != a, b
       const R Taab = D2[a] * D1[b] * ex_ab;
       const R Tabb = D1[a] * D2[b] * ex_ab;
@@ -203,8 +204,8 @@ __device__ __forceinline__ void term_third_contract_k(const TermRegs& t, const R
 #pragma unroll
       for (int cc = b + 1; cc < K; ++cc) {
         const R Tabc = D1[a] * D1[b] * D1[cc] * (pre[a] * mid_ab * mid_bc * suf[cc + 1]);
-        acc[a] += R(2) * Tabc * wget(b, cc);
-        acc[b] += R(2) * Tabc * wget(a, cc);
+        acc[a] += R(2) * Tabc * wget(b, cc, vb, t.var[cc]);
+        acc[b] += R(2) * Tabc * wget(a, cc, va, t.var[cc]);
         acc[cc] += R(2) * Tabc * Wab;
         mid_bc *= D0[cc];
       }
