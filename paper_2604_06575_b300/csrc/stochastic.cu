@@ -234,8 +234,11 @@ struct StochArgs {
 
 }  // namespace
 
-template <typename R, int NT, int QC>
-__global__ void __launch_bounds__(NT, 2) stochastic_kernel(StochArgs a) {
+// MINB: resident CTAs per SM the register budget is sized for (2, or 4 when
+// the point's shared memory allows four CTAs: latency hiding then pays for
+// a few spilled registers)
+template <typename R, int NT, int QC, int MINB>
+__global__ void __launch_bounds__(NT, MINB) stochastic_kernel(StochArgs a) {
   extern __shared__ __align__(16) unsigned char sm[];
   const int n = a.n, E1 = a.E + 1, tid = threadIdx.x;
   // shared: power table, vectors g, dg (|diag H|), e, cbar, Dinv; reductions
@@ -623,7 +626,7 @@ polylab_status launch_stoch(const polylab_plan* plan, const double* X, int64_t P
   PL_TRY(ensure_hessian_pattern(const_cast<polylab_plan*>(plan), s));
   const size_t smem = stoch_smem<R, QC>(n, E1, NT);
   if (smem > 220 * 1024) return POLYLAB_ERR_UNSUPPORTED;
-  auto k = stochastic_kernel<R, NT, QC>;
+  auto k = 4 * smem <= 200 * 1024 ? stochastic_kernel<R, NT, QC, 4> : stochastic_kernel<R, NT, QC, 2>;
   PL_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   PL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NT, smem));
