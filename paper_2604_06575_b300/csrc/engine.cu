@@ -280,12 +280,69 @@ __global__ void keep_flags(const double* __restrict__ sums, int64_t U, double ze
   if (u < U) keep[u] = fabs(sums[u]) > zeroprec ? 1u : 0u;
 }
 
-// Unrank a key into an exponent row (inverse of the rank formula above).
+// Unrank keys into exponent rows (inverse of the rank formula above).  A CTA
+// takes 128 consecutive merged keys: the binomial table and the CTA's rows go
+// to shared memory, each thread unranks one key into its kept row's slot, and
+// the kept rows (contiguous in the output, since kpos is the exclusive scan of
+// keep) leave as one coalesced byte range.
+constexpr int kUnpackThreads = 128;
+
 template <typename K>
-__global__ void unpack_rows(const K* __restrict__ ukeys, const double* __restrict__ sums,
-                            const uint32_t* __restrict__ keep, const uint32_t* __restrict__ kpos, int64_t U, int n,
-                            const K* __restrict__ S, int D1, uint8_t* __restrict__ out_exps,
-                            double* __restrict__ out_coef) {
+__global__ void __launch_bounds__(kUnpackThreads) unpack_rows(const K* __restrict__ ukeys,
+                                                              const double* __restrict__ sums,
+                                                              const uint32_t* __restrict__ keep,
+                                                              const uint32_t* __restrict__ kpos, int64_t U, int n,
+                                                              const K* __restrict__ S, int D1,
+                                                              uint8_t* __restrict__ out_exps,
+                                                              double* __restrict__ out_coef) {
+  extern __shared__ __align__(16) unsigned char sh[];
+  K* Ss = reinterpret_cast<K*>(sh);
+  uint8_t* rows = reinterpret_cast<uint8_t*>(Ss + (size_t)(n + 1) * D1);
+  __shared__ int s_count;
+  const int tid = threadIdx.x;
+  const int64_t u0 = (int64_t)blockIdx.x * kUnpackThreads, u = u0 + tid;
+  for (int i = tid; i < (n + 1) * D1; i += kUnpackThreads) Ss[i] = S[i];
+  for (int i = tid; i < kUnpackThreads * n; i += kUnpackThreads) rows[i] = 0;
+  if (tid == 0) s_count = 0;
+  __syncthreads();
+  const int64_t obase = kpos[u0];  // output row of the first kept key at or after u0
+  const bool kept = u < U && keep[u];
+  if (kept) {
+    atomicAdd(&s_count, 1);
+    const int64_t o = kpos[u];
+    uint8_t* row = rows + (o - obase) * n;
+    const K r = ukeys[u];
+    const int D = D1 - 1;
+    int d = 0;
+    while (d < D && Ss[n * D1 + d] <= r) ++d;
+    K w = r - (d > 0 ? Ss[n * D1 + d - 1] : K(0));
+    int R = d;
+    for (int c = n - 1; c >= 1 && R > 0; --c) {
+      const K top = Ss[c * D1 + R];
+      int a = 0;
+      while (a < R && top - Ss[c * D1 + (R - a - 1)] <= w) ++a;
+      if (a) {
+        w -= top - Ss[c * D1 + (R - a)];
+        R -= a;
+        row[c] = (uint8_t)a;
+      }
+    }
+    row[0] = (uint8_t)R;
+    out_coef[o] = sums[u];
+  }
+  __syncthreads();
+  uint8_t* dst = out_exps + obase * n;
+  const int bytes = s_count * n;
+  for (int i = tid; i < bytes; i += kUnpackThreads) dst[i] = rows[i];
+}
+
+// One thread per key writing its row directly: the fallback when a CTA's rows
+// and the binomial table do not fit in shared memory (very wide rows).
+template <typename K>
+__global__ void unpack_rows_direct(const K* __restrict__ ukeys, const double* __restrict__ sums,
+                                   const uint32_t* __restrict__ keep, const uint32_t* __restrict__ kpos, int64_t U,
+                                   int n, const K* __restrict__ S, int D1, uint8_t* __restrict__ out_exps,
+                                   double* __restrict__ out_coef) {
   const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (u >= U || !keep[u]) return;
   const int64_t o = kpos[u];
@@ -470,9 +527,17 @@ polylab_status run_pipeline(int n, int D, int64_t N, const std::vector<K>& Sh, i
   out->exps = (uint8_t*)alloc((size_t)M * n, ctx);
   out->coef = (double*)alloc((size_t)M * sizeof(double), ctx);
   if (!out->exps || !out->coef) return POLYLAB_ERR_OOM;
-  unpack_rows<K><<<(unsigned)ceil_div(U, 128), 128, 0, s>>>(ukeys, sums, keep, kpos, U, n, S, D1, out->exps,
-                                                            out->coef);
-  return launch_status("unpack_rows");
+  const size_t ush = (size_t)(n + 1) * D1 * sizeof(K) + (size_t)kUnpackThreads * n;
+  if (ush <= 160 * 1024) {
+    if (ush > 48 * 1024)
+      PL_CUDA(cudaFuncSetAttribute(unpack_rows<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ush));
+    unpack_rows<K><<<(unsigned)ceil_div(U, kUnpackThreads), kUnpackThreads, ush, s>>>(ukeys, sums, keep, kpos, U, n,
+                                                                                     S, D1, out->exps, out->coef);
+    return launch_status("unpack_rows");
+  }
+  unpack_rows_direct<K><<<(unsigned)ceil_div(U, 128), 128, 0, s>>>(ukeys, sums, keep, kpos, U, n, S, D1, out->exps,
+                                                                   out->coef);
+  return launch_status("unpack_rows_direct");
 }
 
 template <class Mem>
