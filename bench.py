@@ -635,18 +635,29 @@ def measure_crossover(pl, workloads, torch, dev):
 
 
 def measure_pd3(pl, workloads, torch, dev):
-    """simplify(p_d^3) for p_d = sum_{|a|<=d} x^a in 5 variables, as two
-    products (the paper's heavy-simplify family; it reports 0.158 s for
-    MPOLY-HP at d = 4 on its hardware)."""
+    """simplify(p_d^3) for p_d = sum_{|a|<=d} x^a in 5 variables (the paper's
+    heavy-simplify family; it reports 0.158 s for MPOLY-HP at d = 4 on its
+    hardware), as two products and as one polylab_pow call; plus the symbolic
+    Jacobian (one polylab_diff per variable) of the 5,000-term, 30-variable
+    evaluation polynomial.  Wall time of the calls (each synchronises)."""
+    def wall(fn):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        return round((time.perf_counter() - t0) * 1e3, 3), r
+
     out = {}
     for d in (2, 3, 4):
         dp = pl.to_device(workloads.dense_power_base(d), dev)
-        pl.mul(pl.mul(dp, dp), dp)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        c = pl.mul(pl.mul(dp, dp), dp)
-        torch.cuda.synchronize()
-        out[f"d{d}"] = dict(ms=round((time.perf_counter() - t0) * 1e3, 3), terms=c.m)
+        ms, c = wall(lambda: pl.mul(pl.mul(dp, dp), dp))
+        ms_pow, c2 = wall(lambda: pl.pow(dp, 3))
+        out[f"d{d}"] = dict(ms=ms, terms=c.m, pow_ms=ms_pow, pow_terms=c2.m)
+    poly, _ = workloads.eval_batch(P=1)
+    dp = pl.to_device(poly, dev)
+    ms, jac = wall(lambda: pl.jacobian(dp))
+    out["jacobian_n30_5000_terms"] = dict(ms=ms, polys=len(jac), terms=sum(j.m for j in jac))
     return out
 
 

@@ -114,6 +114,32 @@ polylab_status polylab_add(const polylab_poly* a, const polylab_poly* b, double 
                            polylab_poly_out* out, polylab_alloc_fn alloc, void* alloc_ctx,
                            polylab_stream stream);
 
+/* a - b (Table "coresemantics" "minus"): as polylab_add with the coefficients
+ * of b negated. */
+polylab_status polylab_sub(const polylab_poly* a, const polylab_poly* b, double zeroprec,
+                           polylab_poly_out* out, polylab_alloc_fn alloc, void* alloc_ctx,
+                           polylab_stream stream);
+
+/* p^k for k >= 0 (Table "coresemantics" "mpower"/"prod"; Sec. 6.3 builds p_d^3
+ * this way): the product of k copies of p, each partial product simplified
+ * as by polylab_mul.  Computed by binary exponentiation (squarings and
+ * products of squarings), so the coefficient sums are associated differently
+ * from a left-to-right product; k = 0 gives the constant 1 over p's
+ * variables.  Intermediates live in stream-ordered library memory; the
+ * result goes through `alloc` as for polylab_mul (out->var_ids: p.n_vars
+ * entries).  Synchronises `stream` once per partial product.  Errors as
+ * polylab_mul (POLYLAB_ERR_EXP_OVERFLOW when a power's exponent exceeds
+ * 255); POLYLAB_ERR_INVALID_ARG for k < 0. */
+polylab_status polylab_pow(const polylab_poly* p, int32_t k, double zeroprec, polylab_poly_out* out,
+                           polylab_alloc_fn alloc, void* alloc_ctx, polylab_stream stream);
+
+/* d p / d x_v for the variable with id `var_id` (Sec. 3.3: term by term,
+ * x^a -> a_v x^(a - e_v), terms without x_v vanish), simplified as by
+ * polylab_simplify; variables keep p's ids and order.  An id p does not have
+ * gives the zero polynomial (n_terms = 0).  Synchronises `stream` once. */
+polylab_status polylab_diff(const polylab_poly* p, uint64_t var_id, double zeroprec, polylab_poly_out* out,
+                            polylab_alloc_fn alloc, void* alloc_ctx, polylab_stream stream);
+
 /* polylab_simplify for callers that cannot allocate device memory while the
  * call runs -- a host application that reserved all device memory for its own
  * pool up front, or one that runs under a fixed memory budget where a

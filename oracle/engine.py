@@ -141,3 +141,47 @@ def coefficient_of(a, b, target_row_merged: np.ndarray) -> tuple[float, float]:
             tot += v
             absum += abs(v)
     return tot, absum
+
+
+def sub(a, b, zeroprec: float = 0.0):
+    """a - b (Table "coresemantics" "minus"): the sum of a and b with b's
+    coefficients negated, simplified as ``add``."""
+    return add(a, (b[0], b[1], -np.asarray(b[2], np.float64)), zeroprec)
+
+
+def power(p, k: int, zeroprec: float = 0.0):
+    """p^k (Table "coresemantics" "mpower"/"prod"): the left-to-right product
+    p * p * ... * p of k factors, each partial product simplified as by
+    ``mul``; k = 0 is the constant 1 over p's variables."""
+    if k < 0:
+        raise ValueError("negative power")
+    ids = np.asarray(p[0], dtype=np.uint64)
+    if k == 0:
+        n = len(ids)
+        one = np.ones(1)
+        return ids, np.zeros((1, n), np.uint8), one, one.copy()
+    acc = simplify(p[0], p[1], p[2], zeroprec)
+    for _ in range(k - 1):
+        acc = mul(acc[:3], p, zeroprec)
+    return acc
+
+
+def diff(p, var_id: int, zeroprec: float = 0.0):
+    """d p / d x_v for the variable with id ``var_id`` (Sec. 3.3: term by term,
+    c x^a -> a_v c x^(a - e_v); terms without x_v vanish), simplified; an id p
+    does not have gives the zero polynomial."""
+    ids = np.asarray(p[0], dtype=np.uint64)
+    exps = np.asarray(p[1])
+    coef = np.asarray(p[2], np.float64)
+    hit = np.nonzero(ids == np.uint64(var_id))[0]
+    if hit.size == 0:
+        n = len(ids)
+        return ids, np.zeros((0, n), np.uint8), np.zeros(0), np.zeros(0)
+    v = int(hit[0])
+    keep = exps[:, v] > 0
+    rows = exps[keep].astype(np.int64)
+    c = coef[keep] * rows[:, v]
+    rows[:, v] -= 1
+    e, cc, s = simplify_rows(rows.astype(np.uint8), c, zeroprec)
+    return ids, e, cc, s
+

@@ -144,6 +144,11 @@ void free_gemm_operand(GemmOperand* g, cudaStream_t s);
 
 polylab_status check_poly(const polylab_poly* p);
 
+// The engine (engine.cu): simplify, product, sum or difference of polynomials.
+constexpr int kSimplifyMode = 0, kMulMode = 1, kAddMode = 2, kSubMode = 3;
+polylab_status engine(const polylab_poly* pa, const polylab_poly* pb, int mode, double zeroprec,
+                      polylab_poly_out* out, polylab_alloc_fn alloc, void* ctx, cudaStream_t s);
+
 // Kernel launchers (one per translation unit)
 polylab_status eval_direct(const polylab_plan* plan, const double* X, int64_t P, int order, bool fp32,
                            double* F, double* G, double* H, cudaStream_t s);

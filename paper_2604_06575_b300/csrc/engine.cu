@@ -178,7 +178,9 @@ __global__ void mark_heads(const K* __restrict__ keys, int64_t N, uint32_t* __re
 
 // Coefficient of a sorted item: the input for simplify, one IEEE product for
 // mul, the input of either operand for add.
-enum Mode { kSimplify = 0, kMul = 1, kAdd = 2 };
+enum Mode { kSimplify = 0, kMul = 1, kAdd = 2, kSub = 3 };  // kSub: a - b, terms as kAdd
+static_assert(kSimplify == kSimplifyMode && kMul == kMulMode && kAdd == kAddMode && kSub == kSubMode,
+              "engine modes as declared in common.cuh");
 
 struct CoefOf {
   const double* ca;
@@ -188,6 +190,7 @@ struct CoefOf {
   __device__ __forceinline__ double operator()(uint32_t idx) const {
     if (mode == kSimplify) return ca[idx];
     if (mode == kAdd) return idx < ma ? ca[idx] : cb[idx - ma];
+    if (mode == kSub) return idx < ma ? ca[idx] : -cb[idx - ma];
     const int64_t i = idx / mb, j = idx - i * mb;
     return ca[i] * cb[j];
   }
@@ -472,7 +475,7 @@ polylab_status run_pipeline(int n, int D, int64_t N, const std::vector<K>& Sh, i
   if (mode == kMul) {
     keys_mul<K><<<(unsigned)ceil_div(N, 256), 256, 0, s>>>(A.ptr, A.col, A.ex, A.deg, B.ptr, B.col, B.ex, B.deg, A.m,
                                                            B.m, n, S, D1, keys, vals, ovf);
-  } else if (mode == kAdd) {
+  } else if (mode == kAdd || mode == kSub) {
     keys_add<K><<<(unsigned)ceil_div(N, 256), 256, 0, s>>>(A.ptr, A.col, A.ex, A.deg, B.ptr, B.col, B.ex, B.deg, A.m,
                                                            B.m, n, S, D1, keys, vals);
   } else {
@@ -571,14 +574,14 @@ polylab_status engine_with(Mem& scr, const polylab_poly* pa, const polylab_poly*
   out->exps = nullptr;
   out->coef = nullptr;
   const int64_t N = mode == kMul ? pa->n_terms * pb->n_terms
-                   : mode == kAdd ? pa->n_terms + pb->n_terms : pa->n_terms;
+                   : (mode == kAdd || mode == kSub) ? pa->n_terms + pb->n_terms : pa->n_terms;
   if (N >= ((int64_t)1 << 31)) return POLYLAB_ERR_UNSUPPORTED;
   if (N == 0) return POLYLAB_OK;
   Operand A, B;
   PL_TRY(build_operand(pa, mapA, &A, scr, s));
   if (is_mul) PL_TRY(build_operand(pb, mapB, &B, scr, s));
   const int D = std::max(1, mode == kMul ? A.maxdeg + B.maxdeg
-                            : mode == kAdd ? std::max(A.maxdeg, B.maxdeg) : A.maxdeg);
+                            : (mode == kAdd || mode == kSub) ? std::max(A.maxdeg, B.maxdeg) : A.maxdeg);
   std::vector<u128> S128;
   if (!build_table<u128>(n, D, S128)) return POLYLAB_ERR_UNSUPPORTED;
   const u128 total = S128[(size_t)n * (D + 1) + D];
@@ -592,11 +595,16 @@ polylab_status engine_with(Mem& scr, const polylab_poly* pa, const polylab_poly*
   return run_pipeline<u128, Mem>(n, D, N, S128, mode, A, B, pa, pb, zeroprec, bits, out, alloc, ctx, scr, s);
 }
 
+}  // namespace
+
+// (declared in common.cuh; the algebra entry points call it too)
 polylab_status engine(const polylab_poly* pa, const polylab_poly* pb, int mode, double zeroprec,
                       polylab_poly_out* out, polylab_alloc_fn alloc, void* ctx, cudaStream_t s) {
   Scratch scr(s);
   return engine_with(scr, pa, pb, mode, zeroprec, out, alloc, ctx, s);
 }
+
+namespace {
 
 // ------------------------------------------------ no-allocation simplify
 // For callers that may not allocate device memory during a call: all scratch
@@ -695,6 +703,12 @@ polylab_status polylab_add(const polylab_poly* a, const polylab_poly* b, double 
                            polylab_alloc_fn alloc, void* alloc_ctx, polylab_stream stream) {
   if (!b) return POLYLAB_ERR_INVALID_ARG;
   return polylab::engine(a, b, polylab::kAdd, zeroprec, out, alloc, alloc_ctx, (cudaStream_t)stream);
+}
+
+polylab_status polylab_sub(const polylab_poly* a, const polylab_poly* b, double zeroprec, polylab_poly_out* out,
+                           polylab_alloc_fn alloc, void* alloc_ctx, polylab_stream stream) {
+  if (!b) return POLYLAB_ERR_INVALID_ARG;
+  return polylab::engine(a, b, polylab::kSub, zeroprec, out, alloc, alloc_ctx, (cudaStream_t)stream);
 }
 
 polylab_status polylab_simplify_noalloc(const polylab_poly* p, double zeroprec, polylab_poly_out* out,

@@ -81,6 +81,11 @@ _lib.polylab_simplify.argtypes = [C.POINTER(_Poly), C.c_double, C.POINTER(_PolyO
 _lib.polylab_mul.argtypes = [C.POINTER(_Poly), C.POINTER(_Poly), C.c_double, C.POINTER(_PolyOut), ALLOC_FN,
                              C.c_void_p, C.c_void_p]
 _lib.polylab_add.argtypes = _lib.polylab_mul.argtypes
+_lib.polylab_sub.argtypes = _lib.polylab_mul.argtypes
+_lib.polylab_pow.argtypes = [C.POINTER(_Poly), C.c_int32, C.c_double, C.POINTER(_PolyOut), ALLOC_FN, C.c_void_p,
+                             C.c_void_p]
+_lib.polylab_diff.argtypes = [C.POINTER(_Poly), C.c_uint64, C.c_double, C.POINTER(_PolyOut), ALLOC_FN, C.c_void_p,
+                              C.c_void_p]
 _lib.polylab_simplify_noalloc.argtypes = [C.POINTER(_Poly), C.c_double, C.POINTER(_PolyOut), C.c_int64, C.c_void_p]
 _lib.polylab_an_opts_default.argtypes = [C.POINTER(_AnOpts)]
 _PP = C.POINTER(C.c_void_p)
@@ -106,7 +111,8 @@ _lib.polylab_mlp_pack.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
 _lib.polylab_affine_normal_batched.argtypes = [C.c_int32, C.c_void_p, _PP, _PP, C.POINTER(C.c_int64),
                                                C.POINTER(_AnOpts), _PP, _PP, _PP, C.c_void_p]
 for _f in ("polylab_plan_create", "polylab_plan_destroy", "polylab_eval_derivs", "polylab_affine_normal",
-           "polylab_simplify", "polylab_mul", "polylab_add", "polylab_simplify_noalloc", "polylab_batch_create",
+           "polylab_simplify", "polylab_mul", "polylab_add", "polylab_sub", "polylab_pow", "polylab_diff",
+           "polylab_simplify_noalloc", "polylab_batch_create",
            "polylab_batch_run", "polylab_batch_run_stage", "polylab_batch_check", "polylab_batch_get_config",
            "polylab_batch_set_config", "polylab_batch_autotune", "polylab_batch_destroy", "polylab_affine_normal_batched",
            "polylab_plan_gemm_info", "polylab_mlp_init",
@@ -114,6 +120,7 @@ for _f in ("polylab_plan_create", "polylab_plan_destroy", "polylab_eval_derivs",
     getattr(_lib, _f).restype = C.c_int
 
 EXPORTED = ["polylab_status_string", "polylab_last_error", "polylab_simplify", "polylab_mul", "polylab_add",
+            "polylab_sub", "polylab_pow", "polylab_diff",
             "polylab_plan_create", "polylab_plan_destroy", "polylab_plan_closure_size", "polylab_eval_derivs",
             "polylab_an_opts_default", "polylab_affine_normal", "polylab_simplify_noalloc", "polylab_batch_create",
             "polylab_batch_run", "polylab_batch_run_stage", "polylab_batch_check", "polylab_batch_get_config",
@@ -313,6 +320,32 @@ def add(a: DevPoly, b: DevPoly, zeroprec: float = 0.0) -> DevPoly:
     return _run_out("polylab_add",
                     lambda o, fn: _lib.polylab_add(C.byref(ca), C.byref(cb), zeroprec, o, fn, None, _stream()),
                     a.n + b.n, a.coef.device)
+
+
+def sub(a: DevPoly, b: DevPoly, zeroprec: float = 0.0) -> DevPoly:
+    ca, cb = a.cstruct(), b.cstruct()
+    return _run_out("polylab_sub",
+                    lambda o, fn: _lib.polylab_sub(C.byref(ca), C.byref(cb), zeroprec, o, fn, None, _stream()),
+                    a.n + b.n, a.coef.device)
+
+
+def pow(p: DevPoly, k: int, zeroprec: float = 0.0) -> DevPoly:
+    cp = p.cstruct()
+    return _run_out("polylab_pow",
+                    lambda o, fn: _lib.polylab_pow(C.byref(cp), k, zeroprec, o, fn, None, _stream()),
+                    p.n, p.coef.device)
+
+
+def diff(p: DevPoly, var_id: int, zeroprec: float = 0.0) -> DevPoly:
+    cp = p.cstruct()
+    return _run_out("polylab_diff",
+                    lambda o, fn: _lib.polylab_diff(C.byref(cp), int(var_id), zeroprec, o, fn, None, _stream()),
+                    p.n, p.coef.device)
+
+
+def jacobian(p: DevPoly, zeroprec: float = 0.0) -> list:
+    """The n partial derivatives of p (one polylab_diff per variable)."""
+    return [diff(p, int(v), zeroprec) for v in p.var_ids]
 
 
 def simplify_noalloc(p: DevPoly, exps_out: torch.Tensor, coef_out: torch.Tensor, zeroprec: float = 0.0) -> DevPoly:
