@@ -550,7 +550,43 @@ def measure_rows(pl, workloads, torch, dev, p32, p64):
     rows["stochastic"] = measure_stochastic(pl, workloads, torch, dev, p32)
     rows["crossover"] = measure_crossover(pl, workloads, torch, dev)
     rows["simplify_pd_cubed"] = measure_pd3(pl, workloads, torch, dev)
+    rows["affine_ad"] = measure_ad(pl, workloads, torch, dev, p64)
     return rows
+
+
+def measure_ad(pl, workloads, torch, dev, p64):
+    """The 'ad' route (third-derivative tensor materialised per point, FP64)
+    beside MF-logDet-Exact (FP64) on the same points: n = 6 with 17 random
+    quartic terms (the accuracy table's shape) at 65,536 points, and n = 20
+    with 400 random terms of degree <= 6 at 16,384 points.  The ALU figure
+    counts the tensor contraction alone, m (n^3 + n^2 m + m^2 n) FMAs per
+    point (m = n - 1), against the measured FP64 FMA peak."""
+    stream = torch.cuda.current_stream()
+    out = {}
+    cases = [("n6_17_terms", workloads.sparse_quartic(6, 17, 3, P=65536))]
+    rng = np.random.default_rng(20)
+    e = workloads.sparse_monomials(rng, 20, 400, 6, 6)
+    cases.append(("n20_400_terms", (workloads.convexified(rng, 20, e, 0.1), workloads.shell_points(rng, 20, 16384))))
+    for name, (poly, X) in cases:
+        dp = pl.to_device(poly, dev)
+        Xd = torch.as_tensor(X, device=dev)
+        P, n = X.shape
+        m = n - 1
+        with pl.Plan(dp) as plan:
+            ms_ad, (Da, _, ia) = _time_call(torch, lambda: pl.affine_normal(dp, Xd, plan=plan, method="ad"), stream)
+            ms_ex, (De, _, ie) = _time_call(torch, lambda: pl.affine_normal(dp, Xd, plan=plan), stream)
+        ok = (pl.info_numpy(ia)["flags"] == 0) & (pl.info_numpy(ie)["flags"] == 0)
+        okd = torch.as_tensor(ok, device=dev)
+        rel = (Da[okd] - De[okd]).norm(dim=1) / De[okd].norm(dim=1)
+        fl = 2.0 * m * (n ** 3 + n * n * m + m * m * n) * P
+        ach = fl / (ms_ad * 1e-3) / 1e12
+        out[name] = dict(points=P, terms=poly.m, ad_ms=round(ms_ad, 3), exact_ms=round(ms_ex, 3),
+                         ad_dirs_per_s=round(P / (ms_ad * 1e-3), 1),
+                         max_rel_diff_ad_vs_exact=float(rel.max()) if rel.numel() else None,
+                         roofline=dict(bound="alu", achieved=round(ach, 4), peak=round(p64, 4), unit="TFLOP/s",
+                                       frac=round(ach / p64, 4) if p64 else None, note="tensor contraction FMAs only; "
+                                                                      "measured FP64 FMA peak"))
+    return out
 
 
 def _time_call(torch, fn, stream):
@@ -573,7 +609,7 @@ def measure_stochastic(pl, workloads, torch, dev, p32):
     """Large sparse family (n in {500, 1000, 2000}, 20n random terms of degree
     <= 4, 4,096 points in [-1,1]^n): MF-logDet-Stochastic, FP32, q = 16,
     tol 1e-4, maxit 80; Jacobi at every n, the learned preconditioner (trained
-    on 48 other points) and the exact form at n = 500 as the judge of error."""
+    on 48 other points) and the exact form at n = 500 as the reference for the error."""
     stream = torch.cuda.current_stream()
     out = {}
     r = 1e-4

@@ -220,7 +220,12 @@ polylab_status polylab_eval_derivs(const polylab_poly* p, const polylab_plan* pl
 
 /* ------------------------------------------------------------ affine normal (Sec. 5) */
 
-typedef enum { POLYLAB_MF_EXACT = 0, POLYLAB_MF_STOCHASTIC = 1 } polylab_an_method;
+/* Sec. 5 lists three methods: 'mf-exact' (MF-logDet-Exact, the default),
+ * 'mf-stochastic' (MF-logDet-Stochastic) and 'ad', the reference route that
+ * forms the derivatives literally, the full third-derivative tensor included
+ * (POLYLAB_AD: n <= POLYLAB_AD_MAX_N, FP64 only). */
+typedef enum { POLYLAB_MF_EXACT = 0, POLYLAB_MF_STOCHASTIC = 1, POLYLAB_AD = 2 } polylab_an_method;
+#define POLYLAB_AD_MAX_N 24
 typedef enum {
   POLYLAB_PRECOND_JACOBI = 0,  /* |diag(H)| + r of the ambient Hessian, projected      */
   POLYLAB_PRECOND_NONE = 1,
@@ -263,7 +268,12 @@ typedef struct {
  *   a_i = tr(H_T^{-1} d_{t_i} H_T), tau = H_T^{-1}(h - |g|/(n+1) a),
  *   D = nu = Q_T tau - e   (the paper's d: nu . e = -1, not unit length).
  * MF_EXACT forms a with the exact trace; MF_STOCHASTIC with a Hutchinson
- * estimate over num_probes probes and preconditioned CG solves.
+ * estimate over num_probes probes and preconditioned CG solves; AD from the
+ * materialised third-derivative tensor T: a_i = tr(H_T^{-1} Q_T^T S_i Q_T)
+ * with S_i = sum_l T(l, :, :) (Q_T)_li, one CTA per point, FP64, every
+ * per-point array in shared memory (POLYLAB_ERR_UNSUPPORTED when n >
+ * POLYLAB_AD_MAX_N or the arrays do not fit; POLYLAB_ERR_INVALID_ARG unless
+ * prec is POLYLAB_FP64).
  * X: DEVICE P x n.  D: DEVICE P x n.  Dunit: DEVICE P x n or NULL (nu/|nu|).
  * info: DEVICE array of P records or NULL.  Flagged points get NaN rows. */
 polylab_status polylab_affine_normal(const polylab_poly* p, const polylab_plan* plan, const double* X,

@@ -50,7 +50,8 @@ polylab_status polylab_affine_normal(const polylab_poly* p, const polylab_plan* 
                                      polylab_stream stream) {
   if (!o || P < 0 || (!p && !plan)) return POLYLAB_ERR_INVALID_ARG;
   if (P > 0 && (!X || !D)) return POLYLAB_ERR_INVALID_ARG;
-  if (o->method != POLYLAB_MF_EXACT && o->method != POLYLAB_MF_STOCHASTIC) return POLYLAB_ERR_INVALID_ARG;
+  if (o->method != POLYLAB_MF_EXACT && o->method != POLYLAB_MF_STOCHASTIC && o->method != POLYLAB_AD)
+    return POLYLAB_ERR_INVALID_ARG;
   if (o->prec != POLYLAB_FP64 && o->prec != POLYLAB_FP32) return POLYLAB_ERR_INVALID_ARG;
   if (!(o->regularization >= 0.0)) return POLYLAB_ERR_INVALID_ARG;
   if (o->method == POLYLAB_MF_STOCHASTIC) {
@@ -62,6 +63,7 @@ polylab_status polylab_affine_normal(const polylab_poly* p, const polylab_plan* 
   PlanRef pr(s);
   PL_TRY(pr.init(p, plan, POLYLAB_PLAN_TERMS));
   if (o->method == POLYLAB_MF_EXACT) return affine_exact(pr.plan, X, P, o, D, Dunit, info, s);
+  if (o->method == POLYLAB_AD) return affine_ad(pr.plan, X, P, o, D, Dunit, info, s);
   return affine_stochastic(pr.plan, X, P, o, D, Dunit, info, s);
 }
 

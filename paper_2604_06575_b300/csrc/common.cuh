@@ -156,6 +156,8 @@ polylab_status eval_gemm(const polylab_plan* plan, const double* X, int64_t P, i
                          double* F, double* G, double* H, cudaStream_t s);
 polylab_status affine_exact(const polylab_plan* plan, const double* X, int64_t P, const polylab_an_opts* o,
                             double* D, double* Dunit, polylab_an_info* info, cudaStream_t s);
+polylab_status affine_ad(const polylab_plan* plan, const double* X, int64_t P, const polylab_an_opts* o, double* D,
+                         double* Dunit, polylab_an_info* info, cudaStream_t s);
 polylab_status affine_stochastic(const polylab_plan* plan, const double* X, int64_t P,
                                  const polylab_an_opts* o, double* D, double* Dunit, polylab_an_info* info,
                                  cudaStream_t s);

@@ -24,7 +24,8 @@ OK = 0
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "EXP_OVERFLOW", 3: "DUP_VAR_ID", 4: "OOM", 5: "CUDA", 6: "TIMEOUT",
           7: "UNSUPPORTED"}
 PREC = {"fp64": 0, "tf32x3": 1, "bf16": 2, "fp32": 3}
-METHOD = {"mf-exact": 0, "mf-stochastic": 1}
+METHOD = {"mf-exact": 0, "mf-stochastic": 1, "ad": 2}
+AD_MAX_N = 24
 PRECOND = {"jacobi": 0, "none": 1, "mlp": 2}
 FLAG_ZERO_GRAD, FLAG_NOT_PD, FLAG_KRYLOV_MAXIT = 1, 2, 4
 

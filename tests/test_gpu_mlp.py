@@ -1,6 +1,6 @@
 """Learned preconditioner: the data kernel and the hand-written backward pass
 against the FP64 oracle, and a trained network used inside the stochastic
-solver (gain over the method without it; the exact variant judges the error).
+solver (gain over the method without it; the exact variant is the reference for the error).
 
 Bars: features, diagonal, e and y within 1e-4 relative (FP32); loss within
 1e-4 and gradient within 2e-3 (relative, norm-wise) of the oracle's on the same
