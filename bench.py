@@ -551,7 +551,64 @@ def measure_rows(pl, workloads, torch, dev, p32, p64):
     rows["crossover"] = measure_crossover(pl, workloads, torch, dev)
     rows["simplify_pd_cubed"] = measure_pd3(pl, workloads, torch, dev)
     rows["affine_ad"] = measure_ad(pl, workloads, torch, dev, p64)
+    rows["precision"] = measure_precision(pl, workloads, torch, dev)
     return rows
+
+
+def measure_precision(pl, workloads, torch, dev):
+    """Double versus single storage on the core and affine workloads of the
+    paper's precision table: the 4,000,000-product pair (mul), p_4^3 in 5
+    variables (pow), f/grad/Hessian on the n = 30 batch (65,536 points), and
+    MF-logDet-Exact / -Stochastic on a support-3 sparse quartic with n = 80,
+    m = 320 (4,096 points; stochastic q = 8, tol 1e-4, maxit 40).  The engine
+    rows include their host synchronisations; ms per call, median of 5."""
+    stream = torch.cuda.current_stream()
+
+    def wall(fn):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(5):
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            ts.append((time.perf_counter() - t0) * 1e3)
+        return statistics.median(ts)
+
+    def dev_ms(fn):
+        ts = []
+        for _ in range(5):
+            ms, _ = _time_call(torch, fn, stream)
+            ts.append(ms)
+        return statistics.median(ts)
+
+    out = {}
+    A, B = workloads.product_pair()
+    pd = workloads.dense_power_base(4)
+    ev, Xe = workloads.eval_batch()
+    aq, Xa = workloads.sparse_quartic(80, 320, 3, P=4096)
+    for name, dt in (("double", torch.float64), ("single", torch.float32)):
+        row = {}
+        da, db = pl.to_device(A, dev, dtype=dt), pl.to_device(B, dev, dtype=dt)
+        row["mul_ms"] = round(wall(lambda: pl.mul(da, db)), 3)
+        dpp = pl.to_device(pd, dev, dtype=dt)
+        row["pow_ms"] = round(wall(lambda: pl.pow(dpp, 3)), 3)
+        de = pl.to_device(ev, dev, dtype=dt)
+        Xd = torch.as_tensor(Xe, device=dev, dtype=dt)
+        with pl.Plan(de) as plan:
+            row["eval_ms"] = round(dev_ms(lambda: pl.eval_derivs(de, Xd, plan=plan)), 3)
+        del Xd
+        dq = pl.to_device(aq, dev, dtype=dt)
+        Xq = torch.as_tensor(Xa, device=dev, dtype=dt)
+        prec = "fp32" if dt == torch.float32 else "fp64"
+        with pl.Plan(dq) as plan:
+            row["exact_ms"] = round(dev_ms(lambda: pl.affine_normal(dq, Xq, plan=plan, prec=prec)), 3)
+            row["stochastic_ms"] = round(dev_ms(lambda: pl.affine_normal(
+                dq, Xq, plan=plan, prec=prec, method="mf-stochastic", num_probes=8, krylov_tol=1e-4,
+                krylov_maxit=40)), 3)
+        out[name] = row
+    out["double_over_single"] = {k: round(out["double"][k] / out["single"][k], 2) for k in out["double"]}
+    return out
 
 
 def measure_ad(pl, workloads, torch, dev, p64):

@@ -403,6 +403,71 @@ polylab_status polylab_affine_normal_batched(int32_t n_polys, const polylab_poly
                                              double* const* Dunit, polylab_an_info* const* info,
                                              polylab_stream stream);
 
+/* ----------------------------------------------------- single-precision storage */
+
+/* The paper's precision control (Sec. 3.5: polylab_precision('set','single'),
+ * after which new polynomials carry single-precision coefficients and the
+ * core operations and affine-normal routes run in single precision; Table
+ * "precision" of Sec. 6 compares eval, simplify, mpower, MF-logDet-Exact and
+ * MF-logDet-Stochastic in double and single).  Here the precision is a
+ * property of the data: polylab_poly_f32 is polylab_poly with FP32
+ * coefficients, and each call below is its FP64 namesake with:
+ *   engine calls (simplify/mul/add/sub/pow/diff): coefficients read as FP32,
+ *     products, negation and merged sums computed in FP32 (sums in an order
+ *     of the library's choosing), stored FP32; the zeroprec test compares
+ *     |c| of the FP32 sum (exactly widened) with zeroprec; exponents and the
+ *     term order are those of the FP64 call, bit for bit;
+ *   polylab_plan_create_f32: a plan usable by every call that takes a plan
+ *     (the FP32 coefficients are held exactly);
+ *   polylab_eval_derivs_f32: the POLYLAB_FP32 direct form (FP32 power
+ *     tables, term products and sums) with FP32 points X (P x n) and FP32
+ *     outputs F, G, H laid out as in polylab_eval_derivs;
+ *   polylab_affine_normal_f32: the POLYLAB_FP32 form of the route in
+ *     opts->method (MF_EXACT or MF_STOCHASTIC; opts->prec must be
+ *     POLYLAB_FP32) at FP32 points, D and Dunit rounded to FP32; the points
+ *     are widened on the device into stream-ordered scratch first.
+ * Argument rules, errors and synchronisation are those of the FP64 calls. */
+typedef struct {
+  int32_t n_vars;
+  const uint64_t* var_ids;  /* HOST                    */
+  int64_t n_terms;
+  const uint8_t* exps;      /* DEVICE, m x n row-major */
+  const float* coef;        /* DEVICE, m coefficients  */
+} polylab_poly_f32;
+
+typedef struct {
+  int32_t n_vars;
+  uint64_t* var_ids;
+  int64_t n_terms;
+  uint8_t* exps;
+  float* coef;              /* n_terms, from alloc */
+} polylab_poly_out_f32;
+
+polylab_status polylab_simplify_f32(const polylab_poly_f32* p, double zeroprec, polylab_poly_out_f32* out,
+                                    polylab_alloc_fn alloc, void* alloc_ctx, polylab_stream stream);
+polylab_status polylab_mul_f32(const polylab_poly_f32* a, const polylab_poly_f32* b, double zeroprec,
+                               polylab_poly_out_f32* out, polylab_alloc_fn alloc, void* alloc_ctx,
+                               polylab_stream stream);
+polylab_status polylab_add_f32(const polylab_poly_f32* a, const polylab_poly_f32* b, double zeroprec,
+                               polylab_poly_out_f32* out, polylab_alloc_fn alloc, void* alloc_ctx,
+                               polylab_stream stream);
+polylab_status polylab_sub_f32(const polylab_poly_f32* a, const polylab_poly_f32* b, double zeroprec,
+                               polylab_poly_out_f32* out, polylab_alloc_fn alloc, void* alloc_ctx,
+                               polylab_stream stream);
+polylab_status polylab_pow_f32(const polylab_poly_f32* p, int32_t k, double zeroprec, polylab_poly_out_f32* out,
+                               polylab_alloc_fn alloc, void* alloc_ctx, polylab_stream stream);
+polylab_status polylab_diff_f32(const polylab_poly_f32* p, uint64_t var_id, double zeroprec,
+                                polylab_poly_out_f32* out, polylab_alloc_fn alloc, void* alloc_ctx,
+                                polylab_stream stream);
+polylab_status polylab_plan_create_f32(const polylab_poly_f32* p, uint32_t what, polylab_stream stream,
+                                       polylab_plan** plan);
+polylab_status polylab_eval_derivs_f32(const polylab_poly_f32* p, const polylab_plan* plan, const float* X,
+                                       int64_t P, int32_t order, float* F, float* G, float* H,
+                                       polylab_stream stream);
+polylab_status polylab_affine_normal_f32(const polylab_poly_f32* p, const polylab_plan* plan, const float* X,
+                                         int64_t P, const polylab_an_opts* opts, float* D, float* Dunit,
+                                         polylab_an_info* info, polylab_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

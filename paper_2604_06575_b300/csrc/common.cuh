@@ -5,6 +5,8 @@
 #include <stdint.h>
 
 #include <string>
+#include <type_traits>
+#include <unordered_set>
 #include <vector>
 
 #include "polylab.h"
@@ -135,23 +137,74 @@ struct polylab_plan {
 
 namespace polylab {
 
-// Fill `plan` (terms, m, n, max_exp, max_support); synchronises `s`.
-polylab_status build_term_plan(const polylab_poly* p, cudaStream_t s, polylab_plan* plan);
+// A polynomial with FP64 or FP32 coefficients (the two storage precisions of
+// the C ABI: polylab_poly / polylab_poly_f32), as the engine and the plan
+// builder see it.
+template <typename C>
+struct PolyIn {
+  int32_t n_vars;
+  const uint64_t* var_ids;
+  int64_t n_terms;
+  const uint8_t* exps;
+  const C* coef;
+};
+template <typename C>
+struct PolyOut {
+  int32_t n_vars;
+  uint64_t* var_ids;
+  int64_t n_terms;
+  uint8_t* exps;
+  C* coef;
+};
+template <typename Pub>
+using coef_of = std::remove_cv_t<std::remove_pointer_t<decltype(Pub::coef)>>;
+template <typename Pub>
+inline PolyIn<coef_of<Pub>> poly_in(const Pub& p) {
+  return {p.n_vars, p.var_ids, p.n_terms, p.exps, p.coef};
+}
+template <typename Pub>
+inline PolyOut<coef_of<Pub>> poly_out(const Pub& o) {
+  return {o.n_vars, o.var_ids, o.n_terms, o.exps, o.coef};
+}
+template <typename Pub>
+inline void store_out(const PolyOut<coef_of<Pub>>& o, Pub* out) {
+  out->n_vars = o.n_vars;
+  out->n_terms = o.n_terms;
+  out->exps = o.exps;
+  out->coef = o.coef;
+}
+
+template <typename C>
+polylab_status check_poly(const PolyIn<C>* p) {
+  if (!p || p->n_vars < 1 || p->n_terms < 0 || !p->var_ids) return POLYLAB_ERR_INVALID_ARG;
+  if (p->n_terms > 0 && (!p->exps || !p->coef)) return POLYLAB_ERR_INVALID_ARG;
+  std::unordered_set<uint64_t> seen;
+  for (int i = 0; i < p->n_vars; ++i)
+    if (!seen.insert(p->var_ids[i]).second) return POLYLAB_ERR_DUP_VAR_ID;
+  return POLYLAB_OK;
+}
+
+// Fill `plan` (terms, m, n, max_exp, max_support); synchronises `s`.  FP32
+// coefficients are held in the term list exactly (as doubles).
+template <typename C>
+polylab_status build_term_plan(const PolyIn<C>* p, cudaStream_t s, polylab_plan* plan);
 // Build the Hessian sparsity pattern of `plan` if absent (synchronises `s`).
 polylab_status ensure_hessian_pattern(polylab_plan* plan, cudaStream_t s);
 polylab_status build_gemm_operand(polylab_plan* plan, cudaStream_t s);
 void free_gemm_operand(GemmOperand* g, cudaStream_t s);
 
-polylab_status check_poly(const polylab_poly* p);
-
-// The engine (engine.cu): simplify, product, sum or difference of polynomials.
+// The engine (engine.cu): simplify, product, sum or difference of
+// polynomials, coefficient arithmetic and storage in C (double or float).
 constexpr int kSimplifyMode = 0, kMulMode = 1, kAddMode = 2, kSubMode = 3;
-polylab_status engine(const polylab_poly* pa, const polylab_poly* pb, int mode, double zeroprec,
-                      polylab_poly_out* out, polylab_alloc_fn alloc, void* ctx, cudaStream_t s);
+template <typename C>
+polylab_status engine(const PolyIn<C>* pa, const PolyIn<C>* pb, int mode, double zeroprec, PolyOut<C>* out,
+                      polylab_alloc_fn alloc, void* ctx, cudaStream_t s);
 
 // Kernel launchers (one per translation unit)
 polylab_status eval_direct(const polylab_plan* plan, const double* X, int64_t P, int order, bool fp32,
                            double* F, double* G, double* H, cudaStream_t s);
+polylab_status eval_direct_f32(const polylab_plan* plan, const float* X, int64_t P, int order, float* F, float* G,
+                               float* H, cudaStream_t s);
 polylab_status eval_gemm(const polylab_plan* plan, const double* X, int64_t P, int order, int prec,
                          double* F, double* G, double* H, cudaStream_t s);
 polylab_status affine_exact(const polylab_plan* plan, const double* X, int64_t P, const polylab_an_opts* o,

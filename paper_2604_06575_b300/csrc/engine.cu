@@ -182,12 +182,15 @@ enum Mode { kSimplify = 0, kMul = 1, kAdd = 2, kSub = 3 };  // kSub: a - b, term
 static_assert(kSimplify == kSimplifyMode && kMul == kMulMode && kAdd == kAddMode && kSub == kSubMode,
               "engine modes as declared in common.cuh");
 
+// Coefficient of sort item idx, in the coefficient type C of the operands
+// (products and negation in C).
+template <typename C>
 struct CoefOf {
-  const double* ca;
-  const double* cb;
+  const C* ca;
+  const C* cb;
   int64_t ma, mb;
   int mode;
-  __device__ __forceinline__ double operator()(uint32_t idx) const {
+  __device__ __forceinline__ C operator()(uint32_t idx) const {
     if (mode == kSimplify) return ca[idx];
     if (mode == kAdd) return idx < ma ? ca[idx] : cb[idx - ma];
     if (mode == kSub) return idx < ma ? ca[idx] : -cb[idx - ma];
@@ -201,10 +204,10 @@ struct CoefOf {
 // Within a 32-item window a Hillis-Steele segmented scan on (head, value)
 // runs over shuffles; the open segment's partial sum is carried to the next
 // window.  The lane holding a segment's last item writes sums[slot].
-template <typename K>
+template <typename K, typename C>
 __global__ void seg_reduce(const K* __restrict__ keys, const uint32_t* __restrict__ vals,
                            const uint32_t* __restrict__ head, const uint32_t* __restrict__ slot, int64_t N, int64_t CH,
-                           CoefOf coef, K* __restrict__ ukeys, double* __restrict__ sums) {
+                           CoefOf<C> coef, K* __restrict__ ukeys, C* __restrict__ sums) {
   const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   const int64_t lo = w * CH;
@@ -224,7 +227,7 @@ __global__ void seg_reduce(const K* __restrict__ keys, const uint32_t* __restric
     if (start >= hi_nominal) return;  // no segment starts in this chunk
   }
   if (start >= hi_nominal) return;
-  double carry = 0.0;
+  C carry = C(0);
   for (int64_t base = start;; base += 32) {
     const int64_t k = base + lane;
     const bool in = k < N;
@@ -234,12 +237,12 @@ __global__ void seg_reduce(const K* __restrict__ keys, const uint32_t* __restric
     const unsigned stopmask = __ballot_sync(0xffffffffu, stop_here || !in);
     const int first_stop = stopmask ? __ffs(stopmask) - 1 : 32;
     const bool active = lane < first_stop;
-    double v = active ? coef(vals[k]) : 0.0;
+    C v = active ? coef(vals[k]) : C(0);
     bool f = active ? h : true;
     // segmented inclusive scan
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const double yv = __shfl_up_sync(0xffffffffu, v, o);
+      const C yv = __shfl_up_sync(0xffffffffu, v, o);
       const bool yf = __shfl_up_sync(0xffffffffu, f, o);
       if (lane >= o && !f) {
         v += yv;
@@ -274,13 +277,14 @@ __global__ void seg_reduce(const K* __restrict__ keys, const uint32_t* __restric
       sums[sl] = v;
       ukeys[sl] = keys[k];
     }
-    if (nh) carry = 0.0;
+    if (nh) carry = C(0);
   }
 }
 
-__global__ void keep_flags(const double* __restrict__ sums, int64_t U, double zeroprec, uint32_t* __restrict__ keep) {
+template <typename C>
+__global__ void keep_flags(const C* __restrict__ sums, int64_t U, double zeroprec, uint32_t* __restrict__ keep) {
   const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (u < U) keep[u] = fabs(sums[u]) > zeroprec ? 1u : 0u;
+  if (u < U) keep[u] = fabs((double)sums[u]) > zeroprec ? 1u : 0u;
 }
 
 // Unrank keys into exponent rows (inverse of the rank formula above).  A CTA
@@ -290,14 +294,14 @@ __global__ void keep_flags(const double* __restrict__ sums, int64_t U, double ze
 // keep) leave as one coalesced byte range.
 constexpr int kUnpackThreads = 128;
 
-template <typename K>
+template <typename K, typename C>
 __global__ void __launch_bounds__(kUnpackThreads) unpack_rows(const K* __restrict__ ukeys,
-                                                              const double* __restrict__ sums,
+                                                              const C* __restrict__ sums,
                                                               const uint32_t* __restrict__ keep,
                                                               const uint32_t* __restrict__ kpos, int64_t U, int n,
                                                               const K* __restrict__ S, int D1,
                                                               uint8_t* __restrict__ out_exps,
-                                                              double* __restrict__ out_coef) {
+                                                              C* __restrict__ out_coef) {
   extern __shared__ __align__(16) unsigned char sh[];
   K* Ss = reinterpret_cast<K*>(sh);
   uint8_t* rows = reinterpret_cast<uint8_t*>(Ss + (size_t)(n + 1) * D1);
@@ -341,11 +345,11 @@ __global__ void __launch_bounds__(kUnpackThreads) unpack_rows(const K* __restric
 
 // One thread per key writing its row directly: the fallback when a CTA's rows
 // and the binomial table do not fit in shared memory (very wide rows).
-template <typename K>
-__global__ void unpack_rows_direct(const K* __restrict__ ukeys, const double* __restrict__ sums,
+template <typename K, typename C>
+__global__ void unpack_rows_direct(const K* __restrict__ ukeys, const C* __restrict__ sums,
                                    const uint32_t* __restrict__ keep, const uint32_t* __restrict__ kpos, int64_t U,
                                    int n, const K* __restrict__ S, int D1, uint8_t* __restrict__ out_exps,
-                                   double* __restrict__ out_coef) {
+                                   C* __restrict__ out_coef) {
   const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (u >= U || !keep[u]) return;
   const int64_t o = kpos[u];
@@ -383,8 +387,8 @@ struct Operand {
   uint32_t nnz = 0;
 };
 
-template <class Mem>
-polylab_status build_operand(const polylab_poly* p, const std::vector<int>& colmap_h, Operand* op, Mem& scr,
+template <class Poly, class Mem>
+polylab_status build_operand(const Poly* p, const std::vector<int>& colmap_h, Operand* op, Mem& scr,
                              cudaStream_t s) {
   op->m = p->n_terms;
   const int64_t m = op->m;
@@ -454,10 +458,10 @@ int key_bits_u128(u128 total) {  // bits to represent values 0 .. total-1
   return b;
 }
 
-template <typename K, class Mem>
+template <typename K, typename C, class Mem>
 polylab_status run_pipeline(int n, int D, int64_t N, const std::vector<K>& Sh, int mode, const Operand& A,
-                            const Operand& B, const polylab_poly* pa, const polylab_poly* pb, double zeroprec,
-                            int bits, polylab_poly_out* out, polylab_alloc_fn alloc, void* ctx, Mem& scr,
+                            const Operand& B, const PolyIn<C>* pa, const PolyIn<C>* pb, double zeroprec,
+                            int bits, PolyOut<C>* out, polylab_alloc_fn alloc, void* ctx, Mem& scr,
                             cudaStream_t s) {
   const int D1 = D + 1;
   K* S = nullptr;
@@ -503,14 +507,14 @@ polylab_status run_pipeline(int n, int D, int64_t N, const std::vector<K>& Sh, i
   if (hovf) return POLYLAB_ERR_EXP_OVERFLOW;
   const int64_t U = (int64_t)hU[0] + hU[1];
   K* ukeys;
-  double* sums;
+  C* sums;
   PL_TRY(scr.get(&ukeys, U));
   PL_TRY(scr.get(&sums, U));
   const int64_t CH = 512;
   const int64_t warps = ceil_div(N, CH);
-  CoefOf cf{pa->coef, mode != kSimplify ? pb->coef : nullptr, pa->n_terms, mode != kSimplify ? pb->n_terms : 0,
+  CoefOf<C> cf{pa->coef, mode != kSimplify ? pb->coef : nullptr, pa->n_terms, mode != kSimplify ? pb->n_terms : 0,
             mode};
-  seg_reduce<K><<<(unsigned)ceil_div(warps * 32, 256), 256, 0, s>>>(keys, vals, head, slot, N, CH, cf, ukeys, sums);
+  seg_reduce<K, C><<<(unsigned)ceil_div(warps * 32, 256), 256, 0, s>>>(keys, vals, head, slot, N, CH, cf, ukeys, sums);
   PL_TRY(launch_status("seg_reduce"));
   uint32_t *keep, *kpos;
   PL_TRY(scr.get(&keep, U));
@@ -528,24 +532,24 @@ polylab_status run_pipeline(int n, int D, int64_t N, const std::vector<K>& Sh, i
   out->coef = nullptr;
   if (M == 0) return POLYLAB_OK;
   out->exps = (uint8_t*)alloc((size_t)M * n, ctx);
-  out->coef = (double*)alloc((size_t)M * sizeof(double), ctx);
+  out->coef = (C*)alloc((size_t)M * sizeof(C), ctx);
   if (!out->exps || !out->coef) return POLYLAB_ERR_OOM;
   const size_t ush = (size_t)(n + 1) * D1 * sizeof(K) + (size_t)kUnpackThreads * n;
   if (ush <= 160 * 1024) {
     if (ush > 48 * 1024)
-      PL_CUDA(cudaFuncSetAttribute(unpack_rows<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ush));
-    unpack_rows<K><<<(unsigned)ceil_div(U, kUnpackThreads), kUnpackThreads, ush, s>>>(ukeys, sums, keep, kpos, U, n,
+      PL_CUDA(cudaFuncSetAttribute(unpack_rows<K, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ush));
+    unpack_rows<K, C><<<(unsigned)ceil_div(U, kUnpackThreads), kUnpackThreads, ush, s>>>(ukeys, sums, keep, kpos, U, n,
                                                                                      S, D1, out->exps, out->coef);
     return launch_status("unpack_rows");
   }
-  unpack_rows_direct<K><<<(unsigned)ceil_div(U, 128), 128, 0, s>>>(ukeys, sums, keep, kpos, U, n, S, D1, out->exps,
+  unpack_rows_direct<K, C><<<(unsigned)ceil_div(U, 128), 128, 0, s>>>(ukeys, sums, keep, kpos, U, n, S, D1, out->exps,
                                                                    out->coef);
   return launch_status("unpack_rows_direct");
 }
 
-template <class Mem>
-polylab_status engine_with(Mem& scr, const polylab_poly* pa, const polylab_poly* pb, int mode, double zeroprec,
-                           polylab_poly_out* out, polylab_alloc_fn alloc, void* ctx, cudaStream_t s) {
+template <typename C, class Mem>
+polylab_status engine_with(Mem& scr, const PolyIn<C>* pa, const PolyIn<C>* pb, int mode, double zeroprec,
+                           PolyOut<C>* out, polylab_alloc_fn alloc, void* ctx, cudaStream_t s) {
   if (!out || !alloc || !out->var_ids || !(zeroprec >= 0.0)) return POLYLAB_ERR_INVALID_ARG;
   PL_TRY(check_poly(pa));
   const bool is_mul = mode != kSimplify;  // two operands (mul or add)
@@ -589,20 +593,43 @@ polylab_status engine_with(Mem& scr, const polylab_poly* pa, const polylab_poly*
   if (bits <= 64) {
     std::vector<uint64_t> S64(S128.size());
     for (size_t i = 0; i < S128.size(); ++i) S64[i] = (uint64_t)S128[i];
-    return run_pipeline<uint64_t, Mem>(n, D, N, S64, mode, A, B, pa, pb, zeroprec, bits, out, alloc, ctx, scr,
+    return run_pipeline<uint64_t, C, Mem>(n, D, N, S64, mode, A, B, pa, pb, zeroprec, bits, out, alloc, ctx, scr,
                                        s);
   }
-  return run_pipeline<u128, Mem>(n, D, N, S128, mode, A, B, pa, pb, zeroprec, bits, out, alloc, ctx, scr, s);
+  return run_pipeline<u128, C, Mem>(n, D, N, S128, mode, A, B, pa, pb, zeroprec, bits, out, alloc, ctx, scr, s);
 }
 
 }  // namespace
 
 // (declared in common.cuh; the algebra entry points call it too)
-polylab_status engine(const polylab_poly* pa, const polylab_poly* pb, int mode, double zeroprec,
-                      polylab_poly_out* out, polylab_alloc_fn alloc, void* ctx, cudaStream_t s) {
+template <typename C>
+polylab_status engine(const PolyIn<C>* pa, const PolyIn<C>* pb, int mode, double zeroprec, PolyOut<C>* out,
+                      polylab_alloc_fn alloc, void* ctx, cudaStream_t s) {
   Scratch scr(s);
-  return engine_with(scr, pa, pb, mode, zeroprec, out, alloc, ctx, s);
+  return engine_with<C>(scr, pa, pb, mode, zeroprec, out, alloc, ctx, s);
 }
+template polylab_status engine<double>(const PolyIn<double>*, const PolyIn<double>*, int, double, PolyOut<double>*,
+                                       polylab_alloc_fn, void*, cudaStream_t);
+template polylab_status engine<float>(const PolyIn<float>*, const PolyIn<float>*, int, double, PolyOut<float>*,
+                                      polylab_alloc_fn, void*, cudaStream_t);
+
+namespace {
+
+// A C entry point: the public structs viewed as PolyIn / PolyOut and back.
+template <typename PubIn, typename PubOut>
+polylab_status engine_entry(const PubIn* a, const PubIn* b, int mode, double zeroprec, PubOut* out,
+                            polylab_alloc_fn alloc, void* ctx, cudaStream_t s) {
+  if (!a || !out || (mode != kSimplify && !b)) return POLYLAB_ERR_INVALID_ARG;
+  const auto va = poly_in(*a);
+  auto vb = va;
+  if (b) vb = poly_in(*b);
+  auto o = poly_out(*out);
+  const polylab_status st = engine(&va, b ? &vb : nullptr, mode, zeroprec, &o, alloc, ctx, s);
+  store_out(o, out);
+  return st;
+}
+
+}  // namespace
 
 namespace {
 
@@ -690,25 +717,47 @@ extern "C" {
 
 polylab_status polylab_simplify(const polylab_poly* p, double zeroprec, polylab_poly_out* out,
                                 polylab_alloc_fn alloc, void* alloc_ctx, polylab_stream stream) {
-  return polylab::engine(p, nullptr, polylab::kSimplify, zeroprec, out, alloc, alloc_ctx, (cudaStream_t)stream);
+  return polylab::engine_entry(p, (const polylab_poly*)nullptr, polylab::kSimplify, zeroprec, out, alloc, alloc_ctx,
+                               (cudaStream_t)stream);
 }
 
 polylab_status polylab_mul(const polylab_poly* a, const polylab_poly* b, double zeroprec, polylab_poly_out* out,
                            polylab_alloc_fn alloc, void* alloc_ctx, polylab_stream stream) {
-  if (!b) return POLYLAB_ERR_INVALID_ARG;
-  return polylab::engine(a, b, polylab::kMul, zeroprec, out, alloc, alloc_ctx, (cudaStream_t)stream);
+  return polylab::engine_entry(a, b, polylab::kMul, zeroprec, out, alloc, alloc_ctx, (cudaStream_t)stream);
 }
 
 polylab_status polylab_add(const polylab_poly* a, const polylab_poly* b, double zeroprec, polylab_poly_out* out,
                            polylab_alloc_fn alloc, void* alloc_ctx, polylab_stream stream) {
-  if (!b) return POLYLAB_ERR_INVALID_ARG;
-  return polylab::engine(a, b, polylab::kAdd, zeroprec, out, alloc, alloc_ctx, (cudaStream_t)stream);
+  return polylab::engine_entry(a, b, polylab::kAdd, zeroprec, out, alloc, alloc_ctx, (cudaStream_t)stream);
 }
 
 polylab_status polylab_sub(const polylab_poly* a, const polylab_poly* b, double zeroprec, polylab_poly_out* out,
                            polylab_alloc_fn alloc, void* alloc_ctx, polylab_stream stream) {
-  if (!b) return POLYLAB_ERR_INVALID_ARG;
-  return polylab::engine(a, b, polylab::kSub, zeroprec, out, alloc, alloc_ctx, (cudaStream_t)stream);
+  return polylab::engine_entry(a, b, polylab::kSub, zeroprec, out, alloc, alloc_ctx, (cudaStream_t)stream);
+}
+
+polylab_status polylab_simplify_f32(const polylab_poly_f32* p, double zeroprec, polylab_poly_out_f32* out,
+                                    polylab_alloc_fn alloc, void* alloc_ctx, polylab_stream stream) {
+  return polylab::engine_entry(p, (const polylab_poly_f32*)nullptr, polylab::kSimplify, zeroprec, out, alloc,
+                               alloc_ctx, (cudaStream_t)stream);
+}
+
+polylab_status polylab_mul_f32(const polylab_poly_f32* a, const polylab_poly_f32* b, double zeroprec,
+                               polylab_poly_out_f32* out, polylab_alloc_fn alloc, void* alloc_ctx,
+                               polylab_stream stream) {
+  return polylab::engine_entry(a, b, polylab::kMul, zeroprec, out, alloc, alloc_ctx, (cudaStream_t)stream);
+}
+
+polylab_status polylab_add_f32(const polylab_poly_f32* a, const polylab_poly_f32* b, double zeroprec,
+                               polylab_poly_out_f32* out, polylab_alloc_fn alloc, void* alloc_ctx,
+                               polylab_stream stream) {
+  return polylab::engine_entry(a, b, polylab::kAdd, zeroprec, out, alloc, alloc_ctx, (cudaStream_t)stream);
+}
+
+polylab_status polylab_sub_f32(const polylab_poly_f32* a, const polylab_poly_f32* b, double zeroprec,
+                               polylab_poly_out_f32* out, polylab_alloc_fn alloc, void* alloc_ctx,
+                               polylab_stream stream) {
+  return polylab::engine_entry(a, b, polylab::kSub, zeroprec, out, alloc, alloc_ctx, (cudaStream_t)stream);
 }
 
 polylab_status polylab_simplify_noalloc(const polylab_poly* p, double zeroprec, polylab_poly_out* out,
@@ -726,8 +775,11 @@ polylab_status polylab_simplify_noalloc(const polylab_poly* p, double zeroprec, 
   PL_TRY(noalloc_base(&base));
   Arena arena{base, kNoAllocScratchBytes};
   CallerBuffers buf{out->exps, out->coef, capacity, p->n_vars};
+  const auto vp = poly_in(*p);
+  auto o = poly_out(*out);
   const polylab_status st =
-      engine_with(arena, p, nullptr, kSimplify, zeroprec, out, caller_buffers, &buf, (cudaStream_t)stream);
+      engine_with<double>(arena, &vp, nullptr, kSimplify, zeroprec, &o, caller_buffers, &buf, (cudaStream_t)stream);
+  store_out(o, out);
   // the pipeline resets the output pointers; hand the caller's buffers back
   out->exps = buf.exps;
   out->coef = buf.coef;

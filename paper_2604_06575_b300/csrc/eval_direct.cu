@@ -21,11 +21,13 @@ __host__ __device__ __forceinline__ int tri_index(int i, int j, int n) {  // i <
   return i * (2 * n - i + 1) / 2 + (j - i);
 }
 
-template <typename R, int ORDER>
+// R: arithmetic type; IO: type of the points and outputs (FP64, or FP32 for
+// the single-precision storage calls).
+template <typename R, typename IO, int ORDER>
 __global__ void __launch_bounds__(256) eval_direct_smem(const Term* __restrict__ terms, int64_t m, int n, int E,
-                                                       const double* __restrict__ X, int64_t P, int TP,
-                                                       double* __restrict__ F, double* __restrict__ G,
-                                                       double* __restrict__ H) {
+                                                       const IO* __restrict__ X, int64_t P, int TP,
+                                                       IO* __restrict__ F, IO* __restrict__ G,
+                                                       IO* __restrict__ H) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int E1 = E + 1;
   const int nH = ORDER >= 2 ? n * (n + 1) / 2 : 0;
@@ -38,7 +40,7 @@ __global__ void __launch_bounds__(256) eval_direct_smem(const Term* __restrict__
   for (int i = threadIdx.x; i < NO * TP; i += blockDim.x) acc[i] = R(0);
   for (int i = threadIdx.x; i < TP * n; i += blockDim.x) {
     const int p = i / n, v = i - p * n;
-    const double x = p < tp ? X[(p0 + p) * n + v] : 0.0;
+    const R x = p < tp ? R(X[(p0 + p) * n + v]) : R(0);
     R* w = pw + (size_t)(p * n + v) * E1;
     R cur = R(1);
     w[0] = cur;
@@ -64,11 +66,11 @@ __global__ void __launch_bounds__(256) eval_direct_smem(const Term* __restrict__
   }
   __syncthreads();
 
-  for (int i = threadIdx.x; i < tp; i += blockDim.x) F[p0 + i] = (double)acc[i];
+  for (int i = threadIdx.x; i < tp; i += blockDim.x) F[p0 + i] = (IO)acc[i];
   if (ORDER >= 1)
     for (int i = threadIdx.x; i < tp * n; i += blockDim.x) {
       const int pp = i / n, v = i - pp * n;
-      G[p0 * n + i] = (double)acc[(size_t)(1 + v) * TP + pp];
+      G[p0 * n + i] = (IO)acc[(size_t)(1 + v) * TP + pp];
     }
   if (ORDER >= 2) {
     const int nn = n * n;
@@ -76,24 +78,24 @@ __global__ void __launch_bounds__(256) eval_direct_smem(const Term* __restrict__
       const int pp = i / nn, r = i - pp * nn;
       const int a = r / n, b = r - a * n;
       const int o = 1 + n + (a <= b ? tri_index(a, b, n) : tri_index(b, a, n));
-      H[p0 * nn + i] = (double)acc[(size_t)o * TP + pp];
+      H[p0 * nn + i] = (IO)acc[(size_t)o * TP + pp];
     }
   }
 }
 
 // Fallback for large n: one CTA per point, global atomics into zeroed outputs.
-template <typename R, int ORDER>
+template <typename R, typename IO, int ORDER>
 __global__ void __launch_bounds__(256) eval_direct_global(const Term* __restrict__ terms, int64_t m, int n, int E,
-                                                         const double* __restrict__ X, int64_t P,
-                                                         double* __restrict__ F, double* __restrict__ G,
-                                                         double* __restrict__ H) {
+                                                         const IO* __restrict__ X, int64_t P,
+                                                         IO* __restrict__ F, IO* __restrict__ G,
+                                                         IO* __restrict__ H) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int E1 = E + 1;
   R* pw = reinterpret_cast<R*>(smem_raw);
   for (int64_t p = blockIdx.x; p < P; p += gridDim.x) {
     __syncthreads();
     for (int v = threadIdx.x; v < n; v += blockDim.x) {
-      const double x = X[p * n + v];
+      const R x = R(X[p * n + v]);
       R cur = R(1);
       pw[v * E1] = cur;
       for (int k = 1; k <= E; ++k) {
@@ -105,7 +107,7 @@ __global__ void __launch_bounds__(256) eval_direct_global(const Term* __restrict
     for (int64_t t = threadIdx.x; t < m; t += blockDim.x) {
       const TermRegs tr = load_term(terms, t);
       term_derivs<R, ORDER>(tr, pw, E1, [&](int kind, int i, int j, R v) {
-        const double dv = (double)v;
+        const IO dv = (IO)v;
         if (kind == 0) atomicAdd(&F[p], dv);
         else if (kind == 1) atomicAdd(&G[p * n + i], dv);
         else {
@@ -117,9 +119,9 @@ __global__ void __launch_bounds__(256) eval_direct_global(const Term* __restrict
   }
 }
 
-template <typename R, int ORDER>
-static polylab_status launch_direct(const polylab_plan* plan, const double* X, int64_t P, double* F, double* G,
-                                    double* H, cudaStream_t s) {
+template <typename R, typename IO, int ORDER>
+static polylab_status launch_direct(const polylab_plan* plan, const IO* X, int64_t P, IO* F, IO* G, IO* H,
+                                    cudaStream_t s) {
   const int n = plan->n, E = std::max(plan->max_exp, 1);
   const int nH = ORDER >= 2 ? n * (n + 1) / 2 : 0;
   const size_t NO = 1 + (ORDER >= 1 ? n : 0) + nH;
@@ -133,17 +135,17 @@ static polylab_status launch_direct(const polylab_plan* plan, const double* X, i
     }
   if (TP > 0) {
     const size_t smem = TP * per_point;
-    auto k = eval_direct_smem<R, ORDER>;
+    auto k = eval_direct_smem<R, IO, ORDER>;
     PL_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k<<<(unsigned)ceil_div(P, TP), 256, smem, s>>>(plan->terms, plan->m, n, E, X, P, TP, F, G, H);
     return launch_status("eval_direct_smem");
   }
-  PL_CUDA(cudaMemsetAsync(F, 0, P * sizeof(double), s));
-  if (ORDER >= 1) PL_CUDA(cudaMemsetAsync(G, 0, P * n * sizeof(double), s));
-  if (ORDER >= 2) PL_CUDA(cudaMemsetAsync(H, 0, P * (size_t)n * n * sizeof(double), s));
+  PL_CUDA(cudaMemsetAsync(F, 0, P * sizeof(IO), s));
+  if (ORDER >= 1) PL_CUDA(cudaMemsetAsync(G, 0, P * n * sizeof(IO), s));
+  if (ORDER >= 2) PL_CUDA(cudaMemsetAsync(H, 0, P * (size_t)n * n * sizeof(IO), s));
   const size_t smem = (size_t)n * (E + 1) * sizeof(R);
   if (smem > 200 * 1024) return POLYLAB_ERR_UNSUPPORTED;
-  auto k = eval_direct_global<R, ORDER>;
+  auto k = eval_direct_global<R, IO, ORDER>;
   PL_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int grid = (int)std::min<int64_t>(P, (int64_t)num_sms() * 8);
   k<<<grid, 256, smem, s>>>(plan->terms, plan->m, n, E, X, P, F, G, H);
@@ -154,13 +156,21 @@ polylab_status eval_direct(const polylab_plan* plan, const double* X, int64_t P,
                            double* G, double* H, cudaStream_t s) {
   if (P == 0) return POLYLAB_OK;
   if (fp32) {
-    if (order == 0) return launch_direct<float, 0>(plan, X, P, F, G, H, s);
-    if (order == 1) return launch_direct<float, 1>(plan, X, P, F, G, H, s);
-    return launch_direct<float, 2>(plan, X, P, F, G, H, s);
+    if (order == 0) return launch_direct<float, double, 0>(plan, X, P, F, G, H, s);
+    if (order == 1) return launch_direct<float, double, 1>(plan, X, P, F, G, H, s);
+    return launch_direct<float, double, 2>(plan, X, P, F, G, H, s);
   }
-  if (order == 0) return launch_direct<double, 0>(plan, X, P, F, G, H, s);
-  if (order == 1) return launch_direct<double, 1>(plan, X, P, F, G, H, s);
-  return launch_direct<double, 2>(plan, X, P, F, G, H, s);
+  if (order == 0) return launch_direct<double, double, 0>(plan, X, P, F, G, H, s);
+  if (order == 1) return launch_direct<double, double, 1>(plan, X, P, F, G, H, s);
+  return launch_direct<double, double, 2>(plan, X, P, F, G, H, s);
+}
+
+polylab_status eval_direct_f32(const polylab_plan* plan, const float* X, int64_t P, int order, float* F, float* G,
+                               float* H, cudaStream_t s) {
+  if (P == 0) return POLYLAB_OK;
+  if (order == 0) return launch_direct<float, float, 0>(plan, X, P, F, G, H, s);
+  if (order == 1) return launch_direct<float, float, 1>(plan, X, P, F, G, H, s);
+  return launch_direct<float, float, 2>(plan, X, P, F, G, H, s);
 }
 
 }  // namespace polylab

@@ -29,18 +29,10 @@ int num_sms() {
   return cached;
 }
 
-polylab_status check_poly(const polylab_poly* p) {
-  if (!p || p->n_vars < 1 || p->n_terms < 0 || !p->var_ids) return POLYLAB_ERR_INVALID_ARG;
-  if (p->n_terms > 0 && (!p->exps || !p->coef)) return POLYLAB_ERR_INVALID_ARG;
-  std::unordered_set<uint64_t> seen;
-  for (int i = 0; i < p->n_vars; ++i)
-    if (!seen.insert(p->var_ids[i]).second) return POLYLAB_ERR_DUP_VAR_ID;
-  return POLYLAB_OK;
-}
-
 // One warp per term: scan the exponent row, keep the nonzero entries in
 // column order.  stats[0] = max exponent, stats[1] = max support.
-__global__ void pack_terms_kernel(const uint8_t* __restrict__ exps, const double* __restrict__ coef, int64_t m,
+template <typename C>
+__global__ void pack_terms_kernel(const uint8_t* __restrict__ exps, const C* __restrict__ coef, int64_t m,
                                   int n, Term* __restrict__ terms, int* __restrict__ stats) {
   __shared__ Term stage[8];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -233,7 +225,8 @@ polylab_status ensure_hessian_pattern(polylab_plan* plan, cudaStream_t s) {
   return POLYLAB_OK;
 }
 
-polylab_status build_term_plan(const polylab_poly* p, cudaStream_t s, polylab_plan* plan) {
+template <typename C>
+polylab_status build_term_plan(const PolyIn<C>* p, cudaStream_t s, polylab_plan* plan) {
   PL_TRY(check_poly(p));
   if (p->n_vars > 65535) return POLYLAB_ERR_UNSUPPORTED;
   plan->n = p->n_vars;
@@ -243,7 +236,7 @@ polylab_status build_term_plan(const polylab_poly* p, cudaStream_t s, polylab_pl
   PL_CUDA(cudaMemsetAsync(stats, 0, 2 * sizeof(int), s));
   PL_CUDA(cudaMallocAsync(&plan->terms, std::max<int64_t>(p->n_terms, 1) * sizeof(Term), s));
   if (p->n_terms > 0) {
-    pack_terms_kernel<<<(unsigned)ceil_div(p->n_terms, 8), 256, 0, s>>>(p->exps, p->coef, p->n_terms, p->n_vars,
+    pack_terms_kernel<C><<<(unsigned)ceil_div(p->n_terms, 8), 256, 0, s>>>(p->exps, p->coef, p->n_terms, p->n_vars,
                                                                           plan->terms, stats);
     PL_TRY(launch_status("pack_terms_kernel"));
   }
@@ -286,6 +279,28 @@ polylab_status build_term_plan(const polylab_poly* p, cudaStream_t s, polylab_pl
   return POLYLAB_OK;
 }
 
+namespace {
+
+template <typename Pub>
+polylab_status plan_create(const Pub* p, uint32_t what, polylab_stream stream, polylab_plan** out) {
+  if (!out) return POLYLAB_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!p || what > POLYLAB_PLAN_GEMM) return POLYLAB_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const auto view = poly_in(*p);
+  polylab_plan* plan = new polylab_plan();
+  polylab_status st = build_term_plan(&view, s, plan);
+  if (st == POLYLAB_OK && (what & POLYLAB_PLAN_GEMM)) st = build_gemm_operand(plan, s);
+  if (st != POLYLAB_OK) {
+    polylab_plan_destroy(plan, stream);
+    return st;
+  }
+  *out = plan;
+  return POLYLAB_OK;
+}
+
+}  // namespace
+
 }  // namespace polylab
 
 using namespace polylab;
@@ -310,19 +325,12 @@ const char* polylab_last_error(void) { return g_last_error; }
 
 polylab_status polylab_plan_create(const polylab_poly* p, uint32_t what, polylab_stream stream,
                                    polylab_plan** out) {
-  if (!out) return POLYLAB_ERR_INVALID_ARG;
-  *out = nullptr;
-  if (what > POLYLAB_PLAN_GEMM) return POLYLAB_ERR_INVALID_ARG;
-  cudaStream_t s = (cudaStream_t)stream;
-  polylab_plan* plan = new polylab_plan();
-  polylab_status st = build_term_plan(p, s, plan);
-  if (st == POLYLAB_OK && (what & POLYLAB_PLAN_GEMM)) st = build_gemm_operand(plan, s);
-  if (st != POLYLAB_OK) {
-    polylab_plan_destroy(plan, stream);
-    return st;
-  }
-  *out = plan;
-  return POLYLAB_OK;
+  return plan_create(p, what, stream, out);
+}
+
+polylab_status polylab_plan_create_f32(const polylab_poly_f32* p, uint32_t what, polylab_stream stream,
+                                       polylab_plan** out) {
+  return plan_create(p, what, stream, out);
 }
 
 polylab_status polylab_plan_destroy(polylab_plan* plan, polylab_stream stream) {

@@ -111,13 +111,21 @@ _lib.polylab_mlp_adam.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p
 _lib.polylab_mlp_pack.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
 _lib.polylab_affine_normal_batched.argtypes = [C.c_int32, C.c_void_p, _PP, _PP, C.POINTER(C.c_int64),
                                                C.POINTER(_AnOpts), _PP, _PP, _PP, C.c_void_p]
+# single-precision storage: the same structs with FP32 coefficient pointers
+for _f in ("simplify", "mul", "add", "sub", "pow", "diff", "plan_create"):
+    getattr(_lib, f"polylab_{_f}_f32").argtypes = getattr(_lib, f"polylab_{_f}").argtypes
+_lib.polylab_eval_derivs_f32.argtypes = [C.POINTER(_Poly), C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p,
+                                         C.c_void_p, C.c_void_p, C.c_void_p]
+_lib.polylab_affine_normal_f32.argtypes = _lib.polylab_affine_normal.argtypes
+F32_CALLS = ["polylab_simplify_f32", "polylab_mul_f32", "polylab_add_f32", "polylab_sub_f32", "polylab_pow_f32",
+             "polylab_diff_f32", "polylab_plan_create_f32", "polylab_eval_derivs_f32", "polylab_affine_normal_f32"]
 for _f in ("polylab_plan_create", "polylab_plan_destroy", "polylab_eval_derivs", "polylab_affine_normal",
            "polylab_simplify", "polylab_mul", "polylab_add", "polylab_sub", "polylab_pow", "polylab_diff",
            "polylab_simplify_noalloc", "polylab_batch_create",
            "polylab_batch_run", "polylab_batch_run_stage", "polylab_batch_check", "polylab_batch_get_config",
            "polylab_batch_set_config", "polylab_batch_autotune", "polylab_batch_destroy", "polylab_affine_normal_batched",
            "polylab_plan_gemm_info", "polylab_mlp_init",
-           "polylab_mlp_data", "polylab_mlp_loss_grad", "polylab_mlp_adam", "polylab_mlp_pack"):
+           "polylab_mlp_data", "polylab_mlp_loss_grad", "polylab_mlp_adam", "polylab_mlp_pack", *F32_CALLS):
     getattr(_lib, _f).restype = C.c_int
 
 EXPORTED = ["polylab_status_string", "polylab_last_error", "polylab_simplify", "polylab_mul", "polylab_add",
@@ -128,7 +136,7 @@ EXPORTED = ["polylab_status_string", "polylab_last_error", "polylab_simplify", "
             "polylab_batch_set_config",
             "polylab_batch_autotune", "polylab_batch_destroy", "polylab_affine_normal_batched", "polylab_plan_gemm_info",
             "polylab_mlp_param_count", "polylab_mlp_init", "polylab_mlp_data", "polylab_mlp_loss_grad",
-            "polylab_mlp_adam", "polylab_mlp_pack"]
+            "polylab_mlp_adam", "polylab_mlp_pack", *F32_CALLS]
 
 
 def lib():
@@ -153,10 +161,12 @@ def _ptr(t: torch.Tensor | None) -> int | None:
 
 @dataclass
 class DevPoly:
-    """A polynomial whose exponents and coefficients live on the device."""
+    """A polynomial whose exponents and coefficients live on the device.
+    float32 coefficients select the library's single-precision storage calls
+    (the ``*_f32`` entry points) in every function below."""
     var_ids: np.ndarray   # uint64[n] (host)
     exps: torch.Tensor    # uint8 [m, n] cuda
-    coef: torch.Tensor    # float64 [m] cuda
+    coef: torch.Tensor    # float64 or float32 [m] cuda
 
     @property
     def n(self) -> int:
@@ -166,17 +176,32 @@ class DevPoly:
     def m(self) -> int:
         return int(self.coef.shape[0])
 
+    @property
+    def f32(self) -> bool:
+        return self.coef.dtype == torch.float32
+
     def cstruct(self) -> _Poly:
         ids = np.ascontiguousarray(self.var_ids, dtype=np.uint64)
         self._ids_keep = ids
         return _Poly(self.n, ids.ctypes.data_as(C.POINTER(C.c_uint64)), self.m, _ptr(self.exps), _ptr(self.coef))
 
 
-def to_device(poly, device="cuda") -> DevPoly:
-    """From any object with var_ids / exps / coef arrays (e.g. workloads.Poly)."""
+def to_device(poly, device="cuda", dtype=torch.float64) -> DevPoly:
+    """From any object with var_ids / exps / coef arrays (e.g. workloads.Poly);
+    dtype=torch.float32 stores the coefficients rounded to FP32."""
+    npd = np.float32 if dtype == torch.float32 else np.float64
     return DevPoly(np.asarray(poly.var_ids, dtype=np.uint64),
                    torch.as_tensor(np.ascontiguousarray(poly.exps, dtype=np.uint8), device=device),
-                   torch.as_tensor(np.ascontiguousarray(poly.coef, dtype=np.float64), device=device))
+                   torch.as_tensor(np.ascontiguousarray(poly.coef, dtype=npd), device=device))
+
+
+def _call(name: str, *polys: DevPoly):
+    """(name, function) of the FP64 call or its single-precision namesake."""
+    f32 = {p.f32 for p in polys}
+    if len(f32) != 1:
+        raise ValueError("operands mix FP64 and FP32 coefficient storage")
+    name = name + "_f32" if f32.pop() else name
+    return name, getattr(_lib, name)
 
 
 class Plan:
@@ -186,8 +211,8 @@ class Plan:
         self.p = p
         self.h = C.c_void_p()
         cp = p.cstruct()
-        _check("polylab_plan_create", _lib.polylab_plan_create(C.byref(cp), 1 if gemm else 0, _stream(),
-                                                               C.byref(self.h)))
+        name, fn = _call("polylab_plan_create", p)
+        _check(name, fn(C.byref(cp), 1 if gemm else 0, _stream(), C.byref(self.h)))
 
     @property
     def closure_size(self) -> int:
@@ -217,20 +242,32 @@ class Plan:
         self.close()
 
 
-def eval_derivs(p: DevPoly, X: torch.Tensor, order: int = 2, prec: str = "fp64", plan: Plan | None = None,
+def eval_derivs(p: DevPoly, X: torch.Tensor, order: int = 2, prec: str | None = None, plan: Plan | None = None,
                 out=None):
-    """F[P], G[P,n], H[P,n,n] (float64, device)."""
+    """F[P], G[P,n], H[P,n,n] on the device, in X's dtype: float64 points with
+    an FP64-storage polynomial (prec: fp64 default, fp32, tf32x3, bf16),
+    float32 points with an FP32-storage one (prec fp32 only)."""
     P, n = X.shape
-    assert n == p.n and X.dtype == torch.float64
+    dt = torch.float32 if p.f32 else torch.float64
+    assert n == p.n and X.dtype == dt
+    if prec is None:
+        prec = "fp32" if p.f32 else "fp64"
+    if p.f32 and prec != "fp32":
+        raise ValueError("FP32-storage polynomials evaluate in the fp32 form only")
     if out is None:
-        F = torch.empty(P, dtype=torch.float64, device=X.device)
-        G = torch.empty(P, n, dtype=torch.float64, device=X.device) if order >= 1 else None
-        H = torch.empty(P, n, n, dtype=torch.float64, device=X.device) if order >= 2 else None
+        F = torch.empty(P, dtype=dt, device=X.device)
+        G = torch.empty(P, n, dtype=dt, device=X.device) if order >= 1 else None
+        H = torch.empty(P, n, n, dtype=dt, device=X.device) if order >= 2 else None
     else:
         F, G, H = out
     cp = p.cstruct()
-    _check("polylab_eval_derivs", _lib.polylab_eval_derivs(C.byref(cp), plan.h if plan else None, _ptr(X), P, order,
-                                                           PREC[prec], _ptr(F), _ptr(G), _ptr(H), _stream()))
+    ph = plan.h if plan else None
+    if p.f32:
+        _check("polylab_eval_derivs_f32", _lib.polylab_eval_derivs_f32(C.byref(cp), ph, _ptr(X), P, order, _ptr(F),
+                                                                       _ptr(G), _ptr(H), _stream()))
+    else:
+        _check("polylab_eval_derivs", _lib.polylab_eval_derivs(C.byref(cp), ph, _ptr(X), P, order, PREC[prec],
+                                                               _ptr(F), _ptr(G), _ptr(H), _stream()))
     return F, G, H
 
 
@@ -253,19 +290,28 @@ def an_opts(method="mf-exact", regularization=1e-6, num_probes=8, krylov_tol=1e-
 
 def affine_normal(p: DevPoly, X: torch.Tensor, opts: _AnOpts | None = None, plan: Plan | None = None,
                   want_unit: bool = True, want_info: bool = True, out=None, **kw):
-    """(D, Dunit, info_bytes) on the device; ``info_numpy`` decodes info."""
+    """(D, Dunit, info_bytes) on the device; ``info_numpy`` decodes info.  An
+    FP32-storage polynomial takes float32 points, returns float32 directions
+    and runs the fp32 form (the default ``prec`` for it)."""
     P, n = X.shape
-    assert n == p.n and X.dtype == torch.float64
-    o = opts if opts is not None else an_opts(**kw)
+    dt = torch.float32 if p.f32 else torch.float64
+    assert n == p.n and X.dtype == dt
+    if opts is None:
+        if p.f32:
+            kw.setdefault("prec", "fp32")
+        o = an_opts(**kw)
+    else:
+        o = opts
     if out is None:
-        D = torch.empty(P, n, dtype=torch.float64, device=X.device)
-        Du = torch.empty(P, n, dtype=torch.float64, device=X.device) if want_unit else None
+        D = torch.empty(P, n, dtype=dt, device=X.device)
+        Du = torch.empty(P, n, dtype=dt, device=X.device) if want_unit else None
         info = torch.empty(P, 32, dtype=torch.uint8, device=X.device) if want_info else None
     else:
         D, Du, info = out
     cp = p.cstruct()
-    _check("polylab_affine_normal", _lib.polylab_affine_normal(C.byref(cp), plan.h if plan else None, _ptr(X), P,
-                                                               C.byref(o), _ptr(D), _ptr(Du), _ptr(info), _stream()))
+    name, fn = _call("polylab_affine_normal", p)
+    _check(name, fn(C.byref(cp), plan.h if plan else None, _ptr(X), P, C.byref(o), _ptr(D), _ptr(Du), _ptr(info),
+                    _stream()))
     return D, Du, info
 
 
@@ -286,7 +332,7 @@ class _Allocs:
         self.fn = ALLOC_FN(fn)
 
 
-def _run_out(name, call, n_cap: int, device):
+def _run_out(name, call, n_cap: int, device, dtype=torch.float64):
     ids = np.zeros(max(n_cap, 1), dtype=np.uint64)
     out = _PolyOut(0, ids.ctypes.data_as(C.POINTER(C.c_uint64)), 0, None, None)
     al = _Allocs(device)
@@ -295,53 +341,51 @@ def _run_out(name, call, n_cap: int, device):
     by_ptr = {t.data_ptr(): t for t in al.keep}
     if m > 0:
         exps = by_ptr[out.exps][: m * n].view(m, n)
-        coef = by_ptr[out.coef][: m * 8].view(torch.float64)
+        coef = by_ptr[out.coef][: m * dtype.itemsize].view(dtype)
     else:
         exps = torch.zeros(0, n, dtype=torch.uint8, device=device)
-        coef = torch.zeros(0, dtype=torch.float64, device=device)
+        coef = torch.zeros(0, dtype=dtype, device=device)
     return DevPoly(ids[:n].copy(), exps, coef)
 
 
 def simplify(p: DevPoly, zeroprec: float = 0.0) -> DevPoly:
     cp = p.cstruct()
-    return _run_out("polylab_simplify",
-                    lambda o, fn: _lib.polylab_simplify(C.byref(cp), zeroprec, o, fn, None, _stream()),
-                    p.n, p.coef.device)
+    name, fn = _call("polylab_simplify", p)
+    return _run_out(name, lambda o, al: fn(C.byref(cp), zeroprec, o, al, None, _stream()), p.n, p.coef.device,
+                    p.coef.dtype)
+
+
+def _binary(base: str, a: DevPoly, b: DevPoly, zeroprec: float) -> DevPoly:
+    ca, cb = a.cstruct(), b.cstruct()
+    name, fn = _call(base, a, b)
+    return _run_out(name, lambda o, al: fn(C.byref(ca), C.byref(cb), zeroprec, o, al, None, _stream()), a.n + b.n,
+                    a.coef.device, a.coef.dtype)
 
 
 def mul(a: DevPoly, b: DevPoly, zeroprec: float = 0.0) -> DevPoly:
-    ca, cb = a.cstruct(), b.cstruct()
-    return _run_out("polylab_mul",
-                    lambda o, fn: _lib.polylab_mul(C.byref(ca), C.byref(cb), zeroprec, o, fn, None, _stream()),
-                    a.n + b.n, a.coef.device)
+    return _binary("polylab_mul", a, b, zeroprec)
 
 
 def add(a: DevPoly, b: DevPoly, zeroprec: float = 0.0) -> DevPoly:
-    ca, cb = a.cstruct(), b.cstruct()
-    return _run_out("polylab_add",
-                    lambda o, fn: _lib.polylab_add(C.byref(ca), C.byref(cb), zeroprec, o, fn, None, _stream()),
-                    a.n + b.n, a.coef.device)
+    return _binary("polylab_add", a, b, zeroprec)
 
 
 def sub(a: DevPoly, b: DevPoly, zeroprec: float = 0.0) -> DevPoly:
-    ca, cb = a.cstruct(), b.cstruct()
-    return _run_out("polylab_sub",
-                    lambda o, fn: _lib.polylab_sub(C.byref(ca), C.byref(cb), zeroprec, o, fn, None, _stream()),
-                    a.n + b.n, a.coef.device)
+    return _binary("polylab_sub", a, b, zeroprec)
 
 
 def pow(p: DevPoly, k: int, zeroprec: float = 0.0) -> DevPoly:
     cp = p.cstruct()
-    return _run_out("polylab_pow",
-                    lambda o, fn: _lib.polylab_pow(C.byref(cp), k, zeroprec, o, fn, None, _stream()),
-                    p.n, p.coef.device)
+    name, fn = _call("polylab_pow", p)
+    return _run_out(name, lambda o, al: fn(C.byref(cp), k, zeroprec, o, al, None, _stream()), p.n, p.coef.device,
+                    p.coef.dtype)
 
 
 def diff(p: DevPoly, var_id: int, zeroprec: float = 0.0) -> DevPoly:
     cp = p.cstruct()
-    return _run_out("polylab_diff",
-                    lambda o, fn: _lib.polylab_diff(C.byref(cp), int(var_id), zeroprec, o, fn, None, _stream()),
-                    p.n, p.coef.device)
+    name, fn = _call("polylab_diff", p)
+    return _run_out(name, lambda o, al: fn(C.byref(cp), int(var_id), zeroprec, o, al, None, _stream()), p.n,
+                    p.coef.device, p.coef.dtype)
 
 
 def jacobian(p: DevPoly, zeroprec: float = 0.0) -> list:
