@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--forms", default="fp64,fp32", help="forms to time (profiling runs time one)")
     ap.add_argument("--rows-only", action="store_true", help="only the per-row measurements (profiling runs)")
     ap.add_argument("--config", default=None,
-                    help="threads,ctas_per_sm,order[,term_threads,chunks,terms_ctas,third_ctas] instead of "
+                    help="threads,ctas_per_sm,order[,term_threads,chunks,terms_ctas,third_ctas,frame_split] instead of "
                          "autotuning (profiling runs)")
     return ap.parse_args()
 
@@ -318,7 +318,7 @@ def main():
             batches[form].set_config(*(int(v) for v in args.config.split(",")))
             tuned[form] = dict(batches[form].config(), ms=None)
         else:
-            cfg, ms = batches[form].autotune(reps=1)
+            cfg, ms = batches[form].autotune(reps=2)
             tuned[form] = dict(cfg, ms=round(ms, 3))
         graphs[form] = capture(batches[form])
 

@@ -361,6 +361,12 @@ typedef struct {
   int32_t chunks;
   int32_t terms_ctas;
   int32_t third_ctas;
+  /* frame_split (0 or 1): with chunks = 1, the frame stage runs as up to
+   * three launches over classes of polynomials by n (n > 40 with `threads`
+   * per CTA, 24 < n <= 40 and n <= 24 with 64), each sized for its class's
+   * largest n and taken in an order of n descending; ctas_per_sm caps the
+   * first class only.  0: one launch over all polynomials. */
+  int32_t frame_split;
 } polylab_batch_config;
 
 polylab_status polylab_batch_create(int32_t n_polys, const polylab_poly* polys,
@@ -377,21 +383,23 @@ polylab_status polylab_batch_run(polylab_batch* batch, polylab_stream stream);
 polylab_status polylab_batch_run_stage(polylab_batch* batch, int32_t stage, polylab_stream stream);
 /* Synchronises `stream` and reports whether any run of this batch gave up a
  * bounded wait (a bulk copy into shared memory that did not complete within
- * two seconds): POLYLAB_ERR_TIMEOUT then, POLYLAB_OK otherwise. */
+ * two seconds) since the last check: POLYLAB_ERR_TIMEOUT then (the stage is
+ * named in polylab_last_error(); the record is cleared, so the batch may run
+ * again), POLYLAB_OK otherwise. */
 polylab_status polylab_batch_check(polylab_batch* batch, polylab_stream stream);
 polylab_status polylab_batch_get_config(const polylab_batch* batch, polylab_batch_config* cfg);
 polylab_status polylab_batch_set_config(polylab_batch* batch, const polylab_batch_config* cfg,
                                         polylab_stream stream);
 /* The project's autotuner, stage by stage on this batch (one warm-up and
  * `reps` timed runs per trial, CUDA events on `stream`, synchronising):
- * term_threads in {64,128,256} timed over the two term sweeps, then threads in
- * {64,128,256} x ctas_per_sm in {occupancy, 2, 4} timed over the frame stage,
- * then order in {cost order, given order} timed over the whole run, then
- * pipelined runs (chunks 8 with residency caps {occupancy} and {4, 4, 3} for
- * the term, frame and third stages, then chunks 4 with the better caps), kept
- * if faster than the stages in sequence.  Keeps the fastest of each step and returns the result (and the
- * mean time of a whole run in ms, if best_ms is not NULL).  The outputs hold
- * the last run's results. */
+ * term_threads in {64,128,256} timed over the two term sweeps, then
+ * frame_split in {1, 0} x threads in {64,128,256} x ctas_per_sm in
+ * {occupancy, 2, 4} timed over the frame stage,
+ * then order in {cost order, given order} timed over the whole run, all with
+ * chunks = 1 (pipelined runs are set explicitly; on the bench's batches they
+ * were never faster).  Keeps the fastest of each step and returns the result
+ * (and the mean time of a whole run in ms, if best_ms is not NULL).  The
+ * outputs hold the last run's results. */
 polylab_status polylab_batch_autotune(polylab_batch* batch, int32_t reps, polylab_stream stream,
                                       polylab_batch_config* chosen, float* best_ms);
 polylab_status polylab_batch_destroy(polylab_batch* batch, polylab_stream stream);

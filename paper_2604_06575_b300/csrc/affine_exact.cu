@@ -148,24 +148,23 @@ __device__ __forceinline__ void ldlt_block(int m, Col col, double* __restrict__ 
       __syncwarp();
       pivot(k + 1);
     } else {
-      // columns k+2..m-1 of the trailing triangle, enumerated column-major
-      // over the threads of warps 1..NW-1
+      // columns k+2..m-1 of the trailing triangle over the threads of warps
+      // 1..NW-1: element q of the triangle listed column by column from the
+      // last column (c + 1 rows for column j = m-1-c) sits in the column c
+      // with c(c+1)/2 <= q < (c+1)(c+2)/2, found by a square root (exact
+      // here: 8q + 1 < 2^14) with a one-step guard, so that consecutive
+      // threads take consecutive rows of one column and no thread walks the
+      // column boundaries
       constexpr int S = NT - 32;
-      int len = m - k - 2, c = 0, r = tid - 32;
-      while (len > 0 && r >= len) {
-        r -= len;
-        ++c;
-        --len;
-      }
-      while (len > 0) {
-        const int j = k + 2 + c;
-        col(j)[j + r] -= ck[j + r] * uk[j];
-        r += S;
-        while (len > 0 && r >= len) {
-          r -= len;
-          ++c;
-          --len;
-        }
+      const int len = m - k - 2;
+      const int T = len * (len + 1) / 2;
+      for (int q = tid - 32; q < T; q += S) {
+        int c = (int)((__fsqrt_rn(8.f * (float)q + 1.f) - 1.f) * 0.5f);
+        c += (c + 1) * (c + 2) / 2 <= q;
+        c -= c * (c + 1) / 2 > q;
+        const int j = m - 1 - c;
+        const int i = j + q - c * (c + 1) / 2;
+        col(j)[i] -= ck[i] * uk[j];
       }
     }
     __syncthreads();
@@ -446,6 +445,265 @@ __global__ void __launch_bounds__(NT) exact_terms_kernel(StageArgs<R> a) {
 }
 
 // ------------------------------------------------------------------ stage 2
+// One (polynomial, point) item of the frame stage.  SMEM: the n x n
+// matrices live in shared memory (else in this CTA's global workspace); as a
+// template parameter it lets every matrix access compile to a shared-memory
+// instruction.  Returns false when a bounded wait expired (the kernel stops).
+template <typename R, int NT, bool SMEM>
+__device__ __forceinline__ bool frame_item(const StageArgs<R>& a, const ExactDesc& pd, int64_t p, unsigned char* sm,
+                                           int& s_flag, double* s_sc, uint64_t& s_bar, uint32_t& phase) {
+  constexpr bool kF64 = sizeof(R) == 8;
+  constexpr int NW = NT / 32;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int n = pd.n, m = n - 1, nn = n * n, xs = x_stride(m);
+  const Lay2 L = lay_frame<R>(n, SMEM);
+  double* e = (double*)(sm + L.e);
+  double* v = (double*)(sm + L.v);
+  double* h = (double*)(sm + L.h);
+  double* dv = (double*)(sm + L.dv);
+  double* di = (double*)(sm + L.di);
+  double* uc = (double*)(sm + L.uc);
+  R* vr = (R*)(sm + L.vr);
+  R* u = (R*)(sm + L.u);
+  R* w = (R*)(sm + L.w);
+  unsigned char* gb = a.gws + (size_t)blockIdx.x * a.gws_stride;
+  R* Hr = SMEM ? (R*)(sm + L.Hr) : (R*)gb;
+  unsigned char* rest = SMEM ? nullptr : gb + (size_t)mat_slot<R>(n) * sizeof(R);
+  // FP64 factor storage, element (i, j) of the leading block at col(j)[i]:
+  // in place in Hr (col(j) = row j of the symmetric Hr) for the FP64 form, a
+  // packed column-major lower triangle for the FP32 form; X = L^{-1} with
+  // row stride xs (the FP32 form reuses the factor's storage)
+  double* Ld = kF64 ? (double*)Hr : (SMEM ? (double*)(sm + L.Ld) : (double*)rest);
+  R* Xs = kF64 ? (SMEM ? (R*)(sm + L.X) : (R*)rest) : (R*)Ld;
+  auto col = [Ld, n, m](int j) -> double* {
+    return kF64 ? Ld + (size_t)j * n : Ld + ((size_t)j * m - (size_t)j * (j - 1) / 2 - j);
+  };
+  const R* Hg = a.mats_h + pd.mat_off + p * mat_slot<R>(n);
+  R* Wg = a.mats_w + pd.mat_off + p * mat_slot<R>(n);
+  const uint32_t mat_bytes = (uint32_t)(mat_slot<R>(n) * sizeof(R));
+  double* rec = a.vecs + pd.vec_off + p * vrec(n);
+  // H (upper triangle) into shared memory by one bulk copy
+  if (SMEM) {
+    if (tid == 0) {
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(&s_bar, mat_bytes);
+      bulk_g2s(Hr, Hg, mat_bytes, &s_bar);
+    }
+  } else {
+    for (int i = wid; i < n; i += NW)
+      for (int j = lane; j < n; j += 32) Hr[i * n + j] = Hg[i * n + j];
+  }
+  // |g|, the zero-gradient test and the Householder vector (warp 0)
+  if (wid == 0) {
+    double gg = 0.0;
+    for (int i = lane; i < n; i += 32) gg += rec[i] * rec[i];
+    const double gn = sqrt(warp_sum(gg));
+    bool zero = !(gn > 0.0) || !isfinite(gn);
+    // relative test at the resolution of the form: 1e-14 (FP64), 1e-6 (FP32 sums)
+    if (!a.assume_nonzero_x && gn <= (kF64 ? 1e-14 : 1e-6) * rec[4 * n]) zero = true;
+    double beta = 0.0, sgn = 1.0;
+    if (!zero) {
+      const double ign = 1.0 / gn;
+      const double en = rec[n - 1] * ign;
+      sgn = en >= 0.0 ? 1.0 : -1.0;
+      beta = 1.0 / (1.0 + sgn * en);  // 2 / v^T v with v^T v = 2 (1 + s e_n)
+      for (int i = lane; i < n; i += 32) {
+        const double ei = rec[i] * ign;
+        e[i] = ei;
+        v[i] = ei + (i == n - 1 ? sgn : 0.0);
+        vr[i] = R(v[i]);
+      }
+    }
+    if (lane == 0) {
+      s_sc[0] = gn;
+      s_sc[1] = zero ? 1.0 : 0.0;
+      s_sc[2] = beta;
+      s_sc[3] = sgn;
+      s_flag = 0;
+    }
+  }
+  if (SMEM) {
+    const bool ok = mbar_wait(&s_bar, phase, a.err, 2);
+    phase ^= 1u;
+    if (!ok) return false;
+  }
+  __syncthreads();
+  for (int i = wid; i < n; i += NW)  // mirror the upper triangle
+    for (int j = lane; j < i; j += 32) Hr[i * n + j] = Hr[j * n + i];
+  __syncthreads();
+  const double gn = s_sc[0], beta = s_sc[2], sgn = s_sc[3];
+  if (s_sc[1] != 0.0) {
+    write_failed(pd, p, n, gn, POLYLAB_FLAG_ZERO_GRAD);
+    if (tid == 0) {
+      rec[4 * n + 1] = gn;
+      rec[4 * n + 4] = kStZero;
+    }
+    return true;
+  }
+  for (int i = tid; i < n; i += NT) {  // u = H v (H symmetric: column access, conflict-free)
+    R acc = R(0);
+    for (int j = 0; j < n; ++j) acc += Hr[j * n + i] * vr[j];
+    u[i] = acc;
+  }
+  __syncthreads();
+  if (wid == 0) {  // w = beta u - (beta^2 / 2) (v.u) v
+    double part = 0.0;
+    for (int i = lane; i < n; i += 32) part += v[i] * (double)u[i];
+    const double gamma = warp_sum(part);
+    for (int i = lane; i < n; i += 32) w[i] = R(beta * (double)u[i] - 0.5 * beta * beta * gamma * v[i]);
+  }
+  __syncthreads();
+  for (int i = wid; i < n; i += NW)  // P H P = H - v w^T - w v^T
+    for (int j = lane; j < n; j += 32) Hr[i * n + j] -= vr[i] * w[j] + w[i] * vr[j];
+  __syncthreads();
+  for (int i = tid; i < n; i += NT) h[i] = i < m ? -sgn * (double)Hr[i * n + (n - 1)] : 0.0;
+  if constexpr (kF64) {
+    for (int i = tid; i < m; i += NT) Hr[i * n + i] += a.r;
+  } else {
+    for (int j = wid; j < m; j += NW)
+      for (int i = j + lane; i < m; i += 32) col(j)[i] = (double)Hr[j * n + i];
+    __syncthreads();
+    for (int i = tid; i < m; i += NT) col(i)[i] += a.r;
+  }
+  __syncthreads();
+  ldlt_block<NT>(m, col, uc, dv, di, &s_flag);
+  __syncthreads();
+  if (s_flag) {
+    write_failed(pd, p, n, gn, POLYLAB_FLAG_NOT_PD);
+    if (tid == 0) {
+      rec[4 * n + 1] = gn;
+      rec[4 * n + 4] = kStNotPd;
+    }
+    return true;
+  }
+  // log-det (warp 0) while the others take the factor into the form's
+  // precision: Lt(i, j) = Hr[j*n + i] = l_ij (i > j); sq = d^{-1/2}
+  R* sq = w;
+  if (wid == 0) {
+    double lsum = 0.0;
+    for (int k = lane; k < m; k += 32) lsum += log(dv[k]);
+    lsum = warp_sum(lsum);
+    if (lane == 0) s_sc[1] = lsum;
+  }
+  for (int i = tid; i < m; i += NT) sq[i] = kF64 ? R(sqrt(di[i])) : R(sqrtf((float)di[i]));
+  if constexpr (!kF64) {  // (the factor's storage becomes X after the next barrier)
+    for (int j = wid; j < m; j += NW)
+      for (int i = j + 1 + lane; i < m; i += 32) Hr[j * n + i] = (R)col(j)[i];
+  }
+  __syncthreads();  // L in the form's precision and sq complete
+  // X' = D^{-1/2} X with X = L^{-1} (unit lower), stored transposed:
+  // Xs[j*xs + i] = X'_ij, i >= j; then M = X'^T X'
+  if (m <= 64) {
+    // column j of X is the forward substitution of e_j alone, so columns
+    // are independent: warp w takes columns j = w, w + NW, ... two at a
+    // time, lane q holding rows q and q + 32 in registers; x_k reaches the
+    // other lanes by a shuffle once final (no block barrier)
+    for (int ja = wid; ja < m; ja += 2 * NW) {
+      const int jb = ja + NW;  // second column (none if jb >= m)
+      const int r0 = lane, r1 = lane + 32;
+      R a0 = r0 == ja ? R(1) : R(0), a1 = r1 == ja ? R(1) : R(0);
+      R b0 = r0 == jb ? R(1) : R(0), b1 = r1 == jb ? R(1) : R(0);
+      for (int k = ja; k + 1 < m; ++k) {
+        const R l0 = (r0 > k && r0 < m) ? Hr[k * n + r0] : R(0);
+        const R l1 = (r1 > k && r1 < m) ? Hr[k * n + r1] : R(0);
+        const R xa = __shfl_sync(0xffffffffu, k < 32 ? a0 : a1, k & 31);
+        a0 -= l0 * xa;
+        a1 -= l1 * xa;
+        if (k >= jb) {  // column jb is zero above row jb
+          const R xb = __shfl_sync(0xffffffffu, k < 32 ? b0 : b1, k & 31);
+          b0 -= l0 * xb;
+          b1 -= l1 * xb;
+        }
+      }
+      if (r0 >= ja && r0 < m) Xs[ja * xs + r0] = a0 * sq[r0];
+      if (r1 >= ja && r1 < m) Xs[ja * xs + r1] = a1 * sq[r1];
+      if (jb < m) {
+        if (r0 >= jb && r0 < m) Xs[jb * xs + r0] = b0 * sq[r0];
+        if (r1 >= jb && r1 < m) Xs[jb * xs + r1] = b1 * sq[r1];
+      }
+    }
+  } else {
+    for (int j = wid; j < m; j += NW)
+      for (int i = j + lane; i < m; i += 32) Xs[j * xs + i] = i == j ? R(1) : R(0);
+    __syncthreads();
+    // right-looking: after step k row k of X is final; X_ij -= l_ik X_kj for
+    // j <= k < i, the (m-k-1) x (k+1) rectangle enumerated over the CTA
+    for (int k = 0; k + 1 < m; ++k) {
+      const int rows = m - k - 1;
+      // thread tid starts at q = tid = j * rows + i0 and steps by NT
+      const int dj = NT / rows, di0 = NT - dj * rows;
+      int j = tid / rows, i0 = tid - j * rows;
+      const R* lk = Hr + k * n + k + 1;
+      while (j <= k) {
+        Xs[j * xs + k + 1 + i0] -= lk[i0] * Xs[j * xs + k];
+        j += dj;
+        i0 += di0;
+        if (i0 >= rows) {
+          i0 -= rows;
+          ++j;
+        }
+      }
+      __syncthreads();
+    }
+    for (int j = wid; j < m; j += NW)
+      for (int i = j + lane; i < m; i += 32) Xs[j * xs + i] *= sq[i];
+  }
+  __syncthreads();
+  // M = H_T^{-1} = X'^T X', upper triangle into Hr (L no longer needed)
+  for (int i = wid; i < m; i += NW)
+    for (int j = i + lane; j < m; j += 32) {
+      R acc = R(0);
+      for (int k = j; k < m; ++k) acc += Xs[i * xs + k] * Xs[j * xs + k];
+      Hr[i * n + j] = acc;
+    }
+  __syncthreads();
+  for (int i = wid; i < n; i += NW)  // Hr <- [M 0; 0 0], full symmetric, in place
+    for (int j = lane; j < n; j += 32) {
+      if (i == n - 1 || j == n - 1) Hr[i * n + j] = R(0);
+      else if (i > j) Hr[i * n + j] = Hr[j * n + i];
+    }
+  __syncthreads();
+  for (int i = tid; i < n; i += NT) {  // u = [M 0; 0 0] v
+    R acc = R(0);
+    for (int j = 0; j < n; ++j) acc += Hr[j * n + i] * vr[j];
+    u[i] = acc;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    double part = 0.0;
+    for (int i = lane; i < n; i += 32) part += v[i] * (double)u[i];
+    const double gam2 = warp_sum(part);
+    for (int i = lane; i < n; i += 32) {
+      w[i] = R(beta * (double)u[i] - 0.5 * beta * beta * gam2 * v[i]);
+      rec[n + i] = v[i];
+      rec[2 * n + i] = e[i];
+      rec[3 * n + i] = h[i];
+    }
+    if (lane == 0) {
+      rec[4 * n + 1] = gn;
+      rec[4 * n + 2] = beta;
+      rec[4 * n + 3] = s_sc[1];
+      rec[4 * n + 4] = kStOk;
+    }
+  }
+  __syncthreads();
+  if (SMEM) {  // W = P [M 0; 0 0] P in place, then one bulk copy out
+    for (int i = wid; i < n; i += NW)
+      for (int j = lane; j < n; j += 32) Hr[i * n + j] -= vr[i] * w[j] + w[i] * vr[j];
+    __syncthreads();
+    if (tid == 0) {
+      fence_proxy_async_smem();
+      bulk_s2g(Wg, Hr, mat_bytes);
+      bulk_commit();
+      bulk_wait_read();
+    }
+  } else {
+    for (int i = wid; i < n; i += NW)
+      for (int j = lane; j < n; j += 32) Wg[i * n + j] = Hr[i * n + j] - (vr[i] * w[j] + w[i] * vr[j]);
+  }
+  return true;
+}
+
 template <typename R, int NT>
 __global__ void __launch_bounds__(NT) exact_frame_kernel(StageArgs<R> a) {
   extern __shared__ __align__(16) unsigned char sm[];
@@ -453,9 +711,7 @@ __global__ void __launch_bounds__(NT) exact_frame_kernel(StageArgs<R> a) {
   __shared__ int s_flag;
   __shared__ double s_sc[4];
   __shared__ __align__(8) uint64_t s_bar;
-  constexpr bool kF64 = sizeof(R) == 8;
-  constexpr int NW = NT / 32;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int tid = threadIdx.x;
   if (tid == 0) {
     mbar_init(&s_bar, 1);
     mbar_init_fence();
@@ -467,252 +723,9 @@ __global__ void __launch_bounds__(NT) exact_frame_kernel(StageArgs<R> a) {
     const int lo = find_poly(a.prefix, a.n_desc, item);
     const ExactDesc& pd = a.descs[a.order[lo]];
     const int64_t p = item - a.prefix[lo];
-    const int n = pd.n, m = n - 1, nn = n * n, xs = x_stride(m);
-    const Lay2 L = lay_frame<R>(n, pd.mats_in_smem);
-    double* e = (double*)(sm + L.e);
-    double* v = (double*)(sm + L.v);
-    double* h = (double*)(sm + L.h);
-    double* dv = (double*)(sm + L.dv);
-    double* di = (double*)(sm + L.di);
-    double* uc = (double*)(sm + L.uc);
-    R* vr = (R*)(sm + L.vr);
-    R* u = (R*)(sm + L.u);
-    R* w = (R*)(sm + L.w);
-    unsigned char* gb = a.gws + (size_t)blockIdx.x * a.gws_stride;
-    R* Hr = pd.mats_in_smem ? (R*)(sm + L.Hr) : (R*)gb;
-    unsigned char* rest = pd.mats_in_smem ? nullptr : gb + (size_t)mat_slot<R>(n) * sizeof(R);
-    // FP64 factor storage, element (i, j) of the leading block at col(j)[i]:
-    // in place in Hr (col(j) = row j of the symmetric Hr) for the FP64 form, a
-    // packed column-major lower triangle for the FP32 form; X = L^{-1} with
-    // row stride xs (the FP32 form reuses the factor's storage)
-    double* Ld = kF64 ? (double*)Hr : (pd.mats_in_smem ? (double*)(sm + L.Ld) : (double*)rest);
-    R* Xs = kF64 ? (pd.mats_in_smem ? (R*)(sm + L.X) : (R*)rest) : (R*)Ld;
-    auto col = [Ld, n, m](int j) -> double* {
-      return kF64 ? Ld + (size_t)j * n : Ld + ((size_t)j * m - (size_t)j * (j - 1) / 2 - j);
-    };
-    const R* Hg = a.mats_h + pd.mat_off + p * mat_slot<R>(n);
-    R* Wg = a.mats_w + pd.mat_off + p * mat_slot<R>(n);
-    const uint32_t mat_bytes = (uint32_t)(mat_slot<R>(n) * sizeof(R));
-    double* rec = a.vecs + pd.vec_off + p * vrec(n);
-    // H (upper triangle) into shared memory by one bulk copy
-    if (pd.mats_in_smem) {
-      if (tid == 0) {
-        fence_proxy_async_smem();
-        mbar_arrive_expect_tx(&s_bar, mat_bytes);
-        bulk_g2s(Hr, Hg, mat_bytes, &s_bar);
-      }
-    } else {
-      for (int i = wid; i < n; i += NW)
-        for (int j = lane; j < n; j += 32) Hr[i * n + j] = Hg[i * n + j];
-    }
-    // |g|, the zero-gradient test and the Householder vector (warp 0)
-    if (wid == 0) {
-      double gg = 0.0;
-      for (int i = lane; i < n; i += 32) gg += rec[i] * rec[i];
-      const double gn = sqrt(warp_sum(gg));
-      bool zero = !(gn > 0.0) || !isfinite(gn);
-      // relative test at the resolution of the form: 1e-14 (FP64), 1e-6 (FP32 sums)
-      if (!a.assume_nonzero_x && gn <= (kF64 ? 1e-14 : 1e-6) * rec[4 * n]) zero = true;
-      double beta = 0.0, sgn = 1.0;
-      if (!zero) {
-        const double ign = 1.0 / gn;
-        const double en = rec[n - 1] * ign;
-        sgn = en >= 0.0 ? 1.0 : -1.0;
-        beta = 1.0 / (1.0 + sgn * en);  // 2 / v^T v with v^T v = 2 (1 + s e_n)
-        for (int i = lane; i < n; i += 32) {
-          const double ei = rec[i] * ign;
-          e[i] = ei;
-          v[i] = ei + (i == n - 1 ? sgn : 0.0);
-          vr[i] = R(v[i]);
-        }
-      }
-      if (lane == 0) {
-        s_sc[0] = gn;
-        s_sc[1] = zero ? 1.0 : 0.0;
-        s_sc[2] = beta;
-        s_sc[3] = sgn;
-        s_flag = 0;
-      }
-    }
-    if (pd.mats_in_smem) {
-      const bool ok = mbar_wait(&s_bar, phase, a.err);
-      phase ^= 1u;
-      if (!ok) return;
-    }
-    __syncthreads();
-    for (int i = wid; i < n; i += NW)  // mirror the upper triangle
-      for (int j = lane; j < i; j += 32) Hr[i * n + j] = Hr[j * n + i];
-    __syncthreads();
-    const double gn = s_sc[0], beta = s_sc[2], sgn = s_sc[3];
-    if (s_sc[1] != 0.0) {
-      write_failed(pd, p, n, gn, POLYLAB_FLAG_ZERO_GRAD);
-      if (tid == 0) {
-        rec[4 * n + 1] = gn;
-        rec[4 * n + 4] = kStZero;
-      }
-      continue;
-    }
-    for (int i = tid; i < n; i += NT) {  // u = H v (H symmetric: column access, conflict-free)
-      R acc = R(0);
-      for (int j = 0; j < n; ++j) acc += Hr[j * n + i] * vr[j];
-      u[i] = acc;
-    }
-    __syncthreads();
-    if (wid == 0) {  // w = beta u - (beta^2 / 2) (v.u) v
-      double part = 0.0;
-      for (int i = lane; i < n; i += 32) part += v[i] * (double)u[i];
-      const double gamma = warp_sum(part);
-      for (int i = lane; i < n; i += 32) w[i] = R(beta * (double)u[i] - 0.5 * beta * beta * gamma * v[i]);
-    }
-    __syncthreads();
-    for (int i = wid; i < n; i += NW)  // P H P = H - v w^T - w v^T
-      for (int j = lane; j < n; j += 32) Hr[i * n + j] -= vr[i] * w[j] + w[i] * vr[j];
-    __syncthreads();
-    for (int i = tid; i < n; i += NT) h[i] = i < m ? -sgn * (double)Hr[i * n + (n - 1)] : 0.0;
-    if constexpr (kF64) {
-      for (int i = tid; i < m; i += NT) Hr[i * n + i] += a.r;
-    } else {
-      for (int j = wid; j < m; j += NW)
-        for (int i = j + lane; i < m; i += 32) col(j)[i] = (double)Hr[j * n + i];
-      __syncthreads();
-      for (int i = tid; i < m; i += NT) col(i)[i] += a.r;
-    }
-    __syncthreads();
-    ldlt_block<NT>(m, col, uc, dv, di, &s_flag);
-    __syncthreads();
-    if (s_flag) {
-      write_failed(pd, p, n, gn, POLYLAB_FLAG_NOT_PD);
-      if (tid == 0) {
-        rec[4 * n + 1] = gn;
-        rec[4 * n + 4] = kStNotPd;
-      }
-      continue;
-    }
-    // log-det (warp 0) while the others take the factor into the form's
-    // precision: Lt(i, j) = Hr[j*n + i] = l_ij (i > j); sq = d^{-1/2}
-    R* sq = w;
-    if (wid == 0) {
-      double lsum = 0.0;
-      for (int k = lane; k < m; k += 32) lsum += log(dv[k]);
-      lsum = warp_sum(lsum);
-      if (lane == 0) s_sc[1] = lsum;
-    }
-    for (int i = tid; i < m; i += NT) sq[i] = kF64 ? R(sqrt(di[i])) : R(sqrtf((float)di[i]));
-    if constexpr (!kF64) {  // (the factor's storage becomes X after the next barrier)
-      for (int j = wid; j < m; j += NW)
-        for (int i = j + 1 + lane; i < m; i += 32) Hr[j * n + i] = (R)col(j)[i];
-    }
-    __syncthreads();  // L in the form's precision and sq complete
-    // X' = D^{-1/2} X with X = L^{-1} (unit lower), stored transposed:
-    // Xs[j*xs + i] = X'_ij, i >= j; then M = X'^T X'
-    if (m <= 64) {
-      // column j of X is the forward substitution of e_j alone, so columns
-      // are independent: warp w takes columns j = w, w + NW, ... two at a
-      // time, lane q holding rows q and q + 32 in registers; x_k reaches the
-      // other lanes by a shuffle once final (no block barrier)
-      for (int ja = wid; ja < m; ja += 2 * NW) {
-        const int jb = ja + NW;  // second column (none if jb >= m)
-        const int r0 = lane, r1 = lane + 32;
-        R a0 = r0 == ja ? R(1) : R(0), a1 = r1 == ja ? R(1) : R(0);
-        R b0 = r0 == jb ? R(1) : R(0), b1 = r1 == jb ? R(1) : R(0);
-        for (int k = ja; k + 1 < m; ++k) {
-          const R l0 = (r0 > k && r0 < m) ? Hr[k * n + r0] : R(0);
-          const R l1 = (r1 > k && r1 < m) ? Hr[k * n + r1] : R(0);
-          const R xa = __shfl_sync(0xffffffffu, k < 32 ? a0 : a1, k & 31);
-          a0 -= l0 * xa;
-          a1 -= l1 * xa;
-          if (k >= jb) {  // column jb is zero above row jb
-            const R xb = __shfl_sync(0xffffffffu, k < 32 ? b0 : b1, k & 31);
-            b0 -= l0 * xb;
-            b1 -= l1 * xb;
-          }
-        }
-        if (r0 >= ja && r0 < m) Xs[ja * xs + r0] = a0 * sq[r0];
-        if (r1 >= ja && r1 < m) Xs[ja * xs + r1] = a1 * sq[r1];
-        if (jb < m) {
-          if (r0 >= jb && r0 < m) Xs[jb * xs + r0] = b0 * sq[r0];
-          if (r1 >= jb && r1 < m) Xs[jb * xs + r1] = b1 * sq[r1];
-        }
-      }
-    } else {
-      for (int j = wid; j < m; j += NW)
-        for (int i = j + lane; i < m; i += 32) Xs[j * xs + i] = i == j ? R(1) : R(0);
-      __syncthreads();
-      // right-looking: after step k row k of X is final; X_ij -= l_ik X_kj for
-      // j <= k < i, the (m-k-1) x (k+1) rectangle enumerated over the CTA
-      for (int k = 0; k + 1 < m; ++k) {
-        const int rows = m - k - 1;
-        // thread tid starts at q = tid = j * rows + i0 and steps by NT
-        const int dj = NT / rows, di0 = NT - dj * rows;
-        int j = tid / rows, i0 = tid - j * rows;
-        const R* lk = Hr + k * n + k + 1;
-        while (j <= k) {
-          Xs[j * xs + k + 1 + i0] -= lk[i0] * Xs[j * xs + k];
-          j += dj;
-          i0 += di0;
-          if (i0 >= rows) {
-            i0 -= rows;
-            ++j;
-          }
-        }
-        __syncthreads();
-      }
-      for (int j = wid; j < m; j += NW)
-        for (int i = j + lane; i < m; i += 32) Xs[j * xs + i] *= sq[i];
-    }
-    __syncthreads();
-    // M = H_T^{-1} = X'^T X', upper triangle into Hr (L no longer needed)
-    for (int i = wid; i < m; i += NW)
-      for (int j = i + lane; j < m; j += 32) {
-        R acc = R(0);
-        for (int k = j; k < m; ++k) acc += Xs[i * xs + k] * Xs[j * xs + k];
-        Hr[i * n + j] = acc;
-      }
-    __syncthreads();
-    for (int i = wid; i < n; i += NW)  // Hr <- [M 0; 0 0], full symmetric, in place
-      for (int j = lane; j < n; j += 32) {
-        if (i == n - 1 || j == n - 1) Hr[i * n + j] = R(0);
-        else if (i > j) Hr[i * n + j] = Hr[j * n + i];
-      }
-    __syncthreads();
-    for (int i = tid; i < n; i += NT) {  // u = [M 0; 0 0] v
-      R acc = R(0);
-      for (int j = 0; j < n; ++j) acc += Hr[j * n + i] * vr[j];
-      u[i] = acc;
-    }
-    __syncthreads();
-    if (wid == 0) {
-      double part = 0.0;
-      for (int i = lane; i < n; i += 32) part += v[i] * (double)u[i];
-      const double gam2 = warp_sum(part);
-      for (int i = lane; i < n; i += 32) {
-        w[i] = R(beta * (double)u[i] - 0.5 * beta * beta * gam2 * v[i]);
-        rec[n + i] = v[i];
-        rec[2 * n + i] = e[i];
-        rec[3 * n + i] = h[i];
-      }
-      if (lane == 0) {
-        rec[4 * n + 1] = gn;
-        rec[4 * n + 2] = beta;
-        rec[4 * n + 3] = s_sc[1];
-        rec[4 * n + 4] = kStOk;
-      }
-    }
-    __syncthreads();
-    if (pd.mats_in_smem) {  // W = P [M 0; 0 0] P in place, then one bulk copy out
-      for (int i = wid; i < n; i += NW)
-        for (int j = lane; j < n; j += 32) Hr[i * n + j] -= vr[i] * w[j] + w[i] * vr[j];
-      __syncthreads();
-      if (tid == 0) {
-        fence_proxy_async_smem();
-        bulk_s2g(Wg, Hr, mat_bytes);
-        bulk_commit();
-        bulk_wait_read();
-      }
-    } else {
-      for (int i = wid; i < n; i += NW)
-        for (int j = lane; j < n; j += 32) Wg[i * n + j] = Hr[i * n + j] - (vr[i] * w[j] + w[i] * vr[j]);
-    }
+    const bool ok = pd.mats_in_smem ? frame_item<R, NT, true>(a, pd, p, sm, s_flag, s_sc, s_bar, phase)
+                                    : frame_item<R, NT, false>(a, pd, p, sm, s_flag, s_sc, s_bar, phase);
+    if (!ok) return;
   }
   if (tid == 0) bulk_wait_all();
 }
@@ -762,7 +775,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 1024 / NT : 1) exact_thir
       e[i] = rec[2 * n + i];
     }
     if (pd.w_in_smem) {
-      const bool ok = mbar_wait(&s_bar, phase, a.err);
+      const bool ok = mbar_wait(&s_bar, phase, a.err, 3);
       phase ^= 1u;
       if (!ok) return;
     }
@@ -855,7 +868,9 @@ template <typename R>
 static polylab_status prepare_exact(ExactBatch* b) {
   size_t smem[3] = {0, 0, 0}, gstride = 0;
   int64_t mat = 0, vec = 0;
-  for (auto& d : b->host_descs) {
+  b->frame_need.assign(b->host_descs.size(), 0);
+  for (size_t di = 0; di < b->host_descs.size(); ++di) {
+    ExactDesc& d = b->host_descs[di];
     const int E1 = d.E + 1;
     const int tt = b->cfg.term_threads, ft = b->cfg.threads;
     const bool gat = d.gather != nullptr;
@@ -869,6 +884,7 @@ static polylab_status prepare_exact(ExactBatch* b) {
       if (need[st] > kSmemCap) return POLYLAB_ERR_UNSUPPORTED;
       smem[st] = std::max(smem[st], need[st]);
     }
+    b->frame_need[di] = need[1];
     if (!d.mats_in_smem) gstride = std::max(gstride, frame_gmem<R>(d.n));
     d.mat_off = mat;
     d.vec_off = vec;
@@ -919,6 +935,54 @@ static polylab_status launch_stage_t(ExactBatch* b, int stage, int chunk, cudaSt
   return launch_status(stage == 0 ? "exact_terms_kernel" : stage == 1 ? "exact_frame_kernel" : "exact_third_kernel");
 }
 
+// One class of the split frame stage (sequential runs): the class's item
+// range of the frame order, its own counter and shared memory; the residency
+// cap applies to the first (largest-n) class only.
+template <typename R, int NT>
+static polylab_status launch_frame_class(ExactBatch* b, int cls, cudaStream_t s) {
+  const FrameClass& fc = b->fclass[cls];
+  if (fc.end <= fc.begin) return POLYLAB_OK;
+  auto k = exact_frame_kernel<R, NT>;
+  const size_t smem = std::max<size_t>(fc.smem, 16);
+  PL_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  PL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NT, smem));
+  per_sm = std::max(1, per_sm);
+  if (cls == 0 && b->cfg.ctas_per_sm > 0) per_sm = std::min(per_sm, b->cfg.ctas_per_sm);
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(fc.end - fc.begin, (int64_t)num_sms() * per_sm));
+  if (b->gws_stride > 0 && (size_t)grid * b->gws_stride > b->gws_bytes) return POLYLAB_ERR_UNSUPPORTED;
+  StageArgs<R> a{};
+  a.descs = b->descs;
+  a.n_desc = b->n_desc;
+  a.prefix = b->fprefix;
+  a.order = b->forder;
+  a.item_begin = fc.begin;
+  a.item_end = fc.end;
+  a.counter = b->fcounter + cls;
+  a.mats_h = (R*)b->ws_h;
+  a.mats_w = (R*)b->ws_w;
+  a.vecs = (double*)b->ws_v;
+  a.r = b->opts.regularization;
+  a.assume_nonzero_x = b->opts.assume_nonzero_x;
+  a.gws = b->gws;
+  a.gws_stride = b->gws_stride;
+  a.err = b->err;
+  PL_CUDA(cudaMemsetAsync(a.counter, 0, sizeof(int), s));
+  k<<<(unsigned)grid, NT, smem, s>>>(a);
+  return launch_status("exact_frame_kernel");
+}
+
+template <typename R>
+static polylab_status launch_frame_classes(ExactBatch* b, cudaStream_t s) {
+  for (int c = 0; c < kFrameClasses; ++c) {
+    const int nt = b->fclass[c].threads;
+    if (nt == 64) PL_TRY((launch_frame_class<R, 64>(b, c, s)));
+    else if (nt == 128) PL_TRY((launch_frame_class<R, 128>(b, c, s)));
+    else PL_TRY((launch_frame_class<R, 256>(b, c, s)));
+  }
+  return POLYLAB_OK;
+}
+
 template <typename R>
 static polylab_status launch_stage(ExactBatch* b, int stage, int chunk, cudaStream_t s) {
   const int nt = stage == 1 ? b->cfg.threads : b->cfg.term_threads;
@@ -935,6 +999,8 @@ static polylab_status launch_chunk(ExactBatch* b, int stage, int chunk, cudaStre
 polylab_status run_exact_stage(ExactBatch* b, int stage, cudaStream_t s) {
   if (b->total == 0) return POLYLAB_OK;
   const int C = (int)b->chunk_begin.size() - 1;
+  if (stage == 1 && C <= 1 && b->cfg.frame_split)
+    return b->opts.prec == POLYLAB_FP32 ? launch_frame_classes<float>(b, s) : launch_frame_classes<double>(b, s);
   for (int c = 0; c < C; ++c) PL_TRY(launch_chunk(b, stage, c, s));
   return POLYLAB_OK;
 }

@@ -39,13 +39,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait (2 s of wall time); on expiry records the error and returns false.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
+// Bounded wait (2 s of wall time); on expiry records `code` (which wait gave
+// up) in *err and returns false.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int code = 1) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = gtimer();
   while (!mbar_try_wait(bar, parity)) {
     if (gtimer() - t0 > 2000000000ull) {
-      atomicExch(err, 1);
+      atomicExch(err, code);
       return false;
     }
   }

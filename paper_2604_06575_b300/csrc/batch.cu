@@ -2,6 +2,7 @@
 // configuration and the project's autotuner, plus the public batch API.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <numeric>
 
@@ -23,10 +24,47 @@ polylab_status exact_batch_upload_order(ExactBatch* b, cudaStream_t s) {
   for (int i = 0; i < n; ++i) b->host_prefix[i + 1] = b->host_prefix[i] + b->host_descs[ord[i]].P;
   b->total = b->host_prefix[n];
   exact_batch_chunks(b);
+  // the split frame stage's own order: n descending (its cost is set by n)
+  std::vector<int>& ford = b->host_forder;
+  ford.resize(n);
+  std::iota(ford.begin(), ford.end(), 0);
+  std::stable_sort(ford.begin(), ford.end(),
+                   [&](int x, int y) { return b->host_descs[x].n > b->host_descs[y].n; });
+  b->host_fprefix.assign(n + 1, 0);
+  for (int i = 0; i < n; ++i) b->host_fprefix[i + 1] = b->host_fprefix[i] + b->host_descs[ford[i]].P;
+  exact_frame_classes(b);
   PL_CUDA(cudaMemcpyAsync(b->order, ord.data(), n * sizeof(int), cudaMemcpyHostToDevice, s));
   PL_CUDA(cudaMemcpyAsync(b->prefix, b->host_prefix.data(), (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  PL_CUDA(cudaMemcpyAsync(b->forder, ford.data(), n * sizeof(int), cudaMemcpyHostToDevice, s));
+  PL_CUDA(cudaMemcpyAsync(b->fprefix, b->host_fprefix.data(), (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice,
+                          s));
   PL_CUDA(cudaStreamSynchronize(s));  // host vectors may change after this returns
   return POLYLAB_OK;
+}
+
+// Classes of the split frame stage: n > 40 with the configured CTA size,
+// 24 < n <= 40 and n <= 24 with 64 threads (a point's factorisation has
+// little parallel work there, and smaller CTAs with smaller shared memory
+// keep more points in flight per SM).  Each class is a contiguous range of
+// the frame order; its shared memory is the largest need among its members.
+void exact_frame_classes(ExactBatch* b) {
+  const int bounds[kFrameClasses + 1] = {1 << 30, 40, 24, 0};
+  const int n = b->n_desc;
+  int i = 0;
+  for (int c = 0; c < kFrameClasses; ++c) {
+    FrameClass& fc = b->fclass[c];
+    fc.n_hi = bounds[c];
+    fc.n_lo = bounds[c + 1];
+    fc.threads = c == 0 ? b->cfg.threads : 64;
+    fc.smem = 0;
+    fc.begin = b->host_fprefix.empty() ? 0 : b->host_fprefix[i];
+    while (i < n && b->host_descs[b->host_forder[i]].n > fc.n_lo) {
+      const size_t need = (size_t)b->host_forder[i] < b->frame_need.size() ? b->frame_need[b->host_forder[i]] : 0;
+      fc.smem = std::max(fc.smem, need);
+      ++i;
+    }
+    fc.end = b->host_fprefix.empty() ? 0 : b->host_fprefix[i];
+  }
 }
 
 // Chunk boundaries in the work order at equal shares of the estimated cost
@@ -103,6 +141,9 @@ polylab_status exact_batch_init(ExactBatch* b, int n, const polylab_plan* const*
   PL_CUDA(cudaMallocAsync(&b->order, std::max(n, 1) * sizeof(int), s));
   PL_CUDA(cudaMallocAsync(&b->prefix, (n + 1) * sizeof(int64_t), s));
   PL_CUDA(cudaMallocAsync(&b->counter, 3 * kMaxChunks * sizeof(int), s));
+  PL_CUDA(cudaMallocAsync(&b->forder, std::max(n, 1) * sizeof(int), s));
+  PL_CUDA(cudaMallocAsync(&b->fprefix, (n + 1) * sizeof(int64_t), s));
+  PL_CUDA(cudaMallocAsync(&b->fcounter, kFrameClasses * sizeof(int), s));
   for (auto& st : b->side) PL_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
   b->events.resize(3 * kMaxChunks + 3);
   for (auto& e : b->events) PL_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
@@ -125,6 +166,7 @@ polylab_status exact_batch_init(ExactBatch* b, int n, const polylab_plan* const*
 // descriptors and grow the global workspace when needed.
 polylab_status exact_batch_relayout(ExactBatch* b, cudaStream_t s) {
   PL_TRY(prepare_exact_batch(b));
+  exact_frame_classes(b);
   PL_CUDA(cudaMemcpyAsync(b->descs, b->host_descs.data(), b->n_desc * sizeof(ExactDesc), cudaMemcpyHostToDevice, s));
   const size_t need = (size_t)num_sms() * 32 * b->gws_stride;
   if (need > b->gws_bytes) {
@@ -142,6 +184,12 @@ void exact_batch_release(ExactBatch* b, cudaStream_t s) {
   if (b->order) cudaFreeAsync(b->order, s);
   if (b->prefix) cudaFreeAsync(b->prefix, s);
   if (b->counter) cudaFreeAsync(b->counter, s);
+  if (b->forder) cudaFreeAsync(b->forder, s);
+  if (b->fprefix) cudaFreeAsync(b->fprefix, s);
+  if (b->fcounter) cudaFreeAsync(b->fcounter, s);
+  b->forder = nullptr;
+  b->fprefix = nullptr;
+  b->fcounter = nullptr;
   if (b->gws) cudaFreeAsync(b->gws, s);
   for (auto& st : b->side) {
     if (st) {
@@ -225,7 +273,14 @@ polylab_status polylab_batch_check(polylab_batch* b, polylab_stream stream) {
   int flag = 0;
   PL_CUDA(cudaMemcpyAsync(&flag, b->b.err, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
   PL_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
-  return flag ? POLYLAB_ERR_TIMEOUT : POLYLAB_OK;
+  if (!flag) return POLYLAB_OK;
+  char msg[96];
+  snprintf(msg, sizeof(msg), "a bounded wait of the %s stage expired",
+           flag == 2 ? "frame" : flag == 3 ? "third-derivative" : "batch");
+  set_last_message(msg);
+  PL_CUDA(cudaMemsetAsync(b->b.err, 0, sizeof(int), (cudaStream_t)stream));  // the batch may run again
+  PL_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  return POLYLAB_ERR_TIMEOUT;
 }
 
 polylab_status polylab_batch_get_config(const polylab_batch* b, polylab_batch_config* cfg) {
@@ -237,6 +292,7 @@ polylab_status polylab_batch_get_config(const polylab_batch* b, polylab_batch_co
   cfg->chunks = b->b.cfg.chunks;
   cfg->terms_ctas = b->b.cfg.terms_ctas;
   cfg->third_ctas = b->b.cfg.third_ctas;
+  cfg->frame_split = b->b.cfg.frame_split;
   return POLYLAB_OK;
 }
 
@@ -246,7 +302,8 @@ polylab_status polylab_batch_set_config(polylab_batch* b, const polylab_batch_co
   if (!ok_threads(cfg->threads) || !ok_threads(cfg->term_threads)) return POLYLAB_ERR_INVALID_ARG;
   auto ok_cap = [](int c) { return c >= 0 && c <= 32; };
   if (!ok_cap(cfg->ctas_per_sm) || !ok_cap(cfg->terms_ctas) || !ok_cap(cfg->third_ctas) ||
-      (cfg->order != 0 && cfg->order != 1) || cfg->chunks < 1 || cfg->chunks > kMaxChunks)
+      (cfg->order != 0 && cfg->order != 1) || cfg->chunks < 1 || cfg->chunks > kMaxChunks ||
+      (cfg->frame_split != 0 && cfg->frame_split != 1))
     return POLYLAB_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   const bool reorder = cfg->order != b->b.cfg.order;
@@ -254,6 +311,7 @@ polylab_status polylab_batch_set_config(polylab_batch* b, const polylab_batch_co
   b->b.cfg.chunks = cfg->chunks;
   b->b.cfg.terms_ctas = cfg->terms_ctas;
   b->b.cfg.third_ctas = cfg->third_ctas;
+  b->b.cfg.frame_split = cfg->frame_split;
   const bool relayout = cfg->threads != b->b.cfg.threads || cfg->term_threads != b->b.cfg.term_threads;
   b->b.cfg.threads = cfg->threads;
   b->b.cfg.term_threads = cfg->term_threads;
@@ -270,8 +328,11 @@ polylab_status polylab_batch_autotune(polylab_batch* b, int32_t reps, polylab_st
   if (!b || reps < 1) return POLYLAB_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   ExactBatch* eb = &b->b;
-  polylab_batch_config cur{eb->cfg.threads,      eb->cfg.ctas_per_sm, eb->cfg.order,     eb->cfg.term_threads,
-                           eb->cfg.chunks,       eb->cfg.terms_ctas,  eb->cfg.third_ctas};
+  polylab_batch_config cur{eb->cfg.threads, eb->cfg.ctas_per_sm, eb->cfg.order,      eb->cfg.term_threads,
+                           eb->cfg.chunks,  eb->cfg.terms_ctas,  eb->cfg.third_ctas, eb->cfg.frame_split};
+  cur.chunks = 1;  // the stages one after another
+  cur.terms_ctas = 0;
+  cur.third_ctas = 0;
   cudaEvent_t e0, e1;
   PL_CUDA(cudaEventCreate(&e0));
   PL_CUDA(cudaEventCreate(&e1));
@@ -324,16 +385,20 @@ polylab_status polylab_batch_autotune(polylab_batch* b, int32_t reps, polylab_st
   if (st == POLYLAB_OK) {
     polylab_batch_config best = cur;
     best_t = 1e30f;
-    for (int threads : {64, 128, 256}) {
-      for (int cap : {0, 2, 4}) {
-        polylab_batch_config c = cur;
-        c.threads = threads;
-        c.ctas_per_sm = cap;
-        if ((st = trial(c, 1, 1, &t)) != POLYLAB_OK) break;
-        if (t < best_t) {
-          best_t = t;
-          best = c;
+    for (int split : {1, 0}) {
+      for (int threads : {64, 128, 256}) {
+        for (int cap : {0, 2, 4}) {
+          polylab_batch_config c = cur;
+          c.frame_split = split;
+          c.threads = threads;
+          c.ctas_per_sm = cap;
+          if ((st = trial(c, 1, 1, &t)) != POLYLAB_OK) break;
+          if (t < best_t) {
+            best_t = t;
+            best = c;
+          }
         }
+        if (st != POLYLAB_OK) break;
       }
       if (st != POLYLAB_OK) break;
     }
@@ -351,42 +416,6 @@ polylab_status polylab_batch_autotune(polylab_batch* b, int32_t reps, polylab_st
         best_t = t;
         best = c;
       }
-    }
-    cur = best;
-  }
-  // 4. pipelined runs: per-stage residency caps (term sweeps, frame, third)
-  // that let the stages share each SM, then the number of chunks; kept only
-  // when faster than the stages one after another
-  if (st == POLYLAB_OK) {
-    polylab_batch_config best = cur;
-    const int caps[][3] = {{0, 0, 0}, {4, 4, 3}};
-    polylab_batch_config piped = cur;
-    float piped_t = 1e30f;
-    for (const auto& cp : caps) {
-      polylab_batch_config c = cur;
-      c.chunks = 8;
-      c.terms_ctas = cp[0];
-      c.ctas_per_sm = cp[1];
-      c.third_ctas = cp[2];
-      if ((st = trial(c, 0, 2, &t)) != POLYLAB_OK) break;
-      if (t < piped_t) {
-        piped_t = t;
-        piped = c;
-      }
-    }
-    for (int chunks : {4}) {
-      if (st != POLYLAB_OK) break;
-      polylab_batch_config c = piped;
-      c.chunks = chunks;
-      if ((st = trial(c, 0, 2, &t)) != POLYLAB_OK) break;
-      if (t < piped_t) {
-        piped_t = t;
-        piped = c;
-      }
-    }
-    if (piped_t < best_t) {
-      best_t = piped_t;
-      best = piped;
     }
     cur = best;
   }

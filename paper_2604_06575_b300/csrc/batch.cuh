@@ -42,6 +42,17 @@ struct ExactConfig {
                           // over three streams (1: the stages run one after another)
   int terms_ctas = 0;     // caps on resident CTAs per SM of the term sweeps (0: occupancy limit)
   int third_ctas = 0;
+  int frame_split = 1;    // sequential runs: frame stage in classes of polynomials by n
+};
+
+// A class of the split frame stage: polynomials with n in (n_lo, n_hi], a
+// contiguous range of the frame stage's own work order (n descending), run
+// as one launch with its own CTA size and shared memory.
+constexpr int kFrameClasses = 3;
+struct FrameClass {
+  int n_lo, n_hi, threads;
+  int64_t begin = 0, end = 0;
+  size_t smem = 0;
 };
 
 struct ExactBatch {
@@ -61,6 +72,15 @@ struct ExactBatch {
   int n_desc = 0;
   int64_t total = 0;
   size_t smem[3] = {0, 0, 0};
+  // split frame stage: per-descriptor frame-stage shared memory, the frame
+  // work order and prefix (host and DEVICE), the classes, one counter each
+  std::vector<size_t> frame_need;
+  std::vector<int> host_forder;
+  std::vector<int64_t> host_fprefix;
+  int* forder = nullptr;
+  int64_t* fprefix = nullptr;
+  int* fcounter = nullptr;
+  FrameClass fclass[kFrameClasses];
   // workspaces: H and W (one n x n slot per point each), small vectors
   void* ws_h = nullptr;
   void* ws_w = nullptr;
@@ -77,6 +97,7 @@ polylab_status exact_batch_init(ExactBatch* b, int n, const polylab_plan* const*
                                 double* const* Dunit, polylab_an_info* const* info, cudaStream_t s);
 polylab_status exact_batch_upload_order(ExactBatch* b, cudaStream_t s);
 void exact_batch_chunks(ExactBatch* b);
+void exact_frame_classes(ExactBatch* b);
 polylab_status exact_batch_relayout(ExactBatch* b, cudaStream_t s);
 void exact_batch_release(ExactBatch* b, cudaStream_t s);
 polylab_status prepare_exact_batch(ExactBatch* b);

@@ -33,7 +33,7 @@ FLAG_ZERO_GRAD, FLAG_NOT_PD, FLAG_KRYLOV_MAXIT = 1, 2, 4
 class PolylabError(RuntimeError):
     def __init__(self, fn: str, status: int):
         msg = _lib.polylab_last_error().decode()
-        super().__init__(f"{fn}: {STATUS.get(status, status)}" + (f" [{msg}]" if msg and status == 5 else ""))
+        super().__init__(f"{fn}: {STATUS.get(status, status)}" + (f" [{msg}]" if msg and status in (5, 6) else ""))
         self.status = status
 
 
@@ -56,7 +56,7 @@ class _AnOpts(C.Structure):
 class _BatchConfig(C.Structure):
     _fields_ = [("threads", C.c_int32), ("ctas_per_sm", C.c_int32), ("order", C.c_int32),
                 ("term_threads", C.c_int32), ("chunks", C.c_int32), ("terms_ctas", C.c_int32),
-                ("third_ctas", C.c_int32)]
+                ("third_ctas", C.c_int32), ("frame_split", C.c_int32)]
 
 
 INFO_DTYPE = np.dtype([("grad_norm", "<f8"), ("logdet", "<f8"), ("flags", "<i4"), ("hv_evals", "<i4"),
@@ -445,7 +445,8 @@ class Batch:
     def run_stage(self, stage: int):
         _check("polylab_batch_run_stage", _lib.polylab_batch_run_stage(self.h, stage, _stream()))
 
-    CONFIG_KEYS = ("threads", "ctas_per_sm", "order", "term_threads", "chunks", "terms_ctas", "third_ctas")
+    CONFIG_KEYS = ("threads", "ctas_per_sm", "order", "term_threads", "chunks", "terms_ctas", "third_ctas",
+                   "frame_split")
 
     def config(self):
         c = _BatchConfig()
@@ -453,11 +454,11 @@ class Batch:
         return {k: getattr(c, k) for k in self.CONFIG_KEYS}
 
     def set_config(self, threads, ctas_per_sm, order, term_threads=None, chunks=None, terms_ctas=None,
-                   third_ctas=None):
+                   third_ctas=None, frame_split=None):
         """Keys left as None keep their current value."""
         cur = self.config()
         given = dict(threads=threads, ctas_per_sm=ctas_per_sm, order=order, term_threads=term_threads,
-                     chunks=chunks, terms_ctas=terms_ctas, third_ctas=third_ctas)
+                     chunks=chunks, terms_ctas=terms_ctas, third_ctas=third_ctas, frame_split=frame_split)
         c = _BatchConfig(*[cur[k] if given[k] is None else given[k] for k in self.CONFIG_KEYS])
         _check("polylab_batch_set_config", _lib.polylab_batch_set_config(self.h, C.byref(c), _stream()))
 
