@@ -248,7 +248,7 @@ size_t frame_gmem(int n) {
 }
 
 struct Lay3 {
-  size_t pw, c, v, e, y, yr, W, total;
+  size_t pw, c, v, e, y, yr, ix, W, total;
 };
 template <typename R, int NW>
 __host__ __device__ Lay3 lay_third(int n, int E1, bool in_smem) {
@@ -260,6 +260,7 @@ __host__ __device__ Lay3 lay_third(int n, int E1, bool in_smem) {
   L.e = b.take(n * 8);
   L.y = b.take(n * 8);
   L.yr = b.take(n * sizeof(R));
+  L.ix = b.take(n * sizeof(R));
   L.W = in_smem ? b.take((size_t)mat_slot<R>(n) * sizeof(R)) : 0;
   L.total = b.o;
   return L;
@@ -769,11 +770,19 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 1024 / NT : 1) exact_thir
       bulk_g2s(Ws, Wg, bytes, &s_bar);
     }
     for (int i = tid; i < NW * n; i += NT) c[i] = R(0);
-    power_table<R, NT>(pd.X + p * n, n, E1, pw);
+    const double* X = pd.X + p * n;
+    power_table<R, NT>(X, n, E1, pw);
+    R* ix = (R*)(sm + L.ix);
+    bool in_range = true;
     for (int i = tid; i < n; i += NT) {
       v[i] = rec[n + i];
       e[i] = rec[2 * n + i];
+      const double ax = fabs(X[i]);
+      in_range &= ax >= pd.x_lo && ax <= pd.x_hi;
+      ix[i] = R(1) / R(X[i]);
     }
+    // gather form of the contraction where every |x_v| keeps m and 1/x normal
+    const bool gather = __syncthreads_and(in_range) != 0;
     if (pd.w_in_smem) {
       const bool ok = mbar_wait(&s_bar, phase, a.err, 3);
       phase ^= 1u;
@@ -789,9 +798,16 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 1024 / NT : 1) exact_thir
       for_support<kMaxSupport>([&](auto kc) {
         constexpr int K = decltype(kc)::value;
         if constexpr (K >= 1) {
-          for (int64_t t = pd.k3off[K] + tid; t < pd.koff[K + 1]; t += NT) {
-            const TermRegs tr = load_term(pd.terms, t);
-            term_third_group<R, K>(tr, pw, E1, wget, emit);
+          if (gather) {
+            for (int64_t t = pd.k3off[K] + tid; t < pd.koff[K + 1]; t += NT) {
+              const TermRegs tr = load_term(pd.terms, t);
+              term_third_gather_group<R, K>(tr, pw, E1, ix, wget, emit);
+            }
+          } else {
+            for (int64_t t = pd.k3off[K] + tid; t < pd.koff[K + 1]; t += NT) {
+              const TermRegs tr = load_term(pd.terms, t);
+              term_third_group<R, K>(tr, pw, E1, wget, emit);
+            }
           }
         }
       });

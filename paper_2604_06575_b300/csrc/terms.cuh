@@ -239,6 +239,71 @@ __device__ __forceinline__ void term_third_contract(const TermRegs& t, const R* 
   }
 }
 
+// Gather form of the same contraction, for points where the monomial value
+// m = c x^a and 1/x stay normal numbers.  With u_j = a_j / x_j,
+//   d_l d_j d_k m = m (a_j a_k - delta_jk a_j)(a_l - delta_lj - delta_lk) / (x_l x_j x_k),
+// and grouping the (j, k) of the support by how they meet l,
+//   c_l += m u_l [ 2 sum_{j<k; j,k != l} u_j u_k W_jk + sum_{j != l} u_j (u_j - 1/x_j) W_jj
+//                + 2 (a_l - 1) / x_l sum_{k != l} u_k W_lk + (a_l - 1)(a_l - 2) / x_l^2 W_ll ].
+// Every multiplier is non-negative, so no term cancels another the direct
+// contraction would not; the work is K(K+1)/2 lookups of W, O(K^2)
+// products and O(K^3) additions instead of a product per index multiset.
+// `ix` holds 1/x per variable; wget as above.
+template <typename R, int K, typename WGet, typename Emit>
+__device__ __forceinline__ void term_third_gather_k(const TermRegs& t, const R* __restrict__ pw, int E1,
+                                                   const R* __restrict__ ix, WGet&& wget, Emit&& emit) {
+  R m = R(t.coef), xi[K], uk[K], wd[K], gd[K], rs[K], pp[K][K];
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    const int v = t.var[q];
+    m *= pw[v * E1 + t.exp[q]];
+    xi[q] = ix[v];
+    uk[q] = R(t.exp[q]) * xi[q];
+    wd[q] = wget(q, q, v, v);
+    gd[q] = uk[q] * (uk[q] - xi[q]) * wd[q];
+    rs[q] = R(0);
+  }
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+#pragma unroll
+    for (int k = j + 1; k < K; ++k) {
+      const R w = wget(j, k, t.var[j], t.var[k]);
+      pp[j][k] = uk[j] * uk[k] * w;
+      rs[j] += uk[k] * w;
+      rs[k] += uk[j] * w;
+    }
+  }
+#pragma unroll
+  for (int l = 0; l < K; ++l) {
+    R pairs = R(0), diag = R(0);
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      if (j == l) continue;
+      diag += gd[j];
+#pragma unroll
+      for (int k = j + 1; k < K; ++k)
+        if (k != l) pairs += pp[j][k];
+    }
+    const R al = R(t.exp[l]);
+    const R bracket = R(2) * pairs + diag + R(2) * (al - R(1)) * xi[l] * rs[l] +
+                      (al - R(1)) * (al - R(2)) * xi[l] * xi[l] * wd[l];
+    emit(t.var[l], m * uk[l] * bracket);
+  }
+}
+
+template <typename R, int K, typename WGet, typename Emit>
+__device__ __noinline__ void term_third_gather_wide(const TermRegs& t, const R* __restrict__ pw, int E1,
+                                                    const R* __restrict__ ix, WGet wget, Emit emit) {
+  term_third_gather_k<R, K>(t, pw, E1, ix, wget, emit);
+}
+
+template <typename R, int K, typename WGet, typename Emit>
+__device__ __forceinline__ void term_third_gather_group(const TermRegs& t, const R* __restrict__ pw, int E1,
+                                                       const R* __restrict__ ix, WGet& wget, Emit& emit) {
+  if constexpr (K <= 6) term_third_gather_k<R, K>(t, pw, E1, ix, wget, emit);
+  else term_third_gather_wide<R, K>(t, pw, E1, ix, wget, emit);
+}
+
 // c x^a of one term at one point (any support size).
 template <typename R>
 __device__ __forceinline__ R term_value(const TermRegs& t, const R* __restrict__ pw, int E1) {

@@ -141,3 +141,26 @@ def test_fp32_form_error_bound(pl):
         ang = np.radians(affine.angle_deg(D[i], nu))
         worst = max(worst, ang / max(kap, 1.0))
         assert ang <= 2e-5 * max(kap, 1.0), (i, ang, kap)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_gather_and_term_by_term_sweeps_agree(pl, prec):
+    """Points with a zero or tiny coordinate take the term-by-term sweeps (no
+    division by x); the others take the gather forms of both term sweeps.
+    Both kinds, in one call, against the oracle."""
+    rng = np.random.default_rng(77)
+    n = 20
+    poly = workloads.convexified(rng, n, workloads.sparse_monomials(rng, n, 600, 6, 5), 0.1)
+    X = workloads.shell_points(rng, n, 24)
+    X[0:6, 3] = 0.0
+    X[6:12, 7] = 1e-7
+    D, Du, info = run(pl, poly, X, regularization=1e-6, prec=prec)
+    ref = oracle_all(poly, X, 1e-6, third="contract")
+    if prec == "fp64":
+        assert compare(poly, X, D, info, ref, 1e-6) == 0
+    else:
+        for i, (nu, oi) in enumerate(ref):
+            kap, amb = kappa_and_ambiguity(poly, X[i], 1e-6)
+            assert info["flags"][i] == oi["flags"]
+            if oi["flags"] == 0:
+                assert np.radians(affine.angle_deg(D[i], nu)) <= 2e-5 * max(kap, 1.0), i
