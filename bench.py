@@ -65,8 +65,8 @@ def parse():
     ap.add_argument("--forms", default="fp64,fp32", help="forms to time (profiling runs time one)")
     ap.add_argument("--rows-only", action="store_true", help="only the per-row measurements (profiling runs)")
     ap.add_argument("--config", default=None,
-                    help="threads,ctas_per_sm,order[,term_threads,chunks,terms_ctas,third_ctas,frame_split] instead of "
-                         "autotuning (profiling runs)")
+                    help="threads,ctas_per_sm,order[,term_threads,chunks,terms_ctas,third_ctas,frame_split,"
+                         "third_threads] in place of autotuning (profiling runs)")
     return ap.parse_args()
 
 

@@ -345,7 +345,8 @@ typedef struct polylab_batch polylab_batch;
  * the direction.  threads: frame-stage CTA size (64, 128 or 256 threads per
  * point); ctas_per_sm: cap on resident frame-stage CTAs per SM (0: the
  * occupancy limit); order: 1 = most expensive polynomials first, 0 = as
- * given; term_threads: CTA size of both term sweeps (64, 128 or 256). */
+ * given; term_threads: CTA size of the gradient/Hessian term sweep (64, 128
+ * or 256; third_threads, below, sizes the third-derivative sweep). */
 typedef struct {
   int32_t threads;
   int32_t ctas_per_sm;
@@ -367,6 +368,7 @@ typedef struct {
    * largest n and taken in an order of n descending; ctas_per_sm caps the
    * first class only.  0: one launch over all polynomials. */
   int32_t frame_split;
+  int32_t third_threads;  /* CTA size of the third-derivative sweep (64, 128 or 256) */
 } polylab_batch_config;
 
 polylab_status polylab_batch_create(int32_t n_polys, const polylab_poly* polys,
@@ -392,7 +394,8 @@ polylab_status polylab_batch_set_config(polylab_batch* batch, const polylab_batc
                                         polylab_stream stream);
 /* The project's autotuner, stage by stage on this batch (one warm-up and
  * `reps` timed runs per trial, CUDA events on `stream`, synchronising):
- * term_threads in {64,128,256} timed over the two term sweeps, then
+ * term_threads in {64,128,256} timed over the gradient/Hessian sweep and
+ * third_threads in {64,128,256} over the third-derivative sweep, then
  * frame_split in {1, 0} x threads in {64,128,256} x ctas_per_sm in
  * {occupancy, 2, 4} timed over the frame stage,
  * then order in {cost order, given order} timed over the whole run, all with

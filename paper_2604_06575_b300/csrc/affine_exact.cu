@@ -185,23 +185,33 @@ struct Bump {
 
 struct Lay1 {
   size_t pw, g, red, ix, gs, ga, mv, H, total;
+  size_t pw_step, ix_step, mv_step, H_step;  // offset between the two points' arrays
 };
+// Term sweep of up to kTermPoints points of one polynomial per CTA: power
+// tables, gather sums and monomial values (gather form) and H slots (in
+// shared memory) per point; the per-warp gradient replicas of the scatter
+// form are shared (points are swept one after another there).
 // `gather`: room for the gather form (1/x, gradient sums, one chunk of
 // monomial values)
+constexpr int kTermPoints = 2;
 template <typename R, int NW>
 __host__ __device__ Lay1 lay_terms(int n, int E1, bool in_smem, bool gather) {
   Lay1 L{};
   Bump b;
-  L.pw = b.take((size_t)n * E1 * sizeof(R));
+  L.pw_step = ((size_t)n * E1 * sizeof(R) + 15) & ~size_t(15);
+  L.pw = b.take(kTermPoints * L.pw_step);
   L.g = b.take((size_t)NW * n * sizeof(R));  // one replica per warp
-  L.red = b.take(40 * 8);
+  L.red = b.take(kTermPoints * 40 * 8);
   if (gather) {
-    L.ix = b.take(n * sizeof(R));
-    L.gs = b.take(n * sizeof(R));
-    L.ga = b.take(n * sizeof(R));
-    L.mv = b.take((size_t)kGatherChunk * sizeof(R));
+    L.ix_step = ((size_t)n * sizeof(R) + 15) & ~size_t(15);
+    L.ix = b.take(kTermPoints * L.ix_step);
+    L.gs = b.take(kTermPoints * L.ix_step);
+    L.ga = b.take(kTermPoints * L.ix_step);
+    L.mv_step = (size_t)kGatherChunk * sizeof(R);
+    L.mv = b.take(kTermPoints * L.mv_step);
   }
-  L.H = in_smem ? b.take((size_t)mat_slot<R>(n) * sizeof(R)) : 0;
+  L.H_step = (size_t)mat_slot<R>(n) * sizeof(R);
+  L.H = in_smem ? b.take(kTermPoints * L.H_step) : 0;
   L.total = b.o;
   return L;
 }
@@ -307,6 +317,11 @@ __device__ __forceinline__ void write_failed(const ExactDesc& pd, int64_t p, int
 //          are scaled by 1/x_i (1/x_j) at the end;
 //  scatter (otherwise): every term's derivative values are added to their
 //          entries one by one (per-warp gradient replicas).
+// A CTA takes two consecutive work items at a time; when both are points of
+// the same polynomial and the gather form holds at both, one pass over the
+// terms and records serves the two points (each record is decoded once and
+// applied to both points' monomial values).  Otherwise the points are swept
+// one after another (a pair that straddles two polynomials in two passes).
 template <typename R, int NT>
 __global__ void __launch_bounds__(NT) exact_terms_kernel(StageArgs<R> a) {
   extern __shared__ __align__(16) unsigned char sm[];
@@ -314,132 +329,187 @@ __global__ void __launch_bounds__(NT) exact_terms_kernel(StageArgs<R> a) {
   constexpr int NW = NT / 32;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   while (true) {
-    const int64_t item = a.item_begin + next_item(a.counter, &s_item);
-    if (item >= a.item_end) break;
-    const int lo = find_poly(a.prefix, a.n_desc, item);
-    const ExactDesc& pd = a.descs[a.order[lo]];
-    const int64_t p = item - a.prefix[lo];
-    const int n = pd.n, nn = n * n, E1 = pd.E + 1;
-    const Lay1 L = lay_terms<R, NW>(n, E1, pd.h_in_smem, pd.gather != nullptr);
-    R* pw = (R*)(sm + L.pw);
-    R* g = (R*)(sm + L.g);
-    double* red = (double*)(sm + L.red);
-    R* Hg = a.mats_h + pd.mat_off + p * mat_slot<R>(n);
-    R* Hr = pd.h_in_smem ? (R*)(sm + L.H) : Hg;
-    const double* X = pd.X + p * n;
-    bool in_range = true;
-    for (int i = tid; i < n; i += NT) {
-      const double ax = fabs(X[i]);
-      in_range &= ax >= pd.x_lo && ax <= pd.x_hi;
-    }
-    const bool gather = __syncthreads_and(in_range && pd.gather != nullptr) != 0;
-    R* ix = (R*)(sm + L.ix);
-    R* gs = (R*)(sm + L.gs);
-    R* ga = (R*)(sm + L.ga);
-    R* mv = (R*)(sm + L.mv);
-    if (gather) {
-      for (int i = tid; i < n; i += NT) {
-        ix[i] = R(1) / R(X[i]);
-        gs[i] = R(0);
-        ga[i] = R(0);
+    const int64_t pair = a.item_begin + (int64_t)kTermPoints * next_item(a.counter, &s_item);
+    if (pair >= a.item_end) break;
+    const int64_t pair_end = min(pair + kTermPoints, a.item_end);
+    int np = 0;
+    for (int64_t item = pair; item < pair_end; item += np) {
+      const int lo = find_poly(a.prefix, a.n_desc, item);
+      const ExactDesc& pd = a.descs[a.order[lo]];
+      const int64_t p0 = item - a.prefix[lo];
+      // the points of this pass: the rest of the pair within this polynomial
+      np = (int)min(pair_end - item, pd.P - p0);
+      const int n = pd.n, nn = n * n, E1 = pd.E + 1;
+      const Lay1 L = lay_terms<R, NW>(n, E1, pd.h_in_smem, pd.gather != nullptr);
+      auto pw_of = [&](int q) { return (R*)(sm + L.pw + q * L.pw_step); };
+      auto ix_of = [&](int q) { return (R*)(sm + L.ix + q * L.ix_step); };
+      auto gs_of = [&](int q) { return (R*)(sm + L.gs + q * L.ix_step); };
+      auto ga_of = [&](int q) { return (R*)(sm + L.ga + q * L.ix_step); };
+      auto mv_of = [&](int q) { return (R*)(sm + L.mv + q * L.mv_step); };
+      auto Hg_of = [&](int q) { return a.mats_h + pd.mat_off + (p0 + q) * mat_slot<R>(n); };
+      auto Hr_of = [&](int q) { return pd.h_in_smem ? (R*)(sm + L.H + q * L.H_step) : Hg_of(q); };
+      auto rec_of = [&](int q) { return a.vecs + pd.vec_off + (p0 + q) * vrec(n); };
+      R* g = (R*)(sm + L.g);
+      double* red = (double*)(sm + L.red);
+      bool in_range = true;
+      for (int i = tid; i < np * n; i += NT) {
+        const double ax = fabs(pd.X[p0 * n + i]);
+        in_range &= ax >= pd.x_lo && ax <= pd.x_hi;
       }
-    } else {
-      for (int i = tid; i < NW * n; i += NT) g[i] = R(0);
-    }
-    power_table<R, NT>(X, n, E1, pw);
-    for (int64_t i = tid; i < mat_slot<R>(n); i += NT) Hr[i] = R(0);
-    __syncthreads();
-    double* rec = a.vecs + pd.vec_off + p * vrec(n);
-    R gabs = R(0);  // this thread's share of sum |gradient contributions|
-    if (gather) {
-      auto flush = [&](int e, R acc, R aacc) {
-        if (e < 0 || e == (int)kGatherPad) return;  // nothing yet, or padding
-        if (e >= nn) {
-          atomicAdd(&gs[e - nn], acc);
-          atomicAdd(&ga[e - nn], aacc);
-        } else {
-          atomicAdd(&Hr[e], acc);
-        }
-      };
-      for (int c = 0; c < pd.n_gchunks; ++c) {
-        const int64_t t0 = (int64_t)c * kGatherChunk, t1 = min(pd.m, t0 + kGatherChunk);
-        for (int64_t t = t0 + tid; t < t1; t += NT) mv[t - t0] = term_value<R>(load_term(pd.terms, t), pw, E1);
-        __syncthreads();
-        const int64_t r0 = pd.gather_chunk[c];
-        const int Lc = (int)((pd.gather_chunk[c + 1] - r0) / kGatherStreams);
-        const uint32_t* recs = pd.gather + r0;
-        for (int st = tid; st < kGatherStreams; st += NT) {
-          int cur = -1;
-          R acc = R(0), aacc = R(0);
-          for (int k = 0; k < Lc; k += kGatherUnroll) {
-            uint32_t rr[kGatherUnroll];
-#pragma unroll
-            for (int u = 0; u < kGatherUnroll; ++u) rr[u] = __ldg(recs + (int64_t)(k + u) * kGatherStreams + st);
-#pragma unroll
-            for (int u = 0; u < kGatherUnroll; ++u) {
-              const int e = (int)((rr[u] >> 11) & 0x3fffu);
-              const R v = R(rr[u] >> 25) * mv[rr[u] & 0x7ffu];
-              if (e != cur) {
-                flush(cur, acc, aacc);
-                cur = e;
-                acc = R(0);
-                aacc = R(0);
-              }
-              acc += v;
-              aacc += fabs(v);
-            }
+      const bool gather = __syncthreads_and(in_range && pd.gather != nullptr) != 0;
+      for (int q = 0; q < np; ++q) {
+        const double* X = pd.X + (p0 + q) * n;
+        if (gather) {
+          for (int i = tid; i < n; i += NT) {
+            ix_of(q)[i] = R(1) / R(X[i]);
+            gs_of(q)[i] = R(0);
+            ga_of(q)[i] = R(0);
           }
-          flush(cur, acc, aacc);
         }
-        __syncthreads();
+        power_table<R, NT>(X, n, E1, pw_of(q));
+        R* Hr = Hr_of(q);
+        for (int64_t i = tid; i < mat_slot<R>(n); i += NT) Hr[i] = R(0);
       }
-      for (int i = wid; i < n; i += NW)
-        for (int j = i + lane; j < n; j += 32) Hr[i * n + j] *= ix[i] * ix[j];
-      for (int i = tid; i < n; i += NT) {
-        rec[i] = (double)(gs[i] * ix[i]);
-        gabs += ga[i] * fabs(ix[i]);
-      }
-    } else {
-      R* gw = g + wid * n;
-      auto emit = [&](int kind, int i, int j, R val) {
-        if (kind == 1) {
-          atomicAdd(&gw[i], val);
-          gabs += fabs(val);
-        } else if (kind == 2) {
-          atomicAdd(&Hr[i * n + j], val);
-        }
-      };
-      // one loop per support-size group: inside each loop the support size
-      // is a compile-time constant and the warp never branches on it
-      for_support<kMaxSupport>([&](auto kc) {
-        constexpr int K = decltype(kc)::value;
-        for (int64_t t = pd.koff[K] + tid; t < pd.koff[K + 1]; t += NT) {
-          const TermRegs tr = load_term(pd.terms, t);
-          term_derivs_group<R, 2, K>(tr, pw, E1, emit);
-        }
-      });
       __syncthreads();
-      for (int i = tid; i < n; i += NT) {
-        R s = g[i];
-        for (int q = 1; q < NW; ++q) s += g[q * n + i];
-        rec[i] = (double)s;
+      R gabs[kTermPoints] = {};  // this thread's share of sum |gradient contributions|, per point
+      if (gather) {
+        // one pass over terms and records for NP points
+        auto sweep = [&](auto np_c) {
+          constexpr int NP = decltype(np_c)::value;
+          R* Hr[NP];
+          R* gs[NP];
+          R* ga[NP];
+          const R* mv[NP];
+  #pragma unroll
+          for (int q = 0; q < NP; ++q) {
+            Hr[q] = Hr_of(q);
+            gs[q] = gs_of(q);
+            ga[q] = ga_of(q);
+            mv[q] = mv_of(q);
+          }
+          auto flush = [&](int e, const R* acc, const R* aacc) {
+            if (e < 0 || e == (int)kGatherPad) return;  // nothing yet, or padding
+  #pragma unroll
+            for (int q = 0; q < NP; ++q) {
+              if (e >= nn) {
+                atomicAdd(&gs[q][e - nn], acc[q]);
+                atomicAdd(&ga[q][e - nn], aacc[q]);
+              } else {
+                atomicAdd(&Hr[q][e], acc[q]);
+              }
+            }
+          };
+          for (int c = 0; c < pd.n_gchunks; ++c) {
+            const int64_t t0 = (int64_t)c * kGatherChunk, t1 = min(pd.m, t0 + kGatherChunk);
+            for (int64_t t = t0 + tid; t < t1; t += NT) {
+              const TermRegs tr = load_term(pd.terms, t);
+  #pragma unroll
+              for (int q = 0; q < NP; ++q) mv_of(q)[t - t0] = term_value<R>(tr, pw_of(q), E1);
+            }
+            __syncthreads();
+            const int64_t r0 = pd.gather_chunk[c];
+            const int Lc = (int)((pd.gather_chunk[c + 1] - r0) / kGatherStreams);
+            const uint32_t* recs = pd.gather + r0;
+            for (int st = tid; st < kGatherStreams; st += NT) {
+              int cur = -1;
+              R acc[NP] = {}, aacc[NP] = {};
+              for (int k = 0; k < Lc; k += kGatherUnroll) {
+                uint32_t rr[kGatherUnroll];
+  #pragma unroll
+                for (int u = 0; u < kGatherUnroll; ++u) rr[u] = __ldg(recs + (int64_t)(k + u) * kGatherStreams + st);
+  #pragma unroll
+                for (int u = 0; u < kGatherUnroll; ++u) {
+                  const int e = (int)((rr[u] >> 11) & 0x3fffu);
+                  const R cf = R(rr[u] >> 25);
+                  const int tt = (int)(rr[u] & 0x7ffu);
+                  if (e != cur) {
+                    flush(cur, acc, aacc);
+                    cur = e;
+  #pragma unroll
+                    for (int q = 0; q < NP; ++q) acc[q] = aacc[q] = R(0);
+                  }
+  #pragma unroll
+                  for (int q = 0; q < NP; ++q) {
+                    const R v = cf * mv[q][tt];
+                    acc[q] += v;
+                    aacc[q] += fabs(v);
+                  }
+                }
+              }
+              flush(cur, acc, aacc);
+            }
+            __syncthreads();
+          }
+        };
+        if (np == 2) sweep(std::integral_constant<int, 2>{});
+        else sweep(std::integral_constant<int, 1>{});
+        for (int q = 0; q < np; ++q) {
+          R* Hr = Hr_of(q);
+          const R* ix = ix_of(q);
+          for (int i = wid; i < n; i += NW)
+            for (int j = i + lane; j < n; j += 32) Hr[i * n + j] *= ix[i] * ix[j];
+          double* rec = rec_of(q);
+          for (int i = tid; i < n; i += NT) {
+            rec[i] = (double)(gs_of(q)[i] * ix[i]);
+            gabs[q] += ga_of(q)[i] * fabs(ix[i]);
+          }
+        }
+      } else {
+        for (int q = 0; q < np; ++q) {
+          for (int i = tid; i < NW * n; i += NT) g[i] = R(0);
+          __syncthreads();
+          R* gw = g + wid * n;
+          R* Hr = Hr_of(q);
+          const R* pw = pw_of(q);
+          R ga = R(0);
+          auto emit = [&](int kind, int i, int j, R val) {
+            if (kind == 1) {
+              atomicAdd(&gw[i], val);
+              ga += fabs(val);
+            } else if (kind == 2) {
+              atomicAdd(&Hr[i * n + j], val);
+            }
+          };
+          // one loop per support-size group: inside each loop the support size
+          // is a compile-time constant and the warp never branches on it
+          for_support<kMaxSupport>([&](auto kc) {
+            constexpr int K = decltype(kc)::value;
+            for (int64_t t = pd.koff[K] + tid; t < pd.koff[K + 1]; t += NT) {
+              const TermRegs tr = load_term(pd.terms, t);
+              term_derivs_group<R, 2, K>(tr, pw, E1, emit);
+            }
+          });
+          __syncthreads();
+          double* rec = rec_of(q);
+          for (int i = tid; i < n; i += NT) {
+            R sum = g[i];
+            for (int w = 1; w < NW; ++w) sum += g[w * n + i];
+            rec[i] = (double)sum;
+          }
+          gabs[q] = ga;
+          __syncthreads();
+        }
       }
-    }
-    gabs = warp_sum(gabs);
-    if (lane == 0) red[wid] = (double)gabs;
-    __syncthreads();
-    if (tid == 0) {
-      double gsum = 0.0;
-      for (int q = 0; q < NW; ++q) gsum += red[q];
-      rec[4 * n] = gsum;
-    }
-    // the upper triangle the sweep filled (zeros below) to the workspace by
-    // one bulk copy; its shared-memory source is read before the next item
-    if (pd.h_in_smem && tid == 0) {
-      fence_proxy_async_smem();
-      bulk_s2g(Hg, Hr, (uint32_t)(mat_slot<R>(n) * sizeof(R)));
-      bulk_commit();
-      bulk_wait_read();
+      for (int q = 0; q < np; ++q) {
+        const R gq = warp_sum(gabs[q]);
+        if (lane == 0) red[q * 40 + wid] = (double)gq;
+      }
+      __syncthreads();
+      if (tid < np) {
+        double gsum = 0.0;
+        for (int w = 0; w < NW; ++w) gsum += red[tid * 40 + w];
+        rec_of(tid)[4 * n] = gsum;
+      }
+      // the upper triangles the sweep filled (zeros below) to the workspace by
+      // one bulk copy each; their shared-memory sources are read before the
+      // next pair
+      if (pd.h_in_smem && tid == 0) {
+        fence_proxy_async_smem();
+        for (int q = 0; q < np; ++q) bulk_s2g(Hg_of(q), Hr_of(q), (uint32_t)(mat_slot<R>(n) * sizeof(R)));
+        bulk_commit();
+        bulk_wait_read();
+      }
+      __syncthreads();  // (the next pass reuses the shared arrays)
     }
   }
   if (tid == 0) bulk_wait_all();
@@ -888,14 +958,14 @@ static polylab_status prepare_exact(ExactBatch* b) {
   for (size_t di = 0; di < b->host_descs.size(); ++di) {
     ExactDesc& d = b->host_descs[di];
     const int E1 = d.E + 1;
-    const int tt = b->cfg.term_threads, ft = b->cfg.threads;
+    const int tt = b->cfg.term_threads, ft = b->cfg.threads, t3 = b->cfg.third_threads;
     const bool gat = d.gather != nullptr;
     d.h_in_smem = stage_bytes<R>(0, tt, d.n, E1, true, gat) <= kSmemCap ? 1 : 0;
     d.mats_in_smem = stage_bytes<R>(1, ft, d.n, E1, true, false) <= kSmemCap ? 1 : 0;
-    d.w_in_smem = stage_bytes<R>(2, tt, d.n, E1, true, false) <= kSmemCap ? 1 : 0;
+    d.w_in_smem = stage_bytes<R>(2, t3, d.n, E1, true, false) <= kSmemCap ? 1 : 0;
     const size_t need[3] = {stage_bytes<R>(0, tt, d.n, E1, d.h_in_smem, gat),
                             stage_bytes<R>(1, ft, d.n, E1, d.mats_in_smem, false),
-                            stage_bytes<R>(2, tt, d.n, E1, d.w_in_smem, false)};
+                            stage_bytes<R>(2, t3, d.n, E1, d.w_in_smem, false)};
     for (int st = 0; st < 3; ++st) {
       if (need[st] > kSmemCap) return POLYLAB_ERR_UNSUPPORTED;
       smem[st] = std::max(smem[st], need[st]);
@@ -1001,7 +1071,7 @@ static polylab_status launch_frame_classes(ExactBatch* b, cudaStream_t s) {
 
 template <typename R>
 static polylab_status launch_stage(ExactBatch* b, int stage, int chunk, cudaStream_t s) {
-  const int nt = stage == 1 ? b->cfg.threads : b->cfg.term_threads;
+  const int nt = stage == 0 ? b->cfg.term_threads : stage == 1 ? b->cfg.threads : b->cfg.third_threads;
   if (nt == 64) return launch_stage_t<R, 64>(b, stage, chunk, s);
   if (nt == 128) return launch_stage_t<R, 128>(b, stage, chunk, s);
   return launch_stage_t<R, 256>(b, stage, chunk, s);

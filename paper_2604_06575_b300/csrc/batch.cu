@@ -136,6 +136,7 @@ polylab_status exact_batch_init(ExactBatch* b, int n, const polylab_plan* const*
   }
   if (b->cfg.threads == 0) b->cfg.threads = default_threads(b);
   if (b->cfg.term_threads == 0) b->cfg.term_threads = 128;
+  if (b->cfg.third_threads == 0) b->cfg.third_threads = 128;
   PL_TRY(prepare_exact_batch(b));
   PL_CUDA(cudaMallocAsync(&b->descs, std::max(n, 1) * sizeof(ExactDesc), s));
   PL_CUDA(cudaMallocAsync(&b->order, std::max(n, 1) * sizeof(int), s));
@@ -293,13 +294,15 @@ polylab_status polylab_batch_get_config(const polylab_batch* b, polylab_batch_co
   cfg->terms_ctas = b->b.cfg.terms_ctas;
   cfg->third_ctas = b->b.cfg.third_ctas;
   cfg->frame_split = b->b.cfg.frame_split;
+  cfg->third_threads = b->b.cfg.third_threads;
   return POLYLAB_OK;
 }
 
 polylab_status polylab_batch_set_config(polylab_batch* b, const polylab_batch_config* cfg, polylab_stream stream) {
   if (!b || !cfg) return POLYLAB_ERR_INVALID_ARG;
   auto ok_threads = [](int t) { return t == 64 || t == 128 || t == 256; };
-  if (!ok_threads(cfg->threads) || !ok_threads(cfg->term_threads)) return POLYLAB_ERR_INVALID_ARG;
+  if (!ok_threads(cfg->threads) || !ok_threads(cfg->term_threads) || !ok_threads(cfg->third_threads))
+    return POLYLAB_ERR_INVALID_ARG;
   auto ok_cap = [](int c) { return c >= 0 && c <= 32; };
   if (!ok_cap(cfg->ctas_per_sm) || !ok_cap(cfg->terms_ctas) || !ok_cap(cfg->third_ctas) ||
       (cfg->order != 0 && cfg->order != 1) || cfg->chunks < 1 || cfg->chunks > kMaxChunks ||
@@ -312,7 +315,9 @@ polylab_status polylab_batch_set_config(polylab_batch* b, const polylab_batch_co
   b->b.cfg.terms_ctas = cfg->terms_ctas;
   b->b.cfg.third_ctas = cfg->third_ctas;
   b->b.cfg.frame_split = cfg->frame_split;
-  const bool relayout = cfg->threads != b->b.cfg.threads || cfg->term_threads != b->b.cfg.term_threads;
+  const bool relayout = cfg->threads != b->b.cfg.threads || cfg->term_threads != b->b.cfg.term_threads ||
+                        cfg->third_threads != b->b.cfg.third_threads;
+  b->b.cfg.third_threads = cfg->third_threads;
   b->b.cfg.threads = cfg->threads;
   b->b.cfg.term_threads = cfg->term_threads;
   b->b.cfg.ctas_per_sm = cfg->ctas_per_sm;
@@ -329,7 +334,8 @@ polylab_status polylab_batch_autotune(polylab_batch* b, int32_t reps, polylab_st
   cudaStream_t s = (cudaStream_t)stream;
   ExactBatch* eb = &b->b;
   polylab_batch_config cur{eb->cfg.threads, eb->cfg.ctas_per_sm, eb->cfg.order,      eb->cfg.term_threads,
-                           eb->cfg.chunks,  eb->cfg.terms_ctas,  eb->cfg.third_ctas, eb->cfg.frame_split};
+                           eb->cfg.chunks,  eb->cfg.terms_ctas,  eb->cfg.third_ctas, eb->cfg.frame_split,
+                           eb->cfg.third_threads};
   cur.chunks = 1;  // the stages one after another
   cur.terms_ctas = 0;
   cur.third_ctas = 0;
@@ -365,17 +371,16 @@ polylab_status polylab_batch_autotune(polylab_batch* b, int32_t reps, polylab_st
   polylab_status st = polylab_batch_set_config(b, &cur, stream);
   if (st == POLYLAB_OK) st = run_exact_batch(eb, s);  // every stage's inputs exist from here on
   float best_t = 1e30f, t = 0.f;
-  // 1. CTA size of the two term sweeps
-  if (st == POLYLAB_OK) {
+  // 1. CTA sizes of the two term sweeps, each timed over its own stage
+  for (int sweep = 0; sweep < 2 && st == POLYLAB_OK; ++sweep) {
     polylab_batch_config best = cur;
+    best_t = 1e30f;
     for (int tt : {64, 128, 256}) {
       polylab_batch_config c = cur;
-      c.term_threads = tt;
-      if ((st = trial(c, 0, 0, &t)) != POLYLAB_OK) break;
-      float t3 = 0.f;
-      if ((st = time_stages(2, 2, &t3)) != POLYLAB_OK) break;
-      if (t + t3 < best_t) {
-        best_t = t + t3;
+      (sweep == 0 ? c.term_threads : c.third_threads) = tt;
+      if ((st = trial(c, 2 * sweep, 2 * sweep, &t)) != POLYLAB_OK) break;
+      if (t < best_t) {
+        best_t = t;
         best = c;
       }
     }

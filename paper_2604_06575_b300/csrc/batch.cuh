@@ -37,12 +37,13 @@ struct ExactConfig {
   int threads = 0;        // frame-stage CTA size: 64, 128 or 256 (0: by largest n)
   int ctas_per_sm = 0;    // cap on resident frame-stage CTAs per SM (0: occupancy limit)
   int order = 1;          // 1: most expensive polynomials first, 0: as given
-  int term_threads = 0;   // CTA size of the two term sweeps (0: 128)
+  int term_threads = 0;   // CTA size of the gradient/Hessian term sweep (0: 128)
   int chunks = 1;         // work split into this many chunks of equal estimated cost, pipelined
                           // over three streams (1: the stages run one after another)
   int terms_ctas = 0;     // caps on resident CTAs per SM of the term sweeps (0: occupancy limit)
   int third_ctas = 0;
   int frame_split = 1;    // sequential runs: frame stage in classes of polynomials by n
+  int third_threads = 0;  // CTA size of the third-derivative sweep (0: 128)
 };
 
 // A class of the split frame stage: polynomials with n in (n_lo, n_hi], a

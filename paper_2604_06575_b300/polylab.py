@@ -56,7 +56,7 @@ class _AnOpts(C.Structure):
 class _BatchConfig(C.Structure):
     _fields_ = [("threads", C.c_int32), ("ctas_per_sm", C.c_int32), ("order", C.c_int32),
                 ("term_threads", C.c_int32), ("chunks", C.c_int32), ("terms_ctas", C.c_int32),
-                ("third_ctas", C.c_int32), ("frame_split", C.c_int32)]
+                ("third_ctas", C.c_int32), ("frame_split", C.c_int32), ("third_threads", C.c_int32)]
 
 
 INFO_DTYPE = np.dtype([("grad_norm", "<f8"), ("logdet", "<f8"), ("flags", "<i4"), ("hv_evals", "<i4"),
@@ -446,7 +446,7 @@ class Batch:
         _check("polylab_batch_run_stage", _lib.polylab_batch_run_stage(self.h, stage, _stream()))
 
     CONFIG_KEYS = ("threads", "ctas_per_sm", "order", "term_threads", "chunks", "terms_ctas", "third_ctas",
-                   "frame_split")
+                   "frame_split", "third_threads")
 
     def config(self):
         c = _BatchConfig()
@@ -454,11 +454,12 @@ class Batch:
         return {k: getattr(c, k) for k in self.CONFIG_KEYS}
 
     def set_config(self, threads, ctas_per_sm, order, term_threads=None, chunks=None, terms_ctas=None,
-                   third_ctas=None, frame_split=None):
+                   third_ctas=None, frame_split=None, third_threads=None):
         """Keys left as None keep their current value."""
         cur = self.config()
         given = dict(threads=threads, ctas_per_sm=ctas_per_sm, order=order, term_threads=term_threads,
-                     chunks=chunks, terms_ctas=terms_ctas, third_ctas=third_ctas, frame_split=frame_split)
+                     chunks=chunks, terms_ctas=terms_ctas, third_ctas=third_ctas, frame_split=frame_split,
+                     third_threads=third_threads)
         c = _BatchConfig(*[cur[k] if given[k] is None else given[k] for k in self.CONFIG_KEYS])
         _check("polylab_batch_set_config", _lib.polylab_batch_set_config(self.h, C.byref(c), _stream()))
 
