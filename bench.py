@@ -298,7 +298,7 @@ def main():
             dist.barrier()
 
     def capture(batch):
-        """One run (three memsets of the work counters + three persistent launches) in a CUDA graph."""
+        """One run (the work-counter memsets and the persistent launches of the three stages) in a CUDA graph."""
         g = torch.cuda.CUDAGraph()
         side = torch.cuda.Stream()
         side.wait_stream(torch.cuda.current_stream())
@@ -433,12 +433,15 @@ def main():
                             peak=r["peak"], frac=r["frac"])
     dom = max(STAGES, key=lambda k: stage_ms[k])
     roof = alu_roofline(flops, stage_ms[dom] * 1e-3, chosen, p32, p64, STAGE_PARTS[dom])
-    roof["kernel"] = f"{kernels[dom]} (the longest of the three launches of a step)"
+    roof["kernel"] = f"{kernels[dom]} (the longest of the three stages of a step)"
     tr = profiled_traffic(kernels[dom], npts) if chosen == "fp32" else None
     roof["traffic"] = tr["bytes"] if tr else None
     roof["traffic_note"] = (f"dram read+write per launch from {tr['captured']} ({tr['captured_units']} points), "
                             f"scaled to {npts} points" if tr else "no ncu counters for this kernel at this source")
-    roof["launches_per_step"] = 1
+    launches = stage_launches(tuned[chosen], polys, Xs)
+    roof["launches_per_step"] = launches[dom]
+    roof["note"] = ("achieved = the stage's algorithmic flops / the stage's event-timed duration (all of its "
+                    "launches in a step: the frame stage runs one launch per class of n)")
     roof["stages"] = stages
     roof["path"] = alu_roofline(flops, statistics.median(res[chosen]["step_ms"]) * 1e-3, chosen, p32, p64)
 
@@ -459,7 +462,7 @@ def main():
                            speedup_vs_fp64=round(rate(chosen) / rate("fp64"), 3)),
                 e2e=dict(value=round(e2e_rate, 1), unit="dirs/s", h2d_bytes_per_step=nbytes,
                          d2h_bytes_per_step=nbytes),
-                gpu_launches=3 * args.steps,
+                gpu_launches=sum(launches.values()) * args.steps,
                 autotune=tuned,
                 roofline=roof, clocks=clk)
 
@@ -480,6 +483,22 @@ def main():
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def stage_launches(cfg: dict, polys, Xs) -> dict:
+    """Kernel launches of one run per stage: with chunks = 1 one launch per
+    term sweep and, with frame_split, one frame launch per non-empty class
+    of n (n > 40, 24 < n <= 40, n <= 24); pipelined runs launch every stage
+    once per non-empty chunk (counted as `chunks`)."""
+    if cfg.get("chunks", 1) > 1:
+        c = cfg["chunks"]
+        return dict(terms=c, frame=c, third=c)
+    ns = [p.n for p, X in zip(polys, Xs) if X.shape[0] > 0]
+    if cfg.get("frame_split", 0):
+        frame = sum(1 for lo, hi in ((40, 1 << 30), (24, 40), (0, 24)) if any(lo < n <= hi for n in ns))
+    else:
+        frame = 1
+    return dict(terms=1, frame=frame, third=1)
 
 
 def measure_rows(pl, workloads, torch, dev, p32, p64):
