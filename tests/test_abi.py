@@ -44,3 +44,19 @@ def test_default_options_match_paper_table():
     o = polylab._AnOpts()
     polylab.lib().polylab_an_opts_default(ctypes.byref(o))
     assert (o.method, o.regularization, o.num_probes, o.krylov_tol, o.krylov_maxit) == (0, 1e-6, 8, 1e-4, 40)
+
+
+def test_bench_counts_launches_per_step():
+    """The bench's claim of kernel launches per step follows the configuration:
+    the frame stage runs one launch per non-empty class of n when split."""
+    import numpy as np
+
+    import bench
+    from paper_2604_06575_b300 import workloads
+    rng = np.random.default_rng(0)
+    polys = [workloads.convexified(rng, n, workloads.sparse_monomials(rng, n, 20, 3, 2), 0.1) for n in (5, 30, 50)]
+    Xs = [np.zeros((4, p.n)) for p in polys]
+    assert bench.stage_launches(dict(chunks=1, frame_split=1), polys, Xs) == dict(terms=1, frame=3, third=1)
+    assert bench.stage_launches(dict(chunks=1, frame_split=1), polys[:1], Xs[:1]) == dict(terms=1, frame=1, third=1)
+    assert bench.stage_launches(dict(chunks=1, frame_split=0), polys, Xs) == dict(terms=1, frame=1, third=1)
+    assert bench.stage_launches(dict(chunks=4, frame_split=1), polys, Xs) == dict(terms=4, frame=4, third=4)

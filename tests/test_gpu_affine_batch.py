@@ -77,12 +77,15 @@ def test_autotune_configs_agree_and_graph_replay(pl, batch_inputs):
     torch.cuda.synchronize()
     ref = [d.clone() for d in b.D]
     for threads in (64, 128, 256):
-        for cap, order in ((0, 1), (2, 0)):
-            b.set_config(threads, cap, order)
+        for cap, order, split, t3 in ((0, 1, 1, 128), (2, 0, 0, 64), (0, 1, 0, 256)):
+            # frame stage split by n or one launch; CTA size of the third sweep
+            b.set_config(threads, cap, order, frame_split=split, third_threads=t3)
             b.run()
-            torch.cuda.synchronize()
+            b.check()
             for d, r in zip(b.D, ref):
                 close(d, r, TOL["fp64"])
+    with pytest.raises(pl.PolylabError):
+        b.set_config(128, 0, 1, third_threads=96)  # not a supported CTA size
     # pipelined over three streams: chunks of the work order, per-stage caps
     for chunks, caps in ((4, (2, 3, 2)), (7, (1, 1, 1)), (32, (0, 0, 0))):
         b.set_config(128, caps[1], 1, term_threads=64, chunks=chunks, terms_ctas=caps[0], third_ctas=caps[2])
@@ -90,7 +93,7 @@ def test_autotune_configs_agree_and_graph_replay(pl, batch_inputs):
         b.check()
         for d, r in zip(b.D, ref):
             close(d, r, TOL["fp64"])
-    b.set_config(128, 0, 1, term_threads=128, chunks=1, terms_ctas=0, third_ctas=0)
+    b.set_config(128, 0, 1, term_threads=128, chunks=1, terms_ctas=0, third_ctas=0, frame_split=1, third_threads=128)
     cfg, ms = b.autotune(reps=1)
     assert cfg["threads"] in (64, 128, 256) and ms > 0
     assert b.config() == cfg
