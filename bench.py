@@ -124,19 +124,40 @@ def alu_roofline(flops: dict, t_s: float, form: str, p32: float, p64: float, par
 EXACT_SOURCES = ("affine_exact.cu", "terms.cuh", "async.cuh", "batch.cuh", "common.cuh")
 
 
+def code_text(src: bytes) -> bytes:
+    """Source text with `//` comments, trailing blanks and empty lines removed:
+    what the counters of a capture depend on (a comment edit keeps them)."""
+    out = []
+    for line in src.decode().splitlines():
+        code = line.split("//", 1)[0].rstrip()
+        if code:
+            out.append(code)
+    return "\n".join(out).encode()
+
+
+def source_hash(read) -> str:
+    """SHA-256 prefix over the code text of the exact-path sources; `read(f)`
+    returns the bytes of source file f."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in EXACT_SOURCES:
+        h.update(code_text(read(f)))
+    return h.hexdigest()[:16]
+
+
 def profiled_traffic(kernel: str, units: int):
     """DRAM bytes (read + write) per launch of `kernel` from a committed ncu
     summary under profiles/ (a line `traffic: kernel=K bytes=B units=U
     source=S`), scaled from the captured U units to `units`; None unless the
-    exact-path sources still hash to S (the counters describe this code)."""
+    exact-path sources' code text still hashes to S (the counters describe
+    this code)."""
     import glob
-    import hashlib
     import re
-    h = hashlib.sha256()
-    for f in EXACT_SOURCES:
+
+    def read(f):
         with open(os.path.join(ROOT, "paper_2604_06575_b300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
-    src = h.hexdigest()[:16]
+            return fh.read()
+    src = source_hash(read)
     pat = re.compile(r"^traffic: kernel=(\S+) bytes=(\d+) units=(\d+) source=(\w+)\s*$")
     for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
         with open(path) as fh:

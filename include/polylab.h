@@ -319,27 +319,29 @@ polylab_status polylab_mlp_adam(float* params, const float* grad, float* m, floa
 /* BF16 copy of the parameters for inference (DEVICE, 291 x 2 bytes). */
 polylab_status polylab_mlp_pack(const float* params, void* packed, polylab_stream stream);
 
-/* ------------------------------------------- batched exact directions (one launch) */
+/* ------------------------------------------- batched exact directions (one graph) */
 
 /* A batch is a set of polynomials (each with its own n, term list and point
- * set) whose exact affine-normal directions are computed by three persistent
- * kernel launches over all of them (the stages of polylab_batch_config):
- * (polynomial, point) work items are taken from a device counter per stage,
- * most expensive polynomials first, so an uneven batch keeps every SM busy.
+ * set) whose exact affine-normal directions are computed by three stages of
+ * persistent kernel launches over all of them (polylab_batch_config; the
+ * frame stage may run as one launch per class of n): (polynomial, point)
+ * work items are taken from a device counter per launch, most expensive
+ * polynomials first, so an uneven batch keeps every SM busy.
  * The stages pass each point's H, W (n x n in the form's precision) and a few
  * vectors through a workspace the batch owns (sum over polynomials of
  * P_i (n_i^2 x 2 x element size + (4 n_i + 8) x 8) bytes).
  * polylab_batch_create uploads the descriptors and allocates the workspace
  * (and builds a term plan for every NULL entry of `plans`; `polys` may then
- * not be NULL), so polylab_batch_run only enqueues three memsets and three
- * kernels on `stream` and may be captured into a CUDA graph and replayed.  Each run overwrites
+ * not be NULL), so polylab_batch_run only enqueues the work-counter memsets
+ * and the stages' kernels (three to five) on `stream` and may be captured
+ * into a CUDA graph and replayed.  Each run overwrites
  * D[i], Dunit[i] (DEVICE P[i] x n_i or NULL) and info[i] (DEVICE P[i] records
  * or NULL) from X[i] (DEVICE P[i] x n_i).  opts->method must be
  * POLYLAB_MF_EXACT; opts->prec POLYLAB_FP64 or POLYLAB_FP32.  The arrays of
  * pointers passed to create are read during the call only. */
 typedef struct polylab_batch polylab_batch;
 
-/* Launch configuration.  A run is three persistent launches over the same
+/* Launch configuration.  A run is three stages of persistent launches over the same
  * (polynomial, point) items: the gradient/Hessian term sweep, the frame stage
  * (projected Hessian, FP64 LDL^T, inverse) and the third-derivative sweep with
  * the direction.  threads: frame-stage CTA size (64, 128 or 256 threads per

@@ -1,6 +1,7 @@
 // MF-logDet-Exact affine-normal direction (Sec. 5) for a batch of
-// (polynomial, point) work items, in three persistent launches that pass
-// per-point data through a device workspace:
+// (polynomial, point) work items, in three stages of persistent launches
+// (the frame stage optionally one launch per class of n) that pass per-point
+// data through a device workspace:
 //
 //   stage 1 (terms)  g = grad f(x) and H = Hess f(x) from the term list,
 //                    accumulated in shared memory            -> H, g, sum |g terms|
