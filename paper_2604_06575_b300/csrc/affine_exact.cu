@@ -172,6 +172,100 @@ __device__ __forceinline__ void ldlt_block(int m, Col col, double* __restrict__ 
   }
 }
 
+// The same factorisation in panels of two columns with one barrier per
+// panel, for matrices in global memory (large n), where every trailing
+// element read and written costs a trip to L2 or DRAM: while warps 1.. apply
+// the rank-2 update of panel (k, k+1) to columns k+4.. (a_ij -= l_ik u_jk +
+// l_ik+1 u_jk+1), warp 0 applies it to the next panel's columns k+2, k+3 and
+// factors them.  Each trailing element is read and written once per two
+// columns.  uc holds four unscaled pivot columns.  (In shared memory the
+// one-column form is faster: warp 0's pivot chain per barrier doubles here.)
+template <int NT, typename Col>
+__device__ __forceinline__ void ldlt_block_pairs(int m, Col col, double* __restrict__ uc, double* __restrict__ dv,
+                                                 double* __restrict__ di, int* flag) {
+  static_assert(NT >= 64, "one pivot warp plus at least one update warp");
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (m == 0) return;
+  auto ubuf = [&](int c) { return uc + (c & 3) * m; };
+  auto pivot = [&](int c) -> bool {  // warp 0; false when the pivot fails
+    double* cc = col(c);
+    const double d = cc[c];
+    const long long bits = __double_as_longlong(d);
+    if (!(bits > 0 && bits < 0x7FF0000000000000ll)) {
+      if (lane == 0) *flag = 1;
+      return false;
+    }
+    const double inv = __drcp_rn(d);
+    if (lane == 0) {
+      dv[c] = d;
+      di[c] = inv;
+    }
+    double* u = ubuf(c);
+    for (int i = c + 1 + lane; i < m; i += 32) {
+      const double a = cc[i];
+      u[i] = a;
+      cc[i] = a * inv;
+    }
+    return true;
+  };
+  // column c1 -= column c0 (rows c1..m-1), then its pivot; warp 0
+  auto update_and_pivot = [&](int c0, int c1) -> bool {
+    const double* l0 = col(c0);
+    const double u = ubuf(c0)[c1];
+    double* cc = col(c1);
+    for (int i = c1 + lane; i < m; i += 32) cc[i] -= l0[i] * u;
+    __syncwarp();
+    return pivot(c1);
+  };
+  if (wid == 0 && pivot(0) && m > 1) update_and_pivot(0, 1);
+  __syncthreads();
+  for (int k = 0; k + 2 < m; k += 2) {
+    if (*flag) return;
+    const double* l0 = col(k);
+    const double* l1 = col(k + 1);
+    const double* u0 = ubuf(k);
+    const double* u1 = ubuf(k + 1);
+    if (wid == 0) {
+      for (int c = k + 2; c < k + 4 && c < m; ++c) {
+        const double a0 = u0[c], a1 = u1[c];
+        double* cc = col(c);
+        for (int i = c + lane; i < m; i += 32) cc[i] -= l0[i] * a0 + l1[i] * a1;
+      }
+      __syncwarp();
+      if (pivot(k + 2) && k + 3 < m) update_and_pivot(k + 2, k + 3);
+    } else {
+      // columns k+4..m-1 of the trailing triangle, placed as in ldlt_block;
+      // four elements per thread and round, all loads issued before the
+      // stores, so that a thread keeps several memory trips in flight
+      constexpr int S = NT - 32, U = 4;
+      const int len = m - k - 4;
+      const int T = len > 0 ? len * (len + 1) / 2 : 0;
+      for (int q0 = tid - 32; q0 < T; q0 += U * S) {
+        double* dst[U];
+        double val[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int q = q0 + u * S;
+          dst[u] = nullptr;
+          if (q < T) {
+            int c = (int)((__fsqrt_rn(8.f * (float)q + 1.f) - 1.f) * 0.5f);
+            c += (c + 1) * (c + 2) / 2 <= q;
+            c -= c * (c + 1) / 2 > q;
+            const int j = m - 1 - c;
+            const int i = j + q - c * (c + 1) / 2;
+            dst[u] = col(j) + i;
+            val[u] = *dst[u] - (l0[i] * u0[j] + l1[i] * u1[j]);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (dst[u]) *dst[u] = val[u];
+      }
+    }
+    __syncthreads();
+  }
+}
+
 struct Bump {
   size_t o = 0;
   __host__ __device__ size_t take(size_t bytes) {
@@ -233,7 +327,7 @@ __host__ __device__ Lay2 lay_frame(int n, bool in_smem) {
   L.h = b.take(n * 8);
   L.dv = b.take(m * 8);      // LDL^T pivots d_k
   L.di = b.take(m * 8);      // 1 / d_k
-  L.uc = b.take(2 * m * 8);  // unscaled pivot columns (two buffers)
+  L.uc = b.take((in_smem ? 2 : 4) * m * 8);  // unscaled pivot columns (two buffers; four for the pairs form)
   L.vr = b.take(n * sizeof(R));
   L.u = b.take(n * sizeof(R));
   L.w = b.take(n * sizeof(R));
@@ -638,7 +732,8 @@ __device__ __forceinline__ bool frame_item(const StageArgs<R>& a, const ExactDes
     for (int i = tid; i < m; i += NT) col(i)[i] += a.r;
   }
   __syncthreads();
-  ldlt_block<NT>(m, col, uc, dv, di, &s_flag);
+  if constexpr (SMEM) ldlt_block<NT>(m, col, uc, dv, di, &s_flag);
+  else ldlt_block_pairs<NT>(m, col, uc, dv, di, &s_flag);
   __syncthreads();
   if (s_flag) {
     write_failed(pd, p, n, gn, POLYLAB_FLAG_NOT_PD);

@@ -164,3 +164,22 @@ def test_gather_and_term_by_term_sweeps_agree(pl, prec):
             assert info["flags"][i] == oi["flags"]
             if oi["flags"] == 0:
                 assert np.radians(affine.angle_deg(D[i], nu)) <= 2e-5 * max(kap, 1.0), i
+
+
+@pytest.mark.parametrize("n,prec", [(131, "fp64"), (132, "fp64"), (171, "fp32")])
+def test_global_memory_frame_both_parities(pl, n, prec):
+    """Matrices too large for shared memory take the frame stage's global-memory
+    path (the LDL^T in panels of two columns): even and odd m = n - 1, both forms."""
+    rng = np.random.default_rng(n)
+    poly = workloads.convexified(rng, n, workloads.sparse_monomials(rng, n, 300, 4, 4), 0.1)
+    X = workloads.shell_points(rng, n, 3)
+    D, Du, info = run(pl, poly, X, regularization=1e-6, prec=prec)
+    ref = oracle_all(poly, X, 1e-6, third="contract")
+    if prec == "fp64":
+        compare(poly, X, D, info, ref, 1e-6)
+    else:
+        for i, (nu, oi) in enumerate(ref):
+            kap, amb = kappa_and_ambiguity(poly, X[i], 1e-6)
+            assert info["flags"][i] == oi["flags"]
+            if oi["flags"] == 0:
+                assert np.radians(affine.angle_deg(D[i], nu)) <= 2e-5 * max(kap, 1.0), i
