@@ -82,7 +82,7 @@ STAGES = ("terms", "frame", "third")
 
 
 def exact_flops(poly, P: int):
-    """Algorithmic flops of one exact direction (stated in the design doc), per
+    """Algorithmic flops of one exact direction, per
     stage: the gradient/Hessian term sweep, the frame stage (LDL^T in FP64,
     inverse and the n^2 frame updates in the form's precision) and the
     third-derivative sweep with the direction (W y)."""

@@ -12,7 +12,7 @@ At x with g = grad f(x), e = g/|g| and an orthonormal frame Q = [Q_T, e]:
 d_{t_i} H_T = Q_T^T (sum_l T_l (Q_T)_{l i}) Q_T is the derivative of the tangent
 Hessian block along the tangent axis q_i (T = third-derivative tensor).
 
-Readings (listed in DESIGN.md):
+Readings of the paper taken here, where it is silent or ambiguous:
 * the regularisation r enters every tangent solve: H_T is replaced by
   H_T + r I both in the trace term and in tau (this is what reproduces the
   printed worked example of Sec. 5 to every shown digit);
@@ -144,7 +144,7 @@ def affine_normal_stochastic(exps, coef, x, r: float, q: int, tol: float, maxit:
          Q_T^T c^(s) estimates a_i = tr(H_T^{-1} d_{t_i} H_T).)
       3. a = (1/q) sum_s Q_T^T c^(s); solve A tau = h - |g|/(n+1) a by PCG;
          nu = Q_T tau - e.
-    Preconditioner (reading): 'jacobi' applies Q_T^T D^{-1} Q_T with
+    Preconditioner (a reading; the paper names none): 'jacobi' applies Q_T^T D^{-1} Q_T with
     D = |diag(H)| + r (1 where that is 0; the Jacobi matrix of the ambient H + rI carried into the
     tangent space, so iterates do not depend on the frame); 'none' is the
     identity; 'lowrank' applies Q_T^T (D + U U^T) Q_T with (D, U) given by

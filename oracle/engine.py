@@ -7,7 +7,7 @@ identities, uint8[m, n] exponent rows, float64[m] coefficients -- the paper's
 ``(n, coef, pow)`` model carrying ``vars.id`` (Sec. 2 Table "apisignature",
 Sec. 3.2).
 
-Readings of the paper taken here (each is listed in the design doc):
+Readings of the paper taken here, where it is silent or ambiguous:
 
 * Alignment (Sec. 3.2): the merged variable space is the union of the operand
   ids in ascending id order; with ids assigned in creation order this yields

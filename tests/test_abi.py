@@ -19,7 +19,7 @@ def declared_functions():
 
 
 def test_library_exports_every_declared_symbol():
-    import __graft_entry__  # noqa: F401  (build() is what the driver runs; the .so is in-tree)
+    import __graft_entry__  # noqa: F401  (its build() compiles the in-tree .so)
     path = os.path.join(ROOT, "paper_2604_06575_b300", "libpolylab.so")
     if not os.path.exists(path):
         __graft_entry__.build()
