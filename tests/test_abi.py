@@ -4,6 +4,8 @@ import ctypes
 import os
 import re
 
+import pytest
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
@@ -60,3 +62,27 @@ def test_bench_counts_launches_per_step():
     assert bench.stage_launches(dict(chunks=1, frame_split=1), polys[:1], Xs[:1]) == dict(terms=1, frame=1, third=1)
     assert bench.stage_launches(dict(chunks=1, frame_split=0), polys, Xs) == dict(terms=1, frame=1, third=1)
     assert bench.stage_launches(dict(chunks=4, frame_split=1), polys, Xs) == dict(terms=4, frame=4, third=4)
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/polylab.h is a C interface: it compiles as strict C99 (and as
+    C++), with every declared type usable from C."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use_header.c"
+    src.write_text('#include "polylab.h"\n'
+                   "int main(void) {\n"
+                   "  polylab_an_opts o; polylab_an_opts_default(&o);\n"
+                   "  polylab_poly p = {0}; polylab_poly_f32 q = {0}; polylab_batch_config c = {0};\n"
+                   "  (void)p; (void)q; (void)c; return (int)o.method;\n"
+                   "}\n")
+    inc = os.path.join(ROOT, "include")
+    for cmd in ([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", inc, "-c", str(src),
+                 "-o", str(tmp_path / "a.o")],
+                [gcc, "-x", "c++", "-std=c++17", "-Wall", "-Werror", "-I", inc, "-c", str(src),
+                 "-o", str(tmp_path / "b.o")]):
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
