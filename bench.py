@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--forms", default="fp64,fp32", help="forms to time (profiling runs time one)")
     ap.add_argument("--rows-only", action="store_true", help="only the per-row measurements (profiling runs)")
     ap.add_argument("--config", default=None,
-                    help="threads,ctas_per_sm,order[,term_threads,chunks,terms_ctas,third_ctas,frame_split,"
+                    help="threads,ctas_per_sm,order[,term_threads,terms_ctas,third_ctas,frame_split,"
                          "third_threads] in place of autotuning (profiling runs)")
     return ap.parse_args()
 
@@ -215,33 +215,78 @@ class Clocks:
 
 # ------------------------------------------------------------------ reference / cpu baseline
 
-def oracle_sample(polys, Xs, budget_s: float, r: float = 1e-6):
-    """Run the CPU oracle ('ad' formula) over points taken round-robin from the
-    polynomials until ``budget_s`` seconds of work; returns (directions, seconds,
-    description, {(poly, point): nu})."""
+def _oracle_point(args):
+    """One direction by the CPU oracle ('ad' formula, trace term contracted
+    term by term); a process-pool task."""
     from oracle import affine
+    exps, coef, x, r = args
+    nu, _, _ = affine.affine_normal_ad(exps, coef, x, r=r, third="contract")
+    return nu
+
+
+def _pool_init():
     try:
         from threadpoolctl import threadpool_limits
-        lim = threadpool_limits(1)
+        threadpool_limits(1)
     except Exception:
-        lim = None
-    done, out = 0, {}
-    t0 = time.perf_counter()
-    j = 0
-    while time.perf_counter() - t0 < budget_s and j < 64:
-        for i in range(len(polys)):
-            if j < Xs[i].shape[0]:
-                nu, _, _ = affine.affine_normal_ad(polys[i].exps, polys[i].coef, Xs[i][j], r=r, third="contract")
-                out[(i, j)] = nu
-                done += 1
-            if time.perf_counter() - t0 >= budget_s:
-                break
-        j += 1
-    dt = time.perf_counter() - t0
-    if lim is not None:
-        lim.unregister() if hasattr(lim, "unregister") else None
-    desc = f"{done} points taken round-robin over the {len(polys)} polys (point j of every poly, j=0,1,..), 1 thread"
-    return done, dt, desc, out
+        pass
+
+
+class OraclePool:
+    """The oracle on the host cores: one task per point, ``workers``
+    single-threaded processes (spawned, so that a pool made after the first
+    GPU call is safe)."""
+
+    def __init__(self, workers: int):
+        import multiprocessing as mp
+        self.workers = workers
+        self.pool = mp.get_context("spawn").Pool(workers, initializer=_pool_init)
+
+    def close(self):
+        """Stops the workers (points still running are abandoned)."""
+        self.pool.terminate()
+        self.pool.join()
+
+    def windows(self, polys, Xs, order, n_windows: int, window_s: float, r: float = 1e-6):
+        """Runs points continuously -- taken round-robin over the polynomials in
+        ``order`` (point j of every polynomial, j = 0, 1, ..), one per worker
+        at all times -- through ``n_windows`` consecutive windows of
+        ``window_s`` seconds, and counts the points completed in each window
+        (a point still running at a window's end counts in the window where
+        it completes).  Returns (completions per window, window durations,
+        {(poly, point): nu})."""
+        def tasks():
+            for j in range(1 << 20):
+                for i in order:
+                    if j < Xs[i].shape[0]:
+                        yield (i, j)
+        it = tasks()
+        pending, out, counts, durs = [], {}, [], []
+        for _ in range(n_windows):
+            t0 = time.perf_counter()
+            done = 0
+            while time.perf_counter() - t0 < window_s:
+                while len(pending) < self.workers:
+                    i, j = next(it)
+                    pending.append(((i, j), self.pool.apply_async(
+                        _oracle_point, ((polys[i].exps, polys[i].coef, Xs[i][j], r),))))
+                ready = [q for q in pending if q[1].ready()]
+                for q in ready:
+                    pending.remove(q)
+                    out[q[0]] = q[1].get()
+                    done += 1
+                if not ready:
+                    time.sleep(0.002)
+            counts.append(done)
+            durs.append(time.perf_counter() - t0)
+        return counts, durs, out
+
+
+def sample_order(n_polys: int, seed: int):
+    """A seeded random order of the polynomials (their point counts do not
+    depend on their term counts, so points taken over it estimate the
+    workload's mean cost per point)."""
+    return [int(i) for i in np.random.default_rng(seed).permutation(n_polys)]
 
 
 def run_reference(args):
@@ -250,20 +295,25 @@ def run_reference(args):
     if rank != 0:
         return
     polys, Xs = workloads.batched_uneven(n_polys=args.polys)
-    for _ in range(args.warmup):
-        oracle_sample(polys, Xs, 0.5)
-    vals = []
-    t_all = 0.0
-    for _ in range(args.steps):
-        done, dt, desc, _ = oracle_sample(polys, Xs, args.cpu_budget / max(args.steps, 1) * 2)
-        vals.append(done / dt)
-        t_all += dt
-    v = float(statistics.median(vals))
+    cores = os.cpu_count() or 1
+    pool = OraclePool(cores)
+    window = 3.0
+    # the warm-up windows run the same stream of points (so that the timed
+    # windows see the pool in its steady state) and are not counted
+    counts, durs, _ = pool.windows(polys, Xs, sample_order(len(polys), 0), args.warmup + args.steps, window)
+    pool.close()
+    counts, durs = counts[args.warmup:], durs[args.warmup:]
+    pts, t_all = sum(counts), sum(durs)
+    v = pts / t_all
+    desc = (f"points taken round-robin over the {len(polys)} polys in a seeded random order (point j of every poly), "
+            f"run continuously on {cores} single-threaded processes; each step a {window:.0f} s window counting the "
+            f"points completed in it, after {args.warmup} warm-up windows of the same stream; {pts} points in "
+            f"{args.steps} windows")
     line = dict(metric=METRIC, value=v, unit="dirs/s", n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
                 ms_per_step=t_all / args.steps * 1e3, higher_is_better=True, scaling="weak", vs_baseline=None,
                 dtype="f64", data="synthetic", impl="reference",
                 config=dict(workload=WORKLOAD, polys=args.polys, sample="bounded CPU sample per step"),
-                cpu_baseline=dict(value=v, unit="dirs/s", cores=1, kind="oracle", sample=desc),
+                cpu_baseline=dict(value=v, unit="dirs/s", cores=cores, kind="oracle", sample=desc),
                 e2e=dict(value=v, unit="dirs/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
 
@@ -490,9 +540,11 @@ def main():
                             regularization=1e-6, l2="flushed (256 MB write) before every timed step",
                             parallelism=f"weak: each rank its own {args.polys}-poly batch" if world > 1 else "1 GPU"),
                 forms=dict(fp64=dict(dirs_per_s=round(rate("fp64"), 1),
-                                     ms_per_step=round(res.get("fp64", {}).get("total_ms", float("nan")) / args.steps, 3)),
+                                     ms_per_step=round(res.get("fp64", {}).get("total_ms", float("nan")) / args.steps, 3),
+                                     stage_ms={k: round(v, 3) for k, v in res.get("fp64", {}).get("stage_ms", {}).items()}),
                            fp32=dict(dirs_per_s=round(rate("fp32"), 1),
                                      ms_per_step=round(res.get("fp32", {}).get("total_ms", float("nan")) / args.steps, 3),
+                                     stage_ms={k: round(v, 3) for k, v in res.get("fp32", {}).get("stage_ms", {}).items()},
                                      max_angle_vs_fp64_rad=worst, stated_bound_rad=FP32_BOUND,
                                      flags_equal=flags_equal),
                            speedup_vs_fp64=round(rate(chosen) / rate("fp64"), 3)),
@@ -507,13 +559,29 @@ def main():
         line["rows"] = measure_rows(pl, workloads, torch, dev, p32, p64)
 
     if rank == 0 and not args.no_cpu_baseline:
-        done, dt, desc, ref = oracle_sample(polys, Xs, args.cpu_budget)
+        # the oracle on the host cores: one thread, then every core, each on a
+        # bounded sample of the same workload
+        cores = os.cpu_count() or 1
+        order = sample_order(len(polys), 7)
+        budget = args.cpu_budget
+        one = OraclePool(1)
+        c1, t1, ref = one.windows(polys, Xs, order, 2, budget / 2)  # the first window warms up
+        one.close()
+        alln = OraclePool(cores)
+        cn, tn, ref_n = alln.windows(polys, Xs, order, 2, budget / 2)
+        alln.close()
+        d1, dn, t1, tn = c1[1], cn[1], t1[1], tn[1]
+        ref.update(ref_n)
         errs = []
         for (i, j), nu in ref.items():
             d = outs[chosen][i][0][j].cpu().numpy()
             if np.all(np.isfinite(nu)):
                 errs.append(float(np.linalg.norm(d - nu) / np.linalg.norm(nu)))
-        line["cpu_baseline"] = dict(value=round(done / dt, 3), unit="dirs/s", cores=1, kind="oracle", sample=desc,
+        what = (f"points completed in a {budget / 2:.1f} s window after a {budget / 2:.1f} s warm-up window, taken "
+                f"round-robin over the {len(polys)} polys in a seeded random order (point j of every poly)")
+        line["cpu_baseline"] = dict(value=round(dn / tn, 3), unit="dirs/s", cores=cores, kind="oracle",
+                                    sample=f"{dn} {what}, {cores} single-threaded processes",
+                                    single_thread=dict(value=round(d1 / t1, 3), cores=1, sample=f"{d1} {what}"),
                                     max_rel_err_of_reported_form=max(errs) if errs else None)
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -522,13 +590,9 @@ def main():
 
 
 def stage_launches(cfg: dict, polys, Xs) -> dict:
-    """Kernel launches of one run per stage: with chunks = 1 one launch per
-    term sweep and, with frame_split, one frame launch per non-empty class
-    of n (n > 40, 24 < n <= 40, n <= 24); pipelined runs launch every stage
-    once per non-empty chunk (counted as `chunks`)."""
-    if cfg.get("chunks", 1) > 1:
-        c = cfg["chunks"]
-        return dict(terms=c, frame=c, third=c)
+    """Kernel launches of one run per stage: one launch per term sweep and,
+    with frame_split, one frame launch per non-empty class of n (n > 40,
+    24 < n <= 40, n <= 24)."""
     ns = [p.n for p, X in zip(polys, Xs) if X.shape[0] > 0]
     if cfg.get("frame_split", 0):
         frame = sum(1 for lo, hi in ((40, 1 << 30), (24, 40), (0, 24)) if any(lo < n <= hi for n in ns))

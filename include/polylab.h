@@ -159,11 +159,11 @@ polylab_status polylab_diff(const polylab_poly* p, uint64_t var_id, double zerop
  * POLYLAB_ERR_UNSUPPORTED with a message in polylab_last_error().  If the
  * result has more than `capacity` terms, nothing is written, out->n_terms
  * holds the count needed and the status is POLYLAB_ERR_INVALID_ARG.
- * The first call on a device looks up the device address of the array
- * (cudaGetSymbolAddress); make that first call before any stream capture.
- * Every call uses the same array, so calls that overlap on the GPU (several
- * streams or host threads at once) race: serialise them.  Synchronises
- * `stream` like polylab_simplify. */
+ * Every call looks up the device address of the array on the current device
+ * (cudaGetSymbolAddress) and returns only after all of its work on `stream`
+ * has completed, so calls made one after another are ordered on the GPU
+ * whatever streams they use.  Calls that run at the same time (from several
+ * host threads) share the array and race: serialise them. */
 polylab_status polylab_simplify_noalloc(const polylab_poly* p, double zeroprec, polylab_poly_out* out,
                                         int64_t capacity, polylab_stream stream);
 
@@ -213,10 +213,23 @@ typedef enum {
  * F: DEVICE P; G: DEVICE P x n (order >= 1); H: DEVICE P x n x n, full
  * symmetric matrix (order 2).  Outputs are overwritten.  With POLYLAB_FP64
  * every output agrees with the plain definition within ~1e-15 of the sum of
- * |term contributions|; reduced forms carry their stated error. */
+ * |term contributions|; reduced forms carry their stated error.
+ * Asynchronous in every form when `plan` is given (a NULL plan builds a
+ * temporary one, which synchronises `stream`).  The tensor-core forms
+ * (POLYLAB_TF32X3, POLYLAB_BF16; the plan must be built with
+ * POLYLAB_PLAN_GEMM) bound every device-side wait: a wait that gives up --
+ * a safety net, not an expected event -- writes NaN to the outputs of its
+ * 128-point tile and is reported by the next polylab_eval_check. */
 polylab_status polylab_eval_derivs(const polylab_poly* p, const polylab_plan* plan, const double* X,
                                    int64_t P, int32_t order, polylab_precision prec, double* F,
                                    double* G, double* H, polylab_stream stream);
+
+/* Synchronises `stream` and reports whether a bounded wait of a tensor-core
+ * polylab_eval_derivs call on the current device gave up since the last
+ * check: POLYLAB_ERR_TIMEOUT then (message in polylab_last_error(); the
+ * record is cleared), POLYLAB_OK otherwise.  The record is one word per
+ * device, shared by every stream and thread. */
+polylab_status polylab_eval_check(polylab_stream stream);
 
 /* ------------------------------------------------------------ affine normal (Sec. 5) */
 
@@ -354,21 +367,15 @@ typedef struct {
   int32_t ctas_per_sm;
   int32_t order;
   int32_t term_threads;
-  /* chunks (1..32): the work is cut into this many chunks of equal estimated
-   * cost and the three stages run as a pipeline over three streams (stage 2
-   * of chunk c beside stage 1 of chunk c+1 and stage 3 of chunk c-1), so
-   * FP64-bound and shared-memory-bound work share the SMs; 1 runs the stages
-   * one after another.  terms_ctas, third_ctas: caps on resident CTAs per SM
-   * of the term sweeps (0: the occupancy limit), which leave room for the
-   * other stages' CTAs when pipelined. */
-  int32_t chunks;
+  /* terms_ctas, third_ctas: caps on resident CTAs per SM of the two term
+   * sweeps (0: the occupancy limit). */
   int32_t terms_ctas;
   int32_t third_ctas;
-  /* frame_split (0 or 1): with chunks = 1, the frame stage runs as up to
-   * three launches over classes of polynomials by n (n > 40 with `threads`
-   * per CTA, 24 < n <= 40 and n <= 24 with 64), each sized for its class's
-   * largest n and taken in an order of n descending; ctas_per_sm caps the
-   * first class only.  0: one launch over all polynomials. */
+  /* frame_split (0 or 1): the frame stage runs as up to three launches over
+   * classes of polynomials by n (n > 40 with `threads` per CTA, 24 < n <= 40
+   * and n <= 24 with 64), each sized for its class's largest n and taken in an
+   * order of n descending; ctas_per_sm caps the first class only.  0: one
+   * launch over all polynomials. */
   int32_t frame_split;
   int32_t third_threads;  /* CTA size of the third-derivative sweep (64, 128 or 256) */
 } polylab_batch_config;
@@ -400,9 +407,8 @@ polylab_status polylab_batch_set_config(polylab_batch* batch, const polylab_batc
  * third_threads in {64,128,256} over the third-derivative sweep, then
  * frame_split in {1, 0} x threads in {64,128,256} x ctas_per_sm in
  * {occupancy, 2, 4} timed over the frame stage,
- * then order in {cost order, given order} timed over the whole run, all with
- * chunks = 1 (pipelined runs are set explicitly; on the bench's batches they
- * were never faster).  Keeps the fastest of each step and returns the result
+ * then order in {cost order, given order} timed over the whole run.  Keeps
+ * the fastest of each step and returns the result
  * (and the mean time of a whole run in ms, if best_ms is not NULL).  The
  * outputs hold the last run's results. */
 polylab_status polylab_batch_autotune(polylab_batch* batch, int32_t reps, polylab_stream stream,

@@ -614,7 +614,8 @@ __global__ void __launch_bounds__(NT) exact_terms_kernel(StageArgs<R> a) {
 // One (polynomial, point) item of the frame stage.  SMEM: the n x n
 // matrices live in shared memory (else in this CTA's global workspace); as a
 // template parameter it lets every matrix access compile to a shared-memory
-// instruction.  Returns false when a bounded wait expired (the kernel stops).
+// instruction.  Returns false, for every thread of the CTA, when a bounded
+// wait expired (the kernel stops).
 template <typename R, int NT, bool SMEM>
 __device__ __forceinline__ bool frame_item(const StageArgs<R>& a, const ExactDesc& pd, int64_t p, unsigned char* sm,
                                            int& s_flag, double* s_sc, uint64_t& s_bar, uint32_t& phase) {
@@ -689,11 +690,14 @@ __device__ __forceinline__ bool frame_item(const StageArgs<R>& a, const ExactDes
     }
   }
   if (SMEM) {
-    const bool ok = mbar_wait(&s_bar, phase, a.err, 2);
+    if (!mbar_wait_cta(&s_bar, phase, a.err, 2)) {
+      mbar_drain(&s_bar, phase, a.err, 2);
+      return false;
+    }
     phase ^= 1u;
-    if (!ok) return false;
+  } else {
+    __syncthreads();
   }
-  __syncthreads();
   for (int i = wid; i < n; i += NW)  // mirror the upper triangle
     for (int j = lane; j < i; j += 32) Hr[i * n + j] = Hr[j * n + i];
   __syncthreads();
@@ -892,7 +896,7 @@ __global__ void __launch_bounds__(NT) exact_frame_kernel(StageArgs<R> a) {
     const int64_t p = item - a.prefix[lo];
     const bool ok = pd.mats_in_smem ? frame_item<R, NT, true>(a, pd, p, sm, s_flag, s_sc, s_bar, phase)
                                     : frame_item<R, NT, false>(a, pd, p, sm, s_flag, s_sc, s_bar, phase);
-    if (!ok) return;
+    if (!ok) break;  // (uniform across the CTA)
   }
   if (tid == 0) bulk_wait_all();
 }
@@ -950,9 +954,11 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 1024 / NT : 1) exact_thir
     // gather form of the contraction where every |x_v| keeps m and 1/x normal
     const bool gather = __syncthreads_and(in_range) != 0;
     if (pd.w_in_smem) {
-      const bool ok = mbar_wait(&s_bar, phase, a.err, 3);
+      if (!mbar_wait_cta(&s_bar, phase, a.err, 3)) {
+        mbar_drain(&s_bar, phase, a.err, 3);
+        return;
+      }
       phase ^= 1u;
-      if (!ok) return;
     }
     __syncthreads();
     {
@@ -1081,11 +1087,11 @@ static polylab_status prepare_exact(ExactBatch* b) {
 }
 
 template <typename R, int NT>
-static polylab_status launch_stage_t(ExactBatch* b, int stage, int chunk, cudaStream_t s) {
+static polylab_status launch_stage_t(ExactBatch* b, int stage, cudaStream_t s) {
   void (*k)(StageArgs<R>) = stage == 0   ? exact_terms_kernel<R, NT>
                             : stage == 1 ? exact_frame_kernel<R, NT>
                                          : exact_third_kernel<R, NT>;
-  const int64_t i0 = b->chunk_begin[chunk], i1 = b->chunk_begin[chunk + 1];
+  const int64_t i0 = 0, i1 = b->total;
   if (i1 <= i0) return POLYLAB_OK;
   const size_t smem = b->smem[stage];
   PL_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -1103,7 +1109,7 @@ static polylab_status launch_stage_t(ExactBatch* b, int stage, int chunk, cudaSt
   a.order = b->order;
   a.item_begin = i0;
   a.item_end = i1;
-  a.counter = b->counter + 3 * chunk + stage;
+  a.counter = b->counter + stage;
   a.mats_h = (R*)b->ws_h;
   a.mats_w = (R*)b->ws_w;
   a.vecs = (double*)b->ws_v;
@@ -1117,7 +1123,7 @@ static polylab_status launch_stage_t(ExactBatch* b, int stage, int chunk, cudaSt
   return launch_status(stage == 0 ? "exact_terms_kernel" : stage == 1 ? "exact_frame_kernel" : "exact_third_kernel");
 }
 
-// One class of the split frame stage (sequential runs): the class's item
+// One class of the split frame stage: the class's item
 // range of the frame order, its own counter and shared memory; the residency
 // cap applies to the first (largest-n) class only.
 template <typename R, int NT>
@@ -1166,56 +1172,22 @@ static polylab_status launch_frame_classes(ExactBatch* b, cudaStream_t s) {
 }
 
 template <typename R>
-static polylab_status launch_stage(ExactBatch* b, int stage, int chunk, cudaStream_t s) {
+static polylab_status launch_stage(ExactBatch* b, int stage, cudaStream_t s) {
+  if (stage == 1 && b->cfg.frame_split) return launch_frame_classes<R>(b, s);
   const int nt = stage == 0 ? b->cfg.term_threads : stage == 1 ? b->cfg.threads : b->cfg.third_threads;
-  if (nt == 64) return launch_stage_t<R, 64>(b, stage, chunk, s);
-  if (nt == 128) return launch_stage_t<R, 128>(b, stage, chunk, s);
-  return launch_stage_t<R, 256>(b, stage, chunk, s);
-}
-
-static polylab_status launch_chunk(ExactBatch* b, int stage, int chunk, cudaStream_t s) {
-  return b->opts.prec == POLYLAB_FP32 ? launch_stage<float>(b, stage, chunk, s)
-                                      : launch_stage<double>(b, stage, chunk, s);
+  if (nt == 64) return launch_stage_t<R, 64>(b, stage, s);
+  if (nt == 128) return launch_stage_t<R, 128>(b, stage, s);
+  return launch_stage_t<R, 256>(b, stage, s);
 }
 
 polylab_status run_exact_stage(ExactBatch* b, int stage, cudaStream_t s) {
   if (b->total == 0) return POLYLAB_OK;
-  const int C = (int)b->chunk_begin.size() - 1;
-  if (stage == 1 && C <= 1 && b->cfg.frame_split)
-    return b->opts.prec == POLYLAB_FP32 ? launch_frame_classes<float>(b, s) : launch_frame_classes<double>(b, s);
-  for (int c = 0; c < C; ++c) PL_TRY(launch_chunk(b, stage, c, s));
-  return POLYLAB_OK;
+  return b->opts.prec == POLYLAB_FP32 ? launch_stage<float>(b, stage, s) : launch_stage<double>(b, stage, s);
 }
 
-// One run.  With one chunk the stages follow each other on `s`.  Otherwise
-// stage 1 of every chunk runs on `s`, stage 2 on side[0] and stage 3 on
-// side[1], each chunk's stage waiting on an event of the previous stage of the
-// same chunk: the side streams fork from and join back to `s`, so the run is
-// ordered like any single-stream work on `s` and can be captured in a graph.
+// One run: the three stages one after another on `s` (capturable in a graph).
 polylab_status run_exact_batch(ExactBatch* b, cudaStream_t s) {
-  if (b->total == 0) return POLYLAB_OK;
-  const int C = (int)b->chunk_begin.size() - 1;
-  if (C <= 1) {
-    for (int st = 0; st < 3; ++st) PL_TRY(run_exact_stage(b, st, s));
-    return POLYLAB_OK;
-  }
-  cudaEvent_t* ev = b->events.data();
-  cudaStream_t str[3] = {s, b->side[0], b->side[1]};
-  cudaEvent_t fork = ev[3 * kMaxChunks], join1 = ev[3 * kMaxChunks + 1], join2 = ev[3 * kMaxChunks + 2];
-  PL_CUDA(cudaEventRecord(fork, s));
-  PL_CUDA(cudaStreamWaitEvent(str[1], fork, 0));
-  PL_CUDA(cudaStreamWaitEvent(str[2], fork, 0));
-  for (int c = 0; c < C; ++c) {
-    for (int st = 0; st < 3; ++st) {
-      if (st > 0) PL_CUDA(cudaStreamWaitEvent(str[st], ev[3 * c + st - 1], 0));
-      PL_TRY(launch_chunk(b, st, c, str[st]));
-      if (st < 2) PL_CUDA(cudaEventRecord(ev[3 * c + st], str[st]));
-    }
-  }
-  PL_CUDA(cudaEventRecord(join1, str[1]));
-  PL_CUDA(cudaEventRecord(join2, str[2]));
-  PL_CUDA(cudaStreamWaitEvent(s, join1, 0));
-  PL_CUDA(cudaStreamWaitEvent(s, join2, 0));
+  for (int st = 0; st < 3; ++st) PL_TRY(run_exact_stage(b, st, s));
   return POLYLAB_OK;
 }
 

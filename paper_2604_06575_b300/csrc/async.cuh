@@ -53,6 +53,21 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* e
   return true;
 }
 
+// Bounded wait whose outcome is the same for every thread of the CTA (a
+// barrier): false when any thread gave up.  Callers leave the CTA's loop
+// together on false, after mbar_drain.
+__device__ __forceinline__ bool mbar_wait_cta(uint64_t* bar, uint32_t parity, int* err, int code) {
+  return __syncthreads_and(mbar_wait(bar, parity, err, code)) != 0;
+}
+
+// After a bounded wait gave up: one more bounded wait, by one thread, for the
+// copy still in flight into shared memory, so that the CTA does not exit (and
+// hand its shared memory on) while the copy may still write it.
+__device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity, int* err, int code) {
+  if (threadIdx.x == 0) mbar_wait(bar, parity, err, code);
+  __syncthreads();
+}
+
 // order earlier generic-proxy accesses of shared memory before later
 // async-proxy (bulk copy) accesses of it
 __device__ __forceinline__ void fence_proxy_async_smem() {

@@ -23,7 +23,6 @@ polylab_status exact_batch_upload_order(ExactBatch* b, cudaStream_t s) {
   b->host_prefix.assign(n + 1, 0);
   for (int i = 0; i < n; ++i) b->host_prefix[i + 1] = b->host_prefix[i] + b->host_descs[ord[i]].P;
   b->total = b->host_prefix[n];
-  exact_batch_chunks(b);
   // the split frame stage's own order: n descending (its cost is set by n)
   std::vector<int>& ford = b->host_forder;
   ford.resize(n);
@@ -64,32 +63,6 @@ void exact_frame_classes(ExactBatch* b) {
       ++i;
     }
     fc.end = b->host_fprefix.empty() ? 0 : b->host_fprefix[i];
-  }
-}
-
-// Chunk boundaries in the work order at equal shares of the estimated cost
-// (items are whole points; a chunk may be empty).
-void exact_batch_chunks(ExactBatch* b) {
-  const int C = std::max(1, std::min(b->cfg.chunks, kMaxChunks));
-  const int n = b->n_desc;
-  std::vector<double> cum(n + 1, 0.0);
-  for (int i = 0; i < n; ++i) {
-    const ExactDesc& d = b->host_descs[b->host_order[i]];
-    cum[i + 1] = cum[i] + exact_point_cost(d, d.max_support) * (double)d.P;
-  }
-  b->chunk_begin.assign(C + 1, b->total);
-  b->chunk_begin[0] = 0;
-  int i = 0;
-  for (int c = 1; c < C; ++c) {
-    const double target = cum[n] * c / C;
-    while (i < n && cum[i + 1] <= target) ++i;
-    int64_t item = b->host_prefix[i];
-    if (i < n) {
-      const ExactDesc& d = b->host_descs[b->host_order[i]];
-      const double per = exact_point_cost(d, d.max_support);
-      if (per > 0) item += std::min<int64_t>(d.P, (int64_t)((target - cum[i]) / per));
-    }
-    b->chunk_begin[c] = std::max(b->chunk_begin[c - 1], std::min(item, b->total));
   }
 }
 
@@ -141,13 +114,10 @@ polylab_status exact_batch_init(ExactBatch* b, int n, const polylab_plan* const*
   PL_CUDA(cudaMallocAsync(&b->descs, std::max(n, 1) * sizeof(ExactDesc), s));
   PL_CUDA(cudaMallocAsync(&b->order, std::max(n, 1) * sizeof(int), s));
   PL_CUDA(cudaMallocAsync(&b->prefix, (n + 1) * sizeof(int64_t), s));
-  PL_CUDA(cudaMallocAsync(&b->counter, 3 * kMaxChunks * sizeof(int), s));
+  PL_CUDA(cudaMallocAsync(&b->counter, 3 * sizeof(int), s));
   PL_CUDA(cudaMallocAsync(&b->forder, std::max(n, 1) * sizeof(int), s));
   PL_CUDA(cudaMallocAsync(&b->fprefix, (n + 1) * sizeof(int64_t), s));
   PL_CUDA(cudaMallocAsync(&b->fcounter, kFrameClasses * sizeof(int), s));
-  for (auto& st : b->side) PL_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
-  b->events.resize(3 * kMaxChunks + 3);
-  for (auto& e : b->events) PL_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   PL_CUDA(cudaMallocAsync(&b->err, sizeof(int), s));
   PL_CUDA(cudaMemsetAsync(b->err, 0, sizeof(int), s));
   PL_CUDA(cudaMallocAsync(&b->ws_h, std::max<size_t>(b->ws_mat_bytes, 16), s));
@@ -192,15 +162,6 @@ void exact_batch_release(ExactBatch* b, cudaStream_t s) {
   b->fprefix = nullptr;
   b->fcounter = nullptr;
   if (b->gws) cudaFreeAsync(b->gws, s);
-  for (auto& st : b->side) {
-    if (st) {
-      cudaStreamSynchronize(st);
-      cudaStreamDestroy(st);
-    }
-    st = nullptr;
-  }
-  for (auto& e : b->events) cudaEventDestroy(e);
-  b->events.clear();
   if (b->err) cudaFreeAsync(b->err, s);
   b->err = nullptr;
   if (b->ws_h) cudaFreeAsync(b->ws_h, s);
@@ -290,7 +251,6 @@ polylab_status polylab_batch_get_config(const polylab_batch* b, polylab_batch_co
   cfg->ctas_per_sm = b->b.cfg.ctas_per_sm;
   cfg->order = b->b.cfg.order;
   cfg->term_threads = b->b.cfg.term_threads;
-  cfg->chunks = b->b.cfg.chunks;
   cfg->terms_ctas = b->b.cfg.terms_ctas;
   cfg->third_ctas = b->b.cfg.third_ctas;
   cfg->frame_split = b->b.cfg.frame_split;
@@ -305,13 +265,11 @@ polylab_status polylab_batch_set_config(polylab_batch* b, const polylab_batch_co
     return POLYLAB_ERR_INVALID_ARG;
   auto ok_cap = [](int c) { return c >= 0 && c <= 32; };
   if (!ok_cap(cfg->ctas_per_sm) || !ok_cap(cfg->terms_ctas) || !ok_cap(cfg->third_ctas) ||
-      (cfg->order != 0 && cfg->order != 1) || cfg->chunks < 1 || cfg->chunks > kMaxChunks ||
+      (cfg->order != 0 && cfg->order != 1) ||
       (cfg->frame_split != 0 && cfg->frame_split != 1))
     return POLYLAB_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   const bool reorder = cfg->order != b->b.cfg.order;
-  const bool rechunk = cfg->chunks != b->b.cfg.chunks;
-  b->b.cfg.chunks = cfg->chunks;
   b->b.cfg.terms_ctas = cfg->terms_ctas;
   b->b.cfg.third_ctas = cfg->third_ctas;
   b->b.cfg.frame_split = cfg->frame_split;
@@ -324,7 +282,6 @@ polylab_status polylab_batch_set_config(polylab_batch* b, const polylab_batch_co
   b->b.cfg.order = cfg->order;
   if (relayout) PL_TRY(exact_batch_relayout(&b->b, s));
   if (reorder) PL_TRY(exact_batch_upload_order(&b->b, s));
-  else if (rechunk) exact_batch_chunks(&b->b);
   return POLYLAB_OK;
 }
 
@@ -333,10 +290,9 @@ polylab_status polylab_batch_autotune(polylab_batch* b, int32_t reps, polylab_st
   if (!b || reps < 1) return POLYLAB_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   ExactBatch* eb = &b->b;
-  polylab_batch_config cur{eb->cfg.threads, eb->cfg.ctas_per_sm, eb->cfg.order,      eb->cfg.term_threads,
-                           eb->cfg.chunks,  eb->cfg.terms_ctas,  eb->cfg.third_ctas, eb->cfg.frame_split,
-                           eb->cfg.third_threads};
-  cur.chunks = 1;  // the stages one after another
+  polylab_batch_config cur{eb->cfg.threads,    eb->cfg.ctas_per_sm, eb->cfg.order,
+                           eb->cfg.term_threads, eb->cfg.terms_ctas,  eb->cfg.third_ctas,
+                           eb->cfg.frame_split,  eb->cfg.third_threads};
   cur.terms_ctas = 0;
   cur.third_ctas = 0;
   cudaEvent_t e0, e1;

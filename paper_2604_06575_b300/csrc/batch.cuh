@@ -31,18 +31,14 @@ struct ExactDesc {
   polylab_an_info* info;
 };
 
-constexpr int kMaxChunks = 32;
-
 struct ExactConfig {
   int threads = 0;        // frame-stage CTA size: 64, 128 or 256 (0: by largest n)
   int ctas_per_sm = 0;    // cap on resident frame-stage CTAs per SM (0: occupancy limit)
   int order = 1;          // 1: most expensive polynomials first, 0: as given
   int term_threads = 0;   // CTA size of the gradient/Hessian term sweep (0: 128)
-  int chunks = 1;         // work split into this many chunks of equal estimated cost, pipelined
-                          // over three streams (1: the stages run one after another)
   int terms_ctas = 0;     // caps on resident CTAs per SM of the term sweeps (0: occupancy limit)
   int third_ctas = 0;
-  int frame_split = 1;    // sequential runs: frame stage in classes of polynomials by n
+  int frame_split = 1;    // frame stage in classes of polynomials by n
   int third_threads = 0;  // CTA size of the third-derivative sweep (0: 128)
 };
 
@@ -65,10 +61,7 @@ struct ExactBatch {
   ExactDesc* descs = nullptr;  // DEVICE copies
   int* order = nullptr;
   int64_t* prefix = nullptr;
-  int* counter = nullptr;  // one work counter per (chunk, stage)
-  std::vector<int64_t> chunk_begin;  // item range of chunk c: [chunk_begin[c], chunk_begin[c+1])
-  cudaStream_t side[2] = {nullptr, nullptr};  // streams of the frame and third stages when pipelined
-  std::vector<cudaEvent_t> events;            // stage-done events of the pipelined run
+  int* counter = nullptr;  // one work counter per stage
   int* err = nullptr;      // device flag: a bounded wait of a stage expired
   int n_desc = 0;
   int64_t total = 0;
@@ -97,7 +90,6 @@ polylab_status exact_batch_init(ExactBatch* b, int n, const polylab_plan* const*
                                 const int64_t* P, const polylab_an_opts* o, double* const* D,
                                 double* const* Dunit, polylab_an_info* const* info, cudaStream_t s);
 polylab_status exact_batch_upload_order(ExactBatch* b, cudaStream_t s);
-void exact_batch_chunks(ExactBatch* b);
 void exact_frame_classes(ExactBatch* b);
 polylab_status exact_batch_relayout(ExactBatch* b, cudaStream_t s);
 void exact_batch_release(ExactBatch* b, cudaStream_t s);

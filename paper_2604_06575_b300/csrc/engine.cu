@@ -666,26 +666,17 @@ struct Arena {
   }
 };
 
-// Device address of the array, looked up once per device with that device
-// current (in host code the symbol itself is only a host-side stand-in).
-static std::mutex g_noalloc_mu;
-static void* g_noalloc_addr[256] = {};
-
+// Device address of the array on the current device, looked up on every call
+// (in host code the symbol itself is only a host-side stand-in; a lookup per
+// call stays valid across device resets and new contexts).
 polylab_status noalloc_base(unsigned char** out) {
-  int dev = 0;
-  PL_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 256) return POLYLAB_ERR_UNSUPPORTED;
-  std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_addr[dev]) {
-    void* a = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&a, g_noalloc_scratch);
-    if (e != cudaSuccess) {
-      set_last_error("cudaGetSymbolAddress(g_noalloc_scratch)", e);
-      return POLYLAB_ERR_CUDA;
-    }
-    g_noalloc_addr[dev] = a;
+  void* a = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&a, g_noalloc_scratch);
+  if (e != cudaSuccess) {
+    set_last_error("cudaGetSymbolAddress(g_noalloc_scratch)", e);
+    return POLYLAB_ERR_CUDA;
   }
-  *out = static_cast<unsigned char*>(g_noalloc_addr[dev]);
+  *out = static_cast<unsigned char*>(a);
   return POLYLAB_OK;
 }
 
@@ -783,6 +774,9 @@ polylab_status polylab_simplify_noalloc(const polylab_poly* p, double zeroprec, 
   // the pipeline resets the output pointers; hand the caller's buffers back
   out->exps = buf.exps;
   out->coef = buf.coef;
+  // the array is shared by every call: return only once this call's kernels
+  // (the last reads the array) are done
+  if (st == POLYLAB_OK) PL_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
   if (st == POLYLAB_ERR_OOM && buf.too_small) {
     set_last_message("polylab_simplify_noalloc: the result has more terms than `capacity`; n_terms holds the count");
     return POLYLAB_ERR_INVALID_ARG;

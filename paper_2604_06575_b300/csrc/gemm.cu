@@ -604,7 +604,26 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_eval_kernel(GemmArgs a) 
       }
       __syncthreads();
     }
-  } else if (!s_abort) {
+  } else if (s_abort) {
+    // a bounded wait gave up: this tile's outputs are NaN (the abort is
+    // reported by polylab_eval_check)
+    const int nn = n * n;
+    for (int idx = tid; idx < 128 * Cf::NC; idx += kGemmThreads) {
+      const int64_t p = p0 + idx / Cf::NC;
+      const int o = chunk * Cf::NC + idx % Cf::NC;
+      const int kd = a.kind[o];
+      if (p >= a.P || kd == 3) continue;
+      const double y = nan("");
+      if (kd == 0) {
+        a.F[p] = y;
+      } else if (kd == 1) {
+        if (a.order >= 1) a.G[p * n + a.ti[o]] = y;
+      } else if (a.order >= 2) {
+        a.H[p * nn + a.ti[o] * n + a.tj[o]] = y;
+        a.H[p * nn + a.tj[o] * n + a.ti[o]] = y;
+      }
+    }
+  } else {
     // several column chunks: warps w, w+4, w+8, w+12 read the same TMEM lane
     // quadrant (rows 32(w%4)..) and split the columns between them
     const int64_t p = p0 + (wid & 3) * 32 + (tid & 31);
@@ -821,6 +840,15 @@ polylab_status build_gemm_operand(polylab_plan* plan, cudaStream_t s) {
   return POLYLAB_OK;
 }
 
+// Set by a launch of the contraction whose bounded wait gave up; read and
+// cleared by polylab_eval_check (one word per device that loads the library).
+static __device__ int g_eval_wait_err;
+
+static polylab_status eval_err_word(int** p) {
+  PL_CUDA(cudaGetSymbolAddress((void**)p, g_eval_wait_err));
+  return POLYLAB_OK;
+}
+
 polylab_status eval_gemm(const polylab_plan* plan, const double* X, int64_t P, int order, int prec, double* F,
                          double* G, double* H, cudaStream_t s) {
   if (P == 0) return POLYLAB_OK;
@@ -828,9 +856,7 @@ polylab_status eval_gemm(const polylab_plan* plan, const double* X, int64_t P, i
   if (!g) return POLYLAB_ERR_INVALID_ARG;
   const int n = plan->n;
   int* err;
-  Scratch scr(s);
-  PL_TRY(scr.get(&err, 1));
-  PL_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+  PL_TRY(eval_err_word(&err));
   GemmArgs a{};
   a.X = X;
   a.P = P;
@@ -867,14 +893,25 @@ polylab_status eval_gemm(const polylab_plan* plan, const double* X, int64_t P, i
     PL_CUDA(cudaFuncSetAttribute(gemm_eval_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     gemm_eval_kernel<1><<<dim3(gx, g->Npad / 256), kGemmThreads, smem, s>>>(a);
   }
-  PL_TRY(launch_status("gemm_eval_kernel"));
-  int herr = 0;
-  PL_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
-  PL_CUDA(cudaStreamSynchronize(s));
-  return herr ? POLYLAB_ERR_TIMEOUT : POLYLAB_OK;
+  return launch_status("gemm_eval_kernel");
 }
 
 }  // namespace polylab
+
+extern "C" polylab_status polylab_eval_check(polylab_stream stream) {
+  using namespace polylab;
+  cudaStream_t s = (cudaStream_t)stream;
+  int* err;
+  PL_TRY(eval_err_word(&err));
+  int flag = 0;
+  PL_CUDA(cudaMemcpyAsync(&flag, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  PL_CUDA(cudaStreamSynchronize(s));
+  if (!flag) return POLYLAB_OK;
+  set_last_message("a bounded wait of the tensor-core derivative contraction expired");
+  PL_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+  PL_CUDA(cudaStreamSynchronize(s));
+  return POLYLAB_ERR_TIMEOUT;
+}
 
 extern "C" polylab_status polylab_plan_gemm_info(const polylab_plan* plan, int64_t* K, int32_t* Npad,
                                                  int64_t* bf16_live_halves, int64_t* tf32_live_tiles) {

@@ -55,8 +55,8 @@ class _AnOpts(C.Structure):
 
 class _BatchConfig(C.Structure):
     _fields_ = [("threads", C.c_int32), ("ctas_per_sm", C.c_int32), ("order", C.c_int32),
-                ("term_threads", C.c_int32), ("chunks", C.c_int32), ("terms_ctas", C.c_int32),
-                ("third_ctas", C.c_int32), ("frame_split", C.c_int32), ("third_threads", C.c_int32)]
+                ("term_threads", C.c_int32), ("terms_ctas", C.c_int32), ("third_ctas", C.c_int32),
+                ("frame_split", C.c_int32), ("third_threads", C.c_int32)]
 
 
 INFO_DTYPE = np.dtype([("grad_norm", "<f8"), ("logdet", "<f8"), ("flags", "<i4"), ("hv_evals", "<i4"),
@@ -89,6 +89,7 @@ _lib.polylab_diff.argtypes = [C.POINTER(_Poly), C.c_uint64, C.c_double, C.POINTE
                               C.c_void_p]
 _lib.polylab_simplify_noalloc.argtypes = [C.POINTER(_Poly), C.c_double, C.POINTER(_PolyOut), C.c_int64, C.c_void_p]
 _lib.polylab_an_opts_default.argtypes = [C.POINTER(_AnOpts)]
+_lib.polylab_eval_check.argtypes = [C.c_void_p]
 _PP = C.POINTER(C.c_void_p)
 _lib.polylab_batch_create.argtypes = [C.c_int32, C.c_void_p, _PP, _PP, C.POINTER(C.c_int64), C.POINTER(_AnOpts),
                                       _PP, _PP, _PP, C.c_void_p, C.POINTER(C.c_void_p)]
@@ -119,7 +120,8 @@ _lib.polylab_eval_derivs_f32.argtypes = [C.POINTER(_Poly), C.c_void_p, C.c_void_
 _lib.polylab_affine_normal_f32.argtypes = _lib.polylab_affine_normal.argtypes
 F32_CALLS = ["polylab_simplify_f32", "polylab_mul_f32", "polylab_add_f32", "polylab_sub_f32", "polylab_pow_f32",
              "polylab_diff_f32", "polylab_plan_create_f32", "polylab_eval_derivs_f32", "polylab_affine_normal_f32"]
-for _f in ("polylab_plan_create", "polylab_plan_destroy", "polylab_eval_derivs", "polylab_affine_normal",
+for _f in ("polylab_plan_create", "polylab_plan_destroy", "polylab_eval_derivs", "polylab_eval_check",
+           "polylab_affine_normal",
            "polylab_simplify", "polylab_mul", "polylab_add", "polylab_sub", "polylab_pow", "polylab_diff",
            "polylab_simplify_noalloc", "polylab_batch_create",
            "polylab_batch_run", "polylab_batch_run_stage", "polylab_batch_check", "polylab_batch_get_config",
@@ -131,6 +133,7 @@ for _f in ("polylab_plan_create", "polylab_plan_destroy", "polylab_eval_derivs",
 EXPORTED = ["polylab_status_string", "polylab_last_error", "polylab_simplify", "polylab_mul", "polylab_add",
             "polylab_sub", "polylab_pow", "polylab_diff",
             "polylab_plan_create", "polylab_plan_destroy", "polylab_plan_closure_size", "polylab_eval_derivs",
+            "polylab_eval_check",
             "polylab_an_opts_default", "polylab_affine_normal", "polylab_simplify_noalloc", "polylab_batch_create",
             "polylab_batch_run", "polylab_batch_run_stage", "polylab_batch_check", "polylab_batch_get_config",
             "polylab_batch_set_config",
@@ -269,6 +272,12 @@ def eval_derivs(p: DevPoly, X: torch.Tensor, order: int = 2, prec: str | None = 
         _check("polylab_eval_derivs", _lib.polylab_eval_derivs(C.byref(cp), ph, _ptr(X), P, order, PREC[prec],
                                                                _ptr(F), _ptr(G), _ptr(H), _stream()))
     return F, G, H
+
+
+def eval_check():
+    """Synchronise the current stream and raise if a bounded wait of a
+    tensor-core evaluation expired since the last check."""
+    _check("polylab_eval_check", _lib.polylab_eval_check(_stream()))
 
 
 def an_opts(method="mf-exact", regularization=1e-6, num_probes=8, krylov_tol=1e-4, krylov_maxit=40,
@@ -445,20 +454,20 @@ class Batch:
     def run_stage(self, stage: int):
         _check("polylab_batch_run_stage", _lib.polylab_batch_run_stage(self.h, stage, _stream()))
 
-    CONFIG_KEYS = ("threads", "ctas_per_sm", "order", "term_threads", "chunks", "terms_ctas", "third_ctas",
-                   "frame_split", "third_threads")
+    CONFIG_KEYS = ("threads", "ctas_per_sm", "order", "term_threads", "terms_ctas", "third_ctas", "frame_split",
+                   "third_threads")
 
     def config(self):
         c = _BatchConfig()
         _check("polylab_batch_get_config", _lib.polylab_batch_get_config(self.h, C.byref(c)))
         return {k: getattr(c, k) for k in self.CONFIG_KEYS}
 
-    def set_config(self, threads, ctas_per_sm, order, term_threads=None, chunks=None, terms_ctas=None,
-                   third_ctas=None, frame_split=None, third_threads=None):
+    def set_config(self, threads, ctas_per_sm, order, term_threads=None, terms_ctas=None, third_ctas=None,
+                   frame_split=None, third_threads=None):
         """Keys left as None keep their current value."""
         cur = self.config()
         given = dict(threads=threads, ctas_per_sm=ctas_per_sm, order=order, term_threads=term_threads,
-                     chunks=chunks, terms_ctas=terms_ctas, third_ctas=third_ctas, frame_split=frame_split,
+                     terms_ctas=terms_ctas, third_ctas=third_ctas, frame_split=frame_split,
                      third_threads=third_threads)
         c = _BatchConfig(*[cur[k] if given[k] is None else given[k] for k in self.CONFIG_KEYS])
         _check("polylab_batch_set_config", _lib.polylab_batch_set_config(self.h, C.byref(c), _stream()))

@@ -86,38 +86,31 @@ def test_autotune_configs_agree_and_graph_replay(pl, batch_inputs):
                 close(d, r, TOL["fp64"])
     with pytest.raises(pl.PolylabError):
         b.set_config(128, 0, 1, third_threads=96)  # not a supported CTA size
-    # pipelined over three streams: chunks of the work order, per-stage caps
-    for chunks, caps in ((4, (2, 3, 2)), (7, (1, 1, 1)), (32, (0, 0, 0))):
-        b.set_config(128, caps[1], 1, term_threads=64, chunks=chunks, terms_ctas=caps[0], third_ctas=caps[2])
-        b.run()
-        b.check()
-        for d, r in zip(b.D, ref):
-            close(d, r, TOL["fp64"])
-    b.set_config(128, 0, 1, term_threads=128, chunks=1, terms_ctas=0, third_ctas=0, frame_split=1, third_threads=128)
+    b.set_config(128, 0, 1, term_threads=128, terms_ctas=2, third_ctas=3, frame_split=1, third_threads=128)
+    b.run()
+    b.check()
+    for d, r in zip(b.D, ref):
+        close(d, r, TOL["fp64"])
+    b.set_config(128, 0, 1, term_threads=128, terms_ctas=0, third_ctas=0, frame_split=1, third_threads=128)
     cfg, ms = b.autotune(reps=1)
     assert cfg["threads"] in (64, 128, 256) and ms > 0
     assert b.config() == cfg
-    # capture one run in a CUDA graph and replay it twice: the tuned
-    # configuration, then a pipelined one (side streams forked and joined
-    # inside the capture)
-    for piped in (False, True):
-        if piped:
-            b.set_config(128, 3, 1, term_threads=128, chunks=5, terms_ctas=2, third_ctas=2)
-        for d in b.D:
-            d.zero_()
-        g = torch.cuda.CUDAGraph()
-        s = torch.cuda.Stream()
-        s.wait_stream(torch.cuda.current_stream())
-        with torch.cuda.stream(s):
-            b.run()  # warm the launch path on the capture stream
-        torch.cuda.current_stream().wait_stream(s)
-        torch.cuda.synchronize()
-        for d in b.D:
-            d.zero_()
-        with torch.cuda.graph(g):
-            b.run()
-        g.replay()
-        g.replay()
-        b.check()
-        for d, r in zip(b.D, ref):
-            close(d, r, TOL["fp64"])
+    # capture one run (the tuned configuration) in a CUDA graph and replay it twice
+    for d in b.D:
+        d.zero_()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        b.run()  # warm the launch path on the capture stream
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    for d in b.D:
+        d.zero_()
+    with torch.cuda.graph(g):
+        b.run()
+    g.replay()
+    g.replay()
+    b.check()
+    for d, r in zip(b.D, ref):
+        close(d, r, TOL["fp64"])

@@ -61,7 +61,7 @@ def test_small_ragged(pl, prec):
     with pl.Plan(dp, gemm=True) as plan:
         assert plan.closure_size == closure_count(poly.exps)
         out = pl.eval_derivs(dp, torch.as_tensor(X, device="cuda"), plan=plan, prec=prec)
-        torch.cuda.synchronize()
+        pl.eval_check()  # synchronises; no bounded wait expired
     check(poly, X, out, np.arange(300), BOUND[prec])
 
 
@@ -71,8 +71,8 @@ def test_eval_batch_full_size_sampled(pl, prec):
     dp = pl.to_device(poly)
     with pl.Plan(dp, gemm=True) as plan:
         out = pl.eval_derivs(dp, torch.as_tensor(X, device="cuda"), plan=plan, prec=prec)
-        torch.cuda.synchronize()
-    idx = np.concatenate([np.random.default_rng(1).choice(X.shape[0], 10, replace=False), [0, X.shape[0] - 1]])
+        pl.eval_check()
+    idx = np.concatenate([np.random.default_rng(1).choice(X.shape[0], 254, replace=False), [0, X.shape[0] - 1]])
     check(poly, X, out, idx, BOUND[prec])
     assert torch.equal(out[2], out[2].transpose(1, 2))
 
@@ -82,7 +82,7 @@ def test_orders_and_tiny(pl, order):
     poly, X = workloads.affine_small(P=5)  # fewer points than one tile; repeated monomials
     dp = pl.to_device(poly)
     out = pl.eval_derivs(dp, torch.as_tensor(X, device="cuda"), prec="tf32x3", order=order)
-    torch.cuda.synchronize()
+    pl.eval_check()
     check(poly, X, out, np.arange(5), BOUND["tf32x3"], order)
 
 
@@ -96,5 +96,5 @@ def test_large_n_several_chunks(pl):
     with pl.Plan(dp, gemm=True) as plan:
         for prec in ("bf16", "tf32x3"):
             out = pl.eval_derivs(dp, torch.as_tensor(X, device="cuda"), plan=plan, prec=prec)
-            torch.cuda.synchronize()
+            pl.eval_check()
             check(poly, X, out, np.arange(0, 130, 13), BOUND[prec])

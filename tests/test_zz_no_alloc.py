@@ -62,3 +62,27 @@ def test_noalloc_limits(cuda_ok):
     with pytest.raises(pl.PolylabError) as ei:  # 27 distinct rows, room for 8
         pl.simplify_noalloc(pl.to_device(small), ex, co)
     assert ei.value.status == 1
+
+
+def test_noalloc_arena_overflow_then_normal_call(cuda_ok):
+    """Under the term limit but with a working set larger than the static
+    array (65,000 terms with ~47 nonzero exponents each: the nonzero lists
+    alone take about 15.5 MB of the 16 MiB, the keys 2.6 MB more): status
+    UNSUPPORTED with the array named in the message; a following call still
+    matches polylab_simplify."""
+    from paper_2604_06575_b300 import polylab as pl
+    rng = np.random.default_rng(5)
+    e = (rng.random((65000, 50)) < 0.95).astype(np.uint8)
+    wide = workloads.Poly(np.arange(50, dtype=np.uint64), e, rng.standard_normal(65000))
+    ex = torch.empty((65000, 50), dtype=torch.uint8, device="cuda")
+    co = torch.empty(65000, dtype=torch.float64, device="cuda")
+    with pytest.raises(pl.PolylabError) as ei:
+        pl.simplify_noalloc(pl.to_device(wide), ex, co)
+    assert ei.value.status == 7
+    assert "static scratch array" in pl.lib().polylab_last_error().decode()
+    p1, _ = _inputs()
+    dp = pl.to_device(p1)
+    ref = pl.simplify(dp)
+    got = pl.simplify_noalloc(dp, ex[: p1.m, : p1.n].contiguous(), co[: p1.m].contiguous())
+    assert got.m == ref.m
+    _same(got, ref, np.abs(p1.coef).sum())
