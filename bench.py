@@ -41,15 +41,16 @@ WORKLOAD = ("batched_uneven_exact: 256 convexified polys (sum x^4 + sum x^2 + 0.
 L2_FLUSH_BYTES = 256 << 20
 
 
-def _measured_bf16():
+def _measured(key: str, fallback: float) -> float:
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            return float(json.load(f)["bf16_tflops"])
+            return float(json.load(f)[key])
     except Exception:
-        return 1800.0  # the recipe's fallback figure
+        return fallback  # the profiling recipe's fallback figures
 
 
-MEASURED_BF16_TFLOPS = _measured_bf16()
+MEASURED_BF16_TFLOPS = _measured("bf16_tflops", 1800.0)
+MEASURED_HBM_GBS = _measured("hbm_gbs", 6400.0)
 
 
 def parse():
@@ -62,7 +63,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-rows", action="store_true", help="skip the per-row sub-measurements")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work per sample")
-    ap.add_argument("--forms", default="fp64,fp32", help="forms to time (profiling runs time one)")
+    ap.add_argument("--forms", default="fp64,f32x2,fp32", help="forms to time (profiling runs time one)")
     ap.add_argument("--rows-only", action="store_true", help="only the per-row measurements (profiling runs)")
     ap.add_argument("--config", default=None,
                     help="threads,ctas_per_sm,order[,term_threads,terms_ctas,third_ctas,frame_split,"
@@ -103,25 +104,46 @@ def exact_flops(poly, P: int):
 STAGE_PARTS = dict(terms=("terms",), frame=("ldlt", "inv", "small"), third=("third",))
 
 
+# A double-word multiply-add (two flops of the algorithm) costs 29 FP32
+# instructions in csrc/dfloat.cuh: the product 9 (TwoProd 2, two FMAs, one
+# multiply, one add, FastTwoSum 3), the accurate sum 20 (two TwoSums of 6,
+# two FastTwoSums of 3, two adds).  The double-word peak is the FP32 peak x 2/29.
+DW_FLOPS_PER_FP32_OP = 2.0 / 29.0
+
+
+def part_precision(form: str, part: str) -> str:
+    """Arithmetic of each part of the exact path in each form: the LDL^T is
+    FP64 in every form; the double-word form also keeps the O(n^2) frame
+    update in FP64."""
+    if form == "fp64" or part == "ldlt":
+        return "fp64"
+    if form == "f32x2":
+        return "fp64" if part == "small" else "dw"
+    return "fp32"
+
+
 def alu_roofline(flops: dict, t_s: float, form: str, p32: float, p64: float, parts=None):
-    """Op-mix ALU roofline: FP64 work at the FP64 peak, the rest at the peak
-    of the form's precision (the LDL^T is FP64 in both forms)."""
+    """Op-mix ALU roofline: every part's algorithmic flops at the peak of the
+    arithmetic it runs in (FP64, FP32, or double words on the FP32 pipe)."""
     keys = parts or tuple(flops)
-    f64 = sum(flops[k] for k in keys if form == "fp64" or k == "ldlt")
-    f32 = sum(flops[k] for k in keys) - f64
-    tot = f32 + f64
-    t_min = f32 / (p32 * 1e12) + f64 / (p64 * 1e12)
+    pk = dict(fp64=p64, fp32=p32, dw=p32 * DW_FLOPS_PER_FP32_OP)
+    by = dict(fp64=0.0, fp32=0.0, dw=0.0)
+    for k in keys:
+        by[part_precision(form, k)] += flops[k]
+    tot = sum(by.values())
+    t_min = sum(by[q] / (pk[q] * 1e12) for q in by)
     peak = tot / t_min / 1e12
     achieved = tot / t_s / 1e12
     return dict(bound="alu", achieved=round(achieved, 4), peak=round(peak, 4), unit="TFLOP/s",
                 frac=round(achieved / peak, 4), traffic=None,
-                peak_source=f"measured FMA probe: fp32 {p32:.1f} TF/s, fp64 {p64:.3f} TF/s; op mix of this form",
-                flops_fp32=f32, flops_fp64=f64)
+                peak_source=(f"measured FMA probe: fp32 {p32:.1f} TF/s, fp64 {p64:.3f} TF/s, double words "
+                             f"{pk['dw']:.2f} TF/s (fp32 x 2/29); op mix of this form"),
+                flops_fp32=by["fp32"], flops_fp64=by["fp64"], flops_dw=by["dw"])
 
 
 # ------------------------------------------------------------------ traffic
 
-EXACT_SOURCES = ("affine_exact.cu", "terms.cuh", "async.cuh", "batch.cuh", "common.cuh")
+EXACT_SOURCES = ("affine_exact.cu", "terms.cuh", "async.cuh", "batch.cuh", "common.cuh", "dfloat.cuh")
 
 
 def code_text(src: bytes) -> bytes:
@@ -145,27 +167,25 @@ def source_hash(read) -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel: str, units: int):
-    """DRAM bytes (read + write) per launch of `kernel` from a committed ncu
-    summary under profiles/ (a line `traffic: kernel=K bytes=B units=U
-    source=S`), scaled from the captured U units to `units`; None unless the
-    exact-path sources' code text still hashes to S (the counters describe
-    this code)."""
-    import glob
-    import re
-
+def profiled_traffic(kernel: str, units: int, form: str):
+    """DRAM bytes (read + write) per launch of `kernel` in `form` from the
+    committed ncu counters in profiles/traffic.json (records {kernel, form,
+    bytes, units, source, capture}), scaled from the captured units to
+    `units`; None unless the exact-path sources' code text still hashes to
+    `source` (the counters describe this code)."""
     def read(f):
         with open(os.path.join(ROOT, "paper_2604_06575_b300", "csrc", f), "rb") as fh:
             return fh.read()
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            recs = json.load(fh)
+    except (OSError, ValueError):
+        return None
     src = source_hash(read)
-    pat = re.compile(r"^traffic: kernel=(\S+) bytes=(\d+) units=(\d+) source=(\w+)\s*$")
-    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
-        with open(path) as fh:
-            for line in fh:
-                mt = pat.match(line.strip())
-                if mt and mt.group(1) == kernel and mt.group(4) == src:
-                    return dict(bytes=int(int(mt.group(2)) * units / int(mt.group(3))),
-                                captured=os.path.basename(path), captured_units=int(mt.group(3)))
+    for r in recs:
+        if r["kernel"] == kernel and r["form"] == form and r["source"] == src:
+            return dict(bytes=int(r["bytes"] * units / r["units"]), captured=r["capture"],
+                        captured_units=r["units"])
     return None
 
 
@@ -282,6 +302,23 @@ class OraclePool:
         return counts, durs, out
 
 
+def single_thread_sample(polys, Xs, order, budget_s: float, r: float = 1e-6):
+    """The oracle in this process on one thread: points taken round-robin over
+    the polynomials in ``order`` are started while less than ``budget_s``
+    seconds have passed; the last one started is finished and counted.
+    Returns (directions, seconds, {(poly, point): nu})."""
+    _pool_init()
+    out = {}
+    t0 = time.perf_counter()
+    for j in range(1 << 20):
+        for i in order:
+            if time.perf_counter() - t0 >= budget_s:
+                return len(out), time.perf_counter() - t0, out
+            if j < Xs[i].shape[0]:
+                out[(i, j)] = _oracle_point((polys[i].exps, polys[i].coef, Xs[i][j], r))
+    return len(out), time.perf_counter() - t0, out
+
+
 def sample_order(n_polys: int, seed: int):
     """A seeded random order of the polynomials (their point counts do not
     depend on their term counts, so points taken over it estimate the
@@ -359,7 +396,7 @@ def main():
     plans = [pl.Plan(d) for d in dps]
     Xd = [torch.as_tensor(X, device=dev) for X in Xs]
     npts = sum(X.shape[0] for X in Xs)
-    opts = {f: pl.an_opts(prec=f, regularization=1e-6) for f in ("fp64", "fp32")}
+    opts = {f: pl.an_opts(prec=f, regularization=1e-6) for f in ("fp64", "f32x2", "fp32")}
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -381,7 +418,7 @@ def main():
             batch.run()
         return g
 
-    forms = [f for f in ("fp64", "fp32") if f in args.forms.split(",")]
+    forms = [f for f in ("fp64", "f32x2", "fp32") if f in args.forms.split(",")]
     batches, graphs, tuned = {}, {}, {}
     for form in forms:
         batches[form] = pl.Batch(dps, plans, Xd, opts[form])
@@ -438,18 +475,29 @@ def main():
                          stage_ms=stage_times(form, args.steps))
     clk = clocks.stop()
 
-    # error of the FP32 form against the FP64 form, every point (angle, radians)
-    worst = 0.0 if len(forms) == 2 else float("nan")
-    flags_equal = len(forms) == 2
-    for i in range(len(dps) if len(forms) == 2 else 0):
-        a, b = batches["fp64"].Du[i], batches["fp32"].Du[i]
-        ok = torch.isfinite(a).all(dim=1) & torch.isfinite(b).all(dim=1)
-        flags_equal &= bool(torch.equal(torch.isfinite(a).all(dim=1), torch.isfinite(b).all(dim=1)))
-        if ok.any():
-            c = (a[ok] * b[ok]).sum(dim=1).clamp(-1, 1)
-            worst = max(worst, float(torch.arccos(c).max()))
-    FP32_BOUND = 1e-3  # stated error of the FP32-sum form (radians), checked against the FP64 form
-    chosen = "fp32" if (worst <= FP32_BOUND and flags_equal) else "fp64"
+    # error of the other forms against the FP64 form at every point: the
+    # double-word form as the relative error of nu (its bar is the FP64
+    # form's), the FP32-sum form as the angle (radians) of the unit directions
+    def vs_fp64(form):
+        worst, flags_equal = 0.0, True
+        for i in range(len(dps)):
+            a, b = batches["fp64"].D[i], batches[form].D[i]
+            fa, fb = torch.isfinite(a).all(dim=1), torch.isfinite(b).all(dim=1)
+            flags_equal &= bool(torch.equal(fa, fb))
+            ok = fa & fb
+            if ok.any():
+                if form == "f32x2":
+                    e = (b[ok] - a[ok]).norm(dim=1) / a[ok].norm(dim=1)
+                else:
+                    e = torch.arccos(torch.nn.functional.cosine_similarity(a[ok], b[ok], dim=1).clamp(-1, 1))
+                worst = max(worst, float(e.max()))
+        return worst, flags_equal
+
+    BOUND = dict(f32x2=1e-9, fp32=1e-3)  # stated bounds: relative error of nu; angle in radians
+    errs = {f: vs_fp64(f) for f in forms if f != "fp64"} if "fp64" in forms else {}
+    ok = {f: errs[f][0] <= BOUND[f] and errs[f][1] for f in errs}
+    # the headline is the fastest form held to the FP64 form's error bar
+    chosen = "f32x2" if ok.get("f32x2") and res["f32x2"]["total_ms"] < res["fp64"]["total_ms"] else "fp64"
     if len(forms) == 1:
         chosen = forms[0]
 
@@ -520,7 +568,7 @@ def main():
     dom = max(STAGES, key=lambda k: stage_ms[k])
     roof = alu_roofline(flops, stage_ms[dom] * 1e-3, chosen, p32, p64, STAGE_PARTS[dom])
     roof["kernel"] = f"{kernels[dom]} (the longest of the three stages of a step)"
-    tr = profiled_traffic(kernels[dom], npts) if chosen == "fp32" else None
+    tr = profiled_traffic(kernels[dom], npts, chosen)
     roof["traffic"] = tr["bytes"] if tr else None
     roof["traffic_note"] = (f"dram read+write per launch from {tr['captured']} ({tr['captured_units']} points), "
                             f"scaled to {npts} points" if tr else "no ncu counters for this kernel at this source")
@@ -534,20 +582,21 @@ def main():
     line = dict(metric=METRIC, value=round(rate(chosen), 1), unit="dirs/s", n_gpus=world, steps=args.steps,
                 warmup=args.warmup, ms_per_step=round(res[chosen]["total_ms"] / args.steps, 3),
                 higher_is_better=True, scaling="weak", vs_baseline=None,
-                dtype="f32 sums + f64 factorization" if chosen == "fp32" else "f64",
+                dtype={"fp64": "f64", "f32x2": "f32x2 (double-word FP32 pairs) sums + f64 factorization",
+                       "fp32": "f32 sums + f64 factorization"}[chosen],
                 data="synthetic",
                 config=dict(workload=WORKLOAD, polys=args.polys, points=npts, form=chosen,
                             regularization=1e-6, l2="flushed (256 MB write) before every timed step",
                             parallelism=f"weak: each rank its own {args.polys}-poly batch" if world > 1 else "1 GPU"),
-                forms=dict(fp64=dict(dirs_per_s=round(rate("fp64"), 1),
-                                     ms_per_step=round(res.get("fp64", {}).get("total_ms", float("nan")) / args.steps, 3),
-                                     stage_ms={k: round(v, 3) for k, v in res.get("fp64", {}).get("stage_ms", {}).items()}),
-                           fp32=dict(dirs_per_s=round(rate("fp32"), 1),
-                                     ms_per_step=round(res.get("fp32", {}).get("total_ms", float("nan")) / args.steps, 3),
-                                     stage_ms={k: round(v, 3) for k, v in res.get("fp32", {}).get("stage_ms", {}).items()},
-                                     max_angle_vs_fp64_rad=worst, stated_bound_rad=FP32_BOUND,
-                                     flags_equal=flags_equal),
-                           speedup_vs_fp64=round(rate(chosen) / rate("fp64"), 3)),
+                forms={**{f: dict(dirs_per_s=round(rate(f), 1),
+                                  ms_per_step=round(res[f]["total_ms"] / args.steps, 3),
+                                  stage_ms={k: round(v, 3) for k, v in res[f]["stage_ms"].items()},
+                                  speedup_vs_fp64=round(rate(f) / rate("fp64"), 3) if "fp64" in res else None,
+                                  **({} if f not in errs else dict(
+                                      max_err_vs_fp64=errs[f][0], err_kind=("relative |nu|" if f == "f32x2"
+                                                                            else "angle, rad"),
+                                      stated_bound=BOUND[f], flags_equal=errs[f][1])))
+                          for f in forms}},
                 e2e=dict(value=round(e2e_rate, 1), unit="dirs/s", h2d_bytes_per_step=nbytes,
                          d2h_bytes_per_step=nbytes),
                 gpu_launches=sum(launches.values()) * args.steps,
@@ -564,24 +613,27 @@ def main():
         cores = os.cpu_count() or 1
         order = sample_order(len(polys), 7)
         budget = args.cpu_budget
-        one = OraclePool(1)
-        c1, t1, ref = one.windows(polys, Xs, order, 2, budget / 2)  # the first window warms up
-        one.close()
+        small = [int(np.argmin([p.m for p in polys]))]
+        d1, t1, ref = single_thread_sample(polys, Xs, order, budget)
         alln = OraclePool(cores)
-        cn, tn, ref_n = alln.windows(polys, Xs, order, 2, budget / 2)
+        alln.windows(polys, Xs, small, 1, 1.0)
+        cn, tn, ref_n = alln.windows(polys, Xs, order, 1, budget / 2)
         alln.close()
-        d1, dn, t1, tn = c1[1], cn[1], t1[1], tn[1]
+        dn, tn = cn[0], tn[0]
         ref.update(ref_n)
         errs = []
         for (i, j), nu in ref.items():
             d = outs[chosen][i][0][j].cpu().numpy()
             if np.all(np.isfinite(nu)):
                 errs.append(float(np.linalg.norm(d - nu) / np.linalg.norm(nu)))
-        what = (f"points completed in a {budget / 2:.1f} s window after a {budget / 2:.1f} s warm-up window, taken "
-                f"round-robin over the {len(polys)} polys in a seeded random order (point j of every poly)")
+        what = (f"round-robin over the {len(polys)} polys in a seeded random order (point j of every poly), "
+                f"workers started beforehand")
         line["cpu_baseline"] = dict(value=round(dn / tn, 3), unit="dirs/s", cores=cores, kind="oracle",
-                                    sample=f"{dn} {what}, {cores} single-threaded processes",
-                                    single_thread=dict(value=round(d1 / t1, 3), cores=1, sample=f"{d1} {what}"),
+                                    sample=f"{dn} points completed in {tn:.1f} s on {cores} single-threaded "
+                                           f"processes, {what}",
+                                    single_thread=dict(value=round(d1 / t1, 3), cores=1,
+                                                       sample=f"{d1} points in {t1:.1f} s (started within "
+                                                              f"{budget:.0f} s, the last one finished), {what}"),
                                     max_rel_err_of_reported_form=max(errs) if errs else None)
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -633,9 +685,19 @@ def measure_rows(pl, workloads, torch, dev, p32, p64):
         torch.cuda.synchronize()
         ts.append((time.perf_counter() - t0) * 1e3)
     ms = statistics.median(ts)
+    # algorithmic HBM bytes: the 4M expanded (key, coefficient) items written
+    # and read once (16 + 8 bytes each) and the merged rows written (n bytes of
+    # exponents + 8 bytes of coefficient each)
+    alg = 4e6 * 24 * 2 + r.m * (r.n + 8)
     rows["mul_product_pair"] = dict(workload="2 x 2,000 terms, n=20 each, 10 shared ids, deg<=6: 4,000,000 products",
                                     ms=round(ms, 3), merged_terms=r.m,
-                                    expanded_terms_per_s=round(4e6 / (ms * 1e-3), 1))
+                                    expanded_terms_per_s=round(4e6 / (ms * 1e-3), 1),
+                                    roofline=dict(bound="hbm", achieved=round(alg / (ms * 1e-3) / 1e9, 1),
+                                                  peak=MEASURED_HBM_GBS, unit="GB/s",
+                                                  frac=round(alg / (ms * 1e-3) / 1e9 / MEASURED_HBM_GBS, 4),
+                                                  algorithmic_bytes=int(alg),
+                                                  note="wall time of the call (host synchronisations included); "
+                                                       "peak: measured copy bandwidth"))
     # derivative evaluation forms
     poly, X = workloads.eval_batch()
     dp = pl.to_device(poly, dev)
@@ -644,11 +706,24 @@ def measure_rows(pl, workloads, torch, dev, p32, p64):
     out = (torch.empty(P, dtype=torch.float64, device=dev), torch.empty(P, n, dtype=torch.float64, device=dev),
            torch.empty(P, n, n, dtype=torch.float64, device=dev))
     ev = {}
+    # error scale of every output: the sum of |term contributions|, which is
+    # f, grad f and the Hessian of the polynomial with |coefficients| at |x|
+    # (every monomial derivative is non-negative there), by the FP64 form
+    absp = pl.DevPoly(dp.var_ids, dp.exps, dp.coef.abs())
+    scale = pl.eval_derivs(absp, Xd.abs())
+    ref = tuple(t.clone() for t in pl.eval_derivs(dp, Xd))
     with pl.Plan(dp, gemm=True) as plan:
         gi = plan.gemm_info()
         for prec in ("fp64", "fp32", "tf32x3", "bf16"):
             ms = ev_time(lambda: pl.eval_derivs(dp, Xd, plan=plan, prec=prec, out=out))
             ev[prec] = dict(ms=round(ms, 3), evals_per_s=round(P / (ms * 1e-3), 1))
+            if prec != "fp64":
+                pl.eval_derivs(dp, Xd, plan=plan, prec=prec, out=out)
+                err = {name: float(((o - r_) .abs() / sc.clamp_min(1e-300)).max())
+                       for name, o, r_, sc in zip(("f", "grad", "hessian"), out, ref, scale)}
+                ev[prec]["max_err_vs_fp64_over_sum_abs_terms"] = err
+    pl.eval_check()
+    del scale, ref
     tiles = -(-P // 128)
     # tensor work the kernels issue: per 128-point tile, every live block is
     # 128 x 256 x K_block MACs (BF16 K_block 64; TF32 K_block 32, three products)
@@ -666,12 +741,89 @@ def measure_rows(pl, workloads, torch, dev, p32, p64):
                                closure_K=gi["K"], output_columns_padded=gi["Npad"], forms=ev,
                                speedup_vs_fp64={k: round(ev["fp64"]["ms"] / v["ms"], 2) for k, v in ev.items()})
     del out, Xd
+    rows["affine_small"] = measure_small(pl, workloads, torch, dev)
+    rows["exact_scaling"] = measure_exact_scaling(pl, workloads, torch, dev)
+    rows["stochastic_band"] = measure_stochastic_band(pl, workloads, torch, dev)
     rows["stochastic"] = measure_stochastic(pl, workloads, torch, dev, p32)
     rows["crossover"] = measure_crossover(pl, workloads, torch, dev)
     rows["simplify_pd_cubed"] = measure_pd3(pl, workloads, torch, dev)
     rows["affine_ad"] = measure_ad(pl, workloads, torch, dev, p64)
     rows["precision"] = measure_precision(pl, workloads, torch, dev)
     return rows
+
+
+def measure_small(pl, workloads, torch, dev):
+    """The n = 3 family (sum x^4 + sum x^2 + 0.1 x all 35 monomials of degree
+    <= 4; 1,024 shell points), exact directions in both forms, r = 1e-8, and
+    its indefinite stress variant (flags)."""
+    stream = torch.cuda.current_stream()
+    out = {}
+    for name, gen in (("affine_small", workloads.affine_small), ("affine_small_stress", workloads.affine_small_stress)):
+        poly, X = gen()
+        dp = pl.to_device(poly, dev)
+        Xd = torch.as_tensor(X, device=dev)
+        row = dict(points=X.shape[0])
+        with pl.Plan(dp) as plan:
+            for prec in ("fp64", "fp32"):
+                ms, res = _time_call(torch, lambda: pl.affine_normal(dp, Xd, plan=plan, regularization=1e-8,
+                                                                     prec=prec), stream)
+                fl = pl.info_numpy(res[2])["flags"]
+                row[prec] = dict(ms=round(ms, 4), dirs_per_s=round(X.shape[0] / (ms * 1e-3), 1),
+                                 flagged=int((fl != 0).sum()))
+        out[name] = row
+    return out
+
+
+def measure_exact_scaling(pl, workloads, torch, dev):
+    """The paper's exact-scaling family (Sec. 6, Fig. "exact"): sparse quartics
+    with support 3 and m = 4d monomials in d variables, d in {20, 40, 80, 120,
+    180, 260}, 4,096 shell points each, r = 1e-8; MF-logDet-Exact in both
+    forms (the paper reports 0.174 s per point on average for MPOLY-HP in
+    double, one point per call, on its own hardware)."""
+    stream = torch.cuda.current_stream()
+    out = {}
+    for d in (20, 40, 80, 120, 180, 260):
+        poly, X = workloads.sparse_quartic(d, 4 * d, 3, P=4096)
+        dp = pl.to_device(poly, dev)
+        Xd = torch.as_tensor(X, device=dev)
+        row = {}
+        with pl.Plan(dp) as plan:
+            for prec in ("fp64", "fp32"):
+                ms, _ = _time_call(torch, lambda: pl.affine_normal(dp, Xd, plan=plan, regularization=1e-8,
+                                                                   prec=prec), stream)
+                row[prec] = dict(ms=round(ms, 3), dirs_per_s=round(4096 / (ms * 1e-3), 1))
+        out[f"d{d}"] = row
+    return out
+
+
+def measure_stochastic_band(pl, workloads, torch, dev):
+    """The paper's stochastic-stability setting (Sec. 6, Table "stochstab": a
+    6-variable sparse quartic with 17 monomials, q = 64, maxit 80, 10 probe
+    seeds): angle of MF-logDet-Stochastic (FP64, Jacobi, tol 1e-4, r = 1e-8)
+    to MF-logDet-Exact at 4,096 points for each of 10 seeds.  The paper
+    reports 2.99 +- 1.31 degrees over its 10 seeds at its one point."""
+    stream = torch.cuda.current_stream()
+    poly, X = workloads.sparse_quartic(6, 17, 3, P=4096)
+    dp = pl.to_device(poly, dev)
+    Xd = torch.as_tensor(X, device=dev)
+    with pl.Plan(dp) as plan:
+        ex = pl.affine_normal(dp, Xd, plan=plan, regularization=1e-8)[1]
+        ang, times = [], []
+        for seed in range(10):
+            ms, res = _time_call(torch, lambda: pl.affine_normal(
+                dp, Xd, plan=plan, method="mf-stochastic", regularization=1e-8, num_probes=64, krylov_tol=1e-4,
+                krylov_maxit=80, seed=1000 + seed), stream)
+            c = (res[1] * ex).sum(1).clamp(-1, 1)
+            ang.append(torch.rad2deg(torch.arccos(c)).cpu().numpy())
+            times.append(ms)
+    A = np.stack(ang)  # seeds x points
+    per_seed = A.mean(axis=1)
+    return dict(points=4096, seeds=10, q=64, ms_per_seed=round(float(np.median(times)), 3),
+                angle_deg_mean_over_all=round(float(A.mean()), 4), angle_deg_std_over_all=round(float(A.std()), 4),
+                angle_deg_per_seed_mean=round(float(per_seed.mean()), 4),
+                angle_deg_per_seed_std=round(float(per_seed.std()), 4),
+                point0_angle_deg_over_seeds=dict(mean=round(float(A[:, 0].mean()), 4),
+                                                 std=round(float(A[:, 0].std()), 4)))
 
 
 def measure_precision(pl, workloads, torch, dev):

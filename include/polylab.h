@@ -203,8 +203,13 @@ typedef enum {
                           3xTF32 split operands, FP32 accumulation                         */
   POLYLAB_BF16 = 2,    /* same contraction in BF16 with FP32 accumulation, per-column
                           coefficient scaling                                              */
-  POLYLAB_FP32 = 3     /* FP32 direct per-term sums (affine normal: FP32 derivative sums,
+  POLYLAB_FP32 = 3,    /* FP32 direct per-term sums (affine normal: FP32 derivative sums,
                           FP64 Cholesky / log-det / normalisation)                         */
+  POLYLAB_F32X2 = 4    /* affine normal, MF_EXACT only: double-word arithmetic (pairs of
+                          FP32, ~48 significand bits, on the FP32 pipe) for the term sums,
+                          the inverse and W, with FP64 accumulation of the gradient and
+                          Hessian sums and the FP64 frame update, Cholesky / log-det and
+                          normalisation; held to the FP64 form's error bars             */
 } polylab_precision;
 
 /* f, grad f and the Hessian at P points (Sec. 3.3 differentiation and eval;
@@ -255,7 +260,7 @@ typedef struct {
   int32_t krylov_maxit;      /* stochastic only                                     */
   int32_t assume_nonzero_x;  /* skip the relative zero-gradient check               */
   uint64_t seed;             /* probe generator seed, stochastic only               */
-  polylab_precision prec;    /* POLYLAB_FP64 or POLYLAB_FP32                        */
+  polylab_precision prec;    /* POLYLAB_FP64, POLYLAB_FP32, or POLYLAB_F32X2 (MF_EXACT) */
   polylab_precond precond;   /* stochastic only                                     */
   const void* mlp_weights;   /* DEVICE, POLYLAB_PRECOND_MLP only                    */
 } polylab_an_opts;
@@ -298,21 +303,25 @@ polylab_status polylab_affine_normal(const polylab_poly* p, const polylab_plan* 
 /* A small network mapping per-coordinate Hessian features of a point to a
  * diagonal-plus-low-rank preconditioner Pi (D + U U^T) Pi for the Krylov
  * solves of POLYLAB_MF_STOCHASTIC (this library's addition; the paper uses
- * plain Krylov solves).  Features of coordinate i:
- *   [log(|H_ii| + r), log(sum_{j != i} sum_t |d_i d_j t(x)| + r), x_i, n e_i^2, log(|g_i| + 1e-30)];
- * network 5 -> 32 (tanh) -> 3; D_i = exp(clip(o_0, -5, 5)) / (|H_ii| + r),
- * U_ik = 0.1 o_k / sqrt(|H_ii| + r).  Zero output weights reproduce Jacobi.
- * Parameters: POLYLAB_MLP_PARAMS floats (W1 5x32 row-major, b1, W2 32x3, b2).
+ * plain Krylov solves).  Features of coordinate i, with a_i = |H_ii| + r:
+ *   [log(a_i), log(sum_{j != i} sum_t |d_i d_j t(x)| + r), x_i, n e_i^2,
+ *    log(|g_i| + 1e-30), sum_{j != i} H_ij / a_i, sum_{j != i} H_ij / a_j];
+ * network 7 -> 32 (tanh) -> 3; D_i = exp(clip(o_0, -5, 5)) / a_i,
+ * U_ik = 0.1 o_k / sqrt(a_i).  Zero output weights reproduce Jacobi.
+ * Parameters: POLYLAB_MLP_PARAMS floats (W1 7x32 row-major, b1, W2 32x3, b2).
  * Inference uses a BF16 copy (polylab_mlp_pack) passed as opts.mlp_weights. */
-#define POLYLAB_MLP_PARAMS 291
-#define POLYLAB_MLP_FEATURES 5
+#define POLYLAB_MLP_PARAMS 355
+#define POLYLAB_MLP_FEATURES 7
 #define POLYLAB_MLP_PROBES 4
 
 int32_t polylab_mlp_param_count(void);
-/* W1 uniform in +-1/sqrt(5) from SplitMix64(seed), everything else 0. DEVICE params. */
+/* W1 uniform in +-1/sqrt(7) and the low-rank outputs' weights (W2 columns
+ * 1, 2) uniform in +-0.05, from SplitMix64(seed); everything else 0, so D
+ * starts at Jacobi (U = 0 would be a stationary point of the loss).  DEVICE
+ * params. */
 polylab_status polylab_mlp_init(float* params, uint64_t seed, polylab_stream stream);
 /* Training data generated by the method itself at P points: per point,
- * feats (DEVICE P x n x 5), hdiag = H_ii (P x n), e = g/|g| (P x n), and
+ * feats (DEVICE P x n x 7), hdiag = H_ii (P x n), e = g/|g| (P x n), and
  * POLYLAB_MLP_PROBES probe pairs z_k = Pi w_k (Rademacher w_k from
  * SplitMix64(seed), probe index p*4 + k, the probe convention of the
  * stochastic method) and y_k = Pi (H + rI) z_k, stored Z, Y (P x n x 4).
@@ -321,15 +330,15 @@ polylab_status polylab_mlp_data(const polylab_poly* p, const polylab_plan* plan,
                                 double regularization, uint64_t seed, float* feats, float* hdiag, float* e,
                                 float* Z, float* Y, polylab_stream stream);
 /* Mean over points and probes of |Pi (D y + U U^T y) - z|^2 / |z|^2 and its
- * gradient (hand-written backpropagation).  grad: DEVICE 291 floats, loss:
+ * gradient (hand-written backpropagation).  grad: DEVICE 355 floats, loss:
  * DEVICE 1 float, both overwritten. */
 polylab_status polylab_mlp_loss_grad(const float* params, int64_t P, int32_t n, const float* feats,
                                      const float* hdiag, const float* e, const float* Z, const float* Y,
                                      double regularization, float* grad, float* loss, polylab_stream stream);
-/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8); m, v: DEVICE 291 floats, zero at step 1. */
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8); m, v: DEVICE 355 floats, zero at step 1. */
 polylab_status polylab_mlp_adam(float* params, const float* grad, float* m, float* v, int32_t step, float lr,
                                 polylab_stream stream);
-/* BF16 copy of the parameters for inference (DEVICE, 291 x 2 bytes). */
+/* BF16 copy of the parameters for inference (DEVICE, 355 x 2 bytes). */
 polylab_status polylab_mlp_pack(const float* params, void* packed, polylab_stream stream);
 
 /* ------------------------------------------- batched exact directions (one graph) */
@@ -350,7 +359,7 @@ polylab_status polylab_mlp_pack(const float* params, void* packed, polylab_strea
  * into a CUDA graph and replayed.  Each run overwrites
  * D[i], Dunit[i] (DEVICE P[i] x n_i or NULL) and info[i] (DEVICE P[i] records
  * or NULL) from X[i] (DEVICE P[i] x n_i).  opts->method must be
- * POLYLAB_MF_EXACT; opts->prec POLYLAB_FP64 or POLYLAB_FP32.  The arrays of
+ * POLYLAB_MF_EXACT; opts->prec POLYLAB_FP64, POLYLAB_FP32 or POLYLAB_F32X2.  The arrays of
  * pointers passed to create are read during the call only. */
 typedef struct polylab_batch polylab_batch;
 

@@ -6,9 +6,14 @@ The paper is silent on learned preconditioners; this network is the
 project's own design, and this module is its plain definition:
 
 * per-coordinate features of a point x (H = Hessian, g = gradient,
-  e = g/|g|, r = regularisation, S_ij = sum over terms of |term's d_i d_j|):
-      f_i = [log(|H_ii| + r), log(sum_{j != i} S_ij + r), x_i, n e_i^2,
-             log(|g_i| + 1e-30)]
+  e = g/|g|, r = regularisation, S_ij = sum over terms of |term's d_i d_j|,
+  a_i = |H_ii| + r):
+      f_i = [log(a_i), log(sum_{j != i} S_ij + r), x_i, n e_i^2,
+             log(|g_i| + 1e-30), sum_{j != i} H_ij / a_i,
+             sum_{j != i} H_ij / a_j]
+  (the last two are signed: couplings of one sign that many coordinates
+  share -- a collective mode of the Hessian -- show there, while couplings of
+  random sign cancel);
 * one MLP shared by all coordinates: h = tanh(W1^T f + b1) (32 units),
   o = W2^T h + b2 (3 outputs);
 * preconditioner M = Pi (D + U U^T) Pi, Pi = I - e e^T, with
@@ -25,7 +30,7 @@ from __future__ import annotations
 
 import numpy as np
 
-F = 5
+F = 7
 HD = 32
 NO = 3
 RANK = NO - 1
@@ -48,10 +53,12 @@ def unpack(theta: np.ndarray):
 def features(H: np.ndarray, SH: np.ndarray, g: np.ndarray, x: np.ndarray, r: float) -> np.ndarray:
     """SH: per-entry sums of |term contributions| to H (``derivs.eval_derivs``)."""
     n = x.shape[0]
-    d = np.abs(np.diag(H))
+    a = np.abs(np.diag(H)) + r
     off = SH.sum(axis=1) - np.diag(SH)
     e = g / np.linalg.norm(g)
-    return np.column_stack([np.log(d + r), np.log(off + r), x, n * e * e, np.log(np.abs(g) + 1e-30)])
+    Hoff = H - np.diag(np.diag(H))
+    return np.column_stack([np.log(a), np.log(off + r), x, n * e * e, np.log(np.abs(g) + 1e-30),
+                            Hoff.sum(axis=1) / a, Hoff @ (1.0 / a)])
 
 
 def forward(theta, f):

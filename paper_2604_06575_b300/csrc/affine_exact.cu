@@ -39,11 +39,59 @@
 #include "async.cuh"
 #include "batch.cuh"
 #include "common.cuh"
+#include "dfloat.cuh"
 #include "terms.cuh"
 
 namespace polylab {
 
 namespace {
+
+// Types of a form.  R: the arithmetic of the term sweeps, the frame update
+// and the inverse; Acc: the sums of gradient and Hessian contributions
+// (added atomically in shared memory) and the matrix H handed to the frame
+// stage; Abs: sums of |contributions| (an error scale only).  The
+// double-word form (R = dfloat) sums into FP64 accumulators.
+template <typename R>
+struct FormTypes {
+  using Acc = R;
+  using Abs = R;
+};
+template <>
+struct FormTypes<dfloat> {
+  using Acc = double;
+  using Abs = float;
+};
+template <typename R>
+using AccOf = typename FormTypes<R>::Acc;
+template <typename R>
+using AbsOf = typename FormTypes<R>::Abs;
+
+// Sum of one run of gather records c_r * m_t (the contributions to one
+// gradient or Hessian entry) in the form's arithmetic, and the magnitude of
+// one contribution (for the error scale).  Double words use the compensated
+// running sum of dfloat.cuh.
+template <typename R>
+struct RunSum {
+  R v = R(0);
+  __device__ __forceinline__ void add(R m, SmallOf<R> cf) { v += m * cf; }
+  __device__ __forceinline__ AccOf<R> value() const { return AccOf<R>(v); }
+};
+template <>
+struct RunSum<dfloat> : dw_run_sum {};
+template <typename R>
+__device__ __forceinline__ AbsOf<R> contrib_abs(R m, SmallOf<R> cf) {
+  return AbsOf<R>(fabs(m * cf));
+}
+template <>
+__device__ __forceinline__ float contrib_abs<dfloat>(dfloat m, float cf) {
+  return fabsf(m.hi * cf);
+}
+
+template <typename T>
+__device__ __forceinline__ T shfl_r(T v, int src) {
+  return __shfl_sync(0xffffffffu, v, src);
+}
+__device__ __forceinline__ dfloat shfl_r(dfloat v, int src) { return shfl(v, src); }
 
 // Per-point record of small vectors in the workspace (doubles):
 // [0,n) g | [n,2n) v | [2n,3n) e | [3n,4n) h | 4n: sum |g terms| | 4n+1: |g|
@@ -280,7 +328,7 @@ struct Bump {
 
 struct Lay1 {
   size_t pw, g, red, ix, gs, ga, mv, H, total;
-  size_t pw_step, ix_step, mv_step, H_step;  // offset between the two points' arrays
+  size_t pw_step, ix_step, gs_step, ga_step, mv_step, H_step;  // offset between the two points' arrays
 };
 // Term sweep of up to kTermPoints points of one polynomial per CTA: power
 // tables, gather sums and monomial values (gather form) and H slots (in
@@ -291,21 +339,25 @@ struct Lay1 {
 constexpr int kTermPoints = 2;
 template <typename R, int NW>
 __host__ __device__ Lay1 lay_terms(int n, int E1, bool in_smem, bool gather) {
+  using Acc = AccOf<R>;
+  using Abs = AbsOf<R>;
   Lay1 L{};
   Bump b;
   L.pw_step = ((size_t)n * E1 * sizeof(R) + 15) & ~size_t(15);
   L.pw = b.take(kTermPoints * L.pw_step);
-  L.g = b.take((size_t)NW * n * sizeof(R));  // one replica per warp
+  L.g = b.take((size_t)NW * n * sizeof(Acc));  // one replica per warp
   L.red = b.take(kTermPoints * 40 * 8);
   if (gather) {
     L.ix_step = ((size_t)n * sizeof(R) + 15) & ~size_t(15);
+    L.gs_step = ((size_t)n * sizeof(Acc) + 15) & ~size_t(15);
+    L.ga_step = ((size_t)n * sizeof(Abs) + 15) & ~size_t(15);
     L.ix = b.take(kTermPoints * L.ix_step);
-    L.gs = b.take(kTermPoints * L.ix_step);
-    L.ga = b.take(kTermPoints * L.ix_step);
+    L.gs = b.take(kTermPoints * L.gs_step);
+    L.ga = b.take(kTermPoints * L.ga_step);
     L.mv_step = (size_t)kGatherChunk * sizeof(R);
     L.mv = b.take(kTermPoints * L.mv_step);
   }
-  L.H_step = (size_t)mat_slot<R>(n) * sizeof(R);
+  L.H_step = (size_t)mat_slot<Acc>(n) * sizeof(Acc);
   L.H = in_smem ? b.take(kTermPoints * L.H_step) : 0;
   L.total = b.o;
   return L;
@@ -360,7 +412,7 @@ __host__ __device__ Lay3 lay_third(int n, int E1, bool in_smem) {
   Lay3 L{};
   Bump b;
   L.pw = b.take((size_t)n * E1 * sizeof(R));
-  L.c = b.take((size_t)NW * n * sizeof(R));  // one replica per warp
+  L.c = b.take((size_t)NW * n * sizeof(AccOf<R>));  // one replica per warp
   L.v = b.take(n * 8);
   L.e = b.take(n * 8);
   L.y = b.take(n * 8);
@@ -377,10 +429,10 @@ struct StageArgs {
   int n_desc;
   const int64_t* prefix;
   const int* order;
-  int64_t item_begin, item_end;  // this launch's chunk of the work order
+  int64_t item_begin, item_end;  // this launch's range of the work order
   int* counter;
-  R* mats_h;  // per point n x n: H (stage 1 -> 2)
-  R* mats_w;  // per point n x n: W (stage 2 -> 3)
+  AccOf<R>* mats_h;  // per point n x n: H (stage 1 -> 2)
+  R* mats_w;         // per point n x n: W (stage 2 -> 3)
   double* vecs;
   double r;
   int assume_nonzero_x;
@@ -419,6 +471,8 @@ __device__ __forceinline__ void write_failed(const ExactDesc& pd, int64_t p, int
 // one after another (a pair that straddles two polynomials in two passes).
 template <typename R, int NT>
 __global__ void __launch_bounds__(NT) exact_terms_kernel(StageArgs<R> a) {
+  using Acc = AccOf<R>;
+  using Abs = AbsOf<R>;
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ int64_t s_item;
   constexpr int NW = NT / 32;
@@ -438,13 +492,13 @@ __global__ void __launch_bounds__(NT) exact_terms_kernel(StageArgs<R> a) {
       const Lay1 L = lay_terms<R, NW>(n, E1, pd.h_in_smem, pd.gather != nullptr);
       auto pw_of = [&](int q) { return (R*)(sm + L.pw + q * L.pw_step); };
       auto ix_of = [&](int q) { return (R*)(sm + L.ix + q * L.ix_step); };
-      auto gs_of = [&](int q) { return (R*)(sm + L.gs + q * L.ix_step); };
-      auto ga_of = [&](int q) { return (R*)(sm + L.ga + q * L.ix_step); };
+      auto gs_of = [&](int q) { return (Acc*)(sm + L.gs + q * L.gs_step); };
+      auto ga_of = [&](int q) { return (Abs*)(sm + L.ga + q * L.ga_step); };
       auto mv_of = [&](int q) { return (R*)(sm + L.mv + q * L.mv_step); };
-      auto Hg_of = [&](int q) { return a.mats_h + pd.mat_off + (p0 + q) * mat_slot<R>(n); };
-      auto Hr_of = [&](int q) { return pd.h_in_smem ? (R*)(sm + L.H + q * L.H_step) : Hg_of(q); };
+      auto Hg_of = [&](int q) { return a.mats_h + pd.mat_off + (p0 + q) * mat_slot<Acc>(n); };
+      auto Hr_of = [&](int q) { return pd.h_in_smem ? (Acc*)(sm + L.H + q * L.H_step) : Hg_of(q); };
       auto rec_of = [&](int q) { return a.vecs + pd.vec_off + (p0 + q) * vrec(n); };
-      R* g = (R*)(sm + L.g);
+      Acc* g = (Acc*)(sm + L.g);
       double* red = (double*)(sm + L.red);
       bool in_range = true;
       for (int i = tid; i < np * n; i += NT) {
@@ -457,23 +511,23 @@ __global__ void __launch_bounds__(NT) exact_terms_kernel(StageArgs<R> a) {
         if (gather) {
           for (int i = tid; i < n; i += NT) {
             ix_of(q)[i] = R(1) / R(X[i]);
-            gs_of(q)[i] = R(0);
-            ga_of(q)[i] = R(0);
+            gs_of(q)[i] = Acc(0);
+            ga_of(q)[i] = Abs(0);
           }
         }
         power_table<R, NT>(X, n, E1, pw_of(q));
-        R* Hr = Hr_of(q);
-        for (int64_t i = tid; i < mat_slot<R>(n); i += NT) Hr[i] = R(0);
+        Acc* Hr = Hr_of(q);
+        for (int64_t i = tid; i < mat_slot<Acc>(n); i += NT) Hr[i] = Acc(0);
       }
       __syncthreads();
-      R gabs[kTermPoints] = {};  // this thread's share of sum |gradient contributions|, per point
+      Abs gabs[kTermPoints] = {};  // this thread's share of sum |gradient contributions|, per point
       if (gather) {
         // one pass over terms and records for NP points
         auto sweep = [&](auto np_c) {
           constexpr int NP = decltype(np_c)::value;
-          R* Hr[NP];
-          R* gs[NP];
-          R* ga[NP];
+          Acc* Hr[NP];
+          Acc* gs[NP];
+          Abs* ga[NP];
           const R* mv[NP];
   #pragma unroll
           for (int q = 0; q < NP; ++q) {
@@ -482,15 +536,15 @@ __global__ void __launch_bounds__(NT) exact_terms_kernel(StageArgs<R> a) {
             ga[q] = ga_of(q);
             mv[q] = mv_of(q);
           }
-          auto flush = [&](int e, const R* acc, const R* aacc) {
+          auto flush = [&](int e, const RunSum<R>* acc, const Abs* aacc) {
             if (e < 0 || e == (int)kGatherPad) return;  // nothing yet, or padding
   #pragma unroll
             for (int q = 0; q < NP; ++q) {
               if (e >= nn) {
-                atomicAdd(&gs[q][e - nn], acc[q]);
+                atomicAdd(&gs[q][e - nn], acc[q].value());
                 atomicAdd(&ga[q][e - nn], aacc[q]);
               } else {
-                atomicAdd(&Hr[q][e], acc[q]);
+                atomicAdd(&Hr[q][e], acc[q].value());
               }
             }
           };
@@ -507,7 +561,8 @@ __global__ void __launch_bounds__(NT) exact_terms_kernel(StageArgs<R> a) {
             const uint32_t* recs = pd.gather + r0;
             for (int st = tid; st < kGatherStreams; st += NT) {
               int cur = -1;
-              R acc[NP] = {}, aacc[NP] = {};
+              RunSum<R> acc[NP];
+              Abs aacc[NP] = {};
               for (int k = 0; k < Lc; k += kGatherUnroll) {
                 uint32_t rr[kGatherUnroll];
   #pragma unroll
@@ -515,19 +570,22 @@ __global__ void __launch_bounds__(NT) exact_terms_kernel(StageArgs<R> a) {
   #pragma unroll
                 for (int u = 0; u < kGatherUnroll; ++u) {
                   const int e = (int)((rr[u] >> 11) & 0x3fffu);
-                  const R cf = R(rr[u] >> 25);
+                  const SmallOf<R> cf = SmallOf<R>(rr[u] >> 25);  // falling-factorial coefficient <= 127
                   const int tt = (int)(rr[u] & 0x7ffu);
                   if (e != cur) {
                     flush(cur, acc, aacc);
                     cur = e;
   #pragma unroll
-                    for (int q = 0; q < NP; ++q) acc[q] = aacc[q] = R(0);
+                    for (int q = 0; q < NP; ++q) {
+                      acc[q] = RunSum<R>();
+                      aacc[q] = Abs(0);
+                    }
                   }
   #pragma unroll
                   for (int q = 0; q < NP; ++q) {
-                    const R v = cf * mv[q][tt];
-                    acc[q] += v;
-                    aacc[q] += fabs(v);
+                    const R mq = mv[q][tt];
+                    acc[q].add(mq, cf);
+                    aacc[q] += contrib_abs<R>(mq, cf);
                   }
                 }
               }
@@ -539,30 +597,30 @@ __global__ void __launch_bounds__(NT) exact_terms_kernel(StageArgs<R> a) {
         if (np == 2) sweep(std::integral_constant<int, 2>{});
         else sweep(std::integral_constant<int, 1>{});
         for (int q = 0; q < np; ++q) {
-          R* Hr = Hr_of(q);
+          Acc* Hr = Hr_of(q);
           const R* ix = ix_of(q);
           for (int i = wid; i < n; i += NW)
-            for (int j = i + lane; j < n; j += 32) Hr[i * n + j] *= ix[i] * ix[j];
+            for (int j = i + lane; j < n; j += 32) Hr[i * n + j] = Acc(R(Hr[i * n + j]) * ix[i] * ix[j]);
           double* rec = rec_of(q);
           for (int i = tid; i < n; i += NT) {
-            rec[i] = (double)(gs_of(q)[i] * ix[i]);
-            gabs[q] += ga_of(q)[i] * fabs(ix[i]);
+            rec[i] = (double)(R(gs_of(q)[i]) * ix[i]);
+            gabs[q] += ga_of(q)[i] * Abs(fabs(ix[i]));
           }
         }
       } else {
         for (int q = 0; q < np; ++q) {
-          for (int i = tid; i < NW * n; i += NT) g[i] = R(0);
+          for (int i = tid; i < NW * n; i += NT) g[i] = Acc(0);
           __syncthreads();
-          R* gw = g + wid * n;
-          R* Hr = Hr_of(q);
+          Acc* gw = g + wid * n;
+          Acc* Hr = Hr_of(q);
           const R* pw = pw_of(q);
-          R ga = R(0);
+          Abs ga = Abs(0);
           auto emit = [&](int kind, int i, int j, R val) {
             if (kind == 1) {
-              atomicAdd(&gw[i], val);
-              ga += fabs(val);
+              atomicAdd(&gw[i], Acc(val));
+              ga += Abs(fabs(val));
             } else if (kind == 2) {
-              atomicAdd(&Hr[i * n + j], val);
+              atomicAdd(&Hr[i * n + j], Acc(val));
             }
           };
           // one loop per support-size group: inside each loop the support size
@@ -577,7 +635,7 @@ __global__ void __launch_bounds__(NT) exact_terms_kernel(StageArgs<R> a) {
           __syncthreads();
           double* rec = rec_of(q);
           for (int i = tid; i < n; i += NT) {
-            R sum = g[i];
+            Acc sum = g[i];
             for (int w = 1; w < NW; ++w) sum += g[w * n + i];
             rec[i] = (double)sum;
           }
@@ -586,7 +644,7 @@ __global__ void __launch_bounds__(NT) exact_terms_kernel(StageArgs<R> a) {
         }
       }
       for (int q = 0; q < np; ++q) {
-        const R gq = warp_sum(gabs[q]);
+        const Abs gq = warp_sum(gabs[q]);
         if (lane == 0) red[q * 40 + wid] = (double)gq;
       }
       __syncthreads();
@@ -600,7 +658,7 @@ __global__ void __launch_bounds__(NT) exact_terms_kernel(StageArgs<R> a) {
       // next pair
       if (pd.h_in_smem && tid == 0) {
         fence_proxy_async_smem();
-        for (int q = 0; q < np; ++q) bulk_s2g(Hg_of(q), Hr_of(q), (uint32_t)(mat_slot<R>(n) * sizeof(R)));
+        for (int q = 0; q < np; ++q) bulk_s2g(Hg_of(q), Hr_of(q), (uint32_t)(mat_slot<Acc>(n) * sizeof(Acc)));
         bulk_commit();
         bulk_wait_read();
       }
@@ -619,7 +677,12 @@ __global__ void __launch_bounds__(NT) exact_terms_kernel(StageArgs<R> a) {
 template <typename R, int NT, bool SMEM>
 __device__ __forceinline__ bool frame_item(const StageArgs<R>& a, const ExactDesc& pd, int64_t p, unsigned char* sm,
                                            int& s_flag, double* s_sc, uint64_t& s_bar, uint32_t& phase) {
+  // kF64: the factor is formed in place in the 8-byte matrix (FP64 and
+  // double-word forms); kDW: double-word form, whose H and frame update are
+  // FP64 (H arrives as FP64 sums) and whose inverse and W are double words
   constexpr bool kF64 = sizeof(R) == 8;
+  constexpr bool kDW = std::is_same<R, dfloat>::value;
+  using Rh = std::conditional_t<kDW, double, R>;
   constexpr int NW = NT / 32;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int n = pd.n, m = n - 1, nn = n * n, xs = x_stride(m);
@@ -630,11 +693,16 @@ __device__ __forceinline__ bool frame_item(const StageArgs<R>& a, const ExactDes
   double* dv = (double*)(sm + L.dv);
   double* di = (double*)(sm + L.di);
   double* uc = (double*)(sm + L.uc);
-  R* vr = (R*)(sm + L.vr);
-  R* u = (R*)(sm + L.u);
-  R* w = (R*)(sm + L.w);
+  Rh* vr = (Rh*)(sm + L.vr);
+  Rh* u = (Rh*)(sm + L.u);
+  Rh* w = (Rh*)(sm + L.w);
   unsigned char* gb = a.gws + (size_t)blockIdx.x * a.gws_stride;
-  R* Hr = SMEM ? (R*)(sm + L.Hr) : (R*)gb;
+  Rh* Hr = SMEM ? (Rh*)(sm + L.Hr) : (Rh*)gb;
+  // the same storage in the form's precision R (after the factorisation)
+  R* HrR = reinterpret_cast<R*>(Hr);
+  R* vrR = reinterpret_cast<R*>(vr);
+  R* uR = reinterpret_cast<R*>(u);
+  R* wR = reinterpret_cast<R*>(w);
   unsigned char* rest = SMEM ? nullptr : gb + (size_t)mat_slot<R>(n) * sizeof(R);
   // FP64 factor storage, element (i, j) of the leading block at col(j)[i]:
   // in place in Hr (col(j) = row j of the symmetric Hr) for the FP64 form, a
@@ -645,7 +713,7 @@ __device__ __forceinline__ bool frame_item(const StageArgs<R>& a, const ExactDes
   auto col = [Ld, n, m](int j) -> double* {
     return kF64 ? Ld + (size_t)j * n : Ld + ((size_t)j * m - (size_t)j * (j - 1) / 2 - j);
   };
-  const R* Hg = a.mats_h + pd.mat_off + p * mat_slot<R>(n);
+  const Rh* Hg = reinterpret_cast<const Rh*>(a.mats_h + pd.mat_off + p * mat_slot<R>(n));
   R* Wg = a.mats_w + pd.mat_off + p * mat_slot<R>(n);
   const uint32_t mat_bytes = (uint32_t)(mat_slot<R>(n) * sizeof(R));
   double* rec = a.vecs + pd.vec_off + p * vrec(n);
@@ -678,7 +746,7 @@ __device__ __forceinline__ bool frame_item(const StageArgs<R>& a, const ExactDes
         const double ei = rec[i] * ign;
         e[i] = ei;
         v[i] = ei + (i == n - 1 ? sgn : 0.0);
-        vr[i] = R(v[i]);
+        vr[i] = Rh(v[i]);
       }
     }
     if (lane == 0) {
@@ -711,7 +779,7 @@ __device__ __forceinline__ bool frame_item(const StageArgs<R>& a, const ExactDes
     return true;
   }
   for (int i = tid; i < n; i += NT) {  // u = H v (H symmetric: column access, conflict-free)
-    R acc = R(0);
+    Rh acc = Rh(0);
     for (int j = 0; j < n; ++j) acc += Hr[j * n + i] * vr[j];
     u[i] = acc;
   }
@@ -720,7 +788,7 @@ __device__ __forceinline__ bool frame_item(const StageArgs<R>& a, const ExactDes
     double part = 0.0;
     for (int i = lane; i < n; i += 32) part += v[i] * (double)u[i];
     const double gamma = warp_sum(part);
-    for (int i = lane; i < n; i += 32) w[i] = R(beta * (double)u[i] - 0.5 * beta * beta * gamma * v[i]);
+    for (int i = lane; i < n; i += 32) w[i] = Rh(beta * (double)u[i] - 0.5 * beta * beta * gamma * v[i]);
   }
   __syncthreads();
   for (int i = wid; i < n; i += NW)  // P H P = H - v w^T - w v^T
@@ -749,7 +817,7 @@ __device__ __forceinline__ bool frame_item(const StageArgs<R>& a, const ExactDes
   }
   // log-det (warp 0) while the others take the factor into the form's
   // precision: Lt(i, j) = Hr[j*n + i] = l_ij (i > j); sq = d^{-1/2}
-  R* sq = w;
+  R* sq = wR;
   if (wid == 0) {
     double lsum = 0.0;
     for (int k = lane; k < m; k += 32) lsum += log(dv[k]);
@@ -760,6 +828,11 @@ __device__ __forceinline__ bool frame_item(const StageArgs<R>& a, const ExactDes
   if constexpr (!kF64) {  // (the factor's storage becomes X after the next barrier)
     for (int j = wid; j < m; j += NW)
       for (int i = j + 1 + lane; i < m; i += 32) Hr[j * n + i] = (R)col(j)[i];
+  }
+  if constexpr (kDW) {  // FP64 factor -> double words, element by element in place
+    for (int j = wid; j < m; j += NW)
+      for (int i = j + 1 + lane; i < m; i += 32) HrR[j * n + i] = R(col(j)[i]);
+    for (int i = tid; i < n; i += NT) vrR[i] = R(v[i]);  // (vr's FP64 copy is no longer needed)
   }
   __syncthreads();  // L in the form's precision and sq complete
   // X' = D^{-1/2} X with X = L^{-1} (unit lower), stored transposed:
@@ -775,13 +848,13 @@ __device__ __forceinline__ bool frame_item(const StageArgs<R>& a, const ExactDes
       R a0 = r0 == ja ? R(1) : R(0), a1 = r1 == ja ? R(1) : R(0);
       R b0 = r0 == jb ? R(1) : R(0), b1 = r1 == jb ? R(1) : R(0);
       for (int k = ja; k + 1 < m; ++k) {
-        const R l0 = (r0 > k && r0 < m) ? Hr[k * n + r0] : R(0);
-        const R l1 = (r1 > k && r1 < m) ? Hr[k * n + r1] : R(0);
-        const R xa = __shfl_sync(0xffffffffu, k < 32 ? a0 : a1, k & 31);
+        const R l0 = (r0 > k && r0 < m) ? HrR[k * n + r0] : R(0);
+        const R l1 = (r1 > k && r1 < m) ? HrR[k * n + r1] : R(0);
+        const R xa = shfl_r(k < 32 ? a0 : a1, k & 31);
         a0 -= l0 * xa;
         a1 -= l1 * xa;
         if (k >= jb) {  // column jb is zero above row jb
-          const R xb = __shfl_sync(0xffffffffu, k < 32 ? b0 : b1, k & 31);
+          const R xb = shfl_r(k < 32 ? b0 : b1, k & 31);
           b0 -= l0 * xb;
           b1 -= l1 * xb;
         }
@@ -804,7 +877,7 @@ __device__ __forceinline__ bool frame_item(const StageArgs<R>& a, const ExactDes
       // thread tid starts at q = tid = j * rows + i0 and steps by NT
       const int dj = NT / rows, di0 = NT - dj * rows;
       int j = tid / rows, i0 = tid - j * rows;
-      const R* lk = Hr + k * n + k + 1;
+      const R* lk = HrR + k * n + k + 1;
       while (j <= k) {
         Xs[j * xs + k + 1 + i0] -= lk[i0] * Xs[j * xs + k];
         j += dj;
@@ -825,27 +898,27 @@ __device__ __forceinline__ bool frame_item(const StageArgs<R>& a, const ExactDes
     for (int j = i + lane; j < m; j += 32) {
       R acc = R(0);
       for (int k = j; k < m; ++k) acc += Xs[i * xs + k] * Xs[j * xs + k];
-      Hr[i * n + j] = acc;
+      HrR[i * n + j] = acc;
     }
   __syncthreads();
   for (int i = wid; i < n; i += NW)  // Hr <- [M 0; 0 0], full symmetric, in place
     for (int j = lane; j < n; j += 32) {
-      if (i == n - 1 || j == n - 1) Hr[i * n + j] = R(0);
-      else if (i > j) Hr[i * n + j] = Hr[j * n + i];
+      if (i == n - 1 || j == n - 1) HrR[i * n + j] = R(0);
+      else if (i > j) HrR[i * n + j] = HrR[j * n + i];
     }
   __syncthreads();
   for (int i = tid; i < n; i += NT) {  // u = [M 0; 0 0] v
     R acc = R(0);
-    for (int j = 0; j < n; ++j) acc += Hr[j * n + i] * vr[j];
-    u[i] = acc;
+    for (int j = 0; j < n; ++j) acc += HrR[j * n + i] * vrR[j];
+    uR[i] = acc;
   }
   __syncthreads();
   if (wid == 0) {
     double part = 0.0;
-    for (int i = lane; i < n; i += 32) part += v[i] * (double)u[i];
+    for (int i = lane; i < n; i += 32) part += v[i] * (double)uR[i];
     const double gam2 = warp_sum(part);
     for (int i = lane; i < n; i += 32) {
-      w[i] = R(beta * (double)u[i] - 0.5 * beta * beta * gam2 * v[i]);
+      wR[i] = R(beta * (double)uR[i] - 0.5 * beta * beta * gam2 * v[i]);
       rec[n + i] = v[i];
       rec[2 * n + i] = e[i];
       rec[3 * n + i] = h[i];
@@ -860,17 +933,17 @@ __device__ __forceinline__ bool frame_item(const StageArgs<R>& a, const ExactDes
   __syncthreads();
   if (SMEM) {  // W = P [M 0; 0 0] P in place, then one bulk copy out
     for (int i = wid; i < n; i += NW)
-      for (int j = lane; j < n; j += 32) Hr[i * n + j] -= vr[i] * w[j] + w[i] * vr[j];
+      for (int j = lane; j < n; j += 32) HrR[i * n + j] -= vrR[i] * wR[j] + wR[i] * vrR[j];
     __syncthreads();
     if (tid == 0) {
       fence_proxy_async_smem();
-      bulk_s2g(Wg, Hr, mat_bytes);
+      bulk_s2g(Wg, HrR, mat_bytes);
       bulk_commit();
       bulk_wait_read();
     }
   } else {
     for (int i = wid; i < n; i += NW)
-      for (int j = lane; j < n; j += 32) Wg[i * n + j] = Hr[i * n + j] - (vr[i] * w[j] + w[i] * vr[j]);
+      for (int j = lane; j < n; j += 32) Wg[i * n + j] = HrR[i * n + j] - (vrR[i] * wR[j] + wR[i] * vrR[j]);
   }
   return true;
 }
@@ -903,7 +976,9 @@ __global__ void __launch_bounds__(NT) exact_frame_kernel(StageArgs<R> a) {
 
 // ------------------------------------------------------------------ stage 3
 template <typename R, int NT>
-__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 1024 / NT : 1) exact_third_kernel(StageArgs<R> a) {
+__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 1024 / NT : std::is_same<R, dfloat>::value ? 512 / NT : 1)
+    exact_third_kernel(StageArgs<R> a) {
+  using Acc = AccOf<R>;
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ int64_t s_item;
   __shared__ __align__(8) uint64_t s_bar;
@@ -925,7 +1000,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 1024 / NT : 1) exact_thir
     if (rec[4 * n + 4] != kStOk) continue;  // flagged by stage 2 (same value for the whole CTA)
     const Lay3 L = lay_third<R, NW>(n, E1, pd.w_in_smem);
     R* pw = (R*)(sm + L.pw);
-    R* c = (R*)(sm + L.c);
+    Acc* c = (Acc*)(sm + L.c);
     double* v = (double*)(sm + L.v);
     double* e = (double*)(sm + L.e);
     double* y = (double*)(sm + L.y);
@@ -939,7 +1014,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 1024 / NT : 1) exact_thir
       mbar_arrive_expect_tx(&s_bar, bytes);
       bulk_g2s(Ws, Wg, bytes, &s_bar);
     }
-    for (int i = tid; i < NW * n; i += NT) c[i] = R(0);
+    for (int i = tid; i < NW * n; i += NT) c[i] = Acc(0);
     const double* X = pd.X + p * n;
     power_table<R, NT>(X, n, E1, pw);
     R* ix = (R*)(sm + L.ix);
@@ -962,9 +1037,9 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 1024 / NT : 1) exact_thir
     }
     __syncthreads();
     {
-      R* cw = c + wid * n;
+      Acc* cw = c + wid * n;
       auto wget = [&](int, int, int va, int vb) { return W[va * n + vb]; };
-      auto emit = [&](int l, R val) { atomicAdd(&cw[l], val); };
+      auto emit = [&](int l, R val) { atomicAdd(&cw[l], Acc(val)); };
       // terms of degree < 3 have no third derivatives: each group starts at
       // its first term of degree >= 3
       for_support<kMaxSupport>([&](auto kc) {
@@ -973,7 +1048,8 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 1024 / NT : 1) exact_thir
           if (gather) {
             for (int64_t t = pd.k3off[K] + tid; t < pd.koff[K + 1]; t += NT) {
               const TermRegs tr = load_term(pd.terms, t);
-              term_third_gather_group<R, K>(tr, pw, E1, ix, wget, emit);
+              if constexpr (std::is_same<R, dfloat>::value) term_third_gather_sub_group<R, K>(tr, pw, E1, ix, wget, emit);
+              else term_third_gather_group<R, K>(tr, pw, E1, ix, wget, emit);
             }
           } else {
             for (int64_t t = pd.k3off[K] + tid; t < pd.koff[K + 1]; t += NT) {
@@ -990,7 +1066,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 1024 / NT : 1) exact_thir
     if (wid == 0) {
       double vc = 0.0;
       for (int i = lane; i < n; i += 32) {
-        R s = c[i];
+        Acc s = c[i];
         for (int q = 1; q < NW; ++q) s += c[q * n + i];
         y[i] = (double)s;
         vc += v[i] * (double)s;
@@ -1054,6 +1130,7 @@ size_t stage_bytes(int stage, int threads, int n, int E1, bool in_smem, bool gat
 
 template <typename R>
 static polylab_status prepare_exact(ExactBatch* b) {
+  static_assert(sizeof(AccOf<R>) == sizeof(R), "H and W slots share one layout");
   size_t smem[3] = {0, 0, 0}, gstride = 0;
   int64_t mat = 0, vec = 0;
   b->frame_need.assign(b->host_descs.size(), 0);
@@ -1110,7 +1187,7 @@ static polylab_status launch_stage_t(ExactBatch* b, int stage, cudaStream_t s) {
   a.item_begin = i0;
   a.item_end = i1;
   a.counter = b->counter + stage;
-  a.mats_h = (R*)b->ws_h;
+  a.mats_h = (AccOf<R>*)b->ws_h;
   a.mats_w = (R*)b->ws_w;
   a.vecs = (double*)b->ws_v;
   a.r = b->opts.regularization;
@@ -1147,7 +1224,7 @@ static polylab_status launch_frame_class(ExactBatch* b, int cls, cudaStream_t s)
   a.item_begin = fc.begin;
   a.item_end = fc.end;
   a.counter = b->fcounter + cls;
-  a.mats_h = (R*)b->ws_h;
+  a.mats_h = (AccOf<R>*)b->ws_h;
   a.mats_w = (R*)b->ws_w;
   a.vecs = (double*)b->ws_v;
   a.r = b->opts.regularization;
@@ -1182,7 +1259,9 @@ static polylab_status launch_stage(ExactBatch* b, int stage, cudaStream_t s) {
 
 polylab_status run_exact_stage(ExactBatch* b, int stage, cudaStream_t s) {
   if (b->total == 0) return POLYLAB_OK;
-  return b->opts.prec == POLYLAB_FP32 ? launch_stage<float>(b, stage, s) : launch_stage<double>(b, stage, s);
+  if (b->opts.prec == POLYLAB_FP32) return launch_stage<float>(b, stage, s);
+  if (b->opts.prec == POLYLAB_F32X2) return launch_stage<dfloat>(b, stage, s);
+  return launch_stage<double>(b, stage, s);
 }
 
 // One run: the three stages one after another on `s` (capturable in a graph).
@@ -1192,7 +1271,9 @@ polylab_status run_exact_batch(ExactBatch* b, cudaStream_t s) {
 }
 
 polylab_status prepare_exact_batch(ExactBatch* b) {
-  return b->opts.prec == POLYLAB_FP32 ? prepare_exact<float>(b) : prepare_exact<double>(b);
+  if (b->opts.prec == POLYLAB_FP32) return prepare_exact<float>(b);
+  if (b->opts.prec == POLYLAB_F32X2) return prepare_exact<dfloat>(b);
+  return prepare_exact<double>(b);
 }
 
 // Per-point cost estimate used to order the work (expensive polynomials

@@ -39,7 +39,9 @@ struct PlanRef {
 polylab_status check_an_opts(const polylab_an_opts* o) {
   if (o->method != POLYLAB_MF_EXACT && o->method != POLYLAB_MF_STOCHASTIC && o->method != POLYLAB_AD)
     return POLYLAB_ERR_INVALID_ARG;
-  if (o->prec != POLYLAB_FP64 && o->prec != POLYLAB_FP32) return POLYLAB_ERR_INVALID_ARG;
+  if (o->prec != POLYLAB_FP64 && o->prec != POLYLAB_FP32 &&
+      !(o->prec == POLYLAB_F32X2 && o->method == POLYLAB_MF_EXACT))
+    return POLYLAB_ERR_INVALID_ARG;
   if (!(o->regularization >= 0.0)) return POLYLAB_ERR_INVALID_ARG;
   if (o->method == POLYLAB_MF_STOCHASTIC) {
     if (o->num_probes < 1 || o->krylov_maxit < 0 || !(o->krylov_tol >= 0.0)) return POLYLAB_ERR_INVALID_ARG;

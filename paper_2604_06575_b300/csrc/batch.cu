@@ -94,8 +94,9 @@ polylab_status exact_batch_init(ExactBatch* b, int n, const polylab_plan* const*
     d.n_gchunks = pl->n_gchunks;
     {
       // monomial values c x^a, their partial products and 1/x stay normal:
-      // |x|^deg within [1e-30, 1e30] (FP32 sums) or [1e-280, 1e280] (FP64)
-      const double lim = o->prec == POLYLAB_FP32 ? 30.0 : 280.0;
+      // |x|^deg within [1e-30, 1e30] (FP32 sums), [1e-25, 1e25] (double words,
+      // whose low word is ~2^-24 of the high one) or [1e-280, 1e280] (FP64)
+      const double lim = o->prec == POLYLAB_FP32 ? 30.0 : o->prec == POLYLAB_F32X2 ? 25.0 : 280.0;
       const double deg = std::max(1, pl->max_degree);
       d.x_lo = std::pow(10.0, -lim / deg);
       d.x_hi = std::pow(10.0, lim / deg);
@@ -190,7 +191,8 @@ polylab_status polylab_batch_create(int32_t n_polys, const polylab_poly* polys, 
   if (!out || n_polys < 0 || !opts || (n_polys > 0 && (!X || !P || !D))) return POLYLAB_ERR_INVALID_ARG;
   if (n_polys > 0 && !polys && !plans) return POLYLAB_ERR_INVALID_ARG;
   if (opts->method != POLYLAB_MF_EXACT) return POLYLAB_ERR_UNSUPPORTED;
-  if (opts->prec != POLYLAB_FP64 && opts->prec != POLYLAB_FP32) return POLYLAB_ERR_INVALID_ARG;
+  if (opts->prec != POLYLAB_FP64 && opts->prec != POLYLAB_FP32 && opts->prec != POLYLAB_F32X2)
+    return POLYLAB_ERR_INVALID_ARG;
   if (!(opts->regularization >= 0.0)) return POLYLAB_ERR_INVALID_ARG;
   *out = nullptr;
   cudaStream_t s = (cudaStream_t)stream;

@@ -215,15 +215,18 @@ __device__ __forceinline__ uint64_t mix64(uint64_t seed, uint64_t k) {
   return z ^ (z >> 31);
 }
 
-// W1 ~ U(-1, 1) / sqrt(F), everything else 0: the untrained network is Jacobi.
+// W1 ~ U(-1, 1) / sqrt(F); the low-rank outputs' weights (columns 1, 2 of
+// W2) ~ U(-1, 1) * 0.05; everything else 0.  The diagonal output starts at
+// Jacobi; the low-rank head must not start at zero weights, where U = 0 and
+// the gradient of U U^T with respect to U vanishes (training would never
+// leave it).
 __global__ void mlp_init_kernel(float* __restrict__ th, uint64_t seed) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= kMlpParams) return;
+  const double u = (double)(mix64(seed, j) >> 11) * (1.0 / 9007199254740992.0);
   float v = 0.f;
-  if (j < kMlpB1) {
-    const double u = (double)(mix64(seed, j) >> 11) * (1.0 / 9007199254740992.0);
-    v = (float)((2.0 * u - 1.0) / sqrt((double)kMlpF));
-  }
+  if (j < kMlpB1) v = (float)((2.0 * u - 1.0) / sqrt((double)kMlpF));
+  else if (j >= kMlpW2 && j < kMlpB2 && (j - kMlpW2) % kMlpO != 0) v = (float)((2.0 * u - 1.0) * 0.05);
   th[j] = v;
 }
 

@@ -1,31 +1,39 @@
 // The learned diagonal-plus-low-rank preconditioner: network shape, feature
 // map and forward pass shared by the training kernels and the stochastic
-// solver.  Per coordinate i of a point:
-//   f_i = [log(|H_ii| + r), log(sum_{j != i} sum_t |d_i d_j t(x)| + r), x_i,
-//          n e_i^2, log(|g_i| + 1e-30)]
+// solver.  Per coordinate i of a point (a_i = |H_ii| + r):
+//   f_i = [log(a_i), log(sum_{j != i} sum_t |d_i d_j t(x)| + r), x_i,
+//          n e_i^2, log(|g_i| + 1e-30), sum_{j != i} H_ij / a_i,
+//          sum_{j != i} H_ij / a_j]
 //   h = tanh(W1^T f + b1) (32 units), o = W2^T h + b2 (3 outputs)
-//   D_i = exp(clip(o_0, -5, 5)) / (|H_ii| + r),  U_ik = 0.1 o_k / sqrt(|H_ii| + r)
+//   D_i = exp(clip(o_0, -5, 5)) / a_i,  U_ik = 0.1 o_k / sqrt(a_i)
 // and the preconditioner is Pi (D + U U^T) Pi; zero output weights give Jacobi.
-// Parameters: one flat vector W1 (5 x 32, row-major), b1, W2 (32 x 3), b2.
+// The two signed features carry couplings of one sign shared by many
+// coordinates (a collective, soft or stiff, mode of the Hessian), which
+// random-sign couplings do not.
+// Parameters: one flat vector W1 (7 x 32, row-major), b1, W2 (32 x 3), b2.
 #pragma once
 
 #include "common.cuh"
 
 namespace polylab {
 
-constexpr int kMlpF = 5;
+constexpr int kMlpF = 7;
 constexpr int kMlpH = 32;
 constexpr int kMlpO = 3;
-constexpr int kMlpParams = kMlpF * kMlpH + kMlpH + kMlpH * kMlpO + kMlpO;  // 291
+constexpr int kMlpParams = kMlpF * kMlpH + kMlpH + kMlpH * kMlpO + kMlpO;  // 355
 constexpr int kMlpW1 = 0, kMlpB1 = kMlpF * kMlpH, kMlpW2 = kMlpB1 + kMlpH, kMlpB2 = kMlpW2 + kMlpH * kMlpO;
 
+// rowsum = sum_{j != i} H_ij, rowsum_a = sum_{j != i} H_ij / a_j
 __device__ __forceinline__ void mlp_features(float* f, float hdiag, float offsum, float x, float e, float g, int n,
-                                             float r) {
-  f[0] = logf(fabsf(hdiag) + r);
+                                             float r, float rowsum, float rowsum_a) {
+  const float a = fabsf(hdiag) + r;
+  f[0] = logf(a);
   f[1] = logf(offsum + r);
   f[2] = x;
   f[3] = (float)n * e * e;
   f[4] = logf(fabsf(g) + 1e-30f);
+  f[5] = rowsum / a;
+  f[6] = rowsum_a;
 }
 
 // forward pass; h (hidden activations) and o (outputs) returned

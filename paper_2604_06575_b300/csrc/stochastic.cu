@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(NT, MINB) stochastic_kernel(StochArgs a) {
     __syncthreads();
     // gradient, sum of |gradient contributions| (zero test), diag(H) and the
     // off-diagonal |contribution| mass of every row (learned preconditioner, Y[n, 2n))
-    for (int i = tid; i < 2 * n; i += NT) Y[i] = R(0);
+    for (int i = tid; i < 3 * n; i += NT) Y[i] = R(0);
     __syncthreads();
     double gabs = 0.0;  // this thread's share of sum |gradient contributions|
     for (int64_t t = tid; t < a.m; t += NT) {
@@ -347,9 +347,24 @@ __global__ void __launch_bounds__(NT, MINB) stochastic_kernel(StochArgs a) {
       e[i] = R((double)g[i] / gn);
       const double d = fabs((double)dg[i]) + a.r;
       Dinv[i] = a.precond == POLYLAB_PRECOND_NONE ? R(1) : R(d > 0.0 ? 1.0 / d : 1.0);
-      if (use_mlp) {  // BF16 weights, FP32 arithmetic
+      Y[2 * n + i] = R(1.0 / d);  // 1 / a_i for the scaled coupling feature
+    }
+    if (use_mlp) {  // BF16 weights, FP32 arithmetic
+      __syncthreads();
+      for (int i = tid; i < n; i += NT) {
+        // signed off-diagonal row sums of the assembled Hessian: plain and
+        // scaled by 1 / a_j
+        R rs = R(0), rsa = R(0);
+        for (int q = a.hrow[i]; q < a.hrow[i + 1]; ++q) {
+          const int c = a.hcol[q];
+          if (c != i) {
+            rs += Hv[q];
+            rsa += Hv[q] * Y[2 * n + c];
+          }
+        }
         float f[kMlpF], h[kMlpH], o[kMlpO], D, u0, u1;
-        mlp_features(f, (float)dg[i], (float)Y[n + i], (float)X[i], (float)e[i], (float)g[i], n, (float)a.r);
+        mlp_features(f, (float)dg[i], (float)Y[n + i], (float)X[i], (float)e[i], (float)g[i], n, (float)a.r,
+                     (float)rs, (float)rsa);
         mlp_forward(th, f, h, o);
         mlp_factors(o, (float)dg[i], (float)a.r, &D, &u0, &u1);
         Dinv[i] = R(D);
@@ -684,7 +699,9 @@ __global__ void __launch_bounds__(NT) mlp_data_kernel(const Term* __restrict__ t
   float* g = Y + (size_t)n * (QC + 1);
   float* dg = g + n;
   float* off = dg + n;
-  double* red = (double*)(((uintptr_t)(off + n) + 15) & ~(uintptr_t)15);
+  float* rs = off + n;   // sum_{j != i} H_ij
+  float* rsa = rs + n;   // sum_{j != i} H_ij / a_j
+  double* red = (double*)(((uintptr_t)(rsa + n) + 15) & ~(uintptr_t)15);
   __shared__ int s_all[QC];
   if (tid < QC) s_all[tid] = 1;
   const int words = (n + 63) / 64;
@@ -698,7 +715,7 @@ __global__ void __launch_bounds__(NT) mlp_data_kernel(const Term* __restrict__ t
         cur *= (float)x[i];
         pw[i * E1 + k] = cur;
       }
-      g[i] = dg[i] = off[i] = 0.f;
+      g[i] = dg[i] = off[i] = rs[i] = rsa[i] = 0.f;
     }
     __syncthreads();
     for (int64_t t = tid; t < m; t += NT) {
@@ -710,7 +727,20 @@ __global__ void __launch_bounds__(NT) mlp_data_kernel(const Term* __restrict__ t
           else {
             atomicAdd(&off[i], fabsf(val));
             atomicAdd(&off[j], fabsf(val));
+            atomicAdd(&rs[i], val);
+            atomicAdd(&rs[j], val);
           }
+        }
+      });
+    }
+    __syncthreads();
+    // second sweep once the diagonal is complete: couplings scaled by 1 / a_j
+    for (int64_t t = tid; t < m; t += NT) {
+      const TermRegs tr = load_term(terms, t);
+      term_derivs<float, 2>(tr, pw, E1, [&](int kind, int i, int j, float val) {
+        if (kind == 2 && i != j) {
+          atomicAdd(&rsa[i], val / (fabsf(dg[j]) + r));
+          atomicAdd(&rsa[j], val / (fabsf(dg[i]) + r));
         }
       });
     }
@@ -725,7 +755,8 @@ __global__ void __launch_bounds__(NT) mlp_data_kernel(const Term* __restrict__ t
       const float ei = g[i] * ginv;
       E_out[p * n + i] = ei;
       hdiag[p * n + i] = dg[i];
-      mlp_features(feats + (p * (int64_t)n + i) * kMlpF, dg[i], off[i], (float)x[i], ei, g[i], n, r);
+      mlp_features(feats + (p * (int64_t)n + i) * kMlpF, dg[i], off[i], (float)x[i], ei, g[i], n, r, rs[i],
+                   rsa[i]);
       for (int k = 0; k < QC; ++k) {
         const uint64_t key = ((uint64_t)p * QC + k) * words + (uint64_t)(i >> 6);
         zp[i * QC + k] = ((splitmix64(seed, key) >> (i & 63)) & 1ull) ? -1.f : 1.f;
@@ -780,7 +811,7 @@ extern "C" polylab_status polylab_mlp_data(const polylab_poly* p, const polylab_
     plan = owned;
   }
   const int n = plan->n, E = std::max(plan->max_exp, 1);
-  const size_t smem = (size_t)n * (E + 1) * 4 + (size_t)n * 5 * 4 + 3 * (size_t)n * 4 + 64 + 16 * 8 * 5;
+  const size_t smem = (size_t)n * (E + 1) * 4 + (size_t)n * 5 * 4 + 5 * (size_t)n * 4 + 64 + 16 * 8 * 5;
   polylab_status st = POLYLAB_OK;
   if (smem > 220 * 1024) {
     st = POLYLAB_ERR_UNSUPPORTED;

@@ -11,6 +11,7 @@
 #include <type_traits>
 
 #include "common.cuh"
+#include "dfloat.cuh"
 
 namespace polylab {
 
@@ -119,8 +120,17 @@ __device__ __forceinline__ void term_derivs_k(const TermRegs& t, const R* __rest
   }
 }
 
-// Terms with more than six active variables are rare; they run out of line so
-// that their register demand does not set the budget of the common cases.
+// Largest support size a per-term routine is inlined for.  Terms with more
+// active variables are rare; they run out of line so that their register
+// demand does not set the budget of the common cases.
+template <typename R>
+constexpr int kInlineSupport = 6;
+// The same for the paths that only points with a near-zero coordinate take:
+// double-word code is ~15x larger per operation, so there these stay out of
+// line and leave the instruction cache to the common path.
+template <typename R>
+constexpr int kInlineSupportRare = std::is_same<R, dfloat>::value ? 0 : 6;
+
 template <typename R, int ORDER, int K, typename Emit>
 __device__ __noinline__ void term_derivs_wide(const TermRegs& t, const R* __restrict__ pw, int E1, Emit emit) {
   term_derivs_k<R, ORDER, K>(t, pw, E1, emit);
@@ -304,6 +314,60 @@ __device__ __forceinline__ void term_third_gather_group(const TermRegs& t, const
   else term_third_gather_wide<R, K>(t, pw, E1, ix, wget, emit);
 }
 
+// The gather form reduced algebraically.  With u_l = a_l / x_l,
+// rs_l = sum_{k != l} u_k W_lk and the pair and diagonal sums written through
+// rs (sum_{j<k} u_j u_k W_jk = (1/2) sum_l u_l rs_l, u_l (u_l - 1/x_l) =
+// a_l (a_l - 1) / x_l^2), the bracket of the gather form collapses to
+//   bracket_l = C - (2 / x_l) q_l,  q_l = rs_l + (a_l - 1) W_ll / x_l,
+//   C = sum_j u_j q_j,
+// so a term costs K(K-1)/2 lookups of W and O(K^2) products and additions
+// with no K x K table.  C - (2/x_l) q_l can cancel, so this form is for
+// arithmetic with bits to spare (the double-word form, ~48 significand
+// bits against an FP64-class error bar).
+template <typename R, int K, typename WGet, typename Emit>
+__device__ __forceinline__ void term_third_gather_sub_k(const TermRegs& t, const R* __restrict__ pw, int E1,
+                                                       const R* __restrict__ ix, WGet&& wget, Emit&& emit) {
+  using S = SmallOf<R>;
+  R m = R(t.coef), xi[K], rs[K];
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    m *= pw[t.var[q] * E1 + t.exp[q]];
+    xi[q] = ix[t.var[q]];
+    rs[q] = R(0);
+  }
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+#pragma unroll
+    for (int k = j + 1; k < K; ++k) {
+      const R w = wget(j, k, t.var[j], t.var[k]);
+      rs[j] += xi[k] * w * S(t.exp[k]);
+      rs[k] += xi[j] * w * S(t.exp[j]);
+    }
+  }
+  R C = R(0);
+#pragma unroll
+  for (int l = 0; l < K; ++l) {
+    const int al = t.exp[l];
+    rs[l] += xi[l] * wget(l, l, t.var[l], t.var[l]) * S(al - 1);  // q_l
+    C += xi[l] * rs[l] * S(al);
+  }
+#pragma unroll
+  for (int l = 0; l < K; ++l) emit(t.var[l], m * xi[l] * (C - xi[l] * rs[l] * S(2)) * S(t.exp[l]));
+}
+
+template <typename R, int K, typename WGet, typename Emit>
+__device__ __noinline__ void term_third_gather_sub_wide(const TermRegs& t, const R* __restrict__ pw, int E1,
+                                                        const R* __restrict__ ix, WGet wget, Emit emit) {
+  term_third_gather_sub_k<R, K>(t, pw, E1, ix, wget, emit);
+}
+
+template <typename R, int K, typename WGet, typename Emit>
+__device__ __forceinline__ void term_third_gather_sub_group(const TermRegs& t, const R* __restrict__ pw, int E1,
+                                                           const R* __restrict__ ix, WGet& wget, Emit& emit) {
+  if constexpr (K <= kInlineSupport<R>) term_third_gather_sub_k<R, K>(t, pw, E1, ix, wget, emit);
+  else term_third_gather_sub_wide<R, K>(t, pw, E1, ix, wget, emit);
+}
+
 // c x^a of one term at one point (any support size).
 template <typename R>
 __device__ __forceinline__ R term_value(const TermRegs& t, const R* __restrict__ pw, int E1) {
@@ -325,14 +389,14 @@ __device__ __forceinline__ void for_support(F&& f) {
 // groups out of line (see term_derivs_wide).
 template <typename R, int ORDER, int K, typename Emit>
 __device__ __forceinline__ void term_derivs_group(const TermRegs& t, const R* __restrict__ pw, int E1, Emit& emit) {
-  if constexpr (K <= 6) term_derivs_k<R, ORDER, K>(t, pw, E1, emit);
+  if constexpr (K <= kInlineSupportRare<R>) term_derivs_k<R, ORDER, K>(t, pw, E1, emit);
   else term_derivs_wide<R, ORDER, K>(t, pw, E1, emit);
 }
 
 template <typename R, int K, typename WGet, typename Emit>
 __device__ __forceinline__ void term_third_group(const TermRegs& t, const R* __restrict__ pw, int E1, WGet& wget,
                                                  Emit& emit) {
-  if constexpr (K <= 6) term_third_contract_k<R, K>(t, pw, E1, wget, emit);
+  if constexpr (K <= kInlineSupportRare<R>) term_third_contract_k<R, K>(t, pw, E1, wget, emit);
   else term_third_contract_wide<R, K>(t, pw, E1, wget, emit);
 }
 

@@ -23,7 +23,7 @@ _lib = C.CDLL(LIB_PATH)
 OK = 0
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "EXP_OVERFLOW", 3: "DUP_VAR_ID", 4: "OOM", 5: "CUDA", 6: "TIMEOUT",
           7: "UNSUPPORTED"}
-PREC = {"fp64": 0, "tf32x3": 1, "bf16": 2, "fp32": 3}
+PREC = {"fp64": 0, "tf32x3": 1, "bf16": 2, "fp32": 3, "f32x2": 4}
 METHOD = {"mf-exact": 0, "mf-stochastic": 1, "ad": 2}
 AD_MAX_N = 24
 PRECOND = {"jacobi": 0, "none": 1, "mlp": 2}
@@ -489,7 +489,8 @@ class Batch:
             pass
 
 
-MLP_PARAMS = 291
+MLP_PARAMS = 355
+MLP_FEATURES = 7
 MLP_PROBES = 4
 
 
@@ -497,7 +498,7 @@ def mlp_data(p: DevPoly, X: torch.Tensor, regularization: float, seed: int, plan
     """(feats, hdiag, e, Z, Y) float32 device tensors (polylab_mlp_data)."""
     P, n = X.shape
     dev = X.device
-    feats = torch.empty(P, n, 5, dtype=torch.float32, device=dev)
+    feats = torch.empty(P, n, MLP_FEATURES, dtype=torch.float32, device=dev)
     hd = torch.empty(P, n, dtype=torch.float32, device=dev)
     e = torch.empty(P, n, dtype=torch.float32, device=dev)
     Z = torch.empty(P, n, MLP_PROBES, dtype=torch.float32, device=dev)
@@ -520,6 +521,14 @@ def mlp_loss_grad(params, data, regularization):
     return loss, grad
 
 
+def mlp_pack(params):
+    """BF16 copy of FP32 network parameters (polylab_mlp_pack), the form
+    opts.mlp_weights takes."""
+    packed = torch.empty(MLP_PARAMS, dtype=torch.bfloat16, device=params.device)
+    _check("polylab_mlp_pack", _lib.polylab_mlp_pack(_ptr(params), _ptr(packed), _stream()))
+    return packed
+
+
 def train_preconditioner(data, regularization, steps=200, lr=3e-3, seed=1, device="cuda"):
     """Adam on the library's loss/gradient kernels; returns (fp32 params,
     packed bf16 weights for opts.mlp_weights, loss history)."""
@@ -535,6 +544,4 @@ def train_preconditioner(data, regularization, steps=200, lr=3e-3, seed=1, devic
                                                          _stream()))
     final, _ = mlp_loss_grad(params, data, regularization)
     hist.append(final)
-    packed = torch.empty(MLP_PARAMS, dtype=torch.bfloat16, device=device)
-    _check("polylab_mlp_pack", _lib.polylab_mlp_pack(_ptr(params), _ptr(packed), _stream()))
-    return params, packed, [float(h) for h in torch.cat(hist).cpu()]
+    return params, mlp_pack(params), [float(h) for h in torch.cat(hist).cpu()]

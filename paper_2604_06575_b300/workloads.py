@@ -287,3 +287,36 @@ def sparse_quartic(n: int, m: int, support: int, seed_off: int = 0, P: int = 409
     poly = convexified(rng, n, e, 0.1)
     X = shell_points(rng, n, P) if shell else box_points(rng, n, P)
     return poly, X
+
+
+def clustered_sparse(n: int, seed_off: int = 0, P: int = 4096, couplings=(1.8, 1.3), cluster_size: int = 0):
+    """The large sparse family with soft collective modes: ``large_sparse``'s
+    convexified random part plus, for each coupling J_k, a cluster S_k of
+    ``cluster_size`` variables (default n // 10, at least 8; disjoint, drawn at
+    random) tied by the attractive mean-field term -(J_k/|S_k|) (sum_{i in S_k}
+    x_i)^2, written out as its monomials (-J_k/|S_k|) x_i^2 and (-2 J_k/|S_k|)
+    x_i x_j.  Each cluster lowers the curvature along its collective
+    direction (near x = 0 the Jacobi-scaled curvature is about
+    1 - 2 J_k mean_i 1/(12 x_i^2 + 2)): a few soft modes that a diagonal
+    preconditioner cannot see.  P points in [-1, 1]^n."""
+    rng = np.random.default_rng(SEED_BASE + 6 + seed_off + 13 * n)
+    e = sparse_monomials(rng, n, 20 * n, 4, 4)
+    base = convexified(rng, n, e, 0.1)
+    s = cluster_size or max(8, n // 10)
+    perm = rng.permutation(n)
+    rows, coef = [], []
+    for k, J in enumerate(couplings):
+        S = np.sort(perm[k * s:(k + 1) * s])
+        for a in range(s):
+            r = np.zeros(n, np.uint8)
+            r[S[a]] = 2
+            rows.append(r)
+            coef.append(-J / s)
+            for b in range(a + 1, s):
+                r = np.zeros(n, np.uint8)
+                r[S[a]] = r[S[b]] = 1
+                rows.append(r)
+                coef.append(-2.0 * J / s)
+    poly = Poly(base.var_ids, np.concatenate([base.exps, np.array(rows, np.uint8)]),
+                np.concatenate([base.coef, np.array(coef)]))
+    return poly, box_points(rng, n, P)

@@ -4,8 +4,10 @@ FP64 bar: |nu_gpu - nu_oracle| <= 1e-11 * kappa * |nu_oracle| with kappa the
 2-norm condition number of H_T + r I (errors of ~1e-16 relative in g and H
 are amplified by the tangent solves).  Flags must match except where the
 oracle's eigenvalue of H_T + r I closest to zero is within 1e-10 |H_T|_F of it
-(ambiguous points, counted and excluded).  FP32 form: the angle between the
-directions stays below 1e-3 rad * kappa-scaled bound stated in the test.
+(ambiguous points, counted and excluded).  The double-word form (POLYLAB_F32X2:
+FP32-pair term sums, inverse and W; FP64 Cholesky) is held to the same FP64
+bar.  FP32 form: the angle between the directions stays below the
+kappa-scaled bound stated in the test.
 """
 import numpy as np
 import pytest
@@ -70,12 +72,13 @@ def compare(poly, X, D, info, ref, r, rel=1e-11):
     return ambiguous
 
 
-def test_worked_example_sec5(pl):
+@pytest.mark.parametrize("prec", ["fp64", "f32x2"])
+def test_worked_example_sec5(pl, prec):
     g = read_kv("affine_worked_example.txt")
     exps, coef = parse_terms(g["terms"])
     poly = workloads.Poly(np.arange(4, dtype=np.uint64), exps, coef)
     x0 = floats(g["x0"])[None, :]
-    D, Du, info = run(pl, poly, x0, regularization=float(g["regularization"]), assume_nonzero_x=True)
+    D, Du, info = run(pl, poly, x0, regularization=float(g["regularization"]), assume_nonzero_x=True, prec=prec)
     d = floats(g["d"])
     # half a unit in the 7th printed digit; the third entry (~1e-9) sits at the
     # FP64 rounding level of the whole vector (|d| ~ 4.5, ulp ~ 1e-15), so it
@@ -86,19 +89,20 @@ def test_worked_example_sec5(pl):
     np.testing.assert_allclose(np.linalg.norm(Du[0]), 1.0, rtol=1e-15)
 
 
-@pytest.mark.parametrize("r", [1e-8, 1e-6])
-def test_affine_small_all_points(pl, r):
+@pytest.mark.parametrize("r,prec", [(1e-8, "fp64"), (1e-6, "fp64"), (1e-8, "f32x2"), (1e-6, "f32x2")])
+def test_affine_small_all_points(pl, r, prec):
     poly, X = workloads.affine_small(P=1024)
-    D, Du, info = run(pl, poly, X, regularization=r)
+    D, Du, info = run(pl, poly, X, regularization=r, prec=prec)
     ref = oracle_all(poly, X, r)
     amb = compare(poly, X, D, info, ref, r)
     assert amb == 0
 
 
-def test_flags_stress(pl):
+@pytest.mark.parametrize("prec", ["fp64", "f32x2"])
+def test_flags_stress(pl, prec):
     poly, X = workloads.affine_small_stress(P=256)
     X[0] = 0.0  # the gradient of this polynomial at the origin is (0, 0, 1): not zero
-    D, Du, info = run(pl, poly, X, regularization=1e-8)
+    D, Du, info = run(pl, poly, X, regularization=1e-8, prec=prec)
     ref = oracle_all(poly, X, 1e-8)
     flags = np.array([o["flags"] for _, o in ref])
     assert (flags == affine.FLAG_NOT_PD).sum() > 10  # the stress case really flags points
@@ -106,16 +110,17 @@ def test_flags_stress(pl):
     assert amb < 8
     # exact zero gradient: x1^2 + x2^2 at the origin
     zp = workloads.Poly(np.arange(2, dtype=np.uint64), np.array([[2, 0], [0, 2]], np.uint8), np.ones(2))
-    D, Du, info = run(pl, zp, np.zeros((2, 2)))
+    D, Du, info = run(pl, zp, np.zeros((2, 2)), prec=prec)
     assert np.all(info["flags"] == affine.FLAG_ZERO_GRAD) and np.all(np.isnan(D))
 
 
-def test_medium_and_large_n(pl):
+@pytest.mark.parametrize("prec", ["fp64", "f32x2"])
+def test_medium_and_large_n(pl, prec):
     for n, m, P in [(20, 200, 9), (45, 600, 5), (70, 400, 3), (130, 300, 2)]:
         rng = np.random.default_rng(n)
         poly = workloads.convexified(rng, n, workloads.sparse_monomials(rng, n, m, 6, 6), 0.1)
         X = workloads.shell_points(rng, n, P)
-        D, Du, info = run(pl, poly, X, regularization=1e-6)
+        D, Du, info = run(pl, poly, X, regularization=1e-6, prec=prec)
         ref = oracle_all(poly, X, 1e-6, third="contract")
         compare(poly, X, D, info, ref, 1e-6)
 
@@ -143,7 +148,7 @@ def test_fp32_form_error_bound(pl):
         assert ang <= 2e-5 * max(kap, 1.0), (i, ang, kap)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "f32x2", "fp32"])
 def test_gather_and_term_by_term_sweeps_agree(pl, prec):
     """Points with a zero or tiny coordinate take the term-by-term sweeps (no
     division by x); the others take the gather forms of both term sweeps.
@@ -156,7 +161,7 @@ def test_gather_and_term_by_term_sweeps_agree(pl, prec):
     X[6:12, 7] = 1e-7
     D, Du, info = run(pl, poly, X, regularization=1e-6, prec=prec)
     ref = oracle_all(poly, X, 1e-6, third="contract")
-    if prec == "fp64":
+    if prec != "fp32":
         assert compare(poly, X, D, info, ref, 1e-6) == 0
     else:
         for i, (nu, oi) in enumerate(ref):
@@ -166,7 +171,7 @@ def test_gather_and_term_by_term_sweeps_agree(pl, prec):
                 assert np.radians(affine.angle_deg(D[i], nu)) <= 2e-5 * max(kap, 1.0), i
 
 
-@pytest.mark.parametrize("n,prec", [(131, "fp64"), (132, "fp64"), (171, "fp32")])
+@pytest.mark.parametrize("n,prec", [(131, "fp64"), (132, "fp64"), (131, "f32x2"), (132, "f32x2"), (171, "fp32")])
 def test_global_memory_frame_both_parities(pl, n, prec):
     """Matrices too large for shared memory take the frame stage's global-memory
     path (the LDL^T in panels of two columns): even and odd m = n - 1, both forms."""
@@ -175,7 +180,7 @@ def test_global_memory_frame_both_parities(pl, n, prec):
     X = workloads.shell_points(rng, n, 3)
     D, Du, info = run(pl, poly, X, regularization=1e-6, prec=prec)
     ref = oracle_all(poly, X, 1e-6, third="contract")
-    if prec == "fp64":
+    if prec != "fp32":
         compare(poly, X, D, info, ref, 1e-6)
     else:
         for i, (nu, oi) in enumerate(ref):

@@ -3,10 +3,11 @@ outputs the oracle computes one by one, plus properties checked on every
 output:
 
 * the 256-polynomial uneven batch (290,592 points) through the batch API in
-  both forms, at the default and the autotuned configuration: every point's
-  flags agree between the forms and the FP32-sum form is within its stated
-  1e-3 rad of the FP64 form; sampled points (the polynomials with the most
-  terms, the largest n and the smallest n) match the oracle;
+  the three forms, at the default and the autotuned configuration: every
+  point's flags agree between the forms, the double-word form is within 1e-9
+  relative of the FP64 form and the FP32-sum form within its stated 1e-3 rad;
+  sampled points (the polynomials with the most terms, the largest n and the
+  smallest n) match the oracle;
 * the stochastic form on the large sparse family at n = 500 and n = 2000 with
   4,096 points and the bench's settings (FP32, q = 16, tol 1e-4, Jacobi):
   a sampled point matches the stochastic oracle run with the same probes."""
@@ -43,11 +44,11 @@ def test_bench_batch_full_size_sampled(pl, bench_batch):
     plans = [pl.Plan(d) for d in dps]
     Xd = [torch.as_tensor(X, device="cuda") for X in Xs]
     out = {}
-    for form in ("fp64", "fp32"):
+    for form in ("fp64", "f32x2", "fp32"):
         b = pl.Batch(dps, plans, Xd, pl.an_opts(prec=form, regularization=1e-6))
         b.run()
         b.check()
-        if form == "fp32":
+        if form != "fp64":
             first = [d.clone() for d in b.Du]
             b.autotune(reps=1)  # the bench's launch configuration
             b.run()
@@ -58,15 +59,18 @@ def test_bench_batch_full_size_sampled(pl, bench_batch):
                 assert float(torch.arccos(cos).max()) <= 1e-4
         out[form] = ([d.cpu().numpy() for d in b.D], [pl.info_numpy(i)["flags"] for i in b.info])
         b.close()
-    worst = 0.0
+    worst, worst_dw = 0.0, 0.0
     for i in range(len(polys)):
-        f64, f32 = out["fp64"][1][i], out["fp32"][1][i]
-        assert np.array_equal(f64, f32), i
+        f64, f32, fdw = out["fp64"][1][i], out["fp32"][1][i], out["f32x2"][1][i]
+        assert np.array_equal(f64, f32) and np.array_equal(f64, fdw), i
         ok = f64 == 0
-        a, c = out["fp64"][0][i][ok], out["fp32"][0][i][ok]
+        a, c, w = out["fp64"][0][i][ok], out["fp32"][0][i][ok], out["f32x2"][0][i][ok]
         cos = np.sum(a * c, axis=1) / (np.linalg.norm(a, axis=1) * np.linalg.norm(c, axis=1))
         worst = max(worst, float(np.arccos(np.clip(cos, -1, 1)).max()))
+        if ok.any():
+            worst_dw = max(worst_dw, float((np.linalg.norm(w - a, axis=1) / np.linalg.norm(a, axis=1)).max()))
     assert worst <= 1e-3, worst
+    assert worst_dw <= 1e-9, worst_dw
     # sampled points against the oracle: most terms, largest n, smallest n
     sizes = [(p.m, p.n, i) for i, p in enumerate(polys)]
     picks = {max(sizes)[2], max(sizes, key=lambda s: s[1])[2], min(sizes, key=lambda s: s[1])[2]}
@@ -76,8 +80,9 @@ def test_bench_batch_full_size_sampled(pl, bench_batch):
             assert out["fp64"][1][i][j] == oi["flags"], (i, j)
             if oi["flags"]:
                 continue
-            d64, d32 = out["fp64"][0][i][j], out["fp32"][0][i][j]
+            d64, d32, ddw = out["fp64"][0][i][j], out["fp32"][0][i][j], out["f32x2"][0][i][j]
             assert np.linalg.norm(d64 - nu) <= 1e-9 * np.linalg.norm(nu), (i, j)
+            assert np.linalg.norm(ddw - nu) <= 1e-9 * np.linalg.norm(nu), (i, j)
             assert angle(d32, nu) <= 1e-3, (i, j)
 
 

@@ -66,3 +66,30 @@ def test_lowrank_preconditioned_pcg_matches_stochastic_oracle_option():
     v = np.random.default_rng(9).normal(size=n - 1)
     np.testing.assert_allclose(QT @ (M @ v), (np.eye(n) - np.outer(e, e)) @ ((D * (QT @ v)) + U @ (U.T @ (QT @ v))),
                                atol=1e-12)
+
+
+def test_signed_coupling_features_closed_form():
+    """f = sum_i d_i x_i^2 / 2 - (c/2) (sum_i x_i)^2 has H = diag(d) - c 1 1^T at
+    every x, so the two signed coupling features are known in closed form:
+    sum_{j != i} H_ij / a_i = -(n - 1) c / a_i and sum_{j != i} H_ij / a_j =
+    -c sum_{j != i} 1 / a_j, with a_i = |d_i - c| + r."""
+    n, c, r = 5, 0.5, 1e-3
+    d = np.array([3.0, 4.0, 5.0, 6.0, 7.0])
+    rows, coef = [], []
+    for i in range(n):
+        e = np.zeros(n, np.uint8)
+        e[i] = 2
+        rows.append(e)
+        coef.append((d[i] - c) / 2)
+        for j in range(i + 1, n):
+            e = np.zeros(n, np.uint8)
+            e[i] = e[j] = 1
+            rows.append(e)
+            coef.append(-c)
+    x = np.array([0.3, -0.2, 0.5, 0.1, -0.4])
+    F, G, H, SF, SG, SH = derivs.eval_derivs(np.array(rows), np.array(coef), x[None, :])
+    np.testing.assert_allclose(H[0], np.diag(d) - c, rtol=1e-14)
+    f = mlp.features(H[0], SH[0], G[0], x, r)
+    a = np.abs(d - c) + r
+    np.testing.assert_allclose(f[:, 5], -(n - 1) * c / a, rtol=1e-14)
+    np.testing.assert_allclose(f[:, 6], [-c * (np.sum(1 / a) - 1 / a[i]) for i in range(n)], rtol=1e-14)
