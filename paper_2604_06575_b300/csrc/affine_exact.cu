@@ -47,10 +47,10 @@ namespace polylab {
 namespace {
 
 // Types of a form.  R: the arithmetic of the term sweeps, the frame update
-// and the inverse; Acc: the sums of gradient and Hessian contributions
-// (added atomically in shared memory) and the matrix H handed to the frame
-// stage; Abs: sums of |contributions| (an error scale only).  The
-// double-word form (R = dfloat) sums into FP64 accumulators.
+// and the inverse; Acc: the sums of gradient, Hessian and trace-term
+// contributions (added atomically in shared memory; H is handed to the
+// frame stage in this type); Abs: sums of |contributions| (an error scale
+// only).  The double-word form sums into double words by atomic_add_dw.
 template <typename R>
 struct FormTypes {
   using Acc = R;
@@ -58,13 +58,50 @@ struct FormTypes {
 };
 template <>
 struct FormTypes<dfloat> {
-  using Acc = double;
+  using Acc = dfloat;
   using Abs = float;
 };
 template <typename R>
 using AccOf = typename FormTypes<R>::Acc;
 template <typename R>
 using AbsOf = typename FormTypes<R>::Abs;
+
+// Sum of products a * b in a form's arithmetic: plain multiply-adds, or for
+// double words the compensated sum of the products (17 FP32 operations per
+// term instead of 29).
+template <typename R>
+struct DotAcc {
+  R v = R(0);
+  __device__ __forceinline__ void add(R a, R b) { v += a * b; }
+  __device__ __forceinline__ R value() const { return v; }
+};
+template <>
+struct DotAcc<dfloat> {
+  dw_comp_sum c;
+  __device__ __forceinline__ void add(dfloat a, dfloat b) { c.add(a * b); }
+  __device__ __forceinline__ dfloat value() const { return c.value(); }
+};
+
+// the two points' values of one monomial by one vector load (8 or 16 bytes)
+__device__ __forceinline__ void load_pair(const float* p, float (&v)[2]) {
+  const float2 t = *reinterpret_cast<const float2*>(p);
+  v[0] = t.x;
+  v[1] = t.y;
+}
+template <typename R>
+__device__ __forceinline__ void load_pair(const R* p, R (&v)[2]) {
+  static_assert(sizeof(R) == 8, "8-byte values");
+  const uint4 t = *reinterpret_cast<const uint4*>(p);
+  v[0] = *reinterpret_cast<const R*>(&t.x);
+  v[1] = *reinterpret_cast<const R*>(&t.z);
+}
+
+// atomic accumulation into a form's sums
+template <typename T>
+__device__ __forceinline__ void acc_add(T* p, T v) {
+  atomicAdd(p, v);
+}
+__device__ __forceinline__ void acc_add(dfloat* p, dfloat v) { atomic_add_dw(p, v); }
 
 // Sum of one run of gather records c_r * m_t (the contributions to one
 // gradient or Hessian entry) in the form's arithmetic, and the magnitude of
@@ -337,6 +374,7 @@ struct Lay1 {
 // `gather`: room for the gather form (1/x, gradient sums, one chunk of
 // monomial values)
 constexpr int kTermPoints = 2;
+static_assert(kTermPoints == 2, "the sweep loads the points' monomial values as pairs");
 template <typename R, int NW>
 __host__ __device__ Lay1 lay_terms(int n, int E1, bool in_smem, bool gather) {
   using Acc = AccOf<R>;
@@ -354,8 +392,10 @@ __host__ __device__ Lay1 lay_terms(int n, int E1, bool in_smem, bool gather) {
     L.ix = b.take(kTermPoints * L.ix_step);
     L.gs = b.take(kTermPoints * L.gs_step);
     L.ga = b.take(kTermPoints * L.ga_step);
-    L.mv_step = (size_t)kGatherChunk * sizeof(R);
-    L.mv = b.take(kTermPoints * L.mv_step);
+    // monomial values of the points of a pass interleaved (value of point q
+    // for chunk term t at [t * kTermPoints + q]): one vector load per record
+    L.mv_step = sizeof(R);
+    L.mv = b.take((size_t)kTermPoints * kGatherChunk * sizeof(R));
   }
   L.H_step = (size_t)mat_slot<Acc>(n) * sizeof(Acc);
   L.H = in_smem ? b.take(kTermPoints * L.H_step) : 0;
@@ -494,7 +534,7 @@ __global__ void __launch_bounds__(NT) exact_terms_kernel(StageArgs<R> a) {
       auto ix_of = [&](int q) { return (R*)(sm + L.ix + q * L.ix_step); };
       auto gs_of = [&](int q) { return (Acc*)(sm + L.gs + q * L.gs_step); };
       auto ga_of = [&](int q) { return (Abs*)(sm + L.ga + q * L.ga_step); };
-      auto mv_of = [&](int q) { return (R*)(sm + L.mv + q * L.mv_step); };
+      R* mvi = (R*)(sm + L.mv);  // interleaved: [t * kTermPoints + q]
       auto Hg_of = [&](int q) { return a.mats_h + pd.mat_off + (p0 + q) * mat_slot<Acc>(n); };
       auto Hr_of = [&](int q) { return pd.h_in_smem ? (Acc*)(sm + L.H + q * L.H_step) : Hg_of(q); };
       auto rec_of = [&](int q) { return a.vecs + pd.vec_off + (p0 + q) * vrec(n); };
@@ -528,23 +568,21 @@ __global__ void __launch_bounds__(NT) exact_terms_kernel(StageArgs<R> a) {
           Acc* Hr[NP];
           Acc* gs[NP];
           Abs* ga[NP];
-          const R* mv[NP];
   #pragma unroll
           for (int q = 0; q < NP; ++q) {
             Hr[q] = Hr_of(q);
             gs[q] = gs_of(q);
             ga[q] = ga_of(q);
-            mv[q] = mv_of(q);
           }
           auto flush = [&](int e, const RunSum<R>* acc, const Abs* aacc) {
             if (e < 0 || e == (int)kGatherPad) return;  // nothing yet, or padding
   #pragma unroll
             for (int q = 0; q < NP; ++q) {
               if (e >= nn) {
-                atomicAdd(&gs[q][e - nn], acc[q].value());
+                acc_add(&gs[q][e - nn], acc[q].value());
                 atomicAdd(&ga[q][e - nn], aacc[q]);
               } else {
-                atomicAdd(&Hr[q][e], acc[q].value());
+                acc_add(&Hr[q][e], acc[q].value());
               }
             }
           };
@@ -553,7 +591,7 @@ __global__ void __launch_bounds__(NT) exact_terms_kernel(StageArgs<R> a) {
             for (int64_t t = t0 + tid; t < t1; t += NT) {
               const TermRegs tr = load_term(pd.terms, t);
   #pragma unroll
-              for (int q = 0; q < NP; ++q) mv_of(q)[t - t0] = term_value<R>(tr, pw_of(q), E1);
+              for (int q = 0; q < NP; ++q) mvi[(t - t0) * kTermPoints + q] = term_value<R>(tr, pw_of(q), E1);
             }
             __syncthreads();
             const int64_t r0 = pd.gather_chunk[c];
@@ -581,9 +619,11 @@ __global__ void __launch_bounds__(NT) exact_terms_kernel(StageArgs<R> a) {
                       aacc[q] = Abs(0);
                     }
                   }
+                  R mvp[kTermPoints];
+                  load_pair(mvi + tt * kTermPoints, mvp);
   #pragma unroll
                   for (int q = 0; q < NP; ++q) {
-                    const R mq = mv[q][tt];
+                    const R mq = mvp[q];
                     acc[q].add(mq, cf);
                     aacc[q] += contrib_abs<R>(mq, cf);
                   }
@@ -617,10 +657,10 @@ __global__ void __launch_bounds__(NT) exact_terms_kernel(StageArgs<R> a) {
           Abs ga = Abs(0);
           auto emit = [&](int kind, int i, int j, R val) {
             if (kind == 1) {
-              atomicAdd(&gw[i], Acc(val));
+              acc_add(&gw[i], Acc(val));
               ga += Abs(fabs(val));
             } else if (kind == 2) {
-              atomicAdd(&Hr[i * n + j], Acc(val));
+              acc_add(&Hr[i * n + j], Acc(val));
             }
           };
           // one loop per support-size group: inside each loop the support size
@@ -713,7 +753,9 @@ __device__ __forceinline__ bool frame_item(const StageArgs<R>& a, const ExactDes
   auto col = [Ld, n, m](int j) -> double* {
     return kF64 ? Ld + (size_t)j * n : Ld + ((size_t)j * m - (size_t)j * (j - 1) / 2 - j);
   };
-  const Rh* Hg = reinterpret_cast<const Rh*>(a.mats_h + pd.mat_off + p * mat_slot<R>(n));
+  // H in the form's sum type (double words in the double-word form, converted
+  // to FP64 element by element in place once it is in this CTA's buffer)
+  const AccOf<R>* Hg = a.mats_h + pd.mat_off + p * mat_slot<R>(n);
   R* Wg = a.mats_w + pd.mat_off + p * mat_slot<R>(n);
   const uint32_t mat_bytes = (uint32_t)(mat_slot<R>(n) * sizeof(R));
   double* rec = a.vecs + pd.vec_off + p * vrec(n);
@@ -726,7 +768,7 @@ __device__ __forceinline__ bool frame_item(const StageArgs<R>& a, const ExactDes
     }
   } else {
     for (int i = wid; i < n; i += NW)
-      for (int j = lane; j < n; j += 32) Hr[i * n + j] = Hg[i * n + j];
+      for (int j = lane; j < n; j += 32) Hr[i * n + j] = Rh(Hg[i * n + j]);
   }
   // |g|, the zero-gradient test and the Householder vector (warp 0)
   if (wid == 0) {
@@ -765,6 +807,14 @@ __device__ __forceinline__ bool frame_item(const StageArgs<R>& a, const ExactDes
     phase ^= 1u;
   } else {
     __syncthreads();
+  }
+  if constexpr (kDW) {
+    if (SMEM) {  // double words -> FP64, element by element in place
+      const dfloat* Hd = reinterpret_cast<const dfloat*>(Hr);
+      for (int i = wid; i < n; i += NW)
+        for (int j = i + lane; j < n; j += 32) Hr[i * n + j] = (double)Hd[i * n + j];
+      __syncthreads();
+    }
   }
   for (int i = wid; i < n; i += NW)  // mirror the upper triangle
     for (int j = lane; j < i; j += 32) Hr[i * n + j] = Hr[j * n + i];
@@ -896,9 +946,9 @@ __device__ __forceinline__ bool frame_item(const StageArgs<R>& a, const ExactDes
   // M = H_T^{-1} = X'^T X', upper triangle into Hr (L no longer needed)
   for (int i = wid; i < m; i += NW)
     for (int j = i + lane; j < m; j += 32) {
-      R acc = R(0);
-      for (int k = j; k < m; ++k) acc += Xs[i * xs + k] * Xs[j * xs + k];
-      HrR[i * n + j] = acc;
+      DotAcc<R> acc;
+      for (int k = j; k < m; ++k) acc.add(Xs[i * xs + k], Xs[j * xs + k]);
+      HrR[i * n + j] = acc.value();
     }
   __syncthreads();
   for (int i = wid; i < n; i += NW)  // Hr <- [M 0; 0 0], full symmetric, in place
@@ -908,9 +958,9 @@ __device__ __forceinline__ bool frame_item(const StageArgs<R>& a, const ExactDes
     }
   __syncthreads();
   for (int i = tid; i < n; i += NT) {  // u = [M 0; 0 0] v
-    R acc = R(0);
-    for (int j = 0; j < n; ++j) acc += HrR[j * n + i] * vrR[j];
-    uR[i] = acc;
+    DotAcc<R> acc;
+    for (int j = 0; j < n; ++j) acc.add(HrR[j * n + i], vrR[j]);
+    uR[i] = acc.value();
   }
   __syncthreads();
   if (wid == 0) {
@@ -1039,7 +1089,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 1024 / NT : std::is_same<
     {
       Acc* cw = c + wid * n;
       auto wget = [&](int, int, int va, int vb) { return W[va * n + vb]; };
-      auto emit = [&](int l, R val) { atomicAdd(&cw[l], Acc(val)); };
+      auto emit = [&](int l, R val) { acc_add(&cw[l], Acc(val)); };
       // terms of degree < 3 have no third derivatives: each group starts at
       // its first term of degree >= 3
       for_support<kMaxSupport>([&](auto kc) {
@@ -1048,7 +1098,9 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 1024 / NT : std::is_same<
           if (gather) {
             for (int64_t t = pd.k3off[K] + tid; t < pd.koff[K + 1]; t += NT) {
               const TermRegs tr = load_term(pd.terms, t);
-              if constexpr (std::is_same<R, dfloat>::value) term_third_gather_sub_group<R, K>(tr, pw, E1, ix, wget, emit);
+              // the reduced gather form where the arithmetic has bits to spare
+              // (FP64, double words); the cancellation-free form for FP32
+              if constexpr (sizeof(R) == 8) term_third_gather_sub_group<R, K>(tr, pw, E1, ix, wget, emit);
               else term_third_gather_group<R, K>(tr, pw, E1, ix, wget, emit);
             }
           } else {
@@ -1085,9 +1137,9 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 1024 / NT : std::is_same<
     __syncthreads();
     // nu = W P tv - e  (W symmetric: column access, conflict-free)
     for (int i = tid; i < n; i += NT) {
-      R acc = R(0);
-      for (int j = 0; j < n; ++j) acc += W[j * n + i] * yr[j];
-      y[i] = (double)acc - e[i];
+      DotAcc<R> acc;
+      for (int j = 0; j < n; ++j) acc.add(W[j * n + i], yr[j]);
+      y[i] = (double)acc.value() - e[i];
     }
     __syncthreads();
     if (wid == 0) {

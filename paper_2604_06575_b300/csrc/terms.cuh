@@ -320,10 +320,11 @@ __device__ __forceinline__ void term_third_gather_group(const TermRegs& t, const
 // a_l (a_l - 1) / x_l^2), the bracket of the gather form collapses to
 //   bracket_l = C - (2 / x_l) q_l,  q_l = rs_l + (a_l - 1) W_ll / x_l,
 //   C = sum_j u_j q_j,
-// so a term costs K(K-1)/2 lookups of W and O(K^2) products and additions
+// so a term costs K(K+1)/2 lookups of W and O(K^2) products and additions
 // with no K x K table.  C - (2/x_l) q_l can cancel, so this form is for
-// arithmetic with bits to spare (the double-word form, ~48 significand
-// bits against an FP64-class error bar).
+// arithmetic with bits to spare (FP64 and double words, 53 and ~48
+// significand bits against an FP64-class error bar); FP32 keeps the
+// cancellation-free gather form above.
 template <typename R, int K, typename WGet, typename Emit>
 __device__ __forceinline__ void term_third_gather_sub_k(const TermRegs& t, const R* __restrict__ pw, int E1,
                                                        const R* __restrict__ ix, WGet&& wget, Emit&& emit) {
@@ -355,17 +356,52 @@ __device__ __forceinline__ void term_third_gather_sub_k(const TermRegs& t, const
   for (int l = 0; l < K; ++l) emit(t.var[l], m * xi[l] * (C - xi[l] * rs[l] * S(2)) * S(t.exp[l]));
 }
 
+// The same reduced form in double words, arranged for their cost: u = a/x
+// formed once per slot, and rs and C kept as compensated sums.
+template <int K, typename WGet, typename Emit>
+__device__ __forceinline__ void term_third_gather_dw_k(const TermRegs& t, const dfloat* __restrict__ pw, int E1,
+                                                      const dfloat* __restrict__ ix, WGet&& wget, Emit&& emit) {
+  dfloat m = dfloat(t.coef), xi[K], u[K], qv[K];
+  dw_comp_sum rs[K], C;
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    m *= pw[t.var[q] * E1 + t.exp[q]];
+    xi[q] = ix[t.var[q]];
+    u[q] = xi[q] * (float)t.exp[q];
+  }
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+#pragma unroll
+    for (int k = j + 1; k < K; ++k) {
+      const dfloat w = wget(j, k, t.var[j], t.var[k]);
+      rs[j].add(u[k] * w);
+      rs[k].add(u[j] * w);
+    }
+  }
+#pragma unroll
+  for (int l = 0; l < K; ++l) {
+    rs[l].add(xi[l] * wget(l, l, t.var[l], t.var[l]) * (float)(t.exp[l] - 1));
+    qv[l] = rs[l].value();
+    C.add(u[l] * qv[l]);
+  }
+  const dfloat Cv = C.value();
+#pragma unroll
+  for (int l = 0; l < K; ++l) emit(t.var[l], m * u[l] * (Cv - xi[l] * qv[l] * 2.0f));
+}
+
 template <typename R, int K, typename WGet, typename Emit>
 __device__ __noinline__ void term_third_gather_sub_wide(const TermRegs& t, const R* __restrict__ pw, int E1,
                                                         const R* __restrict__ ix, WGet wget, Emit emit) {
-  term_third_gather_sub_k<R, K>(t, pw, E1, ix, wget, emit);
+  if constexpr (std::is_same<R, dfloat>::value) term_third_gather_dw_k<K>(t, pw, E1, ix, wget, emit);
+  else term_third_gather_sub_k<R, K>(t, pw, E1, ix, wget, emit);
 }
 
 template <typename R, int K, typename WGet, typename Emit>
 __device__ __forceinline__ void term_third_gather_sub_group(const TermRegs& t, const R* __restrict__ pw, int E1,
                                                            const R* __restrict__ ix, WGet& wget, Emit& emit) {
-  if constexpr (K <= kInlineSupport<R>) term_third_gather_sub_k<R, K>(t, pw, E1, ix, wget, emit);
-  else term_third_gather_sub_wide<R, K>(t, pw, E1, ix, wget, emit);
+  if constexpr (K > kInlineSupport<R>) term_third_gather_sub_wide<R, K>(t, pw, E1, ix, wget, emit);
+  else if constexpr (std::is_same<R, dfloat>::value) term_third_gather_dw_k<K>(t, pw, E1, ix, wget, emit);
+  else term_third_gather_sub_k<R, K>(t, pw, E1, ix, wget, emit);
 }
 
 // c x^a of one term at one point (any support size).
