@@ -23,7 +23,9 @@
 // Forms: BF16 operands with per-column coefficient scaling (kind::f16, FP32
 // accumulation), and 3xTF32 (kind::tf32: A_hi B_hi + A_hi B_lo + A_lo B_hi,
 // FP32 accumulation).
+#include <cuda.h>
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cstring>
@@ -350,7 +352,8 @@ struct GemmArgs {
   double* G;
   double* H;
   int* err;
-  int Et;  // depth of the per-point power table (x^1..x^Et)
+  int Et;   // depth of the per-point power table (x^1..x^Et)
+  int tma;  // 1: the CTA's 128 x n point tile arrives by one tensor-map copy (n even, X 16-byte aligned)
 };
 
 template <int KIND>
@@ -370,8 +373,18 @@ struct GemmCfg<1> {  // TF32 hi/lo
 
 constexpr int kGemmThreads = 512;  // 4 producer threads per point row; 16 epilogue warps
 
+// 2-D tiled tensor copy global -> shared (TMA), completion on `bar`; the
+// innermost coordinate x must be a multiple of 16 bytes / element size
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
 template <int KIND>
-__global__ void __launch_bounds__(kGemmThreads, 1) gemm_eval_kernel(GemmArgs a) {
+__global__ void __launch_bounds__(kGemmThreads, 1) gemm_eval_kernel(GemmArgs a, const __grid_constant__ CUtensorMap tmX) {
   using Cf = GemmCfg<KIND>;
   extern __shared__ __align__(1024) unsigned char sm_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)sm_raw + 1023) & ~(uintptr_t)1023);
@@ -387,7 +400,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_eval_kernel(GemmArgs a) 
     recs[0] = (ClosMono*)rb;
     recs[1] = (ClosMono*)(rb + Cf::KT * sizeof(ClosMono));
   }
-  __shared__ __align__(8) uint64_t full[2], done[2], fin, mrec[2];
+  __shared__ __align__(8) uint64_t full[2], done[2], fin, mrec[2], xbar;
   __shared__ uint32_t s_taddr;
   __shared__ int s_started[2];
   __shared__ int s_abort;
@@ -404,6 +417,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_eval_kernel(GemmArgs a) 
     mbar_init(&fin, 1);
     mbar_init(&mrec[0], 1);
     mbar_init(&mrec[1], 1);
+    mbar_init(&xbar, 1);
     s_started[0] = s_started[1] = 0;
     s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -415,10 +429,24 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_eval_kernel(GemmArgs a) 
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   const int Et = a.Et;
+  // the CTA's 128 x n points: one tensor-map copy into the (still unused) B
+  // stage buffers, rows past P filled with zeros by the copy; or plain loads
+  const double* Xt = reinterpret_cast<const double*>(stB[0]);
+  if (a.tma) {
+    if (tid == 0) {
+      mbar_arrive_expect_tx(&xbar, (uint32_t)(128 * n * sizeof(double)));
+      tma_load_2d(stB[0], &tmX, 0, (int)p0, &xbar);
+    }
+    __syncthreads();  // (the barriers' initialisation is visible to every thread from here)
+    if (!mbar_wait_cta(&xbar, 0, a.err, 1)) {
+      mbar_drain(&xbar, 0, a.err, 1);
+      s_abort = 1;
+    }
+  }
   for (int i = tid; i < n * 128; i += kGemmThreads) {
     const int v = i / 128, rr = i % 128;
     const int64_t p = p0 + rr;
-    const float x = p < a.P ? (float)a.X[p * n + v] : 0.0f;
+    const float x = a.tma ? (float)Xt[rr * n + v] : (p < a.P ? (float)a.X[p * n + v] : 0.0f);
     float pw = x;
     for (int e = 0; e < Et; ++e) {
       pwt[(v * Et + e) * 128 + rr] = pw;
@@ -427,6 +455,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_eval_kernel(GemmArgs a) 
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  // the B stage buffers are written by bulk copies from here on: order the
+  // generic-proxy reads of the point tile before them
+  if (tid == 0) fence_proxy_async_smem();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t taddr = s_taddr;
   const int* live = a.live + (size_t)chunk * a.Kt;
@@ -849,6 +880,33 @@ static polylab_status eval_err_word(int** p) {
   return POLYLAB_OK;
 }
 
+// The tensor map of the points X (P rows of n doubles) with a 128 x n box,
+// encoded through the driver entry point the runtime hands out.  False when
+// the layout does not allow it (n odd: rows not a multiple of 16 bytes; X not
+// 16-byte aligned; n > 128: the box would not fit the staging buffer) or the
+// entry point is unavailable -- the kernel then loads the points itself.
+static bool encode_points_map(const double* X, int64_t P, int n, CUtensorMap* map) {
+  if (n % 2 != 0 || n > 128 || ((uintptr_t)X & 15) != 0 || P >= ((int64_t)1 << 31)) return false;
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+      cudaGetLastError();
+      return false;
+    }
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)P};
+  const cuuint64_t strides[1] = {(cuuint64_t)n * sizeof(double)};
+  const cuuint32_t box[2] = {(cuuint32_t)n, 128u};
+  const cuuint32_t estr[2] = {1u, 1u};
+  return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<double*>(X), dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 polylab_status eval_gemm(const polylab_plan* plan, const double* X, int64_t P, int order, int prec, double* F,
                          double* G, double* H, cudaStream_t s) {
   if (P == 0) return POLYLAB_OK;
@@ -857,6 +915,8 @@ polylab_status eval_gemm(const polylab_plan* plan, const double* X, int64_t P, i
   const int n = plan->n;
   int* err;
   PL_TRY(eval_err_word(&err));
+  CUtensorMap tmX{};
+  const bool tma = encode_points_map(X, P, n, &tmX);
   GemmArgs a{};
   a.X = X;
   a.P = P;
@@ -871,6 +931,7 @@ polylab_status eval_gemm(const polylab_plan* plan, const double* X, int64_t P, i
   a.G = G;
   a.H = H;
   a.err = err;
+  a.tma = tma ? 1 : 0;
   const unsigned gx = (unsigned)ceil_div(P, 128);
   if (prec == POLYLAB_BF16) {
     a.Et = table_depth<0>(n, plan->max_exp);
@@ -881,7 +942,7 @@ polylab_status eval_gemm(const polylab_plan* plan, const double* X, int64_t P, i
     a.live = g->live16_dev;
     a.half = g->half16_dev;
     PL_CUDA(cudaFuncSetAttribute(gemm_eval_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    gemm_eval_kernel<0><<<dim3(gx, g->Npad / 512), kGemmThreads, smem, s>>>(a);
+    gemm_eval_kernel<0><<<dim3(gx, g->Npad / 512), kGemmThreads, smem, s>>>(a, tmX);
   } else {
     a.Et = table_depth<1>(n, plan->max_exp);
     const size_t smem = gemm_smem<1>(n, a.Et);
@@ -891,7 +952,7 @@ polylab_status eval_gemm(const polylab_plan* plan, const double* X, int64_t P, i
     a.live = g->live32_dev;
     a.half = nullptr;
     PL_CUDA(cudaFuncSetAttribute(gemm_eval_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    gemm_eval_kernel<1><<<dim3(gx, g->Npad / 256), kGemmThreads, smem, s>>>(a);
+    gemm_eval_kernel<1><<<dim3(gx, g->Npad / 256), kGemmThreads, smem, s>>>(a, tmX);
   }
   return launch_status("gemm_eval_kernel");
 }
