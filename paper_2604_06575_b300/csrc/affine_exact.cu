@@ -1098,9 +1098,10 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 1024 / NT : std::is_same<
           if (gather) {
             for (int64_t t = pd.k3off[K] + tid; t < pd.koff[K + 1]; t += NT) {
               const TermRegs tr = load_term(pd.terms, t);
-              // the reduced gather form where the arithmetic has bits to spare
-              // (FP64, double words); the cancellation-free form for FP32
-              if constexpr (sizeof(R) == 8) term_third_gather_sub_group<R, K>(tr, pw, E1, ix, wget, emit);
+              // the reduced gather form for double words (within their bar);
+              // the cancellation-free form for FP32 and for the FP64 form,
+              // which is the accuracy reference
+              if constexpr (std::is_same<R, dfloat>::value) term_third_gather_sub_group<R, K>(tr, pw, E1, ix, wget, emit);
               else term_third_gather_group<R, K>(tr, pw, E1, ix, wget, emit);
             }
           } else {

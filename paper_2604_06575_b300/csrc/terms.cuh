@@ -321,9 +321,10 @@ __device__ __forceinline__ void term_third_gather_group(const TermRegs& t, const
 //   bracket_l = C - (2 / x_l) q_l,  q_l = rs_l + (a_l - 1) W_ll / x_l,
 //   C = sum_j u_j q_j,
 // so a term costs K(K+1)/2 lookups of W and O(K^2) products and additions
-// with no K x K table.  C - (2/x_l) q_l can cancel, so this form is for
-// arithmetic with bits to spare (FP64 and double words, 53 and ~48
-// significand bits against an FP64-class error bar); FP32 keeps the
+// with no K x K table.  For a_l = 1 the bracket's (u_l - 1/x_l) rs_l part is
+// zero but is formed as a difference here, so the form costs accuracy: it is
+// used for the double-word form, whose error bar leaves room for it; the
+// FP32 form and the FP64 form (the accuracy reference) keep the
 // cancellation-free gather form above.
 template <typename R, int K, typename WGet, typename Emit>
 __device__ __forceinline__ void term_third_gather_sub_k(const TermRegs& t, const R* __restrict__ pw, int E1,
