@@ -65,6 +65,7 @@ def parse():
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work per sample")
     ap.add_argument("--forms", default="fp64,f32x2,fp32", help="forms to time (profiling runs time one)")
     ap.add_argument("--rows-only", action="store_true", help="only the per-row measurements (profiling runs)")
+    ap.add_argument("--rows", default="", help="comma-separated row names to measure (default: every row)")
     ap.add_argument("--config", default=None,
                     help="threads,ctas_per_sm,order[,term_threads,terms_ctas,third_ctas,frame_split,"
                          "third_threads] in place of autotuning (profiling runs)")
@@ -387,7 +388,9 @@ def main():
         return v.value if rc == 0 else float("nan")
 
     if args.rows_only:
-        print(json.dumps(dict(rows=measure_rows(pl, workloads, torch, dev, 0.0, 0.0))), flush=True)
+        only = [r for r in args.rows.split(",") if r]
+        print(json.dumps(dict(rows=measure_rows(pl, workloads, torch, dev, alu_peak(0, 20000), alu_peak(1, 2000),
+                                                only))), flush=True)
         return
 
     # ---- workload (rank r: its own batch, weak scaling)
@@ -605,7 +608,7 @@ def main():
 
     # ---- other rows of the path, measured after the headline
     if not args.no_rows:
-        line["rows"] = measure_rows(pl, workloads, torch, dev, p32, p64)
+        line["rows"] = measure_rows(pl, workloads, torch, dev, p32, p64, [r for r in args.rows.split(",") if r])
 
     if rank == 0 and not args.no_cpu_baseline:
         # the oracle on the host cores: one thread, then every core, each on a
@@ -653,25 +656,42 @@ def stage_launches(cfg: dict, polys, Xs) -> dict:
     return dict(terms=1, frame=frame, third=1)
 
 
-def measure_rows(pl, workloads, torch, dev, p32, p64):
-    rows = {}
+def measure_rows(pl, workloads, torch, dev, p32, p64, only=None):
+    """Every row of the path after the headline, or the named ones (`only`)."""
+    table = (("mul_product_pair", lambda: measure_mul(pl, workloads, torch, dev)),
+             ("eval_derivs", lambda: measure_eval(pl, workloads, torch, dev)),
+             ("affine_small", lambda: measure_small(pl, workloads, torch, dev)),
+             ("exact_scaling", lambda: measure_exact_scaling(pl, workloads, torch, dev)),
+             ("stochastic_band", lambda: measure_stochastic_band(pl, workloads, torch, dev)),
+             ("stochastic", lambda: measure_stochastic(pl, workloads, torch, dev, p32)),
+             ("crossover", lambda: measure_crossover(pl, workloads, torch, dev)),
+             ("simplify_pd_cubed", lambda: measure_pd3(pl, workloads, torch, dev)),
+             ("affine_ad", lambda: measure_ad(pl, workloads, torch, dev, p64)),
+             ("precision", lambda: measure_precision(pl, workloads, torch, dev)))
+    unknown = set(only or ()) - {k for k, _ in table}
+    if unknown:
+        raise SystemExit(f"unknown rows: {sorted(unknown)}")
+    return {k: fn() for k, fn in table if not only or k in only}
+
+
+def _ev_time(torch, fn, reps=5, warm=2):
     stream = torch.cuda.current_stream()
-
-    def ev_time(fn, reps=5, warm=2):
-        for _ in range(warm):
-            fn()
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
         torch.cuda.synchronize()
-        ts = []
-        for _ in range(reps):
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            fn()
-            b.record(stream)
-            torch.cuda.synchronize()
-            ts.append(a.elapsed_time(b))
-        return statistics.median(ts)
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
 
-    # product simplify (4M-term expansion -> merged terms), host syncs included
+
+def measure_mul(pl, workloads, torch, dev):
+    """Product simplify (4M-term expansion -> merged terms), host syncs included."""
     A, B = workloads.product_pair()
     da, db = pl.to_device(A, dev), pl.to_device(B, dev)
     r = pl.mul(da, db)
@@ -689,16 +709,18 @@ def measure_rows(pl, workloads, torch, dev, p32, p64):
     # and read once (16 + 8 bytes each) and the merged rows written (n bytes of
     # exponents + 8 bytes of coefficient each)
     alg = 4e6 * 24 * 2 + r.m * (r.n + 8)
-    rows["mul_product_pair"] = dict(workload="2 x 2,000 terms, n=20 each, 10 shared ids, deg<=6: 4,000,000 products",
-                                    ms=round(ms, 3), merged_terms=r.m,
-                                    expanded_terms_per_s=round(4e6 / (ms * 1e-3), 1),
-                                    roofline=dict(bound="hbm", achieved=round(alg / (ms * 1e-3) / 1e9, 1),
-                                                  peak=MEASURED_HBM_GBS, unit="GB/s",
-                                                  frac=round(alg / (ms * 1e-3) / 1e9 / MEASURED_HBM_GBS, 4),
-                                                  algorithmic_bytes=int(alg),
-                                                  note="wall time of the call (host synchronisations included); "
-                                                       "peak: measured copy bandwidth"))
-    # derivative evaluation forms
+    return dict(workload="2 x 2,000 terms, n=20 each, 10 shared ids, deg<=6: 4,000,000 products",
+                ms=round(ms, 3), merged_terms=r.m, expanded_terms_per_s=round(4e6 / (ms * 1e-3), 1),
+                roofline=dict(bound="hbm", achieved=round(alg / (ms * 1e-3) / 1e9, 1), peak=MEASURED_HBM_GBS,
+                              unit="GB/s", frac=round(alg / (ms * 1e-3) / 1e9 / MEASURED_HBM_GBS, 4),
+                              algorithmic_bytes=int(alg),
+                              note="wall time of the call (host synchronisations included); "
+                                   "peak: measured copy bandwidth"))
+
+
+def measure_eval(pl, workloads, torch, dev):
+    """Derivative evaluation (f, grad, Hessian) in every form on the n = 30
+    batch, with the full-grid errors against FP64 and the tensor roofline."""
     poly, X = workloads.eval_batch()
     dp = pl.to_device(poly, dev)
     Xd = torch.as_tensor(X, device=dev)
@@ -715,7 +737,7 @@ def measure_rows(pl, workloads, torch, dev, p32, p64):
     with pl.Plan(dp, gemm=True) as plan:
         gi = plan.gemm_info()
         for prec in ("fp64", "fp32", "tf32x3", "bf16"):
-            ms = ev_time(lambda: pl.eval_derivs(dp, Xd, plan=plan, prec=prec, out=out))
+            ms = _ev_time(torch, lambda: pl.eval_derivs(dp, Xd, plan=plan, prec=prec, out=out))
             ev[prec] = dict(ms=round(ms, 3), evals_per_s=round(P / (ms * 1e-3), 1))
             if prec != "fp64":
                 pl.eval_derivs(dp, Xd, plan=plan, prec=prec, out=out)
@@ -737,19 +759,11 @@ def measure_rows(pl, workloads, torch, dev, p32, p64):
                                     unit="TFLOP/s", frac=round(fl / t / 1e12 / pk, 4),
                                     note="issued MMA work of live blocks; peak: measured bf16 burst"
                                          + (" x nominal tf32/bf16 ratio" if prec == "tf32x3" else ""))
-    rows["eval_derivs"] = dict(workload="n=30, 5,000 terms deg<=4 <=4 active, 65,536 points in [-1,1]^30",
-                               closure_K=gi["K"], output_columns_padded=gi["Npad"], forms=ev,
-                               speedup_vs_fp64={k: round(ev["fp64"]["ms"] / v["ms"], 2) for k, v in ev.items()})
+    res = dict(workload="n=30, 5,000 terms deg<=4 <=4 active, 65,536 points in [-1,1]^30",
+               closure_K=gi["K"], output_columns_padded=gi["Npad"], forms=ev,
+               speedup_vs_fp64={k: round(ev["fp64"]["ms"] / v["ms"], 2) for k, v in ev.items()})
     del out, Xd
-    rows["affine_small"] = measure_small(pl, workloads, torch, dev)
-    rows["exact_scaling"] = measure_exact_scaling(pl, workloads, torch, dev)
-    rows["stochastic_band"] = measure_stochastic_band(pl, workloads, torch, dev)
-    rows["stochastic"] = measure_stochastic(pl, workloads, torch, dev, p32)
-    rows["crossover"] = measure_crossover(pl, workloads, torch, dev)
-    rows["simplify_pd_cubed"] = measure_pd3(pl, workloads, torch, dev)
-    rows["affine_ad"] = measure_ad(pl, workloads, torch, dev, p64)
-    rows["precision"] = measure_precision(pl, workloads, torch, dev)
-    return rows
+    return res
 
 
 def measure_small(pl, workloads, torch, dev):
@@ -929,51 +943,72 @@ def _time_call(torch, fn, stream):
 
 
 def _angle(torch, D, ref):
-    c = (torch.nn.functional.normalize(D, dim=1) * torch.nn.functional.normalize(ref, dim=1)).sum(1)
+    """Mean angle (rad) between the rows of D and ref, over the rows where both
+    are finite (the exact form returns NaN at points it flags)."""
+    ok = torch.isfinite(D).all(1) & torch.isfinite(ref).all(1)
+    if not bool(ok.any()):
+        return None
+    c = (torch.nn.functional.normalize(D[ok], dim=1) * torch.nn.functional.normalize(ref[ok], dim=1)).sum(1)
     return float(torch.arccos(c.clamp(-1, 1)).mean())
 
 
 def measure_stochastic(pl, workloads, torch, dev, p32):
-    """Large sparse family (n in {500, 1000, 2000}, 20n random terms of degree
-    <= 4, 4,096 points in [-1,1]^n): MF-logDet-Stochastic, FP32, q = 16,
-    tol 1e-4, maxit 80; Jacobi at every n, the learned preconditioner (trained
-    on 48 other points) and the exact form at n = 500 as the reference for the error."""
+    """MF-logDet-Stochastic (FP32, tol 1e-4, maxit 80, r = 1e-4) at 4,096
+    points for n in {500, 1000, 2000} and q in {16, 32, 64} probes, with the
+    Jacobi and the learned preconditioner side by side, on two families: the
+    large sparse one (20n random terms of degree <= 4, points in [-1,1]^n) and
+    the clustered one (the same plus two mean-field clusters that make soft
+    collective modes).  The network is trained per family and n (1,000 Adam
+    steps on 128 points of another draw).  At n = 500 the exact FP32 form at
+    256 of the points is the reference for the error."""
     stream = torch.cuda.current_stream()
     out = {}
     r = 1e-4
-    for n in (500, 1000, 2000):
-        poly, X = workloads.large_sparse(n, P=4096)
-        dp = pl.to_device(poly, dev)
-        Xd = torch.as_tensor(X, device=dev)
-        row = dict(terms=poly.m, points=4096)
-        with pl.Plan(dp) as plan:
-            kw = dict(method="mf-stochastic", regularization=r, num_probes=16, krylov_tol=1e-4, krylov_maxit=80,
-                      prec="fp32", plan=plan, seed=7)
-            ms, res = _time_call(torch, lambda: pl.affine_normal(dp, Xd, precond="jacobi", **kw), stream)
-            info = pl.info_numpy(res[2])
-            row["jacobi"] = dict(ms=round(ms, 2), dirs_per_s=round(4096 / (ms * 1e-3), 1),
-                                 krylov_iters_per_point=round(float(info["krylov_iters"].mean()), 2))
-            if n == 500:
-                tr = workloads.large_sparse(n, P=48, seed_off=1)[1]
+    fams = (("large_sparse", workloads.large_sparse), ("clustered_sparse", workloads.clustered_sparse))
+    for fam, gen in fams:
+        rows = {}
+        for n in (500, 1000, 2000):
+            poly, X = gen(n, P=4096)
+            dp = pl.to_device(poly, dev)
+            Xd = torch.as_tensor(X, device=dev)
+            row = dict(terms=poly.m, points=4096)
+            with pl.Plan(dp) as plan:
+                tr = gen(n, P=128, seed_off=1)[1]
                 data = pl.mlp_data(dp, torch.as_tensor(tr, device=dev), r, seed=21, plan=plan)
                 t0 = time.perf_counter()
-                params, packed, hist = pl.train_preconditioner(data, r, steps=150, lr=3e-3)
+                params, packed, hist = pl.train_preconditioner(data, r, steps=1000, lr=3e-3)
                 torch.cuda.synchronize()
-                train_s = time.perf_counter() - t0
-                ms2, res2 = _time_call(torch, lambda: pl.affine_normal(dp, Xd, precond="mlp", mlp_weights=packed,
-                                                                       **kw), stream)
-                info2 = pl.info_numpy(res2[2])
-                sub = Xd[:256]
-                msx, rex = _time_call(torch, lambda: pl.affine_normal(dp, sub, plan=plan, regularization=r,
-                                                                      prec="fp32"), stream)
-                row["mlp"] = dict(ms=round(ms2, 2), dirs_per_s=round(4096 / (ms2 * 1e-3), 1),
-                                  krylov_iters_per_point=round(float(info2["krylov_iters"].mean()), 2),
-                                  train_steps=150, train_seconds=round(train_s, 2),
-                                  loss_first_last=[round(hist[0], 5), round(hist[-1], 5)])
-                row["exact_fp32_256_points"] = dict(ms=round(msx, 2), dirs_per_s=round(256 / (msx * 1e-3), 1))
-                row["angle_to_exact_rad"] = dict(jacobi=_angle(torch, res[0][:256], rex[0]),
-                                                 mlp=_angle(torch, res2[0][:256], rex[0]))
-        out[f"n{n}"] = row
+                row["train"] = dict(steps=1000, points=128, seconds=round(time.perf_counter() - t0, 2),
+                                    loss_first_last=[round(hist[0], 5), round(hist[-1], 5)])
+                del data
+                ref = None
+                if n == 500:
+                    sub = Xd[:256]
+                    msx, rex = _time_call(torch, lambda: pl.affine_normal(dp, sub, plan=plan, regularization=r,
+                                                                          prec="fp32"), stream)
+                    ref = rex[0]
+                    row["exact_fp32_256_points"] = dict(
+                        ms=round(msx, 2), dirs_per_s=round(256 / (msx * 1e-3), 1),
+                        unflagged=int((pl.info_numpy(rex[2])["flags"] == 0).sum()))
+                for q in (16, 32, 64):
+                    cell = {}
+                    for pre in ("jacobi", "mlp"):
+                        kw = dict(method="mf-stochastic", regularization=r, num_probes=q, krylov_tol=1e-4,
+                                  krylov_maxit=80, prec="fp32", plan=plan, seed=7, precond=pre,
+                                  mlp_weights=packed if pre == "mlp" else None)
+                        ms, res = _time_call(torch, lambda: pl.affine_normal(dp, Xd, **kw), stream)
+                        info = pl.info_numpy(res[2])
+                        c = dict(ms=round(ms, 2), dirs_per_s=round(4096 / (ms * 1e-3), 1),
+                                 krylov_iters_per_point=round(float(info["krylov_iters"].mean()), 2))
+                        if ref is not None:
+                            c["angle_to_exact_rad"] = _angle(torch, res[0][:256], ref)
+                        cell[pre] = c
+                    cell["mlp_over_jacobi_iters"] = round(cell["mlp"]["krylov_iters_per_point"]
+                                                          / cell["jacobi"]["krylov_iters_per_point"], 4)
+                    row[f"q{q}"] = cell
+            rows[f"n{n}"] = row
+            del Xd, dp
+        out[fam] = rows
     return out
 
 
