@@ -45,6 +45,13 @@ inline polylab_status launch_status(const char* where) {
 // ------------------------------------------------------------ scratch memory
 // Stream-ordered scratch buffers: freed in stream order when the guard dies.
 
+// The library's stream-ordered memory pool on the current device: like the
+// device's default pool, but it keeps the memory it has mapped across
+// synchronisations (release threshold: unlimited), so that a call does not
+// map its scratch afresh after the previous call synchronised.  Its memory
+// goes back to the system when the process ends.
+cudaMemPool_t scratch_pool();
+
 struct Scratch {
   cudaStream_t s;
   std::vector<void*> ptrs;
@@ -57,7 +64,9 @@ struct Scratch {
     *out = nullptr;
     if (count == 0) count = 1;
     void* p = nullptr;
-    cudaError_t e = cudaMallocAsync(&p, count * sizeof(T), s);
+    cudaMemPool_t pool = scratch_pool();
+    cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, count * sizeof(T), pool, s)
+                         : cudaMallocAsync(&p, count * sizeof(T), s);
     if (e != cudaSuccess) {
       set_last_error("cudaMallocAsync", e);
       cudaGetLastError();

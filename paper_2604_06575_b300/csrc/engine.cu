@@ -199,180 +199,202 @@ struct CoefOf {
   }
 };
 
-// Each warp owns the segments whose head lies in its chunk [w*CH, (w+1)*CH),
-// so no segment is split between warps and the summation order is fixed.
-// Within a 32-item window a Hillis-Steele segmented scan on (head, value)
-// runs over shuffles; the open segment's partial sum is carried to the next
-// window.  The lane holding a segment's last item writes sums[slot].
-template <typename K, typename C>
-__global__ void seg_reduce(const K* __restrict__ keys, const uint32_t* __restrict__ vals,
-                           const uint32_t* __restrict__ head, const uint32_t* __restrict__ slot, int64_t N, int64_t CH,
-                           CoefOf<C> coef, K* __restrict__ ukeys, C* __restrict__ sums) {
-  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  const int64_t lo = w * CH;
-  if (lo >= N) return;
-  const int64_t hi_nominal = std::min<int64_t>(lo + CH, N);
-  // first head at or after lo
-  int64_t start = lo;
-  while (true) {
-    const int64_t k = start + lane;
-    const bool h = k < N && head[k];
-    const unsigned b = __ballot_sync(0xffffffffu, h);
-    if (b) {
-      start += __ffs(b) - 1;
-      break;
-    }
-    start += 32;
-    if (start >= hi_nominal) return;  // no segment starts in this chunk
-  }
-  if (start >= hi_nominal) return;
-  C carry = C(0);
-  for (int64_t base = start;; base += 32) {
-    const int64_t k = base + lane;
-    const bool in = k < N;
-    const bool h = in ? head[k] != 0u : true;
-    // stop at the first head at or beyond the nominal end (that segment belongs to the next warp)
-    const bool stop_here = h && k >= hi_nominal;
-    const unsigned stopmask = __ballot_sync(0xffffffffu, stop_here || !in);
-    const int first_stop = stopmask ? __ffs(stopmask) - 1 : 32;
-    const bool active = lane < first_stop;
-    C v = active ? coef(vals[k]) : C(0);
-    bool f = active ? h : true;
-    // segmented inclusive scan
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const C yv = __shfl_up_sync(0xffffffffu, v, o);
-      const bool yf = __shfl_up_sync(0xffffffffu, f, o);
-      if (lane >= o && !f) {
-        v += yv;
-        f = yf;
-      }
-      // f now tells whether a head lies in (lane - 2o, lane]
-    }
-    // lanes before the first head of this window continue the carried segment
-    const unsigned heads = __ballot_sync(0xffffffffu, active && h);
-    const int first_head = heads ? __ffs(heads) - 1 : 32;
-    if (active && lane < first_head) v += carry;
-    // segment end: next item is a head, or is inactive
-    const bool next_is_head = __shfl_down_sync(0xffffffffu, (int)(!active || h), 1) != 0;
-    const bool end = active && (lane == 31 ? false : next_is_head);
-    // segment index of item k: heads before k, plus its own head, minus one
-    if (end) {
-      const uint32_t sl = slot[k] + (h ? 1u : 0u) - 1u;
-      sums[sl] = v;
-      ukeys[sl] = keys[k];
-    }
-    // a window that reached a stop closed every segment it holds (the lane
-    // before the stop sees an inactive successor, so `end` was set there)
-    if (first_stop < 32) return;
-    // all 32 lanes active: lane 31's segment stays open
-    carry = __shfl_sync(0xffffffffu, v, 31);
-    // if lane 31 was the end of its segment (next window starts with a head) it
-    // is written when that is known: peek at the next item
-    const int64_t nk = base + 32;
-    const bool nh = nk >= N || head[nk] != 0u;
-    if (nh && lane == 31) {
-      const uint32_t sl = slot[k] + (h ? 1u : 0u) - 1u;
-      sums[sl] = v;
-      ukeys[sl] = keys[k];
-    }
-    if (nh) carry = C(0);
-  }
+// Each warp owns the segments whose head lies in its chunk [w*CH, (w+1)*CH)
+// (CH = 32 * windows, windows <= kSegWindows), so no segment is split
+// between warps and the summation order is fixed.  The warp first loads the
+// head flags, representative items and coefficients of its whole chunk (all
+// loads in flight together), then walks its 32-item windows: a Hillis-Steele
+// segmented scan on (head, value) over shuffles, the open segment's partial
+// sum carried to the next window, and the lane holding a segment's last item
+// writing the segment's sum, representative item and keep flag.  A segment
+// still open at the chunk's end is finished by reading on, window by window,
+// until the next head.
+constexpr int kSegWindows = 16;
+
+template <typename C>
+__device__ __forceinline__ void seg_write(int64_t k, bool h, C v, uint32_t item, const uint32_t* __restrict__ slot,
+                                          double zeroprec, uint32_t* __restrict__ rep, C* __restrict__ sums,
+                                          uint32_t* __restrict__ keep) {
+  const uint32_t sl = slot[k] + (h ? 1u : 0u) - 1u;  // segment index of item k
+  sums[sl] = v;
+  rep[sl] = item;
+  keep[sl] = fabs((double)v) > zeroprec ? 1u : 0u;
 }
 
 template <typename C>
-__global__ void keep_flags(const C* __restrict__ sums, int64_t U, double zeroprec, uint32_t* __restrict__ keep) {
-  const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (u < U) keep[u] = fabs((double)sums[u]) > zeroprec ? 1u : 0u;
+__global__ void seg_reduce(const uint32_t* __restrict__ vals, const uint32_t* __restrict__ head,
+                           const uint32_t* __restrict__ slot, int64_t N, int windows, CoefOf<C> coef, double zeroprec,
+                           uint32_t* __restrict__ rep, C* __restrict__ sums, uint32_t* __restrict__ keep) {
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int64_t lo = w * 32 * windows;
+  if (lo >= N) return;
+  const int64_t hi = std::min<int64_t>(lo + 32 * windows, N);
+  bool hh[kSegWindows];
+  uint32_t vv[kSegWindows];
+  C cv[kSegWindows];
+#pragma unroll
+  for (int r = 0; r < kSegWindows; ++r) {
+    const int64_t k = lo + r * 32 + lane;
+    const bool in = r < windows && k < hi;
+    hh[r] = in ? head[k] != 0u : false;
+    vv[r] = in ? vals[k] : 0u;
+  }
+#pragma unroll
+  for (int r = 0; r < kSegWindows; ++r) {
+    const int64_t k = lo + r * 32 + lane;
+    cv[r] = (r < windows && k < hi) ? coef(vv[r]) : C(0);
+  }
+  // whether the item just past the chunk starts a new segment (or the end)
+  const bool past_is_head = hi >= N || head[hi] != 0u;
+  // first head of the chunk: the items before it belong to the previous warp
+  int64_t fh = hi;
+#pragma unroll
+  for (int r = 0; r < kSegWindows; ++r) {
+    const unsigned b = __ballot_sync(0xffffffffu, hh[r]);
+    if (b && fh == hi) fh = lo + r * 32 + (__ffs(b) - 1);
+  }
+  if (fh >= hi) return;  // no segment starts in this chunk
+  C carry = C(0);
+  C last_v = C(0);
+#pragma unroll
+  for (int r = 0; r < kSegWindows; ++r) {
+    if (r < windows) {
+      const int64_t k = lo + r * 32 + lane;
+      const bool in = k < hi;
+      const bool active = in && k >= fh;
+      const bool h = hh[r];
+      C v = active ? cv[r] : C(0);
+      bool f = active ? h : !in;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const C yv = __shfl_up_sync(0xffffffffu, v, o);
+        const bool yf = __shfl_up_sync(0xffffffffu, f, o);
+        if (lane >= o && !f) {
+          v += yv;
+          f = yf;
+        }
+      }
+      // lanes before this window's first head continue the carried segment
+      const unsigned heads = __ballot_sync(0xffffffffu, active && h);
+      const int first_head = heads ? __ffs(heads) - 1 : 32;
+      if (active && lane < first_head) v += carry;
+      // is the next item a head (or past the end of the data)?
+      // (both shuffles by every lane, before the lanes take their branches)
+      const bool nh_in = __shfl_down_sync(0xffffffffu, (int)h, 1) != 0;
+      const bool nh_next = __shfl_sync(0xffffffffu, (int)hh[r + 1 < kSegWindows ? r + 1 : r], 0) != 0;
+      bool next_head;
+      if (k + 1 >= hi) next_head = past_is_head;
+      else if (lane < 31) next_head = nh_in;
+      else next_head = nh_next;
+      if (active && next_head) seg_write(k, h, v, vv[r], slot, zeroprec, rep, sums, keep);
+      carry = __shfl_sync(0xffffffffu, v, 31);
+      last_v = v;
+    }
+  }
+  if (past_is_head) return;
+  // the chunk's last segment runs on past hi: sum the rest, window by window,
+  // up to the next head
+  const int64_t k_last = hi - 1;
+  const uint32_t item = vals[k_last];
+  C total = __shfl_sync(0xffffffffu, last_v, (int)((k_last - lo) & 31));
+  for (int64_t base = hi;; base += 32) {
+    const int64_t k = base + lane;
+    const bool h = k >= N || head[k] != 0u;
+    const unsigned stops = __ballot_sync(0xffffffffu, h);
+    const int first_stop = stops ? __ffs(stops) - 1 : 32;
+    C v = lane < first_stop ? coef(vals[k]) : C(0);
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    total += v;
+    if (first_stop < 32) break;
+  }
+  if (lane == 0) seg_write(k_last, head[k_last] != 0u, total, item, slot, zeroprec, rep, sums, keep);
 }
 
-// Unrank keys into exponent rows (inverse of the rank formula above).  A CTA
-// takes 128 consecutive merged keys: the binomial table and the CTA's rows go
-// to shared memory, each thread unranks one key into its kept row's slot, and
-// the kept rows (contiguous in the output, since kpos is the exclusive scan of
-// keep) leave as one coalesced byte range.
+// Exponent rows of the kept merged terms.  Every item of a key's run has the
+// same exponent row, so a row is assembled from one representative item: a
+// row of the simplify operand, a row of either add operand, or the sum of the
+// two factor rows of a product, each from its operand's sparse support (whose
+// columns are already merged columns).  A CTA takes 128 consecutive merged
+// terms; with `Staged` the rows are built in shared memory and the kept ones
+// (contiguous in the output, since kpos is the exclusive scan of keep) leave
+// as one coalesced byte range, otherwise (very wide rows) each thread writes
+// its row in place.
 constexpr int kUnpackThreads = 128;
 
-template <typename K, typename C>
-__global__ void __launch_bounds__(kUnpackThreads) unpack_rows(const K* __restrict__ ukeys,
-                                                              const C* __restrict__ sums,
-                                                              const uint32_t* __restrict__ keep,
-                                                              const uint32_t* __restrict__ kpos, int64_t U, int n,
-                                                              const K* __restrict__ S, int D1,
-                                                              uint8_t* __restrict__ out_exps,
-                                                              C* __restrict__ out_coef) {
-  extern __shared__ __align__(16) unsigned char sh[];
-  K* Ss = reinterpret_cast<K*>(sh);
-  uint8_t* rows = reinterpret_cast<uint8_t*>(Ss + (size_t)(n + 1) * D1);
-  __shared__ int s_count;
-  const int tid = threadIdx.x;
-  const int64_t u0 = (int64_t)blockIdx.x * kUnpackThreads, u = u0 + tid;
-  for (int i = tid; i < (n + 1) * D1; i += kUnpackThreads) Ss[i] = S[i];
-  for (int i = tid; i < kUnpackThreads * n; i += kUnpackThreads) rows[i] = 0;
-  if (tid == 0) s_count = 0;
-  __syncthreads();
-  const int64_t obase = kpos[u0];  // output row of the first kept key at or after u0
-  const bool kept = u < U && keep[u];
-  if (kept) {
-    atomicAdd(&s_count, 1);
-    const int64_t o = kpos[u];
-    uint8_t* row = rows + (o - obase) * n;
-    const K r = ukeys[u];
-    const int D = D1 - 1;
-    int d = 0;
-    while (d < D && Ss[n * D1 + d] <= r) ++d;
-    K w = r - (d > 0 ? Ss[n * D1 + d - 1] : K(0));
-    int R = d;
-    for (int c = n - 1; c >= 1 && R > 0; --c) {
-      const K top = Ss[c * D1 + R];
-      int a = 0;
-      while (a < R && top - Ss[c * D1 + (R - a - 1)] <= w) ++a;
-      if (a) {
-        w -= top - Ss[c * D1 + (R - a)];
-        R -= a;
-        row[c] = (uint8_t)a;
-      }
-    }
-    row[0] = (uint8_t)R;
-    out_coef[o] = sums[u];
-  }
-  __syncthreads();
-  uint8_t* dst = out_exps + obase * n;
-  const int bytes = s_count * n;
-  for (int i = tid; i < bytes; i += kUnpackThreads) dst[i] = rows[i];
+struct RowSrc {
+  const uint32_t* pa;
+  const uint32_t* ca;
+  const uint8_t* ea;
+  const uint32_t* pb;
+  const uint32_t* cb;
+  const uint8_t* eb;
+  int64_t ma, mb;
+  int mode;
+};
+
+__device__ __forceinline__ void add_support(uint8_t* row, const uint32_t* __restrict__ ptr,
+                                            const uint32_t* __restrict__ col, const uint8_t* __restrict__ ex,
+                                            int64_t t) {
+  for (uint32_t q = ptr[t]; q < ptr[t + 1]; ++q) row[col[q]] += ex[q];
 }
 
-// One thread per key writing its row directly: the fallback when a CTA's rows
-// and the binomial table do not fit in shared memory (very wide rows).
-template <typename K, typename C>
-__global__ void unpack_rows_direct(const K* __restrict__ ukeys, const C* __restrict__ sums,
-                                   const uint32_t* __restrict__ keep, const uint32_t* __restrict__ kpos, int64_t U,
-                                   int n, const K* __restrict__ S, int D1, uint8_t* __restrict__ out_exps,
-                                   C* __restrict__ out_coef) {
-  const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (u >= U || !keep[u]) return;
-  const int64_t o = kpos[u];
-  uint8_t* row = out_exps + o * (int64_t)n;
-  for (int c = 0; c < n; ++c) row[c] = 0;
-  K r = ukeys[u];
-  const int D = D1 - 1;
-  int d = 0;
-  while (d < D && S[n * D1 + d] <= r) ++d;
-  K w = r - (d > 0 ? S[n * D1 + d - 1] : K(0));
-  int R = d;
-  for (int c = n - 1; c >= 1 && R > 0; --c) {
-    const K top = S[c * D1 + R];
-    int a = 0;
-    while (a < R && top - S[c * D1 + (R - a - 1)] <= w) ++a;
-    if (a) {
-      w -= top - S[c * D1 + (R - a)];
-      R -= a;
-      row[c] = (uint8_t)a;
-    }
+__device__ __forceinline__ void build_row(uint8_t* row, uint32_t idx, const RowSrc& r) {
+  if (r.mode == kMul) {
+    const int64_t i = idx / r.mb, j = idx - i * r.mb;
+    add_support(row, r.pa, r.ca, r.ea, i);
+    add_support(row, r.pb, r.cb, r.eb, j);
+  } else if (r.mode == kSimplify || (int64_t)idx < r.ma) {
+    add_support(row, r.pa, r.ca, r.ea, idx);
+  } else {
+    add_support(row, r.pb, r.cb, r.eb, (int64_t)idx - r.ma);
   }
-  row[0] = (uint8_t)R;
-  out_coef[o] = sums[u];
+}
+
+template <typename C, bool Staged>
+__global__ void __launch_bounds__(kUnpackThreads) assemble_rows(const uint32_t* __restrict__ rep,
+                                                                const C* __restrict__ sums,
+                                                                const uint32_t* __restrict__ keep,
+                                                                const uint32_t* __restrict__ kpos, int64_t U, int n,
+                                                                RowSrc src, uint8_t* __restrict__ out_exps,
+                                                                C* __restrict__ out_coef) {
+  extern __shared__ __align__(16) unsigned char rows[];
+  const int tid = threadIdx.x;
+  const int64_t u0 = (int64_t)blockIdx.x * kUnpackThreads, u = u0 + tid;
+  const bool kept = u < U && keep[u];
+  if constexpr (Staged) {
+    uint32_t* rw = reinterpret_cast<uint32_t*>(rows);
+    for (int i = tid; i < kUnpackThreads * n / 4 + 1; i += kUnpackThreads) rw[i] = 0;
+    __syncthreads();
+    const int64_t obase = kpos[u0];  // output row of the first kept term at or after u0
+    if (kept) {
+      const int64_t o = kpos[u];
+      build_row(rows + (o - obase) * n, rep[u], src);
+      out_coef[o] = sums[u];
+    }
+    const int bytes = __syncthreads_count(kept) * n;
+    // out: bytes up to the first 4-byte boundary of the destination, then
+    // whole words (each packed from four shared-memory bytes), then the rest
+    uint8_t* dst = out_exps + obase * n;
+    const int head = (int)((4 - ((uintptr_t)dst & 3)) & 3);
+    const int lead = head < bytes ? head : bytes;
+    const int words = (bytes - lead) >> 2;
+    if (tid < lead) dst[tid] = rows[tid];
+    uint32_t* dw = reinterpret_cast<uint32_t*>(dst + lead);
+    for (int k = tid; k < words; k += kUnpackThreads) {
+      const unsigned char* r = rows + lead + 4 * k;
+      dw[k] = (uint32_t)r[0] | ((uint32_t)r[1] << 8) | ((uint32_t)r[2] << 16) | ((uint32_t)r[3] << 24);
+    }
+    const int tail = lead + 4 * words;
+    if (tail + tid < bytes) dst[tail + tid] = rows[tail + tid];
+  } else {
+    if (!kept) return;
+    const int64_t o = kpos[u];
+    uint8_t* row = out_exps + o * (int64_t)n;
+    for (int c = 0; c < n; ++c) row[c] = 0;
+    build_row(row, rep[u], src);
+    out_coef[o] = sums[u];
+  }
 }
 
 // ------------------------------------------------------------- host side
@@ -387,9 +409,21 @@ struct Operand {
   uint32_t nnz = 0;
 };
 
+// Host side of an operand's build: the column maps it uploads (kept until the
+// stream is next synchronised, as the copy reads them asynchronously) and the
+// support size and top degree the device reports back.
+struct OperandHost {
+  std::vector<int> ordmap;  // [ord | colmap]
+  int maxdeg = 0;
+  uint32_t nnz = 0;
+};
+
+// First half of an operand's build: per-term support counts and degrees, their
+// scan, and the copies of the top degree and the support total to the host.
+// Nothing waits here; the caller synchronises once for every operand.
 template <class Poly, class Mem>
-polylab_status build_operand(const Poly* p, const std::vector<int>& colmap_h, Operand* op, Mem& scr,
-                             cudaStream_t s) {
+polylab_status count_operand(const Poly* p, const std::vector<int>& colmap_h, Operand* op, OperandHost* hb,
+                             int** ordmap_d, Mem& scr, cudaStream_t s) {
   op->m = p->n_terms;
   const int64_t m = op->m;
   PL_TRY(scr.get(&op->ptr, m + 1));
@@ -397,15 +431,13 @@ polylab_status build_operand(const Poly* p, const std::vector<int>& colmap_h, Op
   int* dev_max = nullptr;
   PL_TRY(scr.get(&dev_max, 1));
   // operand columns in increasing merged-column order
-  std::vector<int> both(2 * colmap_h.size());
+  std::vector<int>& both = hb->ordmap;
+  both.resize(2 * colmap_h.size());
   for (size_t j = 0; j < colmap_h.size(); ++j) both[j] = (int)j;
   std::sort(both.begin(), both.begin() + colmap_h.size(), [&](int x, int y) { return colmap_h[x] < colmap_h[y]; });
   std::copy(colmap_h.begin(), colmap_h.end(), both.begin() + colmap_h.size());
-  int* ordmap = nullptr;  // [ord | colmap]
-  PL_TRY(scr.get(&ordmap, both.size()));
-  // the staging vector must outlive the copy: synchronous copy from pageable memory
-  PL_CUDA(cudaMemcpyAsync(ordmap, both.data(), both.size() * sizeof(int), cudaMemcpyHostToDevice, s));
-  PL_CUDA(cudaStreamSynchronize(s));
+  PL_TRY(scr.get(ordmap_d, both.size()));
+  PL_CUDA(cudaMemcpyAsync(*ordmap_d, both.data(), both.size() * sizeof(int), cudaMemcpyHostToDevice, s));
   PL_CUDA(cudaMemsetAsync(dev_max, 0, sizeof(int), s));
   PL_CUDA(cudaMemsetAsync(op->ptr, 0, (m + 1) * sizeof(uint32_t), s));
   if (m > 0) {
@@ -413,17 +445,22 @@ polylab_status build_operand(const Poly* p, const std::vector<int>& colmap_h, Op
     PL_TRY(launch_status("count_support"));
   }
   PL_TRY(exclusive_scan(op->ptr, op->ptr, m + 1, scr, s));
-  int hmax = 0;
-  uint32_t hnnz = 0;
-  PL_CUDA(cudaMemcpyAsync(&hmax, dev_max, sizeof(int), cudaMemcpyDeviceToHost, s));
-  PL_CUDA(cudaMemcpyAsync(&hnnz, op->ptr + m, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-  PL_CUDA(cudaStreamSynchronize(s));
-  op->maxdeg = hmax;
-  op->nnz = hnnz;
-  PL_TRY(scr.get(&op->col, std::max<uint32_t>(hnnz, 1)));
-  PL_TRY(scr.get(&op->ex, std::max<uint32_t>(hnnz, 1)));
+  PL_CUDA(cudaMemcpyAsync(&hb->maxdeg, dev_max, sizeof(int), cudaMemcpyDeviceToHost, s));
+  PL_CUDA(cudaMemcpyAsync(&hb->nnz, op->ptr + m, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  return POLYLAB_OK;
+}
+
+// Second half, once the host holds the counts: the CSR supports themselves.
+template <class Poly, class Mem>
+polylab_status fill_operand(const Poly* p, const OperandHost& hb, const int* ordmap_d, Operand* op, Mem& scr,
+                            cudaStream_t s) {
+  const int64_t m = op->m;
+  op->maxdeg = hb.maxdeg;
+  op->nnz = hb.nnz;
+  PL_TRY(scr.get(&op->col, std::max<uint32_t>(hb.nnz, 1)));
+  PL_TRY(scr.get(&op->ex, std::max<uint32_t>(hb.nnz, 1)));
   if (m > 0) {
-    fill_support<<<(unsigned)ceil_div(m, 8), 256, 0, s>>>(p->exps, m, p->n_vars, ordmap, ordmap + p->n_vars,
+    fill_support<<<(unsigned)ceil_div(m, 8), 256, 0, s>>>(p->exps, m, p->n_vars, ordmap_d, ordmap_d + p->n_vars,
                                                           op->ptr, op->col, op->ex);
     PL_TRY(launch_status("fill_support"));
   }
@@ -473,9 +510,9 @@ polylab_status run_pipeline(int n, int D, int64_t N, const std::vector<K>& Sh, i
   PL_TRY(scr.get(&akeys, N));
   PL_TRY(scr.get(&vals, N));
   PL_TRY(scr.get(&avals, N));
-  int* ovf = nullptr;
-  PL_TRY(scr.get(&ovf, 1));
-  PL_CUDA(cudaMemsetAsync(ovf, 0, sizeof(int), s));
+  int* ovf = nullptr;  // [exponent overflow, sort look-back gave up]
+  PL_TRY(scr.get(&ovf, 2));
+  PL_CUDA(cudaMemsetAsync(ovf, 0, 2 * sizeof(int), s));
   if (mode == kMul) {
     keys_mul<K><<<(unsigned)ceil_div(N, 256), 256, 0, s>>>(A.ptr, A.col, A.ex, A.deg, B.ptr, B.col, B.ex, B.deg, A.m,
                                                            B.m, n, S, D1, keys, vals, ovf);
@@ -487,45 +524,50 @@ polylab_status run_pipeline(int n, int D, int64_t N, const std::vector<K>& Sh, i
   }
   PL_TRY(launch_status("keys"));
   int which = 0;
-  PL_TRY((radix_sort<K, Mem>(keys, vals, akeys, avals, N, bits, scr, s, &which)));
+  PL_TRY((radix_sort<K, Mem>(keys, vals, akeys, avals, N, bits, scr, s, &which, ovf + 1)));
   if (which) {
     std::swap(keys, akeys);
     std::swap(vals, avals);
   }
-  uint32_t *head, *slot;
+  // Reduce-by-key into arrays sized for the worst case (every key unique), so
+  // that nothing waits for the number U of distinct keys: U is only read on
+  // the device, and the keep flags past U stay zero.
+  uint32_t *head, *slot, *keep, *kpos, *rep;
+  C* sums;
   PL_TRY(scr.get(&head, N));
   PL_TRY(scr.get(&slot, N));
+  PL_TRY(scr.get(&rep, N));
+  PL_TRY(scr.get(&sums, N));
+  PL_TRY(scr.get(&keep, N));
+  PL_TRY(scr.get(&kpos, N));
+  PL_CUDA(cudaMemsetAsync(keep, 0, (size_t)N * sizeof(uint32_t), s));
   mark_heads<K><<<(unsigned)ceil_div(N, 256), 256, 0, s>>>(keys, N, head);
   PL_TRY(launch_status("mark_heads"));
   PL_TRY(exclusive_scan(head, slot, N, scr, s));
-  uint32_t hU[2] = {0, 0};
-  PL_CUDA(cudaMemcpyAsync(&hU[0], slot + N - 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-  PL_CUDA(cudaMemcpyAsync(&hU[1], head + N - 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-  int hovf = 0;
-  PL_CUDA(cudaMemcpyAsync(&hovf, ovf, sizeof(int), cudaMemcpyDeviceToHost, s));
-  PL_CUDA(cudaStreamSynchronize(s));
-  if (hovf) return POLYLAB_ERR_EXP_OVERFLOW;
-  const int64_t U = (int64_t)hU[0] + hU[1];
-  K* ukeys;
-  C* sums;
-  PL_TRY(scr.get(&ukeys, U));
-  PL_TRY(scr.get(&sums, U));
-  const int64_t CH = 512;
-  const int64_t warps = ceil_div(N, CH);
+  // windows of 32 items per warp: up to kSegWindows, fewer when that would
+  // leave SMs idle
+  const int windows = (int)std::min<int64_t>(kSegWindows, std::max<int64_t>(1, ceil_div(N, (int64_t)num_sms() * 32 * 32)));
+  const int64_t warps = ceil_div(N, (int64_t)32 * windows);
   CoefOf<C> cf{pa->coef, mode != kSimplify ? pb->coef : nullptr, pa->n_terms, mode != kSimplify ? pb->n_terms : 0,
             mode};
-  seg_reduce<K, C><<<(unsigned)ceil_div(warps * 32, 256), 256, 0, s>>>(keys, vals, head, slot, N, CH, cf, ukeys, sums);
+  seg_reduce<C><<<(unsigned)ceil_div(warps * 32, 256), 256, 0, s>>>(vals, head, slot, N, windows, cf, zeroprec, rep,
+                                                                    sums, keep);
   PL_TRY(launch_status("seg_reduce"));
-  uint32_t *keep, *kpos;
-  PL_TRY(scr.get(&keep, U));
-  PL_TRY(scr.get(&kpos, U));
-  keep_flags<<<(unsigned)ceil_div(U, 256), 256, 0, s>>>(sums, U, zeroprec, keep);
-  PL_TRY(launch_status("keep_flags"));
-  PL_TRY(exclusive_scan(keep, kpos, U, scr, s));
+  PL_TRY(exclusive_scan(keep, kpos, N, scr, s));
+  // the one wait that sizes the output: kept count, exponent overflow and the
+  // sort's look-back word
   uint32_t hM[2] = {0, 0};
-  PL_CUDA(cudaMemcpyAsync(&hM[0], kpos + U - 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-  PL_CUDA(cudaMemcpyAsync(&hM[1], keep + U - 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  int hflags[2] = {0, 0};
+  PL_CUDA(cudaMemcpyAsync(&hM[0], kpos + N - 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  PL_CUDA(cudaMemcpyAsync(&hM[1], keep + N - 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  PL_CUDA(cudaMemcpyAsync(hflags, ovf, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
   PL_CUDA(cudaStreamSynchronize(s));
+  if (hflags[0]) return POLYLAB_ERR_EXP_OVERFLOW;
+  if (hflags[1]) {
+    set_last_message("radix sort: a look-back wait gave up");
+    return POLYLAB_ERR_TIMEOUT;
+  }
+  const int64_t U = N;  // keep is zero past the distinct keys
   const int64_t M = (int64_t)hM[0] + hM[1];
   out->n_terms = M;
   out->exps = nullptr;
@@ -534,17 +576,17 @@ polylab_status run_pipeline(int n, int D, int64_t N, const std::vector<K>& Sh, i
   out->exps = (uint8_t*)alloc((size_t)M * n, ctx);
   out->coef = (C*)alloc((size_t)M * sizeof(C), ctx);
   if (!out->exps || !out->coef) return POLYLAB_ERR_OOM;
-  const size_t ush = (size_t)(n + 1) * D1 * sizeof(K) + (size_t)kUnpackThreads * n;
-  if (ush <= 160 * 1024) {
+  const RowSrc rs{A.ptr, A.col, A.ex, B.ptr, B.col, B.ex, A.m, B.m, mode};
+  const size_t ush = (size_t)kUnpackThreads * n + 4;
+  const unsigned ublocks = (unsigned)ceil_div(U, kUnpackThreads);
+  if (ush <= 96 * 1024) {
     if (ush > 48 * 1024)
-      PL_CUDA(cudaFuncSetAttribute(unpack_rows<K, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ush));
-    unpack_rows<K, C><<<(unsigned)ceil_div(U, kUnpackThreads), kUnpackThreads, ush, s>>>(ukeys, sums, keep, kpos, U, n,
-                                                                                     S, D1, out->exps, out->coef);
-    return launch_status("unpack_rows");
+      PL_CUDA(cudaFuncSetAttribute(assemble_rows<C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ush));
+    assemble_rows<C, true><<<ublocks, kUnpackThreads, ush, s>>>(rep, sums, keep, kpos, U, n, rs, out->exps, out->coef);
+  } else {
+    assemble_rows<C, false><<<ublocks, kUnpackThreads, 0, s>>>(rep, sums, keep, kpos, U, n, rs, out->exps, out->coef);
   }
-  unpack_rows_direct<K, C><<<(unsigned)ceil_div(U, 128), 128, 0, s>>>(ukeys, sums, keep, kpos, U, n, S, D1, out->exps,
-                                                                   out->coef);
-  return launch_status("unpack_rows_direct");
+  return launch_status("assemble_rows");
 }
 
 template <typename C, class Mem>
@@ -582,8 +624,13 @@ polylab_status engine_with(Mem& scr, const PolyIn<C>* pa, const PolyIn<C>* pb, i
   if (N >= ((int64_t)1 << 31)) return POLYLAB_ERR_UNSUPPORTED;
   if (N == 0) return POLYLAB_OK;
   Operand A, B;
-  PL_TRY(build_operand(pa, mapA, &A, scr, s));
-  if (is_mul) PL_TRY(build_operand(pb, mapB, &B, scr, s));
+  OperandHost ha, hb;
+  int *orda = nullptr, *ordb = nullptr;
+  PL_TRY(count_operand(pa, mapA, &A, &ha, &orda, scr, s));
+  if (is_mul) PL_TRY(count_operand(pb, mapB, &B, &hb, &ordb, scr, s));
+  PL_CUDA(cudaStreamSynchronize(s));  // the one wait before the key width is known
+  PL_TRY(fill_operand(pa, ha, orda, &A, scr, s));
+  if (is_mul) PL_TRY(fill_operand(pb, hb, ordb, &B, scr, s));
   const int D = std::max(1, mode == kMul ? A.maxdeg + B.maxdeg
                             : (mode == kAdd || mode == kSub) ? std::max(A.maxdeg, B.maxdeg) : A.maxdeg);
   std::vector<u128> S128;

@@ -762,7 +762,10 @@ polylab_status build_gemm_operand(polylab_plan* plan, cudaStream_t s) {
     PL_CUDA(cudaMemsetAsync(keys, 0xff, Nc * 8, s));
   }
   int which = 0;
-  PL_TRY((radix_sort<uint64_t, Scratch>(keys, vals, akeys, avals, Nc, 64, scr, s, &which)));
+  int* sort_err = nullptr;
+  PL_TRY(scr.get(&sort_err, 1));
+  PL_CUDA(cudaMemsetAsync(sort_err, 0, sizeof(int), s));
+  PL_TRY((radix_sort<uint64_t, Scratch>(keys, vals, akeys, avals, Nc, 64, scr, s, &which, sort_err)));
   if (which) std::swap(keys, akeys);
   uint32_t *head, *pos;
   PL_TRY(scr.get(&head, Nc));
@@ -771,9 +774,15 @@ polylab_status build_gemm_operand(polylab_plan* plan, cudaStream_t s) {
   PL_TRY(launch_status("mark_unique"));
   PL_TRY(exclusive_scan(head, pos, Nc, scr, s));
   uint32_t hk[2];
+  int herr = 0;
   PL_CUDA(cudaMemcpyAsync(&hk[0], pos + Nc - 1, 4, cudaMemcpyDeviceToHost, s));
   PL_CUDA(cudaMemcpyAsync(&hk[1], head + Nc - 1, 4, cudaMemcpyDeviceToHost, s));
+  PL_CUDA(cudaMemcpyAsync(&herr, sort_err, sizeof(int), cudaMemcpyDeviceToHost, s));
   PL_CUDA(cudaStreamSynchronize(s));
+  if (herr) {
+    set_last_message("radix sort: a look-back wait gave up");
+    return POLYLAB_ERR_TIMEOUT;
+  }
   const int64_t K = (int64_t)hk[0] + hk[1];
   const int64_t Kpad = std::max<int64_t>(64, ceil_div(K, 64) * 64);
   if ((double)Kpad * Npad > (double)(1ll << 28)) return POLYLAB_ERR_UNSUPPORTED;

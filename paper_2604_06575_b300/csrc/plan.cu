@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstring>
 #include <unordered_set>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -17,6 +18,33 @@ void set_last_error(const char* where, cudaError_t e) {
 }
 
 void set_last_message(const char* msg) { snprintf(g_last_error, sizeof(g_last_error), "%s", msg); }
+
+cudaMemPool_t scratch_pool() {
+  static std::mutex mu;
+  static std::vector<cudaMemPool_t> pools;  // by device ordinal
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  if ((int)pools.size() <= dev) pools.resize(dev + 1, nullptr);
+  if (!pools[dev]) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;  // (the caller falls back to the device's default pool)
+    }
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    pools[dev] = pool;
+  }
+  return pools[dev];
+}
 
 int num_sms() {
   static int cached = 0;
