@@ -77,8 +77,8 @@ struct DotAcc {
 };
 template <>
 struct DotAcc<dfloat> {
-  dw_comp_sum c;
-  __device__ __forceinline__ void add(dfloat a, dfloat b) { c.add(a * b); }
+  dw_dot c;
+  __device__ __forceinline__ void add(dfloat a, dfloat b) { c.add(a, b); }
   __device__ __forceinline__ dfloat value() const { return c.value(); }
 };
 
@@ -887,7 +887,38 @@ __device__ __forceinline__ bool frame_item(const StageArgs<R>& a, const ExactDes
   __syncthreads();  // L in the form's precision and sq complete
   // X' = D^{-1/2} X with X = L^{-1} (unit lower), stored transposed:
   // Xs[j*xs + i] = X'_ij, i >= j; then M = X'^T X'
-  if (m <= 64) {
+  if (kDW && m <= 64) {
+    // the same column scheme as below, each row's sum delta_rj - sum_k l_rk x_k
+    // kept as a compensated dot product (dw_dot) and rounded to a double
+    // word only when its x_k is broadcast or stored
+    for (int ja = wid; ja < m; ja += 2 * NW) {
+      const int jb = ja + NW;
+      const int r0 = lane, r1 = lane + 32;
+      dw_dot a0, a1, b0, b1;
+      a0.s = r0 == ja ? 1.f : 0.f;
+      a1.s = r1 == ja ? 1.f : 0.f;
+      b0.s = r0 == jb ? 1.f : 0.f;
+      b1.s = r1 == jb ? 1.f : 0.f;
+      for (int k = ja; k + 1 < m; ++k) {
+        const dfloat l0 = (r0 > k && r0 < m) ? -dfloat(HrR[k * n + r0]) : dfloat(0.f, 0.f);
+        const dfloat l1 = (r1 > k && r1 < m) ? -dfloat(HrR[k * n + r1]) : dfloat(0.f, 0.f);
+        const dfloat xa = shfl((k < 32 ? a0 : a1).value(), k & 31);
+        a0.add(l0, xa);
+        a1.add(l1, xa);
+        if (k >= jb) {  // column jb is zero above row jb
+          const dfloat xb = shfl((k < 32 ? b0 : b1).value(), k & 31);
+          b0.add(l0, xb);
+          b1.add(l1, xb);
+        }
+      }
+      if (r0 >= ja && r0 < m) Xs[ja * xs + r0] = R(a0.value() * dfloat(sq[r0]));
+      if (r1 >= ja && r1 < m) Xs[ja * xs + r1] = R(a1.value() * dfloat(sq[r1]));
+      if (jb < m) {
+        if (r0 >= jb && r0 < m) Xs[jb * xs + r0] = R(b0.value() * dfloat(sq[r0]));
+        if (r1 >= jb && r1 < m) Xs[jb * xs + r1] = R(b1.value() * dfloat(sq[r1]));
+      }
+    }
+  } else if (m <= 64) {
     // column j of X is the forward substitution of e_j alone, so columns
     // are independent: warp w takes columns j = w, w + NW, ... two at a
     // time, lane q holding rows q and q + 32 in registers; x_k reaches the
