@@ -363,7 +363,7 @@ template <int K, typename WGet, typename Emit>
 __device__ __forceinline__ void term_third_gather_dw_k(const TermRegs& t, const dfloat* __restrict__ pw, int E1,
                                                       const dfloat* __restrict__ ix, WGet&& wget, Emit&& emit) {
   dfloat m = dfloat(t.coef), xi[K], u[K], qv[K];
-  dw_comp_sum rs[K], C;
+  dw_dot rs[K], C;
 #pragma unroll
   for (int q = 0; q < K; ++q) {
     m *= pw[t.var[q] * E1 + t.exp[q]];
@@ -375,19 +375,22 @@ __device__ __forceinline__ void term_third_gather_dw_k(const TermRegs& t, const 
 #pragma unroll
     for (int k = j + 1; k < K; ++k) {
       const dfloat w = wget(j, k, t.var[j], t.var[k]);
-      rs[j].add(u[k] * w);
-      rs[k].add(u[j] * w);
+      rs[j].add(u[k], w);
+      rs[k].add(u[j], w);
     }
   }
 #pragma unroll
   for (int l = 0; l < K; ++l) {
-    rs[l].add(xi[l] * wget(l, l, t.var[l], t.var[l]) * (float)(t.exp[l] - 1));
+    rs[l].add(xi[l] * (float)(t.exp[l] - 1), wget(l, l, t.var[l], t.var[l]));
     qv[l] = rs[l].value();
-    C.add(u[l] * qv[l]);
+    C.add(u[l], qv[l]);
   }
   const dfloat Cv = C.value();
 #pragma unroll
-  for (int l = 0; l < K; ++l) emit(t.var[l], m * u[l] * (Cv - xi[l] * qv[l] * 2.0f));
+  for (int l = 0; l < K; ++l) {
+    const dfloat xq = xi[l] * qv[l];
+    emit(t.var[l], m * u[l] * (Cv - dfloat(2.0f * xq.hi, 2.0f * xq.lo)));  // (x2 exact)
+  }
 }
 
 template <typename R, int K, typename WGet, typename Emit>
