@@ -1057,7 +1057,7 @@ __global__ void __launch_bounds__(NT) exact_frame_kernel(StageArgs<R> a) {
 
 // ------------------------------------------------------------------ stage 3
 template <typename R, int NT>
-__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 1024 / NT : std::is_same<R, dfloat>::value ? 512 / NT : 1)
+__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 1024 / NT : std::is_same<R, dfloat>::value ? 640 / NT : 1)
     exact_third_kernel(StageArgs<R> a) {
   using Acc = AccOf<R>;
   extern __shared__ __align__(16) unsigned char sm[];

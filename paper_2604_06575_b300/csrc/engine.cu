@@ -194,121 +194,73 @@ struct CoefOf {
     if (mode == kSimplify) return ca[idx];
     if (mode == kAdd) return idx < ma ? ca[idx] : cb[idx - ma];
     if (mode == kSub) return idx < ma ? ca[idx] : -cb[idx - ma];
-    const int64_t i = idx / mb, j = idx - i * mb;
+    const uint32_t i = idx / (uint32_t)mb, j = idx - i * (uint32_t)mb;  // (N < 2^31)
     return ca[i] * cb[j];
   }
 };
 
-// Each warp owns the segments whose head lies in its chunk [w*CH, (w+1)*CH)
-// (CH = 32 * windows, windows <= kSegWindows), so no segment is split
-// between warps and the summation order is fixed.  The warp first loads the
-// head flags, representative items and coefficients of its whole chunk (all
-// loads in flight together), then walks its 32-item windows: a Hillis-Steele
-// segmented scan on (head, value) over shuffles, the open segment's partial
-// sum carried to the next window, and the lane holding a segment's last item
-// writing the segment's sum, representative item and keep flag.  A segment
-// still open at the chunk's end is finished by reading on, window by window,
-// until the next head.
-constexpr int kSegWindows = 16;
+// Reduce-by-key over the sorted items (runs of equal keys, "segments", start
+// at the head items).  A head item's thread sums its segment left to right
+// while it is at most kSegShort items long (nearly every segment of a
+// product); a longer segment is listed, and one warp per listed segment sums
+// it (lane-strided partial sums, then a fixed shuffle tree).  Both orders are
+// fixed, so the sums do not depend on scheduling.  Each segment writes its
+// sum, a representative item (any item of a segment has the segment's
+// exponent row) and its keep flag at its index (slot of its head).
+constexpr int kSegShort = 32;
 
 template <typename C>
-__device__ __forceinline__ void seg_write(int64_t k, bool h, C v, uint32_t item, const uint32_t* __restrict__ slot,
-                                          double zeroprec, uint32_t* __restrict__ rep, C* __restrict__ sums,
-                                          uint32_t* __restrict__ keep) {
-  const uint32_t sl = slot[k] + (h ? 1u : 0u) - 1u;  // segment index of item k
+__device__ __forceinline__ void seg_write(uint32_t sl, C v, uint32_t item, double zeroprec, uint32_t* __restrict__ rep,
+                                          C* __restrict__ sums, uint32_t* __restrict__ keep) {
   sums[sl] = v;
   rep[sl] = item;
   keep[sl] = fabs((double)v) > zeroprec ? 1u : 0u;
 }
 
 template <typename C>
-__global__ void seg_reduce(const uint32_t* __restrict__ vals, const uint32_t* __restrict__ head,
-                           const uint32_t* __restrict__ slot, int64_t N, int windows, CoefOf<C> coef, double zeroprec,
-                           uint32_t* __restrict__ rep, C* __restrict__ sums, uint32_t* __restrict__ keep) {
-  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  const int64_t lo = w * 32 * windows;
-  if (lo >= N) return;
-  const int64_t hi = std::min<int64_t>(lo + 32 * windows, N);
-  bool hh[kSegWindows];
-  uint32_t vv[kSegWindows];
-  C cv[kSegWindows];
-#pragma unroll
-  for (int r = 0; r < kSegWindows; ++r) {
-    const int64_t k = lo + r * 32 + lane;
-    const bool in = r < windows && k < hi;
-    hh[r] = in ? head[k] != 0u : false;
-    vv[r] = in ? vals[k] : 0u;
-  }
-#pragma unroll
-  for (int r = 0; r < kSegWindows; ++r) {
-    const int64_t k = lo + r * 32 + lane;
-    cv[r] = (r < windows && k < hi) ? coef(vv[r]) : C(0);
-  }
-  // whether the item just past the chunk starts a new segment (or the end)
-  const bool past_is_head = hi >= N || head[hi] != 0u;
-  // first head of the chunk: the items before it belong to the previous warp
-  int64_t fh = hi;
-#pragma unroll
-  for (int r = 0; r < kSegWindows; ++r) {
-    const unsigned b = __ballot_sync(0xffffffffu, hh[r]);
-    if (b && fh == hi) fh = lo + r * 32 + (__ffs(b) - 1);
-  }
-  if (fh >= hi) return;  // no segment starts in this chunk
-  C carry = C(0);
-  C last_v = C(0);
-#pragma unroll
-  for (int r = 0; r < kSegWindows; ++r) {
-    if (r < windows) {
-      const int64_t k = lo + r * 32 + lane;
-      const bool in = k < hi;
-      const bool active = in && k >= fh;
-      const bool h = hh[r];
-      C v = active ? cv[r] : C(0);
-      bool f = active ? h : !in;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const C yv = __shfl_up_sync(0xffffffffu, v, o);
-        const bool yf = __shfl_up_sync(0xffffffffu, f, o);
-        if (lane >= o && !f) {
-          v += yv;
-          f = yf;
-        }
-      }
-      // lanes before this window's first head continue the carried segment
-      const unsigned heads = __ballot_sync(0xffffffffu, active && h);
-      const int first_head = heads ? __ffs(heads) - 1 : 32;
-      if (active && lane < first_head) v += carry;
-      // is the next item a head (or past the end of the data)?
-      // (both shuffles by every lane, before the lanes take their branches)
-      const bool nh_in = __shfl_down_sync(0xffffffffu, (int)h, 1) != 0;
-      const bool nh_next = __shfl_sync(0xffffffffu, (int)hh[r + 1 < kSegWindows ? r + 1 : r], 0) != 0;
-      bool next_head;
-      if (k + 1 >= hi) next_head = past_is_head;
-      else if (lane < 31) next_head = nh_in;
-      else next_head = nh_next;
-      if (active && next_head) seg_write(k, h, v, vv[r], slot, zeroprec, rep, sums, keep);
-      carry = __shfl_sync(0xffffffffu, v, 31);
-      last_v = v;
+__global__ void __launch_bounds__(256) seg_short(const uint32_t* __restrict__ vals, const uint32_t* __restrict__ head,
+                                                 const uint32_t* __restrict__ slot, int64_t N, CoefOf<C> coef,
+                                                 double zeroprec, uint32_t* __restrict__ rep, C* __restrict__ sums,
+                                                 uint32_t* __restrict__ keep, uint32_t* __restrict__ long_list,
+                                                 uint32_t* __restrict__ long_count) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N || !head[k]) return;
+  const uint32_t item = vals[k];
+  C v = coef(item);
+  for (int64_t j = k + 1; j < N && !head[j]; ++j) {
+    if (j - k >= kSegShort) {
+      long_list[atomicAdd(long_count, 1u)] = (uint32_t)k;
+      return;
     }
+    v += coef(vals[j]);
   }
-  if (past_is_head) return;
-  // the chunk's last segment runs on past hi: sum the rest, window by window,
-  // up to the next head
-  const int64_t k_last = hi - 1;
-  const uint32_t item = vals[k_last];
-  C total = __shfl_sync(0xffffffffu, last_v, (int)((k_last - lo) & 31));
-  for (int64_t base = hi;; base += 32) {
-    const int64_t k = base + lane;
-    const bool h = k >= N || head[k] != 0u;
-    const unsigned stops = __ballot_sync(0xffffffffu, h);
-    const int first_stop = stops ? __ffs(stops) - 1 : 32;
-    C v = lane < first_stop ? coef(vals[k]) : C(0);
+  seg_write(slot[k], v, item, zeroprec, rep, sums, keep);
+}
+
+template <typename C>
+__global__ void __launch_bounds__(256) seg_long(const uint32_t* __restrict__ vals, const uint32_t* __restrict__ head,
+                                                const uint32_t* __restrict__ slot, int64_t N, CoefOf<C> coef,
+                                                double zeroprec, uint32_t* __restrict__ rep, C* __restrict__ sums,
+                                                uint32_t* __restrict__ keep, const uint32_t* __restrict__ long_list,
+                                                const uint32_t* __restrict__ long_count) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t count = *long_count;
+  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < count; w += warps) {
+    const int64_t k0 = long_list[w];
+    C v = C(0);
+    for (int64_t base = k0;; base += 32) {
+      const int64_t k = base + lane;
+      // the segment ends before the next head (or the end of the items)
+      const bool stop = k >= N || (k > k0 && head[k] != 0u);
+      const unsigned stops = __ballot_sync(0xffffffffu, stop);
+      const int first_stop = stops ? __ffs(stops) - 1 : 32;
+      if (lane < first_stop) v += coef(vals[k]);
+      if (first_stop < 32) break;
+    }
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    total += v;
-    if (first_stop < 32) break;
+    if (lane == 0) seg_write(slot[k0], v, vals[k0], zeroprec, rep, sums, keep);
   }
-  if (lane == 0) seg_write(k_last, head[k_last] != 0u, total, item, slot, zeroprec, rep, sums, keep);
 }
 
 // Exponent rows of the kept merged terms.  Every item of a key's run has the
@@ -497,9 +449,8 @@ int key_bits_u128(u128 total) {  // bits to represent values 0 .. total-1
 
 template <typename K, typename C, class Mem>
 polylab_status run_pipeline(int n, int D, int64_t N, const std::vector<K>& Sh, int mode, const Operand& A,
-                            const Operand& B, const PolyIn<C>* pa, const PolyIn<C>* pb, double zeroprec,
-                            int bits, PolyOut<C>* out, polylab_alloc_fn alloc, void* ctx, Mem& scr,
-                            cudaStream_t s) {
+                            const Operand& B, const PolyIn<C>* pa, const PolyIn<C>* pb, double zeroprec, int bits,
+                            PolyOut<C>* out, polylab_alloc_fn alloc, void* ctx, Mem& scr, cudaStream_t s) {
   const int D1 = D + 1;
   K* S = nullptr;
   PL_TRY(scr.get(&S, Sh.size()));
@@ -544,15 +495,20 @@ polylab_status run_pipeline(int n, int D, int64_t N, const std::vector<K>& Sh, i
   mark_heads<K><<<(unsigned)ceil_div(N, 256), 256, 0, s>>>(keys, N, head);
   PL_TRY(launch_status("mark_heads"));
   PL_TRY(exclusive_scan(head, slot, N, scr, s));
-  // windows of 32 items per warp: up to kSegWindows, fewer when that would
-  // leave SMs idle
-  const int windows = (int)std::min<int64_t>(kSegWindows, std::max<int64_t>(1, ceil_div(N, (int64_t)num_sms() * 32 * 32)));
-  const int64_t warps = ceil_div(N, (int64_t)32 * windows);
   CoefOf<C> cf{pa->coef, mode != kSimplify ? pb->coef : nullptr, pa->n_terms, mode != kSimplify ? pb->n_terms : 0,
             mode};
-  seg_reduce<C><<<(unsigned)ceil_div(warps * 32, 256), 256, 0, s>>>(vals, head, slot, N, windows, cf, zeroprec, rep,
-                                                                    sums, keep);
-  PL_TRY(launch_status("seg_reduce"));
+  uint32_t* long_list = nullptr;  // heads of the segments longer than kSegShort, then their count
+  const int64_t max_long = N / (kSegShort + 1) + 1;
+  PL_TRY(scr.get(&long_list, max_long + 1));
+  uint32_t* long_count = long_list + max_long;
+  PL_CUDA(cudaMemsetAsync(long_count, 0, sizeof(uint32_t), s));
+  seg_short<C><<<(unsigned)ceil_div(N, 256), 256, 0, s>>>(vals, head, slot, N, cf, zeroprec, rep, sums, keep,
+                                                          long_list, long_count);
+  PL_TRY(launch_status("seg_short"));
+  const int64_t lblocks = std::min<int64_t>(ceil_div(max_long, 8), (int64_t)num_sms() * 8);
+  seg_long<C><<<(unsigned)lblocks, 256, 0, s>>>(vals, head, slot, N, cf, zeroprec, rep, sums, keep, long_list,
+                                                long_count);
+  PL_TRY(launch_status("seg_long"));
   PL_TRY(exclusive_scan(keep, kpos, N, scr, s));
   // the one wait that sizes the output: kept count, exponent overflow and the
   // sort's look-back word
@@ -641,7 +597,7 @@ polylab_status engine_with(Mem& scr, const PolyIn<C>* pa, const PolyIn<C>* pb, i
     std::vector<uint64_t> S64(S128.size());
     for (size_t i = 0; i < S128.size(); ++i) S64[i] = (uint64_t)S128[i];
     return run_pipeline<uint64_t, C, Mem>(n, D, N, S64, mode, A, B, pa, pb, zeroprec, bits, out, alloc, ctx, scr,
-                                       s);
+                                          s);
   }
   return run_pipeline<u128, C, Mem>(n, D, N, S128, mode, A, B, pa, pb, zeroprec, bits, out, alloc, ctx, scr, s);
 }

@@ -12,71 +12,119 @@ namespace {
 
 typedef unsigned __int128 u128;
 
-constexpr int kScanThreads = 256;
-constexpr int kScanItems = 8;
-constexpr int kScanTile = kScanThreads * kScanItems;
-
 // ------------------------------------------------------------------ scan
 
-__global__ void scan_tiles(const uint32_t* __restrict__ in, uint32_t* __restrict__ out, uint32_t* __restrict__ sums,
-                           int64_t n) {
-  __shared__ uint32_t warp_tot[kScanThreads / 32];
-  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
-  uint32_t v[kScanItems];
-  uint32_t run = 0;
-#pragma unroll
-  for (int i = 0; i < kScanItems; ++i) {
-    v[i] = base + i < n ? in[base + i] : 0u;
-    const uint32_t t = v[i];
-    v[i] = run;
-    run += t;
-  }
-  // exclusive scan of thread totals across the block
+constexpr int kScanThreads = 256;
+constexpr int kScanVecs = 4;                                 // 16-byte vectors per thread
+constexpr int kScanTile = kScanThreads * kScanVecs * 4;      // 4096 values
+
+// Exclusive scan of one value per thread over a 256-thread block (wsum: 8
+// words of shared memory).
+__device__ __forceinline__ uint32_t block_excl_scan256(uint32_t v, uint32_t* wsum) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  uint32_t inc = run;
+  uint32_t inc = v;
   for (int o = 1; o < 32; o <<= 1) {
     const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
     if (lane >= o) inc += y;
   }
-  if (lane == 31) warp_tot[wid] = inc;
+  __syncthreads();  // wsum may still be read by an earlier call
+  if (lane == 31) wsum[wid] = inc;
   __syncthreads();
-  if (wid == 0) {
-    uint32_t t = lane < kScanThreads / 32 ? warp_tot[lane] : 0u;
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
-      if (lane >= o) t += y;
-    }
-    if (lane < kScanThreads / 32) warp_tot[lane] = t;
-  }
-  __syncthreads();
-  const uint32_t off = (wid ? warp_tot[wid - 1] : 0u) + inc - run;
+  uint32_t before = 0;
+  for (int w = 0; w < wid; ++w) before += wsum[w];
+  return before + inc - v;
+}
+
+// Four consecutive values starting at q (a multiple of 4): one 16-byte load
+// when the whole vector lies below n and the array is 16-byte aligned,
+// guarded scalar loads otherwise (zeros past n).
+__device__ __forceinline__ uint4 scan_load4(const uint32_t* __restrict__ in, int64_t q, int64_t n, bool vec) {
+  if (vec && q + 3 < n) return *reinterpret_cast<const uint4*>(in + q);
+  uint4 r;
+  r.x = q < n ? in[q] : 0u;
+  r.y = q + 1 < n ? in[q + 1] : 0u;
+  r.z = q + 2 < n ? in[q + 2] : 0u;
+  r.w = q + 3 < n ? in[q + 3] : 0u;
+  return r;
+}
+
+// Scan phase 1: the sum of each 4096-value tile.  Thread t reads vectors
+// t, t + 256, ... of the tile (coalesced).
+__global__ void __launch_bounds__(kScanThreads) scan_tile_sums(const uint32_t* __restrict__ in, int64_t n, bool vec,
+                                                              uint32_t* __restrict__ sums) {
+  __shared__ uint32_t wsum[kScanThreads / 32];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  uint32_t t = 0;
 #pragma unroll
-  for (int i = 0; i < kScanItems; ++i)
-    if (base + i < n) out[base + i] = v[i] + off;
-  if (threadIdx.x == kScanThreads - 1) sums[blockIdx.x] = warp_tot[kScanThreads / 32 - 1];
+  for (int r = 0; r < kScanVecs; ++r) {
+    const uint4 v = scan_load4(in, base + 4 * ((int64_t)r * kScanThreads + threadIdx.x), n, vec);
+    t += v.x + v.y + v.z + v.w;
+  }
+  for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t s = 0;
+    for (int w = 0; w < kScanThreads / 32; ++w) s += wsum[w];
+    sums[blockIdx.x] = s;
+  }
 }
 
-__global__ void add_tile_offsets(uint32_t* __restrict__ out, const uint32_t* __restrict__ offs, int64_t n) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] += offs[i / kScanTile];
+// Scan phase 3: each tile scanned from its offset (offs[tile], or 0 with no
+// offsets), a block scan per round of vectors; in may alias out.
+__global__ void __launch_bounds__(kScanThreads) scan_tiles(const uint32_t* in, uint32_t* out, int64_t n, bool vec,
+                                                          const uint32_t* __restrict__ offs) {
+  __shared__ uint32_t wsum[kScanThreads / 32];
+  __shared__ uint32_t s_total;
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  uint4 v[kScanVecs];
+#pragma unroll
+  for (int r = 0; r < kScanVecs; ++r)
+    v[r] = scan_load4(in, base + 4 * ((int64_t)r * kScanThreads + threadIdx.x), n, vec);
+  uint32_t run = offs ? offs[blockIdx.x] : 0u;
+#pragma unroll
+  for (int r = 0; r < kScanVecs; ++r) {
+    const uint32_t g = v[r].x + v[r].y + v[r].z + v[r].w;
+    const uint32_t pre = run + block_excl_scan256(g, wsum);
+    if (threadIdx.x == kScanThreads - 1) s_total = pre + g;
+    uint4 o;
+    o.x = pre;
+    o.y = o.x + v[r].x;
+    o.z = o.y + v[r].y;
+    o.w = o.z + v[r].z;
+    const int64_t q = base + 4 * ((int64_t)r * kScanThreads + threadIdx.x);
+    if (vec && q + 3 < n) {
+      *reinterpret_cast<uint4*>(out + q) = o;
+    } else {
+      if (q < n) out[q] = o.x;
+      if (q + 1 < n) out[q + 1] = o.y;
+      if (q + 2 < n) out[q + 2] = o.z;
+      if (q + 3 < n) out[q + 3] = o.w;
+    }
+    __syncthreads();
+    run = s_total;
+  }
 }
 
-// Exclusive scan of n uint32 values (in may alias out).  `Mem` provides the
-// scratch buffers (stream-ordered allocations, or a fixed arena).
+// Exclusive scan of n uint32 values (in may alias out): tile sums, their own
+// exclusive scan (recursively), then every tile from its offset.  `Mem`
+// provides the scratch buffers (stream-ordered allocations, or a fixed arena).
 template <class Mem>
 polylab_status exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, Mem& scr, cudaStream_t s) {
   if (n <= 0) return POLYLAB_OK;
   const int64_t tiles = ceil_div(n, kScanTile);
+  const bool vec = (((uintptr_t)in | (uintptr_t)out) & 15) == 0;
+  if (tiles == 1) {
+    scan_tiles<<<1, kScanThreads, 0, s>>>(in, out, n, vec, nullptr);
+    return launch_status("scan_tiles");
+  }
   uint32_t* sums = nullptr;
   PL_TRY(scr.get(&sums, tiles));
-  scan_tiles<<<(unsigned)tiles, kScanThreads, 0, s>>>(in, out, sums, n);
-  PL_TRY(launch_status("scan_tiles"));
-  if (tiles > 1) {
-    PL_TRY(exclusive_scan(sums, sums, tiles, scr, s));
-    add_tile_offsets<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(out, sums, n);
-    PL_TRY(launch_status("add_tile_offsets"));
-  }
-  return POLYLAB_OK;
+  scan_tile_sums<<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, vec, sums);
+  PL_TRY(launch_status("scan_tile_sums"));
+  PL_TRY(exclusive_scan(sums, sums, tiles, scr, s));
+  scan_tiles<<<(unsigned)tiles, kScanThreads, 0, s>>>(in, out, n, vec, sums);
+  return launch_status("scan_tiles");
 }
 
 // -------------------------------------------------------------- radix sort
@@ -85,8 +133,9 @@ polylab_status exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, Mem&
 // Significant Digit Radix Sort for GPUs" (2022):
 //  * a digit pass takes tiles in the order CTAs claim them (an atomic tile
 //    counter, so every earlier tile belongs to a CTA that is already running),
-//    ranks the tile's items by digit in shared memory (per-warp counts from
-//    __match_any_sync, stable), publishes its per-digit counts, and sums the
+//    ranks the tile's items by digit in shared memory (per-warp counts, the
+//    lanes of one digit found by bit ballots; stable), publishes its
+//    per-digit counts, and sums the
 //    counts of the tiles before it by decoupled look-back over their published
 //    words (a word holds a flag -- aggregate of that tile alone, or inclusive
 //    prefix -- and the count; each step reads kLookWidth earlier tiles'
@@ -134,20 +183,19 @@ __device__ __forceinline__ void look_store(uint64_t* p, uint64_t v) {
   asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// Exclusive scan of one value per thread over a 256-thread block.
-__device__ __forceinline__ uint32_t block_excl_scan256(uint32_t v, uint32_t* wsum) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  uint32_t inc = v;
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-    if (lane >= o) inc += y;
+// Lanes of the warp holding the same 8-bit digit d as this lane (lanes whose
+// item is past the end, ok = false, form their own class): one ballot per
+// digit bit, each lane keeping the lanes that agree with it on that bit.
+__device__ __forceinline__ unsigned peers_of_digit(uint32_t d, bool ok) {
+  const unsigned v = __ballot_sync(0xffffffffu, ok);
+  unsigned peers = ok ? v : ~v;
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    const bool bit = (d >> b) & 1u;
+    const unsigned m = __ballot_sync(0xffffffffu, bit);
+    peers &= bit ? m : ~m;
   }
-  __syncthreads();  // wsum may still be read by an earlier call
-  if (lane == 31) wsum[wid] = inc;
-  __syncthreads();
-  uint32_t before = 0;
-  for (int w = 0; w < wid; ++w) before += wsum[w];
-  return before + inc - v;
+  return peers;
 }
 
 template <typename K>
@@ -214,7 +262,7 @@ __global__ void __launch_bounds__(kSortThreads) sort_pass(const K* __restrict__ 
   for (int it = 0; it < IPT; ++it) {
     const bool ok = seg + it * 32 + lane < N;
     const uint32_t d = ok ? digit_of(kk[it], shift) : uint32_t(kSortDigits);
-    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const unsigned peers = peers_of_digit(d, ok);
     const uint32_t before = __popc(peers & lt);
     const uint32_t basec = ok ? mycnt[d] : 0u;
     rk[it] = ok ? basec + before : 0xffffffffu;
@@ -251,7 +299,12 @@ __global__ void __launch_bounds__(kSortThreads) sort_pass(const K* __restrict__ 
   if (t > 0) {
     int64_t tp = (int64_t)t - 1;  // nearest tile not yet summed
     int spins = 0;
-    while (true) {
+    // the previous tile alone first: once the first wave is past, it has
+    // usually published its inclusive count already
+    const uint64_t w1 = look_load(look + (size_t)tp * kSortDigits + d);
+    const bool near = (w1 & ~kLookCount) == kLookInclusive;
+    if (near) excl = w1 & kLookCount;
+    while (!near) {
       uint64_t w[kLookWidth];
 #pragma unroll
       for (int u = 0; u < kLookWidth; ++u)
