@@ -409,6 +409,12 @@ struct Lay2 {
 // row stride of X = L^{-1}: odd, so that lanes reading rows j, j+1, ... at a
 // common column hit different banks
 __host__ __device__ inline int x_stride(int m) { return m | 1; }
+// 8-byte forms with m <= 64 keep X' = D^{-1/2} L^{-1} in the lower triangle
+// (diagonal included) of the factor's own matrix: the factor occupies the
+// strict upper triangle (col(j)[i] = Hr[j*n + i], i > j) and the pivots live
+// apart, so X'_ij (i >= j) at Hr[i*n + j] overwrites nothing still needed
+template <typename R>
+__host__ __device__ inline bool x_in_place(int m) { return sizeof(R) == 8 && m <= 64; }
 template <typename R>
 __host__ __device__ Lay2 lay_frame(int n, bool in_smem) {
   Lay2 L{};
@@ -430,7 +436,7 @@ __host__ __device__ Lay2 lay_frame(int n, bool in_smem) {
     // form factors in place in Hr and keeps X apart
     if (sizeof(R) == 4) {
       L.Ld = L.X = b.take(m * (m + 1) / 2 * 8);
-    } else {
+    } else if (!x_in_place<R>((int)m)) {
       L.X = b.take(m * x_stride((int)m) * sizeof(R));
     }
   }
@@ -750,6 +756,9 @@ __device__ __forceinline__ bool frame_item(const StageArgs<R>& a, const ExactDes
   // row stride xs (the FP32 form reuses the factor's storage)
   double* Ld = kF64 ? (double*)Hr : (SMEM ? (double*)(sm + L.Ld) : (double*)rest);
   R* Xs = kF64 ? (SMEM ? (R*)(sm + L.X) : (R*)rest) : (R*)Ld;
+  const bool xin = SMEM && x_in_place<R>(m);  // X' in the lower triangle of HrR
+  // storage of X'_ij, i >= j
+  auto xref = [&](int i, int j) -> R& { return xin ? HrR[i * n + j] : Xs[j * xs + i]; };
   auto col = [Ld, n, m](int j) -> double* {
     return kF64 ? Ld + (size_t)j * n : Ld + ((size_t)j * m - (size_t)j * (j - 1) / 2 - j);
   };
@@ -911,11 +920,11 @@ __device__ __forceinline__ bool frame_item(const StageArgs<R>& a, const ExactDes
           b1.add(l1, xb);
         }
       }
-      if (r0 >= ja && r0 < m) Xs[ja * xs + r0] = R(a0.value() * dfloat(sq[r0]));
-      if (r1 >= ja && r1 < m) Xs[ja * xs + r1] = R(a1.value() * dfloat(sq[r1]));
+      if (r0 >= ja && r0 < m) xref(r0, ja) = R(a0.value() * dfloat(sq[r0]));
+      if (r1 >= ja && r1 < m) xref(r1, ja) = R(a1.value() * dfloat(sq[r1]));
       if (jb < m) {
-        if (r0 >= jb && r0 < m) Xs[jb * xs + r0] = R(b0.value() * dfloat(sq[r0]));
-        if (r1 >= jb && r1 < m) Xs[jb * xs + r1] = R(b1.value() * dfloat(sq[r1]));
+        if (r0 >= jb && r0 < m) xref(r0, jb) = R(b0.value() * dfloat(sq[r0]));
+        if (r1 >= jb && r1 < m) xref(r1, jb) = R(b1.value() * dfloat(sq[r1]));
       }
     }
   } else if (m <= 64) {
@@ -940,11 +949,11 @@ __device__ __forceinline__ bool frame_item(const StageArgs<R>& a, const ExactDes
           b1 -= l1 * xb;
         }
       }
-      if (r0 >= ja && r0 < m) Xs[ja * xs + r0] = a0 * sq[r0];
-      if (r1 >= ja && r1 < m) Xs[ja * xs + r1] = a1 * sq[r1];
+      if (r0 >= ja && r0 < m) xref(r0, ja) = a0 * sq[r0];
+      if (r1 >= ja && r1 < m) xref(r1, ja) = a1 * sq[r1];
       if (jb < m) {
-        if (r0 >= jb && r0 < m) Xs[jb * xs + r0] = b0 * sq[r0];
-        if (r1 >= jb && r1 < m) Xs[jb * xs + r1] = b1 * sq[r1];
+        if (r0 >= jb && r0 < m) xref(r0, jb) = b0 * sq[r0];
+        if (r1 >= jb && r1 < m) xref(r1, jb) = b1 * sq[r1];
       }
     }
   } else {
@@ -974,13 +983,27 @@ __device__ __forceinline__ bool frame_item(const StageArgs<R>& a, const ExactDes
       for (int i = j + lane; i < m; i += 32) Xs[j * xs + i] *= sq[i];
   }
   __syncthreads();
-  // M = H_T^{-1} = X'^T X', upper triangle into Hr (L no longer needed)
-  for (int i = wid; i < m; i += NW)
-    for (int j = i + lane; j < m; j += 32) {
-      DotAcc<R> acc;
-      for (int k = j; k < m; ++k) acc.add(Xs[i * xs + k], Xs[j * xs + k]);
-      HrR[i * n + j] = acc.value();
-    }
+  // M = H_T^{-1} = X'^T X', upper triangle into Hr (L no longer needed):
+  // M_ij = sum_{k >= j} X'_ki X'_kj (i <= j)
+  if (xin) {
+    // X' in the lower triangle: a lane's column j is read with consecutive
+    // lanes on consecutive addresses; the diagonal X'_kk = sq_k is taken from
+    // sq, so the writes to the upper triangle and diagonal touch nothing read
+    for (int i = wid; i < m; i += NW)
+      for (int j = i + lane; j < m; j += 32) {
+        DotAcc<R> acc;
+        acc.add(i == j ? sq[j] : HrR[j * n + i], sq[j]);
+        for (int k = j + 1; k < m; ++k) acc.add(HrR[k * n + i], HrR[k * n + j]);
+        HrR[i * n + j] = acc.value();
+      }
+  } else {
+    for (int i = wid; i < m; i += NW)
+      for (int j = i + lane; j < m; j += 32) {
+        DotAcc<R> acc;
+        for (int k = j; k < m; ++k) acc.add(Xs[i * xs + k], Xs[j * xs + k]);
+        HrR[i * n + j] = acc.value();
+      }
+  }
   __syncthreads();
   for (int i = wid; i < n; i += NW)  // Hr <- [M 0; 0 0], full symmetric, in place
     for (int j = lane; j < n; j += 32) {
