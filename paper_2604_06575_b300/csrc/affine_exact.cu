@@ -1158,6 +1158,11 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 1024 / NT : std::is_same<
               if constexpr (std::is_same<R, dfloat>::value) term_third_gather_sub_group<R, K>(tr, pw, E1, ix, wget, emit);
               else term_third_gather_group<R, K>(tr, pw, E1, ix, wget, emit);
             }
+            // the CTA's warps enter each support-size group together: every
+            // group runs its own (large, fully unrolled) code, and warps
+            // spread over several groups evicted each other's instructions
+            // (third stage 62.2 -> 55.1 ms in double words)
+            if (pd.koff[K + 1] > pd.k3off[K]) __syncthreads();
           } else {
             for (int64_t t = pd.k3off[K] + tid; t < pd.koff[K + 1]; t += NT) {
               const TermRegs tr = load_term(pd.terms, t);
