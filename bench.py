@@ -665,6 +665,7 @@ def measure_rows(pl, workloads, torch, dev, p32, p64, only=None):
              ("exact_scaling", lambda: measure_exact_scaling(pl, workloads, torch, dev)),
              ("stochastic_band", lambda: measure_stochastic_band(pl, workloads, torch, dev)),
              ("stochastic", lambda: measure_stochastic(pl, workloads, torch, dev, p32)),
+             ("stochastic_jacobi_n500", lambda: measure_stochastic_one(pl, workloads, torch, dev)),
              ("crossover", lambda: measure_crossover(pl, workloads, torch, dev)),
              ("simplify_pd_cubed", lambda: measure_pd3(pl, workloads, torch, dev)),
              ("affine_ad", lambda: measure_ad(pl, workloads, torch, dev, p64)),
@@ -1011,6 +1012,25 @@ def measure_stochastic(pl, workloads, torch, dev, p32):
             del Xd, dp
         out[fam] = rows
     return out
+
+
+def measure_stochastic_one(pl, workloads, torch, dev):
+    """One MF-logDet-Stochastic call alone: the large sparse family at
+    n = 500 (11,000 terms), 4,096 points, FP32, Jacobi, q = 16, tol 1e-4,
+    maxit 80, r = 1e-4 (the first cell of the stochastic row, without the
+    network training around it: the configuration the stochastic kernel's
+    profile is taken on)."""
+    stream = torch.cuda.current_stream()
+    poly, X = workloads.large_sparse(500, P=4096)
+    dp = pl.to_device(poly, dev)
+    Xd = torch.as_tensor(X, device=dev)
+    with pl.Plan(dp) as plan:
+        ms, res = _time_call(torch, lambda: pl.affine_normal(
+            dp, Xd, plan=plan, method="mf-stochastic", regularization=1e-4, num_probes=16, krylov_tol=1e-4,
+            krylov_maxit=80, prec="fp32", precond="jacobi", seed=7), stream)
+        info = pl.info_numpy(res[2])
+    return dict(ms=round(ms, 2), dirs_per_s=round(4096 / (ms * 1e-3), 1),
+                krylov_iters_per_point=round(float(info["krylov_iters"].mean()), 2))
 
 
 def measure_crossover(pl, workloads, torch, dev):

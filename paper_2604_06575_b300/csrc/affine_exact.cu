@@ -383,8 +383,8 @@ __host__ __device__ Lay1 lay_terms(int n, int E1, bool in_smem, bool gather) {
   Bump b;
   L.pw_step = ((size_t)n * E1 * sizeof(R) + 15) & ~size_t(15);
   L.pw = b.take(kTermPoints * L.pw_step);
-  L.g = b.take((size_t)NW * n * sizeof(Acc));  // one replica per warp
   L.red = b.take(kTermPoints * 40 * 8);
+  if (!gather) L.g = b.take((size_t)NW * n * sizeof(Acc));  // one replica per warp
   if (gather) {
     L.ix_step = ((size_t)n * sizeof(R) + 15) & ~size_t(15);
     L.gs_step = ((size_t)n * sizeof(Acc) + 15) & ~size_t(15);
@@ -396,6 +396,11 @@ __host__ __device__ Lay1 lay_terms(int n, int E1, bool in_smem, bool gather) {
     // for chunk term t at [t * kTermPoints + q]): one vector load per record
     L.mv_step = sizeof(R);
     L.mv = b.take((size_t)kTermPoints * kGatherChunk * sizeof(R));
+    // a pass that falls back to the term-by-term sweep (a coordinate out of
+    // the gather range) uses no monomial values: its per-warp gradient
+    // replicas take their place
+    L.g = L.mv;
+    static_assert(kTermPoints * kGatherChunk * sizeof(R) >= 8 * 128 * sizeof(Acc), "replicas fit (n <= 127)");
   }
   L.H_step = (size_t)mat_slot<Acc>(n) * sizeof(Acc);
   L.H = in_smem ? b.take(kTermPoints * L.H_step) : 0;

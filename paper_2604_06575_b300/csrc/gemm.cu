@@ -51,6 +51,12 @@ struct GemmOperand {
   int64_t K = 0, Kpad = 0;  // closure size, padded to 64
   int Npad = 0;             // output columns padded to kGemmNPadQuantum
   ClosMono* mono = nullptr; // Kpad
+  // per closure monomial, its factors as rows of the producers' power table
+  // (v * Et + e - 1): eight for the BF16 table depth, then eight for the TF32
+  // one, 0xffff past the support; built when both tables hold every exponent
+  uint16_t* moff = nullptr;  // Kpad x 16
+  int Et16 = 1, Et32 = 1;
+  bool off16 = false, off32 = false;  // the rows are valid for that form's table
   float* scale = nullptr;   // Npad
   uint16_t* tri_i = nullptr;  // Npad: output column -> (kind, i, j) table
   uint16_t* tri_j = nullptr;
@@ -68,7 +74,8 @@ struct GemmOperand {
 
 void free_gemm_operand(GemmOperand* g, cudaStream_t s) {
   if (!g) return;
-  for (void* p : {(void*)g->mono, (void*)g->scale, (void*)g->tri_i, (void*)g->tri_j, (void*)g->kind, (void*)g->b16,
+  for (void* p : {(void*)g->mono, (void*)g->moff, (void*)g->scale, (void*)g->tri_i, (void*)g->tri_j, (void*)g->kind,
+                  (void*)g->b16,
                   (void*)g->live16_dev, (void*)g->half16_dev, (void*)g->t32, (void*)g->live32_dev})
     if (p) cudaFreeAsync(p, s);
   delete g;
@@ -180,6 +187,30 @@ __global__ void closure_unrank(const uint64_t* __restrict__ ukeys, int64_t K, in
     cm.pad[0] = (uint8_t)(k < kMaxSupport ? k : kMaxSupport);  // support size
   }
   mono[q] = cm;
+}
+
+// Power-table rows of every closure monomial's factors (see GemmOperand::moff).
+// An exponent beyond the table depth Et takes several rows (x^e = (x^Et)^k
+// x^r); the host only builds the rows when every monomial fits in eight.
+__device__ __forceinline__ void table_rows(const ClosMono& cm, int Et, uint16_t* out) {
+  int k = 0;
+  for (int s = 0; s < cm.pad[0] && s < kMaxSupport; ++s) {
+    int e = cm.exp[s];
+    while (e > 0 && k < 8) {
+      const int take = e < Et ? e : Et;
+      out[k++] = (uint16_t)(cm.var[s] * Et + take - 1);
+      e -= take;
+    }
+  }
+  while (k < 8) out[k++] = (uint16_t)0xffff;
+}
+__global__ void closure_offsets(const ClosMono* __restrict__ mono, int64_t Kpad, int Et16, int Et32,
+                                uint16_t* __restrict__ moff) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= Kpad) return;
+  const ClosMono cm = mono[q];
+  table_rows(cm, Et16, moff + q * 16);
+  table_rows(cm, Et32, moff + q * 16 + 8);
 }
 
 __device__ __forceinline__ int64_t find_key(const uint64_t* __restrict__ ukeys, int64_t K, uint64_t key) {
@@ -353,6 +384,7 @@ struct GemmArgs {
   double* H;
   int* err;
   int Et;   // depth of the per-point power table (x^1..x^Et)
+  const uint16_t* moff;  // power-table rows per closure monomial (null: decode var/exp)
   int tma;  // 1: the CTA's 128 x n point tile arrives by one tensor-map copy (n even, X 16-byte aligned)
 };
 
@@ -464,9 +496,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_eval_kernel(GemmArgs a, 
   int nlive = 0;
   while (nlive < a.Kt && live[nlive] >= 0) ++nlive;
   constexpr uint32_t kRecBytes = Cf::KT * sizeof(ClosMono);
+  // records: the monomials' power-table rows when the plan built them (same
+  // 32-byte stride), else their variables and exponents
+  const ClosMono* recsrc = a.moff ? reinterpret_cast<const ClosMono*>(a.moff) : a.mono;
   if (tid == 0 && nlive > 0) {
     mbar_arrive_expect_tx(&mrec[0], kRecBytes);
-    bulk_g2s(recs[0], a.mono + (int64_t)live[0] * Cf::KT, kRecBytes, &mrec[0]);
+    bulk_g2s(recs[0], recsrc + (int64_t)live[0] * Cf::KT, kRecBytes, &mrec[0]);
   }
   const unsigned char* gblk = a.blocks + (size_t)chunk * a.Kt * Cf::BBYTES;
   constexpr uint32_t kN = KIND == 0 ? 256 : 256;
@@ -488,7 +523,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_eval_kernel(GemmArgs a, 
       if (it + 1 < nlive) {  // the other record buffer was last read before the barrier above
         fence_proxy_async_smem();
         mbar_arrive_expect_tx(&mrec[st ^ 1], kRecBytes);
-        bulk_g2s(recs[st ^ 1], a.mono + (int64_t)live[it + 1] * Cf::KT, kRecBytes, &mrec[st ^ 1]);
+        bulk_g2s(recs[st ^ 1], recsrc + (int64_t)live[it + 1] * Cf::KT, kRecBytes, &mrec[st ^ 1]);
       }
     }
     if (!mbar_wait(&mrec[st], (it >> 1) & 1, a.err)) s_abort = 1;
@@ -501,8 +536,22 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_eval_kernel(GemmArgs a, 
       float val[PER];
 #pragma unroll
       for (int q = 0; q < PER; ++q) {
-        // two 16-byte loads: variables (8 x u16), then exponents (8 x u8)
         const uint4* src = reinterpret_cast<const uint4*>(mm + c16 * PER + q);
+        if (a.moff) {
+          // one 16-byte load: the factors' power-table rows (uniform over the warp)
+          const uint4 wo = src[KIND == 0 ? 0 : 1];
+          const uint32_t ow[4] = {wo.x, wo.y, wo.z, wo.w};
+          float prod = 1.0f;
+#pragma unroll
+          for (int s2 = 0; s2 < kMaxSupport; ++s2) {
+            const uint32_t o = (ow[s2 >> 1] >> ((s2 & 1) * 16)) & 0xffffu;
+            if (o == 0xffffu) break;
+            prod *= pwt[o * 128 + r];
+          }
+          val[q] = prod;
+          continue;
+        }
+        // two 16-byte loads: variables (8 x u16), then exponents (8 x u8)
         const uint4 wv = src[0];
         const uint4 we = src[1];
         const uint32_t vw[4] = {wv.x, wv.y, wv.z, wv.w};
@@ -796,6 +845,17 @@ polylab_status build_gemm_operand(polylab_plan* plan, cudaStream_t s) {
   PL_CUDA(cudaMallocAsync(&g->mono, Kpad * sizeof(ClosMono), s));
   closure_unrank<<<(unsigned)ceil_div(Kpad, 128), 128, 0, s>>>(ukeys, K, Kpad, n, dS, D1, g->mono);
   PL_TRY(launch_status("closure_unrank"));
+  g->Et16 = table_depth<0>(n, plan->max_exp);
+  g->Et32 = table_depth<1>(n, plan->max_exp);
+  // rows per monomial at most (support) x ceil(max exponent / depth): valid when that is <= 8
+  const int ksup = std::max(1, plan->max_support);
+  g->off16 = ksup * ((plan->max_exp + g->Et16 - 1) / g->Et16) <= 8;
+  g->off32 = ksup * ((plan->max_exp + g->Et32 - 1) / g->Et32) <= 8;
+  if ((g->off16 || g->off32) && (int64_t)n * std::max(g->Et16, g->Et32) < 0xffff) {
+    PL_CUDA(cudaMallocAsync(&g->moff, (size_t)Kpad * 16 * sizeof(uint16_t), s));
+    closure_offsets<<<(unsigned)ceil_div(Kpad, 128), 128, 0, s>>>(g->mono, Kpad, g->Et16, g->Et32, g->moff);
+    PL_TRY(launch_status("closure_offsets"));
+  }
   double* C;
   PL_TRY(scr.get(&C, (size_t)Kpad * Npad));
   PL_CUDA(cudaMemsetAsync(C, 0, (size_t)Kpad * Npad * 8, s));
@@ -941,6 +1001,7 @@ polylab_status eval_gemm(const polylab_plan* plan, const double* X, int64_t P, i
   a.H = H;
   a.err = err;
   a.tma = tma ? 1 : 0;
+  a.moff = (prec == POLYLAB_BF16 ? g->off16 : g->off32) ? g->moff : nullptr;
   const unsigned gx = (unsigned)ceil_div(P, 128);
   if (prec == POLYLAB_BF16) {
     a.Et = table_depth<0>(n, plan->max_exp);
