@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--forms", default="fp64,f32x2,fp32", help="forms to time (profiling runs time one)")
     ap.add_argument("--rows-only", action="store_true", help="only the per-row measurements (profiling runs)")
     ap.add_argument("--rows", default="", help="comma-separated row names to measure (default: every row)")
+    ap.add_argument("--eager", action="store_true",
+                    help="launch each step's kernels directly instead of replaying a CUDA graph (profiler runs)")
     ap.add_argument("--config", default=None,
                     help="threads,ctas_per_sm,order[,term_threads,terms_ctas,third_ctas,frame_split,"
                          "third_threads] in place of autotuning (profiling runs)")
@@ -408,8 +410,17 @@ def main():
         if world > 1:
             dist.barrier()
 
+    class _Eager:  # stands in for a graph: replay() launches the run directly
+        def __init__(self, batch):
+            self.batch = batch
+
+        def replay(self):
+            self.batch.run()
+
     def capture(batch):
         """One run (the work-counter memsets and the persistent launches of the three stages) in a CUDA graph."""
+        if args.eager:
+            return _Eager(batch)
         g = torch.cuda.CUDAGraph()
         side = torch.cuda.Stream()
         side.wait_stream(torch.cuda.current_stream())
