@@ -73,7 +73,7 @@ def parse():
                     help="launch each step's kernels directly instead of replaying a CUDA graph (profiler runs)")
     ap.add_argument("--config", default=None,
                     help="threads,ctas_per_sm,order[,term_threads,terms_ctas,third_ctas,frame_split,"
-                         "third_threads] in place of autotuning (profiling runs)")
+                         "third_threads,third_split] in place of autotuning (profiling runs)")
     return ap.parse_args()
 
 
@@ -665,15 +665,16 @@ def main():
 
 
 def stage_launches(cfg: dict, polys, Xs) -> dict:
-    """Kernel launches of one run per stage: one launch per term sweep and,
-    with frame_split, one frame launch per non-empty class of n (n > 40,
-    24 < n <= 40, n <= 24)."""
+    """Kernel launches of one run per stage: one launch of the gradient/Hessian
+    sweep, one third-stage launch per range of support sizes (third_split)
+    and, with frame_split, one frame launch per non-empty class of n
+    (n > 40, 24 < n <= 40, n <= 24)."""
     ns = [p.n for p, X in zip(polys, Xs) if X.shape[0] > 0]
     if cfg.get("frame_split", 0):
         frame = sum(1 for lo, hi in ((40, 1 << 30), (24, 40), (0, 24)) if any(lo < n <= hi for n in ns))
     else:
         frame = 1
-    return dict(terms=1, frame=frame, third=1)
+    return dict(terms=1, frame=frame, third=int(cfg.get("third_split", 1)))
 
 
 def measure_rows(pl, workloads, torch, dev, p32, p64, only=None):

@@ -387,6 +387,13 @@ typedef struct {
    * launch over all polynomials. */
   int32_t frame_split;
   int32_t third_threads;  /* CTA size of the third-derivative sweep (64, 128 or 256) */
+  /* third_split (1..4): the third-derivative sweep as that many launches over
+   * ranges of term support sizes ({1..8}; {1..4},{5..8}; {1..3},{4},{5..8};
+   * {1..3},{4},{5},{6..8}), each contracting its terms into the point's
+   * partial trace term and the last forming the direction: every launch then
+   * runs one support size's code at a time on all SMs (instruction-cache
+   * locality), at the price of loading W once per launch. */
+  int32_t third_split;
 } polylab_batch_config;
 
 polylab_status polylab_batch_create(int32_t n_polys, const polylab_poly* polys,
@@ -413,7 +420,8 @@ polylab_status polylab_batch_set_config(polylab_batch* batch, const polylab_batc
 /* The project's autotuner, stage by stage on this batch (one warm-up and
  * `reps` timed runs per trial, CUDA events on `stream`, synchronising):
  * term_threads in {64,128,256} timed over the gradient/Hessian sweep and
- * third_threads in {64,128,256} over the third-derivative sweep, then
+ * third_threads in {64,128,256} and then third_split in {1,2,3} over the
+ * third-derivative sweep, then
  * frame_split in {1, 0} x threads in {64,128,256} x ctas_per_sm in
  * {occupancy, 2, 4} timed over the frame stage,
  * then order in {cost order, given order} timed over the whole run.  Keeps

@@ -133,7 +133,9 @@ __device__ __forceinline__ dfloat shfl_r(dfloat v, int src) { return shfl(v, src
 // Per-point record of small vectors in the workspace (doubles):
 // [0,n) g | [n,2n) v | [2n,3n) e | [3n,4n) h | 4n: sum |g terms| | 4n+1: |g|
 // | 4n+2: beta | 4n+3: log-det | 4n+4: status
-__host__ __device__ inline int64_t vrec(int n) { return 4 * (int64_t)n + 8; }
+// per-point record: g, v, e, h (n each), 8 scalars, then the trace term's
+// partial sums c (n) carried between the launches of a split third stage
+__host__ __device__ inline int64_t vrec(int n) { return 5 * (int64_t)n + 8; }
 constexpr double kStOk = 0.0, kStZero = 1.0, kStNotPd = 2.0;
 
 // Elements of a point's n x n slot in the matrix workspaces: n^2 rounded up to
@@ -490,6 +492,7 @@ struct StageArgs {
   unsigned char* gws;
   size_t gws_stride;
   int* err;  // set when a bounded wait expires
+  int kmin, kmax;  // third stage: the support sizes this launch contracts (all launches of a step cover 1..8)
 };
 
 __device__ __forceinline__ void write_failed(const ExactDesc& pd, int64_t p, int n, double gn, int flag) {
@@ -1107,6 +1110,15 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 1024 / NT : std::is_same<
     const int n = pd.n, m = n - 1, E1 = pd.E + 1;
     const double* rec = a.vecs + pd.vec_off + p * vrec(n);
     if (rec[4 * n + 4] != kStOk) continue;  // flagged by stage 2 (same value for the whole CTA)
+    if (a.kmax < kMaxSupport) {  // a launch before the last: nothing to do without terms of its sizes
+      bool any = false;
+      for (int k = max(a.kmin, 1); k <= a.kmax; ++k) any |= pd.koff[k + 1] > pd.k3off[k];
+      if (!any) {
+        if (a.kmin <= 1)
+          for (int i = tid; i < n; i += NT) const_cast<double*>(rec)[4 * n + 8 + i] = 0.0;
+        continue;
+      }
+    }
     const Lay3 L = lay_third<R, NW>(n, E1, pd.w_in_smem);
     R* pw = (R*)(sm + L.pw);
     Acc* c = (Acc*)(sm + L.c);
@@ -1153,6 +1165,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 1024 / NT : std::is_same<
       // its first term of degree >= 3
       for_support<kMaxSupport>([&](auto kc) {
         constexpr int K = decltype(kc)::value;
+        if (K < a.kmin || K > a.kmax) return;  // (uniform: another launch of the step takes this size)
         if constexpr (K >= 1) {
           if (gather) {
             for (int64_t t = pd.k3off[K] + tid; t < pd.koff[K + 1]; t += NT) {
@@ -1178,6 +1191,18 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 1024 / NT : std::is_same<
       });
     }
     __syncthreads();
+    // c of this launch's support sizes, added to the earlier launches' in
+    // launch order; a launch before the last passes the sum on
+    double* cpart = const_cast<double*>(rec) + 4 * n + 8;
+    const bool first = a.kmin <= 1, last = a.kmax >= kMaxSupport;
+    if (!last) {
+      for (int i = tid; i < n; i += NT) {
+        Acc s = c[i];
+        for (int q = 1; q < NW; ++q) s += c[q * n + i];
+        cpart[i] = (first ? 0.0 : cpart[i]) + (double)s;
+      }
+      continue;  // (the next item's first barrier orders these reads of c before its writes)
+    }
     const double gn = rec[4 * n + 1], beta = rec[4 * n + 2];
     // a = (P c)[0:m] = c - beta v (v.c);  tv = [h - |g|/(n+1) a; 0];  yr = P tv  (warp 0)
     if (wid == 0) {
@@ -1185,8 +1210,9 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 1024 / NT : std::is_same<
       for (int i = lane; i < n; i += 32) {
         Acc s = c[i];
         for (int q = 1; q < NW; ++q) s += c[q * n + i];
-        y[i] = (double)s;
-        vc += v[i] * (double)s;
+        const double ci = (first ? 0.0 : cpart[i]) + (double)s;
+        y[i] = ci;
+        vc += v[i] * ci;
       }
       vc = warp_sum(vc);
       const double wgt = gn / (double)(n + 1);
@@ -1312,9 +1338,27 @@ static polylab_status launch_stage_t(ExactBatch* b, int stage, cudaStream_t s) {
   a.gws = b->gws;
   a.gws_stride = b->gws_stride;
   a.err = b->err;
-  PL_CUDA(cudaMemsetAsync(a.counter, 0, sizeof(int), s));
-  k<<<(unsigned)grid, NT, smem, s>>>(a);
-  return launch_status(stage == 0 ? "exact_terms_kernel" : stage == 1 ? "exact_frame_kernel" : "exact_third_kernel");
+  a.kmin = 1;
+  a.kmax = kMaxSupport;
+  if (stage != 2) {
+    PL_CUDA(cudaMemsetAsync(a.counter, 0, sizeof(int), s));
+    k<<<(unsigned)grid, NT, smem, s>>>(a);
+    return launch_status(stage == 0 ? "exact_terms_kernel" : "exact_frame_kernel");
+  }
+  // the third stage as one launch per range of support sizes, in order
+  static const int kRanges[4][4][2] = {{{1, kMaxSupport}},
+                                       {{1, 4}, {5, kMaxSupport}},
+                                       {{1, 3}, {4, 4}, {5, kMaxSupport}},
+                                       {{1, 3}, {4, 4}, {5, 5}, {6, kMaxSupport}}};
+  const int split = std::min(4, std::max(1, b->cfg.third_split));
+  for (int g = 0; g < split; ++g) {
+    a.kmin = kRanges[split - 1][g][0];
+    a.kmax = kRanges[split - 1][g][1];
+    PL_CUDA(cudaMemsetAsync(a.counter, 0, sizeof(int), s));
+    k<<<(unsigned)grid, NT, smem, s>>>(a);
+    PL_TRY(launch_status("exact_third_kernel"));
+  }
+  return POLYLAB_OK;
 }
 
 // One class of the split frame stage: the class's item

@@ -257,6 +257,7 @@ polylab_status polylab_batch_get_config(const polylab_batch* b, polylab_batch_co
   cfg->third_ctas = b->b.cfg.third_ctas;
   cfg->frame_split = b->b.cfg.frame_split;
   cfg->third_threads = b->b.cfg.third_threads;
+  cfg->third_split = b->b.cfg.third_split;
   return POLYLAB_OK;
 }
 
@@ -268,13 +269,14 @@ polylab_status polylab_batch_set_config(polylab_batch* b, const polylab_batch_co
   auto ok_cap = [](int c) { return c >= 0 && c <= 32; };
   if (!ok_cap(cfg->ctas_per_sm) || !ok_cap(cfg->terms_ctas) || !ok_cap(cfg->third_ctas) ||
       (cfg->order != 0 && cfg->order != 1) ||
-      (cfg->frame_split != 0 && cfg->frame_split != 1))
+      (cfg->frame_split != 0 && cfg->frame_split != 1) || cfg->third_split < 1 || cfg->third_split > 4)
     return POLYLAB_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   const bool reorder = cfg->order != b->b.cfg.order;
   b->b.cfg.terms_ctas = cfg->terms_ctas;
   b->b.cfg.third_ctas = cfg->third_ctas;
   b->b.cfg.frame_split = cfg->frame_split;
+  b->b.cfg.third_split = cfg->third_split;
   const bool relayout = cfg->threads != b->b.cfg.threads || cfg->term_threads != b->b.cfg.term_threads ||
                         cfg->third_threads != b->b.cfg.third_threads;
   b->b.cfg.third_threads = cfg->third_threads;
@@ -294,7 +296,7 @@ polylab_status polylab_batch_autotune(polylab_batch* b, int32_t reps, polylab_st
   ExactBatch* eb = &b->b;
   polylab_batch_config cur{eb->cfg.threads,    eb->cfg.ctas_per_sm, eb->cfg.order,
                            eb->cfg.term_threads, eb->cfg.terms_ctas,  eb->cfg.third_ctas,
-                           eb->cfg.frame_split,  eb->cfg.third_threads};
+                           eb->cfg.frame_split,  eb->cfg.third_threads, eb->cfg.third_split};
   cur.terms_ctas = 0;
   cur.third_ctas = 0;
   cudaEvent_t e0, e1;
@@ -337,6 +339,21 @@ polylab_status polylab_batch_autotune(polylab_batch* b, int32_t reps, polylab_st
       polylab_batch_config c = cur;
       (sweep == 0 ? c.term_threads : c.third_threads) = tt;
       if ((st = trial(c, 2 * sweep, 2 * sweep, &t)) != POLYLAB_OK) break;
+      if (t < best_t) {
+        best_t = t;
+        best = c;
+      }
+    }
+    cur = best;
+  }
+  // 1b. launches of the third-derivative sweep
+  if (st == POLYLAB_OK) {
+    polylab_batch_config best = cur;
+    best_t = 1e30f;
+    for (int sp : {1, 2, 3}) {
+      polylab_batch_config c = cur;
+      c.third_split = sp;
+      if ((st = trial(c, 2, 2, &t)) != POLYLAB_OK) break;
       if (t < best_t) {
         best_t = t;
         best = c;

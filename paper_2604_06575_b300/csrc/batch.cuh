@@ -40,6 +40,7 @@ struct ExactConfig {
   int third_ctas = 0;
   int frame_split = 1;    // frame stage in classes of polynomials by n
   int third_threads = 0;  // CTA size of the third-derivative sweep (0: 128)
+  int third_split = 2;    // launches of the third-derivative sweep (ranges of support sizes)
 };
 
 // A class of the split frame stage: polynomials with n in (n_lo, n_hi], a

@@ -56,7 +56,7 @@ class _AnOpts(C.Structure):
 class _BatchConfig(C.Structure):
     _fields_ = [("threads", C.c_int32), ("ctas_per_sm", C.c_int32), ("order", C.c_int32),
                 ("term_threads", C.c_int32), ("terms_ctas", C.c_int32), ("third_ctas", C.c_int32),
-                ("frame_split", C.c_int32), ("third_threads", C.c_int32)]
+                ("frame_split", C.c_int32), ("third_threads", C.c_int32), ("third_split", C.c_int32)]
 
 
 INFO_DTYPE = np.dtype([("grad_norm", "<f8"), ("logdet", "<f8"), ("flags", "<i4"), ("hv_evals", "<i4"),
@@ -455,7 +455,7 @@ class Batch:
         _check("polylab_batch_run_stage", _lib.polylab_batch_run_stage(self.h, stage, _stream()))
 
     CONFIG_KEYS = ("threads", "ctas_per_sm", "order", "term_threads", "terms_ctas", "third_ctas", "frame_split",
-                   "third_threads")
+                   "third_threads", "third_split")
 
     def config(self):
         c = _BatchConfig()
@@ -463,12 +463,12 @@ class Batch:
         return {k: getattr(c, k) for k in self.CONFIG_KEYS}
 
     def set_config(self, threads, ctas_per_sm, order, term_threads=None, terms_ctas=None, third_ctas=None,
-                   frame_split=None, third_threads=None):
+                   frame_split=None, third_threads=None, third_split=None):
         """Keys left as None keep their current value."""
         cur = self.config()
         given = dict(threads=threads, ctas_per_sm=ctas_per_sm, order=order, term_threads=term_threads,
                      terms_ctas=terms_ctas, third_ctas=third_ctas, frame_split=frame_split,
-                     third_threads=third_threads)
+                     third_threads=third_threads, third_split=third_split)
         c = _BatchConfig(*[cur[k] if given[k] is None else given[k] for k in self.CONFIG_KEYS])
         _check("polylab_batch_set_config", _lib.polylab_batch_set_config(self.h, C.byref(c), _stream()))
 

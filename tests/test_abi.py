@@ -61,6 +61,7 @@ def test_bench_counts_launches_per_step():
     assert bench.stage_launches(dict(frame_split=1), polys, Xs) == dict(terms=1, frame=3, third=1)
     assert bench.stage_launches(dict(frame_split=1), polys[:1], Xs[:1]) == dict(terms=1, frame=1, third=1)
     assert bench.stage_launches(dict(frame_split=0), polys, Xs) == dict(terms=1, frame=1, third=1)
+    assert bench.stage_launches(dict(frame_split=1, third_split=2), polys, Xs) == dict(terms=1, frame=3, third=2)
 
 
 def test_header_is_plain_c(tmp_path):
