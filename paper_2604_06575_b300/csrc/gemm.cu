@@ -55,6 +55,7 @@ struct GemmOperand {
   // (v * Et + e - 1): eight for the BF16 table depth, then eight for the TF32
   // one, 0xffff past the support; built when both tables hold every exponent
   uint16_t* moff = nullptr;  // Kpad x 16
+  int* tslots = nullptr;     // Kpad / 64 (BF16 tiles), then Kpad / 32 (TF32 tiles)
   int Et16 = 1, Et32 = 1;
   bool off16 = false, off32 = false;  // the rows are valid for that form's table
   float* scale = nullptr;   // Npad
@@ -74,7 +75,7 @@ struct GemmOperand {
 
 void free_gemm_operand(GemmOperand* g, cudaStream_t s) {
   if (!g) return;
-  for (void* p : {(void*)g->mono, (void*)g->moff, (void*)g->scale, (void*)g->tri_i, (void*)g->tri_j, (void*)g->kind,
+  for (void* p : {(void*)g->mono, (void*)g->moff, (void*)g->tslots, (void*)g->scale, (void*)g->tri_i, (void*)g->tri_j, (void*)g->kind,
                   (void*)g->b16,
                   (void*)g->live16_dev, (void*)g->half16_dev, (void*)g->t32, (void*)g->live32_dev})
     if (p) cudaFreeAsync(p, s);
@@ -192,7 +193,9 @@ __global__ void closure_unrank(const uint64_t* __restrict__ ukeys, int64_t K, in
 // Power-table rows of every closure monomial's factors (see GemmOperand::moff).
 // An exponent beyond the table depth Et takes several rows (x^e = (x^Et)^k
 // x^r); the host only builds the rows when every monomial fits in eight.
-__device__ __forceinline__ void table_rows(const ClosMono& cm, int Et, uint16_t* out) {
+// Unused rows point at the table's row of ones (row n * Et); returns the
+// number of rows used.
+__device__ __forceinline__ int table_rows(const ClosMono& cm, int n, int Et, uint16_t* out) {
   int k = 0;
   for (int s = 0; s < cm.pad[0] && s < kMaxSupport; ++s) {
     int e = cm.exp[s];
@@ -202,15 +205,20 @@ __device__ __forceinline__ void table_rows(const ClosMono& cm, int Et, uint16_t*
       e -= take;
     }
   }
-  while (k < 8) out[k++] = (uint16_t)0xffff;
+  const int used = k;
+  while (k < 8) out[k++] = (uint16_t)(n * Et);
+  return used;
 }
-__global__ void closure_offsets(const ClosMono* __restrict__ mono, int64_t Kpad, int Et16, int Et32,
-                                uint16_t* __restrict__ moff) {
+// Rows of every monomial, and per K tile the most rows any of its monomials
+// uses (tslots: BF16 tiles of 64 monomials, then TF32 tiles of 32).
+__global__ void closure_offsets(const ClosMono* __restrict__ mono, int64_t Kpad, int n, int Et16, int Et32,
+                                uint16_t* __restrict__ moff, int* __restrict__ tslots16,
+                                int* __restrict__ tslots32) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= Kpad) return;
   const ClosMono cm = mono[q];
-  table_rows(cm, Et16, moff + q * 16);
-  table_rows(cm, Et32, moff + q * 16 + 8);
+  atomicMax(&tslots16[q / 64], table_rows(cm, n, Et16, moff + q * 16));
+  atomicMax(&tslots32[q / 32], table_rows(cm, n, Et32, moff + q * 16 + 8));
 }
 
 __device__ __forceinline__ int64_t find_key(const uint64_t* __restrict__ ukeys, int64_t K, uint64_t key) {
@@ -385,6 +393,7 @@ struct GemmArgs {
   int* err;
   int Et;   // depth of the per-point power table (x^1..x^Et)
   const uint16_t* moff;  // power-table rows per closure monomial (null: decode var/exp)
+  const int* tslots;     // per K tile: rows used by its monomials at most
   int tma;  // 1: the CTA's 128 x n point tile arrives by one tensor-map copy (n even, X 16-byte aligned)
 };
 
@@ -428,7 +437,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_eval_kernel(GemmArgs a, 
   // otherwise be read from L2 by every producer thread)
   ClosMono* recs[2];
   {
-    unsigned char* rb = (unsigned char*)(((uintptr_t)(pwt + (size_t)a.n * a.Et * 128) + 15) & ~(uintptr_t)15);
+    unsigned char* rb = (unsigned char*)(((uintptr_t)(pwt + ((size_t)a.n * a.Et + 1) * 128) + 15) & ~(uintptr_t)15);
     recs[0] = (ClosMono*)rb;
     recs[1] = (ClosMono*)(rb + Cf::KT * sizeof(ClosMono));
   }
@@ -485,6 +494,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_eval_kernel(GemmArgs a, 
       pw *= x;
     }
   }
+  if (tid < 128) pwt[(size_t)n * Et * 128 + tid] = 1.0f;  // the row of ones (padding rows of a monomial)
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   // the B stage buffers are written by bulk copies from here on: order the
@@ -530,27 +540,38 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_eval_kernel(GemmArgs a, 
     // monomial tile: row r, KT consecutive closure monomials in 16-byte chunks;
     // thread part q fills chunks 2q and 2q+1
     const ClosMono* mm = recs[st];
+    const int ns = a.moff ? a.tslots[kt] : 0;  // rows per monomial in this tile (uniform)
 #pragma unroll 1
     for (int c16 = part * 2; c16 < part * 2 + 2; ++c16) {
       constexpr int PER = 16 / Cf::ESZ;
       float val[PER];
+      if (a.moff) {
+        // the chunk's monomials side by side: one 16-byte load of power-table
+        // rows each (the same for the whole warp), then row by row a product
+        // per monomial, so the PER products proceed together
+        uint32_t ow[PER][4];
 #pragma unroll
-      for (int q = 0; q < PER; ++q) {
-        const uint4* src = reinterpret_cast<const uint4*>(mm + c16 * PER + q);
-        if (a.moff) {
-          // one 16-byte load: the factors' power-table rows (uniform over the warp)
-          const uint4 wo = src[KIND == 0 ? 0 : 1];
-          const uint32_t ow[4] = {wo.x, wo.y, wo.z, wo.w};
-          float prod = 1.0f;
-#pragma unroll
-          for (int s2 = 0; s2 < kMaxSupport; ++s2) {
-            const uint32_t o = (ow[s2 >> 1] >> ((s2 & 1) * 16)) & 0xffffu;
-            if (o == 0xffffu) break;
-            prod *= pwt[o * 128 + r];
-          }
-          val[q] = prod;
-          continue;
+        for (int q = 0; q < PER; ++q) {
+          const uint4 wo = reinterpret_cast<const uint4*>(mm + c16 * PER + q)[KIND == 0 ? 0 : 1];
+          ow[q][0] = wo.x;
+          ow[q][1] = wo.y;
+          ow[q][2] = wo.z;
+          ow[q][3] = wo.w;
+          val[q] = 1.0f;
         }
+#pragma unroll
+        for (int s2 = 0; s2 < kMaxSupport; ++s2) {
+          if (s2 >= ns) break;
+#pragma unroll
+          for (int q = 0; q < PER; ++q) {
+            const uint32_t o = (ow[q][s2 >> 1] >> ((s2 & 1) * 16)) & 0xffffu;
+            val[q] *= pwt[o * 128 + r];
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < PER && !a.moff; ++q) {
+        const uint4* src = reinterpret_cast<const uint4*>(mm + c16 * PER + q);
         // two 16-byte loads: variables (8 x u16), then exponents (8 x u8)
         const uint4 wv = src[0];
         const uint4 we = src[1];
@@ -744,7 +765,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_eval_kernel(GemmArgs a, 
 template <int KIND>
 constexpr size_t gemm_smem(int n, int Et) {
   using Cf = GemmCfg<KIND>;
-  return 1024 + 2 * (size_t)Cf::ABYTES + 2 * (size_t)Cf::BBYTES + (size_t)n * Et * 128 * 4 + 16 +
+  return 1024 + 2 * (size_t)Cf::ABYTES + 2 * (size_t)Cf::BBYTES + ((size_t)n * Et + 1) * 128 * 4 + 16 +
          2 * (size_t)Cf::KT * sizeof(ClosMono);
 }
 
@@ -853,7 +874,10 @@ polylab_status build_gemm_operand(polylab_plan* plan, cudaStream_t s) {
   g->off32 = ksup * ((plan->max_exp + g->Et32 - 1) / g->Et32) <= 8;
   if ((g->off16 || g->off32) && (int64_t)n * std::max(g->Et16, g->Et32) < 0xffff) {
     PL_CUDA(cudaMallocAsync(&g->moff, (size_t)Kpad * 16 * sizeof(uint16_t), s));
-    closure_offsets<<<(unsigned)ceil_div(Kpad, 128), 128, 0, s>>>(g->mono, Kpad, g->Et16, g->Et32, g->moff);
+    PL_CUDA(cudaMallocAsync(&g->tslots, (size_t)(Kpad / 64 + Kpad / 32) * sizeof(int), s));
+    PL_CUDA(cudaMemsetAsync(g->tslots, 0, (size_t)(Kpad / 64 + Kpad / 32) * sizeof(int), s));
+    closure_offsets<<<(unsigned)ceil_div(Kpad, 128), 128, 0, s>>>(g->mono, Kpad, n, g->Et16, g->Et32, g->moff,
+                                                                  g->tslots, g->tslots + Kpad / 64);
     PL_TRY(launch_status("closure_offsets"));
   }
   double* C;
@@ -1002,6 +1026,7 @@ polylab_status eval_gemm(const polylab_plan* plan, const double* X, int64_t P, i
   a.err = err;
   a.tma = tma ? 1 : 0;
   a.moff = (prec == POLYLAB_BF16 ? g->off16 : g->off32) ? g->moff : nullptr;
+  a.tslots = g->tslots ? (prec == POLYLAB_BF16 ? g->tslots : g->tslots + g->Kpad / 64) : nullptr;
   const unsigned gx = (unsigned)ceil_div(P, 128);
   if (prec == POLYLAB_BF16) {
     a.Et = table_depth<0>(n, plan->max_exp);
