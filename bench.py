@@ -175,9 +175,9 @@ def source_hash(read) -> str:
 
 
 def profiled_traffic(kernel: str, units: int, form: str):
-    """DRAM bytes (read + write) per launch of `kernel` in `form` from the
-    committed ncu counters in profiles/traffic.json (records {kernel, form,
-    bytes, units, source, capture}), scaled from the captured units to
+    """DRAM bytes (read + write) of `kernel`'s launches in one step of `form`
+    from the committed ncu counters in profiles/traffic.json (records {kernel,
+    form, bytes, units, source, capture}), scaled from the captured units to
     `units`; None unless the exact-path sources' code text still hashes to
     `source` (the counters describe this code)."""
     def read(f):
@@ -593,8 +593,9 @@ def main():
     roof["kernel"] = f"{kernels[dom]} (the longest of the three stages of a step)"
     tr = profiled_traffic(kernels[dom], npts, chosen)
     roof["traffic"] = tr["bytes"] if tr else None
-    roof["traffic_note"] = (f"dram read+write per launch from {tr['captured']} ({tr['captured_units']} points), "
-                            f"scaled to {npts} points" if tr else "no ncu counters for this kernel at this source")
+    roof["traffic_note"] = (f"dram read+write of the stage's launches in one step (launches_per_step), from "
+                            f"{tr['captured']} ({tr['captured_units']} points), scaled to {npts} points"
+                            if tr else "no ncu counters for this kernel at this source")
     launches = stage_launches(tuned[chosen], polys, Xs)
     roof["launches_per_step"] = launches[dom]
     roof["note"] = ("achieved = the stage's algorithmic flops / the stage's event-timed duration (all of its "
