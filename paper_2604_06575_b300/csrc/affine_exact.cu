@@ -1087,9 +1087,17 @@ __global__ void __launch_bounds__(NT) exact_frame_kernel(StageArgs<R> a) {
 }
 
 // ------------------------------------------------------------------ stage 3
-template <typename R, int NT>
-__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 1024 / NT : std::is_same<R, dfloat>::value ? 640 / NT : 1)
-    exact_third_kernel(StageArgs<R> a) {
+// Resident CTAs a launch of the third stage is compiled for: the double-word
+// contraction of support sizes up to 4 needs fewer registers than that of 5..8.
+template <typename R, int NT, int KHI>
+constexpr int third_min_blocks() {
+  return sizeof(R) == 4 ? 1024 / NT : std::is_same<R, dfloat>::value ? (KHI <= 4 ? 768 : 640) / NT : 1;
+}
+// KLO..KHI: the support sizes compiled into this instantiation (a launch also
+// takes its range at run time, a.kmin..a.kmax, within them): a launch over one
+// range carries only that range's code.
+template <typename R, int NT, int KLO = 1, int KHI = kMaxSupport>
+__global__ void __launch_bounds__(NT, third_min_blocks<R, NT, KHI>()) exact_third_kernel(StageArgs<R> a) {
   using Acc = AccOf<R>;
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ int64_t s_item;
@@ -1165,6 +1173,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 1024 / NT : std::is_same<
       // its first term of degree >= 3
       for_support<kMaxSupport>([&](auto kc) {
         constexpr int K = decltype(kc)::value;
+        if constexpr (K < KLO || K > KHI) return;  // not compiled into this instantiation
         if (K < a.kmin || K > a.kmax) return;  // (uniform: another launch of the step takes this size)
         if constexpr (K >= 1) {
           if (gather) {
@@ -1354,8 +1363,23 @@ static polylab_status launch_stage_t(ExactBatch* b, int stage, cudaStream_t s) {
   for (int g = 0; g < split; ++g) {
     a.kmin = kRanges[split - 1][g][0];
     a.kmax = kRanges[split - 1][g][1];
+    // the double-word form has instantiations for the two-launch ranges
+    void (*kt)(StageArgs<R>) = k;
+    if constexpr (std::is_same<R, dfloat>::value) {
+      if (a.kmin == 1 && a.kmax == 4) kt = exact_third_kernel<R, NT, 1, 4>;
+      else if (a.kmin == 5 && a.kmax == kMaxSupport) kt = exact_third_kernel<R, NT, 5, kMaxSupport>;
+    }
+    int64_t gk = grid;
+    if (kt != k) {
+      PL_CUDA(cudaFuncSetAttribute(kt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      int psm = 0;
+      PL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&psm, kt, NT, smem));
+      psm = std::max(1, psm);
+      if (cap > 0) psm = std::min(psm, cap);
+      gk = std::max<int64_t>(1, std::min<int64_t>(i1 - i0, (int64_t)num_sms() * psm));
+    }
     PL_CUDA(cudaMemsetAsync(a.counter, 0, sizeof(int), s));
-    k<<<(unsigned)grid, NT, smem, s>>>(a);
+    kt<<<(unsigned)gk, NT, smem, s>>>(a);
     PL_TRY(launch_status("exact_third_kernel"));
   }
   return POLYLAB_OK;
