@@ -515,6 +515,11 @@ def main():
                 worst = max(worst, float(e.max()))
         return worst, flags_equal
 
+    def flagged(form):
+        """Points the form flagged (zero gradient or projected Hessian not
+        positive definite): their directions are NaN."""
+        return int(sum(int((~torch.isfinite(d).all(dim=1)).sum()) for d in batches[form].D))
+
     BOUND = dict(f32x2=1e-9, fp32=1e-3)  # stated bounds: relative error of nu; angle in radians
     errs = {f: vs_fp64(f) for f in forms if f != "fp64"} if "fp64" in forms else {}
     ok = {f: errs[f][0] <= BOUND[f] and errs[f][1] for f in errs}
@@ -599,7 +604,7 @@ def main():
     launches = stage_launches(tuned[chosen], polys, Xs)
     roof["launches_per_step"] = launches[dom]
     roof["note"] = ("achieved = the stage's algorithmic flops / the stage's event-timed duration (all of its "
-                    "launches in a step: the frame stage runs one launch per class of n)")
+                    "launches in a step: the sweeps and the frame stage run one launch per class of n)")
     roof["stages"] = stages
     roof["path"] = alu_roofline(flops, statistics.median(res[chosen]["step_ms"]) * 1e-3, chosen, p32, p64)
 
@@ -615,6 +620,7 @@ def main():
                 forms={**{f: dict(dirs_per_s=round(rate(f), 1),
                                   ms_per_step=round(res[f]["total_ms"] / args.steps, 3),
                                   stage_ms={k: round(v, 3) for k, v in res[f]["stage_ms"].items()},
+                                  flagged_points=flagged(f),
                                   speedup_vs_fp64=round(rate(f) / rate("fp64"), 3) if "fp64" in res else None,
                                   **({} if f not in errs else dict(
                                       max_err_vs_fp64=errs[f][0], err_kind=("relative |nu|" if f == "f32x2"
@@ -666,16 +672,15 @@ def main():
 
 
 def stage_launches(cfg: dict, polys, Xs) -> dict:
-    """Kernel launches of one run per stage: one launch of the gradient/Hessian
-    sweep, one third-stage launch per range of support sizes (third_split)
-    and, with frame_split, one frame launch per non-empty class of n
-    (n > 40, 24 < n <= 40, n <= 24)."""
+    """Kernel launches of one run per stage: the gradient/Hessian sweep as one
+    gather launch per non-empty class of n (n > 40, 24 < n <= 40, n <= 24) plus
+    one term-by-term launch, one third-stage launch per range of support sizes
+    (third_split) and, with frame_split, one frame launch per non-empty
+    class."""
     ns = [p.n for p, X in zip(polys, Xs) if X.shape[0] > 0]
-    if cfg.get("frame_split", 0):
-        frame = sum(1 for lo, hi in ((40, 1 << 30), (24, 40), (0, 24)) if any(lo < n <= hi for n in ns))
-    else:
-        frame = 1
-    return dict(terms=1, frame=frame, third=int(cfg.get("third_split", 1)))
+    classes = sum(1 for lo, hi in ((40, 1 << 30), (24, 40), (0, 24)) if any(lo < n <= hi for n in ns))
+    frame = classes if cfg.get("frame_split", 0) else 1
+    return dict(terms=classes + 1, frame=frame, third=int(cfg.get("third_split", 1)))
 
 
 def measure_rows(pl, workloads, torch, dev, p32, p64, only=None):

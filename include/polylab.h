@@ -412,7 +412,10 @@ polylab_status polylab_batch_run_stage(polylab_batch* batch, int32_t stage, poly
  * bounded wait (a bulk copy into shared memory that did not complete within
  * two seconds) since the last check: POLYLAB_ERR_TIMEOUT then (the stage is
  * named in polylab_last_error(); the record is cleared, so the batch may run
- * again), POLYLAB_OK otherwise. */
+ * again), POLYLAB_OK otherwise.  The same record carries an internal
+ * consistency failure of the term sweep (its list of passes left to the
+ * term-by-term kernel overflowed: not reachable with the list's sizing), then
+ * reported as POLYLAB_ERR_UNSUPPORTED. */
 polylab_status polylab_batch_check(polylab_batch* batch, polylab_stream stream);
 polylab_status polylab_batch_get_config(const polylab_batch* batch, polylab_batch_config* cfg);
 polylab_status polylab_batch_set_config(polylab_batch* batch, const polylab_batch_config* cfg,

@@ -193,8 +193,12 @@ __device__ __forceinline__ void power_table(const double* __restrict__ X, int n,
 // Column k+1 is updated and pivoted by warp 0 while the other warps apply
 // column k to columns k+2.. (a_ij -= l_ik a_jk, with the unscaled a_jk kept
 // in uc), so a step needs no second barrier.  A pivot that is not positive
-// and finite sets *flag (the block is not positive definite); the caller
-// reads it after the final barrier.
+// and finite sets its flag (the block is not positive definite): pivot c
+// writes flag[c & 1] and every thread reads flag[k & 1] after the barrier
+// that ends the step which made pivot k, so a flag is never written in the
+// step that reads it (warp 0 makes pivot k+1 while a slower warp may still be
+// reading pivot k's flag) and every warp leaves at the same step.  The caller
+// reads flag[0] | flag[1] after the final barrier.
 template <int NT, typename Col>
 __device__ __forceinline__ void ldlt_block(int m, Col col, double* __restrict__ uc, double* __restrict__ dv,
                                            double* __restrict__ di, int* flag) {
@@ -208,7 +212,7 @@ __device__ __forceinline__ void ldlt_block(int m, Col col, double* __restrict__ 
     // exponent below all-ones) on the integer pipe
     const long long bits = __double_as_longlong(d);
     if (!(bits > 0 && bits < 0x7FF0000000000000ll)) {
-      if (lane == 0) *flag = 1;
+      if (lane == 0) flag[c & 1] = 1;
       return;
     }
     const double inv = __drcp_rn(d);
@@ -226,7 +230,7 @@ __device__ __forceinline__ void ldlt_block(int m, Col col, double* __restrict__ 
   if (wid == 0) pivot(0);
   __syncthreads();
   for (int k = 0; k + 1 < m; ++k) {
-    if (*flag) return;
+    if (flag[k & 1]) return;
     const double* ck = col(k);
     const double* uk = uc + (k & 1) * m;
     if (wid == 0) {
@@ -267,6 +271,8 @@ __device__ __forceinline__ void ldlt_block(int m, Col col, double* __restrict__ 
 // factors them.  Each trailing element is read and written once per two
 // columns.  uc holds four unscaled pivot columns.  (In shared memory the
 // one-column form is faster: warp 0's pivot chain per barrier doubles here.)
+// The flags alternate by panel: pivots c of panel c >> 1 write
+// flag[(c >> 1) & 1], read after the barrier that ends their step.
 template <int NT, typename Col>
 __device__ __forceinline__ void ldlt_block_pairs(int m, Col col, double* __restrict__ uc, double* __restrict__ dv,
                                                  double* __restrict__ di, int* flag) {
@@ -279,7 +285,7 @@ __device__ __forceinline__ void ldlt_block_pairs(int m, Col col, double* __restr
     const double d = cc[c];
     const long long bits = __double_as_longlong(d);
     if (!(bits > 0 && bits < 0x7FF0000000000000ll)) {
-      if (lane == 0) *flag = 1;
+      if (lane == 0) flag[(c >> 1) & 1] = 1;
       return false;
     }
     const double inv = __drcp_rn(d);
@@ -307,7 +313,7 @@ __device__ __forceinline__ void ldlt_block_pairs(int m, Col col, double* __restr
   if (wid == 0 && pivot(0) && m > 1) update_and_pivot(0, 1);
   __syncthreads();
   for (int k = 0; k + 2 < m; k += 2) {
-    if (*flag) return;
+    if (flag[(k >> 1) & 1]) return;
     const double* l0 = col(k);
     const double* l1 = col(k + 1);
     const double* u0 = ubuf(k);
@@ -493,6 +499,9 @@ struct StageArgs {
   size_t gws_stride;
   int* err;  // set when a bounded wait expires
   int kmin, kmax;  // third stage: the support sizes this launch contracts (all launches of a step cover 1..8)
+  int64_t* fb;     // term sweep: passes left to the term-by-term launch (first point, points), their count
+  int* fb_count;   // and the list's capacity
+  int fb_cap;
 };
 
 __device__ __forceinline__ void write_failed(const ExactDesc& pd, int64_t p, int n, double gn, int flag) {
@@ -523,8 +532,19 @@ __device__ __forceinline__ void write_failed(const ExactDesc& pd, int64_t p, int
 // terms and records serves the two points (each record is decoded once and
 // applied to both points' monomial values).  Otherwise the points are swept
 // one after another (a pair that straddles two polynomials in two passes).
-template <typename R, int NT>
-__global__ void __launch_bounds__(NT) exact_terms_kernel(StageArgs<R> a) {
+// The sweep is two kernels.  GATHER: the gather passes of an item range; a
+// pass the gather form cannot take (a coordinate outside its range, or a plan
+// without records) is appended to the list a.fb and left to the second
+// kernel, which takes the listed passes term by term.  Split this way the
+// gather kernel carries none of the term-by-term code and keeps a much smaller
+// register allocation (64 against 134 in double words), so twice as many CTAs
+// stay resident.
+template <typename R>
+constexpr int terms_min_blocks(bool gather, int nt) {
+  return !gather ? 1 : (sizeof(R) == 8 && !std::is_same<R, dfloat>::value ? 768 : 1024) / nt;
+}
+template <typename R, int NT, bool GATHER>
+__global__ void __launch_bounds__(NT, terms_min_blocks<R>(GATHER, NT)) exact_terms_kernel(StageArgs<R> a) {
   using Acc = AccOf<R>;
   using Abs = AbsOf<R>;
   extern __shared__ __align__(16) unsigned char sm[];
@@ -532,9 +552,17 @@ __global__ void __launch_bounds__(NT) exact_terms_kernel(StageArgs<R> a) {
   constexpr int NW = NT / 32;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   while (true) {
-    const int64_t pair = a.item_begin + (int64_t)kTermPoints * next_item(a.counter, &s_item);
-    if (pair >= a.item_end) break;
-    const int64_t pair_end = min(pair + kTermPoints, a.item_end);
+    int64_t pair, pair_end;
+    if constexpr (!GATHER) {
+      const int64_t idx = next_item(a.counter, &s_item);
+      if (idx >= (int64_t)min(*a.fb_count, a.fb_cap)) break;  // (written by the gather launches before this one)
+      pair = a.fb[2 * idx];
+      pair_end = pair + a.fb[2 * idx + 1];
+    } else {
+      pair = a.item_begin + (int64_t)kTermPoints * next_item(a.counter, &s_item);
+      if (pair >= a.item_end) break;
+      pair_end = min(pair + kTermPoints, a.item_end);
+    }
     int np = 0;
     for (int64_t item = pair; item < pair_end; item += np) {
       const int lo = find_poly(a.prefix, a.n_desc, item);
@@ -543,7 +571,7 @@ __global__ void __launch_bounds__(NT) exact_terms_kernel(StageArgs<R> a) {
       // the points of this pass: the rest of the pair within this polynomial
       np = (int)min(pair_end - item, pd.P - p0);
       const int n = pd.n, nn = n * n, E1 = pd.E + 1;
-      const Lay1 L = lay_terms<R, NW>(n, E1, pd.h_in_smem, pd.gather != nullptr);
+      const Lay1 L = lay_terms<R, NW>(n, E1, pd.h_in_smem, GATHER);
       auto pw_of = [&](int q) { return (R*)(sm + L.pw + q * L.pw_step); };
       auto ix_of = [&](int q) { return (R*)(sm + L.ix + q * L.ix_step); };
       auto gs_of = [&](int q) { return (Acc*)(sm + L.gs + q * L.gs_step); };
@@ -559,7 +587,21 @@ __global__ void __launch_bounds__(NT) exact_terms_kernel(StageArgs<R> a) {
         const double ax = fabs(pd.X[p0 * n + i]);
         in_range &= ax >= pd.x_lo && ax <= pd.x_hi;
       }
-      const bool gather = __syncthreads_and(in_range && pd.gather != nullptr) != 0;
+      const bool gather = GATHER && __syncthreads_and(in_range && pd.gather != nullptr) != 0;
+      if constexpr (GATHER) {
+        if (!gather) {  // (uniform) the term-by-term launch takes this pass
+          if (tid == 0) {
+            const int idx = atomicAdd(a.fb_count, 1);
+            if (idx < a.fb_cap) {
+              a.fb[2 * idx] = item;
+              a.fb[2 * idx + 1] = np;
+            } else {
+              atomicExch(a.err, 4);  // (the list holds one pass per pair plus one per polynomial)
+            }
+          }
+          continue;
+        }
+      }
       for (int q = 0; q < np; ++q) {
         const double* X = pd.X + (p0 + q) * n;
         if (gather) {
@@ -661,7 +703,7 @@ __global__ void __launch_bounds__(NT) exact_terms_kernel(StageArgs<R> a) {
             gabs[q] += ga_of(q)[i] * Abs(fabs(ix[i]));
           }
         }
-      } else {
+      } else if constexpr (!GATHER) {
         for (int q = 0; q < np; ++q) {
           for (int i = tid; i < NW * n; i += NT) g[i] = Acc(0);
           __syncthreads();
@@ -730,7 +772,7 @@ __global__ void __launch_bounds__(NT) exact_terms_kernel(StageArgs<R> a) {
 // wait expired (the kernel stops).
 template <typename R, int NT, bool SMEM>
 __device__ __forceinline__ bool frame_item(const StageArgs<R>& a, const ExactDesc& pd, int64_t p, unsigned char* sm,
-                                           int& s_flag, double* s_sc, uint64_t& s_bar, uint32_t& phase) {
+                                           int* s_flag, double* s_sc, uint64_t& s_bar, uint32_t& phase) {
   // kF64: the factor is formed in place in the 8-byte matrix (FP64 and
   // double-word forms); kDW: double-word form, whose H and frame update are
   // FP64 (H arrives as FP64 sums) and whose inverse and W are double words
@@ -813,7 +855,7 @@ __device__ __forceinline__ bool frame_item(const StageArgs<R>& a, const ExactDes
       s_sc[1] = zero ? 1.0 : 0.0;
       s_sc[2] = beta;
       s_sc[3] = sgn;
-      s_flag = 0;
+      s_flag[0] = s_flag[1] = 0;
     }
   }
   if (SMEM) {
@@ -871,10 +913,10 @@ __device__ __forceinline__ bool frame_item(const StageArgs<R>& a, const ExactDes
     for (int i = tid; i < m; i += NT) col(i)[i] += a.r;
   }
   __syncthreads();
-  if constexpr (SMEM) ldlt_block<NT>(m, col, uc, dv, di, &s_flag);
-  else ldlt_block_pairs<NT>(m, col, uc, dv, di, &s_flag);
+  if constexpr (SMEM) ldlt_block<NT>(m, col, uc, dv, di, s_flag);
+  else ldlt_block_pairs<NT>(m, col, uc, dv, di, s_flag);
   __syncthreads();
-  if (s_flag) {
+  if (s_flag[0] | s_flag[1]) {
     write_failed(pd, p, n, gn, POLYLAB_FLAG_NOT_PD);
     if (tid == 0) {
       rec[4 * n + 1] = gn;
@@ -1064,7 +1106,7 @@ template <typename R, int NT>
 __global__ void __launch_bounds__(NT) exact_frame_kernel(StageArgs<R> a) {
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ int64_t s_item;
-  __shared__ int s_flag;
+  __shared__ int s_flag[2];  // the factorisation's failure flags (two slots, alternating by step)
   __shared__ double s_sc[4];
   __shared__ __align__(8) uint64_t s_bar;
   const int tid = threadIdx.x;
@@ -1286,6 +1328,8 @@ static polylab_status prepare_exact(ExactBatch* b) {
   size_t smem[3] = {0, 0, 0}, gstride = 0;
   int64_t mat = 0, vec = 0;
   b->frame_need.assign(b->host_descs.size(), 0);
+  b->terms_need.assign(b->host_descs.size(), 0);
+  b->terms_fb_smem = 0;
   for (size_t di = 0; di < b->host_descs.size(); ++di) {
     ExactDesc& d = b->host_descs[di];
     const int E1 = d.E + 1;
@@ -1302,6 +1346,9 @@ static polylab_status prepare_exact(ExactBatch* b) {
       smem[st] = std::max(smem[st], need[st]);
     }
     b->frame_need[di] = need[1];
+    // class-wise sweep: the gather launch (descriptors with records) and the term-by-term launch
+    b->terms_need[di] = gat ? need[0] : 0;
+    b->terms_fb_smem = std::max(b->terms_fb_smem, stage_bytes<R>(0, tt, d.n, E1, d.h_in_smem, false));
     if (!d.mats_in_smem) gstride = std::max(gstride, frame_gmem<R>(d.n));
     d.mat_off = mat;
     d.vec_off = vec;
@@ -1317,9 +1364,7 @@ static polylab_status prepare_exact(ExactBatch* b) {
 
 template <typename R, int NT>
 static polylab_status launch_stage_t(ExactBatch* b, int stage, cudaStream_t s) {
-  void (*k)(StageArgs<R>) = stage == 0   ? exact_terms_kernel<R, NT>
-                            : stage == 1 ? exact_frame_kernel<R, NT>
-                                         : exact_third_kernel<R, NT>;
+  void (*k)(StageArgs<R>) = stage == 1 ? exact_frame_kernel<R, NT> : exact_third_kernel<R, NT>;
   const int64_t i0 = 0, i1 = b->total;
   if (i1 <= i0) return POLYLAB_OK;
   const size_t smem = b->smem[stage];
@@ -1327,7 +1372,7 @@ static polylab_status launch_stage_t(ExactBatch* b, int stage, cudaStream_t s) {
   int per_sm = 0;
   PL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NT, smem));
   per_sm = std::max(1, per_sm);
-  const int cap = stage == 0 ? b->cfg.terms_ctas : stage == 1 ? b->cfg.ctas_per_sm : b->cfg.third_ctas;
+  const int cap = stage == 1 ? b->cfg.ctas_per_sm : b->cfg.third_ctas;
   if (cap > 0) per_sm = std::min(per_sm, cap);
   const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(i1 - i0, (int64_t)num_sms() * per_sm));
   if (stage == 1 && b->gws_stride > 0 && (size_t)grid * b->gws_stride > b->gws_bytes) return POLYLAB_ERR_UNSUPPORTED;
@@ -1349,10 +1394,10 @@ static polylab_status launch_stage_t(ExactBatch* b, int stage, cudaStream_t s) {
   a.err = b->err;
   a.kmin = 1;
   a.kmax = kMaxSupport;
-  if (stage != 2) {
+  if (stage == 1) {
     PL_CUDA(cudaMemsetAsync(a.counter, 0, sizeof(int), s));
     k<<<(unsigned)grid, NT, smem, s>>>(a);
-    return launch_status(stage == 0 ? "exact_terms_kernel" : "exact_frame_kernel");
+    return launch_status("exact_frame_kernel");
   }
   // the third stage as one launch per range of support sizes, in order
   static const int kRanges[4][4][2] = {{{1, kMaxSupport}},
@@ -1383,6 +1428,56 @@ static polylab_status launch_stage_t(ExactBatch* b, int stage, cudaStream_t s) {
     PL_TRY(launch_status("exact_third_kernel"));
   }
   return POLYLAB_OK;
+}
+
+// The gradient/Hessian sweep over the frame stage's classes of n (frame
+// order): one gather launch per class, each with the shared memory of its own
+// largest n, then one term-by-term launch over the passes they left.  (The
+// list and the launch counters are reset on the stream first.)
+template <typename R, int NT>
+static polylab_status launch_terms_classes(ExactBatch* b, cudaStream_t s) {
+  StageArgs<R> a{};
+  a.descs = b->descs;
+  a.n_desc = b->n_desc;
+  a.prefix = b->fprefix;
+  a.order = b->forder;
+  a.mats_h = (AccOf<R>*)b->ws_h;
+  a.mats_w = (R*)b->ws_w;
+  a.vecs = (double*)b->ws_v;
+  a.r = b->opts.regularization;
+  a.assume_nonzero_x = b->opts.assume_nonzero_x;
+  a.gws = b->gws;
+  a.gws_stride = b->gws_stride;
+  a.err = b->err;
+  a.kmin = 1;
+  a.kmax = kMaxSupport;
+  a.fb = b->tfb;
+  a.fb_count = b->tfb_ctl;
+  a.fb_cap = (int)b->tfb_cap;
+  PL_CUDA(cudaMemsetAsync(b->tfb_ctl, 0, (2 + kFrameClasses) * sizeof(int), s));
+  auto launch = [&](void (*k)(StageArgs<R>), size_t smem, int64_t items, int* counter) -> polylab_status {
+    smem = std::max<size_t>(smem, 16);
+    PL_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    PL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NT, smem));
+    per_sm = std::max(1, per_sm);
+    if (b->cfg.terms_ctas > 0) per_sm = std::min(per_sm, b->cfg.terms_ctas);
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)num_sms() * per_sm));
+    a.counter = counter;
+    k<<<(unsigned)grid, NT, smem, s>>>(a);
+    return launch_status("exact_terms_kernel");
+  };
+  for (int c = 0; c < kFrameClasses; ++c) {
+    const FrameClass& fc = b->fclass[c];
+    if (fc.end <= fc.begin) continue;
+    a.item_begin = fc.begin;
+    a.item_end = fc.end;
+    PL_TRY(launch(exact_terms_kernel<R, NT, true>, fc.tsmem, (fc.end - fc.begin + 1) / 2, b->tfb_ctl + 1 + c));
+  }
+  a.item_begin = 0;
+  a.item_end = b->total;
+  return launch(exact_terms_kernel<R, NT, false>, b->terms_fb_smem, (b->total + 1) / 2,
+                b->tfb_ctl + 1 + kFrameClasses);
 }
 
 // One class of the split frame stage: the class's item
@@ -1436,6 +1531,12 @@ static polylab_status launch_frame_classes(ExactBatch* b, cudaStream_t s) {
 template <typename R>
 static polylab_status launch_stage(ExactBatch* b, int stage, cudaStream_t s) {
   if (stage == 1 && b->cfg.frame_split) return launch_frame_classes<R>(b, s);
+  if (stage == 0) {
+    const int nt = b->cfg.term_threads;
+    if (nt == 64) return launch_terms_classes<R, 64>(b, s);
+    if (nt == 128) return launch_terms_classes<R, 128>(b, s);
+    return launch_terms_classes<R, 256>(b, s);
+  }
   const int nt = stage == 0 ? b->cfg.term_threads : stage == 1 ? b->cfg.threads : b->cfg.third_threads;
   if (nt == 64) return launch_stage_t<R, 64>(b, stage, s);
   if (nt == 128) return launch_stage_t<R, 128>(b, stage, s);

@@ -56,10 +56,12 @@ void exact_frame_classes(ExactBatch* b) {
     fc.n_lo = bounds[c + 1];
     fc.threads = c == 0 ? b->cfg.threads : 64;
     fc.smem = 0;
+    fc.tsmem = 0;
     fc.begin = b->host_fprefix.empty() ? 0 : b->host_fprefix[i];
     while (i < n && b->host_descs[b->host_forder[i]].n > fc.n_lo) {
-      const size_t need = (size_t)b->host_forder[i] < b->frame_need.size() ? b->frame_need[b->host_forder[i]] : 0;
-      fc.smem = std::max(fc.smem, need);
+      const size_t d = (size_t)b->host_forder[i];
+      fc.smem = std::max(fc.smem, d < b->frame_need.size() ? b->frame_need[d] : 0);
+      fc.tsmem = std::max(fc.tsmem, d < b->terms_need.size() ? b->terms_need[d] : 0);
       ++i;
     }
     fc.end = b->host_fprefix.empty() ? 0 : b->host_fprefix[i];
@@ -120,6 +122,16 @@ polylab_status exact_batch_init(ExactBatch* b, int n, const polylab_plan* const*
   PL_CUDA(cudaMallocAsync(&b->fprefix, (n + 1) * sizeof(int64_t), s));
   PL_CUDA(cudaMallocAsync(&b->fcounter, kFrameClasses * sizeof(int), s));
   PL_CUDA(cudaMallocAsync(&b->err, sizeof(int), s));
+  {  // passes of the term sweep left to its term-by-term launch: at most one per pair of points plus one
+     // per polynomial (a pass never spans two)
+    int64_t points = 0;
+    for (int i = 0; i < n; ++i) points += P[i];
+    const int64_t cap = points / 2 + n + 2 + kFrameClasses;
+    if (cap > INT32_MAX) return POLYLAB_ERR_UNSUPPORTED;
+    b->tfb_cap = cap;
+    PL_CUDA(cudaMallocAsync(&b->tfb, (size_t)cap * 2 * sizeof(int64_t), s));
+    PL_CUDA(cudaMallocAsync(&b->tfb_ctl, (2 + kFrameClasses) * sizeof(int), s));
+  }
   PL_CUDA(cudaMemsetAsync(b->err, 0, sizeof(int), s));
   PL_CUDA(cudaMallocAsync(&b->ws_h, std::max<size_t>(b->ws_mat_bytes, 16), s));
   PL_CUDA(cudaMallocAsync(&b->ws_w, std::max<size_t>(b->ws_mat_bytes, 16), s));
@@ -164,6 +176,10 @@ void exact_batch_release(ExactBatch* b, cudaStream_t s) {
   b->fcounter = nullptr;
   if (b->gws) cudaFreeAsync(b->gws, s);
   if (b->err) cudaFreeAsync(b->err, s);
+  if (b->tfb) cudaFreeAsync(b->tfb, s);
+  if (b->tfb_ctl) cudaFreeAsync(b->tfb_ctl, s);
+  b->tfb = nullptr;
+  b->tfb_ctl = nullptr;
   b->err = nullptr;
   if (b->ws_h) cudaFreeAsync(b->ws_h, s);
   if (b->ws_w) cudaFreeAsync(b->ws_w, s);
@@ -239,11 +255,15 @@ polylab_status polylab_batch_check(polylab_batch* b, polylab_stream stream) {
   PL_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
   if (!flag) return POLYLAB_OK;
   char msg[96];
-  snprintf(msg, sizeof(msg), "a bounded wait of the %s stage expired",
-           flag == 2 ? "frame" : flag == 3 ? "third-derivative" : "batch");
+  if (flag == 4)
+    snprintf(msg, sizeof(msg), "the term sweep's list of term-by-term passes overflowed");
+  else
+    snprintf(msg, sizeof(msg), "a bounded wait of the %s stage expired",
+             flag == 2 ? "frame" : flag == 3 ? "third-derivative" : "batch");
   set_last_message(msg);
   PL_CUDA(cudaMemsetAsync(b->b.err, 0, sizeof(int), (cudaStream_t)stream));  // the batch may run again
   PL_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  if (flag == 4) return POLYLAB_ERR_UNSUPPORTED;
   return POLYLAB_ERR_TIMEOUT;
 }
 

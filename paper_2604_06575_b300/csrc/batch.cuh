@@ -51,6 +51,7 @@ struct FrameClass {
   int n_lo, n_hi, threads;
   int64_t begin = 0, end = 0;
   size_t smem = 0;
+  size_t tsmem = 0;  // the gradient/Hessian sweep's gather launch over the same class
 };
 
 struct ExactBatch {
@@ -76,6 +77,14 @@ struct ExactBatch {
   int64_t* fprefix = nullptr;
   int* fcounter = nullptr;
   FrameClass fclass[kFrameClasses];
+  // the gradient/Hessian sweep by class of n: per-descriptor
+  // shared memory of its gather launch, that of the term-by-term launch, the
+  // list of passes left to it and [count, one work counter per launch]
+  std::vector<size_t> terms_need;
+  size_t terms_fb_smem = 0;
+  int64_t* tfb = nullptr;
+  int64_t tfb_cap = 0;
+  int* tfb_ctl = nullptr;
   // workspaces: H and W (one n x n slot per point each), small vectors
   void* ws_h = nullptr;
   void* ws_w = nullptr;
