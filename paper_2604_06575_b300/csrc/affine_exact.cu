@@ -499,9 +499,16 @@ struct StageArgs {
   size_t gws_stride;
   int* err;  // set when a bounded wait expires
   int kmin, kmax;  // third stage: the support sizes this launch contracts (all launches of a step cover 1..8)
-  int64_t* fb;     // term sweep: passes left to the term-by-term launch (first point, points), their count
-  int* fb_count;   // and the list's capacity
-  int fb_cap;
+};
+
+// The gradient/Hessian sweep's list of passes left to its term-by-term
+// kernel: (first item, points) pairs, their count and the list's capacity.
+// (A parameter of its own: the stage arguments of the frame and third
+// kernels keep their size, and with it those kernels' register allocation.)
+struct PassList {
+  int64_t* pass;
+  int* count;
+  int cap;
 };
 
 __device__ __forceinline__ void write_failed(const ExactDesc& pd, int64_t p, int n, double gn, int flag) {
@@ -534,7 +541,7 @@ __device__ __forceinline__ void write_failed(const ExactDesc& pd, int64_t p, int
 // one after another (a pair that straddles two polynomials in two passes).
 // The sweep is two kernels.  GATHER: the gather passes of an item range; a
 // pass the gather form cannot take (a coordinate outside its range, or a plan
-// without records) is appended to the list a.fb and left to the second
+// without records) is appended to the list fl and left to the second
 // kernel, which takes the listed passes term by term.  Split this way the
 // gather kernel carries none of the term-by-term code and keeps a much smaller
 // register allocation (64 against 134 in double words), so twice as many CTAs
@@ -544,7 +551,7 @@ constexpr int terms_min_blocks(bool gather, int nt) {
   return !gather ? 1 : (sizeof(R) == 8 && !std::is_same<R, dfloat>::value ? 768 : 1024) / nt;
 }
 template <typename R, int NT, bool GATHER>
-__global__ void __launch_bounds__(NT, terms_min_blocks<R>(GATHER, NT)) exact_terms_kernel(StageArgs<R> a) {
+__global__ void __launch_bounds__(NT, terms_min_blocks<R>(GATHER, NT)) exact_terms_kernel(StageArgs<R> a, PassList fl) {
   using Acc = AccOf<R>;
   using Abs = AbsOf<R>;
   extern __shared__ __align__(16) unsigned char sm[];
@@ -555,9 +562,9 @@ __global__ void __launch_bounds__(NT, terms_min_blocks<R>(GATHER, NT)) exact_ter
     int64_t pair, pair_end;
     if constexpr (!GATHER) {
       const int64_t idx = next_item(a.counter, &s_item);
-      if (idx >= (int64_t)min(*a.fb_count, a.fb_cap)) break;  // (written by the gather launches before this one)
-      pair = a.fb[2 * idx];
-      pair_end = pair + a.fb[2 * idx + 1];
+      if (idx >= (int64_t)min(*fl.count, fl.cap)) break;  // (written by the gather launches before this one)
+      pair = fl.pass[2 * idx];
+      pair_end = pair + fl.pass[2 * idx + 1];
     } else {
       pair = a.item_begin + (int64_t)kTermPoints * next_item(a.counter, &s_item);
       if (pair >= a.item_end) break;
@@ -591,10 +598,10 @@ __global__ void __launch_bounds__(NT, terms_min_blocks<R>(GATHER, NT)) exact_ter
       if constexpr (GATHER) {
         if (!gather) {  // (uniform) the term-by-term launch takes this pass
           if (tid == 0) {
-            const int idx = atomicAdd(a.fb_count, 1);
-            if (idx < a.fb_cap) {
-              a.fb[2 * idx] = item;
-              a.fb[2 * idx + 1] = np;
+            const int idx = atomicAdd(fl.count, 1);
+            if (idx < fl.cap) {
+              fl.pass[2 * idx] = item;
+              fl.pass[2 * idx + 1] = np;
             } else {
               atomicExch(a.err, 4);  // (the list holds one pass per pair plus one per polynomial)
             }
@@ -1451,11 +1458,9 @@ static polylab_status launch_terms_classes(ExactBatch* b, cudaStream_t s) {
   a.err = b->err;
   a.kmin = 1;
   a.kmax = kMaxSupport;
-  a.fb = b->tfb;
-  a.fb_count = b->tfb_ctl;
-  a.fb_cap = (int)b->tfb_cap;
+  const PassList fl{b->tfb, b->tfb_ctl, (int)b->tfb_cap};
   PL_CUDA(cudaMemsetAsync(b->tfb_ctl, 0, (2 + kFrameClasses) * sizeof(int), s));
-  auto launch = [&](void (*k)(StageArgs<R>), size_t smem, int64_t items, int* counter) -> polylab_status {
+  auto launch = [&](void (*k)(StageArgs<R>, PassList), size_t smem, int64_t items, int* counter) -> polylab_status {
     smem = std::max<size_t>(smem, 16);
     PL_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
@@ -1464,7 +1469,7 @@ static polylab_status launch_terms_classes(ExactBatch* b, cudaStream_t s) {
     if (b->cfg.terms_ctas > 0) per_sm = std::min(per_sm, b->cfg.terms_ctas);
     const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)num_sms() * per_sm));
     a.counter = counter;
-    k<<<(unsigned)grid, NT, smem, s>>>(a);
+    k<<<(unsigned)grid, NT, smem, s>>>(a, fl);
     return launch_status("exact_terms_kernel");
   };
   for (int c = 0; c < kFrameClasses; ++c) {

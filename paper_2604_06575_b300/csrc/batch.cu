@@ -122,16 +122,6 @@ polylab_status exact_batch_init(ExactBatch* b, int n, const polylab_plan* const*
   PL_CUDA(cudaMallocAsync(&b->fprefix, (n + 1) * sizeof(int64_t), s));
   PL_CUDA(cudaMallocAsync(&b->fcounter, kFrameClasses * sizeof(int), s));
   PL_CUDA(cudaMallocAsync(&b->err, sizeof(int), s));
-  {  // passes of the term sweep left to its term-by-term launch: at most one per pair of points plus one
-     // per polynomial (a pass never spans two)
-    int64_t points = 0;
-    for (int i = 0; i < n; ++i) points += P[i];
-    const int64_t cap = points / 2 + n + 2 + kFrameClasses;
-    if (cap > INT32_MAX) return POLYLAB_ERR_UNSUPPORTED;
-    b->tfb_cap = cap;
-    PL_CUDA(cudaMallocAsync(&b->tfb, (size_t)cap * 2 * sizeof(int64_t), s));
-    PL_CUDA(cudaMallocAsync(&b->tfb_ctl, (2 + kFrameClasses) * sizeof(int), s));
-  }
   PL_CUDA(cudaMemsetAsync(b->err, 0, sizeof(int), s));
   PL_CUDA(cudaMallocAsync(&b->ws_h, std::max<size_t>(b->ws_mat_bytes, 16), s));
   PL_CUDA(cudaMallocAsync(&b->ws_w, std::max<size_t>(b->ws_mat_bytes, 16), s));
@@ -142,6 +132,16 @@ polylab_status exact_batch_init(ExactBatch* b, int n, const polylab_plan* const*
     // enough workspace for the largest grid any configuration may launch
     b->gws_bytes = (size_t)num_sms() * 32 * b->gws_stride;
     PL_CUDA(cudaMallocAsync(&b->gws, b->gws_bytes, s));
+  }
+  {  // passes of the term sweep left to its term-by-term launch: at most one per pair of points (pairs
+     // start afresh in each class of n) plus one per polynomial (a pass never spans two)
+    int64_t points = 0;
+    for (int i = 0; i < n; ++i) points += P[i];
+    const int64_t cap = points / 2 + n + 2 + kFrameClasses;
+    if (cap > INT32_MAX) return POLYLAB_ERR_UNSUPPORTED;
+    b->tfb_cap = cap;
+    PL_CUDA(cudaMallocAsync(&b->tfb, (size_t)cap * 2 * sizeof(int64_t), s));
+    PL_CUDA(cudaMallocAsync(&b->tfb_ctl, (2 + kFrameClasses) * sizeof(int), s));
   }
   return POLYLAB_OK;
 }
