@@ -548,7 +548,7 @@ __device__ __forceinline__ void write_failed(const ExactDesc& pd, int64_t p, int
 // stay resident.
 template <typename R>
 constexpr int terms_min_blocks(bool gather, int nt) {
-  return !gather ? 1 : (sizeof(R) == 8 && !std::is_same<R, dfloat>::value ? 768 : 1024) / nt;
+  return (!gather ? 512 : sizeof(R) == 8 && !std::is_same<R, dfloat>::value ? 768 : 1024) / nt;
 }
 template <typename R, int NT, bool GATHER>
 __global__ void __launch_bounds__(NT, terms_min_blocks<R>(GATHER, NT)) exact_terms_kernel(StageArgs<R> a, PassList fl) {
