@@ -1412,14 +1412,19 @@ static polylab_status launch_stage_t(ExactBatch* b, int stage, cudaStream_t s) {
                                        {{1, 3}, {4, 4}, {5, kMaxSupport}},
                                        {{1, 3}, {4, 4}, {5, 5}, {6, kMaxSupport}}};
   const int split = std::min(4, std::max(1, b->cfg.third_split));
+  int max_support = 0;
+  for (const ExactDesc& d : b->host_descs) max_support = std::max(max_support, d.max_support);
   for (int g = 0; g < split; ++g) {
     a.kmin = kRanges[split - 1][g][0];
     a.kmax = kRanges[split - 1][g][1];
-    // the double-word form has instantiations for the two-launch ranges
+    // the double-word form has instantiations for the two-launch ranges, the
+    // second without the (out-of-line) support sizes 7 and 8 when the batch
+    // has no such terms
     void (*kt)(StageArgs<R>) = k;
     if constexpr (std::is_same<R, dfloat>::value) {
       if (a.kmin == 1 && a.kmax == 4) kt = exact_third_kernel<R, NT, 1, 4>;
-      else if (a.kmin == 5 && a.kmax == kMaxSupport) kt = exact_third_kernel<R, NT, 5, kMaxSupport>;
+      else if (a.kmin == 5 && a.kmax == kMaxSupport)
+        kt = max_support <= 6 ? exact_third_kernel<R, NT, 5, 6> : exact_third_kernel<R, NT, 5, kMaxSupport>;
     }
     int64_t gk = grid;
     if (kt != k) {
