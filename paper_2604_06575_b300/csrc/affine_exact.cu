@@ -1136,11 +1136,14 @@ __global__ void __launch_bounds__(NT) exact_frame_kernel(StageArgs<R> a) {
 }
 
 // ------------------------------------------------------------------ stage 3
-// Resident CTAs a launch of the third stage is compiled for: the double-word
-// contraction of support sizes up to 4 needs fewer registers than that of 5..8.
+// Resident CTAs a launch of the third stage is compiled for, in double
+// words: seven (73 registers) over support sizes 1..4, six (85) over 5..6
+// (the bench batch's third stage: 47.0 ms at six, 47.5 at seven, 48.6 at five
+// and 51.8 at four), five for the generic launch whose out-of-line sizes 7
+// and 8 carry a large stack.
 template <typename R, int NT, int KHI>
 constexpr int third_min_blocks() {
-  return sizeof(R) == 4 ? 1024 / NT : std::is_same<R, dfloat>::value ? (KHI <= 4 ? 768 : 640) / NT : 1;
+  return sizeof(R) == 4 ? 1024 / NT : std::is_same<R, dfloat>::value ? (KHI <= 4 ? 896 : KHI <= 6 ? 768 : 640) / NT : 1;
 }
 // KLO..KHI: the support sizes compiled into this instantiation (a launch also
 // takes its range at run time, a.kmin..a.kmax, within them): a launch over one
