@@ -104,9 +104,8 @@ __device__ __forceinline__ void acc_add(T* p, T v) {
 __device__ __forceinline__ void acc_add(dfloat* p, dfloat v) { atomic_add_dw(p, v); }
 
 // Sum of one run of gather records c_r * m_t (the contributions to one
-// gradient or Hessian entry) in the form's arithmetic, and the magnitude of
-// one contribution (for the error scale).  Double words use the compensated
-// running sum of dfloat.cuh.
+// gradient or Hessian entry) in the form's arithmetic.  Double words use the
+// compensated running sum of dfloat.cuh.
 template <typename R>
 struct RunSum {
   R v = R(0);
@@ -115,13 +114,21 @@ struct RunSum {
 };
 template <>
 struct RunSum<dfloat> : dw_run_sum {};
+// |v| in the precision of the zero-gradient scale (a double word's high word)
+__device__ __forceinline__ double abs_of(double v) { return fabs(v); }
+__device__ __forceinline__ float abs_of(float v) { return fabsf(v); }
+__device__ __forceinline__ float abs_of(dfloat v) { return fabsf(v.hi); }
+
+// sum_i a_i / |x_i| over a term's active variables (ix = 1/x): times |c m_t|
+// it is the sum of the magnitudes of the term's gradient contributions
+// c a_i m_t / x_i, the scale of the zero-gradient test
 template <typename R>
-__device__ __forceinline__ AbsOf<R> contrib_abs(R m, SmallOf<R> cf) {
-  return AbsOf<R>(fabs(m * cf));
-}
-template <>
-__device__ __forceinline__ float contrib_abs<dfloat>(dfloat m, float cf) {
-  return fabsf(m.hi * cf);
+__device__ __forceinline__ AbsOf<R> grad_abs_factor(const TermRegs& t, const R* __restrict__ ix) {
+  AbsOf<R> s = AbsOf<R>(0);
+#pragma unroll
+  for (int k = 0; k < kMaxSupport; ++k)
+    if (t.exp[k]) s += AbsOf<R>(t.exp[k]) * abs_of(ix[t.var[k]]);
+  return s;
 }
 
 template <typename T>
@@ -372,8 +379,8 @@ struct Bump {
 // `in_smem` false: the n x n matrices live in global memory instead.
 
 struct Lay1 {
-  size_t pw, g, red, ix, gs, ga, mv, H, total;
-  size_t pw_step, ix_step, gs_step, ga_step, mv_step, H_step;  // offset between the two points' arrays
+  size_t pw, g, red, ix, gs, mv, H, total;
+  size_t pw_step, ix_step, gs_step, mv_step, H_step;  // offset between the two points' arrays
 };
 // Term sweep of up to kTermPoints points of one polynomial per CTA: power
 // tables, gather sums and monomial values (gather form) and H slots (in
@@ -396,10 +403,8 @@ __host__ __device__ Lay1 lay_terms(int n, int E1, bool in_smem, bool gather) {
   if (gather) {
     L.ix_step = ((size_t)n * sizeof(R) + 15) & ~size_t(15);
     L.gs_step = ((size_t)n * sizeof(Acc) + 15) & ~size_t(15);
-    L.ga_step = ((size_t)n * sizeof(Abs) + 15) & ~size_t(15);
     L.ix = b.take(kTermPoints * L.ix_step);
     L.gs = b.take(kTermPoints * L.gs_step);
-    L.ga = b.take(kTermPoints * L.ga_step);
     // monomial values of the points of a pass interleaved (value of point q
     // for chunk term t at [t * kTermPoints + q]): one vector load per record
     L.mv_step = sizeof(R);
@@ -582,7 +587,6 @@ __global__ void __launch_bounds__(NT, terms_min_blocks<R>(GATHER, NT)) exact_ter
       auto pw_of = [&](int q) { return (R*)(sm + L.pw + q * L.pw_step); };
       auto ix_of = [&](int q) { return (R*)(sm + L.ix + q * L.ix_step); };
       auto gs_of = [&](int q) { return (Acc*)(sm + L.gs + q * L.gs_step); };
-      auto ga_of = [&](int q) { return (Abs*)(sm + L.ga + q * L.ga_step); };
       R* mvi = (R*)(sm + L.mv);  // interleaved: [t * kTermPoints + q]
       auto Hg_of = [&](int q) { return a.mats_h + pd.mat_off + (p0 + q) * mat_slot<Acc>(n); };
       auto Hr_of = [&](int q) { return pd.h_in_smem ? (Acc*)(sm + L.H + q * L.H_step) : Hg_of(q); };
@@ -615,7 +619,6 @@ __global__ void __launch_bounds__(NT, terms_min_blocks<R>(GATHER, NT)) exact_ter
           for (int i = tid; i < n; i += NT) {
             ix_of(q)[i] = R(1) / R(X[i]);
             gs_of(q)[i] = Acc(0);
-            ga_of(q)[i] = Abs(0);
           }
         }
         power_table<R, NT>(X, n, E1, pw_of(q));
@@ -630,20 +633,17 @@ __global__ void __launch_bounds__(NT, terms_min_blocks<R>(GATHER, NT)) exact_ter
           constexpr int NP = decltype(np_c)::value;
           Acc* Hr[NP];
           Acc* gs[NP];
-          Abs* ga[NP];
   #pragma unroll
           for (int q = 0; q < NP; ++q) {
             Hr[q] = Hr_of(q);
             gs[q] = gs_of(q);
-            ga[q] = ga_of(q);
           }
-          auto flush = [&](int e, const RunSum<R>* acc, const Abs* aacc) {
+          auto flush = [&](int e, const RunSum<R>* acc) {
             if (e < 0 || e == (int)kGatherPad) return;  // nothing yet, or padding
   #pragma unroll
             for (int q = 0; q < NP; ++q) {
               if (e >= nn) {
                 acc_add(&gs[q][e - nn], acc[q].value());
-                atomicAdd(&ga[q][e - nn], aacc[q]);
               } else {
                 acc_add(&Hr[q][e], acc[q].value());
               }
@@ -653,8 +653,13 @@ __global__ void __launch_bounds__(NT, terms_min_blocks<R>(GATHER, NT)) exact_ter
             const int64_t t0 = (int64_t)c * kGatherChunk, t1 = min(pd.m, t0 + kGatherChunk);
             for (int64_t t = t0 + tid; t < t1; t += NT) {
               const TermRegs tr = load_term(pd.terms, t);
+              // the zero-gradient scale once per term, not per gradient record
   #pragma unroll
-              for (int q = 0; q < NP; ++q) mvi[(t - t0) * kTermPoints + q] = term_value<R>(tr, pw_of(q), E1);
+              for (int q = 0; q < NP; ++q) {
+                const R mv = term_value<R>(tr, pw_of(q), E1);
+                mvi[(t - t0) * kTermPoints + q] = mv;
+                gabs[q] += abs_of(mv) * grad_abs_factor<R>(tr, ix_of(q));
+              }
             }
             __syncthreads();
             const int64_t r0 = pd.gather_chunk[c];
@@ -663,7 +668,6 @@ __global__ void __launch_bounds__(NT, terms_min_blocks<R>(GATHER, NT)) exact_ter
             for (int st = tid; st < kGatherStreams; st += NT) {
               int cur = -1;
               RunSum<R> acc[NP];
-              Abs aacc[NP] = {};
               for (int k = 0; k < Lc; k += kGatherUnroll) {
                 uint32_t rr[kGatherUnroll];
   #pragma unroll
@@ -674,25 +678,18 @@ __global__ void __launch_bounds__(NT, terms_min_blocks<R>(GATHER, NT)) exact_ter
                   const SmallOf<R> cf = SmallOf<R>(rr[u] >> 25);  // falling-factorial coefficient <= 127
                   const int tt = (int)(rr[u] & 0x7ffu);
                   if (e != cur) {
-                    flush(cur, acc, aacc);
+                    flush(cur, acc);
                     cur = e;
   #pragma unroll
-                    for (int q = 0; q < NP; ++q) {
-                      acc[q] = RunSum<R>();
-                      aacc[q] = Abs(0);
-                    }
+                    for (int q = 0; q < NP; ++q) acc[q] = RunSum<R>();
                   }
                   R mvp[kTermPoints];
                   load_pair(mvi + tt * kTermPoints, mvp);
   #pragma unroll
-                  for (int q = 0; q < NP; ++q) {
-                    const R mq = mvp[q];
-                    acc[q].add(mq, cf);
-                    aacc[q] += contrib_abs<R>(mq, cf);
-                  }
+                  for (int q = 0; q < NP; ++q) acc[q].add(mvp[q], cf);
                 }
               }
-              flush(cur, acc, aacc);
+              flush(cur, acc);
             }
             __syncthreads();
           }
@@ -705,10 +702,7 @@ __global__ void __launch_bounds__(NT, terms_min_blocks<R>(GATHER, NT)) exact_ter
           for (int i = wid; i < n; i += NW)
             for (int j = i + lane; j < n; j += 32) Hr[i * n + j] = Acc(R(Hr[i * n + j]) * ix[i] * ix[j]);
           double* rec = rec_of(q);
-          for (int i = tid; i < n; i += NT) {
-            rec[i] = (double)(R(gs_of(q)[i]) * ix[i]);
-            gabs[q] += ga_of(q)[i] * Abs(fabs(ix[i]));
-          }
+          for (int i = tid; i < n; i += NT) rec[i] = (double)(R(gs_of(q)[i]) * ix[i]);
         }
       } else if constexpr (!GATHER) {
         for (int q = 0; q < np; ++q) {
