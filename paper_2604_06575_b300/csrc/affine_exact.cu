@@ -555,12 +555,25 @@ template <typename R>
 constexpr int terms_min_blocks(bool gather, int nt) {
   return (!gather ? 512 : sizeof(R) == 8 && !std::is_same<R, dfloat>::value ? 768 : 1024) / nt;
 }
+// The small integer c of a gather record in the form's multiplier type.
+template <typename R>
+__device__ __forceinline__ SmallOf<R> small_coef(uint32_t c, const double*) {
+  return SmallOf<R>(c);
+}
+template <>
+__device__ __forceinline__ double small_coef<double>(uint32_t c, const double* table) {
+  return table[c];
+}
+
 template <typename R, int NT, bool GATHER>
 __global__ void __launch_bounds__(NT, terms_min_blocks<R>(GATHER, NT)) exact_terms_kernel(StageArgs<R> a, PassList fl) {
   using Acc = AccOf<R>;
   using Abs = AbsOf<R>;
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ int64_t s_item;
+  __shared__ double s_cf[std::is_same<R, double>::value ? 128 : 1];  // c -> (double)c, c < 128
+  if constexpr (std::is_same<R, double>::value)
+    for (int i = threadIdx.x; i < 128; i += NT) s_cf[i] = (double)i;
   constexpr int NW = NT / 32;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   while (true) {
@@ -675,7 +688,9 @@ __global__ void __launch_bounds__(NT, terms_min_blocks<R>(GATHER, NT)) exact_ter
   #pragma unroll
                 for (int u = 0; u < kGatherUnroll; ++u) {
                   const int e = (int)((rr[u] >> 11) & 0x3fffu);
-                  const SmallOf<R> cf = SmallOf<R>(rr[u] >> 25);  // falling-factorial coefficient <= 127
+                  // falling-factorial coefficient <= 127 (FP64: from a table, keeping the
+                  // integer conversion off the FP64 pipe)
+                  const SmallOf<R> cf = small_coef<R>(rr[u] >> 25, s_cf);
                   const int tt = (int)(rr[u] & 0x7ffu);
                   if (e != cur) {
                     flush(cur, acc);
