@@ -382,41 +382,36 @@ struct Lay1 {
   size_t pw, g, red, ix, gs, mv, H, total;
   size_t pw_step, ix_step, gs_step, mv_step, H_step;  // offset between the two points' arrays
 };
-// Term sweep of up to kTermPoints points of one polynomial per CTA: power
-// tables, gather sums and monomial values (gather form) and H slots (in
-// shared memory) per point; the per-warp gradient replicas of the scatter
-// form are shared (points are swept one after another there).
+// Term sweep of up to `pts` (1 or kTermPoints) points of one polynomial per
+// CTA: power tables, gather sums and monomial values (gather form) and H
+// slots (in shared memory) per point; the per-warp gradient replicas of the
+// term-by-term form are shared (points are swept one after another there).
 // `gather`: room for the gather form (1/x, gradient sums, one chunk of
 // monomial values)
 constexpr int kTermPoints = 2;
 static_assert(kTermPoints == 2, "the sweep loads the points' monomial values as pairs");
 template <typename R, int NW>
-__host__ __device__ Lay1 lay_terms(int n, int E1, bool in_smem, bool gather) {
+__host__ __device__ Lay1 lay_terms(int n, int E1, bool in_smem, bool gather, int pts = kTermPoints) {
   using Acc = AccOf<R>;
   using Abs = AbsOf<R>;
   Lay1 L{};
   Bump b;
   L.pw_step = ((size_t)n * E1 * sizeof(R) + 15) & ~size_t(15);
-  L.pw = b.take(kTermPoints * L.pw_step);
+  L.pw = b.take(pts * L.pw_step);
   L.red = b.take(kTermPoints * 40 * 8);
   if (!gather) L.g = b.take((size_t)NW * n * sizeof(Acc));  // one replica per warp
   if (gather) {
     L.ix_step = ((size_t)n * sizeof(R) + 15) & ~size_t(15);
     L.gs_step = ((size_t)n * sizeof(Acc) + 15) & ~size_t(15);
-    L.ix = b.take(kTermPoints * L.ix_step);
-    L.gs = b.take(kTermPoints * L.gs_step);
+    L.ix = b.take(pts * L.ix_step);
+    L.gs = b.take(pts * L.gs_step);
     // monomial values of the points of a pass interleaved (value of point q
-    // for chunk term t at [t * kTermPoints + q]): one vector load per record
+    // for chunk term t at [t * pts + q]): one vector load per record
     L.mv_step = sizeof(R);
-    L.mv = b.take((size_t)kTermPoints * kGatherChunk * sizeof(R));
-    // a pass that falls back to the term-by-term sweep (a coordinate out of
-    // the gather range) uses no monomial values: its per-warp gradient
-    // replicas take their place
-    L.g = L.mv;
-    static_assert(kTermPoints * kGatherChunk * sizeof(R) >= 8 * 128 * sizeof(Acc), "replicas fit (n <= 127)");
+    L.mv = b.take((size_t)pts * kGatherChunk * sizeof(R));
   }
   L.H_step = (size_t)mat_slot<Acc>(n) * sizeof(Acc);
-  L.H = in_smem ? b.take(kTermPoints * L.H_step) : 0;
+  L.H = in_smem ? b.take(pts * L.H_step) : 0;
   L.total = b.o;
   return L;
 }
@@ -514,6 +509,7 @@ struct PassList {
   int64_t* pass;
   int* count;
   int cap;
+  int pts;  // points per pass of the gather launch (1 or kTermPoints)
 };
 
 __device__ __forceinline__ void write_failed(const ExactDesc& pd, int64_t p, int n, double gn, int flag) {
@@ -584,9 +580,9 @@ __global__ void __launch_bounds__(NT, terms_min_blocks<R>(GATHER, NT)) exact_ter
       pair = fl.pass[2 * idx];
       pair_end = pair + fl.pass[2 * idx + 1];
     } else {
-      pair = a.item_begin + (int64_t)kTermPoints * next_item(a.counter, &s_item);
+      pair = a.item_begin + (int64_t)fl.pts * next_item(a.counter, &s_item);
       if (pair >= a.item_end) break;
-      pair_end = min(pair + kTermPoints, a.item_end);
+      pair_end = min(pair + fl.pts, a.item_end);
     }
     int np = 0;
     for (int64_t item = pair; item < pair_end; item += np) {
@@ -596,11 +592,12 @@ __global__ void __launch_bounds__(NT, terms_min_blocks<R>(GATHER, NT)) exact_ter
       // the points of this pass: the rest of the pair within this polynomial
       np = (int)min(pair_end - item, pd.P - p0);
       const int n = pd.n, nn = n * n, E1 = pd.E + 1;
-      const Lay1 L = lay_terms<R, NW>(n, E1, pd.h_in_smem, GATHER);
+      const int pts = GATHER ? fl.pts : kTermPoints;
+      const Lay1 L = lay_terms<R, NW>(n, E1, pd.h_in_smem, GATHER, pts);
       auto pw_of = [&](int q) { return (R*)(sm + L.pw + q * L.pw_step); };
       auto ix_of = [&](int q) { return (R*)(sm + L.ix + q * L.ix_step); };
       auto gs_of = [&](int q) { return (Acc*)(sm + L.gs + q * L.gs_step); };
-      R* mvi = (R*)(sm + L.mv);  // interleaved: [t * kTermPoints + q]
+      R* mvi = (R*)(sm + L.mv);  // interleaved: [t * pts + q]
       auto Hg_of = [&](int q) { return a.mats_h + pd.mat_off + (p0 + q) * mat_slot<Acc>(n); };
       auto Hr_of = [&](int q) { return pd.h_in_smem ? (Acc*)(sm + L.H + q * L.H_step) : Hg_of(q); };
       auto rec_of = [&](int q) { return a.vecs + pd.vec_off + (p0 + q) * vrec(n); };
@@ -670,7 +667,7 @@ __global__ void __launch_bounds__(NT, terms_min_blocks<R>(GATHER, NT)) exact_ter
   #pragma unroll
               for (int q = 0; q < NP; ++q) {
                 const R mv = term_value<R>(tr, pw_of(q), E1);
-                mvi[(t - t0) * kTermPoints + q] = mv;
+                mvi[(t - t0) * pts + q] = mv;
                 gabs[q] += abs_of(mv) * grad_abs_factor<R>(tr, ix_of(q));
               }
             }
@@ -699,7 +696,8 @@ __global__ void __launch_bounds__(NT, terms_min_blocks<R>(GATHER, NT)) exact_ter
                     for (int q = 0; q < NP; ++q) acc[q] = RunSum<R>();
                   }
                   R mvp[kTermPoints];
-                  load_pair(mvi + tt * kTermPoints, mvp);
+                  if constexpr (NP == 2) load_pair(mvi + tt * kTermPoints, mvp);  // (pts = 2)
+                  else mvp[0] = mvi[tt * pts];
   #pragma unroll
                   for (int q = 0; q < NP; ++q) acc[q].add(mvp[q], cf);
                 }
@@ -1326,17 +1324,17 @@ namespace {
 constexpr size_t kSmemCap = 200 * 1024;
 
 template <typename R, int NW>
-size_t lay_bytes(int stage, int n, int E1, bool in_smem, bool gather) {
-  if (stage == 0) return lay_terms<R, NW>(n, E1, in_smem, gather).total;
+size_t lay_bytes(int stage, int n, int E1, bool in_smem, bool gather, int pts) {
+  if (stage == 0) return lay_terms<R, NW>(n, E1, in_smem, gather, pts).total;
   if (stage == 1) return lay_frame<R>(n, in_smem).total;
   return lay_third<R, NW>(n, E1, in_smem).total;
 }
 
 template <typename R>
-size_t stage_bytes(int stage, int threads, int n, int E1, bool in_smem, bool gather) {
-  if (threads == 64) return lay_bytes<R, 2>(stage, n, E1, in_smem, gather);
-  if (threads == 128) return lay_bytes<R, 4>(stage, n, E1, in_smem, gather);
-  return lay_bytes<R, 8>(stage, n, E1, in_smem, gather);
+size_t stage_bytes(int stage, int threads, int n, int E1, bool in_smem, bool gather, int pts = kTermPoints) {
+  if (threads == 64) return lay_bytes<R, 2>(stage, n, E1, in_smem, gather, pts);
+  if (threads == 128) return lay_bytes<R, 4>(stage, n, E1, in_smem, gather, pts);
+  return lay_bytes<R, 8>(stage, n, E1, in_smem, gather, pts);
 }
 
 }  // namespace
@@ -1348,6 +1346,7 @@ static polylab_status prepare_exact(ExactBatch* b) {
   int64_t mat = 0, vec = 0;
   b->frame_need.assign(b->host_descs.size(), 0);
   b->terms_need.assign(b->host_descs.size(), 0);
+  b->terms_need1.assign(b->host_descs.size(), 0);
   b->terms_fb_smem = 0;
   for (size_t di = 0; di < b->host_descs.size(); ++di) {
     ExactDesc& d = b->host_descs[di];
@@ -1367,6 +1366,7 @@ static polylab_status prepare_exact(ExactBatch* b) {
     b->frame_need[di] = need[1];
     // class-wise sweep: the gather launch (descriptors with records) and the term-by-term launch
     b->terms_need[di] = gat ? need[0] : 0;
+    b->terms_need1[di] = gat ? stage_bytes<R>(0, tt, d.n, E1, d.h_in_smem, true, 1) : 0;
     b->terms_fb_smem = std::max(b->terms_fb_smem, stage_bytes<R>(0, tt, d.n, E1, d.h_in_smem, false));
     if (!d.mats_in_smem) gstride = std::max(gstride, frame_gmem<R>(d.n));
     d.mat_off = mat;
@@ -1475,7 +1475,7 @@ static polylab_status launch_terms_classes(ExactBatch* b, cudaStream_t s) {
   a.err = b->err;
   a.kmin = 1;
   a.kmax = kMaxSupport;
-  const PassList fl{b->tfb, b->tfb_ctl, (int)b->tfb_cap};
+  PassList fl{b->tfb, b->tfb_ctl, (int)b->tfb_cap, kTermPoints};
   PL_CUDA(cudaMemsetAsync(b->tfb_ctl, 0, (2 + kFrameClasses) * sizeof(int), s));
   auto launch = [&](void (*k)(StageArgs<R>, PassList), size_t smem, int64_t items, int* counter) -> polylab_status {
     smem = std::max<size_t>(smem, 16);
@@ -1489,12 +1489,28 @@ static polylab_status launch_terms_classes(ExactBatch* b, cudaStream_t s) {
     k<<<(unsigned)grid, NT, smem, s>>>(a, fl);
     return launch_status("exact_terms_kernel");
   };
+  // resident CTAs of the gather kernel at `smem` bytes
+  auto resident = [&](size_t smem) -> int {
+    smem = std::max<size_t>(smem, 16);
+    int r = 0;
+    if (cudaFuncSetAttribute(exact_terms_kernel<R, NT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, exact_terms_kernel<R, NT, true>, NT, smem) != cudaSuccess)
+      return 0;
+    return r;
+  };
   for (int c = 0; c < kFrameClasses; ++c) {
     const FrameClass& fc = b->fclass[c];
     if (fc.end <= fc.begin) continue;
     a.item_begin = fc.begin;
     a.item_end = fc.end;
-    PL_TRY(launch(exact_terms_kernel<R, NT, true>, fc.tsmem, (fc.end - fc.begin + 1) / 2, b->tfb_ctl + 1 + c));
+    // one point per pass where that at least doubles the resident CTAs (the
+    // shared memory of two points' Hessian slots limits a class of large n);
+    // two otherwise, each record then decoded once for both
+    fl.pts = kTermPoints;
+    if (fc.tsmem1 > 0 && resident(fc.tsmem1) >= 2 * std::max(1, resident(fc.tsmem))) fl.pts = 1;
+    PL_TRY(launch(exact_terms_kernel<R, NT, true>, fl.pts == 1 ? fc.tsmem1 : fc.tsmem,
+                  (fc.end - fc.begin + fl.pts - 1) / fl.pts, b->tfb_ctl + 1 + c));
   }
   a.item_begin = 0;
   a.item_end = b->total;

@@ -51,7 +51,8 @@ struct FrameClass {
   int n_lo, n_hi, threads;
   int64_t begin = 0, end = 0;
   size_t smem = 0;
-  size_t tsmem = 0;  // the gradient/Hessian sweep's gather launch over the same class
+  size_t tsmem = 0;   // the gradient/Hessian sweep's gather launch over the same class (two points per pass)
+  size_t tsmem1 = 0;  // the same at one point per pass
 };
 
 struct ExactBatch {
@@ -80,7 +81,7 @@ struct ExactBatch {
   // the gradient/Hessian sweep by class of n: per-descriptor
   // shared memory of its gather launch, that of the term-by-term launch, the
   // list of passes left to it and [count, one work counter per launch]
-  std::vector<size_t> terms_need;
+  std::vector<size_t> terms_need, terms_need1;  // (two and one points per pass)
   size_t terms_fb_smem = 0;
   int64_t* tfb = nullptr;
   int64_t tfb_cap = 0;
