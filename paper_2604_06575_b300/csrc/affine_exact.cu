@@ -1504,11 +1504,11 @@ static polylab_status launch_terms_classes(ExactBatch* b, cudaStream_t s) {
     if (fc.end <= fc.begin) continue;
     a.item_begin = fc.begin;
     a.item_end = fc.end;
-    // one point per pass where that at least doubles the resident CTAs (the
-    // shared memory of two points' Hessian slots limits a class of large n);
+    // one point per pass where that raises the resident CTAs (the shared
+    // memory of two points' Hessian slots limits the classes of larger n);
     // two otherwise, each record then decoded once for both
     fl.pts = kTermPoints;
-    if (fc.tsmem1 > 0 && resident(fc.tsmem1) >= 2 * std::max(1, resident(fc.tsmem))) fl.pts = 1;
+    if (fc.tsmem1 > 0 && resident(fc.tsmem1) > resident(fc.tsmem)) fl.pts = 1;
     PL_TRY(launch(exact_terms_kernel<R, NT, true>, fl.pts == 1 ? fc.tsmem1 : fc.tsmem,
                   (fc.end - fc.begin + fl.pts - 1) / fl.pts, b->tfb_ctl + 1 + c));
   }
