@@ -388,7 +388,7 @@ typedef struct {
   int32_t frame_split;
   int32_t third_threads;  /* CTA size of the third-derivative sweep (64, 128 or 256) */
   /* third_split (1..4): the third-derivative sweep as that many launches over
-   * ranges of term support sizes ({1..8}; {1..4},{5..8}; {1..3},{4},{5..8};
+   * ranges of term support sizes ({1..8}; {1..4},{5..8}; {1..4},{5},{6..8};
    * {1..3},{4},{5},{6..8}), each contracting its terms into the point's
    * partial trace term and the last forming the direction: every launch then
    * runs one support size's code at a time on all SMs (instruction-cache

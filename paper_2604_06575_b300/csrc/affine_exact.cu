@@ -1421,7 +1421,7 @@ static polylab_status launch_stage_t(ExactBatch* b, int stage, cudaStream_t s) {
   // the third stage as one launch per range of support sizes, in order
   static const int kRanges[4][4][2] = {{{1, kMaxSupport}},
                                        {{1, 4}, {5, kMaxSupport}},
-                                       {{1, 3}, {4, 4}, {5, kMaxSupport}},
+                                       {{1, 4}, {5, 5}, {6, kMaxSupport}},
                                        {{1, 3}, {4, 4}, {5, 5}, {6, kMaxSupport}}};
   const int split = std::min(4, std::max(1, b->cfg.third_split));
   int max_support = 0;
@@ -1429,14 +1429,19 @@ static polylab_status launch_stage_t(ExactBatch* b, int stage, cudaStream_t s) {
   for (int g = 0; g < split; ++g) {
     a.kmin = kRanges[split - 1][g][0];
     a.kmax = kRanges[split - 1][g][1];
-    // the double-word form has instantiations for the two-launch ranges, the
-    // second without the (out-of-line) support sizes 7 and 8 when the batch
-    // has no such terms
+    // the double-word form has instantiations for the ranges of two and
+    // three launches, the last without the (out-of-line) support sizes 7 and
+    // 8 when the batch has no such terms: a launch carries only its own
+    // sizes' (large, unrolled) code (four launches, with generic kernels for
+    // 1..3 and 4, measured slower: 46.6 against 45.5 ms)
     void (*kt)(StageArgs<R>) = k;
     if constexpr (std::is_same<R, dfloat>::value) {
       if (a.kmin == 1 && a.kmax == 4) kt = exact_third_kernel<R, NT, 1, 4>;
+      else if (a.kmin == 5 && a.kmax == 5) kt = exact_third_kernel<R, NT, 5, 5>;
       else if (a.kmin == 5 && a.kmax == kMaxSupport)
         kt = max_support <= 6 ? exact_third_kernel<R, NT, 5, 6> : exact_third_kernel<R, NT, 5, kMaxSupport>;
+      else if (a.kmin == 6 && a.kmax == kMaxSupport)
+        kt = max_support <= 6 ? exact_third_kernel<R, NT, 6, 6> : exact_third_kernel<R, NT, 6, kMaxSupport>;
     }
     int64_t gk = grid;
     if (kt != k) {
