@@ -438,10 +438,14 @@ __host__ __device__ Lay2 lay_frame(int n, bool in_smem) {
   L.h = b.take(n * 8);
   L.dv = b.take(m * 8);      // LDL^T pivots d_k
   L.di = b.take(m * 8);      // 1 / d_k
-  L.uc = b.take((in_smem ? 2 : 4) * m * 8);  // unscaled pivot columns (two buffers; four for the pairs form)
   L.vr = b.take(n * sizeof(R));
   L.u = b.take(n * sizeof(R));
   L.w = b.take(n * sizeof(R));
+  // unscaled pivot columns (two buffers; four for the pairs form).  With
+  // 8-byte values the two buffers of the shared-memory form live in u and w
+  // (2 x 8n bytes >= 2 x 8m), which the factorisation leaves unused: one
+  // more CTA per SM at n = 60 (seven instead of six)
+  L.uc = (in_smem && sizeof(R) == 8) ? L.u : b.take((in_smem ? 2 : 4) * m * 8);
   if (in_smem) {
     L.Hr = b.take((size_t)mat_slot<R>(n) * sizeof(R));
     // FP32 form: FP64 factor in a packed column-major lower triangle, whose
