@@ -674,13 +674,13 @@ def main():
 def stage_launches(cfg: dict, polys, Xs) -> dict:
     """Kernel launches of one run per stage: the gradient/Hessian sweep as one
     gather launch per non-empty class of n (n > 40, 24 < n <= 40, n <= 24) plus
-    one term-by-term launch, one third-stage launch per range of support sizes
-    (third_split) and, with frame_split, one frame launch per non-empty
-    class."""
+    one term-by-term launch, the third-derivative sweep as one launch per range
+    of support sizes (third_split) and class, and, with frame_split, one frame
+    launch per class."""
     ns = [p.n for p, X in zip(polys, Xs) if X.shape[0] > 0]
     classes = sum(1 for lo, hi in ((40, 1 << 30), (24, 40), (0, 24)) if any(lo < n <= hi for n in ns))
     frame = classes if cfg.get("frame_split", 0) else 1
-    return dict(terms=classes + 1, frame=frame, third=int(cfg.get("third_split", 1)))
+    return dict(terms=classes + 1, frame=frame, third=int(cfg.get("third_split", 1)) * classes)
 
 
 def measure_rows(pl, workloads, torch, dev, p32, p64, only=None):

@@ -392,7 +392,9 @@ typedef struct {
    * {1..3},{4},{5},{6..8}), each contracting its terms into the point's
    * partial trace term and the last forming the direction: every launch then
    * runs one support size's code at a time on all SMs (instruction-cache
-   * locality), at the price of loading W once per launch. */
+   * locality), at the price of loading W once per launch.  Each range runs as
+   * one launch per class of n of the frame stage (n > 40, 24 < n <= 40,
+   * n <= 24), each sized for its class's shared memory. */
   int32_t third_split;
 } polylab_batch_config;
 

@@ -1349,6 +1349,7 @@ static polylab_status prepare_exact(ExactBatch* b) {
   size_t smem[3] = {0, 0, 0}, gstride = 0;
   int64_t mat = 0, vec = 0;
   b->frame_need.assign(b->host_descs.size(), 0);
+  b->third_need.assign(b->host_descs.size(), 0);
   b->terms_need.assign(b->host_descs.size(), 0);
   b->terms_need1.assign(b->host_descs.size(), 0);
   b->terms_fb_smem = 0;
@@ -1368,6 +1369,7 @@ static polylab_status prepare_exact(ExactBatch* b) {
       smem[st] = std::max(smem[st], need[st]);
     }
     b->frame_need[di] = need[1];
+    b->third_need[di] = need[2];
     // class-wise sweep: the gather launch (descriptors with records) and the term-by-term launch
     b->terms_need[di] = gat ? need[0] : 0;
     b->terms_need1[di] = gat ? stage_bytes<R>(0, tt, d.n, E1, d.h_in_smem, true, 1) : 0;
@@ -1447,19 +1449,29 @@ static polylab_status launch_stage_t(ExactBatch* b, int stage, cudaStream_t s) {
       else if (a.kmin == 6 && a.kmax == kMaxSupport)
         kt = max_support <= 6 ? exact_third_kernel<R, NT, 6, 6> : exact_third_kernel<R, NT, 6, kMaxSupport>;
     }
-    int64_t gk = grid;
-    if (kt != k) {
-      PL_CUDA(cudaFuncSetAttribute(kt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // within a range, one launch per class of n of the frame stage (frame
+    // order), each with its own class's shared memory: a launch over all
+    // polynomials reserved the largest n's W for every CTA
+    a.prefix = b->fprefix;
+    a.order = b->forder;
+    for (int c = 0; c < kFrameClasses; ++c) {
+      const FrameClass& fc = b->fclass[c];
+      if (fc.end <= fc.begin) continue;
+      const size_t sm3 = std::max<size_t>(fc.t3smem, 16);
+      PL_CUDA(cudaFuncSetAttribute(kt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
       int psm = 0;
-      PL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&psm, kt, NT, smem));
+      PL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&psm, kt, NT, sm3));
       psm = std::max(1, psm);
       if (cap > 0) psm = std::min(psm, cap);
-      gk = std::max<int64_t>(1, std::min<int64_t>(i1 - i0, (int64_t)num_sms() * psm));
+      const int64_t gk = std::max<int64_t>(1, std::min<int64_t>(fc.end - fc.begin, (int64_t)num_sms() * psm));
+      a.item_begin = fc.begin;
+      a.item_end = fc.end;
+      PL_CUDA(cudaMemsetAsync(a.counter, 0, sizeof(int), s));
+      kt<<<(unsigned)gk, NT, sm3, s>>>(a);
+      PL_TRY(launch_status("exact_third_kernel"));
     }
-    PL_CUDA(cudaMemsetAsync(a.counter, 0, sizeof(int), s));
-    kt<<<(unsigned)gk, NT, smem, s>>>(a);
-    PL_TRY(launch_status("exact_third_kernel"));
   }
+  (void)grid;
   return POLYLAB_OK;
 }
 

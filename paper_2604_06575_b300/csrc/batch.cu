@@ -58,12 +58,14 @@ void exact_frame_classes(ExactBatch* b) {
     fc.smem = 0;
     fc.tsmem = 0;
     fc.tsmem1 = 0;
+    fc.t3smem = 0;
     fc.begin = b->host_fprefix.empty() ? 0 : b->host_fprefix[i];
     while (i < n && b->host_descs[b->host_forder[i]].n > fc.n_lo) {
       const size_t d = (size_t)b->host_forder[i];
       fc.smem = std::max(fc.smem, d < b->frame_need.size() ? b->frame_need[d] : 0);
       fc.tsmem = std::max(fc.tsmem, d < b->terms_need.size() ? b->terms_need[d] : 0);
       fc.tsmem1 = std::max(fc.tsmem1, d < b->terms_need1.size() ? b->terms_need1[d] : 0);
+      fc.t3smem = std::max(fc.t3smem, d < b->third_need.size() ? b->third_need[d] : 0);
       ++i;
     }
     fc.end = b->host_fprefix.empty() ? 0 : b->host_fprefix[i];

@@ -53,6 +53,7 @@ struct FrameClass {
   size_t smem = 0;
   size_t tsmem = 0;   // the gradient/Hessian sweep's gather launch over the same class (two points per pass)
   size_t tsmem1 = 0;  // the same at one point per pass
+  size_t t3smem = 0;  // the third-derivative sweep's launches over the same class
 };
 
 struct ExactBatch {
@@ -71,7 +72,7 @@ struct ExactBatch {
   size_t smem[3] = {0, 0, 0};
   // split frame stage: per-descriptor frame-stage shared memory, the frame
   // work order and prefix (host and DEVICE), the classes, one counter each
-  std::vector<size_t> frame_need;
+  std::vector<size_t> frame_need, third_need;
   std::vector<int> host_forder;
   std::vector<int64_t> host_fprefix;
   int* forder = nullptr;

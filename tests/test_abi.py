@@ -58,10 +58,10 @@ def test_bench_counts_launches_per_step():
     rng = np.random.default_rng(0)
     polys = [workloads.convexified(rng, n, workloads.sparse_monomials(rng, n, 20, 3, 2), 0.1) for n in (5, 30, 50)]
     Xs = [np.zeros((4, p.n)) for p in polys]
-    assert bench.stage_launches(dict(frame_split=1), polys, Xs) == dict(terms=4, frame=3, third=1)
+    assert bench.stage_launches(dict(frame_split=1), polys, Xs) == dict(terms=4, frame=3, third=3)
     assert bench.stage_launches(dict(frame_split=1), polys[:1], Xs[:1]) == dict(terms=2, frame=1, third=1)
-    assert bench.stage_launches(dict(frame_split=0), polys, Xs) == dict(terms=4, frame=1, third=1)
-    assert bench.stage_launches(dict(frame_split=1, third_split=2), polys, Xs) == dict(terms=4, frame=3, third=2)
+    assert bench.stage_launches(dict(frame_split=0), polys, Xs) == dict(terms=4, frame=1, third=3)
+    assert bench.stage_launches(dict(frame_split=1, third_split=2), polys, Xs) == dict(terms=4, frame=3, third=6)
 
 
 def test_header_is_plain_c(tmp_path):
