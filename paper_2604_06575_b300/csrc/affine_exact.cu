@@ -1159,8 +1159,10 @@ constexpr int third_min_blocks() {
 // KLO..KHI: the support sizes compiled into this instantiation (a launch also
 // takes its range at run time, a.kmin..a.kmax, within them): a launch over one
 // range carries only that range's code.
-template <typename R, int NT, int KLO = 1, int KHI = kMaxSupport>
-__global__ void __launch_bounds__(NT, third_min_blocks<R, NT, KHI>()) exact_third_kernel(StageArgs<R> a) {
+// MB > 0: that many resident CTAs instead (the classes of smaller n, whose
+// shared memory allows more than the register budget of the default).
+template <typename R, int NT, int KLO = 1, int KHI = kMaxSupport, int MB = 0>
+__global__ void __launch_bounds__(NT, MB > 0 ? MB : third_min_blocks<R, NT, KHI>()) exact_third_kernel(StageArgs<R> a) {
   using Acc = AccOf<R>;
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ int64_t s_item;
@@ -1458,16 +1460,22 @@ static polylab_status launch_stage_t(ExactBatch* b, int stage, cudaStream_t s) {
       const FrameClass& fc = b->fclass[c];
       if (fc.end <= fc.begin) continue;
       const size_t sm3 = std::max<size_t>(fc.t3smem, 16);
-      PL_CUDA(cudaFuncSetAttribute(kt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
+      void (*kc)(StageArgs<R>) = kt;
+      if constexpr (std::is_same<R, dfloat>::value && NT == 128) {
+        // sizes 5 and 6 at seven CTAs per SM where the class's shared memory allows them
+        if (c > 0 && kt == exact_third_kernel<R, NT, 5, 5>) kc = exact_third_kernel<R, NT, 5, 5, 7>;
+        if (c > 0 && kt == exact_third_kernel<R, NT, 6, 6>) kc = exact_third_kernel<R, NT, 6, 6, 7>;
+      }
+      PL_CUDA(cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
       int psm = 0;
-      PL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&psm, kt, NT, sm3));
+      PL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&psm, kc, NT, sm3));
       psm = std::max(1, psm);
       if (cap > 0) psm = std::min(psm, cap);
       const int64_t gk = std::max<int64_t>(1, std::min<int64_t>(fc.end - fc.begin, (int64_t)num_sms() * psm));
       a.item_begin = fc.begin;
       a.item_end = fc.end;
       PL_CUDA(cudaMemsetAsync(a.counter, 0, sizeof(int), s));
-      kt<<<(unsigned)gk, NT, sm3, s>>>(a);
+      kc<<<(unsigned)gk, NT, sm3, s>>>(a);
       PL_TRY(launch_status("exact_third_kernel"));
     }
   }
