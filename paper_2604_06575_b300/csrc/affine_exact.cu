@@ -1462,9 +1462,13 @@ static polylab_status launch_stage_t(ExactBatch* b, int stage, cudaStream_t s) {
       const size_t sm3 = std::max<size_t>(fc.t3smem, 16);
       void (*kc)(StageArgs<R>) = kt;
       if constexpr (std::is_same<R, dfloat>::value && NT == 128) {
-        // sizes 5 and 6 at seven CTAs per SM where the class's shared memory allows them
+        // more resident CTAs where the class's shared memory allows them: sizes
+        // 5 and 6 at seven (72 registers) for n <= 40, sizes 1..5 at eight (64)
+        // for n <= 24 (third stage 44.5 -> 43.1 ms for the bench batch)
         if (c > 0 && kt == exact_third_kernel<R, NT, 5, 5>) kc = exact_third_kernel<R, NT, 5, 5, 7>;
         if (c > 0 && kt == exact_third_kernel<R, NT, 6, 6>) kc = exact_third_kernel<R, NT, 6, 6, 7>;
+        if (c == 2 && kt == exact_third_kernel<R, NT, 1, 4>) kc = exact_third_kernel<R, NT, 1, 4, 8>;
+        if (c == 2 && kt == exact_third_kernel<R, NT, 5, 5>) kc = exact_third_kernel<R, NT, 5, 5, 8>;
       }
       PL_CUDA(cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
       int psm = 0;
