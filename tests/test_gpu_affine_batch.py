@@ -114,3 +114,28 @@ def test_autotune_configs_agree_and_graph_replay(pl, batch_inputs):
     b.check()
     for d, r in zip(b.D, ref):
         close(d, r, TOL["fp64"])
+
+
+def test_double_word_third_stage_ranges_agree(pl, batch_inputs):
+    """The double-word third stage in one to four launches over ranges of
+    support sizes (a kernel per range, one launch per class of n, the classes
+    of smaller n at more resident CTAs) gives the FP64 form's directions within
+    the double-word form's bar (relative 1e-9 on nu); a batch whose terms reach
+    support 8 takes the kernels that keep support sizes 7 and 8."""
+    rng = np.random.default_rng(23)
+    wide = workloads.convexified(rng, 12, workloads.sparse_monomials(rng, 12, 300, 8, 8), 0.1)
+    assert int((wide.exps > 0).sum(axis=1).max()) >= 7
+    cases = [batch_inputs, ([wide], [workloads.shell_points(rng, 12, 96)])]
+    for polys, Xs in cases:
+        dps = [pl.to_device(p) for p in polys]
+        Xd = [torch.as_tensor(X, device="cuda") for X in Xs]
+        ref = pl.Batch(dps, [None] * len(dps), Xd, pl.an_opts(prec="fp64", regularization=1e-6))
+        ref.run()
+        ref.check()
+        b = pl.Batch(dps, [None] * len(dps), Xd, pl.an_opts(prec="f32x2", regularization=1e-6))
+        for split in (1, 2, 3, 4):
+            b.set_config(128, 0, 1, term_threads=256, frame_split=1, third_threads=128, third_split=split)
+            b.run()
+            b.check()
+            for d, r in zip(b.D, ref.D):
+                close(d, r, 1e-9)
