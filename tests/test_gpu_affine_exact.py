@@ -171,6 +171,23 @@ def test_gather_and_term_by_term_sweeps_agree(pl, prec):
                 assert np.radians(affine.angle_deg(D[i], nu)) <= 2e-5 * max(kap, 1.0), i
 
 
+@pytest.mark.parametrize("prec", ["fp64", "f32x2"])
+def test_gather_and_term_by_term_sweeps_agree_large_n(pl, prec):
+    """The same at n = 50 (the class of n > 40, whose gather launch takes one
+    point per pass in double words): the passes with a zero or tiny coordinate
+    go through the list to the term-by-term launch; all points against the
+    oracle."""
+    rng = np.random.default_rng(78)
+    n = 50
+    poly = workloads.convexified(rng, n, workloads.sparse_monomials(rng, n, 400, 6, 5), 0.1)
+    X = workloads.shell_points(rng, n, 20)
+    X[0:4, 3] = 0.0
+    X[7:11, 41] = 1e-7
+    D, Du, info = run(pl, poly, X, regularization=1e-6, prec=prec)
+    ref = oracle_all(poly, X, 1e-6, third="contract")
+    assert compare(poly, X, D, info, ref, 1e-6) == 0
+
+
 @pytest.mark.parametrize("n,prec", [(131, "fp64"), (132, "fp64"), (131, "f32x2"), (132, "f32x2"), (171, "fp32")])
 def test_global_memory_frame_both_parities(pl, n, prec):
     """Matrices too large for shared memory take the frame stage's global-memory
